@@ -1,0 +1,343 @@
+"""FP64 CPU oracle for ANTS2 maximum-likelihood reconstruction.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU
+baseline leg of ``bench.py`` are the only users.  The product library never
+imports, links or runs anything here, and this package imports nothing from
+the product.  The arithmetic lives in ``ants_oracle.c`` (plain C, FP64, built
+with gcc without fast-math); this module only marshals numpy arrays.
+
+Functions follow the paper (Morozov et al., arXiv:1602.07247):
+  cog            Sec. 5.1.1 centroid equation
+  cgs            Sec. 5.1.2 / 5.1.2.2 ML contracting grids, E = sum s / sum eta
+  cgs_replay     the same search replayed along another implementation's
+                 chosen nodes, with the tie-certification rule
+  lrf_fit        Sec. 6 B-spline LRFs fitted to (position, value) data
+  lrf_eval       Sec. 6.1.1 / 6.1.2 axial, XY and XYZ LRFs, Sec. 6.2 grouping
+  bspline_*      uniform cubic B-spline basis (Cox-de Boor)
+Parity pins live in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ants_oracle.c")
+
+RADIAL, XY, XYZ = 1, 2, 3
+EVT_OK, EVT_ZERO_SIGNAL, EVT_BAD_SIGNAL, EVT_OUT_OF_DOMAIN = 0, 2, 3, 4
+TAU_REL = 8.0 * 2.0 ** -24
+
+
+def _so_path(mutant: int = 0) -> str:
+    name = "liboracle.so" if mutant == 0 else f"liboracle_m{mutant}.so"
+    return os.path.join(_HERE, "_build", name)
+
+
+def build(mutant: int = 0, force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast-math, OpenMP when present)."""
+    out = _so_path(mutant)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", f"-DOR_MUTANT={mutant}"]
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = base + ["-fopenmp", _SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:  # no OpenMP runtime: build single-threaded
+        r = subprocess.run(base + [_SRC, "-o", tmp, "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, out)
+    return out
+
+
+_libs: dict[int, C.CDLL] = {}
+
+
+def lib(mutant: int = 0) -> C.CDLL:
+    if mutant not in _libs:
+        L = C.CDLL(build(mutant))
+        _declare(L)
+        _libs[mutant] = L
+    return _libs[mutant]
+
+
+class _Lrf(C.Structure):
+    _fields_ = [
+        ("type", C.c_int),
+        ("n_sensors", C.c_int),
+        ("n_int", C.c_int * 3),
+        ("lo", C.c_double * 3),
+        ("hi", C.c_double * 3),
+        ("shared", C.c_int),
+        ("coef", C.POINTER(C.c_double)),
+        ("gain", C.POINTER(C.c_double)),
+        ("sensor_xy", C.POINTER(C.c_double)),
+    ]
+
+
+class _Cgs(C.Structure):
+    _fields_ = [
+        ("n_xy", C.c_int),
+        ("n_z", C.c_int),
+        ("iters", C.c_int),
+        ("shrink", C.c_double),
+        ("step_xy", C.c_double),
+        ("step_z", C.c_double),
+        ("z0", C.c_double),
+    ]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def _declare(L: C.CDLL) -> None:
+    L.or_bspline_basis_all.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _D]
+    L.or_bspline_basis_all.restype = C.c_int
+    L.or_bspline_basis4.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _D]
+    L.or_bspline_basis4.restype = C.c_int
+    L.or_lrf_eval.argtypes = [C.POINTER(_Lrf), C.c_long, _D, C.c_int, _D]
+    L.or_spline_eval.argtypes = [C.c_int, _I, _D, _D, _D, C.c_long, _D, _D]
+    L.or_lrf_fit.argtypes = [C.c_int, _I, _D, _D, C.c_long, _D, C.c_int, _D, C.c_double, _D, _D]
+    L.or_lrf_fit.restype = C.c_int
+    L.or_cog.argtypes = [C.c_long, C.c_int, _D, _D, _D, _D]
+    L.or_objective_at.argtypes = [C.POINTER(_Lrf), C.c_long, _D, _D, _D]
+    L.or_energy_logl_at.argtypes = [C.POINTER(_Lrf), C.c_long, _D, _D, _D, _D]
+    L.or_logl_at_energy.argtypes = [C.POINTER(_Lrf), _D, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.or_logl_at_energy.restype = C.c_double
+    L.or_cgs.argtypes = [C.POINTER(_Lrf), C.POINTER(_Cgs), _D, _D, C.c_long, _D, _D, _D, _D, _I, _I]
+    L.or_cgs_replay.argtypes = [C.POINTER(_Lrf), C.POINTER(_Cgs), _D, _D, C.c_long, _D, _I, C.c_double,
+                                _D, _D, _D, _I, _I, _I]
+    L.or_brute_force.argtypes = [C.POINTER(_Lrf), C.c_long, _D, C.c_double, C.c_double, C.c_int,
+                                 C.c_double, C.c_double, C.c_int, C.c_double, _D, _D]
+    L.or_num_threads.restype = C.c_int
+
+
+def _d(a: np.ndarray) -> C.POINTER(C.c_double):
+    return a.ctypes.data_as(_D)
+
+
+def _i(a: np.ndarray) -> C.POINTER(C.c_int):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# data model
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Lrf:
+    """A set of LRFs: type, per-axis knot grid and FP64 coefficients.
+
+    coef has shape [n_sets, n_coef]; n_sets is 1 for a shared radial LRF
+    (Sec. 6.2 "one group"), else n_sensors.  Coefficients are stored x
+    fastest, then y, then z.  gain multiplies a radial LRF per sensor.
+    """
+
+    type: int
+    sensor_xy: np.ndarray
+    n_int: tuple
+    lo: tuple
+    hi: tuple
+    coef: np.ndarray
+    shared: bool = False
+    gain: np.ndarray | None = None
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def n_sensors(self) -> int:
+        return int(self.sensor_xy.shape[0])
+
+    def _struct(self) -> _Lrf:
+        s = _Lrf()
+        s.type = self.type
+        s.n_sensors = self.n_sensors
+        dims = 1 if self.type == RADIAL else (2 if self.type == XY else 3)
+        for a in range(3):
+            s.n_int[a] = int(self.n_int[a]) if a < dims else 0
+            s.lo[a] = float(self.lo[a]) if a < dims else 0.0
+            s.hi[a] = float(self.hi[a]) if a < dims else 0.0
+        s.shared = 1 if self.shared else 0
+        coef = _f64(self.coef)
+        sxy = _f64(self.sensor_xy)
+        gain = _f64(self.gain) if self.gain is not None else None
+        self._keep[:] = [coef, sxy, gain]
+        s.coef = _d(coef)
+        s.sensor_xy = _d(sxy)
+        s.gain = _d(gain) if gain is not None else C.cast(None, _D)
+        return s
+
+
+@dataclass
+class CgsParams:
+    n_xy: int
+    iters: int
+    step_xy: float
+    shrink: float = 0.5
+    n_z: int = 1
+    step_z: float = 0.0
+    z0: float = 0.0
+
+    def _struct(self) -> _Cgs:
+        p = _Cgs()
+        p.n_xy, p.n_z, p.iters = self.n_xy, self.n_z, self.iters
+        p.shrink, p.step_xy, p.step_z, p.z0 = self.shrink, self.step_xy, self.step_z, self.z0
+        return p
+
+
+# --------------------------------------------------------------------------
+# wrappers
+# --------------------------------------------------------------------------
+
+
+def bspline_basis_all(n_int: int, lo: float, hi: float, x: float, mutant: int = 0):
+    B = np.zeros(n_int + 3)
+    m = lib(mutant).or_bspline_basis_all(n_int, lo, hi, x, _d(B))
+    return m, B
+
+
+def bspline_basis4(n_int: int, lo: float, hi: float, x: float, mutant: int = 0):
+    B = np.zeros(4)
+    j0 = lib(mutant).or_bspline_basis4(n_int, lo, hi, x, _d(B))
+    return j0, B
+
+
+def spline_eval(n_int, lo, hi, coef, pts, mutant: int = 0) -> np.ndarray:
+    pts = _f64(pts)
+    dim = pts.shape[1]
+    ni = np.ascontiguousarray(np.asarray(n_int, dtype=np.int32))
+    out = np.empty(pts.shape[0])
+    lib(mutant).or_spline_eval(dim, _i(ni), _d(_f64(lo)), _d(_f64(hi)), _d(_f64(coef)), pts.shape[0],
+                               _d(pts), _d(out))
+    return out
+
+
+def lrf_fit(n_int, lo, hi, pts, vals, ridge: float = 0.0, mutant: int = 0):
+    """Least-squares B-spline fit; returns (coef[n_out, n_coef], rc, lambda)."""
+    pts = _f64(pts)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    vals = _f64(vals)
+    if vals.ndim == 1:
+        vals = vals[:, None]
+    dim = pts.shape[1]
+    ni = np.ascontiguousarray(np.asarray(n_int[:dim], dtype=np.int32))
+    nc = int(np.prod([n + 3 for n in ni]))
+    coef = np.zeros((vals.shape[1], nc))
+    lam = np.zeros(1)
+    rc = lib(mutant).or_lrf_fit(dim, _i(ni), _d(_f64(lo[:dim])), _d(_f64(hi[:dim])), pts.shape[0],
+                                _d(pts), vals.shape[1], _d(vals), float(ridge), _d(coef), _d(lam))
+    if rc < 0:
+        raise RuntimeError("oracle LRF fit failed")
+    return coef, rc, float(lam[0])
+
+
+def lrf_eval(lrf: Lrf, pts, mutant: int = 0) -> np.ndarray:
+    pts = _f64(pts)
+    s = lrf._struct()
+    out = np.empty((pts.shape[0], lrf.n_sensors))
+    lib(mutant).or_lrf_eval(C.byref(s), pts.shape[0], _d(pts), pts.shape[1], _d(out))
+    return out
+
+
+def cog(sig, sensor_xy, gain=None, mutant: int = 0) -> np.ndarray:
+    sig = _f64(sig)
+    out = np.empty((sig.shape[0], 2))
+    g = _f64(gain) if gain is not None else None
+    lib(mutant).or_cog(sig.shape[0], sig.shape[1], _d(sig), _d(_f64(sensor_xy)),
+                       _d(g) if g is not None else C.cast(None, _D), _d(out))
+    return out
+
+
+def objective_at(lrf: Lrf, sig, xyz, mutant: int = 0) -> np.ndarray:
+    sig, xyz = _f64(sig), _f64(xyz)
+    s = lrf._struct()
+    out = np.empty(sig.shape[0])
+    lib(mutant).or_objective_at(C.byref(s), sig.shape[0], _d(sig), _d(xyz), _d(out))
+    return out
+
+
+def energy_logl_at(lrf: Lrf, sig, xyz, mutant: int = 0):
+    sig, xyz = _f64(sig), _f64(xyz)
+    s = lrf._struct()
+    E = np.empty(sig.shape[0])
+    L = np.empty(sig.shape[0])
+    lib(mutant).or_energy_logl_at(C.byref(s), sig.shape[0], _d(sig), _d(xyz), _d(E), _d(L))
+    return E, L
+
+
+def logl_at_energy(lrf: Lrf, s, xyz, E: float, mutant: int = 0) -> float:
+    s = _f64(s)
+    st = lrf._struct()
+    return float(lib(mutant).or_logl_at_energy(C.byref(st), _d(s), float(xyz[0]), float(xyz[1]),
+                                               float(xyz[2]), float(E)))
+
+
+def _opt(a):
+    return _f64(a) if a is not None else None
+
+
+def _p(a):
+    return _d(a) if a is not None else C.cast(None, _D)
+
+
+def cgs(lrf: Lrf, params: CgsParams, sig, gain_cog=None, start_xyz=None, mutant: int = 0):
+    """Plain contracting-grid ML search.  Returns dict of xyz, E, logL,
+    status and trace (chosen flat node index per grid).  start_xyz [n, 3]
+    replaces the COG start when given."""
+    sig = _f64(sig)
+    n = sig.shape[0]
+    s, p = lrf._struct(), params._struct()
+    xyz = np.empty((n, 3))
+    E = np.empty(n)
+    logL = np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    trace = np.empty((n, params.iters), dtype=np.int32)
+    g, st = _opt(gain_cog), _opt(start_xyz)
+    lib(mutant).or_cgs(C.byref(s), C.byref(p), _p(g), _p(st), n, _d(sig), _d(xyz), _d(E), _d(logL),
+                       _i(status), _i(trace))
+    return dict(xyz=xyz, E=E, logL=logL, status=status, trace=trace)
+
+
+def cgs_replay(lrf: Lrf, params: CgsParams, sig, trace, gain_cog=None, start_xyz=None,
+               tau_rel: float = TAU_REL, mutant: int = 0):
+    sig = _f64(sig)
+    n = sig.shape[0]
+    tr = np.ascontiguousarray(np.asarray(trace, dtype=np.int32))
+    s, p = lrf._struct(), params._struct()
+    xyz = np.empty((n, 3))
+    E = np.empty(n)
+    logL = np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    n_tie = np.empty(n, dtype=np.int32)
+    n_bad = np.empty(n, dtype=np.int32)
+    g, st = _opt(gain_cog), _opt(start_xyz)
+    lib(mutant).or_cgs_replay(C.byref(s), C.byref(p), _p(g), _p(st), n, _d(sig), _i(tr), float(tau_rel), _d(xyz), _d(E), _d(logL), _i(status),
+                              _i(n_tie), _i(n_bad))
+    return dict(xyz=xyz, E=E, logL=logL, status=status, n_tie=n_tie, n_bad=n_bad)
+
+
+def brute_force(lrf: Lrf, sig, x_rng, nx, y_rng, ny, z=0.0, mutant: int = 0):
+    sig = _f64(sig)
+    n = sig.shape[0]
+    s = lrf._struct()
+    xy = np.empty((n, 2))
+    F = np.empty(n)
+    lib(mutant).or_brute_force(C.byref(s), n, _d(sig), float(x_rng[0]), float(x_rng[1]), int(nx),
+                               float(y_rng[0]), float(y_rng[1]), int(ny), float(z), _d(xy), _d(F))
+    return xy, F
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())

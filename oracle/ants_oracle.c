@@ -1,0 +1,731 @@
+/*
+ * ants_oracle.c -- plain, slow FP64 CPU oracle for the maximum-likelihood
+ * position/energy reconstruction of ANTS2 (Morozov et al., arXiv:1602.07247).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * loads this file; only the test suite, the smoke check and the CPU baseline
+ * leg of the benchmark do.  It shares no code, header, table or constant
+ * with the CUDA path.
+ *
+ * What it follows (paper sections):
+ *   - Sec. 5.1.1, centroid (COG) equation: x = sum X_i S_i/g_i / sum S_i/g_i.
+ *   - Sec. 5.1.2, statistical reconstruction: best match between measured
+ *     signals and LRF-model signals by Maximum Likelihood.
+ *   - Sec. 5.1.2.2, contracting grids: regular grid centred on the start
+ *     position, best node becomes the centre of a finer grid with the same
+ *     node count, fixed number of iterations; the energy at each node is the
+ *     ratio (sum of signals) / (sum of LRF values).
+ *   - Sec. 6 / 6.1.1 / 6.1.2, LRFs are B-spline parameterised functions of
+ *     1 (axial), 2 (XY) or 3 (XYZ) coordinates, computed from datasets of
+ *     (position, signal) pairs; Sec. 6.2, one group = one shared LRF times a
+ *     per-sensor relative gain.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - B-spline: uniform cubic on [lo,hi] with n intervals, n+3 basis
+ *     functions on the extended knots t_j = lo + (j-3)h; evaluated with the
+ *     Cox-de Boor recursion; x == hi uses the last interval.
+ *   - LRF fit: least squares by the normal equations (B^T B + lambda I) c =
+ *     B^T v solved with a Cholesky factorisation; lambda = 0 unless the matrix
+ *     is not positive definite, then lambda = 1e-10 * trace / n_coef.
+ *   - Likelihood: Poisson, mu_i = E eta_i(x).  At fixed x the ML energy is
+ *     E = S/H (S = sum s_i, H = sum eta_i), which is the ratio of Sec. 5.1.2.2;
+ *     substituting it, the search maximises F(x) = sum s_i ln eta_i - S ln H.
+ *     eta_i <= 1e-30 is replaced by 1e-30.
+ *   - Contracting grid: N x N (x N_z) nodes, flat index (iz, iy, ix) row
+ *     major, node = centre + (index - (N-1)/2) * step; step *= shrink after
+ *     each iteration; nodes outside the LRF domain score -inf; ties go to the
+ *     lowest flat index; the result is the best node of the last grid.
+ *   - Start: COG with the detector's relative gains, clamped into the XY
+ *     domain of an XY/XYZ LRF; z starts at a given z0.
+ *   - Reported logL: sum_i [ s_i ln mu_i - mu_i - lgamma(s_i+1) ] at the
+ *     result, with s_i = 0 terms equal to -mu_i.
+ *
+ * Every function is a direct transcription of a definition; no blocking,
+ * fusion or reordering is done beyond what the definition states.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_RADIAL 1
+#define OR_XY 2
+#define OR_XYZ 3
+
+#define OR_EVT_OK 0
+#define OR_EVT_ZERO_SIGNAL 2
+#define OR_EVT_BAD_SIGNAL 3
+#define OR_EVT_OUT_OF_DOMAIN 4
+
+#define OR_ETA_FLOOR 1e-30
+
+/* Optional planted mistakes, used only by the test that shows the pins catch
+ * them.  OR_MUTANT == 0 (the default build) is the oracle itself. */
+#ifndef OR_MUTANT
+#define OR_MUTANT 0
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Uniform cubic B-splines (Cox-de Boor recursion)                           */
+/* ------------------------------------------------------------------------ */
+
+/* Knot t_j of the extended uniform knot vector, j = 0 .. n+6. */
+static double or_knot(int n_int, double lo, double hi, int j)
+{
+    double h = (hi - lo) / (double)n_int;
+    return lo + (double)(j - 3) * h;
+}
+
+/* Knot span m (3 <= m <= n+2) with t_m <= x < t_{m+1}; x == hi is put into
+ * the last span.  Returns -1 when x lies outside [lo, hi]. */
+static int or_span(int n_int, double lo, double hi, double x)
+{
+    if (!(x >= lo && x <= hi)) return -1;
+    if (x == hi) return n_int + 2;
+    /* first guess from the uniform spacing, then settle it by comparing
+     * against the knots themselves */
+    int m = 3 + (int)floor((x - lo) / ((hi - lo) / (double)n_int));
+    if (m < 3) m = 3;
+    if (m > n_int + 2) m = n_int + 2;
+    while (m > 3 && x < or_knot(n_int, lo, hi, m)) --m;
+    while (m < n_int + 2 && x >= or_knot(n_int, lo, hi, m + 1)) ++m;
+    return m;
+}
+
+/* All n+3 cubic basis values B_{j,3}(x), j = 0..n+2, by the full Cox-de Boor
+ * recursion B_{j,0} = [t_j <= x < t_{j+1}],
+ * B_{j,k} = (x - t_j)/(t_{j+k} - t_j) B_{j,k-1}
+ *         + (t_{j+k+1} - x)/(t_{j+k+1} - t_{j+1}) B_{j+1,k-1}.
+ * Returns the span m, or -1 (all zeros) when x is outside [lo, hi]. */
+int or_bspline_basis_all(int n_int, double lo, double hi, double x, double *B)
+{
+    int nk = n_int + 7;        /* knots */
+    int nb0 = nk - 1;          /* degree-0 functions */
+    double *N = (double *)calloc((size_t)nb0, sizeof(double));
+    int m = or_span(n_int, lo, hi, x);
+    for (int j = 0; j < n_int + 3; ++j) B[j] = 0.0;
+    if (m < 0) { free(N); return -1; }
+    N[m] = 1.0;
+    for (int k = 1; k <= 3; ++k) {
+        for (int j = 0; j + k < nb0; ++j) {
+            double tj = or_knot(n_int, lo, hi, j);
+            double tjk = or_knot(n_int, lo, hi, j + k);
+            double tj1 = or_knot(n_int, lo, hi, j + 1);
+            double tjk1 = or_knot(n_int, lo, hi, j + k + 1);
+            double left = (x - tj) / (tjk - tj) * N[j];
+#if OR_MUTANT == 2
+            double right = (x - tjk1) / (tjk1 - tj1) * N[j + 1];
+#else
+            double right = (tjk1 - x) / (tjk1 - tj1) * N[j + 1];
+#endif
+            N[j] = left + right;
+        }
+    }
+    for (int j = 0; j < n_int + 3; ++j) B[j] = N[j];
+    free(N);
+    return m;
+}
+
+/* The four basis functions that can be non-zero at x, B_{m-3..m,3}(x), by
+ * the same recursion restricted to the triangle of non-zero terms (the
+ * support of B_{j,3} is [t_j, t_{j+4})).  Returns the index m-3 of the first
+ * one (0 .. n-1), or -1 when x is outside [lo, hi]. */
+int or_bspline_basis4(int n_int, double lo, double hi, double x, double B[4])
+{
+    double full[4][4];
+    int m = or_span(n_int, lo, hi, x);
+    if (m < 0) return -1;
+    /* full[k][r] holds B_{m-k+r, k}(x), r = 0..k */
+    full[0][0] = 1.0;
+    for (int k = 1; k <= 3; ++k) {
+        for (int r = 0; r <= k; ++r) {
+            int j = m - k + r;
+            double v = 0.0;
+            if (r >= 1) { /* B_{j,k-1} term: exists when j >= m-k+1 */
+                double tj = or_knot(n_int, lo, hi, j);
+#if OR_MUTANT == 9
+                double tjk = or_knot(n_int, lo, hi, j + k + 1);
+#else
+                double tjk = or_knot(n_int, lo, hi, j + k);
+#endif
+                v += (x - tj) / (tjk - tj) * full[k - 1][r - 1];
+            }
+            if (r <= k - 1) { /* B_{j+1,k-1} term */
+                double tj1 = or_knot(n_int, lo, hi, j + 1);
+                double tjk1 = or_knot(n_int, lo, hi, j + k + 1);
+                v += (tjk1 - x) / (tjk1 - tj1) * full[k - 1][r];
+            }
+            full[k][r] = v;
+        }
+    }
+    for (int r = 0; r < 4; ++r) B[r] = full[3][r];
+    return m - 3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Light response functions (Sec. 6, 6.1, 6.2)                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int type;               /* OR_RADIAL, OR_XY, OR_XYZ */
+    int n_sensors;
+    int n_int[3];           /* intervals per axis (radial: axis 0 = r) */
+    double lo[3], hi[3];    /* domain per axis */
+    int shared;             /* radial only: one coefficient set for all sensors */
+    const double *coef;     /* [n_sets][n_coef], x fastest, then y, then z */
+    const double *gain;     /* [n_sensors] relative gain on a radial LRF; NULL = 1 */
+    const double *sensor_xy;/* [n_sensors][2] sensor centres (mm) */
+} or_lrf;
+
+static int or_n_coef(const or_lrf *L)
+{
+    if (L->type == OR_RADIAL) return L->n_int[0] + 3;
+    if (L->type == OR_XY) return (L->n_int[0] + 3) * (L->n_int[1] + 3);
+    return (L->n_int[0] + 3) * (L->n_int[1] + 3) * (L->n_int[2] + 3);
+}
+
+/* eta_i at (x, y, z) from the B-spline expansion.  *ok = 0 when the point
+ * lies outside the LRF's domain for this sensor. */
+static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, int *ok)
+{
+    int nc = or_n_coef(L);
+    *ok = 1;
+    if (L->type == OR_RADIAL) {
+        const double *c = L->coef + (size_t)(L->shared ? 0 : i) * nc;
+        double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+        double r = sqrt(dx * dx + dy * dy);
+        double B[4];
+        int j0 = or_bspline_basis4(L->n_int[0], L->lo[0], L->hi[0], r, B);
+        if (j0 < 0) { *ok = 0; return 0.0; }
+        double f = 0.0;
+        for (int a = 0; a < 4; ++a) f += c[j0 + a] * B[a];
+        double g = L->gain ? L->gain[i] : 1.0;
+        return g * f;
+    }
+    const double *c = L->coef + (size_t)i * nc;
+    double Bx[4], By[4], Bz[4] = {1.0, 0.0, 0.0, 0.0};
+    int jx = or_bspline_basis4(L->n_int[0], L->lo[0], L->hi[0], x, Bx);
+    int jy = or_bspline_basis4(L->n_int[1], L->lo[1], L->hi[1], y, By);
+    int jz = 0, nz = 1;
+    if (L->type == OR_XYZ) {
+        jz = or_bspline_basis4(L->n_int[2], L->lo[2], L->hi[2], z, Bz);
+        nz = 4;
+    }
+    if (jx < 0 || jy < 0 || jz < 0) { *ok = 0; return 0.0; }
+    int sx = L->n_int[0] + 3, sy = L->n_int[1] + 3;
+    double f = 0.0;
+    for (int cz = 0; cz < nz; ++cz)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+#if OR_MUTANT == 3
+                size_t idx = ((size_t)(jz + cz) * sy + (size_t)(jx + a)) * sx + (size_t)(jy + b);
+#else
+                size_t idx = ((size_t)(jz + cz) * sy + (size_t)(jy + b)) * sx + (size_t)(jx + a);
+#endif
+                f += c[idx] * Bx[a] * By[b] * Bz[cz];
+            }
+    return f;
+}
+
+/* eta for every (point, sensor): out[p * n_sensors + i]; NaN outside. */
+void or_lrf_eval(const or_lrf *L, long n_pts, const double *pts, int dim, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < n_pts; ++p) {
+        double x = pts[p * dim], y = dim > 1 ? pts[p * dim + 1] : 0.0;
+        double z = dim > 2 ? pts[p * dim + 2] : 0.0;
+        for (int i = 0; i < L->n_sensors; ++i) {
+            int ok;
+            double v = or_lrf_eta(L, i, x, y, z, &ok);
+            out[p * L->n_sensors + i] = ok ? v : NAN;
+        }
+    }
+}
+
+/* Value of one B-spline expansion (no sensor geometry) at d-dim points:
+ * f(p) = sum c_{j..} B_j(p_x) B_k(p_y) [B_l(p_z)].  Used to check fits. */
+void or_spline_eval(int dim, const int *n_int, const double *lo, const double *hi,
+                    const double *coef, long n_pts, const double *pts, double *out)
+{
+    for (long p = 0; p < n_pts; ++p) {
+        double B[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
+        int j0[3] = {0, 0, 0}, nn[3] = {1, 1, 1}, st[3] = {1, 1, 1};
+        int bad = 0;
+        for (int a = 0; a < dim; ++a) {
+            j0[a] = or_bspline_basis4(n_int[a], lo[a], hi[a], pts[p * dim + a], B[a]);
+            if (j0[a] < 0) bad = 1;
+            nn[a] = 4;
+        }
+        if (bad) { out[p] = NAN; continue; }
+        st[0] = 1;
+        st[1] = n_int[0] + 3;
+        st[2] = (n_int[0] + 3) * (dim > 1 ? n_int[1] + 3 : 1);
+        double f = 0.0;
+        for (int c = 0; c < nn[2]; ++c)
+            for (int b = 0; b < nn[1]; ++b)
+                for (int a = 0; a < nn[0]; ++a)
+                    f += coef[(size_t)(j0[0] + a) * st[0] + (size_t)(j0[1] + b) * st[1] +
+                              (size_t)(j0[2] + c) * st[2]] * B[0][a] * B[1][b] * B[2][c];
+        out[p] = f;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Least-squares B-spline fit (Sec. 6: LRFs computed from (position, signal) */
+/* datasets); normal equations + Cholesky, FP64.                             */
+/* ------------------------------------------------------------------------ */
+
+/* Cholesky A = L L^T in place (lower triangle).  Returns 0, or -1 when a
+ * pivot is not positive. */
+static int or_cholesky(int n, double *A)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0.0)) return -1;
+        double ljj = sqrt(d);
+        A[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[(size_t)i * n + j];
+#if OR_MUTANT == 8
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)k * n + j];
+#else
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+#endif
+            A[(size_t)i * n + j] = v / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Solve L L^T x = b in place. */
+static void or_cholesky_solve(int n, const double *Lm, double *b)
+{
+    for (int i = 0; i < n; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= Lm[(size_t)i * n + k] * b[k];
+        b[i] = v / Lm[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int k = i + 1; k < n; ++k) v -= Lm[(size_t)k * n + i] * b[k];
+        b[i] = v / Lm[(size_t)i * n + i];
+    }
+}
+
+/* Fit coefficients of a dim-dimensional tensor-product cubic B-spline to
+ * n_out value sets sampled at the same n_pts points:
+ *   minimise sum_p (f(p) - v[p][o])^2  for each o.
+ * coef_out[o][n_coef].  Returns 0 (plain solve), 1 (ridge retry used) or
+ * -1 (failure).  *ridge_used receives the lambda that was applied. */
+int or_lrf_fit(int dim, const int *n_int, const double *lo, const double *hi,
+               long n_pts, const double *pts, int n_out, const double *vals,
+               double ridge, double *coef_out, double *ridge_used)
+{
+    int st[3] = {1, 1, 1}, nc = 1;
+    for (int a = 0; a < dim; ++a) nc *= n_int[a] + 3;
+    st[1] = n_int[0] + 3;
+    st[2] = (n_int[0] + 3) * (dim > 1 ? n_int[1] + 3 : 1);
+    double *A = (double *)calloc((size_t)nc * nc, sizeof(double));
+    double *Bv = (double *)calloc((size_t)nc * n_out, sizeof(double));
+    double *A0 = (double *)malloc((size_t)nc * nc * sizeof(double));
+    if (!A || !Bv || !A0) { free(A); free(Bv); free(A0); return -1; }
+    int nterm = 1;
+    for (int a = 0; a < dim; ++a) nterm *= 4;
+    int *idx = (int *)malloc(sizeof(int) * nterm);
+    double *w = (double *)malloc(sizeof(double) * nterm);
+    /* Assemble B^T B and B^T v from the non-zero basis products of each point. */
+    for (long p = 0; p < n_pts; ++p) {
+        double B[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
+        int j0[3] = {0, 0, 0}, nn[3] = {1, 1, 1}, bad = 0;
+        for (int a = 0; a < dim; ++a) {
+            j0[a] = or_bspline_basis4(n_int[a], lo[a], hi[a], pts[p * dim + a], B[a]);
+            if (j0[a] < 0) bad = 1;
+            nn[a] = 4;
+        }
+        if (bad) continue; /* samples outside the domain carry no information */
+        int t = 0;
+        for (int c = 0; c < nn[2]; ++c)
+            for (int b = 0; b < nn[1]; ++b)
+                for (int a = 0; a < nn[0]; ++a) {
+                    idx[t] = (j0[0] + a) * st[0] + (j0[1] + b) * st[1] + (j0[2] + c) * st[2];
+                    w[t] = B[0][a] * B[1][b] * B[2][c];
+                    ++t;
+                }
+        for (int u = 0; u < t; ++u) {
+            for (int v = 0; v < t; ++v) A[(size_t)idx[u] * nc + idx[v]] += w[u] * w[v];
+            for (int o = 0; o < n_out; ++o) Bv[(size_t)o * nc + idx[u]] += w[u] * vals[(size_t)p * n_out + o];
+        }
+    }
+    free(idx);
+    free(w);
+    memcpy(A0, A, (size_t)nc * nc * sizeof(double));
+    double lam = ridge;
+    int rc = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        memcpy(A, A0, (size_t)nc * nc * sizeof(double));
+        for (int j = 0; j < nc; ++j) A[(size_t)j * nc + j] += lam;
+        if (or_cholesky(nc, A) == 0) break;
+        if (attempt == 1) { rc = -1; break; }
+        double tr = 0.0;
+        for (int j = 0; j < nc; ++j) tr += A0[(size_t)j * nc + j];
+        lam = 1e-10 * tr / (double)nc;
+        rc = 1;
+    }
+    if (rc >= 0) {
+        for (int o = 0; o < n_out; ++o) {
+            memcpy(coef_out + (size_t)o * nc, Bv + (size_t)o * nc, sizeof(double) * nc);
+            or_cholesky_solve(nc, A, coef_out + (size_t)o * nc);
+        }
+    }
+    if (ridge_used) *ridge_used = lam;
+    free(A);
+    free(A0);
+    free(Bv);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Centroid (Sec. 5.1.1)                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* x = sum X_i s_i/g_i / sum s_i/g_i (and y).  Returns the denominator. */
+static double or_cog1(int n_s, const double *s, const double *sensor_xy, const double *gain,
+                      double *x, double *y)
+{
+    double num_x = 0.0, num_y = 0.0, den = 0.0;
+    for (int i = 0; i < n_s; ++i) {
+        double g = gain ? gain[i] : 1.0;
+#if OR_MUTANT == 4
+        double w = s[i];
+        (void)g;
+#else
+        double w = s[i] / g;
+#endif
+        num_x += sensor_xy[2 * i] * w;
+        num_y += sensor_xy[2 * i + 1] * w;
+        den += w;
+    }
+    *x = num_x / den;
+    *y = num_y / den;
+    return den;
+}
+
+void or_cog(long n_e, int n_s, const double *sig, const double *sensor_xy, const double *gain,
+            double *out_xy)
+{
+    for (long e = 0; e < n_e; ++e)
+        or_cog1(n_s, sig + e * n_s, sensor_xy, gain, &out_xy[2 * e], &out_xy[2 * e + 1]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Likelihood (Sec. 5.1.2, energy ratio of Sec. 5.1.2.2)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Whether a node is inside the LRF's domain. */
+static int or_node_valid(const or_lrf *L, double x, double y, double z)
+{
+    if (L->type == OR_RADIAL) {
+        for (int i = 0; i < L->n_sensors; ++i) {
+            double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r >= L->lo[0] && r <= L->hi[0])) return 0;
+        }
+        return 1;
+    }
+    if (!(x >= L->lo[0] && x <= L->hi[0] && y >= L->lo[1] && y <= L->hi[1])) return 0;
+    if (L->type == OR_XYZ && !(z >= L->lo[2] && z <= L->hi[2])) return 0;
+    return 1;
+}
+
+static double or_eta_floored(const or_lrf *L, int i, double x, double y, double z)
+{
+    int ok;
+    double v = or_lrf_eta(L, i, x, y, z, &ok);
+    return v > OR_ETA_FLOOR ? v : OR_ETA_FLOOR;
+}
+
+/* Profiled objective F = sum s_i ln eta_i - S ln H; -inf outside the domain. */
+static double or_objective(const or_lrf *L, const double *s, double S, double x, double y, double z)
+{
+    if (!or_node_valid(L, x, y, z)) return -INFINITY;
+    double acc = 0.0, H = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        double eta = or_eta_floored(L, i, x, y, z);
+        if (s[i] != 0.0) acc += s[i] * log(eta);
+        H += eta;
+    }
+#if OR_MUTANT == 1
+    (void)S;
+    return acc;
+#else
+    return acc - S * log(H);
+#endif
+}
+
+/* ML energy E = S / H and the full Poisson log-likelihood at (x, y, z). */
+static void or_energy_logl(const or_lrf *L, const double *s, double x, double y, double z,
+                           double *E_out, double *logL_out)
+{
+    double S = 0.0, H = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        S += s[i];
+        H += or_eta_floored(L, i, x, y, z);
+    }
+#if OR_MUTANT == 6
+    double E = H / S;
+#else
+    double E = S / H;
+#endif
+    double ll = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        double mu = E * or_eta_floored(L, i, x, y, z);
+#if OR_MUTANT == 7
+        ll += (s[i] != 0.0 ? s[i] * log(mu) : 0.0) - mu - lgamma(s[i]);
+#else
+        ll += (s[i] != 0.0 ? s[i] * log(mu) : 0.0) - mu - lgamma(s[i] + 1.0);
+#endif
+    }
+    *E_out = E;
+    *logL_out = ll;
+}
+
+/* Full Poisson logL at an arbitrary energy, for the tests that check the
+ * profiled energy is the maximiser. */
+double or_logl_at_energy(const or_lrf *L, const double *s, double x, double y, double z, double E)
+{
+    double ll = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        double mu = E * or_eta_floored(L, i, x, y, z);
+        ll += (s[i] != 0.0 ? s[i] * log(mu) : 0.0) - mu - lgamma(s[i] + 1.0);
+    }
+    return ll;
+}
+
+/* F at given points, one per event: out[e]. */
+void or_objective_at(const or_lrf *L, long n_e, const double *sig, const double *xyz, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        double S = 0.0;
+        for (int i = 0; i < L->n_sensors; ++i) S += s[i];
+        out[e] = or_objective(L, s, S, xyz[3 * e], xyz[3 * e + 1], xyz[3 * e + 2]);
+    }
+}
+
+/* E and full logL at given points, one per event. */
+void or_energy_logl_at(const or_lrf *L, long n_e, const double *sig, const double *xyz,
+                       double *E, double *logL)
+{
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < n_e; ++e)
+        or_energy_logl(L, sig + e * L->n_sensors, xyz[3 * e], xyz[3 * e + 1], xyz[3 * e + 2],
+                       &E[e], &logL[e]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Contracting grids (Sec. 5.1.2.2)                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int n_xy;       /* nodes per axis in x and y (odd) */
+    int n_z;        /* nodes along z (odd; 1 for 2D LRFs) */
+    int iters;      /* number of grids */
+    double shrink;  /* step factor between grids */
+    double step_xy; /* first grid's node spacing in x and y */
+    double step_z;  /* first grid's node spacing in z */
+    double z0;      /* start z for XYZ LRFs */
+} or_cgs_params;
+
+/* Start position: the given one when start_xyz is not NULL, else the COG
+ * clamped into the LRF's XY box (XY/XYZ) with z = z0.  Returns an event
+ * status. */
+static int or_start(const or_lrf *L, const or_cgs_params *P, const double *gain_cog,
+                    const double *start_xyz, const double *s, double *cx, double *cy, double *cz,
+                    double *S_out)
+{
+    double S = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        if (!isfinite(s[i]) || s[i] < 0.0) return OR_EVT_BAD_SIGNAL;
+        S += s[i];
+    }
+    *S_out = S;
+    if (!(S > 0.0)) return OR_EVT_ZERO_SIGNAL;
+    if (start_xyz) {
+        *cx = start_xyz[0];
+        *cy = start_xyz[1];
+        *cz = start_xyz[2];
+        if (!or_node_valid(L, *cx, *cy, *cz)) return OR_EVT_OUT_OF_DOMAIN;
+        return OR_EVT_OK;
+    }
+    or_cog1(L->n_sensors, s, L->sensor_xy, gain_cog, cx, cy);
+    *cz = (L->type == OR_XYZ) ? P->z0 : 0.0;
+    if (L->type != OR_RADIAL) {
+        if (*cx < L->lo[0]) *cx = L->lo[0];
+        if (*cx > L->hi[0]) *cx = L->hi[0];
+        if (*cy < L->lo[1]) *cy = L->lo[1];
+        if (*cy > L->hi[1]) *cy = L->hi[1];
+    }
+    if (!or_node_valid(L, *cx, *cy, *cz)) return OR_EVT_OUT_OF_DOMAIN;
+    return OR_EVT_OK;
+}
+
+/* Node coordinates of flat index k on the grid centred at (cx, cy, cz). */
+static void or_node(const or_cgs_params *P, double cx, double cy, double cz, double sxy, double sz,
+                    int k, double *x, double *y, double *z)
+{
+    int n = P->n_xy, c = (P->n_xy - 1) / 2, cz_i = (P->n_z - 1) / 2;
+    int ix = k % n, iy = (k / n) % n, iz = k / (n * n);
+    *x = cx + (double)(ix - c) * sxy;
+    *y = cy + (double)(iy - c) * sxy;
+    *z = cz + (double)(iz - cz_i) * sz;
+}
+
+static void or_set_nan(double *xyz, double *E, double *logL)
+{
+    xyz[0] = xyz[1] = xyz[2] = NAN;
+    *E = NAN;
+    *logL = NAN;
+}
+
+/* Plain contracting-grid search for each event.  start_xyz[e][3] gives the
+ * start positions (nullable: COG).  trace[e][it] receives the flat index of
+ * the chosen node of grid it (nullable). */
+void or_cgs(const or_lrf *L, const or_cgs_params *P, const double *gain_cog,
+            const double *start_xyz, long n_e, const double *sig, double *xyz, double *E,
+            double *logL, int *status, int *trace)
+{
+    int nodes = P->n_xy * P->n_xy * P->n_z;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        double cx, cy, cz, S;
+        int st = or_start(L, P, gain_cog, start_xyz ? start_xyz + 3 * e : NULL, s, &cx, &cy, &cz,
+                          &S);
+        status[e] = st;
+        if (st != OR_EVT_OK) {
+            or_set_nan(&xyz[3 * e], &E[e], &logL[e]);
+            if (trace) for (int it = 0; it < P->iters; ++it) trace[e * P->iters + it] = -1;
+            continue;
+        }
+        double sxy = P->step_xy, sz = P->step_z;
+        for (int it = 0; it < P->iters; ++it) {
+            double best = -INFINITY;
+            int best_k = -1;
+            for (int k = 0; k < nodes; ++k) {
+                double x, y, z;
+                or_node(P, cx, cy, cz, sxy, sz, k, &x, &y, &z);
+                double F = or_objective(L, s, S, x, y, z);
+#if OR_MUTANT == 5
+                if (F >= best) { best = F; best_k = k; }
+#else
+                if (F > best) { best = F; best_k = k; }
+#endif
+            }
+            double x, y, z;
+            or_node(P, cx, cy, cz, sxy, sz, best_k, &x, &y, &z);
+            cx = x; cy = y; cz = z;
+            if (trace) trace[e * P->iters + it] = best_k;
+            sxy *= P->shrink;
+            sz *= P->shrink;
+        }
+        xyz[3 * e] = cx;
+        xyz[3 * e + 1] = cy;
+        xyz[3 * e + 2] = cz;
+        or_energy_logl(L, s, cx, cy, cz, &E[e], &logL[e]);
+    }
+}
+
+/* Replay of another implementation's path (its chosen node per grid, in
+ * trace_in) with the tie-certification rule: at every grid the chosen node
+ * must score within tau = tau_rel * sum_i |s_i ln p_i(centre)| of the FP64
+ * best node (p_i = eta_i / H), and it must lie in the domain.  The replay
+ * continues from the chosen node.  Per event: n_tie = grids where the
+ * choice was not the FP64 best but within tau; n_bad = grids where it was
+ * outside tau or invalid; xyz/E/logL = FP64 values at the replayed end. */
+void or_cgs_replay(const or_lrf *L, const or_cgs_params *P, const double *gain_cog,
+                   const double *start_xyz, long n_e, const double *sig, const int *trace_in, double tau_rel, double *xyz, double *E,
+                   double *logL, int *status, int *n_tie, int *n_bad)
+{
+    int nodes = P->n_xy * P->n_xy * P->n_z;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        double cx, cy, cz, S;
+        int st = or_start(L, P, gain_cog, start_xyz ? start_xyz + 3 * e : NULL, s, &cx, &cy, &cz,
+                          &S);
+        status[e] = st;
+        n_tie[e] = 0;
+        n_bad[e] = 0;
+        if (st != OR_EVT_OK) { or_set_nan(&xyz[3 * e], &E[e], &logL[e]); continue; }
+        double sxy = P->step_xy, sz = P->step_z;
+        for (int it = 0; it < P->iters; ++it) {
+            double best = -INFINITY;
+            int best_k = -1;
+            for (int k = 0; k < nodes; ++k) {
+                double x, y, z;
+                or_node(P, cx, cy, cz, sxy, sz, k, &x, &y, &z);
+                double F = or_objective(L, s, S, x, y, z);
+                if (F > best) { best = F; best_k = k; }
+            }
+            int g = trace_in[e * P->iters + it];
+            if (g < 0 || g >= nodes) { n_bad[e]++; g = best_k; }
+            double gx, gy, gz;
+            or_node(P, cx, cy, cz, sxy, sz, g, &gx, &gy, &gz);
+            if (g != best_k) {
+                double Fg = or_objective(L, s, S, gx, gy, gz);
+                /* tau from the magnitude of the terms summed at the centre */
+                double H = 0.0, mag = 0.0;
+                for (int i = 0; i < L->n_sensors; ++i) H += or_eta_floored(L, i, cx, cy, cz);
+                for (int i = 0; i < L->n_sensors; ++i)
+                    mag += fabs(s[i] * log(or_eta_floored(L, i, cx, cy, cz) / H));
+                double tau = tau_rel * mag;
+                if (isfinite(Fg) && Fg >= best - tau) n_tie[e]++;
+                else n_bad[e]++;
+            }
+            cx = gx; cy = gy; cz = gz;
+            sxy *= P->shrink;
+            sz *= P->shrink;
+        }
+        xyz[3 * e] = cx;
+        xyz[3 * e + 1] = cy;
+        xyz[3 * e + 2] = cz;
+        or_energy_logl(L, s, cx, cy, cz, &E[e], &logL[e]);
+    }
+}
+
+/* Exhaustive search: the best node of a regular nx x ny grid over
+ * [x_lo, x_hi] x [y_lo, y_hi] at height z (ties to the lowest index). */
+void or_brute_force(const or_lrf *L, long n_e, const double *sig, double x_lo, double x_hi,
+                    int nx, double y_lo, double y_hi, int ny, double z, double *out_xy,
+                    double *out_F)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        double S = 0.0;
+        for (int i = 0; i < L->n_sensors; ++i) S += s[i];
+        double best = -INFINITY, bx = NAN, by = NAN;
+        for (int k = 0; k < ny; ++k)
+            for (int j = 0; j < nx; ++j) {
+                double x = x_lo + (x_hi - x_lo) * (double)j / (double)(nx - 1);
+                double y = y_lo + (y_hi - y_lo) * (double)k / (double)(ny - 1);
+                double F = or_objective(L, s, S, x, y, z);
+                if (F > best) { best = F; bx = x; by = y; }
+            }
+        out_xy[2 * e] = bx;
+        out_xy[2 * e + 1] = by;
+        out_F[e] = best;
+    }
+}
+
+/* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

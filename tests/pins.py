@@ -1,0 +1,397 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each pin takes ``mutant`` (0 = the real oracle; k > 0 = a build with one
+planted mistake) and raises AssertionError when the oracle disagrees with
+the fact.  tests/test_oracle_pins.py runs them on the real oracle;
+tests/test_oracle_mutants.py checks that every planted mistake trips at
+least one of them.  The facts are closed forms, textbook values, library
+routines (scipy) and exhaustive search on tiny inputs.
+"""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+import synth
+import synth.workloads
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_bspline():
+    rows = []
+    with open(os.path.join(GOLDEN, "uniform_cubic_bspline.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            parts = line.split()
+            t = Fraction(int(parts[0]), int(parts[1]))
+            b = [Fraction(p) for p in parts[2:6]]
+            rows.append((t, b))
+    return rows
+
+
+# --------------------------------------------------------------------------
+# B-spline basis
+# --------------------------------------------------------------------------
+
+
+def pin_bspline_golden(mutant=0):
+    """Basis values on a span equal the closed-form uniform cubic segment
+    polynomials (golden fractions), for the full and the local recursion."""
+    n, lo, hi = 5, -1.0, 9.0  # h = 2
+    for t, b in _golden_bspline():
+        for span in (0, 2, 4):
+            x = lo + 2.0 * (span + float(t))
+            m, B = oracle.bspline_basis_all(n, lo, hi, x, mutant)
+            j0, B4 = oracle.bspline_basis4(n, lo, hi, x, mutant)
+            assert j0 == span, (j0, span)
+            want = np.array([float(v) for v in b])
+            assert np.allclose(B[span:span + 4], want, rtol=0, atol=1e-15), (B[span:span + 4], want)
+            assert np.allclose(B4, want, rtol=0, atol=1e-15), (B4, want)
+            assert np.all(np.delete(B, range(span, span + 4)) == 0.0)
+
+
+def pin_partition_of_unity(mutant=0):
+    """sum_j B_j(x) = 1 on [lo, hi], including both ends and the knots."""
+    rng = np.random.default_rng(5)
+    for n, lo, hi in ((1, 0.0, 1.0), (4, -3.0, 5.0), (20, 0.0, 150.0), (32, -25.6, 25.6)):
+        xs = np.concatenate([rng.uniform(lo, hi, 50), np.linspace(lo, hi, n + 1)])
+        for x in xs:
+            m, B = oracle.bspline_basis_all(n, lo, hi, float(x), mutant)
+            j0, B4 = oracle.bspline_basis4(n, lo, hi, float(x), mutant)
+            assert abs(B.sum() - 1.0) < 1e-14, (n, x, B.sum())
+            assert abs(B4.sum() - 1.0) < 1e-14, (n, x, B4.sum())
+            assert np.all(B >= -1e-16) and np.all(B4 >= -1e-16)
+        m, B = oracle.bspline_basis_all(n, lo, hi, hi + 1e-9, mutant)
+        assert m == -1 and not B.any()
+
+
+# --------------------------------------------------------------------------
+# least-squares fit
+# --------------------------------------------------------------------------
+
+
+def _poly_nd(pts, coefs):
+    v = np.zeros(pts.shape[0])
+    for powers, c in coefs.items():
+        term = np.full(pts.shape[0], c)
+        for a, pw in enumerate(powers):
+            term = term * pts[:, a] ** pw
+        v += term
+    return v
+
+
+def pin_fit_reproduces_cubics(mutant=0):
+    """Cubic splines reproduce (tensor) cubic polynomials exactly, so the
+    least-squares fit of polynomial samples recovers them to rounding."""
+    rng = np.random.default_rng(7)
+    cases = [
+        ((7,), (0.0,), (10.0,)),
+        ((5, 6), (-3.0, -2.0), (4.0, 5.0)),
+        ((3, 4, 2), (-1.0, 0.0, 0.0), (2.0, 3.0, 2.0)),
+    ]
+    for n_int, lo, hi in cases:
+        d = len(n_int)
+        coefs = {}
+        for powers in np.ndindex(*([4] * d)):
+            coefs[powers] = rng.uniform(-1.0, 1.0) / (1.0 + sum(powers)) ** 2
+        pts = synth.grid_samples(n_int, lo, hi, per_interval=3)
+        vals = _poly_nd(pts, coefs)
+        coef, rc, lam = oracle.lrf_fit(n_int, lo, hi, pts, vals, mutant=mutant)
+        assert rc == 0
+        test = np.stack([rng.uniform(lo[a], hi[a], 300) for a in range(d)], axis=1)
+        got = oracle.spline_eval(n_int, lo, hi, coef[0], test, mutant=mutant)
+        want = _poly_nd(test, coefs)
+        scale = np.abs(want).max()
+        assert np.abs(got - want).max() < 1e-10 * max(scale, 1.0), (n_int, np.abs(got - want).max())
+
+
+def pin_fit_h4_convergence(mutant=0):
+    """The cubic-spline fit error of the smooth axial LRF falls as h^4:
+    halving h cuts the maximum error by about 16."""
+    r = np.linspace(0.0, 150.0, 3001)
+    errs = []
+    for n in (10, 20, 40):
+        pts = synth.grid_samples((n,), (0.0,), (150.0,), per_interval=4)
+        coef, rc, _ = oracle.lrf_fit((n,), (0.0,), (150.0,), pts, synth.eta_axial(pts[:, 0]), mutant=mutant)
+        got = oracle.spline_eval((n,), (0.0,), (150.0,), coef[0], r[:, None], mutant=mutant)
+        errs.append(np.abs(got - synth.eta_axial(r)).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 10.0 < a / b < 24.0, errs
+
+
+def pin_lrf_matches_closed_form(mutant=0):
+    """Fitted LRFs evaluated through the sensor geometry reproduce the
+    closed-form truth: axial (20 intervals on [0,150]) and per-sensor XY
+    (24 x 24 on +-24 mm, off-centre sensors) within 1e-4 relative."""
+    w = synth.workloads.get("hex19_radial")
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals, mutant=mutant)
+    L = oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), coef,
+                   shared=True)
+    rng = np.random.default_rng(11)
+    p = rng.uniform(-60, 60, (400, 2))
+    got = oracle.lrf_eval(L, p, mutant=mutant)
+    want = synth.truth_eta(w.sensor_xy, w.gains, p)
+    assert np.nanmax(np.abs(got / want - 1.0)) < 1e-4
+    w = synth.workloads.get("sipm8x8_xy")
+    sel = [0, 9, 27, 62]  # corner, inner and edge sensors: no symmetry to hide a transposition
+    sxy = w.sensor_xy[sel]
+    g = w.gains[sel]
+    pts = synth.grid_samples(w.n_int, w.lo, w.hi, 4)
+    vals = synth.truth_eta(sxy, g, pts)
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals, mutant=mutant)
+    L = oracle.Lrf(oracle.XY, sxy, w.n_int + (0,), w.lo + (0,), w.hi + (0,), coef)
+    p = rng.uniform(-24, 24, (400, 2))
+    got = oracle.lrf_eval(L, p, mutant=mutant)
+    want = synth.truth_eta(sxy, g, p)
+    assert np.abs(got / want - 1.0).max() < 1e-4, np.abs(got / want - 1.0).max()
+
+
+# --------------------------------------------------------------------------
+# centroid
+# --------------------------------------------------------------------------
+
+
+def pin_cog(mutant=0):
+    """COG of symmetric patterns is the array centre; one lit sensor gives
+    its own position; mirrored signals give the mirrored COG; with two lit
+    sensors and gains g_i, s_i = g_i w_i gives (X1 w1 + X2 w2)/(w1 + w2)."""
+    sxy = synth.hex_array(2, 30.0)
+    n = sxy.shape[0]
+    c = oracle.cog(np.ones((1, n)), sxy, mutant=mutant)
+    assert np.abs(c).max() < 1e-12
+    r = np.hypot(sxy[:, 0], sxy[:, 1])
+    c = oracle.cog(np.exp(-r / 30.0)[None, :], sxy, mutant=mutant)
+    assert np.abs(c).max() < 1e-12
+    for i in (0, 7, 18):
+        s = np.zeros((1, n))
+        s[0, i] = 123.0
+        assert np.allclose(oracle.cog(s, sxy, mutant=mutant)[0], sxy[i], atol=1e-12)
+    rng = np.random.default_rng(3)
+    s = rng.uniform(1, 100, n)
+    # mirror x -> -x maps sensor i to sensor j with X_j = -X_i, Y_j = Y_i
+    perm = [int(np.argmin(np.hypot(sxy[:, 0] + sxy[i, 0], sxy[:, 1] - sxy[i, 1]))) for i in range(n)]
+    s_m = np.empty(n)
+    s_m[perm] = s
+    c1 = oracle.cog(s[None], sxy, mutant=mutant)[0]
+    c2 = oracle.cog(s_m[None], sxy, mutant=mutant)[0]
+    assert abs(c1[0] + c2[0]) < 1e-12 and abs(c1[1] - c2[1]) < 1e-12
+    gains = rng.uniform(0.5, 2.0, n)
+    s = np.zeros((1, n))
+    s[0, 3], s[0, 11] = gains[3] * 5.0, gains[11] * 15.0
+    want = (sxy[3] * 5.0 + sxy[11] * 15.0) / 20.0
+    assert np.allclose(oracle.cog(s, sxy, gains, mutant=mutant)[0], want, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# likelihood and energy
+# --------------------------------------------------------------------------
+
+
+def _small_xy_lrf(mutant=0):
+    sxy = synth.square_array(3, 8.0)
+    g = np.linspace(0.9, 1.1, 9)
+    n_int, lo, hi = (8, 8), (-16.0, -16.0), (16.0, 16.0)
+    pts = synth.grid_samples(n_int, lo, hi, 4)
+    coef, _, _ = oracle.lrf_fit(n_int, lo, hi, pts, synth.truth_eta(sxy, g, pts), mutant=mutant)
+    return oracle.Lrf(oracle.XY, sxy, n_int + (0,), lo + (0,), hi + (0,), coef), g
+
+
+def pin_energy_is_ml(mutant=0):
+    """At fixed position the Poisson likelihood is maximised over E at
+    E = sum s / sum eta (Sec. 5.1.2.2): the reported E beats E(1 +- 1e-3)."""
+    L, _ = _small_xy_lrf(mutant)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        x = np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), 0.0])
+        s = rng.poisson(800 * synth.truth_eta(L.sensor_xy, np.ones(9), x[None, :2])[0]).astype(float)
+        E, _ = oracle.energy_logl_at(L, s[None], x[None], mutant=mutant)
+        l0 = oracle.logl_at_energy(L, s, x, E[0], mutant=mutant)
+        for f in (1 - 1e-3, 1 + 1e-3):
+            assert oracle.logl_at_energy(L, s, x, E[0] * f, mutant=mutant) < l0
+
+
+def pin_logl_is_poisson(mutant=0):
+    """The reported logL equals the sum of scipy's Poisson log-pmf at
+    mu_i = E eta_i for integer signals."""
+    from scipy.stats import poisson
+    L, _ = _small_xy_lrf(mutant)
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        x = np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), 0.0])
+        s = rng.poisson(500 * synth.truth_eta(L.sensor_xy, np.ones(9), x[None, :2])[0]).astype(float)
+        s[2] = 0.0
+        E, logL = oracle.energy_logl_at(L, s[None], x[None], mutant=mutant)
+        eta = oracle.lrf_eval(L, x[None, :2], mutant=mutant)[0]
+        want = poisson.logpmf(s, E[0] * eta).sum()
+        assert abs(logL[0] - want) < 1e-9 * abs(want), (logL[0], want)
+
+
+def pin_profile_identity(mutant=0):
+    """max_E logL(x, E), found numerically by scipy, equals the searched
+    objective F(x) = sum s ln eta - S ln H plus S ln S - S - sum lgamma(s+1)."""
+    from scipy.optimize import minimize_scalar
+    L, _ = _small_xy_lrf(mutant)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        x = np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), 0.0])
+        s = rng.poisson(700 * synth.truth_eta(L.sensor_xy, np.ones(9), x[None, :2])[0]).astype(float)
+        S = s.sum()
+        res = minimize_scalar(lambda E: -oracle.logl_at_energy(L, s, x, E, mutant=mutant),
+                              bounds=(1.0, 1e5), method="bounded", options={"xatol": 1e-7})
+        F = oracle.objective_at(L, s[None], x[None], mutant=mutant)[0]
+        want = F + S * math.log(S) - S - sum(math.lgamma(v + 1.0) for v in s)
+        assert abs(-res.fun - want) < 1e-6 * abs(want), (-res.fun, want)
+
+
+# --------------------------------------------------------------------------
+# contracting grids
+# --------------------------------------------------------------------------
+
+
+def pin_noise_free_recovery(mutant=0):
+    """With s = E eta(x_true) (no noise) and x_true on a node of the first
+    grid, the search lands exactly on x_true and E = E_true: by Gibbs'
+    inequality sum s ln p, p = eta/H, is maximal only where p = s/S."""
+    L, _ = _small_xy_lrf(mutant)
+    P = oracle.CgsParams(n_xy=9, iters=6, step_xy=1.5)
+    xt = np.array([[3.25, -2.5, 0.0], [-6.5, 4.75, 0.0], [0.5, 0.25, 0.0]])
+    off = np.array([[2, -1, 0], [-3, 4, 0], [0, 1, 0]], dtype=float)
+    start = xt - off * P.step_xy
+    eta = oracle.lrf_eval(L, xt[:, :2], mutant=mutant)
+    E_true = np.array([900.0, 1500.0, 4000.0])
+    s = E_true[:, None] * eta
+    r = oracle.cgs(L, P, s, start_xyz=start, mutant=mutant)
+    assert np.all(r["status"] == 0)
+    assert np.abs(r["xyz"] - xt).max() < 1e-12, r["xyz"]
+    assert np.abs(r["E"] / E_true - 1.0).max() < 1e-12, r["E"]
+    c = (P.n_xy - 1) // 2
+    for e in range(3):
+        k0 = (c + int(off[e, 1])) * P.n_xy + (c + int(off[e, 0]))
+        assert r["trace"][e, 0] == k0
+        assert np.all(r["trace"][e, 1:] == c * P.n_xy + c)
+    # axial LRF on the PMT array, from the COG start of a central event
+    w = synth.workloads.get("hex19_radial")
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals, mutant=mutant)
+    Lr = oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), coef,
+                    shared=True)
+    Pr = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy)
+    xt = np.array([[7.5, -15.0, 0.0]])
+    s = 1e4 * oracle.lrf_eval(Lr, xt[:, :2], mutant=mutant)
+    r = oracle.cgs(Lr, Pr, s, start_xyz=xt - np.array([[1.0, 2.0, 0.0]]) * Pr.step_xy, mutant=mutant)
+    assert np.abs(r["xyz"] - xt).max() < 1e-12 and abs(r["E"][0] / 1e4 - 1.0) < 1e-12
+
+
+def pin_cg_matches_brute_force(mutant=0):
+    """On a tiny detector (2 x 2 sensors) the contracting-grid result is the
+    global maximum found by exhaustive search on a fine grid."""
+    sxy = synth.square_array(2, 10.0)
+    g = np.array([1.0, 0.95, 1.05, 1.02])
+    n_int, lo, hi = (10, 10), (-15.0, -15.0), (15.0, 15.0)
+    pts = synth.grid_samples(n_int, lo, hi, 4)
+    coef, _, _ = oracle.lrf_fit(n_int, lo, hi, pts, synth.truth_eta(sxy, g, pts, r0=20.0), mutant=mutant)
+    L = oracle.Lrf(oracle.XY, sxy, n_int + (0,), lo + (0,), hi + (0,), coef)
+    # sources inside the array, where four sensors pin the position; far
+    # outside it the profiled likelihood has flat valleys and no unique max
+    ev = synth.draw_events(sxy, g, 120, 77, region="square", extent=6.0, e0=4000.0, r0=20.0)
+    P = oracle.CgsParams(n_xy=9, iters=8, step_xy=3.75)
+    r = oracle.cgs(L, P, ev.signals, gain_cog=g, mutant=mutant)
+    fine = 0.05
+    xy, F = oracle.brute_force(L, ev.signals, (-15, 15), int(30 / fine) + 1, (-15, 15), int(30 / fine) + 1,
+                               mutant=mutant)
+    d = np.hypot(*(r["xyz"][:, :2] - xy).T)
+    final = P.step_xy * P.shrink ** (P.iters - 1)
+    ok = d <= 2.0 * (fine + final)
+    assert ok.mean() >= 0.99, (ok.mean(), d.max())
+
+
+def pin_ties_go_to_lowest_index(mutant=0):
+    """With a single sensor, F = s ln eta - s ln eta = 0 exactly at every
+    node, so all nodes tie; the search must take the lowest flat index (the
+    (-,-) corner) on every grid."""
+    sxy = np.array([[3.0, 1.0]])
+    n_int, lo, hi = (4, 4), (-40.0, -40.0), (40.0, 40.0)
+    coef = np.random.default_rng(2).uniform(0.5, 1.5, (1, 49))
+    L = oracle.Lrf(oracle.XY, sxy, n_int + (0,), lo + (0,), hi + (0,), coef)
+    P = oracle.CgsParams(n_xy=5, iters=4, step_xy=2.0)
+    s = np.array([[37.0]])
+    start = np.array([[1.0, -3.0, 0.0]])
+    r = oracle.cgs(L, P, s, start_xyz=start, mutant=mutant)
+    assert np.all(r["trace"] == 0), r["trace"]
+    walk = -2.0 * P.step_xy * sum(P.shrink ** k for k in range(P.iters))
+    assert np.allclose(r["xyz"][0, :2], start[0, :2] + walk, atol=1e-12)
+
+
+def pin_domain(mutant=0):
+    """Nodes outside the LRF's box score -inf: with every node tied, the
+    search takes the lowest-index node inside the box (re-derived here by
+    direct enumeration)."""
+    sxy = np.array([[3.0, 1.0]])  # one sensor: every node ties exactly
+    n_int, lo, hi = (4, 4), (-20.0, -20.0), (20.0, 20.0)
+    coef = np.random.default_rng(6).uniform(0.5, 1.5, (1, 49))
+    L = oracle.Lrf(oracle.XY, sxy, n_int + (0,), lo + (0,), hi + (0,), coef)
+    P = oracle.CgsParams(n_xy=5, iters=5, step_xy=4.0)
+    s = np.array([[42.0]])
+    start = np.array([[-18.8, 17.0, 0.0]])
+    r = oracle.cgs(L, P, s, start_xyz=start, mutant=mutant)
+    cx, cy, st = start[0, 0], start[0, 1], P.step_xy
+    for it in range(P.iters):
+        pick = None
+        for k in range(P.n_xy * P.n_xy):
+            x = cx + (k % P.n_xy - 2) * st
+            y = cy + (k // P.n_xy - 2) * st
+            if -20.0 <= x <= 20.0 and -20.0 <= y <= 20.0:
+                pick = (k, x, y)
+                break
+        assert r["trace"][0, it] == pick[0], (it, r["trace"][0], pick)
+        cx, cy = pick[1], pick[2]
+        st *= P.shrink
+    assert abs(r["xyz"][0, 0] - cx) < 1e-12 and abs(r["xyz"][0, 1] - cy) < 1e-12
+
+
+def pin_event_status(mutant=0):
+    """Zero total signal -> zero-signal status; negative, NaN or infinite
+    signals -> bad-signal status; outputs NaN for both."""
+    L, _ = _small_xy_lrf(mutant)
+    P = oracle.CgsParams(n_xy=5, iters=2, step_xy=1.0)
+    s = np.full((5, 9), 10.0)
+    s[0] = 0.0
+    s[1, 3] = -1.0
+    s[2, 4] = np.nan
+    s[3, 5] = np.inf
+    r = oracle.cgs(L, P, s, mutant=mutant)
+    assert list(r["status"]) == [2, 3, 3, 3, 0]
+    assert np.all(np.isnan(r["xyz"][:4])) and np.all(np.isnan(r["E"][:4]))
+    assert np.all(np.isfinite(r["xyz"][4]))
+
+
+def pin_replay(mutant=0):
+    """Replaying the oracle's own path certifies it with no ties; a path
+    that takes a clearly worse node is flagged."""
+    L, g = _small_xy_lrf(mutant)
+    ev = synth.draw_events(L.sensor_xy, g, 40, 5, region="square", extent=10.0, e0=2000.0)
+    P = oracle.CgsParams(n_xy=7, iters=5, step_xy=2.0)
+    r = oracle.cgs(L, P, ev.signals, gain_cog=g, mutant=mutant)
+    rp = oracle.cgs_replay(L, P, ev.signals, r["trace"], gain_cog=g, mutant=mutant)
+    assert np.all(rp["n_tie"] == 0) and np.all(rp["n_bad"] == 0)
+    assert np.array_equal(rp["xyz"], r["xyz"]) and np.array_equal(rp["logL"], r["logL"])
+    bad = r["trace"].copy()
+    bad[:, 0] = np.where(bad[:, 0] == 0, 48, 0)  # a far corner instead of the best node
+    rp = oracle.cgs_replay(L, P, ev.signals, bad, gain_cog=g, mutant=mutant)
+    assert np.all(rp["n_bad"] >= 1)
+
+
+ALL_PINS = [
+    pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
+    pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
+    pin_noise_free_recovery, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
+    pin_event_status, pin_replay,
+]

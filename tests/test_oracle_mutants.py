@@ -1,0 +1,29 @@
+"""Every planted mistake in the oracle (a dropped term, a flipped sign, a
+transposed index, a wrong tie rule ...) trips at least one pin.  The mistakes
+are compiled into separate copies of the oracle on the CPU (OR_MUTANT=k)."""
+import pytest
+
+import pins
+
+MUTANTS = {
+    1: "search objective without the -S ln H term",
+    2: "sign flip in the full Cox-de Boor recursion",
+    3: "x and y coefficient indices transposed",
+    4: "COG without the relative-gain division",
+    5: "argmax ties resolved to the highest index",
+    6: "energy H/S instead of S/H",
+    7: "lgamma(s) instead of lgamma(s+1)",
+    8: "transposed factor in the Cholesky update",
+    9: "wrong knot in the local Cox-de Boor recursion",
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS), ids=lambda k: f"m{k}")
+def test_mutant_is_caught(mutant):
+    caught = []
+    for pin in pins.ALL_PINS:
+        try:
+            pin(mutant)
+        except (AssertionError, RuntimeError, ValueError, IndexError, TypeError):
+            caught.append(pin.__name__)
+    assert caught, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
