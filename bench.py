@@ -1,0 +1,307 @@
+"""Benchmark: events/s of maximum-likelihood position reconstruction.
+
+Default workload (1 GPU): 8 x 8 SiPM array, per-sensor XY B-spline LRFs
+(24 x 24 intervals), 10^6 synthetic events, plain FP32 contracting-grid
+search 11 x 11 nodes x 8 grids.  One step = one reconstruction of all events
+(signals already resident in HBM; 256 MB of signals, larger than the 129 MB
+L2, so every step streams them from HBM).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank reconstructs its own 10^6 events (weak scaling, no
+collective on the data path); value = all ranks' events / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "events/s of ML position reconstruction, plain CGS vs chosen form, same error"
+SM_COUNT = 152
+MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    import synth.workloads
+    return synth.workloads.get("sipm8x8_xy")
+
+
+def cpu_oracle_rate(w, n_sample: int, seed: int):
+    """Events/s of the FP64 oracle (as it stands) on a sample of the workload."""
+    import oracle
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    L = oracle.Lrf(oracle.XY, w.sensor_xy, w.n_int + (0,), w.lo + (0,), w.hi + (0,), coef)
+    P = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    ev = w.events(n_sample, seed=seed)
+    sig = ev.signals.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.cgs(L, P, sig, gain_cog=w.gains)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt, oracle.num_threads(), (L, P, sig)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload()
+    import oracle
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    L = oracle.Lrf(oracle.XY, w.sensor_xy, w.n_int + (0,), w.lo + (0,), w.hi + (0,), coef)
+    P = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    n_step = args.ref_events
+    ev = w.events(n_step * (args.warmup + args.steps), seed=w.event_seed)
+    sig = ev.signals.astype(np.float64)
+    for k in range(args.warmup):
+        oracle.cgs(L, P, sig[k * n_step:(k + 1) * n_step], gain_cog=w.gains)
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        oracle.cgs(L, P, sig[k * n_step:(k + 1) * n_step], gain_cog=w.gains)
+    dt = time.perf_counter() - t0
+    value = n_step * args.steps / dt
+    sample = f"{n_step} events of the 10^6-event workload per step, FP64 C oracle with OpenMP"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, w.n_events),
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, n_events):
+    return {"workload": f"{w.name}: {w.n_sensors} sensors, XY B-spline LRF {w.n_int[0]}x{w.n_int[1]} intervals, "
+                        f"{n_events} events, contracting grid {w.n_xy}x{w.n_xy} x {w.iters} grids",
+            "n_events": n_events, "n_sensors": w.n_sensors, "grid": f"{w.n_xy}x{w.n_xy}", "iters": w.iters,
+            "method": "plain FP32 contracting grids", "l2": "inputs larger than L2 (256 MB of signals per step)"}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1602_07247_gb300 as ants
+    from paper_1602_07247_gb300 import _build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    w = workload()
+    n = args.events or w.n_events
+    ctx = ants.Context(dev)
+    det = ants.Detector(w.sensor_xy, w.gains)
+    pts, vals = w.fit_samples()
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)  # FP64 fit on the GPU
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    ev = w.events(n, seed=w.event_seed + 7919 * rank)
+    sig = torch.from_numpy(ev.signals).cuda()
+    xyz = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    E = torch.empty(n, dtype=torch.float32, device="cuda")
+    logL = torch.empty(n, dtype=torch.float32, device="cuda")
+    status = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ants.ants_reconstruct(ctx.handle, lrf.handle, ants.ANTS_CGS_PLAIN, p, sig, w.n_sensors, xyz, E, logL,
+                              status, stream=stream)
+        return ants.last_launch_count()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        launches += step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    value = n * world * args.steps / dt
+    kernel_s = dt / args.steps  # one kernel launch per step
+
+    # accuracy of this run (not timed): RMS |dxy| against the true positions
+    d = xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+    rms = float(np.sqrt((d ** 2).sum(1).mean()))
+
+    # end-to-end through host buffers (H2D signals, D2H results inside the timed region)
+    sig_host = torch.from_numpy(ev.signals).pin_memory()
+    outs = {k: torch.empty(shape, dtype=dt_).pin_memory() for k, shape, dt_ in
+            (("xyz", (n, 3), torch.float32), ("E", (n,), torch.float32), ("logL", (n,), torch.float32),
+             ("status", (n,), torch.int32))}
+
+    def step_host():
+        ants.ants_reconstruct_host(ctx.handle, lrf.handle, ants.ANTS_CGS_PLAIN, p, sig_host, w.n_sensors,
+                                   outs["xyz"], outs["E"], outs["logL"], outs["status"])
+
+    for _ in range(max(1, args.warmup // 2)):
+        step_host()
+    e2e_steps = max(3, args.steps // 3)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": n * world * e2e_steps / t_e2e, "unit": "events/s",
+           "h2d_bytes_per_step": int(sig_host.numel() * 4),
+           "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
+
+    if rank != 0:
+        return 0
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    evals = n * w.iters * w.n_xy * w.n_xy * w.n_sensors
+    peak_evals = SM_COUNT * MUFU_PER_CLK_SM * sm_mhz * 1e6
+    achieved = evals / kernel_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_evals / 1e12, "unit": "Teval/s",
+                "frac": achieved / peak_evals, "traffic": None,
+                "peak_kind": f"derived: {SM_COUNT} SMs x {MUFU_PER_CLK_SM} log2/clk x {sm_mhz:.0f} MHz "
+                             f"({pk_kind} max clock); one eval = one LRF value + one log2 per (node, sensor)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, secs, cores, _ = cpu_oracle_rate(w, args.cpu_events, seed=w.event_seed)
+        cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_events} events of this workload ({secs:.1f} s), FP64 C oracle, OpenMP"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        "rms_dxy_mm": rms,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--events", type=int, default=0, help="override the event count (default: workload's)")
+    ap.add_argument("--cpu-events", type=int, default=4096)
+    ap.add_argument("--ref-events", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * ants.h -- C ABI of libants, a GB300 (sm_103a) library for the statistical
+ * position/energy reconstruction of Anger-camera type detectors described in
+ * "ANTS2 package: simulation and experimental data processing for Anger
+ * camera type detectors" (Morozov et al., arXiv:1602.07247).
+ *
+ * The library reconstructs, for every event, the source position (x, y[, z])
+ * and energy E from the photosensor signals by maximum likelihood, with the
+ * light response functions (LRFs) of the sensors parameterised by cubic
+ * B-splines (Sec. 5.1.2, 5.1.2.2, 6, 6.1).
+ *
+ * Conventions for every entry point:
+ *   - Plain pointers and sizes only.  Arguments named *_dev are device
+ *     pointers (CUDA global memory of the context's device), *_host are host
+ *     pointers.  All of them are owned by the caller, who keeps them alive
+ *     until the work on `stream` has completed.
+ *   - Handles (ants_ctx, ants_detector, ants_lrf) are owned by the library
+ *     and released with the matching *_free / *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that take a stream are asynchronous with respect to
+ *     the host unless documented otherwise.
+ *   - Every call returns an ants_status.  Argument errors are detected
+ *     before any launch and leave outputs untouched.  ants_last_error()
+ *     returns a message for the calling thread's last non-OK return.
+ *   - Problems of individual events never fail a call; they are reported in
+ *     the per-event status array (ants_evt_status).
+ *   - Coordinates are in millimetres; signals are photo-electron counts (or
+ *     proportional amplitudes), non-negative.
+ */
+#ifndef ANTS_H
+#define ANTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ANTS_API __attribute__((visibility("default")))
+#else
+#define ANTS_API
+#endif
+
+/* Return codes. */
+typedef enum {
+    ANTS_OK = 0,
+    ANTS_E_ARG = -1,           /* invalid argument (null pointer, bad size, bad enum) */
+    ANTS_E_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+    ANTS_E_OOM = -3,           /* device or host allocation failed */
+    ANTS_E_LRF = -4,           /* LRF fit failed (normal matrix singular even with ridge) */
+    ANTS_E_SHAPE = -5,         /* sizes inconsistent with the LRF or detector */
+    ANTS_E_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    ANTS_E_INTERNAL = -7,      /* internal consistency check failed */
+    ANTS_E_UNIMPLEMENTED = -8, /* method or option not available */
+    ANTS_E_IO = -9             /* file could not be read or written, or bad format */
+} ants_status;
+
+/* LRF parameterisations (Sec. 6.1.1 "Axial" and "XY", Sec. 6.1 3D). */
+typedef enum {
+    ANTS_LRF_RADIAL = 1, /* eta_i(x,y) = g_i f(|(x,y) - (X_i,Y_i)|), f a cubic B-spline in r */
+    ANTS_LRF_XY = 2,     /* eta_i(x,y) = sum_jk c_ijk B_j(x) B_k(y), one tensor spline per sensor */
+    ANTS_LRF_XYZ = 3     /* eta_i(x,y,z) = sum_jkl c_ijkl B_j(x) B_k(y) B_l(z) */
+} ants_lrf_type;
+
+/* Per-event status codes written by the reconstruction calls. */
+typedef enum {
+    ANTS_EVT_OK = 0,
+    ANTS_EVT_FALLBACK = 1,      /* reserved: event re-run by a fallback search */
+    ANTS_EVT_ZERO_SIGNAL = 2,   /* sum of signals <= 0: outputs NaN */
+    ANTS_EVT_BAD_SIGNAL = 3,    /* a signal is negative, NaN or infinite: outputs NaN */
+    ANTS_EVT_OUT_OF_DOMAIN = 4, /* the start position lies outside the LRF domain: outputs NaN */
+    ANTS_EVT_LOW_LOGL = 5       /* reserved: logL below a threshold */
+} ants_evt_status;
+
+/* Reconstruction methods. */
+typedef enum {
+    ANTS_CGS_PLAIN = 0 /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
+} ants_method;
+
+/* Signal element types. */
+typedef enum { ANTS_F32 = 0 } ants_dtype;
+
+typedef struct ants_ctx ants_ctx;
+typedef struct ants_detector ants_detector;
+typedef struct ants_lrf ants_lrf;
+
+/* Parameters of the contracting-grid search (Sec. 5.1.2.2).
+ * The grid has n_xy x n_xy (x n_z) nodes centred on the current centre with
+ * spacing step_xy (step_z); flat node index k = (iz*n_xy + iy)*n_xy + ix.
+ * After each of `iters` grids the best node (maximum likelihood, ties to
+ * the lowest k) becomes the centre and the spacings are multiplied by
+ * `shrink`.  The result is the best node of the last grid.
+ * n_xy, n_z odd; n_xy in [3, 15], n_z in [1, 15] (n_z = 1 unless the LRF is
+ * ANTS_LRF_XYZ); iters in [1, 32]; 0 < shrink < 1; step_xy > 0; z0 is the
+ * start z for XYZ LRFs. */
+typedef struct {
+    int n_xy;
+    int n_z;
+    int iters;
+    float shrink;
+    float step_xy;
+    float step_z;
+    float z0;
+} ants_cgs_params;
+
+/* ------------------------------------------------------------------------ */
+/* Library and context                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Message for the calling thread's last non-OK return ("" if none).  The
+ * string stays valid until the thread's next ants_* call. */
+ANTS_API const char *ants_last_error(void);
+
+/* ABI version of this header (increases on incompatible changes). */
+ANTS_API int ants_version(void);
+
+/* Create a context on CUDA device `device` (makes it current for the
+ * calling thread).  *out receives the handle.  Errors: ANTS_E_ARG (null
+ * out, bad device), ANTS_E_CUDA. */
+ANTS_API int ants_ctx_create(int device, ants_ctx **out);
+
+/* Release a context and the device buffers it owns (NULL is a no-op).  The
+ * caller must have synchronised all streams that used it. */
+ANTS_API void ants_ctx_destroy(ants_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Detector definition (Sec. 2 "detector definitions"; Sec. 5.1.1 gains)      */
+/* ------------------------------------------------------------------------ */
+
+/* Describe a planar sensor array: sensor_xy_host[n_sensors][2] sensor
+ * centres (mm, row-major), rel_gain_host[n_sensors] the relative gains g_i
+ * used by the centroid x = sum X_i S_i/g_i / sum S_i/g_i (Sec. 5.1.1,
+ * centroid equation); NULL means g_i = 1.  Gains must be > 0.  Data are
+ * copied.  n_sensors in [1, 1024].  Errors: ANTS_E_ARG. */
+ANTS_API int ants_detector_create(int n_sensors, const double *sensor_xy_host,
+                                  const double *rel_gain_host, ants_detector **out);
+ANTS_API void ants_detector_free(ants_detector *det);
+
+/* ------------------------------------------------------------------------ */
+/* Light response functions (Sec. 6, 6.1, 6.2)                               */
+/* ------------------------------------------------------------------------ */
+
+/* Build an LRF set from FP64 B-spline coefficients.
+ * type: ants_lrf_type.  Axis a (a < dims; dims = 1 radial, 2 XY, 3 XYZ) has
+ * n_int[a] uniform intervals on [lo[a], hi[a]] and n_int[a] + 3 cubic
+ * B-spline coefficients (knots lo + (j-3)h, j = 0..n+6).  For RADIAL, axis 0
+ * is r = distance in the sensor plane, with lo[0] = 0.
+ * coef_host: [n_sets][n_coef] with n_coef = prod_a (n_int[a] + 3), x index
+ * fastest, then y, then z; n_sets = 1 when `shared` (one group, Sec. 6.2:
+ * one LRF for all sensors times gain_host[i]) else n_sensors.  shared is
+ * allowed for RADIAL only.  gain_host (RADIAL only, nullable = 1) scales
+ * sensor i's LRF.  n_int[a] in [1, 256]; lo < hi.
+ * The coefficients are kept in FP64 on the host and uploaded as FP32.
+ * Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                             const double *lo, const double *hi, int shared,
+                             const double *coef_host, const double *gain_host, ants_lrf **out);
+
+/* Fit an LRF set by FP64 least squares on the device and return it as
+ * ants_lrf_create would (Sec. 6: LRFs are computed from datasets of source
+ * positions and sensor signals; Sec. 6.2: one group shares one LRF).
+ * pts_host [n_pts][dims] FP64 sample positions (RADIAL: r; XY: x, y; XYZ:
+ * x, y, z), vals_host [n_pts][n_sets] FP64 values, n_sets = 1 when `shared`
+ * else n_sensors.  Grid arguments as in ants_lrf_create.  Solves
+ * (B^T B + ridge I) c = B^T v per value set with a square-root-free
+ * Cholesky (L D L^T) factorisation of the banded normal matrix; when it is
+ * not positive definite (a region without samples) the solve is retried
+ * once with ridge = 1e-10 trace(B^T B) / n_coef.  *ridge_used (nullable)
+ * receives the ridge applied.  Samples outside the domain are ignored.
+ * Synchronous; the result is bitwise reproducible.
+ * Errors: ANTS_E_ARG, ANTS_E_LRF (still singular), ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                          const double *lo, const double *hi, int shared, long n_pts,
+                          const double *pts_host, const double *vals_host, double ridge,
+                          double *ridge_used, ants_lrf **out);
+
+/* Copy the FP64 coefficients ([n_sets][n_coef]) to coef_host; `count` is
+ * the capacity in doubles and must be >= n_sets*n_coef.  *n_sets_out and
+ * *n_coef_out (nullable) receive the shape.  Errors: ANTS_E_ARG. */
+ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_t count,
+                                   int *n_sets_out, int *n_coef_out);
+
+/* Evaluate eta_i at n_pts points for all sensors: pts_dev[n_pts][dim] FP32
+ * (dim = 2 for RADIAL/XY, 3 for XYZ), out_dev[n_pts][n_sensors] FP32.
+ * Points outside the LRF domain give NaN.  Asynchronous on `stream`.
+ * Errors: ANTS_E_ARG, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_eval(const ants_lrf *lrf, const float *pts_dev, long n_pts, int dim,
+                           float *out_dev, void *stream);
+
+/* Save / load an LRF set (versioned little-endian binary file: header,
+ * grid, gains, FP64 coefficients).  load binds the LRF to `det`, whose
+ * sensor count must match the file.  Errors: ANTS_E_IO, ANTS_E_SHAPE,
+ * ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_save(const ants_lrf *lrf, const char *path);
+ANTS_API int ants_lrf_load(ants_ctx *ctx, const ants_detector *det, const char *path,
+                           ants_lrf **out);
+
+ANTS_API void ants_lrf_free(ants_lrf *lrf);
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction (Sec. 5.1.2 maximum likelihood, 5.1.2.2 contracting grids)  */
+/* ------------------------------------------------------------------------ */
+
+/* Reconstruct n_events events.
+ *   method: ANTS_CGS_PLAIN; params: const ants_cgs_params*.
+ *   signals_dev: [n_events][n_sensors] row-major, element type signal_dtype
+ *     (ANTS_F32); n_sensors must equal the LRF's.
+ *   start_xyz_dev: nullable [n_events][3] FP32 start positions; NULL = the
+ *     centroid (Sec. 5.1.1) clamped into the XY domain of an XY/XYZ LRF,
+ *     with z = params->z0 (Sec. 5.1.2.1 start options).
+ *   Outputs (FP32 unless stated): xyz_dev [n_events][3] (z = 0 for 2D
+ *   LRFs), E_dev [n_events] = sum s / sum eta at the result (Sec. 5.1.2.2),
+ *   logL_dev [n_events] = sum_i [s_i ln mu_i - mu_i - lgamma(s_i+1)] with
+ *   mu_i = E eta_i (Poisson), status_dev [n_events] int32 ants_evt_status.
+ *   trace_dev: nullable [n_events][iters] int16, the flat index of the node
+ *   chosen on each grid (-1 for events that were not searched).
+ * The likelihood is Poisson with the energy profiled out: each node scores
+ * F = sum_i s_i ln eta_i - S ln sum_i eta_i (S = sum s), eta_i floored at
+ * 1e-30; nodes outside the LRF domain score -inf (RADIAL: every sensor
+ * within r <= hi[0]; XY/XYZ: inside the box).
+ * n_events == 0 is a no-op.  Asynchronous on `stream`.
+ * Errors: ANTS_E_ARG, ANTS_E_SHAPE, ANTS_E_UNIMPLEMENTED, ANTS_E_CUDA. */
+ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+                              const void *signals_dev, int signal_dtype, long n_events,
+                              int n_sensors, const float *start_xyz_dev, float *xyz_dev,
+                              float *E_dev, float *logL_dev, int32_t *status_dev,
+                              int16_t *trace_dev, void *stream);
+
+/* The same reconstruction with HOST buffers (signals_host [n_events]
+ * [n_sensors], outputs xyz_host [n_events][3], E_host, logL_host,
+ * status_host; nullable start_xyz_host).  The library streams the events
+ * through device buffers owned by the context in chunks, overlapping the
+ * host-to-device copy, the search and the device-to-host copy on two
+ * internal streams.  Page-locked host memory gives full copy bandwidth.
+ * Synchronous: returns when the outputs are in host memory.
+ * Errors: as ants_reconstruct, plus ANTS_E_OOM. */
+ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int method,
+                                   const void *params, const void *signals_host, int signal_dtype,
+                                   long n_events, int n_sensors, const float *start_xyz_host,
+                                   float *xyz_host, float *E_host, float *logL_host,
+                                   int32_t *status_host);
+
+/* Number of kernels the calling thread's last successful ants_* call
+ * launched (for accounting in benchmarks). */
+ANTS_API long ants_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANTS_H */

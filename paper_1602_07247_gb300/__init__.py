@@ -1,0 +1,335 @@
+"""Python binding of libants (include/ants.h): argument marshalling only.
+
+Every step of the reconstruction runs in the CUDA kernels of libants.so; this
+module converts torch tensors / numpy arrays to pointers and sizes and turns
+non-OK return codes into exceptions.  There is no CPU path: if the library is
+missing or cannot load, every call raises.
+
+The functions keep the C names (ants_ctx_create, ants_lrf_create,
+ants_reconstruct, ...).  Small wrapper classes (Context, Detector, Lrf) own
+the handles and free them when collected.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+# enums of include/ants.h
+ANTS_OK = 0
+ANTS_LRF_RADIAL, ANTS_LRF_XY, ANTS_LRF_XYZ = 1, 2, 3
+ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
+ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
+ANTS_CGS_PLAIN = 0
+ANTS_F32 = 0
+
+_STATUS_NAMES = {0: "ANTS_OK", -1: "ANTS_E_ARG", -2: "ANTS_E_CUDA", -3: "ANTS_E_OOM", -4: "ANTS_E_LRF",
+                 -5: "ANTS_E_SHAPE", -6: "ANTS_E_TIMEOUT", -7: "ANTS_E_INTERNAL", -8: "ANTS_E_UNIMPLEMENTED",
+                 -9: "ANTS_E_IO"}
+
+
+class AntsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CgsParams(C.Structure):
+    """ants_cgs_params: contracting-grid search settings."""
+    _fields_ = [("n_xy", C.c_int), ("n_z", C.c_int), ("iters", C.c_int), ("shrink", C.c_float),
+                ("step_xy", C.c_float), ("step_z", C.c_float), ("z0", C.c_float)]
+
+    def __init__(self, n_xy=9, iters=6, step_xy=1.0, shrink=0.5, n_z=1, step_z=0.0, z0=0.0):
+        super().__init__(n_xy, n_z, iters, shrink, step_xy, step_z, z0)
+
+
+_lib: C.CDLL | None = None
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+def lib() -> C.CDLL:
+    """Load libants.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libants.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        L.ants_last_error.restype = C.c_char_p
+        L.ants_version.restype = C.c_int
+        L.ants_last_launch_count.restype = C.c_long
+        L.ants_ctx_create.argtypes = [C.c_int, C.POINTER(_VP)]
+        L.ants_ctx_destroy.argtypes = [_VP]
+        L.ants_ctx_destroy.restype = None
+        L.ants_detector_create.argtypes = [C.c_int, _DP, _DP, C.POINTER(_VP)]
+        L.ants_detector_free.argtypes = [_VP]
+        L.ants_detector_free.restype = None
+        L.ants_lrf_create.argtypes = [_VP, _VP, C.c_int, _IP, _DP, _DP, C.c_int, _DP, _DP, C.POINTER(_VP)]
+        L.ants_lrf_fit.argtypes = [_VP, _VP, C.c_int, _IP, _DP, _DP, C.c_int, C.c_long, _DP, _DP, C.c_double, _DP,
+                                   C.POINTER(_VP)]
+        L.ants_lrf_coefficients.argtypes = [_VP, _DP, C.c_size_t, _IP, _IP]
+        L.ants_lrf_eval.argtypes = [_VP, _VP, C.c_long, C.c_int, _VP, _VP]
+        L.ants_lrf_save.argtypes = [_VP, C.c_char_p]
+        L.ants_lrf_load.argtypes = [_VP, _VP, C.c_char_p, C.POINTER(_VP)]
+        L.ants_lrf_free.argtypes = [_VP]
+        L.ants_lrf_free.restype = None
+        L.ants_reconstruct.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP, _VP, _VP,
+                                       _VP, _VP, _VP, _VP]
+        L.ants_reconstruct_host.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP, _VP,
+                                            _VP, _VP, _VP]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != ANTS_OK:
+        raise AntsError(rc, lib().ants_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP) if a is not None else C.cast(None, _DP)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _tptr(t) -> int | None:
+    """Device (or host) address of a torch tensor / numpy array; None -> NULL."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def last_launch_count() -> int:
+    return int(lib().ants_last_launch_count())
+
+
+# --------------------------------------------------------------------------
+# C-named calls
+# --------------------------------------------------------------------------
+
+
+def ants_version() -> int:
+    return int(lib().ants_version())
+
+
+def ants_ctx_create(device: int = 0) -> int:
+    h = _VP()
+    _check(lib().ants_ctx_create(device, C.byref(h)))
+    return h.value
+
+
+def ants_ctx_destroy(ctx: int) -> None:
+    lib().ants_ctx_destroy(ctx)
+
+
+def ants_detector_create(sensor_xy, rel_gain=None) -> int:
+    xy = _f64(sensor_xy)
+    g = _f64(rel_gain)
+    h = _VP()
+    _check(lib().ants_detector_create(int(xy.shape[0]), _dptr(xy), _dptr(g), C.byref(h)))
+    return h.value
+
+
+def ants_detector_free(det: int) -> None:
+    lib().ants_detector_free(det)
+
+
+def ants_lrf_create(ctx: int, det: int, type: int, n_int, lo, hi, shared: bool, coef, gain=None) -> int:
+    ni = (C.c_int * 3)(*[int(v) for v in (list(n_int) + [0, 0, 0])[:3]])
+    lo_ = _f64((list(lo) + [0.0, 0.0, 0.0])[:3])
+    hi_ = _f64((list(hi) + [0.0, 0.0, 0.0])[:3])
+    cf = _f64(coef)
+    g = _f64(gain)
+    h = _VP()
+    _check(lib().ants_lrf_create(ctx, det, int(type), ni, _dptr(lo_), _dptr(hi_), 1 if shared else 0, _dptr(cf),
+                                 _dptr(g), C.byref(h)))
+    return h.value
+
+
+def ants_lrf_fit(ctx: int, det: int, type: int, n_int, lo, hi, shared: bool, pts, vals, ridge: float = 0.0):
+    """Returns (handle, ridge_used)."""
+    ni = (C.c_int * 3)(*[int(v) for v in (list(n_int) + [0, 0, 0])[:3]])
+    lo_ = _f64((list(lo) + [0.0, 0.0, 0.0])[:3])
+    hi_ = _f64((list(hi) + [0.0, 0.0, 0.0])[:3])
+    p = _f64(pts)
+    v = _f64(vals)
+    if v.ndim == 1:
+        v = v[:, None]
+    lam = C.c_double()
+    h = _VP()
+    _check(lib().ants_lrf_fit(ctx, det, int(type), ni, _dptr(lo_), _dptr(hi_), 1 if shared else 0,
+                              int(p.shape[0]), _dptr(p), _dptr(v), float(ridge), C.byref(lam), C.byref(h)))
+    return h.value, lam.value
+
+
+def ants_lrf_coefficients(lrf: int) -> np.ndarray:
+    ns, nc = C.c_int(), C.c_int()
+    _check(lib().ants_lrf_coefficients(lrf, None, 0, C.byref(ns), C.byref(nc)))
+    out = np.empty((ns.value, nc.value))
+    _check(lib().ants_lrf_coefficients(lrf, _dptr(out), out.size, None, None))
+    return out
+
+
+def ants_lrf_eval(lrf: int, pts, out, stream=None) -> None:
+    _check(lib().ants_lrf_eval(lrf, _tptr(pts), int(pts.shape[0]), int(pts.shape[1]), _tptr(out),
+                               _stream_handle(stream)))
+
+
+def ants_lrf_save(lrf: int, path: str) -> None:
+    _check(lib().ants_lrf_save(lrf, path.encode()))
+
+
+def ants_lrf_load(ctx: int, det: int, path: str) -> int:
+    h = _VP()
+    _check(lib().ants_lrf_load(ctx, det, path.encode(), C.byref(h)))
+    return h.value
+
+
+def ants_lrf_free(lrf: int) -> None:
+    lib().ants_lrf_free(lrf)
+
+
+def ants_reconstruct(ctx: int, lrf: int, method: int, params, signals, n_sensors: int, xyz, E, logL, status,
+                     start_xyz=None, trace=None, stream=None, signal_dtype: int = ANTS_F32) -> None:
+    _check(lib().ants_reconstruct(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
+                                  int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz), _tptr(E),
+                                  _tptr(logL), _tptr(status), _tptr(trace), _stream_handle(stream)))
+
+
+def ants_reconstruct_host(ctx: int, lrf: int, method: int, params, signals, n_sensors: int, xyz, E, logL,
+                          status, start_xyz=None, signal_dtype: int = ANTS_F32) -> None:
+    _check(lib().ants_reconstruct_host(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
+                                       int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
+                                       _tptr(E), _tptr(logL), _tptr(status)))
+
+
+# --------------------------------------------------------------------------
+# owning wrappers
+# --------------------------------------------------------------------------
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.handle = ants_ctx_create(device)
+        self.device = device
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_ctx_destroy(self.handle)
+            self.handle = None
+
+
+class Detector:
+    def __init__(self, sensor_xy, rel_gain=None):
+        self.sensor_xy = np.asarray(sensor_xy, dtype=np.float64)
+        self.n_sensors = int(self.sensor_xy.shape[0])
+        self.handle = ants_detector_create(self.sensor_xy, rel_gain)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_detector_free(self.handle)
+            self.handle = None
+
+
+class Lrf:
+    """An LRF set living on the context's device."""
+
+    def __init__(self, ctx: Context, det: Detector, handle: int, type: int):
+        self.ctx, self.det, self.handle, self.type = ctx, det, handle, type
+        self.n_sensors = det.n_sensors
+
+    @classmethod
+    def from_coefficients(cls, ctx, det, type, n_int, lo, hi, coef, shared=False, gain=None):
+        return cls(ctx, det, ants_lrf_create(ctx.handle, det.handle, type, n_int, lo, hi, shared, coef, gain), type)
+
+    @classmethod
+    def fit(cls, ctx, det, type, n_int, lo, hi, pts, vals, shared=False, ridge=0.0):
+        h, lam = ants_lrf_fit(ctx.handle, det.handle, type, n_int, lo, hi, shared, pts, vals, ridge)
+        L = cls(ctx, det, h, type)
+        L.ridge_used = lam
+        return L
+
+    @classmethod
+    def load(cls, ctx, det, path):
+        h = ants_lrf_load(ctx.handle, det.handle, path)
+        L = cls(ctx, det, h, 0)
+        return L
+
+    def save(self, path):
+        ants_lrf_save(self.handle, path)
+
+    def coefficients(self) -> np.ndarray:
+        return ants_lrf_coefficients(self.handle)
+
+    def eval(self, pts, stream=None):
+        import torch
+        out = torch.empty((pts.shape[0], self.n_sensors), dtype=torch.float32, device=pts.device)
+        ants_lrf_eval(self.handle, pts, out, stream)
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_lrf_free(self.handle)
+            self.handle = None
+
+
+@dataclass
+class Result:
+    xyz: object
+    E: object
+    logL: object
+    status: object
+    trace: object = None
+
+
+def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=None, want_trace=False,
+                stream=None, method: int = ANTS_CGS_PLAIN) -> Result:
+    """Reconstruct device-resident signals [n, n_sensors] (torch, float32)."""
+    import torch
+    n = int(signals.shape[0])
+    dev = signals.device
+    xyz = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    E = torch.empty(n, dtype=torch.float32, device=dev)
+    logL = torch.empty(n, dtype=torch.float32, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    trace = torch.empty((n, params.iters), dtype=torch.int16, device=dev) if want_trace else None
+    n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
+    ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
+                     start_xyz=start_xyz, trace=trace, stream=stream)
+    return Result(xyz, E, logL, status, trace)
+
+
+def reconstruct_host(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndarray, start_xyz=None,
+                     method: int = ANTS_CGS_PLAIN) -> Result:
+    """Reconstruct host-resident signals (numpy float32 or pinned torch CPU tensor); synchronous."""
+    n = int(signals.shape[0])
+    xyz = np.empty((n, 3), dtype=np.float32)
+    E = np.empty(n, dtype=np.float32)
+    logL = np.empty(n, dtype=np.float32)
+    status = np.empty(n, dtype=np.int32)
+    n_s = int(signals.shape[1]) if signals.ndim == 2 else -1
+    ants_reconstruct_host(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
+                          start_xyz=start_xyz)
+    return Result(xyz, E, logL, status)

@@ -1,0 +1,466 @@
+// libants: handles, errors, LRF storage and evaluation, host-buffer driver.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+#include "bspline.cuh"
+
+namespace ants {
+
+static thread_local std::string t_err;
+static thread_local long t_launches = 0;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(ANTS_E_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void begin_call()
+{
+    t_err.clear();
+    t_launches = 0;
+}
+
+void count_launch(long n) { t_launches += n; }
+
+int lrf_dims(int type) { return type == ANTS_LRF_RADIAL ? 1 : (type == ANTS_LRF_XY ? 2 : 3); }
+
+}  // namespace ants
+
+using namespace ants;
+
+extern "C" {
+
+ANTS_API const char *ants_last_error(void) { return t_err.c_str(); }
+
+ANTS_API int ants_version(void) { return 1; }
+
+ANTS_API long ants_last_launch_count(void) { return t_launches; }
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+ANTS_API int ants_ctx_create(int device, ants_ctx **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_ctx_create: out is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    ANTS_CUDA_TRY(cudaGetDeviceCount(&n_dev), "cudaGetDeviceCount");
+    if (device < 0 || device >= n_dev)
+        return fail(ANTS_E_ARG, "ants_ctx_create: device %d not in [0, %d)", device, n_dev);
+    ANTS_CUDA_TRY(cudaSetDevice(device), "cudaSetDevice");
+    ants_ctx *c = new (std::nothrow) ants_ctx();
+    if (!c) return fail(ANTS_E_OOM, "ants_ctx_create: out of host memory");
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    c->n_sm = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    for (int k = 0; k < 2; ++k) {
+        e = cudaStreamCreateWithFlags(&c->stream[k], cudaStreamNonBlocking);
+        if (e != cudaSuccess) { ants_ctx_destroy(c); return cuda_fail(e, "cudaStreamCreate"); }
+    }
+    *out = c;
+    return ANTS_OK;
+}
+
+static void free_host_buffers(ants_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->d_sig[k]);
+        cudaFree(c->d_start[k]);
+        cudaFree(c->d_out[k]);
+        cudaFree(c->d_status[k]);
+        c->d_sig[k] = nullptr;
+        c->d_start[k] = nullptr;
+        c->d_out[k] = nullptr;
+        c->d_status[k] = nullptr;
+    }
+    c->host_cap_events = 0;
+    c->host_cap_sensors = 0;
+}
+
+ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_host_buffers(ctx);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);
+    delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// detector
+// ---------------------------------------------------------------------------
+
+ANTS_API int ants_detector_create(int n_sensors, const double *sensor_xy_host,
+                                  const double *rel_gain_host, ants_detector **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_detector_create: out is NULL");
+    *out = nullptr;
+    if (n_sensors < 1 || n_sensors > 1024)
+        return fail(ANTS_E_ARG, "ants_detector_create: n_sensors %d not in [1, 1024]", n_sensors);
+    if (!sensor_xy_host) return fail(ANTS_E_ARG, "ants_detector_create: sensor_xy_host is NULL");
+    for (int i = 0; i < 2 * n_sensors; ++i)
+        if (!std::isfinite(sensor_xy_host[i]))
+            return fail(ANTS_E_ARG, "ants_detector_create: sensor position %d not finite", i / 2);
+    if (rel_gain_host)
+        for (int i = 0; i < n_sensors; ++i)
+            if (!(rel_gain_host[i] > 0.0) || !std::isfinite(rel_gain_host[i]))
+                return fail(ANTS_E_ARG, "ants_detector_create: gain of sensor %d must be > 0", i);
+    ants_detector *d = new (std::nothrow) ants_detector();
+    if (!d) return fail(ANTS_E_OOM, "ants_detector_create: out of host memory");
+    d->n_s = n_sensors;
+    d->xy.assign(sensor_xy_host, sensor_xy_host + 2 * n_sensors);
+    d->gain.assign(n_sensors, 1.0);
+    if (rel_gain_host) d->gain.assign(rel_gain_host, rel_gain_host + n_sensors);
+    *out = d;
+    return ANTS_OK;
+}
+
+ANTS_API void ants_detector_free(ants_detector *det) { delete det; }
+
+// ---------------------------------------------------------------------------
+// LRF
+// ---------------------------------------------------------------------------
+
+static int upload_lrf(ants_lrf *L)
+{
+    std::vector<float> c(L->coef.size()), xy(L->sxy.size()), g(L->n_s), w(L->n_s);
+    int positive = 1;
+    for (size_t k = 0; k < c.size(); ++k) {
+        c[k] = (float)L->coef[k];
+        if (!(c[k] > 0.0f)) positive = 0;
+    }
+    for (size_t k = 0; k < xy.size(); ++k) xy[k] = (float)L->sxy[k];
+    for (int i = 0; i < L->n_s; ++i) {
+        g[i] = (float)L->gain[i];
+        w[i] = (float)(1.0 / L->rel_gain[i]);
+    }
+    ANTS_CUDA_TRY(cudaSetDevice(L->ctx->device), "cudaSetDevice");
+    ANTS_CUDA_TRY(cudaMalloc(&L->d_coef, c.size() * sizeof(float)), "cudaMalloc(lrf coef)");
+    ANTS_CUDA_TRY(cudaMalloc(&L->d_sxy, xy.size() * sizeof(float)), "cudaMalloc(lrf sxy)");
+    ANTS_CUDA_TRY(cudaMalloc(&L->d_gain, g.size() * sizeof(float)), "cudaMalloc(lrf gain)");
+    ANTS_CUDA_TRY(cudaMalloc(&L->d_cogw, w.size() * sizeof(float)), "cudaMalloc(lrf cogw)");
+    ANTS_CUDA_TRY(cudaMemcpy(L->d_coef, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice),
+                  "upload coef");
+    ANTS_CUDA_TRY(cudaMemcpy(L->d_sxy, xy.data(), xy.size() * sizeof(float), cudaMemcpyHostToDevice),
+                  "upload sxy");
+    ANTS_CUDA_TRY(cudaMemcpy(L->d_gain, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice),
+                  "upload gain");
+    ANTS_CUDA_TRY(cudaMemcpy(L->d_cogw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice),
+                  "upload cog weights");
+    LrfDev &D = L->dev;
+    D.type = L->type;
+    D.n_s = L->n_s;
+    D.shared = L->shared;
+    D.n_coef = L->n_coef;
+    for (int a = 0; a < 3; ++a) {
+        D.n_int[a] = L->n_int[a];
+        D.lo[a] = (float)L->lo[a];
+        D.hi[a] = (float)L->hi[a];
+        D.inv_h[a] = L->n_int[a] > 0 ? (float)((double)L->n_int[a] / (L->hi[a] - L->lo[a])) : 0.0f;
+    }
+    D.stride_y = L->n_int[0] + 3;
+    D.stride_z = (L->n_int[0] + 3) * (L->type == ANTS_LRF_RADIAL ? 1 : L->n_int[1] + 3);
+    D.positive = positive;
+    D.coef = L->d_coef;
+    D.sxy = L->d_sxy;
+    D.gain = L->d_gain;
+    D.cog_w = L->d_cogw;
+    return ANTS_OK;
+}
+
+ANTS_API void ants_lrf_free(ants_lrf *lrf)
+{
+    if (!lrf) return;
+    if (lrf->ctx) cudaSetDevice(lrf->ctx->device);
+    cudaFree(lrf->d_coef);
+    cudaFree(lrf->d_sxy);
+    cudaFree(lrf->d_gain);
+    cudaFree(lrf->d_cogw);
+    delete lrf;
+}
+
+ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                             const double *lo, const double *hi, int shared,
+                             const double *coef_host, const double *gain_host, ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create: out is NULL");
+    *out = nullptr;
+    if (!ctx || !det || !n_int || !lo || !hi || !coef_host)
+        return fail(ANTS_E_ARG, "ants_lrf_create: NULL argument");
+    if (type != ANTS_LRF_RADIAL && type != ANTS_LRF_XY && type != ANTS_LRF_XYZ)
+        return fail(ANTS_E_ARG, "ants_lrf_create: unknown LRF type %d", type);
+    if (shared && type != ANTS_LRF_RADIAL)
+        return fail(ANTS_E_ARG, "ants_lrf_create: shared coefficients need a RADIAL LRF");
+    if (gain_host && type != ANTS_LRF_RADIAL)
+        return fail(ANTS_E_ARG, "ants_lrf_create: gains apply to RADIAL LRFs only");
+    int dims = lrf_dims(type);
+    ants_lrf *L = new (std::nothrow) ants_lrf();
+    if (!L) return fail(ANTS_E_OOM, "ants_lrf_create: out of host memory");
+    L->ctx = ctx;
+    L->type = type;
+    L->n_s = det->n_s;
+    L->shared = shared ? 1 : 0;
+    L->n_coef = 1;
+    for (int a = 0; a < dims; ++a) {
+        if (n_int[a] < 1 || n_int[a] > 256 || !(lo[a] < hi[a]) || !std::isfinite(lo[a]) ||
+            !std::isfinite(hi[a])) {
+            delete L;
+            return fail(ANTS_E_ARG, "ants_lrf_create: axis %d needs 1 <= n_int <= 256, lo < hi", a);
+        }
+        L->n_int[a] = n_int[a];
+        L->lo[a] = lo[a];
+        L->hi[a] = hi[a];
+        L->n_coef *= n_int[a] + 3;
+    }
+    if (type == ANTS_LRF_RADIAL && lo[0] != 0.0) {
+        delete L;
+        return fail(ANTS_E_ARG, "ants_lrf_create: a RADIAL LRF starts at r = 0");
+    }
+    L->n_sets = L->shared ? 1 : L->n_s;
+    size_t nc = (size_t)L->n_sets * L->n_coef;
+    L->coef.assign(coef_host, coef_host + nc);
+    for (size_t k = 0; k < nc; ++k)
+        if (!std::isfinite(L->coef[k])) {
+            delete L;
+            return fail(ANTS_E_ARG, "ants_lrf_create: coefficient %zu not finite", k);
+        }
+    L->gain.assign(L->n_s, 1.0);
+    if (gain_host) L->gain.assign(gain_host, gain_host + L->n_s);
+    L->sxy = det->xy;
+    L->rel_gain = det->gain;
+    int rc = upload_lrf(L);
+    if (rc != ANTS_OK) {
+        std::string keep = t_err;
+        ants_lrf_free(L);
+        t_err = keep;
+        return rc;
+    }
+    *out = L;
+    return ANTS_OK;
+}
+
+ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_t count,
+                                   int *n_sets_out, int *n_coef_out)
+{
+    begin_call();
+    if (!lrf) return fail(ANTS_E_ARG, "ants_lrf_coefficients: lrf is NULL");
+    if (n_sets_out) *n_sets_out = lrf->n_sets;
+    if (n_coef_out) *n_coef_out = lrf->n_coef;
+    if (!coef_host) return ANTS_OK;
+    if (count < lrf->coef.size())
+        return fail(ANTS_E_ARG, "ants_lrf_coefficients: capacity %zu < %zu", count, lrf->coef.size());
+    std::memcpy(coef_host, lrf->coef.data(), lrf->coef.size() * sizeof(double));
+    return ANTS_OK;
+}
+
+// eta_i at arbitrary points: one thread per (point, sensor)
+__global__ void lrf_eval_kernel(LrfDev L, const float *pts, long n_pts, int dim, float *out)
+{
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = n_pts * L.n_s;
+    for (; tid < total; tid += (long)gridDim.x * blockDim.x) {
+        long p = tid / L.n_s;
+        int i = (int)(tid - p * L.n_s);
+        float x = pts[p * dim], y = pts[p * dim + 1], z = dim > 2 ? pts[p * dim + 2] : 0.0f;
+        bool ok;
+        float v = lrf_eta_point(L, i, x, y, z, ok);
+        out[tid] = ok ? v : __int_as_float(0x7fc00000);
+    }
+}
+
+ANTS_API int ants_lrf_eval(const ants_lrf *lrf, const float *pts_dev, long n_pts, int dim,
+                           float *out_dev, void *stream)
+{
+    begin_call();
+    if (!lrf) return fail(ANTS_E_ARG, "ants_lrf_eval: lrf is NULL");
+    if (n_pts < 0) return fail(ANTS_E_ARG, "ants_lrf_eval: n_pts < 0");
+    int need = lrf->type == ANTS_LRF_XYZ ? 3 : 2;
+    if (dim != need) return fail(ANTS_E_SHAPE, "ants_lrf_eval: dim %d, LRF needs %d", dim, need);
+    if (n_pts == 0) return ANTS_OK;
+    if (!pts_dev || !out_dev) return fail(ANTS_E_ARG, "ants_lrf_eval: NULL buffer");
+    ANTS_CUDA_TRY(cudaSetDevice(lrf->ctx->device), "cudaSetDevice");
+    long total = n_pts * lrf->n_s;
+    long blocks = (total + 255) / 256;
+    long cap = (long)lrf->ctx->n_sm * 16;
+    if (blocks > cap) blocks = cap;
+    lrf_eval_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(lrf->dev, pts_dev, n_pts, dim,
+                                                                          out_dev);
+    ANTS_CUDA_TRY(cudaGetLastError(), "lrf_eval_kernel launch");
+    count_launch();
+    return ANTS_OK;
+}
+
+// --- save / load ------------------------------------------------------------
+
+static const char kMagic[8] = {'A', 'N', 'T', 'S', 'L', 'R', 'F', '1'};
+
+ANTS_API int ants_lrf_save(const ants_lrf *lrf, const char *path)
+{
+    begin_call();
+    if (!lrf || !path) return fail(ANTS_E_ARG, "ants_lrf_save: NULL argument");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ANTS_E_IO, "ants_lrf_save: cannot open %s", path);
+    int32_t hdr[8] = {1, lrf->type, lrf->n_s, lrf->shared, lrf->n_int[0], lrf->n_int[1], lrf->n_int[2],
+                      lrf->n_coef};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 8, f) == 8 &&
+              fwrite(lrf->lo, sizeof(double), 3, f) == 3 && fwrite(lrf->hi, sizeof(double), 3, f) == 3 &&
+              fwrite(lrf->gain.data(), sizeof(double), lrf->n_s, f) == (size_t)lrf->n_s &&
+              fwrite(lrf->coef.data(), sizeof(double), lrf->coef.size(), f) == lrf->coef.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(ANTS_E_IO, "ants_lrf_save: write to %s failed", path);
+    return ANTS_OK;
+}
+
+ANTS_API int ants_lrf_load(ants_ctx *ctx, const ants_detector *det, const char *path, ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_load: out is NULL");
+    *out = nullptr;
+    if (!ctx || !det || !path) return fail(ANTS_E_ARG, "ants_lrf_load: NULL argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ANTS_E_IO, "ants_lrf_load: cannot open %s", path);
+    char magic[8];
+    int32_t hdr[8];
+    double lo[3], hi[3];
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              fread(hdr, sizeof(int32_t), 8, f) == 8 && hdr[0] == 1 &&
+              fread(lo, sizeof(double), 3, f) == 3 && fread(hi, sizeof(double), 3, f) == 3;
+    if (!ok) { fclose(f); return fail(ANTS_E_IO, "ants_lrf_load: %s is not an LRF file", path); }
+    int type = hdr[1], n_s = hdr[2], shared = hdr[3];
+    if (n_s != det->n_s) {
+        fclose(f);
+        return fail(ANTS_E_SHAPE, "ants_lrf_load: file has %d sensors, detector %d", n_s, det->n_s);
+    }
+    int n_int[3] = {hdr[4], hdr[5], hdr[6]};
+    int dims = (type == ANTS_LRF_RADIAL) ? 1 : (type == ANTS_LRF_XY ? 2 : (type == ANTS_LRF_XYZ ? 3 : 0));
+    long nc = 1;
+    for (int a = 0; a < dims; ++a) nc *= (n_int[a] >= 1 && n_int[a] <= 256) ? n_int[a] + 3 : -1000000;
+    if (dims == 0 || nc != hdr[7] || nc <= 0) {
+        fclose(f);
+        return fail(ANTS_E_IO, "ants_lrf_load: %s has an inconsistent header", path);
+    }
+    std::vector<double> gain(n_s), coef((size_t)(shared ? 1 : n_s) * nc);
+    ok = fread(gain.data(), sizeof(double), n_s, f) == (size_t)n_s &&
+         fread(coef.data(), sizeof(double), coef.size(), f) == coef.size();
+    fclose(f);
+    if (!ok) return fail(ANTS_E_IO, "ants_lrf_load: %s is truncated", path);
+    return ants_lrf_create(ctx, det, type, n_int, lo, hi, shared, coef.data(),
+                           type == ANTS_LRF_RADIAL ? gain.data() : nullptr, out);
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction entry points
+// ---------------------------------------------------------------------------
+
+static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+                        int signal_dtype, long n_events, int n_sensors)
+{
+    if (!ctx || !lrf || !params) return fail(ANTS_E_ARG, "ants_reconstruct: NULL ctx, lrf or params");
+    if (lrf->ctx != ctx) return fail(ANTS_E_ARG, "ants_reconstruct: lrf belongs to another context");
+    if (n_events < 0) return fail(ANTS_E_ARG, "ants_reconstruct: n_events < 0");
+    if (n_sensors != lrf->n_s)
+        return fail(ANTS_E_SHAPE, "ants_reconstruct: n_sensors %d but the LRF has %d", n_sensors, lrf->n_s);
+    if (signal_dtype != ANTS_F32) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: dtype %d", signal_dtype);
+    if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
+    return check_cgs_params(lrf, (const ants_cgs_params *)params);
+}
+
+ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+                              const void *signals_dev, int signal_dtype, long n_events, int n_sensors,
+                              const float *start_xyz_dev, float *xyz_dev, float *E_dev, float *logL_dev,
+                              int32_t *status_dev, int16_t *trace_dev, void *stream)
+{
+    begin_call();
+    int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
+    if (rc != ANTS_OK) return rc;
+    if (n_events == 0) return ANTS_OK;
+    if (!signals_dev || !xyz_dev || !E_dev || !logL_dev || !status_dev)
+        return fail(ANTS_E_ARG, "ants_reconstruct: NULL signal or output buffer");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, (const float *)signals_dev,
+                            n_events, start_xyz_dev, xyz_dev, E_dev, logL_dev, status_dev, trace_dev,
+                            (cudaStream_t)stream);
+}
+
+ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+                                   const void *signals_host, int signal_dtype, long n_events,
+                                   int n_sensors, const float *start_xyz_host, float *xyz_host,
+                                   float *E_host, float *logL_host, int32_t *status_host)
+{
+    begin_call();
+    int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
+    if (rc != ANTS_OK) return rc;
+    if (n_events == 0) return ANTS_OK;
+    if (!signals_host || !xyz_host || !E_host || !logL_host || !status_host)
+        return fail(ANTS_E_ARG, "ants_reconstruct_host: NULL signal or output buffer");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const ants_cgs_params &p = *(const ants_cgs_params *)params;
+    // chunk large enough to fill the GPU, small enough to pipeline
+    const long chunk = 1L << 17;
+    if (ctx->host_cap_events < (size_t)chunk || ctx->host_cap_sensors < n_sensors) {
+        free_host_buffers(ctx);
+        for (int k = 0; k < 2; ++k) {
+            cudaError_t e = cudaMalloc(&ctx->d_sig[k], (size_t)chunk * n_sensors * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->d_start[k], (size_t)chunk * 3 * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->d_out[k], (size_t)chunk * 5 * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status[k], (size_t)chunk * sizeof(int32_t));
+            if (e != cudaSuccess) {
+                free_host_buffers(ctx);
+                return fail(ANTS_E_OOM, "ants_reconstruct_host: device buffers: %s", cudaGetErrorString(e));
+            }
+        }
+        ctx->host_cap_events = chunk;
+        ctx->host_cap_sensors = n_sensors;
+    }
+    for (long off = 0, c = 0; off < n_events; off += chunk, ++c) {
+        int k = (int)(c & 1);
+        cudaStream_t s = ctx->stream[k];
+        long n = n_events - off < chunk ? n_events - off : chunk;
+        const float *sig = (const float *)signals_host + off * n_sensors;
+        ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_sig[k], sig, (size_t)n * n_sensors * sizeof(float),
+                                      cudaMemcpyHostToDevice, s), "H2D signals");
+        if (start_xyz_host)
+            ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_start[k], start_xyz_host + off * 3, (size_t)n * 3 * sizeof(float),
+                                          cudaMemcpyHostToDevice, s), "H2D start");
+        float *o = ctx->d_out[k];
+        rc = launch_cgs_plain(ctx, lrf, p, (const float *)ctx->d_sig[k], n,
+                              start_xyz_host ? ctx->d_start[k] : nullptr, o, o + 3 * chunk, o + 4 * chunk,
+                              ctx->d_status[k], nullptr, s);
+        if (rc != ANTS_OK) return rc;
+        ANTS_CUDA_TRY(cudaMemcpyAsync(xyz_host + off * 3, o, (size_t)n * 3 * sizeof(float),
+                                      cudaMemcpyDeviceToHost, s), "D2H xyz");
+        ANTS_CUDA_TRY(cudaMemcpyAsync(E_host + off, o + 3 * chunk, (size_t)n * sizeof(float),
+                                      cudaMemcpyDeviceToHost, s), "D2H E");
+        ANTS_CUDA_TRY(cudaMemcpyAsync(logL_host + off, o + 4 * chunk, (size_t)n * sizeof(float),
+                                      cudaMemcpyDeviceToHost, s), "D2H logL");
+        ANTS_CUDA_TRY(cudaMemcpyAsync(status_host + off, ctx->d_status[k], (size_t)n * sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, s), "D2H status");
+    }
+    ANTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream[0]), "stream 0");
+    ANTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream[1]), "stream 1");
+    return ANTS_OK;
+}
+
+}  // extern "C"

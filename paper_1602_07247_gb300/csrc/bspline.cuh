@@ -1,0 +1,96 @@
+// Uniform cubic B-spline evaluation on the device (LRFs of Sec. 6, 6.1).
+//
+// On a uniform knot grid the four basis functions that are non-zero on a span
+// are fixed cubic polynomials of the local parameter t in [0, 1]; the kernels
+// evaluate them in that segment form (the CPU oracle uses the Cox-de Boor
+// recursion instead).
+#pragma once
+
+#include "internal.cuh"
+
+namespace ants {
+
+// the four non-zero uniform cubic B-spline weights at local parameter t
+__device__ __forceinline__ void bs_weights(float t, float w[4])
+{
+    const float k = 1.0f / 6.0f;
+    float t2 = t * t, t3 = t2 * t, u = 1.0f - t;
+    w[0] = k * u * u * u;
+    w[1] = k * fmaf(3.0f, t3, fmaf(-6.0f, t2, 4.0f));
+    w[2] = k * fmaf(-3.0f, t3, fmaf(3.0f, t2, fmaf(3.0f, t, 1.0f)));
+    w[3] = k * t3;
+}
+
+// span index j in [0, n-1] of x and its local parameter t; x == hi falls in
+// the last span with t = 1
+__device__ __forceinline__ int bs_span(float x, float lo, float inv_h, int n, float &t)
+{
+    float u = (x - lo) * inv_h;
+    int j = (int)floorf(u);
+    j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+    t = u - (float)j;
+    return j;
+}
+
+__device__ __forceinline__ bool in_box(const LrfDev &L, float x, float y, float z)
+{
+    bool ok = x >= L.lo[0] && x <= L.hi[0] && y >= L.lo[1] && y <= L.hi[1];
+    if (L.type == ANTS_LRF_XYZ) ok = ok && z >= L.lo[2] && z <= L.hi[2];
+    return ok;
+}
+
+// axial LRF of sensor i at distance r (caller checks r <= hi)
+__device__ __forceinline__ float radial_eta(const LrfDev &L, int i, float r)
+{
+    float t, w[4];
+    int j = bs_span(r, 0.0f, L.inv_h[0], L.n_int[0], t);
+    bs_weights(t, w);
+    const float *c = L.coef + (L.shared ? 0 : i * L.n_coef) + j;
+    float f = c[0] * w[0];
+    f = fmaf(c[1], w[1], f);
+    f = fmaf(c[2], w[2], f);
+    f = fmaf(c[3], w[3], f);
+    return L.gain[i] * f;
+}
+
+// eta_i at one point; ok = false outside the domain (used by the evaluation
+// entry point and by per-event prologue/epilogue code)
+__device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, float y, float z, bool &ok)
+{
+    if (L.type == ANTS_LRF_RADIAL) {
+        float dx = x - L.sxy[2 * i], dy = y - L.sxy[2 * i + 1];
+        float r = sqrtf(fmaf(dx, dx, dy * dy));
+        ok = r <= L.hi[0];
+        return ok ? radial_eta(L, i, r) : 0.0f;
+    }
+    ok = in_box(L, x, y, z);
+    if (!ok) return 0.0f;
+    float tx, ty, tz = 0.0f, wx[4], wy[4], wz[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+    int jx = bs_span(x, L.lo[0], L.inv_h[0], L.n_int[0], tx);
+    int jy = bs_span(y, L.lo[1], L.inv_h[1], L.n_int[1], ty);
+    int jz = 0, nz = 1;
+    bs_weights(tx, wx);
+    bs_weights(ty, wy);
+    if (L.type == ANTS_LRF_XYZ) {
+        jz = bs_span(z, L.lo[2], L.inv_h[2], L.n_int[2], tz);
+        bs_weights(tz, wz);
+        nz = 4;
+    }
+    const float *c = L.coef + (size_t)i * L.n_coef;
+    float f = 0.0f;
+    for (int cz = 0; cz < nz; ++cz) {
+        float fz = 0.0f;
+        for (int b = 0; b < 4; ++b) {
+            const float *row = c + (jz + cz) * L.stride_z + (jy + b) * L.stride_y + jx;
+            float fr = row[0] * wx[0];
+            fr = fmaf(row[1], wx[1], fr);
+            fr = fmaf(row[2], wx[2], fr);
+            fr = fmaf(row[3], wx[3], fr);
+            fz = fmaf(fr, wy[b], fz);
+        }
+        f = fmaf(fz, wz[cz], f);
+    }
+    return f;
+}
+
+}  // namespace ants

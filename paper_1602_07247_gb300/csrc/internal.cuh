@@ -1,0 +1,89 @@
+// Internal declarations shared by the libants translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "ants.h"
+
+namespace ants {
+
+// ---------------------------------------------------------------------------
+// errors and launch accounting (thread-local, reported through the C ABI)
+// ---------------------------------------------------------------------------
+int fail(int code, const char *fmt, ...);          // records a message, returns code
+int cuda_fail(cudaError_t e, const char *what);    // ANTS_E_CUDA with the CUDA message
+void begin_call();                                 // clears the error, zeroes the launch count
+void count_launch(long n = 1);
+
+#define ANTS_CUDA_TRY(expr, what)                           \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ::ants::cuda_fail(_e, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device view of an LRF set, passed by value to kernels
+// ---------------------------------------------------------------------------
+struct LrfDev {
+    int type;          // ANTS_LRF_*
+    int n_s;           // sensors
+    int shared;        // RADIAL: one coefficient set for all sensors
+    int n_coef;        // coefficients per set
+    int n_int[3];      // intervals per axis
+    int stride_y;      // n_int[0] + 3
+    int stride_z;      // (n_int[0] + 3) * (n_int[1] + 3)
+    int positive;      // every coefficient > 0 (eta > 0 everywhere)
+    float lo[3], hi[3], inv_h[3];
+    const float *coef; // [n_sets][n_coef] FP32
+    const float *sxy;  // [n_s][2]
+    const float *gain; // [n_s] factor on a RADIAL LRF
+    const float *cog_w;// [n_s] 1 / relative gain (centroid weights)
+};
+
+}  // namespace ants
+
+struct ants_ctx {
+    int device = 0;
+    int n_sm = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream[2] = {nullptr, nullptr};
+    // chunk buffers of ants_reconstruct_host (grown on demand)
+    size_t host_cap_events = 0;
+    int host_cap_sensors = 0;
+    void *d_sig[2] = {nullptr, nullptr};
+    float *d_start[2] = {nullptr, nullptr};
+    float *d_out[2] = {nullptr, nullptr};   // xyz(3) E logL per event
+    int32_t *d_status[2] = {nullptr, nullptr};
+};
+
+struct ants_detector {
+    int n_s = 0;
+    std::vector<double> xy;    // [n_s][2]
+    std::vector<double> gain;  // [n_s] relative gains (1 when not given)
+};
+
+struct ants_lrf {
+    ants_ctx *ctx = nullptr;
+    int type = 0, n_s = 0, shared = 0, n_sets = 0, n_coef = 0;
+    int n_int[3] = {0, 0, 0};
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    std::vector<double> coef;      // FP64 master [n_sets][n_coef]
+    std::vector<double> gain;      // [n_s] (RADIAL factor; 1 otherwise)
+    std::vector<double> sxy;       // [n_s][2]
+    std::vector<double> rel_gain;  // [n_s] detector relative gains
+    float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
+    ants::LrfDev dev{};
+};
+
+namespace ants {
+int lrf_dims(int type);
+// launches of the reconstruction kernels (cgs.cu)
+int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p,
+                     const float *sig, long n_e, const float *start, float *xyz, float *E,
+                     float *logL, int32_t *status, int16_t *trace, cudaStream_t stream);
+int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
+}  // namespace ants
