@@ -169,6 +169,23 @@ static int upload_lrf(ants_lrf *L)
     ANTS_CUDA_TRY(cudaMemcpy(L->d_cogw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice),
                   "upload cog weights");
     LrfDev &D = L->dev;
+    D.coef2 = nullptr;
+    D.n_pairs = (L->n_s + 1) / 2;
+    D.pair_stride = 0;
+    if (L->type == ANTS_LRF_XY) {
+        const int ps = L->n_coef;
+        std::vector<float2> c2((size_t)D.n_pairs * ps);
+        for (int p = 0; p < D.n_pairs; ++p)
+            for (int k = 0; k < ps; ++k) {
+                int i0 = 2 * p, i1 = 2 * p + 1;
+                c2[(size_t)p * ps + k] = make_float2(c[(size_t)i0 * ps + k], i1 < L->n_s ? c[(size_t)i1 * ps + k] : 0.0f);
+            }
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_coef2, c2.size() * sizeof(float2)), "cudaMalloc(lrf coef pairs)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_coef2, c2.data(), c2.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                      "upload coef pairs");
+        D.coef2 = L->d_coef2;
+        D.pair_stride = ps;
+    }
     D.type = L->type;
     D.n_s = L->n_s;
     D.shared = L->shared;
@@ -197,6 +214,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_sxy);
     cudaFree(lrf->d_gain);
     cudaFree(lrf->d_cogw);
+    cudaFree(lrf->d_coef2);
     delete lrf;
 }
 

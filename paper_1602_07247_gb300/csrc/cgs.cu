@@ -309,6 +309,8 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
                      long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
                      int16_t *trace, cudaStream_t stream)
 {
+    if (cgs_xy_supported(lrf, p))
+        return launch_cgs_xy(ctx, lrf, p, sig, n_e, start, xyz, E, logL, status, trace, stream);
     CgsArgs a;
     a.L = lrf->dev;
     a.n_xy = p.n_xy;

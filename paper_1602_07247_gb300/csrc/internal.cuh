@@ -42,6 +42,11 @@ struct LrfDev {
     const float *sxy;  // [n_s][2]
     const float *gain; // [n_s] factor on a RADIAL LRF
     const float *cog_w;// [n_s] 1 / relative gain (centroid weights)
+    // XY LRFs: sensors interleaved in pairs, [n_pairs][n_int[1]+3][n_int[0]+3]
+    // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
+    const float2 *coef2;
+    int n_pairs;
+    int pair_stride;   // (n_int[1]+3) * (n_int[0]+3)
 };
 
 }  // namespace ants
@@ -76,6 +81,7 @@ struct ants_lrf {
     std::vector<double> sxy;       // [n_s][2]
     std::vector<double> rel_gain;  // [n_s] detector relative gains
     float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
+    float2 *d_coef2 = nullptr;
     ants::LrfDev dev{};
 };
 
@@ -86,4 +92,8 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
                      const float *sig, long n_e, const float *start, float *xyz, float *E,
                      float *logL, int32_t *status, int16_t *trace, cudaStream_t stream);
 int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
+bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
+int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, long n_e,
+                  const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
+                  cudaStream_t stream);
 }  // namespace ants

@@ -102,7 +102,19 @@ def sipm16x16_xy() -> Workload:
         event=dict(region="square", extent=24.0, e0=2000.0))
 
 
-WORKLOADS = {w().name: w for w in (hex19_radial, sipm8x8_xy, sipm16x16_xy)}
+def sipm4x4_xyz() -> Workload:
+    """Small 3D case: 4 x 4 SiPMs, pitch 6 mm; per-sensor XYZ LRFs of the
+    depth-dependent truth (8 x 8 x 4 intervals over 24 x 24 x 20 mm); sources
+    uniform in x, y and z; contracting grid 7 x 7 x 5, 5 grids."""
+    sxy = square_array(4, 6.0)
+    return Workload(
+        name="sipm4x4_xyz", sensor_xy=sxy, gains=sensor_gains(16, 0.05, 104), lrf_type="xyz",
+        n_int=(8, 8, 4), lo=(-12.0, -12.0, 0.0), hi=(12.0, 12.0, 20.0), shared=False, n_xy=7, iters=5,
+        step_xy=4.0, n_z=5, step_z=5.0, z0=10.0, n_events=10_000, event_seed=1004,
+        event=dict(region="square", extent=9.0, e0=3000.0, z_range=(0.0, 20.0)))
+
+
+WORKLOADS = {w().name: w for w in (hex19_radial, sipm8x8_xy, sipm16x16_xy, sipm4x4_xyz)}
 
 
 def get(name: str) -> Workload:

@@ -290,6 +290,28 @@ def pin_noise_free_recovery(mutant=0):
     assert np.abs(r["xyz"] - xt).max() < 1e-12 and abs(r["E"][0] / 1e4 - 1.0) < 1e-12
 
 
+def pin_noise_free_recovery_3d(mutant=0):
+    """The same Gibbs argument in 3D: an XYZ LRF, x_true on a node of the
+    first x-y-z grid, noise-free signals -> exactly x_true and E_true."""
+    import synth.workloads
+    w = synth.workloads.get("sipm4x4_xyz")
+    pts = synth.grid_samples(w.n_int, w.lo, w.hi, 2)
+    vals = synth.truth_eta(w.sensor_xy, w.gains, pts)
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals, mutant=mutant)
+    L = oracle.Lrf(oracle.XYZ, w.sensor_xy, w.n_int, w.lo, w.hi, coef)
+    P = oracle.CgsParams(n_xy=7, iters=4, step_xy=2.0, n_z=5, step_z=4.0)
+    xt = np.array([[2.5, -3.0, 6.0], [-5.0, 1.5, 14.0]])
+    off = np.array([[1, -2, -1], [-3, 0, 2]], dtype=float)
+    start = xt - off * np.array([2.0, 2.0, 4.0])
+    s = np.array([[1500.0], [2600.0]]) * oracle.lrf_eval(L, xt, mutant=mutant)
+    r = oracle.cgs(L, P, s, start_xyz=start, mutant=mutant)
+    assert np.abs(r["xyz"] - xt).max() < 1e-12, r["xyz"]
+    assert np.abs(r["E"] / np.array([1500.0, 2600.0]) - 1.0).max() < 1e-12
+    # flat index (iz, iy, ix) of the first choice
+    k0 = [((2 + int(o[2])) * 7 + (3 + int(o[1]))) * 7 + (3 + int(o[0])) for o in off]
+    assert list(r["trace"][:, 0]) == k0, (r["trace"][:, 0], k0)
+
+
 def pin_cg_matches_brute_force(mutant=0):
     """On a tiny detector (2 x 2 sensors) the contracting-grid result is the
     global maximum found by exhaustive search on a fine grid."""
@@ -392,6 +414,6 @@ def pin_replay(mutant=0):
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
-    pin_noise_free_recovery, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
+    pin_noise_free_recovery, pin_noise_free_recovery_3d, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
     pin_event_status, pin_replay,
 ]

@@ -193,3 +193,46 @@ def test_full_size_sampled(torch_cuda, ctx):
     rms = float(np.sqrt((d ** 2).sum(1).mean()))
     print("rms |dxy| vs truth", rms)
     assert rms < 2.0
+
+
+@pytest.mark.parametrize("n_xy", [5, 7, 9, 13, 15])
+@pytest.mark.parametrize("rows", [3, 4])
+def test_cgs_xy_grid_sizes_and_odd_sensor_counts(torch_cuda, ctx, n_xy, rows):
+    """Every templated grid size of the separable XY kernel; 9 sensors (odd:
+    one padding sensor) and 16 sensors (even)."""
+    sxy = synth.square_array(rows, 6.0)
+    half = 3.0 * rows
+    w = synth.workloads.sipm8x8_xy().with_(
+        name="small", sensor_xy=sxy, gains=synth.sensor_gains(rows * rows, 0.05, 7), n_int=(12, 12),
+        lo=(-half, -half), hi=(half, half), n_xy=n_xy, iters=5, step_xy=2.0 * half / (n_xy - 1),
+        event=dict(region="square", extent=half - 3.0, e0=2500.0))
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(333, seed=n_xy * 10 + rows)
+    gpu = run_gpu(torch_cuda, ctx, lrf, p, ev.signals)
+    stats = compare(w, L, ev.signals, gpu)
+    print(n_xy, rows, stats)
+
+
+def test_cgs_xy_table_in_global_memory(torch_cuda, ctx):
+    """16 x 16 SiPMs: the 1.25 MB coefficient table exceeds shared memory and
+    is read through L1/L2 instead."""
+    w = synth.workloads.get("sipm16x16_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(257, seed=5)
+    gpu = run_gpu(torch_cuda, ctx, lrf, p, ev.signals)
+    stats = compare(w, L, ev.signals, gpu)
+    print(stats)
+
+
+def test_cgs_xyz_parity(torch_cuda, ctx):
+    w = synth.workloads.get("sipm4x4_xyz")
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(401, seed=3)
+    gpu = run_gpu(torch_cuda, ctx, lrf, p, ev.signals)
+    stats = compare(w, L, ev.signals, gpu)
+    print(stats)
+    d = np.abs(gpu["xyz"] - ev.xyz)
+    print("median |dx|, |dz| vs truth", np.median(d[:, 0]), np.median(d[:, 2]))
