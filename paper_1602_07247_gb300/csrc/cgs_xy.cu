@@ -1,19 +1,26 @@
-// Contracting-grid ML search for XY LRFs (Sec. 5.1.2.2 with Sec. 6.1.1 XY
-// LRFs), separable form.  FP32.
+// Contracting-grid ML search for XY LRFs (Sec. 5.1.2.2 with the XY LRFs of
+// Sec. 6.1.1), separable form, FP32.
 //
-// Work decomposition (one warp per event, grid-stride over events):
-//   lane = (column j of the N x N grid, sensor slot q), Q = 32 / N slots;
-//   slot q owns sensor pairs q, q+Q, ...  (pairs are interleaved as float2
-//   in the coefficient table, so one 64-bit load serves two sensors).
-// A lane sweeps the N nodes of its column.  Because every node of a column
-// shares x, the tensor-product B-spline eta(x_j, y_k) = sum_a wy_k[a] T[iy_k+a]
-// with T[r] = sum_b wx_j[b] C[r][ix_j+b] reuses the x-contracted rows T of the
-// column: a 4-row window slides along y and only rows entering the window are
-// loaded (4 float2 loads + 4 packed FMAs per new row).
-// Per node and sensor: r = eta / eta(centre) (packed), log2 r on the MUFU
-// pipe, acc += s log2 r, dH += eta - eta(centre); the slots of a column are
-// summed with shuffles, and F = acc - S log2(1 + dH / H(centre)) decides the
-// argmax (ties to the lowest flat node index), as in the generic kernel.
+// Decomposition: a team of TEAM warps reconstructs one event at a time
+// (teams grid-stride over events; a block holds several teams and one
+// shared copy of the coefficient table).  Team lane t < N*Q is
+// (slot q = t / N, grid column j = t % N), Q = 32*TEAM / N.  Sensors are
+// interleaved in pairs (float2 coefficients), and slot q owns pairs
+// q, q+Q, q+2Q, ...; a lane processes them PPL at a time so that PPL
+// independent dependency chains are in flight.
+//
+// Column trick: every node of column j shares x_j, so with
+//   T[r] = sum_b wx_j[b] C[r][ix_j + b]          (x-contracted row r)
+//   eta(x_j, y_k) = sum_a wy_k[a] T[iy_k + a],
+// a 4-row window of T slides along y and only rows entering it are loaded.
+//
+// Per node and sensor, relative to the grid centre c (log2 units):
+//   acc += s log2(eta / eta_c),  dH += eta - eta_c,
+// and F = acc - S log2(1 + dH / H_c) is the Poisson log-likelihood with the
+// energy E = S/H profiled out (Sec. 5.1.2.2), up to a per-event constant.
+// Lanes store per-(node, slot) partial sums in shared memory; one thread per
+// node adds the slots, and a team argmax (ties to the lowest flat index)
+// picks the next centre.
 #include "bspline.cuh"
 #include "internal.cuh"
 
@@ -24,7 +31,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
 constexpr float kInvLn2 = 1.4426950408889634f;
-constexpr int kXyThreads = 384;  // 12 warps: up to 168 registers per thread, one block per SM
+constexpr int kXyThreads = 384;  // 12 warps per block, one block per SM
+constexpr int kPPL = 3;          // sensor pairs in flight per lane
 
 struct XyArgs {
     LrfDev L;
@@ -38,40 +46,27 @@ struct XyArgs {
     int16_t *trace;
 };
 
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// 64-bit load of one coefficient pair: from shared memory by 32-bit address,
+// or through the read-only path when the table stays in global memory
+template <bool SMEM>
+__device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
+{
+    if (SMEM) {
+        float2 v;
+        asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(saddr));
+        return v;
+    }
+    return __ldg(gptr);
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
-}
-
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
-{
-    float2 d;
-    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
-    unsigned long long rc = *reinterpret_cast<unsigned long long *>(&c);
-    unsigned long long rd;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
-    d = *reinterpret_cast<float2 *>(&rd);
-    return d;
-}
-
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b)
-{
-    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
-    unsigned long long rd;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    return *reinterpret_cast<float2 *>(&rd);
-}
-
-__device__ __forceinline__ float2 fsub2(float2 a, float2 b)
-{
-    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
-    unsigned long long rd;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    return *reinterpret_cast<float2 *>(&rd);
 }
 
 // s ln s - s - lgamma(s+1), s > 0 (Stirling series for s >= 10, A&S 6.1.41)
@@ -85,8 +80,7 @@ __device__ __forceinline__ float poisson_const(float s)
     return s * logf(s) - s - lgammaf(s + 1.0f);
 }
 
-// eta of both sensors of pair p at one point (inside the box), from the
-// interleaved table
+// eta of both sensors of pair p at one point inside the box
 __device__ __forceinline__ float2 pair_eta(const LrfDev &L, const float2 *coef2, int p, float x, float y)
 {
     float tx, ty, wx[4], wy[4];
@@ -107,24 +101,57 @@ __device__ __forceinline__ float2 pair_eta(const LrfDev &L, const float2 *coef2,
     return f;
 }
 
-// x-contracted row r of the lane's column: sum_b wx[b] C[r][ix+b] (both sensors)
-__device__ __forceinline__ float2 trow(const float2 *colbase, int stride_y, int r, const float2 wx2[4])
+// x-contracted row: sum_b wx[b] C[r][ix+b] for both sensors of a pair;
+// `g` / `sa` address C[r][ix] (global pointer / shared byte address)
+template <bool SMEM>
+__device__ __forceinline__ float2 trow(const float2 *g, unsigned sa, const float2 wx2[4])
 {
-    const float2 *row = colbase + r * stride_y;
-    float2 v = fmul2(wx2[0], row[0]);
-    v = ffma2(wx2[1], row[1], v);
-    v = ffma2(wx2[2], row[2], v);
-    v = ffma2(wx2[3], row[3], v);
+    float2 v = fmul2(wx2[0], ldc<SMEM>(g, sa));
+    v = ffma2(wx2[1], ldc<SMEM>(g + 1, sa + 8), v);
+    v = ffma2(wx2[2], ldc<SMEM>(g + 2, sa + 16), v);
+    v = ffma2(wx2[3], ldc<SMEM>(g + 3, sa + 24), v);
     return v;
 }
 
-template <int N, bool SMEM, bool FLOOR>
-__global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
+template <int TEAM>
+__device__ __forceinline__ void team_sync(int team)
+{
+    if (TEAM == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TEAM * 32) : "memory");
+    }
+}
+
+// per-team shared-memory layout (floats): signals, 1/eta_c, eta_c [n_pad each],
+// row bases as duplicated pairs [N][8] (16-byte aligned) and iy [N], partial
+// sums acc [N][LT+N] then dH [N][LT+N] (row stride = N mod 32: a warp of node
+// threads reads 32 different banks), reduction scratch [32]
+// (disjoint slots per phase: argmax 0..7, centre H 8..11, final H 12..15,
+// prologue sums 16..31, final logL 16..19)
+struct TeamSmem {
+    int n_pad, part_stride;
+    // the one place the layout is defined, for the launcher and the kernel
+    __device__ __host__ static TeamSmem make(int n_pad, int lt, int n) { return TeamSmem{n_pad, lt + n}; }
+    __device__ __host__ int sig() const { return 0; }
+    __device__ __host__ int ic() const { return n_pad; }
+    __device__ __host__ int ec() const { return 2 * n_pad; }  // holds -eta_c
+    __device__ __host__ int rows() const { return (3 * n_pad + 3) & ~3; }
+    __device__ __host__ int part(int N) const { return rows() + 9 * N; }
+    __device__ __host__ int red(int N) const { return part(N) + 2 * N * part_stride; }
+    __device__ __host__ int total(int N) const { return (red(N) + 32 + 3) & ~3; }
+};
+
+template <int N, int TEAM, bool SMEM, bool FLOOR>
+__global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int teams_per_block, int team_floats)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LT = 32 * TEAM;  // lanes per team
+    constexpr int Q = LT / N;      // sensor slots
+    constexpr int C = (N - 1) / 2;
     const LrfDev &L = a.L;
     const int n_s = L.n_s, n_pairs = L.n_pairs, n_pad = 2 * n_pairs;
-    const size_t table = SMEM ? (size_t)n_pairs * L.pair_stride : 0;
+    const size_t table = SMEM ? (size_t)n_pairs * L.pair_stride : 0;  // float2 entries
     float2 *cs = reinterpret_cast<float2 *>(smem_raw);
     const float2 *coef2 = L.coef2;
     if (SMEM) {
@@ -135,25 +162,34 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
         __syncthreads();
         coef2 = cs;
     }
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    float *wbase = reinterpret_cast<float *>(cs + table) + (size_t)wib * 3 * n_pad;
-    float *s_sig = wbase, *s_ic = wbase + n_pad, *s_ec = wbase + 2 * n_pad;
+    const size_t table_even = (table + 1) & ~(size_t)1;  // team data stays 16-byte aligned
+    const int team = threadIdx.x / LT;
+    if (team >= teams_per_block) return;  // no block-wide barrier follows
+    const int t = threadIdx.x - team * LT;  // lane within the team
+    const int lane = threadIdx.x & 31, wit = t >> 5;
+    const TeamSmem lay = TeamSmem::make(n_pad, LT, N);
+    float *ts = reinterpret_cast<float *>(cs + table_even) + (size_t)team * team_floats;
+    float *s_sig = ts + lay.sig(), *s_ic = ts + lay.ic(), *s_ec = ts + lay.ec();
+    float4 *s_wy = reinterpret_cast<float4 *>(ts + lay.rows());  // [N][2]: (w0,w0,w1,w1), (w2,w2,w3,w3)
+    int *s_iy = reinterpret_cast<int *>(ts + lay.rows() + 8 * N);
+    float *s_part = ts + lay.part(N);
+    float *s_red = ts + lay.red(N);
     const float2 *s_sig2 = reinterpret_cast<const float2 *>(s_sig);
     const float2 *s_ic2 = reinterpret_cast<const float2 *>(s_ic);
     const float2 *s_ec2 = reinterpret_cast<const float2 *>(s_ec);
 
-    constexpr int Q = 32 / N;
-    constexpr int C = (N - 1) / 2;
-    const int q = lane / N, j = lane - q * N;
+    const int q = t / N, j = t - q * N;
     const bool active = q < Q;
+    const int pairs_mine = active ? (n_pairs - q + Q - 1) / Q : 0;  // pairs q, q+Q, ... below n_pairs
     const float qnan = __int_as_float(0x7fc00000);
+    const long team_stride = (long)gridDim.x * teams_per_block;
 
-    for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb) {
-        // ---- prologue: signals, S, centroid, status --------------------------
+    for (long e = (long)blockIdx.x * teams_per_block + team; e < a.n_e; e += team_stride) {
+        // ---- prologue: signals, S, centroid, status ----------------------------
         const float *sg = a.sig + e * n_s;
         float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
         int bad = 0;
-        for (int i = lane; i < n_pad; i += 32) {
+        for (int i = t; i < n_pad; i += LT) {
             float v = i < n_s ? sg[i] : 0.0f;
             bad |= !(v >= 0.0f) || isinf(v);
             s_sig[i] = v;
@@ -170,6 +206,25 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
         Sx = warp_sum(Sx);
         Sy = warp_sum(Sy);
         Sw = warp_sum(Sw);
+        if (TEAM > 1) {
+            if (lane == 0) {
+                s_red[16 + 4 * wit] = S;
+                s_red[16 + 4 * wit + 1] = Sx;
+                s_red[16 + 4 * wit + 2] = Sy;
+                s_red[16 + 4 * wit + 3] = bad ? -1.0f : Sw;
+            }
+            team_sync<TEAM>(team);
+            S = Sx = Sy = Sw = 0.0f;
+            bad = 0;
+            for (int w = 0; w < TEAM; ++w) {
+                S += s_red[16 + 4 * w];
+                Sx += s_red[16 + 4 * w + 1];
+                Sy += s_red[16 + 4 * w + 2];
+                float v = s_red[16 + 4 * w + 3];
+                bad |= v < 0.0f;
+                Sw += v;
+            }
+        }
         int st = ANTS_EVT_OK;
         float cx = 0.0f, cy = 0.0f, cz = 0.0f;
         if (bad) st = ANTS_EVT_BAD_SIGNAL;
@@ -186,145 +241,179 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
             if (!in_box(L, cx, cy, cz)) st = ANTS_EVT_OUT_OF_DOMAIN;
         }
         if (st != ANTS_EVT_OK) {
-            if (lane == 0) {
+            if (t == 0) {
                 a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
                 a.E[e] = qnan;
                 a.logL[e] = qnan;
                 a.status[e] = st;
             }
             if (a.trace)
-                for (int it = lane; it < a.iters; it += 32) a.trace[e * a.iters + it] = -1;
-            __syncwarp();
+                for (int it = t; it < a.iters; it += LT) a.trace[e * a.iters + it] = -1;
+            team_sync<TEAM>(team);
             continue;
         }
 
         float sxy = a.step_xy;
         for (int it = 0; it < a.iters; ++it) {
-            // ---- centre: eta_i, 1/eta_i, H -------------------------------------
+            // ---- phase 1: centre values and row bases -------------------------
             float hc = 0.0f;
-            for (int p = lane; p < n_pairs; p += 32) {
+            for (int p = t; p < n_pairs; p += LT) {
                 float2 ec = pair_eta(L, coef2, p, cx, cy);
                 if (FLOOR) {
                     ec.x = fmaxf(ec.x, kEtaFloor);
                     ec.y = fmaxf(ec.y, kEtaFloor);
                 }
-                s_ec[2 * p] = ec.x;
-                s_ec[2 * p + 1] = ec.y;
+                s_ec[2 * p] = -ec.x;
+                s_ec[2 * p + 1] = -ec.y;
                 s_ic[2 * p] = __frcp_rn(ec.x);
                 s_ic[2 * p + 1] = __frcp_rn(ec.y);
                 hc += ec.x + (2 * p + 1 < n_s ? ec.y : 0.0f);
             }
+            if (t < N) {
+                float ty, w[4];
+                float y = fmaf((float)(t - C), sxy, cy);
+                int iy = bs_span(y, L.lo[1], L.inv_h[1], L.n_int[1], ty);
+                bs_weights(ty, w);
+                s_wy[2 * t] = make_float4(w[0], w[0], w[1], w[1]);
+                s_wy[2 * t + 1] = make_float4(w[2], w[2], w[3], w[3]);
+                s_iy[t] = iy;
+            }
             hc = warp_sum(hc);
+            if (TEAM > 1) {
+                if (lane == 0) s_red[8 + wit] = hc;
+                team_sync<TEAM>(team);
+                hc = 0.0f;
+                for (int w = 0; w < TEAM; ++w) hc += s_red[8 + w];
+            } else {
+                __syncwarp();
+            }
             const float inv_hc = __frcp_rn(hc);
 
-            // ---- row bases (lane k computes row k, then broadcast) ----------
-            float my_w[4], ty_;
-            int my_iy = 0;
-            bool my_yok = false;
-            {
-                int k = lane < N ? lane : 0;
-                float y = fmaf((float)(k - C), sxy, cy);
-                my_yok = y >= L.lo[1] && y <= L.hi[1];
-                my_iy = bs_span(y, L.lo[1], L.inv_h[1], L.n_int[1], ty_);
-                bs_weights(ty_, my_w);
-            }
-            float wy[N][4];
-            int iy[N];
-            unsigned yok_mask = __ballot_sync(kFull, my_yok && lane < N);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                iy[k] = __shfl_sync(kFull, my_iy, k);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) wy[k][t] = __shfl_sync(kFull, my_w[t], k);
-            }
-            // ---- the lane's column basis ------------------------------------
+            // ---- phase 2: each lane sums its column over its sensor pairs -----
             const float x = fmaf((float)(j - C), sxy, cx);
-            const bool xok = x >= L.lo[0] && x <= L.hi[0];
             float tx, wxs[4];
             const int ix = bs_span(x, L.lo[0], L.inv_h[0], L.n_int[0], tx);
             bs_weights(tx, wxs);
             float2 wx2[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) wx2[t] = make_float2(wxs[t], wxs[t]);
-            __syncwarp();
-
-            float acc[N], dh[N];
+            for (int b = 0; b < 4; ++b) wx2[b] = make_float2(wxs[b], wxs[b]);
+            const int ps = lay.part_stride;
+            const int sy = L.stride_y;
+            if (active && pairs_mine == 0) {
+                for (int k = 0; k < N; ++k) {
+                    s_part[k * ps + t] = 0.0f;
+                    s_part[(N + k) * ps + t] = 0.0f;
+                }
+            }
+            const unsigned rowb = (unsigned)sy * 8u;  // bytes per table row
+            for (int g = 0; g < pairs_mine; g += kPPL) {
+                const float2 *gb[kPPL];
+                unsigned sb[kPPL];
+                float2 sp[kPPL], ic[kPPL], nec[kPPL];
+                bool on[kPPL];
 #pragma unroll
-            for (int k = 0; k < N; ++k) acc[k] = dh[k] = 0.0f;
-            if (active) {
-                for (int p = q; p < n_pairs; p += Q) {
-                    const float2 sp = s_sig2[p], ic = s_ic2[p], ec = s_ec2[p];
-                    const float2 *colbase = coef2 + (size_t)p * L.pair_stride + ix;
-                    float2 W0 = trow(colbase, L.stride_y, iy[0], wx2);
-                    float2 W1 = trow(colbase, L.stride_y, iy[0] + 1, wx2);
-                    float2 W2 = trow(colbase, L.stride_y, iy[0] + 2, wx2);
-                    float2 W3 = trow(colbase, L.stride_y, iy[0] + 3, wx2);
+                for (int m = 0; m < kPPL; ++m) {
+                    on[m] = g + m < pairs_mine;
+                    const int p = q + (on[m] ? g + m : g) * Q;
+                    gb[m] = coef2 + (size_t)p * L.pair_stride + ix;
+                    sb[m] = SMEM ? (unsigned)__cvta_generic_to_shared(gb[m]) : 0u;
+                    sp[m] = on[m] ? s_sig2[p] : make_float2(0.0f, 0.0f);
+                    ic[m] = s_ic2[p];
+                    nec[m] = s_ec2[p];
+                }
+                float2 W[kPPL][4];
+                int top = s_iy[0];
 #pragma unroll
-                    for (int k = 0; k < N; ++k) {
-                        if (k > 0) {
-                            int adv = iy[k] - iy[k - 1];
-                            if (adv >= 4) {
-                                W0 = trow(colbase, L.stride_y, iy[k], wx2);
-                                W1 = trow(colbase, L.stride_y, iy[k] + 1, wx2);
-                                W2 = trow(colbase, L.stride_y, iy[k] + 2, wx2);
-                                W3 = trow(colbase, L.stride_y, iy[k] + 3, wx2);
-                            } else {
-                                for (int t = 0; t < adv; ++t) {
-                                    W0 = W1;
-                                    W1 = W2;
-                                    W2 = W3;
-                                    W3 = trow(colbase, L.stride_y, iy[k] + 4 - adv + t, wx2);
-                                }
-                            }
+                for (int m = 0; m < kPPL; ++m)
+#pragma unroll
+                    for (int a4 = 0; a4 < 4; ++a4)
+                        W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2);
+#pragma unroll 1
+                for (int k = 0; k < N; ++k) {
+                    const int iyk = s_iy[k];
+                    const int adv = iyk - top;
+                    const int r4 = top + 4;  // first row not yet in the window
+                    if (adv == 1) {
+#pragma unroll
+                        for (int m = 0; m < kPPL; ++m) {
+                            W[m][0] = W[m][1];
+                            W[m][1] = W[m][2];
+                            W[m][2] = W[m][3];
+                            W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
                         }
-                        float2 eta;
-                        eta.x = wy[k][0] * W0.x;
-                        eta.y = wy[k][0] * W0.y;
-                        eta.x = fmaf(wy[k][1], W1.x, eta.x);
-                        eta.y = fmaf(wy[k][1], W1.y, eta.y);
-                        eta.x = fmaf(wy[k][2], W2.x, eta.x);
-                        eta.y = fmaf(wy[k][2], W2.y, eta.y);
-                        eta.x = fmaf(wy[k][3], W3.x, eta.x);
-                        eta.y = fmaf(wy[k][3], W3.y, eta.y);
+                    } else if (adv == 2) {
+#pragma unroll
+                        for (int m = 0; m < kPPL; ++m) {
+                            W[m][0] = W[m][2];
+                            W[m][1] = W[m][3];
+                            W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                            W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
+                        }
+                    } else if (adv == 3) {
+#pragma unroll
+                        for (int m = 0; m < kPPL; ++m) {
+                            W[m][0] = W[m][3];
+                            W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                            W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
+                            W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2);
+                        }
+                    } else if (adv >= 4) {
+#pragma unroll
+                        for (int m = 0; m < kPPL; ++m)
+#pragma unroll
+                            for (int a4 = 0; a4 < 4; ++a4)
+                                W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
+                                                      wx2);
+                    }
+                    top = iyk;
+                    const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
+                    const float2 w0 = make_float2(wa.x, wa.y), w1 = make_float2(wa.z, wa.w);
+                    const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
+                    float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int m = 0; m < kPPL; ++m) {
+                        float2 eta = fmul2(w0, W[m][0]);
+                        eta = ffma2(w1, W[m][1], eta);
+                        eta = ffma2(w2, W[m][2], eta);
+                        eta = ffma2(w3, W[m][3], eta);
                         if (FLOOR) {
                             eta.x = fmaxf(eta.x, kEtaFloor);
                             eta.y = fmaxf(eta.y, kEtaFloor);
                         }
-                        const float2 r = fmul2(eta, ic);
-                        acc[k] = fmaf(sp.x, __log2f(r.x), acc[k]);
-                        acc[k] = fmaf(sp.y, __log2f(r.y), acc[k]);
-                        const float2 d = fsub2(eta, ec);
-                        dh[k] += d.x;
-                        dh[k] += d.y;
+                        const float2 r = fmul2(eta, ic[m]);
+                        acc = ffma2(sp[m], make_float2(__log2f(r.x), __log2f(r.y)), acc);
+                        if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
                     }
+                    float va = acc.x + acc.y, vd = dh.x + dh.y;
+                    float *pa = s_part + k * ps + t, *pd = s_part + (N + k) * ps + t;
+                    if (g > 0) {
+                        va += *pa;
+                        vd += *pd;
+                    }
+                    *pa = va;
+                    *pd = vd;
                 }
             }
-            // ---- sum the slots of each column into slot 0 -------------------
-#pragma unroll
-            for (int t = 1; t < Q; ++t) {
-                int src = lane + t * N;
-#pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    float va = __shfl_sync(kFull, acc[k], src < 32 ? src : lane);
-                    float vd = __shfl_sync(kFull, dh[k], src < 32 ? src : lane);
-                    if (q == 0 && src < 32) {
-                        acc[k] += va;
-                        dh[k] += vd;
-                    }
-                }
-            }
-            // ---- node scores, argmax (ties to the lowest flat index k*N+j) --
+            team_sync<TEAM>(team);
+
+            // ---- phase 3: node scores and team argmax --------------------------
             float bestF = -INFINITY;
             int bestk = 0x7fffffff;
-            if (q == 0) {
-#pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    bool ok = xok && ((yok_mask >> k) & 1u);
-                    float F = ok ? acc[k] - S * (log1pf(dh[k] * inv_hc) * kInvLn2) : -INFINITY;
-                    if (F > bestF) {
-                        bestF = F;
-                        bestk = k * N + j;
-                    }
+            for (int node = t; node < N * N; node += LT) {
+                const int k = node / N, jj = node - k * N;
+                float sa = 0.0f, sd = 0.0f;
+#pragma unroll 4
+                for (int qq = 0; qq < Q; ++qq) {
+                    sa += s_part[k * lay.part_stride + qq * N + jj];
+                    sd += s_part[(N + k) * lay.part_stride + qq * N + jj];
+                }
+                const float xn = fmaf((float)(jj - C), sxy, cx);
+                const float yn = fmaf((float)(k - C), sxy, cy);
+                const bool ok = xn >= L.lo[0] && xn <= L.hi[0] && yn >= L.lo[1] && yn <= L.hi[1];
+                const float F = ok ? sa - S * (log1pf(sd * inv_hc) * kInvLn2) : -INFINITY;
+                if (F > bestF) {
+                    bestF = F;
+                    bestk = node;
                 }
             }
             for (int o = 16; o; o >>= 1) {
@@ -335,44 +424,66 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
                     bestk = k2;
                 }
             }
+            if (TEAM > 1) {
+                if (lane == 0) {
+                    s_red[2 * wit] = bestF;
+                    s_red[2 * wit + 1] = __int_as_float(bestk);
+                }
+                team_sync<TEAM>(team);
+                bestF = s_red[0];
+                bestk = __float_as_int(s_red[1]);
+                for (int w = 1; w < TEAM; ++w) {
+                    float F2 = s_red[2 * w];
+                    int k2 = __float_as_int(s_red[2 * w + 1]);
+                    if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
+                        bestF = F2;
+                        bestk = k2;
+                    }
+                }
+            }
             const int bj = bestk % N, bk = bestk / N;
             cx = fmaf((float)(bj - C), sxy, cx);
             cy = fmaf((float)(bk - C), sxy, cy);
-            if (a.trace && lane == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
+            if (a.trace && t == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
             sxy *= a.shrink;
-            __syncwarp();
         }
 
-        // ---- energy and full Poisson log-likelihood at the result -----------
+        // ---- energy and full Poisson log-likelihood at the result -------------
         float H = 0.0f, ll = 0.0f;
-        float2 etas[2];
-        int np = 0;
-        for (int p = lane; p < n_pairs; p += 32, ++np) {
+        for (int p = t; p < n_pairs; p += LT) {
             float2 v = pair_eta(L, coef2, p, cx, cy);
             v.x = fmaxf(v.x, kEtaFloor);
             v.y = fmaxf(v.y, kEtaFloor);
-            if (np < 2) etas[np] = v;
             H += v.x + (2 * p + 1 < n_s ? v.y : 0.0f);
         }
         H = warp_sum(H);
+        if (TEAM > 1) {
+            if (lane == 0) s_red[12 + wit] = H;
+            team_sync<TEAM>(team);
+            H = 0.0f;
+            for (int w = 0; w < TEAM; ++w) H += s_red[12 + w];
+        }
         const float E = S / H;
-        np = 0;
-        for (int p = lane; p < n_pairs; p += 32, ++np) {
-            float2 v = np < 2 ? etas[np] : pair_eta(L, coef2, p, cx, cy);
-            v.x = fmaxf(v.x, kEtaFloor);
-            v.y = fmaxf(v.y, kEtaFloor);
-            float vv[2] = {v.x, v.y};
+        for (int p = t; p < n_pairs; p += LT) {
+            float2 v = pair_eta(L, coef2, p, cx, cy);
+            float vv[2] = {fmaxf(v.x, kEtaFloor), fmaxf(v.y, kEtaFloor)};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                int i = 2 * p + h;
+                const int i = 2 * p + h;
                 if (i >= n_s) continue;
-                float mu = E * vv[h];
-                float s = s_sig[i];
+                const float mu = E * vv[h];
+                const float s = s_sig[i];
                 ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
             }
         }
         ll = warp_sum(ll);
-        if (lane == 0) {
+        if (TEAM > 1) {
+            if (lane == 0) s_red[16 + wit] = ll;
+            team_sync<TEAM>(team);
+            ll = 0.0f;
+            for (int w = 0; w < TEAM; ++w) ll += s_red[16 + w];
+        }
+        if (t == 0) {
             a.xyz[3 * e] = cx;
             a.xyz[3 * e + 1] = cy;
             a.xyz[3 * e + 2] = cz;
@@ -380,28 +491,37 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a)
             a.logL[e] = ll;
             a.status[e] = ANTS_EVT_OK;
         }
-        __syncwarp();
+        team_sync<TEAM>(team);  // s_sig and s_red are reused by the next event
     }
 }
 
-template <int N>
-int launch_n(const ants_ctx *ctx, const XyArgs &a, bool floor_needed, cudaStream_t stream)
+template <int N, int TEAM>
+int launch_nt(const ants_ctx *ctx, const XyArgs &a, bool floor_needed, cudaStream_t stream)
 {
-    const int threads = kXyThreads, wpb = threads / 32;
-    const size_t table = (size_t)a.L.n_pairs * a.L.pair_stride * sizeof(float2);
-    const size_t per_warp = (size_t)wpb * 3 * 2 * a.L.n_pairs * sizeof(float);
-    bool smem_table = table + per_warp <= ctx->smem_optin;
-    size_t smem = per_warp + (smem_table ? table : 0);
-    cudaError_t e = cudaSuccess;
-    long blocks = (a.n_e + wpb - 1) / wpb;
-    long cap = (long)ctx->n_sm;
+    constexpr int LT = 32 * TEAM;
+    const TeamSmem lay = TeamSmem::make(2 * a.L.n_pairs, LT, N);
+    const int team_floats = lay.total(N);
+    const size_t table = (((size_t)a.L.n_pairs * a.L.pair_stride + 1) & ~(size_t)1) * sizeof(float2);
+    const size_t per_team = (size_t)team_floats * sizeof(float);
+    const int max_teams = kXyThreads / LT;
+    // keep the coefficient table in shared memory with as many teams as fit;
+    // otherwise read it through L1/L2 with every team
+    int teams = max_teams;
+    while (teams > 0 && table + teams * per_team > ctx->smem_optin) --teams;
+    const bool smem_table = teams > 0;
+    if (!smem_table) teams = max_teams;
+    const size_t smem = teams * per_team + (smem_table ? table : 0);
+    if (smem > ctx->smem_optin) return fail(ANTS_E_UNIMPLEMENTED, "cgs_xy: %zu bytes of shared memory", smem);
+    long blocks = (a.n_e + teams - 1) / teams;
+    const long cap = (long)ctx->n_sm;
     if (blocks > cap) blocks = cap;
-#define ANTS_XY_LAUNCH(SM, FL)                                                                               \
-    do {                                                                                                     \
-        e = cudaFuncSetAttribute(cgs_xy_kernel<N, SM, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                 (int)smem);                                                                 \
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_xy)");                            \
-        cgs_xy_kernel<N, SM, FL><<<(unsigned)blocks, threads, smem, stream>>>(a);                             \
+    cudaError_t e = cudaSuccess;
+#define ANTS_XY_LAUNCH(SM, FL)                                                                                 \
+    do {                                                                                                       \
+        e = cudaFuncSetAttribute(cgs_xy_kernel<N, TEAM, SM, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 (int)smem);                                                                   \
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_xy)");                              \
+        cgs_xy_kernel<N, TEAM, SM, FL><<<(unsigned)blocks, kXyThreads, smem, stream>>>(a, teams, team_floats); \
     } while (0)
     if (smem_table) {
         if (floor_needed) ANTS_XY_LAUNCH(true, true);
@@ -443,15 +563,15 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     a.status = status;
     a.trace = trace;
     // the floor is needed when an LRF value can be <= 0, or to neutralise the
-    // padding sensor of an odd sensor count (zero coefficients)
+    // zero-coefficient padding sensor of an odd sensor count
     bool floor_needed = !lrf->dev.positive || (lrf->n_s & 1);
     switch (p.n_xy) {
-    case 5: return launch_n<5>(ctx, a, floor_needed, stream);
-    case 7: return launch_n<7>(ctx, a, floor_needed, stream);
-    case 9: return launch_n<9>(ctx, a, floor_needed, stream);
-    case 11: return launch_n<11>(ctx, a, floor_needed, stream);
-    case 13: return launch_n<13>(ctx, a, floor_needed, stream);
-    default: return launch_n<15>(ctx, a, floor_needed, stream);
+    case 5: return launch_nt<5, 1>(ctx, a, floor_needed, stream);
+    case 7: return launch_nt<7, 1>(ctx, a, floor_needed, stream);
+    case 9: return launch_nt<9, 4>(ctx, a, floor_needed, stream);
+    case 11: return launch_nt<11, 4>(ctx, a, floor_needed, stream);
+    case 13: return launch_nt<13, 4>(ctx, a, floor_needed, stream);
+    default: return launch_nt<15, 4>(ctx, a, floor_needed, stream);
     }
 }
 
