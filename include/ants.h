@@ -242,6 +242,51 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
                                    float *xyz_host, float *E_host, float *logL_host,
                                    int32_t *status_host);
 
+/* ------------------------------------------------------------------------ */
+/* Reconstruction without device allocation                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of the static device staging area behind
+ * ants_reconstruct_host_noalloc (32 MiB). */
+#define ANTS_NOALLOC_STAGE_BYTES 33554432
+
+/* The same reconstruction as ants_reconstruct_host, for callers that must not
+ * allocate device memory.  The paper has no counterpart: this is a service of
+ * the library, not a step of the method.
+ *
+ * Who needs it: programs that hand all device memory to their own pool (or
+ * to another framework) at start-up, acquisition loops that cannot afford a
+ * failed allocation or the device-wide synchronisation that cudaMalloc and
+ * cudaFree may cause while data are streaming, and plug-ins whose host
+ * application forbids allocating on its GPU.  This call stages signals and
+ * results through a fixed area that the library declares statically, so it
+ * calls neither cudaMalloc nor cudaFree nor any allocating library routine.
+ *
+ * Arguments and results are those of ants_reconstruct_host (host buffers;
+ * synchronous: returns when the outputs are in host memory).  Limits and
+ * behaviour:
+ *   - The staging area holds ANTS_NOALLOC_STAGE_BYTES on every GPU that loads
+ *     the library, until the process exits.
+ *   - The whole batch must fit it: 4*n_events*n_sensors bytes of signals,
+ *     24*n_events bytes of results and, with start positions, 12*n_events
+ *     more, each region rounded up to 256 bytes — about
+ *     33,554,432 / (4*n_sensors + 24) events (119,837 for 64 sensors).
+ *     Larger batches are rejected with ANTS_E_ARG before any copy.
+ *   - The first call on a device looks up the area's device address with
+ *     cudaGetSymbolAddress while that device is current; make that first
+ *     call before any stream capture begins.
+ *   - Every call uses the same area and leaves the last call's data in it;
+ *     nothing in it has to start at zero.  Calls that overlap on the GPU (for
+ *     example from two host threads on the same device at once) race on the
+ *     area: serialise them.
+ * Errors: as ants_reconstruct_host (ANTS_E_ARG also for a batch beyond the
+ * capacity). */
+ANTS_API int ants_reconstruct_host_noalloc(ants_ctx *ctx, const ants_lrf *lrf, int method,
+                                           const void *params, const void *signals_host,
+                                           int signal_dtype, long n_events, int n_sensors,
+                                           const float *start_xyz_host, float *xyz_host,
+                                           float *E_host, float *logL_host, int32_t *status_host);
+
 /* Number of kernels the calling thread's last successful ants_* call
  * launched (for accounting in benchmarks). */
 ANTS_API long ants_last_launch_count(void);

@@ -28,6 +28,7 @@ ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
 ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
 ANTS_CGS_PLAIN = 0
 ANTS_F32 = 0
+ANTS_NOALLOC_STAGE_BYTES = 33554432
 
 _STATUS_NAMES = {0: "ANTS_OK", -1: "ANTS_E_ARG", -2: "ANTS_E_CUDA", -3: "ANTS_E_OOM", -4: "ANTS_E_LRF",
                  -5: "ANTS_E_SHAPE", -6: "ANTS_E_TIMEOUT", -7: "ANTS_E_INTERNAL", -8: "ANTS_E_UNIMPLEMENTED",
@@ -84,6 +85,8 @@ def lib() -> C.CDLL:
                                        _VP, _VP, _VP, _VP]
         L.ants_reconstruct_host.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP, _VP,
                                             _VP, _VP, _VP]
+        L.ants_reconstruct_host_noalloc.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP,
+                                                    _VP, _VP, _VP, _VP]
         _lib = L
     return _lib
 
@@ -225,6 +228,15 @@ def ants_reconstruct_host(ctx: int, lrf: int, method: int, params, signals, n_se
                                        _tptr(E), _tptr(logL), _tptr(status)))
 
 
+def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signals, n_sensors: int, xyz, E, logL,
+                                  status, start_xyz=None, signal_dtype: int = ANTS_F32) -> None:
+    """Host-buffer reconstruction through the library's static staging area
+    (no device allocation; batch limited by ANTS_NOALLOC_STAGE_BYTES)."""
+    _check(lib().ants_reconstruct_host_noalloc(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
+                                               int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
+                                               _tptr(E), _tptr(logL), _tptr(status)))
+
+
 # --------------------------------------------------------------------------
 # owning wrappers
 # --------------------------------------------------------------------------
@@ -319,6 +331,20 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
                      start_xyz=start_xyz, trace=trace, stream=stream)
     return Result(xyz, E, logL, status, trace)
+
+
+def reconstruct_host_noalloc(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndarray, start_xyz=None,
+                             method: int = ANTS_CGS_PLAIN) -> Result:
+    """As reconstruct_host, without any device allocation (static staging area)."""
+    n = int(signals.shape[0])
+    xyz = np.empty((n, 3), dtype=np.float32)
+    E = np.empty(n, dtype=np.float32)
+    logL = np.empty(n, dtype=np.float32)
+    status = np.empty(n, dtype=np.int32)
+    n_s = int(signals.shape[1]) if signals.ndim == 2 else -1
+    ants_reconstruct_host_noalloc(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
+                                  start_xyz=start_xyz)
+    return Result(xyz, E, logL, status)
 
 
 def reconstruct_host(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndarray, start_xyz=None,
