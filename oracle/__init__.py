@@ -341,3 +341,98 @@ def brute_force(lrf: Lrf, sig, x_rng, nx, y_rng, ny, z=0.0, mutant: int = 0):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+# --------------------------------------------------------------------------
+# learned proposal (multilayer perceptron) and deviance
+# --------------------------------------------------------------------------
+
+
+class _Mlp(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("n_hid", C.c_int), ("n_out", C.c_int), ("W1", _D), ("b1", _D), ("W2", _D),
+                ("b2", _D), ("W3", _D), ("b3", _D)]
+
+
+@dataclass
+class Mlp:
+    """Weights of u -> GELU(W1 u + b1) -> GELU(W2 . + b2) -> W3 . + b3 (row-major [out][in])."""
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+    W3: np.ndarray
+    b3: np.ndarray
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def shape(self):
+        return self.W1.shape[1], self.W1.shape[0], self.W3.shape[0]
+
+    def _struct(self) -> _Mlp:
+        arrs = [_f64(a) for a in (self.W1, self.b1, self.W2, self.b2, self.W3, self.b3)]
+        self._keep[:] = arrs
+        s = _Mlp()
+        s.n_in, s.n_hid, s.n_out = self.shape
+        s.W1, s.b1, s.W2, s.b2, s.W3, s.b3 = [_d(a) for a in arrs]
+        return s
+
+    def params(self):
+        return [self.W1, self.b1, self.W2, self.b2, self.W3, self.b3]
+
+
+def _declare_mlp(L):
+    L.or_gelu_value.argtypes = [C.c_double]
+    L.or_gelu_value.restype = C.c_double
+    L.or_mlp_forward.argtypes = [C.POINTER(_Mlp), C.c_long, _D, _D]
+    L.or_mlp_loss_grad.argtypes = [C.POINTER(_Mlp), C.c_long, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.or_mlp_loss_grad.restype = C.c_double
+    L.or_adam_step.argtypes = [C.c_long, _D, _D, _D, _D, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.or_deviance_at.argtypes = [C.POINTER(_Lrf), C.c_long, _D, _D, _D]
+
+
+def _mlib(mutant=0):
+    L = lib(mutant)
+    if not getattr(L, "_mlp_declared", False):
+        _declare_mlp(L)
+        L._mlp_declared = True
+    return L
+
+
+def gelu(x: float, mutant: int = 0) -> float:
+    return float(_mlib(mutant).or_gelu_value(float(x)))
+
+
+def mlp_forward(mlp: Mlp, sig, mutant: int = 0) -> np.ndarray:
+    """Normalise signals by their sum and run the network: [n, n_out]."""
+    sig = _f64(sig)
+    s = mlp._struct()
+    out = np.empty((sig.shape[0], s.n_out))
+    _mlib(mutant).or_mlp_forward(C.byref(s), sig.shape[0], _d(sig), _d(out))
+    return out
+
+
+def mlp_loss_grad(mlp: Mlp, sig, target, mutant: int = 0):
+    """Mean squared error and its gradient [gW1, gb1, gW2, gb2, gW3, gb3]."""
+    sig, target = _f64(sig), _f64(target)
+    s = mlp._struct()
+    grads = [np.zeros_like(_f64(a)) for a in mlp.params()]
+    loss = _mlib(mutant).or_mlp_loss_grad(C.byref(s), sig.shape[0], _d(sig), _d(target), *[_d(g) for g in grads])
+    return float(loss), grads
+
+
+def adam_step(p: np.ndarray, g, m: np.ndarray, v: np.ndarray, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8,
+              mutant: int = 0) -> None:
+    """In-place Adam update of float64 arrays p, m, v."""
+    g = _f64(g)
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _mlib(mutant).or_adam_step(p.size, _d(p), _d(g), _d(m), _d(v), int(t), lr, b1, b2, eps)
+
+
+def deviance_at(lrf: Lrf, sig, xyz, mutant: int = 0) -> np.ndarray:
+    """Poisson deviance 2 sum[s ln(s/mu) - (s - mu)] at the given positions (E = S/H)."""
+    sig, xyz = _f64(sig), _f64(xyz)
+    s = lrf._struct()
+    D = np.empty(sig.shape[0])
+    _mlib(mutant).or_deviance_at(C.byref(s), sig.shape[0], _d(sig), _d(xyz), _d(D))
+    return D

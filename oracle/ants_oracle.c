@@ -729,3 +729,174 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal: multilayer perceptron (the ANN role of Sec. 5.1.3)      */
+/* ------------------------------------------------------------------------ */
+/* u = s / sum(s); z1 = W1 u + b1; h1 = GELU(z1); z2 = W2 h1 + b2;
+ * h2 = GELU(z2); o = W3 h2 + b3.  GELU(x) = x Phi(x) = 0.5 x (1 + erf(x/sqrt 2)).
+ * Weights are row-major [out][in].  Training loss: mean squared error over
+ * the batch and the n_out outputs. */
+
+typedef struct {
+    int n_in, n_hid, n_out;
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+} or_mlp;
+
+static double or_gelu(double x)
+{
+#if OR_MUTANT == 10
+    return 0.5 * x * (1.0 + erf(x));
+#else
+    return 0.5 * x * (1.0 + erf(x / sqrt(2.0)));
+#endif
+}
+
+/* d GELU / dx = Phi(x) + x phi(x) */
+static double or_gelu_grad(double x)
+{
+    const double inv_sqrt_2pi = 0.3989422804014327;
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * inv_sqrt_2pi * exp(-0.5 * x * x);
+}
+
+double or_gelu_value(double x) { return or_gelu(x); }
+
+/* Forward pass of one event (input already normalised); act (nullable)
+ * receives z1, h1, z2, h2 (4 * n_hid values). */
+static void or_mlp_forward1(const or_mlp *M, const double *u, double *o, double *act)
+{
+    int H = M->n_hid;
+    double *z1 = (double *)malloc(sizeof(double) * 4 * H);
+    double *h1 = z1 + H, *z2 = z1 + 2 * H, *h2 = z1 + 3 * H;
+    for (int j = 0; j < H; ++j) {
+        double v = M->b1[j];
+        for (int i = 0; i < M->n_in; ++i) v += M->W1[(size_t)j * M->n_in + i] * u[i];
+        z1[j] = v;
+        h1[j] = or_gelu(v);
+    }
+    for (int j = 0; j < H; ++j) {
+        double v = M->b2[j];
+        for (int i = 0; i < H; ++i) v += M->W2[(size_t)j * H + i] * h1[i];
+        z2[j] = v;
+        h2[j] = or_gelu(v);
+    }
+    for (int k = 0; k < M->n_out; ++k) {
+        double v = M->b3[k];
+        for (int i = 0; i < H; ++i) v += M->W3[(size_t)k * H + i] * h2[i];
+        o[k] = v;
+    }
+    if (act) memcpy(act, z1, sizeof(double) * 4 * H);
+    free(z1);
+}
+
+/* u = s / sum(s) for every event, then the forward pass: out[n][n_out]. */
+void or_mlp_forward(const or_mlp *M, long n, const double *sig, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < n; ++e) {
+        double *u = (double *)malloc(sizeof(double) * M->n_in);
+        double S = 0.0;
+        for (int i = 0; i < M->n_in; ++i) S += sig[e * M->n_in + i];
+        for (int i = 0; i < M->n_in; ++i) u[i] = S > 0.0 ? sig[e * M->n_in + i] / S : 0.0;
+        or_mlp_forward1(M, u, out + e * M->n_out, NULL);
+        free(u);
+    }
+}
+
+/* Mean squared error L = 1/(n n_out) sum (o - t)^2 over a batch of signals,
+ * and its gradient by back-propagation, accumulated in the order of the
+ * parameters: gW1, gb1, gW2, gb2, gW3, gb3 (same shapes).  Returns L. */
+double or_mlp_loss_grad(const or_mlp *M, long n, const double *sig, const double *target, double *gW1,
+                        double *gb1, double *gW2, double *gb2, double *gW3, double *gb3)
+{
+    int H = M->n_hid, I = M->n_in, O = M->n_out;
+    memset(gW1, 0, sizeof(double) * H * I);
+    memset(gb1, 0, sizeof(double) * H);
+    memset(gW2, 0, sizeof(double) * H * H);
+    memset(gb2, 0, sizeof(double) * H);
+    memset(gW3, 0, sizeof(double) * O * H);
+    memset(gb3, 0, sizeof(double) * O);
+    double *u = (double *)malloc(sizeof(double) * I);
+    double *act = (double *)malloc(sizeof(double) * 4 * H);
+    double *o = (double *)malloc(sizeof(double) * O);
+    double *dz1 = (double *)malloc(sizeof(double) * H), *dz2 = (double *)malloc(sizeof(double) * H);
+    double loss = 0.0, scale = 1.0 / ((double)n * O);
+    for (long e = 0; e < n; ++e) {
+        double S = 0.0;
+        for (int i = 0; i < I; ++i) S += sig[e * I + i];
+        for (int i = 0; i < I; ++i) u[i] = S > 0.0 ? sig[e * I + i] / S : 0.0;
+        or_mlp_forward1(M, u, o, act);
+        double *z1 = act, *h1 = act + H, *z2 = act + 2 * H, *h2 = act + 3 * H;
+        /* dL/do = 2 (o - t) / (n O) */
+        double dout[16];
+        for (int k = 0; k < O; ++k) {
+            double d = o[k] - target[e * O + k];
+            loss += d * d * scale;
+#if OR_MUTANT == 11
+            dout[k] = d * scale;
+#else
+            dout[k] = 2.0 * d * scale;
+#endif
+        }
+        for (int k = 0; k < O; ++k) {
+            gb3[k] += dout[k];
+            for (int i = 0; i < H; ++i) gW3[(size_t)k * H + i] += dout[k] * h2[i];
+        }
+        for (int i = 0; i < H; ++i) {
+            double v = 0.0;
+            for (int k = 0; k < O; ++k) v += M->W3[(size_t)k * H + i] * dout[k];
+            dz2[i] = v * or_gelu_grad(z2[i]);
+        }
+        for (int j = 0; j < H; ++j) {
+            gb2[j] += dz2[j];
+            for (int i = 0; i < H; ++i) gW2[(size_t)j * H + i] += dz2[j] * h1[i];
+        }
+        for (int i = 0; i < H; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < H; ++j) v += M->W2[(size_t)j * H + i] * dz2[j];
+            dz1[i] = v * or_gelu_grad(z1[i]);
+        }
+        for (int j = 0; j < H; ++j) {
+            gb1[j] += dz1[j];
+            for (int i = 0; i < I; ++i) gW1[(size_t)j * I + i] += dz1[j] * u[i];
+        }
+    }
+    free(u);
+    free(act);
+    free(o);
+    free(dz1);
+    free(dz2);
+    return loss;
+}
+
+/* One Adam step (Kingma & Ba, Algorithm 1) on n parameters, step t >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr mhat / (sqrt(vhat) + eps)
+ * with mhat = m / (1 - b1^t), vhat = v / (1 - b2^t). */
+void or_adam_step(long n, double *p, const double *g, double *m, double *v, int t, double lr, double b1, double b2,
+                  double eps)
+{
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        p[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* Poisson deviance D = 2 sum_i [ s_i ln(s_i / mu_i) - (s_i - mu_i) ] at the
+ * given positions (s_i = 0 terms: 2 mu_i) -- twice the gap to the saturated
+ * likelihood, used to flag events for the fallback search. */
+void or_deviance_at(const or_lrf *L, long n_e, const double *sig, const double *xyz, double *D)
+{
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        double E, ll;
+        or_energy_logl(L, s, xyz[3 * e], xyz[3 * e + 1], xyz[3 * e + 2], &E, &ll);
+        double sat = 0.0;
+        for (int i = 0; i < L->n_sensors; ++i)
+            if (s[i] > 0.0) sat += s[i] * log(s[i]) - s[i] - lgamma(s[i] + 1.0);
+        D[e] = 2.0 * (sat - ll);
+    }
+}

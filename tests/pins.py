@@ -411,9 +411,97 @@ def pin_replay(mutant=0):
     assert np.all(rp["n_bad"] >= 1)
 
 
+# --------------------------------------------------------------------------
+# learned proposal
+# --------------------------------------------------------------------------
+
+
+def _small_mlp(seed, n_in=6, n_hid=5, n_out=3, scale=0.7):
+    rng = np.random.default_rng(seed)
+    return oracle.Mlp(rng.normal(0, scale, (n_hid, n_in)), rng.normal(0, 0.3, n_hid),
+                      rng.normal(0, scale, (n_hid, n_hid)), rng.normal(0, 0.3, n_hid),
+                      rng.normal(0, scale, (n_out, n_hid)), rng.normal(0, 0.3, n_out))
+
+
+def pin_gelu(mutant=0):
+    """GELU(x) = x Phi(x): Phi from scipy's normal CDF; GELU(x) - GELU(-x) = x."""
+    from scipy.stats import norm
+    for x in (-3.0, -0.7, 0.0, 0.4, 1.3, 3.0):
+        assert abs(oracle.gelu(x, mutant) - x * norm.cdf(x)) < 1e-14
+        assert abs(oracle.gelu(x, mutant) - oracle.gelu(-x, mutant) - x) < 1e-14
+
+
+def pin_mlp_forward(mutant=0):
+    """With W1 = W2 = 0 the output is W3 GELU(b2) + b3 (GELU by scipy); the
+    sum normalisation makes the output invariant to scaling all signals."""
+    from scipy.stats import norm
+    M = _small_mlp(3)
+    M.W1[:] = 0.0
+    M.W2[:] = 0.0
+    sig = np.random.default_rng(1).uniform(1, 50, (4, 6))
+    want = M.W3 @ (M.b2 * norm.cdf(M.b2)) + M.b3
+    out = oracle.mlp_forward(M, sig, mutant)
+    assert np.abs(out - want[None, :]).max() < 1e-12
+    M = _small_mlp(4)
+    a = oracle.mlp_forward(M, sig, mutant)
+    b = oracle.mlp_forward(M, 7.5 * sig, mutant)
+    assert np.abs(a - b).max() < 1e-12
+
+
+def pin_mlp_gradient(mutant=0):
+    """Back-propagated gradients of the mean squared error match central
+    differences of the loss (relative error <= 1e-6)."""
+    M = _small_mlp(5)
+    rng = np.random.default_rng(6)
+    sig = rng.uniform(1, 40, (7, 6))
+    tgt = rng.normal(0, 1, (7, 3))
+    loss, grads = oracle.mlp_loss_grad(M, sig, tgt, mutant)
+    h = 1e-6
+    for P, G in zip(M.params(), grads):
+        flat, gflat = P.reshape(-1), G.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 6)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = oracle.mlp_loss_grad(M, sig, tgt, mutant)
+            flat[idx] = old - h
+            lm, _ = oracle.mlp_loss_grad(M, sig, tgt, mutant)
+            flat[idx] = old
+            num = (lp - lm) / (2 * h)
+            assert abs(num - gflat[idx]) <= 1e-6 * max(1e-3, abs(num)), (num, gflat[idx])
+
+
+def pin_adam(mutant=0):
+    """From m = v = 0 the first Adam step moves every parameter by
+    -lr g / (|g| + eps); the second step follows the bias-corrected moments."""
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p = np.array([1.0, 2.0, 3.0, 4.0])
+    m, v = np.zeros(4), np.zeros(4)
+    oracle.adam_step(p, g, m, v, 1, lr=0.01, mutant=mutant)
+    want = np.array([1.0, 2.0, 3.0, 4.0]) - 0.01 * g / (np.abs(g) + 1e-8)
+    assert np.abs(p - want).max() < 1e-12
+    g2 = np.array([0.1, 0.1, 0.1, 0.1])
+    m2 = 0.9 * (0.1 * g) + 0.1 * g2
+    v2 = 0.999 * (0.001 * g * g) + 0.001 * g2 * g2
+    want2 = want - 0.01 * (m2 / (1 - 0.81)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-8)
+    oracle.adam_step(p, g2, m, v, 2, lr=0.01, mutant=mutant)
+    assert np.abs(p - want2).max() < 1e-12
+
+
+def pin_deviance(mutant=0):
+    """The Poisson deviance is 0 for noise-free signals at the true position
+    and positive elsewhere."""
+    L, _ = _small_xy_lrf(mutant)
+    xt = np.array([[2.0, -1.5, 0.0], [-4.0, 3.0, 0.0]])
+    s = 1200.0 * oracle.lrf_eval(L, xt[:, :2], mutant=mutant)
+    D = oracle.deviance_at(L, s, xt, mutant=mutant)
+    assert np.abs(D).max() < 1e-9, D
+    D2 = oracle.deviance_at(L, s, xt + np.array([[0.5, 0.0, 0.0]]), mutant=mutant)
+    assert np.all(D2 > 1e-3)
+
+
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
     pin_noise_free_recovery, pin_noise_free_recovery_3d, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
-    pin_event_status, pin_replay,
+    pin_event_status, pin_replay, pin_gelu, pin_mlp_forward, pin_mlp_gradient, pin_adam, pin_deviance,
 ]

@@ -15,6 +15,8 @@ MUTANTS = {
     7: "lgamma(s) instead of lgamma(s+1)",
     8: "transposed factor in the Cholesky update",
     9: "wrong knot in the local Cox-de Boor recursion",
+    10: "GELU with erf(x) instead of erf(x / sqrt 2)",
+    11: "loss gradient missing the factor 2",
 }
 
 
