@@ -76,7 +76,8 @@ typedef enum {
 
 /* Reconstruction methods. */
 typedef enum {
-    ANTS_CGS_PLAIN = 0 /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
+    ANTS_CGS_PLAIN = 0, /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
+    ANTS_MLP_SEEDED = 2 /* network proposal + local contracting grids + plain fallback */
 } ants_method;
 
 /* Signal element types. */
@@ -85,6 +86,7 @@ typedef enum { ANTS_F32 = 0 } ants_dtype;
 typedef struct ants_ctx ants_ctx;
 typedef struct ants_detector ants_detector;
 typedef struct ants_lrf ants_lrf;
+typedef struct ants_mlp ants_mlp;
 
 /* Parameters of the contracting-grid search (Sec. 5.1.2.2).
  * The grid has n_xy x n_xy (x n_z) nodes centred on the current centre with
@@ -104,6 +106,54 @@ typedef struct {
     float step_z;
     float z0;
 } ants_cgs_params;
+
+/* Learned proposal network (the neural-network reconstruction role of
+ * Sec. 5.1.3): u = s / sum(s); h1 = GELU(W1 u + b1); h2 = GELU(W2 h1 + b2);
+ * o = W3 h2 + b3, GELU(x) = x Phi(x).  Outputs: o0 = x / xy_scale,
+ * o1 = y / xy_scale, o2 = (ln E - loge_mean) / loge_std. */
+typedef struct {
+    int n_hidden;    /* width of both hidden layers, 4..1024 */
+    float xy_scale;  /* > 0 */
+    float loge_mean;
+    float loge_std;  /* > 0 */
+} ants_mlp_config;
+
+/* Training settings (Adam on FP32 master weights; Sec. 5.1.3: the last
+ * monitor_frac of the events is held out and training stops when its error
+ * has not improved by 0.1 % for `patience` epochs; the best weights are kept). */
+typedef struct {
+    int epochs;          /* maximum number of epochs */
+    int batch;           /* events per step, 1..65536 */
+    float lr, beta1, beta2, eps;
+    float monitor_frac;  /* in (0, 1) */
+    int patience;        /* >= 1 */
+    int bf16;            /* 1: BF16 matrix-product operands, FP32 accumulation */
+    uint64_t seed;       /* shuffling */
+} ants_train_params;
+
+typedef struct {
+    int epochs_run;
+    int best_epoch;
+    float best_monitor_mse;
+    float last_train_mse;
+} ants_train_report;
+
+/* Parameters of ANTS_MLP_SEEDED: the network's (x, y), clamped into the LRF's
+ * XY box, starts the `refine` search; events whose Poisson deviance
+ * D = 2 sum_i [s_i ln(s_i/mu_i) - (s_i - mu_i)] exceeds deviance_max (> 0
+ * enables the test), whose final refine node lies on the border of the last
+ * grid (border_fallback = 1), or whose start is outside the domain, are
+ * searched again with `fallback` from the centroid (status ANTS_EVT_FALLBACK).
+ * The call waits for the count of flagged events before it launches the
+ * fallback search.  XY and RADIAL LRFs. */
+typedef struct {
+    const ants_mlp *mlp;
+    int bf16;                 /* network precision at inference */
+    ants_cgs_params refine;   /* e.g. 5 x 5 nodes, 4 grids */
+    ants_cgs_params fallback; /* e.g. the plain 11 x 11 x 8 search */
+    float deviance_max;
+    int border_fallback;
+} ants_mlp_seeded_params;
 
 /* ------------------------------------------------------------------------ */
 /* Library and context                                                        */
@@ -204,7 +254,9 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf);
 /* ------------------------------------------------------------------------ */
 
 /* Reconstruct n_events events.
- *   method: ANTS_CGS_PLAIN; params: const ants_cgs_params*.
+ *   method: ANTS_CGS_PLAIN with params = const ants_cgs_params*, or
+ *     ANTS_MLP_SEEDED with params = const ants_mlp_seeded_params* (no
+ *     start_xyz_dev; trace_dev then records the refine grids).
  *   signals_dev: [n_events][n_sensors] row-major, element type signal_dtype
  *     (ANTS_F32); n_sensors must equal the LRF's.
  *   start_xyz_dev: nullable [n_events][3] FP32 start positions; NULL = the
@@ -241,6 +293,60 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
                                    long n_events, int n_sensors, const float *start_xyz_host,
                                    float *xyz_host, float *E_host, float *logL_host,
                                    int32_t *status_host);
+
+/* Poisson deviance D = 2 sum_i [s_i ln(s_i/mu_i) - (s_i - mu_i)] (s_i = 0:
+ * 2 mu_i) with mu_i = E eta_i(xyz) and E = S/H, for each event at the given
+ * position xyz_dev [n_events][3] -- a goodness-of-fit statistic for the
+ * event filters of Sec. 5.2.  D_dev [n_events]; NaN where xyz is outside the
+ * LRF domain.  Asynchronous on `stream`. */
+ANTS_API int ants_deviance(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
+                           int n_sensors, const float *xyz_dev, float *D_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal network                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Create a network for n_in inputs (the sensor count) with He-normal hidden
+ * and Xavier-normal output weights from `seed`, zero biases. */
+ANTS_API int ants_mlp_create(ants_ctx *ctx, int n_in, const ants_mlp_config *cfg, uint64_t seed,
+                             ants_mlp **out);
+ANTS_API void ants_mlp_free(ants_mlp *mlp);
+
+/* Shape: inputs, hidden width, number of parameters (nullable outputs). */
+ANTS_API int ants_mlp_shape(const ants_mlp *mlp, int *n_in, int *n_hidden, long *n_params);
+
+/* FP32 parameters, concatenated in the order W1 [H][n_in], b1 [H],
+ * W2 [H][H], b2 [H], W3 [3][H], b3 [3] (row-major [out][in]).  set resets the
+ * optimiser state.  count must equal (get: be at least) n_params. */
+ANTS_API int ants_mlp_set_params(ants_mlp *mlp, const float *params_host, long count);
+ANTS_API int ants_mlp_get_params(const ants_mlp *mlp, float *params_host, long count);
+
+/* Network outputs for device signals [n_events][n_sensors]: out_dev
+ * [n_events][3] raw outputs; start_xyz_dev (nullable) [n_events][3] =
+ * (o0 xy_scale, o1 xy_scale, 0); E_dev (nullable, needs start_xyz_dev)
+ * = exp(o2 loge_std + loge_mean).  Uses the context's device scratch. */
+ANTS_API int ants_mlp_forward(ants_ctx *ctx, const ants_mlp *mlp, const float *signals_dev,
+                              long n_events, int n_sensors, int bf16, float *out_dev,
+                              float *start_xyz_dev, float *E_dev, void *stream);
+
+/* Mean squared error of the network on device signals and truth
+ * [n_events][4] = (x, y, z, E), and its gradient (same layout as the
+ * parameters) -- for checking the backward pass.  Synchronous. */
+ANTS_API int ants_mlp_loss_grad(ants_ctx *ctx, const ants_mlp *mlp, const float *signals_dev,
+                                const float *truth_dev, long n_events, int n_sensors, int bf16,
+                                float *loss_host, float *grads_host);
+
+/* Train on device signals and truth [n_events][4] (x, y, z, E).  The first
+ * (1 - monitor_frac) of the events are shuffled into batches every epoch;
+ * the rest is the monitor set.  Synchronous; bitwise reproducible for a
+ * given seed.  report nullable. */
+ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *mlp, const float *signals_dev,
+                            const float *truth_dev, long n_events, int n_sensors,
+                            const ants_train_params *params, ants_train_report *report);
+
+/* Save / load (versioned binary: header, config, FP32 parameters). */
+ANTS_API int ants_mlp_save(const ants_mlp *mlp, const char *path);
+ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
 
 /* ------------------------------------------------------------------------ */
 /* Reconstruction without device allocation                                   */

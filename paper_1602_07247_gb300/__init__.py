@@ -27,6 +27,7 @@ ANTS_LRF_RADIAL, ANTS_LRF_XY, ANTS_LRF_XYZ = 1, 2, 3
 ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
 ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
 ANTS_CGS_PLAIN = 0
+ANTS_MLP_SEEDED = 2
 ANTS_F32 = 0
 ANTS_NOALLOC_STAGE_BYTES = 33554432
 
@@ -48,6 +49,33 @@ class CgsParams(C.Structure):
 
     def __init__(self, n_xy=9, iters=6, step_xy=1.0, shrink=0.5, n_z=1, step_z=0.0, z0=0.0):
         super().__init__(n_xy, n_z, iters, shrink, step_xy, step_z, z0)
+
+
+class MlpConfig(C.Structure):
+    """ants_mlp_config: hidden width and output scaling of the proposal network."""
+    _fields_ = [("n_hidden", C.c_int), ("xy_scale", C.c_float), ("loge_mean", C.c_float), ("loge_std", C.c_float)]
+
+
+class TrainParams(C.Structure):
+    """ants_train_params."""
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("monitor_frac", C.c_float), ("patience", C.c_int),
+                ("bf16", C.c_int), ("seed", C.c_uint64)]
+
+    def __init__(self, epochs=20, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, monitor_frac=0.1,
+                 patience=3, bf16=1, seed=2001):
+        super().__init__(epochs, batch, lr, beta1, beta2, eps, monitor_frac, patience, bf16, seed)
+
+
+class TrainReport(C.Structure):
+    _fields_ = [("epochs_run", C.c_int), ("best_epoch", C.c_int), ("best_monitor_mse", C.c_float),
+                ("last_train_mse", C.c_float)]
+
+
+class SeededParams(C.Structure):
+    """ants_mlp_seeded_params: network start, local refine, plain fallback."""
+    _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
+                ("deviance_max", C.c_float), ("border_fallback", C.c_int)]
 
 
 _lib: C.CDLL | None = None
@@ -87,6 +115,20 @@ def lib() -> C.CDLL:
                                             _VP, _VP, _VP]
         L.ants_reconstruct_host_noalloc.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP,
                                                     _VP, _VP, _VP, _VP]
+        L.ants_reconstruct_host_noalloc.restype = C.c_int
+        L.ants_deviance.argtypes = [_VP, _VP, _VP, C.c_long, C.c_int, _VP, _VP, _VP]
+        L.ants_mlp_create.argtypes = [_VP, C.c_int, C.POINTER(MlpConfig), C.c_uint64, C.POINTER(_VP)]
+        L.ants_mlp_free.argtypes = [_VP]
+        L.ants_mlp_free.restype = None
+        L.ants_mlp_shape.argtypes = [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_long)]
+        L.ants_mlp_set_params.argtypes = [_VP, _VP, C.c_long]
+        L.ants_mlp_get_params.argtypes = [_VP, _VP, C.c_long]
+        L.ants_mlp_forward.argtypes = [_VP, _VP, _VP, C.c_long, C.c_int, C.c_int, _VP, _VP, _VP, _VP]
+        L.ants_mlp_loss_grad.argtypes = [_VP, _VP, _VP, _VP, C.c_long, C.c_int, C.c_int, C.POINTER(C.c_float), _VP]
+        L.ants_mlp_train.argtypes = [_VP, _VP, _VP, _VP, C.c_long, C.c_int, C.POINTER(TrainParams),
+                                     C.POINTER(TrainReport)]
+        L.ants_mlp_save.argtypes = [_VP, C.c_char_p]
+        L.ants_mlp_load.argtypes = [_VP, C.c_char_p, C.POINTER(_VP)]
         _lib = L
     return _lib
 
@@ -237,6 +279,71 @@ def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signa
                                                _tptr(E), _tptr(logL), _tptr(status)))
 
 
+def ants_deviance(ctx: int, lrf: int, signals, xyz, D, stream=None) -> None:
+    _check(lib().ants_deviance(ctx, lrf, _tptr(signals), int(signals.shape[0]), int(signals.shape[1]), _tptr(xyz),
+                               _tptr(D), _stream_handle(stream)))
+
+
+def ants_mlp_create(ctx: int, n_in: int, cfg: MlpConfig, seed: int = 0) -> int:
+    h = _VP()
+    _check(lib().ants_mlp_create(ctx, int(n_in), C.byref(cfg), int(seed), C.byref(h)))
+    return h.value
+
+
+def ants_mlp_free(mlp: int) -> None:
+    lib().ants_mlp_free(mlp)
+
+
+def ants_mlp_shape(mlp: int):
+    a, b, c = C.c_int(), C.c_int(), C.c_long()
+    _check(lib().ants_mlp_shape(mlp, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def ants_mlp_set_params(mlp: int, params) -> None:
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    _check(lib().ants_mlp_set_params(mlp, p.ctypes.data, int(p.size)))
+
+
+def ants_mlp_get_params(mlp: int) -> np.ndarray:
+    n = ants_mlp_shape(mlp)[2]
+    out = np.empty(n, dtype=np.float32)
+    _check(lib().ants_mlp_get_params(mlp, out.ctypes.data, n))
+    return out
+
+
+def ants_mlp_forward(ctx: int, mlp: int, signals, out, start_xyz=None, E=None, bf16: int = 1, stream=None) -> None:
+    _check(lib().ants_mlp_forward(ctx, mlp, _tptr(signals), int(signals.shape[0]), int(signals.shape[1]), int(bf16),
+                                  _tptr(out), _tptr(start_xyz), _tptr(E), _stream_handle(stream)))
+
+
+def ants_mlp_loss_grad(ctx: int, mlp: int, signals, truth, bf16: int = 0):
+    """Returns (loss, grads as one float32 vector in parameter order)."""
+    n = ants_mlp_shape(mlp)[2]
+    g = np.empty(n, dtype=np.float32)
+    loss = C.c_float()
+    _check(lib().ants_mlp_loss_grad(ctx, mlp, _tptr(signals), _tptr(truth), int(signals.shape[0]),
+                                    int(signals.shape[1]), int(bf16), C.byref(loss), g.ctypes.data))
+    return float(loss.value), g
+
+
+def ants_mlp_train(ctx: int, mlp: int, signals, truth, params: TrainParams) -> TrainReport:
+    rep = TrainReport()
+    _check(lib().ants_mlp_train(ctx, mlp, _tptr(signals), _tptr(truth), int(signals.shape[0]), int(signals.shape[1]),
+                                C.byref(params), C.byref(rep)))
+    return rep
+
+
+def ants_mlp_save(mlp: int, path: str) -> None:
+    _check(lib().ants_mlp_save(mlp, path.encode()))
+
+
+def ants_mlp_load(ctx: int, path: str) -> int:
+    h = _VP()
+    _check(lib().ants_mlp_load(ctx, path.encode(), C.byref(h)))
+    return h.value
+
+
 # --------------------------------------------------------------------------
 # owning wrappers
 # --------------------------------------------------------------------------
@@ -307,6 +414,55 @@ class Lrf:
             self.handle = None
 
 
+class Mlp:
+    """The learned proposal network (owning wrapper)."""
+
+    def __init__(self, ctx: Context, handle: int):
+        self.ctx, self.handle = ctx, handle
+        self.n_in, self.n_hidden, self.n_params = ants_mlp_shape(handle)
+
+    @classmethod
+    def create(cls, ctx: Context, n_in: int, n_hidden: int, xy_scale: float, loge_mean: float, loge_std: float,
+               seed: int = 2001):
+        cfg = MlpConfig(n_hidden, xy_scale, loge_mean, loge_std)
+        return cls(ctx, ants_mlp_create(ctx.handle, n_in, cfg, seed))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str):
+        return cls(ctx, ants_mlp_load(ctx.handle, path))
+
+    def save(self, path: str):
+        ants_mlp_save(self.handle, path)
+
+    def params(self) -> np.ndarray:
+        return ants_mlp_get_params(self.handle)
+
+    def set_params(self, p):
+        ants_mlp_set_params(self.handle, p)
+
+    def train(self, signals, truth, params: TrainParams | None = None) -> TrainReport:
+        return ants_mlp_train(self.ctx.handle, self.handle, signals, truth, params or TrainParams())
+
+    def forward(self, signals, bf16: int = 1, stream=None):
+        import torch
+        n = signals.shape[0]
+        out = torch.empty((n, 3), dtype=torch.float32, device=signals.device)
+        xyz = torch.empty((n, 3), dtype=torch.float32, device=signals.device)
+        E = torch.empty(n, dtype=torch.float32, device=signals.device)
+        ants_mlp_forward(self.ctx.handle, self.handle, signals, out, xyz, E, bf16=bf16, stream=stream)
+        return out, xyz, E
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_mlp_free(self.handle)
+            self.handle = None
+
+
+def seeded_params(mlp: Mlp, refine: CgsParams, fallback: CgsParams, deviance_max: float = 0.0,
+                  border_fallback: bool = True, bf16: int = 1) -> SeededParams:
+    return SeededParams(mlp.handle, int(bf16), refine, fallback, float(deviance_max), 1 if border_fallback else 0)
+
+
 @dataclass
 class Result:
     xyz: object
@@ -326,7 +482,8 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     E = torch.empty(n, dtype=torch.float32, device=dev)
     logL = torch.empty(n, dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
-    trace = torch.empty((n, params.iters), dtype=torch.int16, device=dev) if want_trace else None
+    iters = params.refine.iters if isinstance(params, SeededParams) else params.iters
+    trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
     ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
                      start_xyz=start_xyz, trace=trace, stream=stream)

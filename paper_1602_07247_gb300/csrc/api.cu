@@ -38,6 +38,27 @@ void count_launch(long n) { t_launches += n; }
 
 int lrf_dims(int type) { return type == ANTS_LRF_RADIAL ? 1 : (type == ANTS_LRF_XY ? 2 : 3); }
 
+void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
+{
+    if (slot < 0 || slot >= 8) {
+        fail(ANTS_E_INTERNAL, "scratch slot %d", slot);
+        return nullptr;
+    }
+    if (ctx->scratch_cap[slot] >= bytes && ctx->scratch[slot]) return ctx->scratch[slot];
+    cudaFree(ctx->scratch[slot]);
+    ctx->scratch[slot] = nullptr;
+    ctx->scratch_cap[slot] = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&ctx->scratch[slot], want);
+    if (e != cudaSuccess) {
+        fail(ANTS_E_OOM, "device scratch of %zu bytes: %s", want, cudaGetErrorString(e));
+        ctx->scratch[slot] = nullptr;
+        return nullptr;
+    }
+    ctx->scratch_cap[slot] = want;
+    return ctx->scratch[slot];
+}
+
 }  // namespace ants
 
 using namespace ants;
@@ -101,6 +122,7 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_host_buffers(ctx);
+    for (int k = 0; k < 8; ++k) cudaFree(ctx->scratch[k]);
     for (int k = 0; k < 2; ++k)
         if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);
     delete ctx;
@@ -401,6 +423,7 @@ static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const vo
     if (n_sensors != lrf->n_s)
         return fail(ANTS_E_SHAPE, "ants_reconstruct: n_sensors %d but the LRF has %d", n_sensors, lrf->n_s);
     if (signal_dtype != ANTS_F32) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: dtype %d", signal_dtype);
+    if (method == ANTS_MLP_SEEDED) return check_seeded_params(lrf, (const ants_mlp_seeded_params *)params);
     if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
     return check_cgs_params(lrf, (const ants_cgs_params *)params);
 }
@@ -417,6 +440,12 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
     if (!signals_dev || !xyz_dev || !E_dev || !logL_dev || !status_dev)
         return fail(ANTS_E_ARG, "ants_reconstruct: NULL signal or output buffer");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (method == ANTS_MLP_SEEDED) {
+        if (start_xyz_dev) return fail(ANTS_E_ARG, "ants_reconstruct: the learned form proposes its own start");
+        return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, (const float *)signals_dev,
+                                      n_events, xyz_dev, E_dev, logL_dev, status_dev, trace_dev,
+                                      (cudaStream_t)stream);
+    }
     return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, (const float *)signals_dev,
                             n_events, start_xyz_dev, xyz_dev, E_dev, logL_dev, status_dev, trace_dev,
                             (cudaStream_t)stream);
@@ -430,6 +459,7 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
     begin_call();
     int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
     if (rc != ANTS_OK) return rc;
+    if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct_host: method %d", method);
     if (n_events == 0) return ANTS_OK;
     if (!signals_host || !xyz_host || !E_host || !logL_host || !status_host)
         return fail(ANTS_E_ARG, "ants_reconstruct_host: NULL signal or output buffer");

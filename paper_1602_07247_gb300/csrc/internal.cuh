@@ -63,6 +63,9 @@ struct ants_ctx {
     float *d_start[2] = {nullptr, nullptr};
     float *d_out[2] = {nullptr, nullptr};   // xyz(3) E logL per event
     int32_t *d_status[2] = {nullptr, nullptr};
+    // general device scratch slots (grown on demand by ants::ctx_scratch)
+    void *scratch[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t scratch_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct ants_detector {
@@ -92,6 +95,19 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
                      const float *sig, long n_e, const float *start, float *xyz, float *E,
                      float *logL, int32_t *status, int16_t *trace, cudaStream_t stream);
 int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
+// device scratch slot `slot` (0..7) of at least `bytes`; NULL (error recorded) on failure.
+// Growing a slot frees the old buffer, so the caller must not have work in
+// flight that uses it.
+void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
+// learned proposal (mlp.cu)
+int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s);
+int mlp_decode(const ants_mlp *M, const float *O, long n, float *xyz, float *E, cudaStream_t s);
+int mlp_n_in(const ants_mlp *M);
+// learned-proposal reconstruction (seeded.cu)
+int check_seeded_params(const ants_lrf *lrf, const ants_mlp_seeded_params *P);
+int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_seeded_params &P, const float *sig,
+                           long n, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
+                           cudaStream_t s);
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
 int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, long n_e,
                   const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,

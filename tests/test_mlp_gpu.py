@@ -1,0 +1,161 @@
+"""Learned proposal on the GPU against the FP64 oracle: forward pass,
+back-propagated gradients (FP32 and BF16 operand modes), deterministic
+training, deviance, and the seeded reconstruction pipeline."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import synth.workloads
+from parity import compare, gpu_objects, oracle_lrf, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1602_07247_gb300 as ants
+    return torch, ants, ants.Context(0)
+
+
+def unpack(flat, n_in, H):
+    o, parts = 0, []
+    for shape in ((H, n_in), (H,), (H, H), (H,), (3, H), (3,)):
+        n = int(np.prod(shape))
+        parts.append(np.asarray(flat[o:o + n], dtype=np.float64).reshape(shape))
+        o += n
+    return parts
+
+
+def random_net(ants, ctx, n_in, H, seed):
+    cfg_scale, mu, sd = 24.0, np.log(3000.0), 0.05
+    M = ants.Mlp.create(ctx, n_in, H, cfg_scale, mu, sd, seed=seed)
+    rng = np.random.default_rng(seed)
+    p = M.params().astype(np.float64)
+    p += rng.normal(0, 0.02, p.size)  # non-zero biases too
+    M.set_params(p.astype(np.float32))
+    return M, oracle.Mlp(*unpack(M.params(), n_in, H))
+
+
+def test_forward_matches_oracle(env):
+    torch, ants, ctx = env
+    M, ref = random_net(ants, ctx, 64, 96, 3)
+    sig = synth.workloads.get("sipm8x8_xy").events(777, seed=4).signals
+    want = oracle.mlp_forward(ref, sig.astype(np.float64))
+    s = torch.from_numpy(sig).cuda()
+    out32 = torch.empty((777, 3), device="cuda")
+    ants.ants_mlp_forward(ctx.handle, M.handle, s, out32, bf16=0)
+    out16 = torch.empty((777, 3), device="cuda")
+    ants.ants_mlp_forward(ctx.handle, M.handle, s, out16, bf16=1)
+    scale = np.abs(want).max()
+    e32 = np.abs(out32.cpu().numpy() - want).max() / scale
+    e16 = np.abs(out16.cpu().numpy() - want).max() / scale
+    print("forward rel err fp32", e32, "bf16", e16)
+    assert e32 < 1e-5 and e16 < 3e-2
+
+
+@pytest.mark.parametrize("bf16,tol", [(0, 1e-4), (1, 3e-2)])
+def test_gradients_match_oracle(env, bf16, tol):
+    torch, ants, ctx = env
+    M, ref = random_net(ants, ctx, 64, 96, 5)
+    w = synth.workloads.get("sipm8x8_xy")
+    ev = w.events(300, seed=6)
+    truth = np.concatenate([ev.xyz, ev.energy[:, None]], axis=1).astype(np.float32)
+    tgt = np.stack([truth[:, 0] / 24.0, truth[:, 1] / 24.0, (np.log(truth[:, 3]) - np.log(3000.0)) / 0.05], axis=1)
+    loss_o, g_o = oracle.mlp_loss_grad(ref, ev.signals.astype(np.float64), tgt.astype(np.float64))
+    loss_g, g_flat = ants.ants_mlp_loss_grad(ctx.handle, M.handle, torch.from_numpy(ev.signals).cuda(),
+                                             torch.from_numpy(truth).cuda(), bf16=bf16)
+    assert abs(loss_g / loss_o - 1.0) < tol
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), unpack(g_flat, 64, 96), g_o):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print(bf16, name, rel)
+        assert rel < tol, (name, rel)
+
+
+def train_small(ants, ctx, torch, seed=2001, n=24000, epochs=4):
+    w = synth.workloads.get("sipm8x8_xy")
+    ev = w.events(n, seed=2001)
+    truth = np.concatenate([ev.xyz, ev.energy[:, None]], axis=1).astype(np.float32)
+    M = ants.Mlp.create(ctx, 64, 128, 24.0, float(np.log(3000.0)), 0.05, seed=seed)
+    rep = M.train(torch.from_numpy(ev.signals).cuda(), torch.from_numpy(truth).cuda(),
+                  ants.TrainParams(epochs=epochs, batch=512, seed=7))
+    return M, rep
+
+
+def test_training_is_deterministic_and_learns(env, tmp_path):
+    torch, ants, ctx = env
+    M1, r1 = train_small(ants, ctx, torch)
+    M2, r2 = train_small(ants, ctx, torch)
+    assert np.array_equal(M1.params(), M2.params())
+    assert r1.best_monitor_mse == r2.best_monitor_mse
+    print("epochs", r1.epochs_run, "best monitor mse", r1.best_monitor_mse)
+    assert r1.best_monitor_mse < 0.5  # targets have unit scale; an untrained net is far worse
+    path = str(tmp_path / "net.bin")
+    M1.save(path)
+    M3 = ants.Mlp.load(ctx, path)
+    assert np.array_equal(M3.params(), M1.params())
+
+
+def test_deviance_matches_oracle(env):
+    torch, ants, ctx = env
+    w = synth.workloads.get("sipm8x8_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(500, seed=8)
+    pos = ev.xyz.copy()
+    pos[:, :2] += np.random.default_rng(1).normal(0, 0.5, (500, 2))
+    pos = np.clip(pos, -23.0, 23.0).astype(np.float32)
+    pos[:, 2] = 0.0
+    D = torch.empty(500, device="cuda")
+    ants.ants_deviance(ctx.handle, lrf.handle, torch.from_numpy(ev.signals).cuda(), torch.from_numpy(pos).cuda(), D)
+    want = oracle.deviance_at(L, ev.signals.astype(np.float64), pos.astype(np.float64))
+    got = D.cpu().numpy()
+    assert np.abs(got - want).max() < 2e-3 * max(1.0, np.abs(want).max()), np.abs(got - want).max()
+
+
+def test_seeded_pipeline_consistency_and_gain(env):
+    """The learned form equals its parts: refine from the (clamped) network
+    start for kept events, plain search for flagged ones.  Against the plain
+    refine from the centroid at the same small budget, the network start
+    gains accuracy."""
+    torch, ants, ctx = env
+    M, rep = train_small(ants, ctx, torch, epochs=6)
+    w = synth.workloads.get("sipm8x8_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, plain = gpu_objects(w, L, ctx)
+    refine = ants.CgsParams(n_xy=5, iters=4, step_xy=0.5)
+    ev = w.events(3000, seed=3001)
+    sig = torch.from_numpy(ev.signals).cuda()
+    # plain search on a calibration set fixes the deviance threshold (99.5th percentile)
+    cal = w.events(3000, seed=3002)
+    rc = ants.reconstruct(ctx, lrf, plain, torch.from_numpy(cal.signals).cuda())
+    Dc = torch.empty(3000, device="cuda")
+    ants.ants_deviance(ctx.handle, lrf.handle, torch.from_numpy(cal.signals).cuda(), rc.xyz, Dc)
+    thr = float(np.quantile(Dc.cpu().numpy(), 0.995))
+    sp = ants.seeded_params(M, refine, plain, deviance_max=thr, border_fallback=True, bf16=1)
+    res = to_numpy(ants.reconstruct(ctx, lrf, sp, sig, method=ants.ANTS_MLP_SEEDED, want_trace=True))
+    # parts
+    _, seeds, _ = M.forward(sig, bf16=1)
+    seeds = seeds.clamp(-24.0, 24.0)
+    seeds[:, 2] = 0.0
+    ref = to_numpy(ants.reconstruct(ctx, lrf, refine, sig, start_xyz=seeds.contiguous(), want_trace=True))
+    full = to_numpy(ants.reconstruct(ctx, lrf, plain, sig))
+    fb = res["status"] == ants.ANTS_EVT_FALLBACK
+    kept = res["status"] == ants.ANTS_EVT_OK
+    print("fallback fraction", fb.mean())
+    assert fb.mean() < 0.5
+    assert np.array_equal(res["xyz"][kept], ref["xyz"][kept])
+    assert np.array_equal(res["xyz"][fb], full["xyz"][fb])
+    # the refine stage itself against the oracle, from the same starts
+    cmp = compare(w.with_(n_xy=5, iters=4, step_xy=0.5), L, ev.signals, ref,
+                  start=seeds.double().cpu().numpy())
+    print("refine parity", cmp)
+    # gain of the network start at the same refine budget
+    cog = to_numpy(ants.reconstruct(ctx, lrf, refine, sig))
+    rms = lambda r: float(np.sqrt(((r["xyz"][:, :2] - ev.xyz[:, :2]) ** 2).sum(1).mean()))
+    print("rms: learned form", rms(res), "refine from network", rms(ref), "refine from centroid", rms(cog),
+          "plain", rms(full))
+    assert rms(ref) < 0.5 * rms(cog)
+    assert rms(res) <= 1.10 * rms(full)
