@@ -157,6 +157,60 @@ def config_of(w, n_events):
             "method": "plain FP32 contracting grids", "l2": "inputs larger than L2 (256 MB of signals per step)"}
 
 
+def forms_comparison(args, ants, torch, ctx, stream):
+    """Plain contracting grids vs the learned form (network start + 5x5x4
+    refine + deviance fallback) on the 16x16 SiPM detector, same events."""
+    import synth.workloads
+    w = synth.workloads.get("sipm16x16_xy")
+    t0 = time.perf_counter()
+    det = ants.Detector(w.sensor_xy, w.gains)
+    pts, vals = w.fit_samples()
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)
+    plain = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    refine = ants.CgsParams(n_xy=5, iters=4, step_xy=0.5, shrink=0.5)
+    tr = w.events(args.train_events, seed=2001)
+    truth = np.concatenate([tr.xyz, tr.energy[:, None]], axis=1).astype(np.float32)
+    mlp = ants.Mlp.create(ctx, w.n_sensors, 256, 25.6, float(np.log(2000.0)), 0.05, seed=2001)
+    rep = mlp.train(torch.from_numpy(tr.signals).cuda(), torch.from_numpy(truth).cuda(),
+                    ants.TrainParams(epochs=20, batch=1024, bf16=1, seed=2001))
+    cal = w.events(20000, seed=2002)
+    csig = torch.from_numpy(cal.signals).cuda()
+    rc = ants.reconstruct(ctx, lrf, plain, csig)
+    Dc = torch.empty(cal.signals.shape[0], device="cuda")
+    ants.ants_deviance(ctx.handle, lrf.handle, csig, rc.xyz, Dc)
+    thr = float(np.quantile(Dc.cpu().numpy(), 0.995))
+    sp = ants.seeded_params(mlp, refine, plain, deviance_max=thr, border_fallback=True, bf16=1)
+    ev = w.events(args.forms_events, seed=3001)
+    sig = torch.from_numpy(ev.signals).cuda()
+    n = sig.shape[0]
+    setup_s = time.perf_counter() - t0
+    out = {}
+    for name, method, params in (("plain", ants.ANTS_CGS_PLAIN, plain), ("learned", ants.ANTS_MLP_SEEDED, sp)):
+        res = ants.reconstruct(ctx, lrf, params, sig, method=method, stream=stream)
+        for _ in range(2):
+            ants.reconstruct(ctx, lrf, params, sig, method=method, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.forms_steps):
+            res = ants.reconstruct(ctx, lrf, params, sig, method=method, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / args.forms_steps
+        d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+        err = np.sqrt((d ** 2).sum(1))
+        st = res.status.cpu().numpy()
+        out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt, "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
+                     "median_dxy_mm": float(np.median(err)), "p95_dxy_mm": float(np.quantile(err, 0.95)),
+                     "fallback_frac": float((st == ants.ANTS_EVT_FALLBACK).mean())}
+    out["learned"]["speedup_vs_plain"] = out["learned"]["events_per_s"] / out["plain"]["events_per_s"]
+    out["learned"]["rms_ratio_vs_plain"] = out["learned"]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
+    return {"workload": f"{w.name}: 256 sensors, XY LRF 32x32, {n} events; plain {w.n_xy}x{w.n_xy}x{w.iters} vs "
+                        f"MLP 256-256-256-3 (BF16, trained on the GPU on {args.train_events} events, "
+                        f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile",
+            "setup_s": setup_s, "deviance_max": thr, **out}
+
+
 def run_ours(args):
     import torch
 
@@ -271,12 +325,13 @@ def run_ours(args):
         rate, secs, cores, _ = cpu_oracle_rate(w, args.cpu_events, seed=w.event_seed)
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_events} events of this workload ({secs:.1f} s), FP64 C oracle, OpenMP"}
+    forms = None if args.no_forms else forms_comparison(args, ants, torch, ctx, stream)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-        "rms_dxy_mm": rms,
+        "rms_dxy_mm": rms, "forms_16x16": forms,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -295,6 +350,10 @@ def main():
     ap.add_argument("--cpu-events", type=int, default=4096)
     ap.add_argument("--ref-events", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the plain vs learned comparison")
+    ap.add_argument("--forms-events", type=int, default=500_000)
+    ap.add_argument("--forms-steps", type=int, default=3)
+    ap.add_argument("--train-events", type=int, default=200_000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
