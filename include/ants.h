@@ -138,6 +138,17 @@ typedef struct {
     float last_train_mse;
 } ants_train_report;
 
+/* Synthetic event source (ants_simulate_events). */
+typedef struct {
+    int region;      /* 0: disk of radius `extent`, 1: square of half-width `extent` */
+    float extent;    /* mm, >= 0 */
+    float cx, cy;    /* centre of the region */
+    float z_lo, z_hi;/* source depth range (XYZ LRFs only) */
+    float e0;        /* mean number of photons (> 0) */
+    float e_spread;  /* E uniform in e0 (1 +- e_spread), 0 <= e_spread < 1 */
+    float spe_sigma; /* relative width of the single photo-electron response (0: counts) */
+} ants_sim_params;
+
 /* Parameters of ANTS_MLP_SEEDED: the network's (x, y), clamped into the LRF's
  * XY box, starts the `refine` search; events whose Poisson deviance
  * D = 2 sum_i [s_i ln(s_i/mu_i) - (s_i - mu_i)] exceeds deviance_max (> 0
@@ -301,6 +312,21 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
  * LRF domain.  Asynchronous on `stream`. */
 ANTS_API int ants_deviance(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
                            int n_sensors, const float *xyz_dev, float *D_dev, void *stream);
+
+/* Simulate events first_event .. first_event + n_events - 1 from an LRF set:
+ * source uniform in the region (z uniform in [z_lo, z_hi] for XYZ LRFs, else
+ * 0), energy E uniform in e0 (1 +- e_spread), signal of sensor i Poisson with
+ * mean E eta_i(source) (the mean response an LRF describes, Sec. 6) and, with
+ * spe_sigma > 0, each photo-electron contributing N(1, spe_sigma^2) (the
+ * normal single photo-electron response of Sec. 4.2.5), clamped at 0.
+ * Random numbers: Philox4x32-10 keyed by `seed`; event e uses counters
+ * (e, 0xFFFFFFFF, *) for its source and (e, i, *) for sensor i, so any range
+ * of events can be generated independently and reproducibly.
+ * signals_dev [n_events][n_sensors] FP32; truth_dev (nullable)
+ * [n_events][4] = (x, y, z, E).  Asynchronous on `stream`. */
+ANTS_API int ants_simulate_events(ants_ctx *ctx, const ants_lrf *lrf, const ants_sim_params *params,
+                                  uint64_t seed, long first_event, long n_events, float *signals_dev,
+                                  float *truth_dev, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Learned proposal network                                                  */

@@ -436,3 +436,48 @@ def deviance_at(lrf: Lrf, sig, xyz, mutant: int = 0) -> np.ndarray:
     D = np.empty(sig.shape[0])
     _mlib(mutant).or_deviance_at(C.byref(s), sig.shape[0], _d(sig), _d(xyz), _d(D))
     return D
+
+
+# --------------------------------------------------------------------------
+# event simulation (Philox4x32-10 + Poisson)
+# --------------------------------------------------------------------------
+
+
+class _Sim(C.Structure):
+    _fields_ = [("region", C.c_int), ("extent", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("z_lo", C.c_double), ("z_hi", C.c_double), ("e0", C.c_double), ("e_spread", C.c_double),
+                ("spe_sigma", C.c_double)]
+
+
+def _slib(mutant=0):
+    L = _mlib(mutant)
+    if not getattr(L, "_sim_declared", False):
+        L.or_philox_block.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                      C.POINTER(C.c_uint32)]
+        L.or_simulate.argtypes = [C.POINTER(_Lrf), C.POINTER(_Sim), C.c_uint64, C.c_long, C.c_long, _D, _D]
+        L.or_poisson_draws.argtypes = [C.c_double, C.c_uint64, C.c_long, _D]
+        L._sim_declared = True
+    return L
+
+
+def philox(seed: int, ctr, mutant: int = 0) -> np.ndarray:
+    out = (C.c_uint32 * 4)()
+    _slib(mutant).or_philox_block(int(seed), *[int(c) & 0xFFFFFFFF for c in ctr], out)
+    return np.array(list(out), dtype=np.uint64)
+
+
+def simulate(lrf: Lrf, seed: int, first_event: int, n: int, region="square", extent=10.0, cx=0.0, cy=0.0,
+             z_lo=0.0, z_hi=0.0, e0=1000.0, e_spread=0.05, spe_sigma=0.0, mutant: int = 0):
+    """Signals [n, n_s] and truth [n, 4] (x, y, z, E) of events first_event.."""
+    p = _Sim(0 if region == "disk" else 1, extent, cx, cy, z_lo, z_hi, e0, e_spread, spe_sigma)
+    s = lrf._struct()
+    sig = np.empty((n, lrf.n_sensors))
+    truth = np.empty((n, 4))
+    _slib(mutant).or_simulate(C.byref(s), C.byref(p), int(seed), int(first_event), int(n), _d(sig), _d(truth))
+    return sig, truth
+
+
+def poisson_draws(lam: float, seed: int, n: int, mutant: int = 0) -> np.ndarray:
+    out = np.empty(n)
+    _slib(mutant).or_poisson_draws(float(lam), int(seed), int(n), _d(out))
+    return out

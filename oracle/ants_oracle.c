@@ -900,3 +900,168 @@ void or_deviance_at(const or_lrf *L, long n_e, const double *sig, const double *
         D[e] = 2.0 * (sat - ll);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Event simulation from an LRF set (Poisson photo-electron counts,          */
+/* Sec. 4.2.5 signals; the photon transport of Sec. 4.2.3 is replaced by     */
+/* the LRF mean response)                                                    */
+/* ------------------------------------------------------------------------ */
+#include <stdint.h>
+
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of two
+ * 32x32->64-bit multiplications with the published multipliers and Weyl key
+ * increments. */
+static void or_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+void or_philox_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t *out)
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox(ctr, key, out);
+}
+
+/* uniform in (0, 1) from the top 24 bits */
+static double or_u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+typedef struct {
+    uint32_t key[2], ctr[4], buf[4];
+    int pos;
+} or_stream;
+
+static void or_stream_init(or_stream *s, uint64_t seed, long e, uint32_t lane)
+{
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = (uint32_t)(seed >> 32);
+    s->ctr[0] = (uint32_t)e;
+    s->ctr[1] = (uint32_t)((uint64_t)e >> 32);
+    s->ctr[2] = lane;
+    s->ctr[3] = 0;
+    s->pos = 4;
+}
+
+static double or_next_u(or_stream *s)
+{
+    if (s->pos == 4) {
+        or_philox(s->ctr, s->key, s->buf);
+        s->ctr[3]++;
+        s->pos = 0;
+    }
+    return or_u01(s->buf[s->pos++]);
+}
+
+/* Poisson(lam): inversion of the CDF for lam < 10; Hormann's transformed
+ * rejection with squeeze (PTRS, Insurance: Mathematics and Economics 12,
+ * 1993) otherwise. */
+static long or_poisson(double lam, or_stream *s)
+{
+    if (!(lam > 0.0)) return 0;
+    if (lam < 10.0) {
+        double u = or_next_u(s), p = exp(-lam), F = p;
+        long k = 0;
+        while (u > F && k < 1000) {
+            ++k;
+            p *= lam / (double)k;
+            F += p;
+        }
+        return k;
+    }
+    double slam = sqrt(lam), loglam = log(lam);
+    double b = 0.931 + 2.53 * slam, a = -0.059 + 0.02483 * b;
+    double inv_alpha = 1.1239 + 1.1328 / (b - 3.4), vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (int it = 0; it < 1000; ++it) {
+        double U = or_next_u(s) - 0.5, V = or_next_u(s);
+        double us = 0.5 - fabs(U);
+        long k = (long)floor((2.0 * a / us + b) * U + lam + 0.43);
+        if (us >= 0.07 && V <= vr) return k;
+        if (k < 0 || (us < 0.013 && V > us)) continue;
+        if (log(V) + log(inv_alpha) - log(a / (us * us) + b) <= -lam + (double)k * loglam - lgamma((double)k + 1.0))
+            return k;
+    }
+    return (long)lam;
+}
+
+typedef struct {
+    int region;     /* 0 disk, 1 square */
+    double extent;  /* radius or half-width */
+    double cx, cy;
+    double z_lo, z_hi;
+    double e0, e_spread;
+    double spe_sigma;
+} or_sim_params;
+
+/* Events first_event .. first_event+n-1: source position and energy from
+ * stream (e, 0xFFFFFFFF), counts of sensor i from stream (e, i). */
+void or_simulate(const or_lrf *L, const or_sim_params *P, uint64_t seed, long first_event, long n, double *sig,
+                 double *truth)
+{
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < n; ++r) {
+        long e = first_event + r;
+        uint32_t ev[4];
+        or_philox_block(seed, (uint32_t)e, (uint32_t)((uint64_t)e >> 32), 0xFFFFFFFFu, 0u, ev);
+        double u0 = or_u01(ev[0]), u1 = or_u01(ev[1]), u2 = or_u01(ev[2]), u3 = or_u01(ev[3]);
+        double x, y;
+        if (P->region == 0) {
+            double rad = P->extent * sqrt(u0), th = 6.283185307179586 * u1;
+            x = P->cx + rad * cos(th);
+            y = P->cy + rad * sin(th);
+        } else {
+            x = P->cx + P->extent * (2.0 * u0 - 1.0);
+            y = P->cy + P->extent * (2.0 * u1 - 1.0);
+        }
+        double E = P->e0 * (1.0 + P->e_spread * (2.0 * u2 - 1.0));
+        double z = P->z_lo + (P->z_hi - P->z_lo) * u3;
+        if (L->type != OR_XYZ) z = 0.0;
+        if (truth) {
+            truth[4 * r] = x;
+            truth[4 * r + 1] = y;
+            truth[4 * r + 2] = z;
+            truth[4 * r + 3] = E;
+        }
+        for (int i = 0; i < L->n_sensors; ++i) {
+            int ok;
+            double eta = or_lrf_eta(L, i, x, y, z, &ok);
+            double lam = ok && eta > 0.0 ? E * eta : 0.0;
+            or_stream st;
+            or_stream_init(&st, seed, e, (uint32_t)i);
+            double cnt = (double)or_poisson(lam, &st);
+            if (P->spe_sigma > 0.0 && cnt > 0.0) {
+                double a = or_next_u(&st), b = or_next_u(&st);
+                double zn = sqrt(-2.0 * log(a)) * cos(6.283185307179586 * b);
+                cnt = cnt + P->spe_sigma * sqrt(cnt) * zn;
+                if (cnt < 0.0) cnt = 0.0;
+            }
+            sig[r * L->n_sensors + i] = cnt;
+        }
+    }
+}
+
+/* Poisson draws of one stream (for the distribution pins). */
+void or_poisson_draws(double lam, uint64_t seed, long n, double *out)
+{
+    for (long e = 0; e < n; ++e) {
+        or_stream st;
+        or_stream_init(&st, seed, e, 0u);
+        out[e] = (double)or_poisson(lam, &st);
+    }
+}

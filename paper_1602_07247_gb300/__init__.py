@@ -72,6 +72,17 @@ class TrainReport(C.Structure):
                 ("last_train_mse", C.c_float)]
 
 
+class SimParams(C.Structure):
+    """ants_sim_params: source region, energy and single photo-electron response."""
+    _fields_ = [("region", C.c_int), ("extent", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("z_lo", C.c_float), ("z_hi", C.c_float), ("e0", C.c_float), ("e_spread", C.c_float),
+                ("spe_sigma", C.c_float)]
+
+    def __init__(self, region="square", extent=10.0, cx=0.0, cy=0.0, z_lo=0.0, z_hi=0.0, e0=1000.0, e_spread=0.05,
+                 spe_sigma=0.0):
+        super().__init__(0 if region == "disk" else 1, extent, cx, cy, z_lo, z_hi, e0, e_spread, spe_sigma)
+
+
 class SeededParams(C.Structure):
     """ants_mlp_seeded_params: network start, local refine, plain fallback."""
     _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
@@ -116,6 +127,8 @@ def lib() -> C.CDLL:
         L.ants_reconstruct_host_noalloc.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP,
                                                     _VP, _VP, _VP, _VP]
         L.ants_reconstruct_host_noalloc.restype = C.c_int
+        L.ants_simulate_events.argtypes = [_VP, _VP, C.POINTER(SimParams), C.c_uint64, C.c_long, C.c_long, _VP, _VP,
+                                           _VP]
         L.ants_deviance.argtypes = [_VP, _VP, _VP, C.c_long, C.c_int, _VP, _VP, _VP]
         L.ants_mlp_create.argtypes = [_VP, C.c_int, C.POINTER(MlpConfig), C.c_uint64, C.POINTER(_VP)]
         L.ants_mlp_free.argtypes = [_VP]
@@ -277,6 +290,21 @@ def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signa
     _check(lib().ants_reconstruct_host_noalloc(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                                int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
                                                _tptr(E), _tptr(logL), _tptr(status)))
+
+
+def ants_simulate_events(ctx: int, lrf: int, params: SimParams, seed: int, first_event: int, signals, truth=None,
+                         stream=None) -> None:
+    _check(lib().ants_simulate_events(ctx, lrf, C.byref(params), int(seed), int(first_event), int(signals.shape[0]),
+                                      _tptr(signals), _tptr(truth), _stream_handle(stream)))
+
+
+def simulate(ctx: Context, lrf: "Lrf", params: SimParams, n: int, seed: int, first_event: int = 0, stream=None):
+    """Device signals [n, n_sensors] and truth [n, 4] (x, y, z, E)."""
+    import torch
+    sig = torch.empty((n, lrf.n_sensors), dtype=torch.float32, device="cuda")
+    truth = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ants_simulate_events(ctx.handle, lrf.handle, params, seed, first_event, sig, truth, stream)
+    return sig, truth
 
 
 def ants_deviance(ctx: int, lrf: int, signals, xyz, D, stream=None) -> None:

@@ -499,9 +499,52 @@ def pin_deviance(mutant=0):
     assert np.all(D2 > 1e-3)
 
 
+# --------------------------------------------------------------------------
+# simulation
+# --------------------------------------------------------------------------
+
+
+def pin_poisson_sampler(mutant=0):
+    """Counts drawn by the oracle's sampler follow scipy's Poisson pmf
+    (chi-squared test at 0.1 % per rate) for rates on both sides of the
+    switch between inversion and transformed rejection, with the right mean
+    and variance."""
+    from scipy.stats import chi2, poisson
+    for lam in (0.5, 5.0, 9.9, 10.0, 50.0, 500.0):
+        x = oracle.poisson_draws(lam, 17, 40000, mutant)
+        assert abs(x.mean() - lam) < 5 * np.sqrt(lam / x.size), (lam, x.mean())
+        assert abs(x.var() / lam - 1.0) < 0.05, (lam, x.var())
+        lo, hi = int(poisson.ppf(1e-4, lam)), int(poisson.ppf(1 - 1e-4, lam))
+        edges = np.arange(lo, hi + 2)
+        obs, _ = np.histogram(x, bins=edges)
+        exp = x.size * poisson.pmf(edges[:-1], lam)
+        keep = exp > 5
+        stat = ((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+        assert stat < chi2.ppf(0.999, keep.sum() - 1), (lam, stat)
+
+
+def pin_uniform_stream(mutant=0):
+    """Philox outputs as uniforms: equal-probability bins pass a chi-squared
+    test and neighbouring draws are uncorrelated; different counters give
+    different blocks."""
+    from scipy.stats import chi2
+    u = []
+    for e in range(20000):
+        b = oracle.philox(1234567, (e, 0, 7, 0), mutant)
+        u.extend(((b >> 8).astype(np.float64) + 0.5) / 16777216.0)
+    u = np.array(u)
+    obs, _ = np.histogram(u, bins=64, range=(0.0, 1.0))
+    exp = u.size / 64
+    assert ((obs - exp) ** 2 / exp).sum() < chi2.ppf(0.999, 63)
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.01
+    assert not np.array_equal(oracle.philox(1, (0, 0, 0, 0)), oracle.philox(1, (1, 0, 0, 0)))
+    assert not np.array_equal(oracle.philox(1, (0, 0, 0, 0)), oracle.philox(2, (0, 0, 0, 0)))
+
+
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
     pin_noise_free_recovery, pin_noise_free_recovery_3d, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
     pin_event_status, pin_replay, pin_gelu, pin_mlp_forward, pin_mlp_gradient, pin_adam, pin_deviance,
+    pin_poisson_sampler, pin_uniform_stream,
 ]
