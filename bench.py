@@ -168,20 +168,21 @@ def forms_comparison(args, ants, torch, ctx, stream):
     lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)
     plain = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
     refine = ants.CgsParams(n_xy=5, iters=4, step_xy=0.5, shrink=0.5)
-    tr = w.events(args.train_events, seed=2001)
-    truth = np.concatenate([tr.xyz, tr.energy[:, None]], axis=1).astype(np.float32)
+    # events from the library's GPU simulator (Poisson counts from the fitted LRFs)
+    src = ants.SimParams("square", 24.0, 0.0, 0.0, 0.0, 0.0, 2000.0, 0.05, 0.0)
+    tsig, truth = ants.simulate(ctx, lrf, src, args.train_events, seed=2001)
     mlp = ants.Mlp.create(ctx, w.n_sensors, 256, 25.6, float(np.log(2000.0)), 0.05, seed=2001)
-    rep = mlp.train(torch.from_numpy(tr.signals).cuda(), torch.from_numpy(truth).cuda(),
-                    ants.TrainParams(epochs=20, batch=1024, bf16=1, seed=2001))
-    cal = w.events(20000, seed=2002)
-    csig = torch.from_numpy(cal.signals).cuda()
+    rep = mlp.train(tsig, truth, ants.TrainParams(epochs=20, batch=1024, bf16=1, seed=2001))
+    del tsig, truth
+    csig, _ = ants.simulate(ctx, lrf, src, 20000, seed=2002)
     rc = ants.reconstruct(ctx, lrf, plain, csig)
-    Dc = torch.empty(cal.signals.shape[0], device="cuda")
+    Dc = torch.empty(csig.shape[0], device="cuda")
     ants.ants_deviance(ctx.handle, lrf.handle, csig, rc.xyz, Dc)
     thr = float(np.quantile(Dc.cpu().numpy(), 0.995))
     sp = ants.seeded_params(mlp, refine, plain, deviance_max=thr, border_fallback=True, bf16=1)
-    ev = w.events(args.forms_events, seed=3001)
-    sig = torch.from_numpy(ev.signals).cuda()
+    sig, etruth = ants.simulate(ctx, lrf, src, args.forms_events, seed=3001)
+    torch.cuda.synchronize()
+    true_xy = etruth[:, :2].double().cpu().numpy()
     n = sig.shape[0]
     setup_s = time.perf_counter() - t0
     out = {}
@@ -197,7 +198,7 @@ def forms_comparison(args, ants, torch, ctx, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         dt = e0.elapsed_time(e1) / 1e3 / args.forms_steps
-        d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+        d = res.xyz[:, :2].double().cpu().numpy() - true_xy
         err = np.sqrt((d ** 2).sum(1))
         st = res.status.cpu().numpy()
         out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt, "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
@@ -351,9 +352,9 @@ def main():
     ap.add_argument("--ref-events", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain vs learned comparison")
-    ap.add_argument("--forms-events", type=int, default=500_000)
+    ap.add_argument("--forms-events", type=int, default=4_000_000)
     ap.add_argument("--forms-steps", type=int, default=3)
-    ap.add_argument("--train-events", type=int, default=200_000)
+    ap.add_argument("--train-events", type=int, default=1_000_000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

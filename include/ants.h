@@ -87,6 +87,7 @@ typedef struct ants_ctx ants_ctx;
 typedef struct ants_detector ants_detector;
 typedef struct ants_lrf ants_lrf;
 typedef struct ants_mlp ants_mlp;
+typedef struct ants_batch_plan ants_batch_plan;
 
 /* Parameters of the contracting-grid search (Sec. 5.1.2.2).
  * The grid has n_xy x n_xy (x n_z) nodes centred on the current centre with
@@ -327,6 +328,59 @@ ANTS_API int ants_deviance(ants_ctx *ctx, const ants_lrf *lrf, const float *sign
 ANTS_API int ants_simulate_events(ants_ctx *ctx, const ants_lrf *lrf, const ants_sim_params *params,
                                   uint64_t seed, long first_event, long n_events, float *signals_dev,
                                   float *truth_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched reconstruction of several detectors in one persistent launch      */
+/* ------------------------------------------------------------------------ */
+
+/* One detector's share of a batch: its LRF set (with the detector bound to
+ * it), search settings, device signals and outputs as in ants_reconstruct. */
+typedef struct {
+    const ants_lrf *lrf;
+    ants_cgs_params params;
+    const float *signals_dev;    /* [n_events][n_sensors of the LRF] */
+    long n_events;
+    const float *start_xyz_dev;  /* nullable */
+    float *xyz_dev;
+    float *E_dev;
+    float *logL_dev;
+    int32_t *status_dev;
+    int16_t *trace_dev;          /* nullable [n_events][iters] */
+} ants_batch_item;
+
+/* Launch shape of a batch: events per work unit, warps per block (1..8),
+ * blocks per SM (1..32). */
+typedef struct {
+    int unit_events;
+    int warps_per_block;
+    int blocks_per_sm;
+} ants_batch_config;
+
+/* Build a plan: the work units (unit_events events of one detector each)
+ * sorted by cost (nodes x iterations x sensors x events) largest first, and a
+ * CUDA graph that resets a work counter and launches one persistent kernel in
+ * which every warp takes units from that counter and runs the per-event
+ * contracting-grid search of the unit's detector (Sec. 5.1.2.2; any mix of
+ * RADIAL, XY and XYZ LRFs).  Items and their buffers must outlive the plan.
+ * cfg nullable (16 events per unit, 8 warps per block, 4 blocks per SM).
+ * Errors: ANTS_E_ARG, ANTS_E_CUDA, ANTS_E_OOM. */
+ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch_item *items,
+                                    const ants_batch_config *cfg, ants_batch_plan **out);
+
+/* Launch the plan's graph on `stream` (asynchronous).  Calls with one plan
+ * must not overlap (they share the work counter). */
+ANTS_API int ants_batch_run(ants_batch_plan *plan, void *stream);
+
+/* Choose the launch shape: time every candidate (units of 4/16/64 events,
+ * 4/8 warps per block, 2/4/8 blocks per SM) on the first events_per_item
+ * events of every detector (<= 0: 2048) and keep the fastest.  With
+ * cache_path, a previous choice for the same batch signature is reused, and
+ * a new choice is appended to that text file.  Synchronous.  The plan is
+ * rebuilt with the choice; *chosen (nullable) receives it. */
+ANTS_API int ants_batch_autotune(ants_batch_plan *plan, const char *cache_path, long events_per_item,
+                                 ants_batch_config *chosen);
+ANTS_API int ants_batch_get_config(const ants_batch_plan *plan, ants_batch_config *cfg);
+ANTS_API void ants_batch_plan_free(ants_batch_plan *plan);
 
 /* ------------------------------------------------------------------------ */
 /* Learned proposal network                                                  */

@@ -83,6 +83,18 @@ class SimParams(C.Structure):
         super().__init__(0 if region == "disk" else 1, extent, cx, cy, z_lo, z_hi, e0, e_spread, spe_sigma)
 
 
+class BatchItem(C.Structure):
+    """ants_batch_item: one detector's share of a batched run."""
+    _fields_ = [("lrf", C.c_void_p), ("params", CgsParams), ("signals_dev", C.c_void_p), ("n_events", C.c_long),
+                ("start_xyz_dev", C.c_void_p), ("xyz_dev", C.c_void_p), ("E_dev", C.c_void_p),
+                ("logL_dev", C.c_void_p), ("status_dev", C.c_void_p), ("trace_dev", C.c_void_p)]
+
+
+class BatchConfig(C.Structure):
+    """ants_batch_config: events per work unit, warps per block, blocks per SM."""
+    _fields_ = [("unit_events", C.c_int), ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
 class SeededParams(C.Structure):
     """ants_mlp_seeded_params: network start, local refine, plain fallback."""
     _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
@@ -127,6 +139,13 @@ def lib() -> C.CDLL:
         L.ants_reconstruct_host_noalloc.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP,
                                                     _VP, _VP, _VP, _VP]
         L.ants_reconstruct_host_noalloc.restype = C.c_int
+        L.ants_batch_plan_create.argtypes = [_VP, C.c_int, C.POINTER(BatchItem), C.POINTER(BatchConfig),
+                                             C.POINTER(_VP)]
+        L.ants_batch_run.argtypes = [_VP, _VP]
+        L.ants_batch_autotune.argtypes = [_VP, C.c_char_p, C.c_long, C.POINTER(BatchConfig)]
+        L.ants_batch_get_config.argtypes = [_VP, C.POINTER(BatchConfig)]
+        L.ants_batch_plan_free.argtypes = [_VP]
+        L.ants_batch_plan_free.restype = None
         L.ants_simulate_events.argtypes = [_VP, _VP, C.POINTER(SimParams), C.c_uint64, C.c_long, C.c_long, _VP, _VP,
                                            _VP]
         L.ants_deviance.argtypes = [_VP, _VP, _VP, C.c_long, C.c_int, _VP, _VP, _VP]
@@ -290,6 +309,70 @@ def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signa
     _check(lib().ants_reconstruct_host_noalloc(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                                int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
                                                _tptr(E), _tptr(logL), _tptr(status)))
+
+
+def ants_batch_plan_create(ctx: int, items, cfg: BatchConfig | None = None) -> int:
+    arr = (BatchItem * len(items))(*items)
+    h = _VP()
+    _check(lib().ants_batch_plan_create(ctx, len(items), arr, C.byref(cfg) if cfg is not None else None, C.byref(h)))
+    return h.value
+
+
+def ants_batch_run(plan: int, stream=None) -> None:
+    _check(lib().ants_batch_run(plan, _stream_handle(stream)))
+
+
+def ants_batch_autotune(plan: int, cache_path: str | None = None, events_per_item: int = 2048) -> BatchConfig:
+    c = BatchConfig()
+    _check(lib().ants_batch_autotune(plan, cache_path.encode() if cache_path else None, int(events_per_item),
+                                     C.byref(c)))
+    return c
+
+
+def ants_batch_get_config(plan: int) -> BatchConfig:
+    c = BatchConfig()
+    _check(lib().ants_batch_get_config(plan, C.byref(c)))
+    return c
+
+
+def ants_batch_plan_free(plan: int) -> None:
+    lib().ants_batch_plan_free(plan)
+
+
+class BatchPlan:
+    """A batched persistent run over several detectors (owning wrapper).
+
+    items: list of (lrf, params, signals, start_xyz or None); outputs are
+    allocated here (xyz, E, logL, status, trace per item)."""
+
+    def __init__(self, ctx: Context, items, cfg: BatchConfig | None = None, want_trace=False):
+        import torch
+        self.ctx, self.outs, self._keep = ctx, [], []
+        c_items = []
+        for lrf, params, sig, start in items:
+            n = int(sig.shape[0])
+            o = Result(torch.empty((n, 3), device=sig.device), torch.empty(n, device=sig.device),
+                       torch.empty(n, device=sig.device), torch.empty(n, dtype=torch.int32, device=sig.device),
+                       torch.empty((n, params.iters), dtype=torch.int16, device=sig.device) if want_trace else None)
+            self.outs.append(o)
+            self._keep.append((lrf, sig, start))
+            c_items.append(BatchItem(lrf.handle, params, sig.data_ptr(), n, _tptr(start), o.xyz.data_ptr(),
+                                     o.E.data_ptr(), o.logL.data_ptr(), o.status.data_ptr(), _tptr(o.trace)))
+        self.handle = ants_batch_plan_create(ctx.handle, c_items, cfg)
+
+    def run(self, stream=None):
+        ants_batch_run(self.handle, stream)
+
+    def autotune(self, cache_path=None, events_per_item=2048) -> BatchConfig:
+        return ants_batch_autotune(self.handle, cache_path, events_per_item)
+
+    def config(self) -> BatchConfig:
+        return ants_batch_get_config(self.handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_batch_plan_free(self.handle)
+            self.handle = None
 
 
 def ants_simulate_events(ctx: int, lrf: int, params: SimParams, seed: int, first_event: int, signals, truth=None,

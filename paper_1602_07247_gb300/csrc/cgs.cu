@@ -11,7 +11,12 @@
 //              two large rounded sums); warp-shuffle argmax, ties to the
 //              lowest node index.
 //   epilogue   E = S/H and the full Poisson logL at the final node.
+#include <algorithm>
 #include <cfloat>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
 
 #include "bspline.cuh"
 #include "internal.cuh"
@@ -131,139 +136,147 @@ __device__ __forceinline__ float node_score(const LrfDev &L, const float *s_sig,
     return acc - S * (log1pf(dH * inv_hc) * 1.4426950408889634f);
 }
 
+// Reconstruct event e of a (one warp; s_sig, s_ic, s_ec: 3 n_s floats of
+// this warp's shared memory).  Shared by the plain and the batched kernels.
+template <int TYPE>
+__device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig, float *s_ic, float *s_ec,
+                                          int lane)
+{
+    const LrfDev &L = a.L;
+    const int n_s = L.n_s;
+    const int nodes = a.n_xy * a.n_xy * a.n_z;
+    const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
+    const float qnan = __int_as_float(0x7fc00000);
+    const float *sg = a.sig + e * n_s;
+    float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
+    int bad = 0;
+    for (int i = lane; i < n_s; i += 32) {
+        float v = sg[i];
+        bad |= !(v >= 0.0f) || isinf(v);
+        s_sig[i] = v;
+        float w = v * L.cog_w[i];
+        S += v;
+        Sx = fmaf(L.sxy[2 * i], w, Sx);
+        Sy = fmaf(L.sxy[2 * i + 1], w, Sy);
+        Sw += w;
+    }
+    bad = __any_sync(kFull, bad);
+    S = warp_sum(S);
+    Sx = warp_sum(Sx);
+    Sy = warp_sum(Sy);
+    Sw = warp_sum(Sw);
+    __syncwarp();
+    int st = ANTS_EVT_OK;
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    if (bad) st = ANTS_EVT_BAD_SIGNAL;
+    else if (!(S > 0.0f)) st = ANTS_EVT_ZERO_SIGNAL;
+    if (st == ANTS_EVT_OK) {
+        if (a.start) {
+            cx = a.start[3 * e];
+            cy = a.start[3 * e + 1];
+            cz = a.start[3 * e + 2];
+        } else {
+            cx = Sx / Sw;
+            cy = Sy / Sw;
+            cz = TYPE == ANTS_LRF_XYZ ? a.z0 : 0.0f;
+            if (TYPE != ANTS_LRF_RADIAL) {
+                cx = fminf(fmaxf(cx, L.lo[0]), L.hi[0]);
+                cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
+            }
+        }
+        bool ok = TYPE == ANTS_LRF_RADIAL ? node_in_domain_radial(L, cx, cy) : in_box(L, cx, cy, cz);
+        if (!ok) st = ANTS_EVT_OUT_OF_DOMAIN;
+    }
+    if (st != ANTS_EVT_OK) {
+        if (lane == 0) {
+            a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
+            a.E[e] = qnan;
+            a.logL[e] = qnan;
+            a.status[e] = st;
+        }
+        if (a.trace)
+            for (int it = lane; it < a.iters; it += 32) a.trace[e * a.iters + it] = -1;
+        return;
+    }
+
+    float sxy = a.step_xy, sz = a.step_z;
+    for (int it = 0; it < a.iters; ++it) {
+        // eta_i and H at the grid centre
+        float hc = 0.0f;
+        for (int i = lane; i < n_s; i += 32) {
+            float eta = eta_floor<TYPE>(L, i, cx, cy, cz);
+            s_ec[i] = eta;
+            s_ic[i] = __frcp_rn(eta);
+            hc += eta;
+        }
+        hc = warp_sum(hc);
+        const float inv_hc = __frcp_rn(hc);
+        __syncwarp();
+        float bestF = -INFINITY;
+        int bestk = 0x7fffffff;
+        for (int k = lane; k < nodes; k += 32) {
+            int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
+            float x = fmaf((float)(ix - c_xy), sxy, cx);
+            float y = fmaf((float)(iy - c_xy), sxy, cy);
+            float z = fmaf((float)(iz - c_z), sz, cz);
+            float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
+            if (F > bestF) {
+                bestF = F;
+                bestk = k;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            float F2 = __shfl_xor_sync(kFull, bestF, o);
+            int k2 = __shfl_xor_sync(kFull, bestk, o);
+            if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
+                bestF = F2;
+                bestk = k2;
+            }
+        }
+        int ix = bestk % a.n_xy, iy = (bestk / a.n_xy) % a.n_xy, iz = bestk / (a.n_xy * a.n_xy);
+        cx = fmaf((float)(ix - c_xy), sxy, cx);
+        cy = fmaf((float)(iy - c_xy), sxy, cy);
+        cz = fmaf((float)(iz - c_z), sz, cz);
+        if (a.trace && lane == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
+        sxy *= a.shrink;
+        sz *= a.shrink;
+        __syncwarp();
+    }
+
+    // energy and full Poisson log-likelihood at the result
+    float H = 0.0f;
+    for (int i = lane; i < n_s; i += 32) H += eta_floor<TYPE>(L, i, cx, cy, cz);
+    H = warp_sum(H);
+    const float E = S / H;
+    float ll = 0.0f;
+    for (int i = lane; i < n_s; i += 32) {
+        float mu = E * eta_floor<TYPE>(L, i, cx, cy, cz);
+        float s = s_sig[i];
+        ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
+    }
+    ll = warp_sum(ll);
+    if (lane == 0) {
+        a.xyz[3 * e] = cx;
+        a.xyz[3 * e + 1] = cy;
+        a.xyz[3 * e + 2] = cz;
+        a.E[e] = E;
+        a.logL[e] = ll;
+        a.status[e] = ANTS_EVT_OK;
+    }
+    __syncwarp();
+}
+
 template <int TYPE>
 __global__ void __launch_bounds__(256) cgs_plain_kernel(CgsArgs a)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const LrfDev &L = a.L;
-    const int n_s = L.n_s;
+    const int n_s = a.L.n_s;
     float *s_sig = smem + (size_t)wib * 3 * n_s;
     float *s_ic = s_sig + n_s;  // 1 / eta_i(centre)
     float *s_ec = s_ic + n_s;   // eta_i(centre)
-    const int nodes = a.n_xy * a.n_xy * a.n_z;
-    const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
-    const float qnan = __int_as_float(0x7fc00000);
-
-    for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb) {
-        const float *sg = a.sig + e * n_s;
-        float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
-        int bad = 0;
-        for (int i = lane; i < n_s; i += 32) {
-            float v = sg[i];
-            bad |= !(v >= 0.0f) || isinf(v);
-            s_sig[i] = v;
-            float w = v * L.cog_w[i];
-            S += v;
-            Sx = fmaf(L.sxy[2 * i], w, Sx);
-            Sy = fmaf(L.sxy[2 * i + 1], w, Sy);
-            Sw += w;
-        }
-        bad = __any_sync(kFull, bad);
-        S = warp_sum(S);
-        Sx = warp_sum(Sx);
-        Sy = warp_sum(Sy);
-        Sw = warp_sum(Sw);
-        __syncwarp();
-        int st = ANTS_EVT_OK;
-        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-        if (bad) st = ANTS_EVT_BAD_SIGNAL;
-        else if (!(S > 0.0f)) st = ANTS_EVT_ZERO_SIGNAL;
-        if (st == ANTS_EVT_OK) {
-            if (a.start) {
-                cx = a.start[3 * e];
-                cy = a.start[3 * e + 1];
-                cz = a.start[3 * e + 2];
-            } else {
-                cx = Sx / Sw;
-                cy = Sy / Sw;
-                cz = TYPE == ANTS_LRF_XYZ ? a.z0 : 0.0f;
-                if (TYPE != ANTS_LRF_RADIAL) {
-                    cx = fminf(fmaxf(cx, L.lo[0]), L.hi[0]);
-                    cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
-                }
-            }
-            bool ok = TYPE == ANTS_LRF_RADIAL ? node_in_domain_radial(L, cx, cy) : in_box(L, cx, cy, cz);
-            if (!ok) st = ANTS_EVT_OUT_OF_DOMAIN;
-        }
-        if (st != ANTS_EVT_OK) {
-            if (lane == 0) {
-                a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
-                a.E[e] = qnan;
-                a.logL[e] = qnan;
-                a.status[e] = st;
-            }
-            if (a.trace)
-                for (int it = lane; it < a.iters; it += 32) a.trace[e * a.iters + it] = -1;
-            continue;
-        }
-
-        float sxy = a.step_xy, sz = a.step_z;
-        for (int it = 0; it < a.iters; ++it) {
-            // eta_i and H at the grid centre
-            float hc = 0.0f;
-            for (int i = lane; i < n_s; i += 32) {
-                float eta = eta_floor<TYPE>(L, i, cx, cy, cz);
-                s_ec[i] = eta;
-                s_ic[i] = __frcp_rn(eta);
-                hc += eta;
-            }
-            hc = warp_sum(hc);
-            const float inv_hc = __frcp_rn(hc);
-            __syncwarp();
-            float bestF = -INFINITY;
-            int bestk = 0x7fffffff;
-            for (int k = lane; k < nodes; k += 32) {
-                int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
-                float x = fmaf((float)(ix - c_xy), sxy, cx);
-                float y = fmaf((float)(iy - c_xy), sxy, cy);
-                float z = fmaf((float)(iz - c_z), sz, cz);
-                float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
-                if (F > bestF) {
-                    bestF = F;
-                    bestk = k;
-                }
-            }
-            for (int o = 16; o; o >>= 1) {
-                float F2 = __shfl_xor_sync(kFull, bestF, o);
-                int k2 = __shfl_xor_sync(kFull, bestk, o);
-                if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
-                    bestF = F2;
-                    bestk = k2;
-                }
-            }
-            int ix = bestk % a.n_xy, iy = (bestk / a.n_xy) % a.n_xy, iz = bestk / (a.n_xy * a.n_xy);
-            cx = fmaf((float)(ix - c_xy), sxy, cx);
-            cy = fmaf((float)(iy - c_xy), sxy, cy);
-            cz = fmaf((float)(iz - c_z), sz, cz);
-            if (a.trace && lane == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
-            sxy *= a.shrink;
-            sz *= a.shrink;
-            __syncwarp();
-        }
-
-        // energy and full Poisson log-likelihood at the result
-        float H = 0.0f;
-        for (int i = lane; i < n_s; i += 32) H += eta_floor<TYPE>(L, i, cx, cy, cz);
-        H = warp_sum(H);
-        const float E = S / H;
-        float ll = 0.0f;
-        for (int i = lane; i < n_s; i += 32) {
-            float mu = E * eta_floor<TYPE>(L, i, cx, cy, cz);
-            float s = s_sig[i];
-            ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
-        }
-        ll = warp_sum(ll);
-        if (lane == 0) {
-            a.xyz[3 * e] = cx;
-            a.xyz[3 * e + 1] = cy;
-            a.xyz[3 * e + 2] = cz;
-            a.E[e] = E;
-            a.logL[e] = ll;
-            a.status[e] = ANTS_EVT_OK;
-        }
-        __syncwarp();
-    }
+    for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb)
+        cgs_event<TYPE>(a, e, s_sig, s_ic, s_ec, lane);
 }
 
 template <int TYPE>
@@ -336,3 +349,325 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
 }
 
 }  // namespace ants
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch over several detectors (one work queue)
+// ---------------------------------------------------------------------------
+
+namespace ants {
+namespace {
+
+struct BatchUnit {
+    int item;    // index into the items
+    int count;   // events in this unit
+    long first;  // first event of the unit
+};
+
+// Persistent warps take units from a global counter (largest work first) and
+// reconstruct their events with the per-event search of the unit's detector.
+__global__ void __launch_bounds__(256) cgs_batched_kernel(const CgsArgs *__restrict__ items,
+                                                          const BatchUnit *__restrict__ units, int n_units,
+                                                          int *__restrict__ counter, int max_ns)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *s_sig = smem + (size_t)wib * 3 * max_ns;
+    float *s_ic = s_sig + max_ns;
+    float *s_ec = s_ic + max_ns;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(counter, 1);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= n_units) break;
+        const BatchUnit U = units[u];
+        const CgsArgs a = items[U.item];
+        const long end = U.first + U.count;
+        switch (a.L.type) {
+        case ANTS_LRF_RADIAL:
+            for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_RADIAL>(a, e, s_sig, s_ic, s_ec, lane);
+            break;
+        case ANTS_LRF_XY:
+            for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_XY>(a, e, s_sig, s_ic, s_ec, lane);
+            break;
+        default:
+            for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_XYZ>(a, e, s_sig, s_ic, s_ec, lane);
+            break;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ants
+
+struct ants_batch_plan {
+    ants_ctx *ctx = nullptr;
+    std::vector<ants_batch_item> items;
+    ants_batch_config cfg{};
+    ants::CgsArgs *d_items = nullptr;
+    ants::BatchUnit *d_units = nullptr;
+    int *d_counter = nullptr;
+    int n_units = 0, max_ns = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace ants {
+namespace {
+
+void release_plan_device(ants_batch_plan *P)
+{
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    cudaFree(P->d_items);
+    cudaFree(P->d_units);
+    cudaFree(P->d_counter);
+    P->exec = nullptr;
+    P->graph = nullptr;
+    P->d_items = nullptr;
+    P->d_units = nullptr;
+    P->d_counter = nullptr;
+}
+
+// (Re)build the work list and the captured graph for the plan's config;
+// event_cap > 0 limits every detector to its first event_cap events.
+int build_plan(ants_batch_plan *P, long event_cap)
+{
+    release_plan_device(P);
+    const ants_ctx *ctx = P->ctx;
+    const int n_items = (int)P->items.size();
+    std::vector<CgsArgs> args(n_items);
+    std::vector<BatchUnit> units;
+    std::vector<double> cost;
+    P->max_ns = 1;
+    for (int k = 0; k < n_items; ++k) {
+        const ants_batch_item &it = P->items[k];
+        CgsArgs &a = args[k];
+        a.L = it.lrf->dev;
+        a.n_xy = it.params.n_xy;
+        a.n_z = it.params.n_z;
+        a.iters = it.params.iters;
+        a.shrink = it.params.shrink;
+        a.step_xy = it.params.step_xy;
+        a.step_z = it.params.step_z;
+        a.z0 = it.params.z0;
+        a.sig = it.signals_dev;
+        a.n_e = it.n_events;
+        a.start = it.start_xyz_dev;
+        a.xyz = it.xyz_dev;
+        a.E = it.E_dev;
+        a.logL = it.logL_dev;
+        a.status = it.status_dev;
+        a.trace = it.trace_dev;
+        P->max_ns = std::max(P->max_ns, it.lrf->n_s);
+        const long n = event_cap > 0 ? std::min(event_cap, it.n_events) : it.n_events;
+        const double per_event = (double)a.n_xy * a.n_xy * a.n_z * a.iters * it.lrf->n_s;
+        for (long f = 0; f < n; f += P->cfg.unit_events) {
+            BatchUnit u{k, (int)std::min<long>(P->cfg.unit_events, n - f), f};
+            units.push_back(u);
+            cost.push_back(per_event * u.count);
+        }
+    }
+    // largest units first; ties in (item, first) order
+    std::vector<int> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<BatchUnit> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    P->n_units = (int)sorted.size();
+    ANTS_CUDA_TRY(cudaMalloc(&P->d_items, sizeof(CgsArgs) * std::max(1, n_items)), "plan items");
+    ANTS_CUDA_TRY(cudaMalloc(&P->d_units, sizeof(BatchUnit) * std::max<size_t>(1, sorted.size())), "plan units");
+    ANTS_CUDA_TRY(cudaMalloc(&P->d_counter, 256), "plan counter");
+    ANTS_CUDA_TRY(cudaMemcpy(P->d_items, args.data(), sizeof(CgsArgs) * n_items, cudaMemcpyHostToDevice), "upload");
+    if (!sorted.empty())
+        ANTS_CUDA_TRY(cudaMemcpy(P->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice),
+                      "upload");
+    const int threads = 32 * P->cfg.warps_per_block;
+    const size_t smem = (size_t)P->cfg.warps_per_block * 3 * P->max_ns * sizeof(float);
+    ANTS_CUDA_TRY(cudaFuncSetAttribute(cgs_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "cudaFuncSetAttribute(batched)");
+    const unsigned blocks = (unsigned)(ctx->n_sm * P->cfg.blocks_per_sm);
+    if (!P->cap) ANTS_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "plan stream");
+    // the run is one graph: reset the work counter, launch the persistent kernel
+    ANTS_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaMemsetAsync(P->d_counter, 0, sizeof(int), P->cap);
+    cgs_batched_kernel<<<blocks, threads, smem, P->cap>>>(P->d_items, P->d_units, P->n_units, P->d_counter,
+                                                         P->max_ns);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(P->cap, &P->graph);
+    if (e1 != cudaSuccess) return cuda_fail(e1, "batched launch (capture)");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    ANTS_CUDA_TRY(cudaGraphInstantiate(&P->exec, P->graph, 0), "graph instantiate");
+    return ANTS_OK;
+}
+
+int check_config(const ants_batch_config &c)
+{
+    if (c.unit_events < 1 || c.unit_events > (1 << 20) || c.warps_per_block < 1 || c.warps_per_block > 8 ||
+        c.blocks_per_sm < 1 || c.blocks_per_sm > 32)
+        return fail(ANTS_E_ARG, "batch config: unit_events 1..2^20, warps_per_block 1..8, blocks_per_sm 1..32");
+    return ANTS_OK;
+}
+
+std::string plan_signature(const ants_batch_plan *P)
+{
+    std::string sig;
+    char buf[128];
+    for (const auto &it : P->items) {
+        snprintf(buf, sizeof buf, "%d:%d:%d:%d:%d:%d:%ld;", it.lrf->type, it.lrf->n_s, it.lrf->n_coef,
+                 it.params.n_xy * it.params.n_xy * it.params.n_z, it.params.iters, 0, it.n_events);
+        sig += buf;
+    }
+    return sig;
+}
+
+}  // namespace
+}  // namespace ants
+
+extern "C" {
+
+ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch_item *items,
+                                    const ants_batch_config *cfg, ants_batch_plan **out)
+{
+    using namespace ants;
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_batch_plan_create: out is NULL");
+    *out = nullptr;
+    if (!ctx || n_items < 1 || n_items > 4096 || !items) return fail(ANTS_E_ARG, "ants_batch_plan_create: bad items");
+    for (int k = 0; k < n_items; ++k) {
+        const ants_batch_item &it = items[k];
+        if (!it.lrf || it.lrf->ctx != ctx) return fail(ANTS_E_ARG, "batch item %d: LRF of another context", k);
+        if (it.n_events < 0) return fail(ANTS_E_ARG, "batch item %d: n_events < 0", k);
+        if (it.n_events > 0 && (!it.signals_dev || !it.xyz_dev || !it.E_dev || !it.logL_dev || !it.status_dev))
+            return fail(ANTS_E_ARG, "batch item %d: NULL buffer", k);
+        int rc = check_cgs_params(it.lrf, &it.params);
+        if (rc != ANTS_OK) return rc;
+    }
+    ants_batch_config c = cfg ? *cfg : ants_batch_config{16, 8, 4};
+    int rc = check_config(c);
+    if (rc != ANTS_OK) return rc;
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ants_batch_plan *P = new (std::nothrow) ants_batch_plan();
+    if (!P) return fail(ANTS_E_OOM, "ants_batch_plan_create: out of host memory");
+    P->ctx = ctx;
+    P->items.assign(items, items + n_items);
+    P->cfg = c;
+    rc = build_plan(P, 0);
+    if (rc != ANTS_OK) {
+        std::string keep = ants_last_error();
+        ants_batch_plan_free(P);
+        return fail(rc, "%s", keep.c_str());
+    }
+    *out = P;
+    return ANTS_OK;
+}
+
+ANTS_API int ants_batch_run(ants_batch_plan *P, void *stream)
+{
+    using namespace ants;
+    begin_call();
+    if (!P || !P->exec) return fail(ANTS_E_ARG, "ants_batch_run: no plan");
+    ANTS_CUDA_TRY(cudaSetDevice(P->ctx->device), "cudaSetDevice");
+    ANTS_CUDA_TRY(cudaGraphLaunch(P->exec, (cudaStream_t)stream), "graph launch");
+    count_launch();
+    return ANTS_OK;
+}
+
+ANTS_API int ants_batch_get_config(const ants_batch_plan *P, ants_batch_config *cfg)
+{
+    using namespace ants;
+    begin_call();
+    if (!P || !cfg) return fail(ANTS_E_ARG, "ants_batch_get_config: NULL argument");
+    *cfg = P->cfg;
+    return ANTS_OK;
+}
+
+ANTS_API int ants_batch_autotune(ants_batch_plan *P, const char *cache_path, long events_per_item,
+                                 ants_batch_config *chosen)
+{
+    using namespace ants;
+    begin_call();
+    if (!P) return fail(ANTS_E_ARG, "ants_batch_autotune: no plan");
+    if (events_per_item < 1) events_per_item = 2048;
+    ANTS_CUDA_TRY(cudaSetDevice(P->ctx->device), "cudaSetDevice");
+    const std::string sig = plan_signature(P);
+    // cached choice for this batch signature
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[8192];
+            while (fgets(line, sizeof line, f)) {
+                char key[8000];
+                ants_batch_config c;
+                if (sscanf(line, "%7999s %d %d %d", key, &c.unit_events, &c.warps_per_block, &c.blocks_per_sm) == 4 &&
+                    sig == key && check_config(c) == ANTS_OK) {
+                    fclose(f);
+                    P->cfg = c;
+                    int rc = build_plan(P, 0);
+                    if (rc == ANTS_OK && chosen) *chosen = c;
+                    return rc;
+                }
+            }
+            fclose(f);
+        }
+    }
+    const int units[] = {4, 16, 64};
+    const int warps[] = {4, 8};
+    const int blocks[] = {2, 4, 8};
+    ants_batch_config best = P->cfg;
+    float best_ms = INFINITY;
+    cudaEvent_t e0, e1;
+    ANTS_CUDA_TRY(cudaEventCreate(&e0), "event");
+    ANTS_CUDA_TRY(cudaEventCreate(&e1), "event");
+    int rc = ANTS_OK;
+    for (int u : units)
+        for (int w : warps)
+            for (int b : blocks) {
+                if (rc != ANTS_OK) break;
+                if (w * b > 64) continue;  // at most 64 warps per SM
+                P->cfg = ants_batch_config{u, w, b};
+                rc = build_plan(P, events_per_item);
+                if (rc != ANTS_OK) break;
+                float ms = 0.0f;
+                cudaGraphLaunch(P->exec, P->cap);  // warm-up
+                cudaEventRecord(e0, P->cap);
+                cudaGraphLaunch(P->exec, P->cap);
+                cudaGraphLaunch(P->exec, P->cap);
+                cudaEventRecord(e1, P->cap);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "autotune timing");
+                    break;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = P->cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ANTS_OK) return rc;
+    P->cfg = best;
+    rc = build_plan(P, 0);
+    if (rc != ANTS_OK) return rc;
+    if (chosen) *chosen = best;
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d %d\n", sig.c_str(), best.unit_events, best.warps_per_block, best.blocks_per_sm);
+            fclose(f);
+        }
+    }
+    count_launch(0);
+    return ANTS_OK;
+}
+
+ANTS_API void ants_batch_plan_free(ants_batch_plan *P)
+{
+    if (!P) return;
+    cudaSetDevice(P->ctx->device);
+    ants::release_plan_device(P);
+    if (P->cap) cudaStreamDestroy(P->cap);
+    delete P;
+}
+
+}  // extern "C"

@@ -117,5 +117,36 @@ def sipm4x4_xyz() -> Workload:
 WORKLOADS = {w().name: w for w in (hex19_radial, sipm8x8_xy, sipm16x16_xy, sipm4x4_xyz)}
 
 
+def batch8_xyz() -> list:
+    """Eight detectors with depth-dependent (XYZ) LRFs for one batched run:
+    hexagonal PMT arrays of 19/37/61/91/127 at pitch 30 mm and square SiPM
+    arrays 8 x 8 at 6 mm and 2 x (16 x 16) at 3.2 mm.  LRFs: 16 x 16 x 8
+    intervals over the field of view x z in [0, 20] mm; sources uniform over
+    the sensor area and in z; contracting grid 7 x 7 x 5, 7 grids.  Event
+    counts 2e5, 1e4, 6e4, 3.5e5, 3e4, 1e5, 2e6, 2.5e5 (3.0e6 in total)."""
+    out = []
+    hexes = ((2, 200_000), (3, 10_000), (4, 60_000), (5, 30_000), (6, 100_000))
+    for k, (rings, n) in enumerate(hexes):
+        sxy = hex_array(rings, 30.0)
+        half = rings * 30.0 + 30.0
+        out.append(Workload(
+            name=f"hex{sxy.shape[0]}_xyz", sensor_xy=sxy, gains=sensor_gains(sxy.shape[0], 0.05, 110 + k),
+            lrf_type="xyz", n_int=(16, 16, 8), lo=(-half, -half, 0.0), hi=(half, half, 20.0), shared=False,
+            n_xy=7, iters=7, step_xy=10.0, n_z=5, step_z=5.0, z0=10.0, n_events=n, event_seed=1010 + k,
+            event=dict(region="disk", extent=rings * 30.0, e0=1.0e4, z_range=(0.0, 20.0))))
+    squares = ((8, 6.0, 350_000, 3000.0), (16, 3.2, 2_000_000, 2000.0), (16, 3.2, 250_000, 2000.0))
+    for k, (m, pitch, n, e0) in enumerate(squares):
+        sxy = square_array(m, pitch)
+        half = m * pitch / 2.0
+        out.append(Workload(
+            name=f"sipm{m}x{m}{'ab'[k - 1] if m == 16 else ''}_xyz", sensor_xy=sxy,
+            gains=sensor_gains(m * m, 0.05, 120 + k), lrf_type="xyz", n_int=(16, 16, 8), lo=(-half, -half, 0.0),
+            hi=(half, half, 20.0), shared=False, n_xy=7, iters=7, step_xy=half / 3.0, n_z=5, step_z=5.0, z0=10.0,
+            n_events=n, event_seed=1020 + k,
+            event=dict(region="square", extent=half - pitch / 2.0, e0=e0, z_range=(0.0, 20.0))))
+    order = [0, 1, 2, 5, 3, 4, 6, 7]  # sensor counts 19, 37, 61, 64, 91, 127, 256, 256
+    return [out[i] for i in order]
+
+
 def get(name: str) -> Workload:
     return WORKLOADS[name]()
