@@ -77,6 +77,7 @@ typedef enum {
 /* Reconstruction methods. */
 typedef enum {
     ANTS_CGS_PLAIN = 0, /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
+    ANTS_GEMM_TOPK = 1, /* global-grid tensor-core scores, top-K, local contracting grids */
     ANTS_MLP_SEEDED = 2 /* network proposal + local contracting grids + plain fallback */
 } ants_method;
 
@@ -88,6 +89,7 @@ typedef struct ants_detector ants_detector;
 typedef struct ants_lrf ants_lrf;
 typedef struct ants_mlp ants_mlp;
 typedef struct ants_batch_plan ants_batch_plan;
+typedef struct ants_logtable ants_logtable;
 
 /* Parameters of the contracting-grid search (Sec. 5.1.2.2).
  * The grid has n_xy x n_xy (x n_z) nodes centred on the current centre with
@@ -149,6 +151,18 @@ typedef struct {
     float e_spread;  /* E uniform in e0 (1 +- e_spread), 0 <= e_spread < 1 */
     float spe_sigma; /* relative width of the single photo-electron response (0: counts) */
 } ants_sim_params;
+
+/* Parameters of ANTS_GEMM_TOPK: every event is scored at every point of the
+ * table's global grid with one BF16 tensor-core product (FP32 accumulation),
+ * the top_k points (1..8) are kept, candidates within nms_cells grid cells
+ * (Chebyshev distance) of a better one are dropped, each remaining one
+ * starts the `refine` search, and the result with the largest logL wins. */
+typedef struct {
+    const ants_logtable *table;
+    int top_k;
+    float nms_cells;
+    ants_cgs_params refine;
+} ants_gemm_params;
 
 /* Parameters of ANTS_MLP_SEEDED: the network's (x, y), clamped into the LRF's
  * XY box, starts the `refine` search; events whose Poisson deviance
@@ -266,9 +280,11 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf);
 /* ------------------------------------------------------------------------ */
 
 /* Reconstruct n_events events.
- *   method: ANTS_CGS_PLAIN with params = const ants_cgs_params*, or
- *     ANTS_MLP_SEEDED with params = const ants_mlp_seeded_params* (no
- *     start_xyz_dev; trace_dev then records the refine grids).
+ *   method: ANTS_CGS_PLAIN with params = const ants_cgs_params*,
+ *     ANTS_GEMM_TOPK with params = const ants_gemm_params* (no start_xyz_dev,
+ *     no trace_dev), or ANTS_MLP_SEEDED with params = const
+ *     ants_mlp_seeded_params* (no start_xyz_dev; trace_dev then records the
+ *     refine grids).
  *   signals_dev: [n_events][n_sensors] row-major, element type signal_dtype
  *     (ANTS_F32); n_sensors must equal the LRF's.
  *   start_xyz_dev: nullable [n_events][3] FP32 start positions; NULL = the
@@ -328,6 +344,32 @@ ANTS_API int ants_deviance(ants_ctx *ctx, const ants_lrf *lrf, const float *sign
 ANTS_API int ants_simulate_events(ants_ctx *ctx, const ants_lrf *lrf, const ants_sim_params *params,
                                   uint64_t seed, long first_event, long n_events, float *signals_dev,
                                   float *truth_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Global-grid log-response table (precision form)                           */
+/* ------------------------------------------------------------------------ */
+
+/* Tabulate T[g][i] = ln p_i(g) - m_i on the nx x ny cell centres g of an XY
+ * LRF's box, p_i = eta_i / sum_j eta_j and m_i = mean_g ln p_i(g), stored as
+ * BF16 [nx*ny][n_sensors].  With the energy profiled out (E = S/H,
+ * Sec. 5.1.2.2) the Poisson log-likelihood of an event at g is
+ * sum_i s_i ln p_i(g) plus a term of the event alone, so the scores
+ * sum_i s_i T[g][i] rank the grid points exactly as the likelihood does (the
+ * m_i shift every score of an event equally and keep |T| small for BF16).
+ * Synchronous.  XY LRFs, n_sensors a multiple of 8, nx*ny <= 2^20. */
+ANTS_API int ants_logtable_create(ants_ctx *ctx, const ants_lrf *lrf, int nx, int ny, ants_logtable **out);
+
+/* Copy the table as FP32 (table_host [nx*ny][n_sensors], nullable) and the
+ * centring constants m (mean_host [n_sensors], nullable). */
+ANTS_API int ants_logtable_values(const ants_logtable *table, float *table_host, float *mean_host);
+
+/* Top-K grid points of each event by score sum_i s_i T[g][i]: score_dev and
+ * index_dev [n_events][top_k], descending score, ties to the lower index.
+ * Signals FP32 (rounded to BF16 for the product).  Asynchronous. */
+ANTS_API int ants_logtable_topk(ants_ctx *ctx, const ants_logtable *table, const float *signals_dev,
+                                long n_events, int n_sensors, int top_k, float *score_dev,
+                                int32_t *index_dev, void *stream);
+ANTS_API void ants_logtable_free(ants_logtable *table);
 
 /* ------------------------------------------------------------------------ */
 /* Batched reconstruction of several detectors in one persistent launch      */

@@ -481,3 +481,16 @@ def poisson_draws(lam: float, seed: int, n: int, mutant: int = 0) -> np.ndarray:
     out = np.empty(n)
     _slib(mutant).or_poisson_draws(float(lam), int(seed), int(n), _d(out))
     return out
+
+
+def logtable(lrf: Lrf, nx: int, ny: int, mutant: int = 0):
+    """T [nx*ny, n_s] = ln p_i(g) - m_i and m [n_s] (FP64)."""
+    L = _mlib(mutant)
+    if not getattr(L, "_lt_declared", False):
+        L.or_logtable.argtypes = [C.POINTER(_Lrf), C.c_int, C.c_int, _D, _D]
+        L._lt_declared = True
+    s = lrf._struct()
+    T = np.empty((nx * ny, lrf.n_sensors))
+    m = np.empty(lrf.n_sensors)
+    L.or_logtable(C.byref(s), int(nx), int(ny), _d(T), _d(m))
+    return T, m

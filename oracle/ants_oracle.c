@@ -1065,3 +1065,28 @@ void or_poisson_draws(double lam, uint64_t seed, long n, double *out)
         out[e] = (double)or_poisson(lam, &st);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Global-grid log-response table of the precision form                     */
+/* ------------------------------------------------------------------------ */
+/* T[g][i] = ln p_i(g) - m_i with p_i = eta_i / sum_j eta_j at the centres of
+ * the nx x ny cells of the XY box and m_i = mean_g ln p_i(g). */
+void or_logtable(const or_lrf *L, int nx, int ny, double *T, double *m)
+{
+    long G = (long)nx * ny;
+    int n = L->n_sensors;
+#pragma omp parallel for schedule(static)
+    for (long g = 0; g < G; ++g) {
+        double x = L->lo[0] + ((double)(g % nx) + 0.5) * (L->hi[0] - L->lo[0]) / nx;
+        double y = L->lo[1] + ((double)(g / nx) + 0.5) * (L->hi[1] - L->lo[1]) / ny;
+        double H = 0.0;
+        for (int i = 0; i < n; ++i) H += or_eta_floored(L, i, x, y, 0.0);
+        for (int i = 0; i < n; ++i) T[g * n + i] = log(or_eta_floored(L, i, x, y, 0.0) / H);
+    }
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (long g = 0; g < G; ++g) acc += T[g * n + i];
+        m[i] = acc / (double)G;
+        for (long g = 0; g < G; ++g) T[g * n + i] -= m[i];
+    }
+}

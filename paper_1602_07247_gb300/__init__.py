@@ -27,6 +27,7 @@ ANTS_LRF_RADIAL, ANTS_LRF_XY, ANTS_LRF_XYZ = 1, 2, 3
 ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
 ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
 ANTS_CGS_PLAIN = 0
+ANTS_GEMM_TOPK = 1
 ANTS_MLP_SEEDED = 2
 ANTS_F32 = 0
 ANTS_NOALLOC_STAGE_BYTES = 33554432
@@ -95,6 +96,11 @@ class BatchConfig(C.Structure):
     _fields_ = [("unit_events", C.c_int), ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int)]
 
 
+class GemmParams(C.Structure):
+    """ants_gemm_params: log-response table, top-K, suppression radius, refine."""
+    _fields_ = [("table", C.c_void_p), ("top_k", C.c_int), ("nms_cells", C.c_float), ("refine", CgsParams)]
+
+
 class SeededParams(C.Structure):
     """ants_mlp_seeded_params: network start, local refine, plain fallback."""
     _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
@@ -139,6 +145,11 @@ def lib() -> C.CDLL:
         L.ants_reconstruct_host_noalloc.argtypes = [_VP, _VP, C.c_int, _VP, _VP, C.c_int, C.c_long, C.c_int, _VP,
                                                     _VP, _VP, _VP, _VP]
         L.ants_reconstruct_host_noalloc.restype = C.c_int
+        L.ants_logtable_create.argtypes = [_VP, _VP, C.c_int, C.c_int, C.POINTER(_VP)]
+        L.ants_logtable_values.argtypes = [_VP, _VP, _VP]
+        L.ants_logtable_topk.argtypes = [_VP, _VP, _VP, C.c_long, C.c_int, C.c_int, _VP, _VP, _VP]
+        L.ants_logtable_free.argtypes = [_VP]
+        L.ants_logtable_free.restype = None
         L.ants_batch_plan_create.argtypes = [_VP, C.c_int, C.POINTER(BatchItem), C.POINTER(BatchConfig),
                                              C.POINTER(_VP)]
         L.ants_batch_run.argtypes = [_VP, _VP]
@@ -309,6 +320,55 @@ def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signa
     _check(lib().ants_reconstruct_host_noalloc(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                                int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
                                                _tptr(E), _tptr(logL), _tptr(status)))
+
+
+def ants_logtable_create(ctx: int, lrf: int, nx: int, ny: int) -> int:
+    h = _VP()
+    _check(lib().ants_logtable_create(ctx, lrf, int(nx), int(ny), C.byref(h)))
+    return h.value
+
+
+def ants_logtable_values(table: int, n_points: int, n_sensors: int):
+    T = np.empty((n_points, n_sensors), dtype=np.float32)
+    m = np.empty(n_sensors, dtype=np.float32)
+    _check(lib().ants_logtable_values(table, T.ctypes.data, m.ctypes.data))
+    return T, m
+
+
+def ants_logtable_topk(ctx: int, table: int, signals, top_k: int, score, index, stream=None) -> None:
+    _check(lib().ants_logtable_topk(ctx, table, _tptr(signals), int(signals.shape[0]), int(signals.shape[1]),
+                                    int(top_k), _tptr(score), _tptr(index), _stream_handle(stream)))
+
+
+def ants_logtable_free(table: int) -> None:
+    lib().ants_logtable_free(table)
+
+
+class LogTable:
+    """Global-grid log-response table of an XY LRF set (owning wrapper)."""
+
+    def __init__(self, ctx: Context, lrf: "Lrf", nx: int, ny: int):
+        self.ctx, self.lrf, self.nx, self.ny = ctx, lrf, nx, ny
+        self.handle = ants_logtable_create(ctx.handle, lrf.handle, nx, ny)
+
+    def values(self):
+        return ants_logtable_values(self.handle, self.nx * self.ny, self.lrf.n_sensors)
+
+    def topk(self, signals, k: int, stream=None):
+        import torch
+        n = signals.shape[0]
+        sc = torch.empty((n, k), dtype=torch.float32, device=signals.device)
+        ix = torch.empty((n, k), dtype=torch.int32, device=signals.device)
+        ants_logtable_topk(self.ctx.handle, self.handle, signals, k, sc, ix, stream)
+        return sc, ix
+
+    def params(self, refine: CgsParams, top_k: int = 8, nms_cells: float = 1.5) -> GemmParams:
+        return GemmParams(self.handle, int(top_k), float(nms_cells), refine)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            ants_logtable_free(self.handle)
+            self.handle = None
 
 
 def ants_batch_plan_create(ctx: int, items, cfg: BatchConfig | None = None) -> int:
@@ -593,7 +653,7 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     E = torch.empty(n, dtype=torch.float32, device=dev)
     logL = torch.empty(n, dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
-    iters = params.refine.iters if isinstance(params, SeededParams) else params.iters
+    iters = params.refine.iters if isinstance(params, (SeededParams, GemmParams)) else params.iters
     trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
     ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,

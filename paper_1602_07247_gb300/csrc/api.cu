@@ -424,6 +424,7 @@ static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const vo
         return fail(ANTS_E_SHAPE, "ants_reconstruct: n_sensors %d but the LRF has %d", n_sensors, lrf->n_s);
     if (signal_dtype != ANTS_F32) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: dtype %d", signal_dtype);
     if (method == ANTS_MLP_SEEDED) return check_seeded_params(lrf, (const ants_mlp_seeded_params *)params);
+    if (method == ANTS_GEMM_TOPK) return check_gemm_params(lrf, (const ants_gemm_params *)params);
     if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
     return check_cgs_params(lrf, (const ants_cgs_params *)params);
 }
@@ -440,6 +441,11 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
     if (!signals_dev || !xyz_dev || !E_dev || !logL_dev || !status_dev)
         return fail(ANTS_E_ARG, "ants_reconstruct: NULL signal or output buffer");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (method == ANTS_GEMM_TOPK) {
+        if (start_xyz_dev || trace_dev) return fail(ANTS_E_ARG, "ants_reconstruct: the precision form takes no start or trace");
+        return reconstruct_gemm_topk(ctx, lrf, *(const ants_gemm_params *)params, (const float *)signals_dev, n_events,
+                                     xyz_dev, E_dev, logL_dev, status_dev, (cudaStream_t)stream);
+    }
     if (method == ANTS_MLP_SEEDED) {
         if (start_xyz_dev) return fail(ANTS_E_ARG, "ants_reconstruct: the learned form proposes its own start");
         return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, (const float *)signals_dev,

@@ -34,6 +34,7 @@ struct CgsArgs {
     float shrink, step_xy, step_z, z0;
     const float *sig;
     long n_e;
+    int row_div;  // event e reads signal row e / row_div (several searches per event)
     const float *start;
     float *xyz, *E, *logL;
     int32_t *status;
@@ -147,7 +148,7 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
     const int nodes = a.n_xy * a.n_xy * a.n_z;
     const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
     const float qnan = __int_as_float(0x7fc00000);
-    const float *sg = a.sig + e * n_s;
+    const float *sg = a.sig + (e / a.row_div) * n_s;
     float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
     int bad = 0;
     for (int i = lane; i < n_s; i += 32) {
@@ -322,9 +323,17 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
                      long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
                      int16_t *trace, cudaStream_t stream)
 {
+    return launch_cgs_rows(ctx, lrf, p, sig, 1, n_e, start, xyz, E, logL, status, trace, stream);
+}
+
+int launch_cgs_rows(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig,
+                    int row_div, long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                    int16_t *trace, cudaStream_t stream)
+{
     if (cgs_xy_supported(lrf, p))
-        return launch_cgs_xy(ctx, lrf, p, sig, n_e, start, xyz, E, logL, status, trace, stream);
+        return launch_cgs_xy(ctx, lrf, p, sig, row_div, n_e, start, xyz, E, logL, status, trace, stream);
     CgsArgs a;
+    a.row_div = row_div;
     a.L = lrf->dev;
     a.n_xy = p.n_xy;
     a.n_z = p.n_z;
@@ -453,6 +462,7 @@ int build_plan(ants_batch_plan *P, long event_cap)
         a.z0 = it.params.z0;
         a.sig = it.signals_dev;
         a.n_e = it.n_events;
+        a.row_div = 1;
         a.start = it.start_xyz_dev;
         a.xyz = it.xyz_dev;
         a.E = it.E_dev;

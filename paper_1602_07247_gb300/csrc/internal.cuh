@@ -103,13 +103,21 @@ void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
 int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s);
 int mlp_decode(const ants_mlp *M, const float *O, long n, float *xyz, float *E, cudaStream_t s);
 int mlp_n_in(const ants_mlp *M);
+// precision form (precision.cu)
+int check_gemm_params(const ants_lrf *lrf, const ants_gemm_params *P);
+int reconstruct_gemm_topk(ants_ctx *ctx, const ants_lrf *lrf, const ants_gemm_params &P, const float *sig, long n,
+                          float *xyz, float *E, float *logL, int32_t *status, cudaStream_t s);
 // learned-proposal reconstruction (seeded.cu)
 int check_seeded_params(const ants_lrf *lrf, const ants_mlp_seeded_params *P);
 int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_seeded_params &P, const float *sig,
                            long n, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                            cudaStream_t s);
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
-int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, long n_e,
-                  const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
+int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, int row_div,
+                  long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                   cudaStream_t stream);
+// as launch_cgs_plain, with event e reading signal row e / row_div
+int launch_cgs_rows(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig,
+                    int row_div, long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                    int16_t *trace, cudaStream_t stream);
 }  // namespace ants

@@ -541,10 +541,28 @@ def pin_uniform_stream(mutant=0):
     assert not np.array_equal(oracle.philox(1, (0, 0, 0, 0)), oracle.philox(2, (0, 0, 0, 0)))
 
 
+def pin_logtable_ranks_like_likelihood(mutant=0):
+    """The table scores sum_i s_i T[g][i] differ from the profiled
+    log-likelihood F(g) = sum s ln eta - S ln H by a constant per event, and
+    every column of T averages to zero over the grid."""
+    L, _ = _small_xy_lrf(mutant)
+    T, m = oracle.logtable(L, 9, 7, mutant)
+    assert np.abs(T.mean(axis=0)).max() < 1e-12
+    rng = np.random.default_rng(31)
+    sig = rng.poisson(900 * synth.truth_eta(L.sensor_xy, np.ones(9), rng.uniform(-8, 8, (5, 2)))).astype(float)
+    gx = -16.0 + (np.arange(9) + 0.5) * 32.0 / 9
+    gy = -16.0 + (np.arange(7) + 0.5) * 32.0 / 7
+    pts = np.array([(x, y, 0.0) for y in gy for x in gx])
+    for s in sig:
+        F = oracle.objective_at(L, np.repeat(s[None], len(pts), 0), pts, mutant)
+        d = s @ T.T - F
+        assert np.abs(d - d[0]).max() < 1e-9 * max(1.0, np.abs(F).max())
+
+
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
     pin_noise_free_recovery, pin_noise_free_recovery_3d, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
     pin_event_status, pin_replay, pin_gelu, pin_mlp_forward, pin_mlp_gradient, pin_adam, pin_deviance,
-    pin_poisson_sampler, pin_uniform_stream,
+    pin_poisson_sampler, pin_uniform_stream, pin_logtable_ranks_like_likelihood,
 ]

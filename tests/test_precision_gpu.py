@@ -1,0 +1,92 @@
+"""Precision form on the GPU: log-response table against the FP64 oracle,
+tensor-core top-K against an FP64 product of the same BF16 operands, and the
+whole form against the oracle's refine of every candidate."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import synth.workloads
+from parity import gpu_objects, oracle_lrf, oracle_params, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(x):
+    """Round float32 to the nearest BF16 (ties to even) and back."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def setup16():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1602_07247_gb300 as ants
+    ctx = ants.Context(0)
+    w = synth.workloads.get("sipm16x16_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, plain = gpu_objects(w, L, ctx)
+    table = ants.LogTable(ctx, lrf, 64, 64)
+    return torch, ants, ctx, w, L, det, lrf, plain, table
+
+
+def test_table_matches_oracle(setup16):
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    T, m = table.values()
+    To, mo = oracle.logtable(L, 64, 64)
+    assert np.abs(m - mo).max() < 1e-4
+    err = np.abs(T - To)
+    assert np.all(err <= np.abs(To) * 2.0 ** -8 + 2e-4), err.max()
+
+
+def test_topk_scores_match_fp64_product(setup16):
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    ev = w.events(1037, seed=71)  # ragged against the 64-row tile
+    sc, ix = table.topk(torch.from_numpy(ev.signals).cuda(), 8)
+    sc, ix = sc.cpu().numpy(), ix.cpu().numpy()
+    T, _ = table.values()  # the BF16 table values
+    A = bf16_round(ev.signals).astype(np.float64)
+    full = A @ T.astype(np.float64).T  # [n, 4096]
+    bound = 256 * 2.0 ** -23 * (np.abs(A) @ np.abs(T.astype(np.float64)).T)
+    rows = np.arange(ix.shape[0])[:, None]
+    assert np.all(np.abs(sc - full[rows, ix]) <= bound[rows, ix] + 1e-6)
+    assert np.all(np.diff(sc, axis=1) <= 0)
+    kth = -np.sort(-full, axis=1)[:, 7]
+    slack = bound.max(axis=1) * 2
+    assert np.all(full[rows, ix] >= kth[:, None] - slack[:, None])
+
+
+def test_precision_form_against_oracle_refines(setup16):
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    refine = ants.CgsParams(n_xy=7, iters=5, step_xy=0.8 / 3)
+    gp = table.params(refine, top_k=8, nms_cells=1.5)
+    ev = w.events(301, seed=72)
+    sig = torch.from_numpy(ev.signals).cuda()
+    res = to_numpy(ants.reconstruct(ctx, lrf, gp, sig, method=ants.ANTS_GEMM_TOPK))
+    _, ix = table.topk(sig, 8)
+    ix = ix.cpu().numpy()
+    T, _ = table.values()
+    nx = 64
+    x0, dx = -25.6 + 0.4, 0.8
+    P = oracle.CgsParams(n_xy=7, iters=5, step_xy=0.8 / 3)
+    sig64 = ev.signals.astype(np.float64)
+    best_logl = np.full(len(ev.signals), -np.inf)
+    for e in range(len(ev.signals)):
+        kept = []
+        for g in ix[e]:
+            if all(max(abs(g % nx - h % nx), abs(g // nx - h // nx)) > 1.5 for h in kept):
+                kept.append(g)
+        starts = np.array([[np.float32(x0 + dx * (g % nx)), np.float32(x0 + dx * (g // nx)), 0.0] for g in kept])
+        r = oracle.cgs(L, P, np.repeat(sig64[e:e + 1], len(kept), 0), start_xyz=starts)
+        best_logl[e] = r["logL"].max()
+    E, got_logl = oracle.energy_logl_at(L, sig64, res["xyz"])
+    # the GPU's choice is (within FP32 noise) the best refine the oracle finds
+    tol = 1e-5 * np.abs(best_logl) + 5e-3
+    assert np.all(got_logl >= best_logl - tol), (best_logl - got_logl).max()
+    assert np.abs(res["logL"] / got_logl - 1.0).max() < 1e-5
+    full = to_numpy(ants.reconstruct(ctx, lrf, plain, sig))
+    rms = lambda r: float(np.sqrt(((r["xyz"][:, :2] - ev.xyz[:, :2]) ** 2).sum(1).mean()))
+    print("rms precision form", rms(res), "plain", rms(full))
+    assert rms(res) <= 1.05 * rms(full)
