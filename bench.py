@@ -180,13 +180,16 @@ def forms_comparison(args, ants, torch, ctx, stream):
     ants.ants_deviance(ctx.handle, lrf.handle, csig, rc.xyz, Dc)
     thr = float(np.quantile(Dc.cpu().numpy(), 0.995))
     sp = ants.seeded_params(mlp, refine, plain, deviance_max=thr, border_fallback=True, bf16=1)
+    table = ants.LogTable(ctx, lrf, 64, 64)
+    gp = table.params(ants.CgsParams(n_xy=7, iters=5, step_xy=0.8 / 3, shrink=0.5), top_k=8, nms_cells=1.5)
     sig, etruth = ants.simulate(ctx, lrf, src, args.forms_events, seed=3001)
     torch.cuda.synchronize()
     true_xy = etruth[:, :2].double().cpu().numpy()
     n = sig.shape[0]
     setup_s = time.perf_counter() - t0
     out = {}
-    for name, method, params in (("plain", ants.ANTS_CGS_PLAIN, plain), ("learned", ants.ANTS_MLP_SEEDED, sp)):
+    for name, method, params in (("plain", ants.ANTS_CGS_PLAIN, plain), ("learned", ants.ANTS_MLP_SEEDED, sp),
+                                 ("precision", ants.ANTS_GEMM_TOPK, gp)):
         res = ants.reconstruct(ctx, lrf, params, sig, method=method, stream=stream)
         for _ in range(2):
             ants.reconstruct(ctx, lrf, params, sig, method=method, stream=stream)
@@ -204,11 +207,13 @@ def forms_comparison(args, ants, torch, ctx, stream):
         out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt, "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
                      "median_dxy_mm": float(np.median(err)), "p95_dxy_mm": float(np.quantile(err, 0.95)),
                      "fallback_frac": float((st == ants.ANTS_EVT_FALLBACK).mean())}
-    out["learned"]["speedup_vs_plain"] = out["learned"]["events_per_s"] / out["plain"]["events_per_s"]
-    out["learned"]["rms_ratio_vs_plain"] = out["learned"]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
+    for k in ("learned", "precision"):
+        out[k]["speedup_vs_plain"] = out[k]["events_per_s"] / out["plain"]["events_per_s"]
+        out[k]["rms_ratio_vs_plain"] = out[k]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
     return {"workload": f"{w.name}: 256 sensors, XY LRF 32x32, {n} events; plain {w.n_xy}x{w.n_xy}x{w.iters} vs "
                         f"MLP 256-256-256-3 (BF16, trained on the GPU on {args.train_events} events, "
-                        f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile",
+                        f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile; precision form: "
+                        f"64x64 BF16 log-response table, tensor-core top-8, suppression 1.5 cells, refine 7x7x5",
             "setup_s": setup_s, "deviance_max": thr, **out}
 
 

@@ -33,6 +33,9 @@ struct ants_mlp {
     float *d_par = nullptr;  // FP32 master weights
     float *d_m = nullptr, *d_v = nullptr;
     int adam_t = 0;
+    // BF16 copies of W1 and W2 for tensor-core inference, refreshed on use
+    __nv_bfloat16 *d_w1b = nullptr, *d_w2b = nullptr;
+    bool bf16_stale = true;
 };
 
 namespace ants {
@@ -241,6 +244,33 @@ __global__ void decode_outputs(const float *__restrict__ O, long n, ants_mlp_con
 
 unsigned blocks_for(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+__global__ void to_bf16(const float *__restrict__ x, size_t n, __nv_bfloat16 *__restrict__ y)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// o[r][k] = sum_i bf16(h[r][i]) bf16(W3[k][i]) + b3[k]; one warp per row
+__global__ void output_layer(const __nv_bfloat16 *__restrict__ h, long n, int H, const float *__restrict__ W3,
+                             const float *__restrict__ b3, float *__restrict__ O)
+{
+    const long r = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = lane; i < H; i += 32) {
+        const float hv = __bfloat162float(h[r * H + i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] = fmaf(hv, rbf16(W3[k * H + i]), acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float v = acc[k];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) O[r * 3 + k] = v + b3[k];
+    }
+}
+
 // C = opA(A) opB(B) (+ beta C), dispatching on transposes and precision
 int gemm(bool ta, bool tb, bool bf, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
          int ldc, float beta, cudaStream_t s)
@@ -352,9 +382,54 @@ constexpr int kLossBlocks = 64;
 
 }  // namespace
 
+int mma_bias_gelu(const void *A, bool a_f32, const __nv_bfloat16 *B, const float *bias, int M, int N, int K,
+                  __nv_bfloat16 *out, cudaStream_t s);
+
+// BF16 inference on the tensor cores: the same roundings as the BF16 training
+// path (operands rounded to BF16, FP32 accumulation), in fewer passes
+int mlp_forward_tc(ants_ctx *ctx, const ants_mlp *Mc, const float *sig, long n, float *O, cudaStream_t s)
+{
+    ants_mlp *M = const_cast<ants_mlp *>(Mc);
+    const Offsets o = offsets(M->n_in, M->H);
+    const int H = M->H, I = M->n_in;
+    if (!M->d_w1b) {
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w1b, (size_t)H * I * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w2b, (size_t)H * H * sizeof(__nv_bfloat16)), "bf16 weights");
+        M->bf16_stale = true;
+    }
+    if (M->bf16_stale) {
+        to_bf16<<<blocks_for((long)H * I, 256), 256, 0, s>>>(M->d_par + o.W1, (size_t)H * I, M->d_w1b);
+        to_bf16<<<blocks_for((long)H * H, 256), 256, 0, s>>>(M->d_par + o.W2, (size_t)H * H, M->d_w2b);
+        count_launch(2);
+        M->bf16_stale = false;
+    }
+    const long chunk = 1L << 17;
+    const long cap = n < chunk ? n : chunk;
+    const size_t bytes = (size_t)cap * I * sizeof(float) + 2 * (size_t)cap * H * sizeof(__nv_bfloat16) + 256;
+    unsigned char *base = (unsigned char *)ctx_scratch(ctx, 0, bytes);
+    if (!base) return ANTS_E_OOM;
+    float *U = (float *)base;
+    __nv_bfloat16 *H1 = (__nv_bfloat16 *)(base + (size_t)cap * I * sizeof(float));
+    __nv_bfloat16 *H2 = H1 + (size_t)cap * H;
+    for (long off = 0; off < n; off += chunk) {
+        const long m = n - off < chunk ? n - off : chunk;
+        normalize_rows<<<blocks_for(m, 8), 256, 0, s>>>(sig + off * I, nullptr, m, I, U);
+        count_launch();
+        int rc = mma_bias_gelu(U, true, M->d_w1b, M->d_par + o.b1, (int)m, H, I, H1, s);
+        if (rc != ANTS_OK) return rc;
+        rc = mma_bias_gelu(H1, false, M->d_w2b, M->d_par + o.b2, (int)m, H, H, H2, s);
+        if (rc != ANTS_OK) return rc;
+        output_layer<<<blocks_for(m, 8), 256, 0, s>>>(H2, m, H, M->d_par + o.W3, M->d_par + o.b3, O + off * 3);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ANTS_OK : cuda_fail(e, "mlp tensor-core forward");
+}
+
 // forward of n rows (device signals) into raw outputs O [n][3]; chunked
 int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s)
 {
+    if (bf) return mlp_forward_tc(ctx, M, sig, n, O, s);
     const long chunk = 1L << 16;
     const long cap = n < chunk ? n : chunk;
     float *base = (float *)ctx_scratch(ctx, 0, acts_floats(cap, M->n_in, M->H) * sizeof(float));
@@ -441,6 +516,8 @@ ANTS_API void ants_mlp_free(ants_mlp *M)
     cudaFree(M->d_par);
     cudaFree(M->d_m);
     cudaFree(M->d_v);
+    cudaFree(M->d_w1b);
+    cudaFree(M->d_w2b);
     delete M;
 }
 
@@ -465,6 +542,7 @@ ANTS_API int ants_mlp_set_params(ants_mlp *M, const float *params_host, long cou
     ANTS_CUDA_TRY(cudaMemset(M->d_m, 0, M->n_par * sizeof(float)), "memset");
     ANTS_CUDA_TRY(cudaMemset(M->d_v, 0, M->n_par * sizeof(float)), "memset");
     M->adam_t = 0;
+    M->bf16_stale = true;
     return ANTS_OK;
 }
 
@@ -626,6 +704,7 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
     }
     ANTS_CUDA_TRY(cudaMemcpyAsync(M->d_par, best.p, M->n_par * sizeof(float), cudaMemcpyDeviceToDevice, s),
                   "restore best");
+    M->bf16_stale = true;
     ANTS_CUDA_TRY(cudaStreamSynchronize(s), "mlp train");
     if (report) {
         report->epochs_run = epochs_run;
