@@ -201,6 +201,13 @@ ANTS_API int ants_ctx_create(int device, ants_ctx **out);
  * caller must have synchronised all streams that used it. */
 ANTS_API void ants_ctx_destroy(ants_ctx *ctx);
 
+/* Read and clear the context's device fault word (no counterpart in the
+ * paper; robustness of the tensor-core kernels).  Synchronises the device,
+ * stores 1 in *fault if a kernel launched through this context gave up a
+ * bounded device-side wait since the last call (its outputs are then
+ * undefined) and returns ANTS_E_TIMEOUT; otherwise stores 0, returns ANTS_OK. */
+ANTS_API int ants_ctx_fault(ants_ctx *ctx, int *fault);
+
 /* ------------------------------------------------------------------------ */
 /* Detector definition (Sec. 2 "detector definitions"; Sec. 5.1.1 gains)      */
 /* ------------------------------------------------------------------------ */

@@ -126,6 +126,7 @@ def lib() -> C.CDLL:
         L.ants_ctx_create.argtypes = [C.c_int, C.POINTER(_VP)]
         L.ants_ctx_destroy.argtypes = [_VP]
         L.ants_ctx_destroy.restype = None
+        L.ants_ctx_fault.argtypes = [_VP, C.POINTER(C.c_int)]
         L.ants_detector_create.argtypes = [C.c_int, _DP, _DP, C.POINTER(_VP)]
         L.ants_detector_free.argtypes = [_VP]
         L.ants_detector_free.restype = None
@@ -230,6 +231,14 @@ def ants_ctx_create(device: int = 0) -> int:
 
 def ants_ctx_destroy(ctx: int) -> None:
     lib().ants_ctx_destroy(ctx)
+
+
+def ants_ctx_fault(ctx: int) -> int:
+    """Synchronise, read and clear the device fault word (0: no kernel gave up a
+    bounded wait); raises AntsError(ANTS_E_TIMEOUT) when it was set."""
+    f = C.c_int(0)
+    _check(lib().ants_ctx_fault(ctx, C.byref(f)))
+    return f.value
 
 
 def ants_detector_create(sensor_xy, rel_gain=None) -> int:

@@ -97,6 +97,9 @@ ANTS_API int ants_ctx_create(int device, ants_ctx **out)
         e = cudaStreamCreateWithFlags(&c->stream[k], cudaStreamNonBlocking);
         if (e != cudaSuccess) { ants_ctx_destroy(c); return cuda_fail(e, "cudaStreamCreate"); }
     }
+    e = cudaMalloc(&c->d_fault, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_fault, 0, sizeof(int));
+    if (e != cudaSuccess) { ants_ctx_destroy(c); return cuda_fail(e, "fault word"); }
     *out = c;
     return ANTS_OK;
 }
@@ -123,9 +126,21 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     cudaSetDevice(ctx->device);
     free_host_buffers(ctx);
     for (int k = 0; k < 8; ++k) cudaFree(ctx->scratch[k]);
+    cudaFree(ctx->d_fault);
     for (int k = 0; k < 2; ++k)
         if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);
     delete ctx;
+}
+
+ANTS_API int ants_ctx_fault(ants_ctx *ctx, int *fault)
+{
+    begin_call();
+    if (!ctx || !fault) return fail(ANTS_E_ARG, "ants_ctx_fault: NULL argument");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ANTS_CUDA_TRY(cudaDeviceSynchronize(), "ants_ctx_fault: synchronize");
+    ANTS_CUDA_TRY(cudaMemcpy(fault, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost), "ants_ctx_fault: read");
+    ANTS_CUDA_TRY(cudaMemset(ctx->d_fault, 0, sizeof(int)), "ants_ctx_fault: clear");
+    return *fault ? fail(ANTS_E_TIMEOUT, "a device-side wait ran out of time") : ANTS_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libants translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -66,6 +67,8 @@ struct ants_ctx {
     // general device scratch slots (grown on demand by ants::ctx_scratch)
     void *scratch[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t scratch_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // device word set by a kernel whose bounded wait ran out (ants_ctx_fault)
+    int *d_fault = nullptr;
 };
 
 struct ants_detector {
@@ -103,6 +106,12 @@ void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
 int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s);
 int mlp_decode(const ants_mlp *M, const float *O, long n, float *xyz, float *E, cudaStream_t s);
 int mlp_n_in(const ants_mlp *M);
+// tcgen05 products with fused epilogues (umma.cu); B [N][K] BF16, K <= 256
+// top-K: columns ranked by value, ties by order[n] (the grid index of column n)
+int mma_topk(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const int *order, int M, int N,
+             int K, int topk, float *val, int *idx, cudaStream_t s);
+int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const float *bias, int M,
+                  int N, int K, __nv_bfloat16 *out, cudaStream_t s);
 // precision form (precision.cu)
 int check_gemm_params(const ants_lrf *lrf, const ants_gemm_params *P);
 int reconstruct_gemm_topk(ants_ctx *ctx, const ants_lrf *lrf, const ants_gemm_params &P, const float *sig, long n,

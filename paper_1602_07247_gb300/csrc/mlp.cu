@@ -33,8 +33,11 @@ struct ants_mlp {
     float *d_par = nullptr;  // FP32 master weights
     float *d_m = nullptr, *d_v = nullptr;
     int adam_t = 0;
-    // BF16 copies of W1 and W2 for tensor-core inference, refreshed on use
+    // BF16 copies of W1 [Hp][Ip] and W2 [Hp][Hp] and FP32 biases [Hp] for
+    // tensor-core inference, zero-padded to multiples of 8 (Ip, Hp); refreshed
+    // on use
     __nv_bfloat16 *d_w1b = nullptr, *d_w2b = nullptr;
+    float *d_bpad = nullptr;  // b1 [Hp], b2 [Hp]
     bool bf16_stale = true;
 };
 
@@ -244,14 +247,38 @@ __global__ void decode_outputs(const float *__restrict__ O, long n, ants_mlp_con
 
 unsigned blocks_for(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-__global__ void to_bf16(const float *__restrict__ x, size_t n, __nv_bfloat16 *__restrict__ y)
+// y[r][c] = bf16(x[r][c]) for c < cols, 0 for cols <= c < ld (rows of ld)
+__global__ void to_bf16_pad(const float *__restrict__ x, long rows, int cols, int ld, __nv_bfloat16 *__restrict__ y)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * ld) return;
+    const long r = i / ld;
+    const int c = (int)(i - r * ld);
+    y[i] = c < cols ? __float2bfloat16_rn(x[r * cols + c]) : __float2bfloat16_rn(0.0f);
 }
 
-// o[r][k] = sum_i bf16(h[r][i]) bf16(W3[k][i]) + b3[k]; one warp per row
-__global__ void output_layer(const __nv_bfloat16 *__restrict__ h, long n, int H, const float *__restrict__ W3,
+__global__ void copy_pad(const float *__restrict__ x, int n, int ld, float *__restrict__ y)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ld) y[i] = i < n ? x[i] : 0.0f;
+}
+
+// U[r][i] = s[r][i] / S_r for i < n_in, 0 up to the row stride ld
+__global__ void normalize_rows_pad(const float *__restrict__ sig, long n, int n_in, int ld, float *__restrict__ U)
+{
+    const long r = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *s = sig + r * n_in;
+    float S = 0.0f;
+    for (int i = lane; i < n_in; i += 32) S += s[i];
+    for (int o = 16; o; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+    const float inv = S > 0.0f ? 1.0f / S : 0.0f;
+    for (int i = lane; i < ld; i += 32) U[r * ld + i] = i < n_in ? s[i] * inv : 0.0f;
+}
+
+// o[r][k] = sum_i bf16(h[r][i]) bf16(W3[k][i]) + b3[k] (h rows of ld); one warp per row
+__global__ void output_layer(const __nv_bfloat16 *__restrict__ h, long n, int H, int ld, const float *__restrict__ W3,
                              const float *__restrict__ b3, float *__restrict__ O)
 {
     const long r = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -259,7 +286,7 @@ __global__ void output_layer(const __nv_bfloat16 *__restrict__ h, long n, int H,
     if (r >= n) return;
     float acc[3] = {0.0f, 0.0f, 0.0f};
     for (int i = lane; i < H; i += 32) {
-        const float hv = __bfloat162float(h[r * H + i]);
+        const float hv = __bfloat162float(h[r * ld + i]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc[k] = fmaf(hv, rbf16(W3[k * H + i]), acc[k]);
     }
@@ -382,9 +409,6 @@ constexpr int kLossBlocks = 64;
 
 }  // namespace
 
-int mma_bias_gelu(const void *A, bool a_f32, const __nv_bfloat16 *B, const float *bias, int M, int N, int K,
-                  __nv_bfloat16 *out, cudaStream_t s);
-
 // BF16 inference on the tensor cores: the same roundings as the BF16 training
 // path (operands rounded to BF16, FP32 accumulation), in fewer passes
 int mlp_forward_tc(ants_ctx *ctx, const ants_mlp *Mc, const float *sig, long n, float *O, cudaStream_t s)
@@ -392,34 +416,45 @@ int mlp_forward_tc(ants_ctx *ctx, const ants_mlp *Mc, const float *sig, long n, 
     ants_mlp *M = const_cast<ants_mlp *>(Mc);
     const Offsets o = offsets(M->n_in, M->H);
     const int H = M->H, I = M->n_in;
+    const int Hp = (H + 7) & ~7, Ip = (I + 7) & ~7;  // 16-byte rows for the tensor-core operands
+    if (Ip > 256 || Hp > 256)
+        return fail(ANTS_E_UNIMPLEMENTED, "BF16 inference: inputs and hidden width must be <= 256 (%d, %d)", I, H);
     if (!M->d_w1b) {
-        ANTS_CUDA_TRY(cudaMalloc(&M->d_w1b, (size_t)H * I * sizeof(__nv_bfloat16)), "bf16 weights");
-        ANTS_CUDA_TRY(cudaMalloc(&M->d_w2b, (size_t)H * H * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w1b, (size_t)Hp * Ip * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w2b, (size_t)Hp * Hp * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_bpad, 2 * (size_t)Hp * sizeof(float)), "padded biases");
         M->bf16_stale = true;
     }
     if (M->bf16_stale) {
-        to_bf16<<<blocks_for((long)H * I, 256), 256, 0, s>>>(M->d_par + o.W1, (size_t)H * I, M->d_w1b);
-        to_bf16<<<blocks_for((long)H * H, 256), 256, 0, s>>>(M->d_par + o.W2, (size_t)H * H, M->d_w2b);
-        count_launch(2);
+        // padded rows of W carry zero weights and zero bias, so their GELU is 0
+        to_bf16_pad<<<blocks_for((long)Hp * Ip, 256), 256, 0, s>>>(M->d_par + o.W1, H, I, Ip, M->d_w1b);
+        to_bf16_pad<<<blocks_for((long)Hp * Hp, 256), 256, 0, s>>>(M->d_par + o.W2, H, H, Hp, M->d_w2b);
+        if (Hp > H) {
+            ANTS_CUDA_TRY(cudaMemsetAsync(M->d_w1b + (size_t)H * Ip, 0, (size_t)(Hp - H) * Ip * 2, s), "pad");
+            ANTS_CUDA_TRY(cudaMemsetAsync(M->d_w2b + (size_t)H * Hp, 0, (size_t)(Hp - H) * Hp * 2, s), "pad");
+        }
+        copy_pad<<<1, 256, 0, s>>>(M->d_par + o.b1, H, Hp, M->d_bpad);
+        copy_pad<<<1, 256, 0, s>>>(M->d_par + o.b2, H, Hp, M->d_bpad + Hp);
+        count_launch(4);
         M->bf16_stale = false;
     }
     const long chunk = 1L << 17;
     const long cap = n < chunk ? n : chunk;
-    const size_t bytes = (size_t)cap * I * sizeof(float) + 2 * (size_t)cap * H * sizeof(__nv_bfloat16) + 256;
+    const size_t bytes = (size_t)cap * Ip * sizeof(float) + 2 * (size_t)cap * Hp * sizeof(__nv_bfloat16) + 256;
     unsigned char *base = (unsigned char *)ctx_scratch(ctx, 0, bytes);
     if (!base) return ANTS_E_OOM;
     float *U = (float *)base;
-    __nv_bfloat16 *H1 = (__nv_bfloat16 *)(base + (size_t)cap * I * sizeof(float));
-    __nv_bfloat16 *H2 = H1 + (size_t)cap * H;
+    __nv_bfloat16 *H1 = (__nv_bfloat16 *)(base + (size_t)cap * Ip * sizeof(float));
+    __nv_bfloat16 *H2 = H1 + (size_t)cap * Hp;
     for (long off = 0; off < n; off += chunk) {
         const long m = n - off < chunk ? n - off : chunk;
-        normalize_rows<<<blocks_for(m, 8), 256, 0, s>>>(sig + off * I, nullptr, m, I, U);
+        normalize_rows_pad<<<blocks_for(m, 8), 256, 0, s>>>(sig + off * I, m, I, Ip, U);
         count_launch();
-        int rc = mma_bias_gelu(U, true, M->d_w1b, M->d_par + o.b1, (int)m, H, I, H1, s);
+        int rc = mma_bias_gelu(ctx, U, true, M->d_w1b, M->d_bpad, (int)m, Hp, Ip, H1, s);
         if (rc != ANTS_OK) return rc;
-        rc = mma_bias_gelu(H1, false, M->d_w2b, M->d_par + o.b2, (int)m, H, H, H2, s);
+        rc = mma_bias_gelu(ctx, H1, false, M->d_w2b, M->d_bpad + Hp, (int)m, Hp, Hp, H2, s);
         if (rc != ANTS_OK) return rc;
-        output_layer<<<blocks_for(m, 8), 256, 0, s>>>(H2, m, H, M->d_par + o.W3, M->d_par + o.b3, O + off * 3);
+        output_layer<<<blocks_for(m, 8), 256, 0, s>>>(H2, m, H, Hp, M->d_par + o.W3, M->d_par + o.b3, O + off * 3);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
@@ -518,6 +553,7 @@ ANTS_API void ants_mlp_free(ants_mlp *M)
     cudaFree(M->d_v);
     cudaFree(M->d_w1b);
     cudaFree(M->d_w2b);
+    cudaFree(M->d_bpad);
     delete M;
 }
 

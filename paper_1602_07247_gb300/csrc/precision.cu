@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "bspline.cuh"
@@ -29,12 +30,14 @@ struct ants_logtable {
     float x0 = 0, y0 = 0, dx = 0, dy = 0;  // centre of cell (0, 0) and spacing
     __nv_bfloat16 *d_T = nullptr;          // [nx*ny][n_s]
     float *d_m = nullptr;                  // [n_s]
+    // the table the tensor-core scan reads: row r is grid point d_order[r],
+    // a fixed pseudo-random order (the running top-K threshold then rises
+    // after a few hundred points instead of tracking the raster order)
+    __nv_bfloat16 *d_Tp = nullptr;         // [nx*ny][n_s]
+    int *d_order = nullptr;                // [nx*ny]
 };
 
 namespace ants {
-
-int mma_topk(const void *A, bool a_f32, const __nv_bfloat16 *B, int M, int N, int K, int topk, float *val, int *idx,
-             cudaStream_t s);
 
 namespace {
 
@@ -129,6 +132,33 @@ __global__ void pick_best(long n, int K, const float *xyz_c, const float *E_c, c
 
 unsigned nb(long n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// Tp[r] = T[order[r]]
+__global__ void permute_rows(const __nv_bfloat16 *T, const int *order, long G, int n_s, __nv_bfloat16 *Tp)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G * n_s) return;
+    const long r = t / n_s;
+    Tp[t] = T[(long)order[r] * n_s + (t - r * n_s)];
+}
+
+// Fisher-Yates shuffle driven by splitmix64 (Steele, Lea and Flood 2014), fixed seed
+std::vector<int> scan_order(long G)
+{
+    std::vector<int> o((size_t)G);
+    for (long g = 0; g < G; ++g) o[(size_t)g] = (int)g;
+    uint64_t x = 0x414E545332ull;
+    for (long i = G - 1; i > 0; --i) {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const long j = (long)(z % (uint64_t)(i + 1));
+        std::swap(o[(size_t)i], o[(size_t)j]);
+    }
+    return o;
+}
+
 }  // namespace
 
 int check_gemm_params(const ants_lrf *lrf, const ants_gemm_params *P)
@@ -158,7 +188,8 @@ int reconstruct_gemm_topk(ants_ctx *ctx, const ants_lrf *lrf, const ants_gemm_pa
     const long chunk = 1L << 24;
     for (long off = 0; off < n; off += chunk) {
         const long m = n - off < chunk ? n - off : chunk;
-        int rc = mma_topk(sig + off * n_s, true, T->d_T, (int)m, (int)G, n_s, K, val + off * K, idx + off * K, s);
+        int rc = mma_topk(ctx, sig + off * n_s, true, T->d_Tp, T->d_order, (int)m, (int)G, n_s, K, val + off * K,
+                          idx + off * K, s);
         if (rc != ANTS_OK) return rc;
     }
     candidate_starts<<<nb(n, 256), 256, 0, s>>>(idx, n, K, T->nx, T->x0, T->y0, T->dx, T->dy, P.nms_cells, starts);
@@ -203,10 +234,17 @@ ANTS_API int ants_logtable_create(ants_ctx *ctx, const ants_lrf *lrf, int nx, in
     cudaError_t e = cudaMalloc(&lnp, (size_t)G * T->n_s * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&T->d_T, (size_t)G * T->n_s * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&T->d_m, (size_t)T->n_s * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&T->d_Tp, (size_t)G * T->n_s * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&T->d_order, (size_t)G * sizeof(int));
+    if (e == cudaSuccess) {
+        const std::vector<int> order = scan_order(G);
+        e = cudaMemcpy(T->d_order, order.data(), (size_t)G * sizeof(int), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) {
         table_lnp<<<nb(G, 8), 256>>>(lrf->dev, nx, ny, T->x0, T->y0, T->dx, T->dy, lnp);
         table_center<<<nb(T->n_s, 128), 128>>>(lnp, G, T->n_s, T->d_m, T->d_T);
-        count_launch(2);
+        permute_rows<<<nb(G * T->n_s, 256), 256>>>(T->d_T, T->d_order, G, T->n_s, T->d_Tp);
+        count_launch(3);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
@@ -245,8 +283,8 @@ ANTS_API int ants_logtable_topk(ants_ctx *ctx, const ants_logtable *T, const flo
     if (n_events == 0) return ANTS_OK;
     if (!signals_dev || !score_dev || !index_dev) return fail(ANTS_E_ARG, "ants_logtable_topk: NULL buffer");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
-    return mma_topk(signals_dev, true, T->d_T, (int)n_events, T->nx * T->ny, T->n_s, top_k, score_dev, index_dev,
-                    (cudaStream_t)stream);
+    return mma_topk(ctx, signals_dev, true, T->d_Tp, T->d_order, (int)n_events, T->nx * T->ny, T->n_s, top_k,
+                    score_dev, index_dev, (cudaStream_t)stream);
 }
 
 ANTS_API void ants_logtable_free(ants_logtable *T)
@@ -255,6 +293,8 @@ ANTS_API void ants_logtable_free(ants_logtable *T)
     cudaSetDevice(T->ctx->device);
     cudaFree(T->d_T);
     cudaFree(T->d_m);
+    cudaFree(T->d_Tp);
+    cudaFree(T->d_order);
     delete T;
 }
 

@@ -1,0 +1,700 @@
+// BF16 products on the fifth-generation tensor cores (tcgen05) with fused row
+// epilogues:
+//
+//   C[m][n] = sum_k A[m][k] B[n][k]     A [M][K]: FP32 (rounded to BF16 while
+//                                       it is staged) or BF16;  B [N][K] BF16
+//
+// K <= 256 and a multiple of 8; A rows 16-byte aligned.  Persistent CTAs (one
+// per SM) take 128-row bands of C ("m-tiles") in a fixed stride; every band
+// walks all of N in 256-column n-tiles.  Warp roles (14 warps):
+//   warp 0      TMA producer: B as 256 x 64 boxes (128-byte swizzle) through
+//               a 4-stage ring, re-read from L2 for every band;
+//   warp 1      allocates 512 TMEM columns; one thread issues
+//               tcgen05.mma.kind::f16 (M = 128, N = 256, K = 16) into one of
+//               two 128 x 256 FP32 accumulators;
+//   warps 2-5   stage the band's A in shared memory in the same swizzled
+//               K-major layout, one 64-wide K chunk at a time; a chunk is
+//               refilled for the next band as soon as the last MMA reading it
+//               has completed (its own full/empty mbarrier pair);
+//   warps 6-13  epilogue: tcgen05.ld of the finished accumulator while the
+//               other one fills (warp w reads TMEM lanes 32(w%4)..+31, i.e. C
+//               rows; the two groups of four warps split the columns).
+// Epilogues:
+//   EPI_TOPK       running top-K per row over all N (value desc, column asc),
+//                  written as K (score, column) pairs per row;
+//   EPI_BIAS_GELU  GELU(C + bias[n]) stored as BF16 (N a multiple of 8).
+// Every mbarrier wait is bounded in time.  A wait that runs out sets a shared
+// abort flag and the context's fault word; every role then stops, waits
+// (bounded) for its own copies and products in flight, and the block frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace ants {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4, kMaxK = 256, kMaxTop = 8;
+constexpr int kAChunks = kMaxK / kBK;
+constexpr int kThreads = 14 * 32;
+constexpr int kLoaderWarp0 = 2, kEpiWarp0 = 6;
+constexpr uint32_t kAChunkBytes = kBM * kBK * 2;  // 16 KiB
+constexpr uint32_t kBStageBytes = kBN * kBK * 2;  // 32 KiB
+constexpr uint64_t kWaitNs = 1000000000ull;       // 1 s per wait
+
+enum { EPI_TOPK = 0, EPI_BIAS_GELU = 1 };
+
+// shared-memory map (offsets from a 1024-byte aligned base)
+constexpr uint32_t kOffA = 0;
+constexpr uint32_t kOffB = kOffA + kAChunks * kAChunkBytes;
+constexpr int kChunk = 32;                                                // columns staged per candidate pass
+constexpr uint32_t kOffCand = kOffB + kStages * kBStageBytes;             // staged values [kChunk][256]
+constexpr uint32_t kOffBar = kOffCand + kChunk * 256 * 4;
+constexpr int kNumBars = 2 * kStages + 2 * kAChunks + 4 + 1 + 2;
+constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;                     // tmem base, abort flag
+constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;                     // + alignment slack
+
+struct UmmaArgs {
+    int M, N, K;
+    const void *A;
+    int topk;
+    const int *order;  // grid index of column n (top-K ranks ties by it)
+    float *top_val;
+    int *top_idx;
+    const float *bias;
+    __nv_bfloat16 *out;
+    int *fault;
+};
+
+// ---- PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait; false once this or another role has given up
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int *abort, int *fault)
+{
+    if (bar_try(b, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (true) {
+        if (bar_try(b, parity)) return true;
+        if (*abort) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            *abort = 1;
+            atomicExch(fault, 1);
+            return false;
+        }
+    }
+}
+
+// bounded wait used while draining (ignores the abort flag)
+__device__ __forceinline__ void bar_drain(uint32_t b, uint32_t parity, int *fault)
+{
+    const uint64_t t0 = now_ns();
+    while (!bar_try(b, parity))
+        if (now_ns() - t0 > kWaitNs) {
+            atomicExch(fault, 1);
+            return;
+        }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(b)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (leading offset unused for this layout; set to 16 bytes)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane (two loads, one wait)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
+          "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
+          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]),
+          "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]),
+          "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// grid index of column n; the empty-entry marker -1 ranks last
+__device__ __forceinline__ int gidx(const int *order, int n) { return n >= 0 ? __ldg(order + n) : 0x7fffffff; }
+
+// (x, grid index ox) ranks before list entry (w, column d)
+__device__ __forceinline__ bool ahead_of(float x, int ox, float w, int d, const int *order)
+{
+    return x > w || (x == w && ox < gidx(order, d));
+}
+
+// insert (x, column n) into the descending list (tv, tn); entries past the
+// k-th are kept but never reported
+__device__ __forceinline__ void reg_insert(float (&tv)[kMaxTop], int (&tn)[kMaxTop], float x, int n, const int *order)
+{
+    int p = 0;  // entries that stay ahead of x
+    bool tie = false;
+#pragma unroll
+    for (int j = 0; j < kMaxTop; ++j) {
+        p += tv[j] > x ? 1 : 0;
+        tie = tie || tv[j] == x;
+    }
+    if (tie) {  // equal values rank by grid index (loaded only then)
+        const int ox = gidx(order, n);
+        p = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxTop; ++j) p += (tv[j] > x || (tv[j] == x && gidx(order, tn[j]) < ox)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int j = kMaxTop - 1; j >= 0; --j) {
+        const float pv = j > 0 ? tv[j - 1] : x;
+        const int pn = j > 0 ? tn[j - 1] : n;
+        tv[j] = j > p ? pv : (j == p ? x : tv[j]);
+        tn[j] = j > p ? pn : (j == p ? n : tn[j]);
+    }
+}
+
+// entry k-1 of a register list, by masking (a select chain on k would be
+// turned into an indexed local-memory load)
+__device__ __forceinline__ float kth(const float (&t)[kMaxTop], int k)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxTop; ++j) r |= __float_as_uint(t[j]) & (0u - (uint32_t)(j == k - 1));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ int kth(const int (&t)[kMaxTop], int k)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxTop; ++j) r |= (uint32_t)t[j] & (0u - (uint32_t)(j == k - 1));
+    return (int)r;
+}
+
+// ---- the kernel -------------------------------------------------------------
+template <int EPI, bool A_F32>
+__global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_constant__ CUtensorMap tmB, UmmaArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                            ~static_cast<uintptr_t>(1023));
+    const uint32_t sbase = su32(smem);
+    const uint32_t sA = sbase + kOffA, sB = sbase + kOffB;
+    const uint32_t bars = sbase + kOffBar;
+    auto b_full = [&](int s) { return bars + 8u * s; };
+    auto b_empty = [&](int s) { return bars + 8u * (kStages + s); };
+    auto a_full = [&](int c) { return bars + 8u * (2 * kStages + c); };
+    auto a_empty = [&](int c) { return bars + 8u * (2 * kStages + kAChunks + c); };
+    auto acc_full = [&](int i) { return bars + 8u * (2 * kStages + 2 * kAChunks + i); };
+    auto acc_empty = [&](int i) { return bars + 8u * (2 * kStages + 2 * kAChunks + 2 + i); };
+    const uint32_t mma_done = bars + 8u * (2 * kStages + 2 * kAChunks + 4);
+    const uint32_t mrg_full = mma_done + 8u, mrg_empty = mma_done + 16u;  // top-K merge buffer hand-off
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc);
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_mt = (a.M + kBM - 1) / kBM, n_nt = (a.N + kBN - 1) / kBN;
+    const int n_kc = (a.K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(b_full(s), 1);
+            bar_init(b_empty(s), 1);
+        }
+        for (int c = 0; c < kAChunks; ++c) {
+            bar_init(a_full(c), 4 * 32);
+            bar_init(a_empty(c), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            bar_init(acc_full(i), 1);
+            bar_init(acc_empty(i), 8 * 32);
+        }
+        bar_init(mma_done, 1);
+        bar_init(mrg_full, 4 * 32);
+        bar_init(mrg_empty, 4 * 32);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0, issued = 0, issued_ph = 0;
+            bool ok = true;
+            for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x)
+                for (int nt = 0; nt < n_nt && ok; ++nt)
+                    for (int kc = 0; kc < n_kc && ok; ++kc) {
+                        ok = bar_wait(b_empty(s), ph ^ 1, abort, a.fault);
+                        if (!ok) break;
+                        bar_expect_tx(b_full(s), kBStageBytes);
+                        tma_load_2d(sB + s * kBStageBytes, &tmB, kc * kBK, nt * kBN, b_full(s));
+                        issued |= 1u << s;
+                        issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+                        if (++s == kStages) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                    }
+            // every copy issued has landed before the block may exit
+            for (int t = 0; t < kStages; ++t)
+                if (issued & (1u << t)) bar_drain(b_full(t), (issued_ph >> t) & 1, a.fault);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int s = 0, j = 0, it = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
+                for (int nt = 0; nt < n_nt && ok; ++nt, ++j) {
+                    const int ab = j & 1;
+                    const uint32_t use = (uint32_t)(j >> 1);
+                    ok = bar_wait(acc_empty(ab), (use & 1) ^ 1, abort, a.fault);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(ab * kBN);
+                    for (int kc = 0; kc < n_kc; ++kc) {
+                        if (nt == 0) {
+                            ok = bar_wait(a_full(kc), (uint32_t)(it & 1), abort, a.fault);
+                            if (!ok) break;
+                        }
+                        ok = bar_wait(b_full(s), ph, abort, a.fault);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const int ksteps = min(kBK / 16, (a.K - kc * kBK + 15) / 16);
+                        for (int ks = 0; ks < ksteps; ++ks)
+                            umma(d, sdesc(sA + kc * kAChunkBytes + ks * 32), sdesc(sB + s * kBStageBytes + ks * 32),
+                                 (kc | ks) != 0);
+                        umma_commit(b_empty(s));
+                        if (nt == n_nt - 1) umma_commit(a_empty(kc));
+                        if (++s == kStages) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                    }
+                    if (!ok) break;
+                    umma_commit(acc_full(ab));
+                }
+            }
+            // every product issued has completed before the block may exit
+            umma_commit(mma_done);
+            bar_drain(mma_done, 0, a.fault);
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarp0) {
+        // ---------------- A loaders (FP32 -> BF16, or BF16) ----------------
+        const int lt = threadIdx.x - kLoaderWarp0 * 32;  // 0..127
+        int it = 0;
+        bool ok = true;
+        for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
+            const long m0 = (long)mt * kBM;
+            for (int kc = 0; kc < n_kc && ok; ++kc) {
+                ok = bar_wait(a_empty(kc), (uint32_t)(it & 1) ^ 1, abort, a.fault);
+                if (!ok) break;
+                uint4 packed[8];
+                if (A_F32) {
+                    float4 lo[8], hi[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
+                        const long m = m0 + r;
+                        const int k = kc * kBK + c8 * 8;
+                        if (m < a.M && k < a.K) {
+                            const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(a.A) +
+                                                                               (size_t)m * a.K + k);
+                            lo[q] = __ldcs(p);
+                            hi[q] = __ldcs(p + 1);
+                        } else {
+                            lo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            hi[q] = lo[q];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(lo[q].x, lo[q].y);
+                        __nv_bfloat162 h1 = __floats2bfloat162_rn(lo[q].z, lo[q].w);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(hi[q].x, hi[q].y);
+                        __nv_bfloat162 h3 = __floats2bfloat162_rn(hi[q].z, hi[q].w);
+                        packed[q] = make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
+                                               *reinterpret_cast<uint32_t *>(&h2), *reinterpret_cast<uint32_t *>(&h3));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
+                        const long m = m0 + r;
+                        const int k = kc * kBK + c8 * 8;
+                        packed[q] = make_uint4(0u, 0u, 0u, 0u);
+                        if (m < a.M && k < a.K)
+                            packed[q] = __ldcs(reinterpret_cast<const uint4 *>(
+                                static_cast<const __nv_bfloat16 *>(a.A) + (size_t)m * a.K + k));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
+                    const uint32_t dst = sA + kc * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
+                                 "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
+                                 : "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_arrive(a_full(kc));
+            }
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int ew = warp - kEpiWarp0, grp = ew >> 2, quarter = warp & 3;
+        const int row = quarter * 32 + lane, et = ew * 32 + lane;  // et and et + 128 share a row
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        // staged values [kChunk][256]; at the end of a band the group-1 thread
+        // on row r leaves its list in its own slots (entry q: value in row q,
+        // column in row kMaxTop + q) for the group-0 thread on that row
+        float *cand = reinterpret_cast<float *>(smem + kOffCand);
+        int j = 0, it = 0;
+        bool ok = true;
+        for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
+            const long m = (long)mt * kBM + row;
+            const uint32_t par = (uint32_t)(it & 1);
+            float tv[kMaxTop];
+            int tn[kMaxTop];
+#pragma unroll
+            for (int q = 0; q < kMaxTop; ++q) {
+                tv[q] = -INFINITY;
+                tn[q] = -1;
+            }
+            float thr = -INFINITY;  // k-th value so far
+            if (EPI == EPI_TOPK && grp == 1) {
+                // group 0 has read this thread's list of the previous band
+                if (!(ok = bar_wait(mrg_empty, par ^ 1, abort, a.fault))) break;
+            }
+            for (int nt = 0; nt < n_nt; ++nt, ++j) {
+                const int ab = j & 1;
+                const uint32_t use = (uint32_t)(j >> 1);
+                ok = bar_wait(acc_full(ab), use & 1, abort, a.fault);
+                if (!ok) break;
+                tc_fence_after();
+                if (EPI == EPI_TOPK) {
+                    for (int h = 0; h < 2; ++h) {
+                        const int colh = grp * 128 + h * 64;
+                        uint32_t v[64];
+                        tmem_ld64(tl + (uint32_t)(ab * kBN + colh), v);
+                        if (h == 1) {
+                            tc_fence_before();
+                            bar_arrive(acc_empty(ab));
+                        }
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int n0 = nt * kBN + colh + b * kChunk;
+                            // candidates: values not below the k-th (ties are
+                            // ranked by grid index below)
+                            uint32_t mask = 0;
+                            if (n0 + kChunk <= a.N) {
+#pragma unroll
+                                for (int q = 0; q < kChunk; ++q)
+                                    mask |= __uint_as_float(v[b * kChunk + q]) >= thr ? (1u << q) : 0u;
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < kChunk; ++q)
+                                    mask |= (n0 + q < a.N && __uint_as_float(v[b * kChunk + q]) >= thr) ? (1u << q)
+                                                                                                       : 0u;
+                            }
+                            if (__any_sync(0xffffffffu, mask != 0)) {
+#pragma unroll
+                                for (int q = 0; q < kChunk; ++q) cand[q * 256 + et] = __uint_as_float(v[b * kChunk + q]);
+                                // the warp drains its lanes' candidates together
+                                while (__any_sync(0xffffffffu, mask != 0)) {
+                                    if (mask) {
+                                        const int q = __ffs(mask) - 1;
+                                        mask &= mask - 1;
+                                        const float x = cand[q * 256 + et];
+                                        const int n = n0 + q;
+                                        if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, kth(tn, a.topk)))) {
+                                            reg_insert(tv, tn, x, n, a.order);
+                                            thr = kth(tv, a.topk);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    for (int c = 0; c < 4; ++c) {
+                        const int col0 = grp * 128 + c * 32;
+                        uint32_t v[32];
+                        tmem_ld32(tl + (uint32_t)(ab * kBN + col0), v);
+                        if (c == 3) {
+                            tc_fence_before();
+                            bar_arrive(acc_empty(ab));
+                        }
+                        const int n0 = nt * kBN + col0;
+                        if (m >= a.M) continue;
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int n = n0 + 2 * q;
+                            const float y0 = n < a.N ? gelu_f(__uint_as_float(v[2 * q]) + __ldg(a.bias + n)) : 0.f;
+                            const float y1 =
+                                n + 1 < a.N ? gelu_f(__uint_as_float(v[2 * q + 1]) + __ldg(a.bias + n + 1)) : 0.f;
+                            __nv_bfloat162 h = __floats2bfloat162_rn(y0, y1);
+                            pk[q] = *reinterpret_cast<uint32_t *>(&h);
+                        }
+                        __nv_bfloat16 *o = a.out + (size_t)m * a.N + n0;
+                        for (int q = 0; q < 4 && 8 * q < a.N - n0; ++q)
+                            reinterpret_cast<uint4 *>(o)[q] =
+                                make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                    }
+                }
+            }
+            if (!ok) break;
+            if (EPI == EPI_TOPK) {
+                // group 0 merges the list of the group-1 thread on its row
+                if (grp == 1) {
+#pragma unroll
+                    for (int q = 0; q < kMaxTop; ++q)
+                        if (q < a.topk) {
+                            cand[q * 256 + et] = tv[q];
+                            cand[(kMaxTop + q) * 256 + et] = __int_as_float(tn[q]);
+                        }
+                    bar_arrive(mrg_full);
+                } else {
+                    ok = bar_wait(mrg_full, par, abort, a.fault);
+                    if (!ok) break;
+                    for (int q = 0; q < a.topk; ++q) {
+                        const float x = cand[q * 256 + et + 128];
+                        const int n = __float_as_int(cand[(kMaxTop + q) * 256 + et + 128]);
+                        if (n >= 0 && ahead_of(x, gidx(a.order, n), kth(tv, a.topk), kth(tn, a.topk), a.order))
+                            reg_insert(tv, tn, x, n, a.order);
+                    }
+                    bar_arrive(mrg_empty);
+                    if (m < a.M)
+#pragma unroll
+                        for (int q = 0; q < kMaxTop; ++q)
+                            if (q < a.topk) {
+                                a.top_val[(size_t)m * a.topk + q] = tv[q];
+                                a.top_idx[(size_t)m * a.topk + q] = tn[q] >= 0 ? gidx(a.order, tn[q]) : 0x7fffffff;
+                            }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// ---- host side --------------------------------------------------------------
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// B [N][K] BF16 row-major as 256-row x 64-column boxes, 128-byte swizzle,
+// zeros outside the matrix
+int encode_b(CUtensorMap *map, const __nv_bfloat16 *B, int N, int K)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return fail(ANTS_E_CUDA, "tensor core product: cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBN};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(B), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ANTS_E_INTERNAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ANTS_OK;
+}
+
+int check_shape(const void *A, const __nv_bfloat16 *B, int M, int N, int K)
+{
+    if (M < 0 || N < 1 || K < 8 || K > kMaxK || K % 8 != 0)
+        return fail(ANTS_E_SHAPE, "tensor core product: need 8 <= K <= %d, K %% 8 == 0 (K = %d, N = %d)", kMaxK, K, N);
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+        return fail(ANTS_E_ARG, "tensor core product: operands must be 16-byte aligned");
+    return ANTS_OK;
+}
+
+template <int EPI, bool AF>
+int launch(const ants_ctx *ctx, const CUtensorMap &map, const UmmaArgs &a, cudaStream_t s)
+{
+    static bool attr = false;  // per process; the attribute is per function
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(umma_tn_kernel<EPI, AF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tensor core product)");
+        attr = true;
+    }
+    const int n_mt = (a.M + kBM - 1) / kBM;
+    const int grid = n_mt < ctx->n_sm ? n_mt : ctx->n_sm;
+    umma_tn_kernel<EPI, AF><<<grid, kThreads, kSmemBytes, s>>>(map, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor core product launch");
+    count_launch();
+    return ANTS_OK;
+}
+
+}  // namespace
+
+int mma_topk(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const int *order, int M, int N,
+             int K, int topk, float *val, int *idx, cudaStream_t s)
+{
+    if (topk < 1 || topk > kMaxTop) return fail(ANTS_E_ARG, "top-K: K must be in [1, %d]", kMaxTop);
+    int rc = check_shape(A, B, M, N, K);
+    if (rc != ANTS_OK || M == 0) return rc;
+    CUtensorMap map;
+    rc = encode_b(&map, B, N, K);
+    if (rc != ANTS_OK) return rc;
+    UmmaArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.topk = topk;
+    a.order = order;
+    a.top_val = val;
+    a.top_idx = idx;
+    a.fault = ctx->d_fault;
+    return a_f32 ? launch<EPI_TOPK, true>(ctx, map, a, s) : launch<EPI_TOPK, false>(ctx, map, a, s);
+}
+
+int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const float *bias, int M,
+                  int N, int K, __nv_bfloat16 *out, cudaStream_t s)
+{
+    int rc = check_shape(A, B, M, N, K);
+    if (rc != ANTS_OK || M == 0) return rc;
+    if (N % 8 != 0 || (reinterpret_cast<uintptr_t>(out) & 15))
+        return fail(ANTS_E_SHAPE, "tensor core product: GELU output needs N %% 8 == 0 and 16-byte alignment");
+    CUtensorMap map;
+    rc = encode_b(&map, B, N, K);
+    if (rc != ANTS_OK) return rc;
+    UmmaArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.bias = bias;
+    a.out = out;
+    a.fault = ctx->d_fault;
+    return a_f32 ? launch<EPI_BIAS_GELU, true>(ctx, map, a, s) : launch<EPI_BIAS_GELU, false>(ctx, map, a, s);
+}
+
+}  // namespace ants

@@ -56,6 +56,21 @@ def test_forward_matches_oracle(env):
     assert e32 < 1e-5 and e16 < 3e-2
 
 
+def test_forward_unaligned_widths(env):
+    """19 inputs and 36 hidden units: the tensor-core operands are zero-padded
+    to 16-byte rows; one row and a ragged 130-row batch."""
+    torch, ants, ctx = env
+    M, ref = random_net(ants, ctx, 19, 36, 5)
+    for n in (1, 130):
+        sig = synth.workloads.get("hex19_radial").events(n, seed=9).signals
+        want = oracle.mlp_forward(ref, sig.astype(np.float64))
+        out = torch.empty((n, 3), device="cuda")
+        ants.ants_mlp_forward(ctx.handle, M.handle, torch.from_numpy(sig).cuda(), out, bf16=1)
+        err = np.abs(out.cpu().numpy() - want).max() / np.abs(want).max()
+        assert err < 3e-2, err
+    assert ants.ants_ctx_fault(ctx.handle) == 0
+
+
 @pytest.mark.parametrize("bf16,tol", [(0, 1e-4), (1, 3e-2)])
 def test_gradients_match_oracle(env, bf16, tol):
     torch, ants, ctx = env

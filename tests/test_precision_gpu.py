@@ -90,3 +90,58 @@ def test_precision_form_against_oracle_refines(setup16):
     rms = lambda r: float(np.sqrt(((r["xyz"][:, :2] - ev.xyz[:, :2]) ** 2).sum(1).mean()))
     print("rms precision form", rms(res), "plain", rms(full))
     assert rms(res) <= 1.05 * rms(full)
+
+
+def _check_topk(sig, T, sc, ix, k):
+    """Scores equal the FP64 product of the BF16 operands within the FP32
+    accumulation bound, lists are sorted, and no omitted column beats a kept one
+    by more than that bound."""
+    A = bf16_round(sig).astype(np.float64)
+    full = A @ T.astype(np.float64).T
+    bound = T.shape[1] * 2.0 ** -23 * (np.abs(A) @ np.abs(T.astype(np.float64)).T) + 1e-6
+    rows = np.arange(ix.shape[0])[:, None]
+    assert ix.shape[1] == k
+    assert np.all((ix >= 0) & (ix < T.shape[0]))
+    assert np.all(np.abs(sc - full[rows, ix]) <= bound[rows, ix])
+    assert np.all(np.diff(sc, axis=1) <= 0)
+    for r in range(ix.shape[0]):
+        assert len(set(ix[r].tolist())) == k
+    kth = -np.sort(-full, axis=1)[:, k - 1]
+    assert np.all(full[rows, ix] >= kth[:, None] - 2 * bound.max(axis=1)[:, None])
+
+
+@pytest.mark.parametrize("nx,ny,k,n", [(10, 10, 1, 1), (10, 10, 8, 129), (33, 31, 3, 300), (16, 16, 8, 257),
+                                       (64, 64, 5, 128)])
+def test_topk_edge_shapes_8x8(nx, ny, k, n):
+    """K = 64 sensors; grids smaller than one 256-column tile, ragged against
+    it, and exactly one tile; event counts of 1, one tile, and ragged."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    ctx = ants.Context(0)
+    w = synth.workloads.get("sipm8x8_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, _ = gpu_objects(w, L, ctx)
+    table = ants.LogTable(ctx, lrf, nx, ny)
+    T, _ = table.values()
+    assert T.shape == (nx * ny, 64)
+    ev = w.events(n, seed=90 + nx + k)
+    sc, ix = table.topk(torch.from_numpy(ev.signals).cuda(), k)
+    _check_topk(ev.signals, T, sc.cpu().numpy(), ix.cpu().numpy(), k)
+    assert ants.ants_ctx_fault(ctx.handle) == 0
+
+
+def test_topk_many_bands_16x16(setup16):
+    """More 128-row bands than SMs, so every block takes several bands in turn
+    (the A chunks are refilled while the previous band's products finish)."""
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    ev = w.events(152 * 128 * 2 + 77, seed=93)
+    sig = torch.from_numpy(ev.signals).cuda()
+    sc, ix = table.topk(sig, 8)
+    sc, ix = sc.cpu().numpy(), ix.cpu().numpy()
+    T, _ = table.values()
+    pick = np.r_[0:200, len(ev.signals) - 300:len(ev.signals)]
+    _check_topk(ev.signals[pick], T, sc[pick], ix[pick], 8)
+    # every band agrees with a launch that sees it alone (no state leaks between bands)
+    sc1, ix1 = table.topk(sig[-300:], 8)
+    assert np.array_equal(ix1.cpu().numpy(), ix[-300:]) and np.array_equal(sc1.cpu().numpy(), sc[-300:])
+    assert ants.ants_ctx_fault(ctx.handle) == 0
