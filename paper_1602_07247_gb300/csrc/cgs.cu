@@ -39,6 +39,9 @@ struct CgsArgs {
     float *xyz, *E, *logL;
     int32_t *status;
     int16_t *trace;
+    // XYZ only: separable node evaluation (sep != 0) with per-warp tables
+    // sized for at most ry_cap coefficient rows and rz_cap planes
+    int sep, ry_cap, rz_cap;
 };
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -137,19 +140,19 @@ __device__ __forceinline__ float node_score(const LrfDev &L, const float *s_sig,
     return acc - S * (log1pf(dH * inv_hc) * 1.4426950408889634f);
 }
 
-// Reconstruct event e of a (one warp; s_sig, s_ic, s_ec: 3 n_s floats of
-// this warp's shared memory).  Shared by the plain and the batched kernels.
+// Event prologue (one warp): signals into s_sig, S, the start (centroid of
+// Sec. 5.1.1 or a given start) and its checks.  Returns false, with the
+// outputs written, for an event that is not searched.
 template <int TYPE>
-__device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig, float *s_ic, float *s_ec,
-                                          int lane)
+__device__ __forceinline__ bool event_prologue(const CgsArgs &a, long e, float *s_sig, int lane, float &S, float &cx,
+                                               float &cy, float &cz)
 {
     const LrfDev &L = a.L;
     const int n_s = L.n_s;
-    const int nodes = a.n_xy * a.n_xy * a.n_z;
-    const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
     const float qnan = __int_as_float(0x7fc00000);
     const float *sg = a.sig + (e / a.row_div) * n_s;
-    float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
+    float Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
+    S = 0.0f;
     int bad = 0;
     for (int i = lane; i < n_s; i += 32) {
         float v = sg[i];
@@ -168,7 +171,7 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
     Sw = warp_sum(Sw);
     __syncwarp();
     int st = ANTS_EVT_OK;
-    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    cx = cy = cz = 0.0f;
     if (bad) st = ANTS_EVT_BAD_SIGNAL;
     else if (!(S > 0.0f)) st = ANTS_EVT_ZERO_SIGNAL;
     if (st == ANTS_EVT_OK) {
@@ -188,69 +191,71 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
         bool ok = TYPE == ANTS_LRF_RADIAL ? node_in_domain_radial(L, cx, cy) : in_box(L, cx, cy, cz);
         if (!ok) st = ANTS_EVT_OUT_OF_DOMAIN;
     }
-    if (st != ANTS_EVT_OK) {
-        if (lane == 0) {
-            a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
-            a.E[e] = qnan;
-            a.logL[e] = qnan;
-            a.status[e] = st;
-        }
-        if (a.trace)
-            for (int it = lane; it < a.iters; it += 32) a.trace[e * a.iters + it] = -1;
-        return;
+    if (st == ANTS_EVT_OK) return true;
+    if (lane == 0) {
+        a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
+        a.E[e] = qnan;
+        a.logL[e] = qnan;
+        a.status[e] = st;
     }
+    if (a.trace)
+        for (int it = lane; it < a.iters; it += 32) a.trace[e * a.iters + it] = -1;
+    return false;
+}
 
-    float sxy = a.step_xy, sz = a.step_z;
-    for (int it = 0; it < a.iters; ++it) {
-        // eta_i and H at the grid centre
-        float hc = 0.0f;
-        for (int i = lane; i < n_s; i += 32) {
-            float eta = eta_floor<TYPE>(L, i, cx, cy, cz);
-            s_ec[i] = eta;
-            s_ic[i] = __frcp_rn(eta);
-            hc += eta;
-        }
-        hc = warp_sum(hc);
-        const float inv_hc = __frcp_rn(hc);
-        __syncwarp();
-        float bestF = -INFINITY;
-        int bestk = 0x7fffffff;
-        for (int k = lane; k < nodes; k += 32) {
-            int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
-            float x = fmaf((float)(ix - c_xy), sxy, cx);
-            float y = fmaf((float)(iy - c_xy), sxy, cy);
-            float z = fmaf((float)(iz - c_z), sz, cz);
-            float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
-            if (F > bestF) {
-                bestF = F;
-                bestk = k;
-            }
-        }
-        for (int o = 16; o; o >>= 1) {
-            float F2 = __shfl_xor_sync(kFull, bestF, o);
-            int k2 = __shfl_xor_sync(kFull, bestk, o);
-            if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
-                bestF = F2;
-                bestk = k2;
-            }
-        }
-        int ix = bestk % a.n_xy, iy = (bestk / a.n_xy) % a.n_xy, iz = bestk / (a.n_xy * a.n_xy);
-        cx = fmaf((float)(ix - c_xy), sxy, cx);
-        cy = fmaf((float)(iy - c_xy), sxy, cy);
-        cz = fmaf((float)(iz - c_z), sz, cz);
-        if (a.trace && lane == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
-        sxy *= a.shrink;
-        sz *= a.shrink;
-        __syncwarp();
+// eta_i and 1/eta_i at the grid centre into s_ec, s_ic; returns 1 / H(centre)
+template <int TYPE>
+__device__ __forceinline__ float centre_values(const LrfDev &L, float *s_ic, float *s_ec, float cx, float cy,
+                                               float cz, int lane)
+{
+    float hc = 0.0f;
+    for (int i = lane; i < L.n_s; i += 32) {
+        float eta = eta_floor<TYPE>(L, i, cx, cy, cz);
+        s_ec[i] = eta;
+        s_ic[i] = __frcp_rn(eta);
+        hc += eta;
     }
+    hc = warp_sum(hc);
+    __syncwarp();
+    return __frcp_rn(hc);
+}
 
-    // energy and full Poisson log-likelihood at the result
+// warp argmax (ties to the lowest node index), then the centre moves to the
+// best node and the spacings shrink
+__device__ __forceinline__ void pick_and_move(const CgsArgs &a, long e, int it, float bestF, int bestk, float &cx,
+                                              float &cy, float &cz, float &sxy, float &sz, int lane)
+{
+    const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
+    for (int o = 16; o; o >>= 1) {
+        float F2 = __shfl_xor_sync(kFull, bestF, o);
+        int k2 = __shfl_xor_sync(kFull, bestk, o);
+        if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
+            bestF = F2;
+            bestk = k2;
+        }
+    }
+    int ix = bestk % a.n_xy, iy = (bestk / a.n_xy) % a.n_xy, iz = bestk / (a.n_xy * a.n_xy);
+    cx = fmaf((float)(ix - c_xy), sxy, cx);
+    cy = fmaf((float)(iy - c_xy), sxy, cy);
+    cz = fmaf((float)(iz - c_z), sz, cz);
+    if (a.trace && lane == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
+    sxy *= a.shrink;
+    sz *= a.shrink;
+    __syncwarp();
+}
+
+// energy and full Poisson log-likelihood at the result
+template <int TYPE>
+__device__ __forceinline__ void event_epilogue(const CgsArgs &a, long e, const float *s_sig, float S, float cx,
+                                               float cy, float cz, int lane)
+{
+    const LrfDev &L = a.L;
     float H = 0.0f;
-    for (int i = lane; i < n_s; i += 32) H += eta_floor<TYPE>(L, i, cx, cy, cz);
+    for (int i = lane; i < L.n_s; i += 32) H += eta_floor<TYPE>(L, i, cx, cy, cz);
     H = warp_sum(H);
     const float E = S / H;
     float ll = 0.0f;
-    for (int i = lane; i < n_s; i += 32) {
+    for (int i = lane; i < L.n_s; i += 32) {
         float mu = E * eta_floor<TYPE>(L, i, cx, cy, cz);
         float s = s_sig[i];
         ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
@@ -267,33 +272,296 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
     __syncwarp();
 }
 
+// Reconstruct event e of a (one warp; s_sig, s_ic, s_ec: 3 n_s floats of
+// this warp's shared memory), every node evaluated on its own.  Shared by the
+// plain and the batched kernels.
 template <int TYPE>
-__global__ void __launch_bounds__(256) cgs_plain_kernel(CgsArgs a)
+__device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig, float *s_ic, float *s_ec,
+                                          int lane)
+{
+    const LrfDev &L = a.L;
+    const int nodes = a.n_xy * a.n_xy * a.n_z;
+    const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
+    float S, cx, cy, cz;
+    if (!event_prologue<TYPE>(a, e, s_sig, lane, S, cx, cy, cz)) return;
+    float sxy = a.step_xy, sz = a.step_z;
+    for (int it = 0; it < a.iters; ++it) {
+        const float inv_hc = centre_values<TYPE>(L, s_ic, s_ec, cx, cy, cz, lane);
+        float bestF = -INFINITY;
+        int bestk = 0x7fffffff;
+        for (int k = lane; k < nodes; k += 32) {
+            int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
+            float x = fmaf((float)(ix - c_xy), sxy, cx);
+            float y = fmaf((float)(iy - c_xy), sxy, cy);
+            float z = fmaf((float)(iz - c_z), sz, cz);
+            float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
+            if (F > bestF) {
+                bestF = F;
+                bestk = k;
+            }
+        }
+        pick_and_move(a, e, it, bestF, bestk, cx, cy, cz, sxy, sz, lane);
+    }
+    event_epilogue<TYPE>(a, e, s_sig, S, cx, cy, cz, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Separable evaluation of an XYZ grid.  For sensor i the node values
+//   eta(x_j, y_k, z_l) = sum_{a,b,c} C[jz_l+c][jy_k+b][jx_j+a] wx_j,a wy_k,b wz_l,c
+// are contracted one axis at a time through per-warp shared memory:
+//   T1[zz][yy][j] = sum_a C[jz0+zz][jy0+yy][jx_j+a] wx_j,a     (x first)
+//   T2[zz][k][j]  = sum_b T1[zz][jy_k-jy0+b][j] wy_k,b          (then y)
+//   eta[l][k][j]  = sum_c T2[jz_l-jz0+c][k][j] wz_l,c           (then z)
+// over the coefficient rows jy0.. and planes jz0.. that the grid touches.
+// Once the spacing is below the knot spacing the grids touch a few rows and
+// planes, and a node costs about 12 multiply-adds instead of 64 loads and
+// multiply-adds.  Lanes own (row, x node) pairs in the first contraction and
+// (y node, x node) columns in the other two, with the z loop inside, so the
+// index arithmetic is done once per grid.  Limits: n_xy <= 7, n_z <= 8,
+// n_xy x (rows touched) <= 32 kSepQ1.
+// ---------------------------------------------------------------------------
+constexpr int kSepAxis = 15, kSepQ1 = 5, kSepQ2 = 2, kSepZ = 8;
+
+// per-warp shared memory of the separable path, after the 3 n_s floats
+struct SepSmem {
+    int t1, t2, tab;  // float offsets of T1, T2 and the axis tables
+    int total;        // floats
+    __host__ __device__ static SepSmem make(int n_xy, int n_z, int ry_cap, int rz_cap)
+    {
+        SepSmem m;
+        m.t1 = 0;
+        m.t2 = m.t1 + n_xy * ry_cap * rz_cap;
+        m.tab = m.t2 + n_xy * n_xy * rz_cap;
+        // per axis and node: 4 weights, span index, inside flag
+        m.total = m.tab + 3 * kSepAxis * 6;
+        m.total = (m.total + 3) & ~3;
+        return m;
+    }
+};
+
+// coefficient rows (or planes) a grid of n nodes, spacing s, can touch
+__host__ __device__ inline int sep_rows(int n, float s, float inv_h, int n_int)
+{
+    const int span = (int)floorf((float)(n - 1) * s * inv_h) + 2;  // distinct spans, with rounding slack
+    const int r = span + 3;
+    return r < n_int + 3 ? r : n_int + 3;
+}
+
+__device__ __forceinline__ void cgs_event_xyz_sep(const CgsArgs &a, long e, float *s_sig, float *s_ic, float *s_ec,
+                                                  float *sep, int lane)
+{
+    const LrfDev &L = a.L;
+    const int NX = a.n_xy, NZ = a.n_z, NXX = NX * NX;
+    const int nodes = NXX * NZ;
+    const int c_xy = (NX - 1) / 2, c_z = (NZ - 1) / 2;
+    const SepSmem sm = SepSmem::make(NX, NZ, a.ry_cap, a.rz_cap);
+    float *T1 = sep + sm.t1, *T2 = sep + sm.t2;
+    float *W = sep + sm.tab;                                  // [3][kSepAxis][4] weights
+    int *J = reinterpret_cast<int *>(W + 3 * kSepAxis * 4);   // [3][kSepAxis] span index
+    int *OK = J + 3 * kSepAxis;                               // [3][kSepAxis] node inside the box
+    float S, cx, cy, cz;
+    if (!event_prologue<ANTS_LRF_XYZ>(a, e, s_sig, lane, S, cx, cy, cz)) return;
+    float sxy = a.step_xy, sz = a.step_z;
+    for (int it = 0; it < a.iters; ++it) {
+        const float inv_hc = centre_values<ANTS_LRF_XYZ>(L, s_ic, s_ec, cx, cy, cz, lane);
+        // node coordinates along each axis: span, weights, inside flag
+        for (int t = lane; t < 2 * NX + NZ; t += 32) {
+            const int ax = t < NX ? 0 : (t < 2 * NX ? 1 : 2);
+            const int q = ax == 0 ? t : (ax == 1 ? t - NX : t - 2 * NX);
+            const float c0 = ax == 0 ? cx : (ax == 1 ? cy : cz);
+            const float v = ax < 2 ? fmaf((float)(q - c_xy), sxy, c0) : fmaf((float)(q - c_z), sz, c0);
+            float tt, w[4];
+            const int j = bs_span(v, L.lo[ax], L.inv_h[ax], L.n_int[ax], tt);
+            bs_weights(tt, w);
+            float *wq = W + (ax * kSepAxis + q) * 4;
+            wq[0] = w[0];
+            wq[1] = w[1];
+            wq[2] = w[2];
+            wq[3] = w[3];
+            J[ax * kSepAxis + q] = j;
+            OK[ax * kSepAxis + q] = v >= L.lo[ax] && v <= L.hi[ax];
+        }
+        __syncwarp();
+        const int jy0 = J[kSepAxis], jz0 = J[2 * kSepAxis];
+        const int Ry = J[kSepAxis + NX - 1] - jy0 + 4, Rz = J[2 * kSepAxis + NZ - 1] - jz0 + 4;
+        float bestF = -INFINITY;
+        int bestk = 0x7fffffff;
+        if (Ry > a.ry_cap || Rz > a.rz_cap || NX * Ry > 32 * kSepQ1) {
+            // the grid touches more rows than the tables hold (not expected for
+            // the caps the launcher derives): evaluate every node on its own
+            for (int k = lane; k < nodes; k += 32) {
+                int ix = k % NX, iy = (k / NX) % NX, iz = k / NXX;
+                float x = fmaf((float)(ix - c_xy), sxy, cx);
+                float y = fmaf((float)(iy - c_xy), sxy, cy);
+                float z = fmaf((float)(iz - c_z), sz, cz);
+                float F = node_score<ANTS_LRF_XYZ>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
+                if (F > bestF) {
+                    bestF = F;
+                    bestk = k;
+                }
+            }
+        } else {
+            // this lane's (row, x node) pairs of the first contraction
+            int co[kSepQ1], to[kSepQ1];
+            float wx[kSepQ1][4];
+#pragma unroll
+            for (int q = 0; q < kSepQ1; ++q) {
+                const int p = lane + 32 * q;
+                const int j = p % NX, yy = p / NX;
+                co[q] = p < NX * Ry ? yy * L.stride_y + J[j] : -1;
+                to[q] = yy * NX + j;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) wx[q][c] = W[j * 4 + c];
+            }
+            // this lane's (y node, x node) columns of the other two
+            int r2[kSepQ2];
+            float wy[kSepQ2][4];
+#pragma unroll
+            for (int q = 0; q < kSepQ2; ++q) {
+                const int p = lane + 32 * q;
+                const int j = p % NX, k = p / NX;
+                r2[q] = p < NXX ? (J[kSepAxis + k] - jy0) * NX + j : -1;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) wy[q][c] = W[(kSepAxis + (k < NX ? k : 0)) * 4 + c];
+            }
+            float acc[kSepQ2 * kSepZ], dH[kSepQ2 * kSepZ];
+#pragma unroll
+            for (int m = 0; m < kSepQ2 * kSepZ; ++m) acc[m] = dH[m] = 0.0f;
+            const int t1_plane = Ry * NX;
+            for (int i = 0; i < L.n_s; ++i) {
+                const float *C = L.coef + (size_t)i * L.n_coef + (size_t)jz0 * L.stride_z + (size_t)jy0 * L.stride_y;
+#pragma unroll
+                for (int q = 0; q < kSepQ1; ++q)
+                    if (co[q] >= 0)
+                        for (int zz = 0; zz < Rz; ++zz) {
+                            const float *c = C + zz * L.stride_z + co[q];
+                            float f = __ldg(c) * wx[q][0];
+                            f = fmaf(__ldg(c + 1), wx[q][1], f);
+                            f = fmaf(__ldg(c + 2), wx[q][2], f);
+                            f = fmaf(__ldg(c + 3), wx[q][3], f);
+                            T1[zz * t1_plane + to[q]] = f;
+                        }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < kSepQ2; ++q)
+                    if (r2[q] >= 0)
+                        for (int zz = 0; zz < Rz; ++zz) {
+                            const float *c = T1 + zz * t1_plane + r2[q];
+                            float f = c[0] * wy[q][0];
+                            f = fmaf(c[NX], wy[q][1], f);
+                            f = fmaf(c[2 * NX], wy[q][2], f);
+                            f = fmaf(c[3 * NX], wy[q][3], f);
+                            T2[zz * NXX + lane + 32 * q] = f;
+                        }
+                __syncwarp();
+                const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
+#pragma unroll
+                for (int iz = 0; iz < kSepZ; ++iz) {
+                    if (iz < NZ) {
+                        const float *wz = W + (2 * kSepAxis + iz) * 4;
+                        const float *c = T2 + (J[2 * kSepAxis + iz] - jz0) * NXX;
+#pragma unroll
+                        for (int q = 0; q < kSepQ2; ++q)
+                            if (r2[q] >= 0) {
+                                const float *cq = c + lane + 32 * q;
+                                float f = cq[0] * wz[0];
+                                f = fmaf(cq[NXX], wz[1], f);
+                                f = fmaf(cq[2 * NXX], wz[2], f);
+                                f = fmaf(cq[3 * NXX], wz[3], f);
+                                const float eta = fmaxf(f, kEtaFloor);
+                                acc[q * kSepZ + iz] = fmaf(si, __log2f(eta * ici), acc[q * kSepZ + iz]);
+                                dH[q * kSepZ + iz] += eta - eci;
+                            }
+                    }
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int iz = 0; iz < kSepZ; ++iz)
+#pragma unroll
+                for (int q = 0; q < kSepQ2; ++q) {
+                    const int p = lane + 32 * q;
+                    if (iz < NZ && p < NXX) {
+                        const int k = iz * NXX + p, ix = p % NX, iy = p / NX;
+                        const bool inside = OK[ix] && OK[kSepAxis + iy] && OK[2 * kSepAxis + iz];
+                        const float F = inside ? acc[q * kSepZ + iz] -
+                                                     S * (log1pf(dH[q * kSepZ + iz] * inv_hc) * 1.4426950408889634f)
+                                               : -INFINITY;
+                        if (F > bestF || (F == bestF && k < bestk)) {
+                            bestF = F;
+                            bestk = k;
+                        }
+                    }
+                }
+        }
+        pick_and_move(a, e, it, bestF, bestk, cx, cy, cz, sxy, sz, lane);
+    }
+    event_epilogue<ANTS_LRF_XYZ>(a, e, s_sig, S, cx, cy, cz, lane);
+}
+
+// floats of shared memory one warp needs for an item
+__host__ inline int warp_smem_floats(const CgsArgs &a)
+{
+    int f = 3 * a.L.n_s;
+    f = (f + 3) & ~3;
+    if (a.sep) f += SepSmem::make(a.n_xy, a.n_z, a.ry_cap, a.rz_cap).total;
+    return f;
+}
+
+// enable the separable XYZ path when the grid fits it
+__host__ inline void setup_sep(CgsArgs &a)
+{
+    a.sep = 0;
+    a.ry_cap = a.rz_cap = 0;
+    if (a.L.type != ANTS_LRF_XYZ || a.n_xy * a.n_xy > 32 * kSepQ2 || a.n_z > kSepZ) return;
+    const int ry = sep_rows(a.n_xy, a.step_xy, a.L.inv_h[1], a.L.n_int[1]);
+    if (a.n_xy * ry > 32 * kSepQ1) return;
+    a.sep = 1;
+    a.ry_cap = ry;
+    a.rz_cap = sep_rows(a.n_z, a.step_z, a.L.inv_h[2], a.L.n_int[2]);
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(256) cgs_plain_kernel(CgsArgs a, int warp_floats)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int n_s = a.L.n_s;
-    float *s_sig = smem + (size_t)wib * 3 * n_s;
+    float *s_sig = smem + (size_t)wib * warp_floats;
     float *s_ic = s_sig + n_s;  // 1 / eta_i(centre)
     float *s_ec = s_ic + n_s;   // eta_i(centre)
-    for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb)
-        cgs_event<TYPE>(a, e, s_sig, s_ic, s_ec, lane);
+    float *sep = s_sig + ((3 * n_s + 3) & ~3);
+    for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb) {
+        if (TYPE == ANTS_LRF_XYZ && a.sep)
+            cgs_event_xyz_sep(a, e, s_sig, s_ic, s_ec, sep, lane);
+        else
+            cgs_event<TYPE>(a, e, s_sig, s_ic, s_ec, lane);
+    }
 }
 
 template <int TYPE>
-int launch_typed(const ants_ctx *ctx, const CgsArgs &a, cudaStream_t stream)
+int launch_typed(const ants_ctx *ctx, CgsArgs a, cudaStream_t stream, bool allow_sep = true)
 {
-    const int threads = 256, wpb = threads / 32;
-    size_t smem = (size_t)wpb * 3 * a.L.n_s * sizeof(float);
+    if (allow_sep) setup_sep(a);
+    else a.sep = 0;
+    const int warp_floats = warp_smem_floats(a);
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * warp_floats * sizeof(float) > ctx->smem_optin) wpb /= 2;
+    if ((size_t)wpb * warp_floats * sizeof(float) > ctx->smem_optin && a.sep) {
+        return launch_typed<TYPE>(ctx, a, stream, false);  // tables too large: per-node evaluation
+    }
+    const int threads = 32 * wpb;
+    size_t smem = (size_t)wpb * warp_floats * sizeof(float);
+    if (smem > ctx->smem_optin) return fail(ANTS_E_SHAPE, "cgs: %d sensors need too much shared memory", a.L.n_s);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(cgs_plain_kernel<TYPE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_plain)");
     }
     long blocks = (a.n_e + wpb - 1) / wpb;
-    long cap = (long)ctx->n_sm * 8;
+    long cap = (long)ctx->n_sm * (64 / wpb);
     if (blocks > cap) blocks = cap;
-    cgs_plain_kernel<TYPE><<<(unsigned)blocks, threads, smem, stream>>>(a);
+    cgs_plain_kernel<TYPE><<<(unsigned)blocks, threads, smem, stream>>>(a, warp_floats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cgs_plain_kernel launch");
     count_launch();
@@ -376,13 +644,11 @@ struct BatchUnit {
 // reconstruct their events with the per-event search of the unit's detector.
 __global__ void __launch_bounds__(256) cgs_batched_kernel(const CgsArgs *__restrict__ items,
                                                           const BatchUnit *__restrict__ units, int n_units,
-                                                          int *__restrict__ counter, int max_ns)
+                                                          int *__restrict__ counter, int warp_floats)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *s_sig = smem + (size_t)wib * 3 * max_ns;
-    float *s_ic = s_sig + max_ns;
-    float *s_ec = s_ic + max_ns;
+    float *base = smem + (size_t)wib * warp_floats;
     for (;;) {
         int u = 0;
         if (lane == 0) u = atomicAdd(counter, 1);
@@ -391,6 +657,9 @@ __global__ void __launch_bounds__(256) cgs_batched_kernel(const CgsArgs *__restr
         const BatchUnit U = units[u];
         const CgsArgs a = items[U.item];
         const long end = U.first + U.count;
+        const int n_s = a.L.n_s;
+        float *s_sig = base, *s_ic = base + n_s, *s_ec = base + 2 * n_s;
+        float *sep = base + ((3 * n_s + 3) & ~3);
         switch (a.L.type) {
         case ANTS_LRF_RADIAL:
             for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_RADIAL>(a, e, s_sig, s_ic, s_ec, lane);
@@ -399,7 +668,10 @@ __global__ void __launch_bounds__(256) cgs_batched_kernel(const CgsArgs *__restr
             for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_XY>(a, e, s_sig, s_ic, s_ec, lane);
             break;
         default:
-            for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_XYZ>(a, e, s_sig, s_ic, s_ec, lane);
+            if (a.sep)
+                for (long e = U.first; e < end; ++e) cgs_event_xyz_sep(a, e, s_sig, s_ic, s_ec, sep, lane);
+            else
+                for (long e = U.first; e < end; ++e) cgs_event<ANTS_LRF_XYZ>(a, e, s_sig, s_ic, s_ec, lane);
             break;
         }
     }
@@ -415,7 +687,7 @@ struct ants_batch_plan {
     ants::CgsArgs *d_items = nullptr;
     ants::BatchUnit *d_units = nullptr;
     int *d_counter = nullptr;
-    int n_units = 0, max_ns = 0;
+    int n_units = 0, warp_floats = 0;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -448,7 +720,7 @@ int build_plan(ants_batch_plan *P, long event_cap)
     std::vector<CgsArgs> args(n_items);
     std::vector<BatchUnit> units;
     std::vector<double> cost;
-    P->max_ns = 1;
+    P->warp_floats = 4;
     for (int k = 0; k < n_items; ++k) {
         const ants_batch_item &it = P->items[k];
         CgsArgs &a = args[k];
@@ -469,7 +741,8 @@ int build_plan(ants_batch_plan *P, long event_cap)
         a.logL = it.logL_dev;
         a.status = it.status_dev;
         a.trace = it.trace_dev;
-        P->max_ns = std::max(P->max_ns, it.lrf->n_s);
+        setup_sep(a);
+        P->warp_floats = std::max(P->warp_floats, warp_smem_floats(a));
         const long n = event_cap > 0 ? std::min(event_cap, it.n_events) : it.n_events;
         const double per_event = (double)a.n_xy * a.n_xy * a.n_z * a.iters * it.lrf->n_s;
         for (long f = 0; f < n; f += P->cfg.unit_events) {
@@ -493,7 +766,10 @@ int build_plan(ants_batch_plan *P, long event_cap)
         ANTS_CUDA_TRY(cudaMemcpy(P->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice),
                       "upload");
     const int threads = 32 * P->cfg.warps_per_block;
-    const size_t smem = (size_t)P->cfg.warps_per_block * 3 * P->max_ns * sizeof(float);
+    const size_t smem = (size_t)P->cfg.warps_per_block * P->warp_floats * sizeof(float);
+    if (smem > ctx->smem_optin)
+        return fail(ANTS_E_SHAPE, "batch: %d warps of %d floats exceed the shared memory of a block",
+                    P->cfg.warps_per_block, P->warp_floats);
     ANTS_CUDA_TRY(cudaFuncSetAttribute(cgs_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "cudaFuncSetAttribute(batched)");
     const unsigned blocks = (unsigned)(ctx->n_sm * P->cfg.blocks_per_sm);
@@ -502,7 +778,7 @@ int build_plan(ants_batch_plan *P, long event_cap)
     ANTS_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaMemsetAsync(P->d_counter, 0, sizeof(int), P->cap);
     cgs_batched_kernel<<<blocks, threads, smem, P->cap>>>(P->d_items, P->d_units, P->n_units, P->d_counter,
-                                                         P->max_ns);
+                                                         P->warp_floats);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamEndCapture(P->cap, &P->graph);
     if (e1 != cudaSuccess) return cuda_fail(e1, "batched launch (capture)");

@@ -236,3 +236,19 @@ def test_cgs_xyz_parity(torch_cuda, ctx):
     print(stats)
     d = np.abs(gpu["xyz"] - ev.xyz)
     print("median |dx|, |dz| vs truth", np.median(d[:, 0]), np.median(d[:, 2]))
+
+
+@pytest.mark.parametrize("n_xy,n_z,iters,step_xy,step_z", [
+    (7, 5, 5, 4.0, 5.0),    # separable path, the workload's grid
+    (5, 3, 6, 12.0, 10.0),  # separable, first grids wider than the whole lattice
+    (7, 1, 4, 3.0, 0.0),    # separable with a single z plane (z stays at z0)
+    (9, 5, 4, 3.0, 4.0),    # 405 nodes: per-node evaluation
+])
+def test_cgs_xyz_grids(torch_cuda, ctx, n_xy, n_z, iters, step_xy, step_z):
+    """XYZ searches through both evaluation paths against the oracle."""
+    w = synth.workloads.get("sipm4x4_xyz").with_(n_xy=n_xy, n_z=n_z, iters=iters, step_xy=step_xy, step_z=step_z)
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(157, seed=11 + n_xy)
+    gpu = run_gpu(torch_cuda, ctx, lrf, p, ev.signals)
+    print(compare(w, L, ev.signals, gpu))
