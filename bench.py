@@ -210,6 +210,27 @@ def forms_comparison(args, ants, torch, ctx, stream):
     for k in ("learned", "precision"):
         out[k]["speedup_vs_plain"] = out[k]["events_per_s"] / out["plain"]["events_per_s"]
         out[k]["rms_ratio_vs_plain"] = out[k]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
+    # the precision form's tensor-core scan on its own (tcgen05 product + top-8)
+    sc = torch.empty((n, 8), device="cuda")
+    ix = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        ants.ants_logtable_topk(ctx.handle, table.handle, sig, 8, sc, ix, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.forms_steps):
+        ants.ants_logtable_topk(ctx.handle, table.handle, sig, 8, sc, ix, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / args.forms_steps
+    flop = 2.0 * n * 64 * 64 * w.n_sensors
+    pk, pk_kind = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    out["precision"]["scan_roofline"] = {
+        "kernel": "umma_tn_kernel<TOPK> (tcgen05 BF16 product, fused top-8)", "bound": "tensor",
+        "achieved": flop / dt / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": flop / dt / 1e12 / peak,
+        "ms": 1e3 * dt, "flop_per_event": 2 * 64 * 64 * w.n_sensors,
+        "peak_kind": f"{pk_kind} bf16 burst (cuBLAS 8192^3)"}
     return {"workload": f"{w.name}: 256 sensors, XY LRF 32x32, {n} events; plain {w.n_xy}x{w.n_xy}x{w.iters} vs "
                         f"MLP 256-256-256-3 (BF16, trained on the GPU on {args.train_events} events, "
                         f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile; precision form: "

@@ -6,9 +6,9 @@
 //
 // K <= 256 and a multiple of 8; A rows 16-byte aligned.  Persistent CTAs (one
 // per SM) take 128-row bands of C ("m-tiles") in a fixed stride; every band
-// walks all of N in 256-column n-tiles.  Warp roles (14 warps):
+// walks all of N in 256-column n-tiles.  Warp roles (22 warps):
 //   warp 0      TMA producer: B as 256 x 64 boxes (128-byte swizzle) through
-//               a 4-stage ring, re-read from L2 for every band;
+//               a 3-stage ring, re-read from L2 for every band;
 //   warp 1      allocates 512 TMEM columns; one thread issues
 //               tcgen05.mma.kind::f16 (M = 128, N = 256, K = 16) into one of
 //               two 128 x 256 FP32 accumulators;
@@ -16,9 +16,9 @@
 //               K-major layout, one 64-wide K chunk at a time; a chunk is
 //               refilled for the next band as soon as the last MMA reading it
 //               has completed (its own full/empty mbarrier pair);
-//   warps 6-13  epilogue: tcgen05.ld of the finished accumulator while the
+//   warps 6-21  epilogue: tcgen05.ld of the finished accumulator while the
 //               other one fills (warp w reads TMEM lanes 32(w%4)..+31, i.e. C
-//               rows; the two groups of four warps split the columns).
+//               rows; four groups of four warps take 64 columns each).
 // Epilogues:
 //   EPI_TOPK       running top-K per row over all N (value desc, column asc),
 //                  written as K (score, column) pairs per row;
@@ -36,10 +36,12 @@ namespace ants {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4, kMaxK = 256, kMaxTop = 8;
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 3, kMaxK = 256, kMaxTop = 8;
 constexpr int kAChunks = kMaxK / kBK;
-constexpr int kThreads = 14 * 32;
-constexpr int kLoaderWarp0 = 2, kEpiWarp0 = 6;
+constexpr int kLoaderWarp0 = 2, kEpiWarp0 = 6, kEpiWarps = 16;
+constexpr int kEpiGroups = kEpiWarps / 4, kGroupCols = kBN / kEpiGroups;  // 4 groups of 64 columns
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr uint32_t kAChunkBytes = kBM * kBK * 2;  // 16 KiB
 constexpr uint32_t kBStageBytes = kBN * kBK * 2;  // 32 KiB
 constexpr uint64_t kWaitNs = 1000000000ull;       // 1 s per wait
@@ -50,8 +52,8 @@ enum { EPI_TOPK = 0, EPI_BIAS_GELU = 1 };
 constexpr uint32_t kOffA = 0;
 constexpr uint32_t kOffB = kOffA + kAChunks * kAChunkBytes;
 constexpr int kChunk = 32;                                                // columns staged per candidate pass
-constexpr uint32_t kOffCand = kOffB + kStages * kBStageBytes;             // staged values [kChunk][256]
-constexpr uint32_t kOffBar = kOffCand + kChunk * 256 * 4;
+constexpr uint32_t kOffCand = kOffB + kStages * kBStageBytes;             // staged values [kChunk][kEpiThreads]
+constexpr uint32_t kOffBar = kOffCand + kChunk * kEpiThreads * 4;
 constexpr int kNumBars = 2 * kStages + 2 * kAChunks + 4 + 1 + 2;
 constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;                     // tmem base, abort flag
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;                     // + alignment slack
@@ -184,28 +186,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 64 consecutive FP32 columns of this thread's TMEM lane (two loads, one wait)
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-          "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
-          "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
-          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]),
-          "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]),
-          "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-        : "r"(taddr), "r"(taddr + 32u)
-        : "memory");
-}
-
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
 // grid index of column n; the empty-entry marker -1 ranks last
@@ -297,11 +277,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
         }
         for (int i = 0; i < 2; ++i) {
             bar_init(acc_full(i), 1);
-            bar_init(acc_empty(i), 8 * 32);
+            bar_init(acc_empty(i), kEpiThreads);
         }
         bar_init(mma_done, 1);
-        bar_init(mrg_full, 4 * 32);
-        bar_init(mrg_empty, 4 * 32);
+        bar_init(mrg_full, (kEpiGroups - 1) * 128);
+        bar_init(mrg_empty, 128);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -392,52 +372,55 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
             for (int kc = 0; kc < n_kc && ok; ++kc) {
                 ok = bar_wait(a_empty(kc), (uint32_t)(it & 1) ^ 1, abort, a.fault);
                 if (!ok) break;
-                uint4 packed[8];
-                if (A_F32) {
-                    float4 lo[8], hi[8];
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half) {
+                    uint4 packed[4];
+                    if (A_F32) {
+                        float4 lo[4], hi[4];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
-                        const long m = m0 + r;
-                        const int k = kc * kBK + c8 * 8;
-                        if (m < a.M && k < a.K) {
-                            const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(a.A) +
-                                                                               (size_t)m * a.K + k);
-                            lo[q] = __ldcs(p);
-                            hi[q] = __ldcs(p + 1);
-                        } else {
-                            lo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            hi[q] = lo[q];
+                        for (int q = 0; q < 4; ++q) {
+                            const int item = lt + 128 * (4 * half + q), r = item >> 3, c8 = item & 7;
+                            const long m = m0 + r;
+                            const int k = kc * kBK + c8 * 8;
+                            if (m < a.M && k < a.K) {
+                                const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(a.A) +
+                                                                                   (size_t)m * a.K + k);
+                                lo[q] = __ldcs(p);
+                                hi[q] = __ldcs(p + 1);
+                            } else {
+                                lo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                hi[q] = lo[q];
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            __nv_bfloat162 h0 = __floats2bfloat162_rn(lo[q].x, lo[q].y);
+                            __nv_bfloat162 h1 = __floats2bfloat162_rn(lo[q].z, lo[q].w);
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(hi[q].x, hi[q].y);
+                            __nv_bfloat162 h3 = __floats2bfloat162_rn(hi[q].z, hi[q].w);
+                            packed[q] = make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
+                                                   *reinterpret_cast<uint32_t *>(&h2), *reinterpret_cast<uint32_t *>(&h3));
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int item = lt + 128 * (4 * half + q), r = item >> 3, c8 = item & 7;
+                            const long m = m0 + r;
+                            const int k = kc * kBK + c8 * 8;
+                            packed[q] = make_uint4(0u, 0u, 0u, 0u);
+                            if (m < a.M && k < a.K)
+                                packed[q] = __ldcs(reinterpret_cast<const uint4 *>(
+                                    static_cast<const __nv_bfloat16 *>(a.A) + (size_t)m * a.K + k));
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        __nv_bfloat162 h0 = __floats2bfloat162_rn(lo[q].x, lo[q].y);
-                        __nv_bfloat162 h1 = __floats2bfloat162_rn(lo[q].z, lo[q].w);
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(hi[q].x, hi[q].y);
-                        __nv_bfloat162 h3 = __floats2bfloat162_rn(hi[q].z, hi[q].w);
-                        packed[q] = make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
-                                               *reinterpret_cast<uint32_t *>(&h2), *reinterpret_cast<uint32_t *>(&h3));
+                    for (int q = 0; q < 4; ++q) {
+                        const int item = lt + 128 * (4 * half + q), r = item >> 3, c8 = item & 7;
+                        const uint32_t dst = sA + kc * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
+                                     "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
+                                     : "memory");
                     }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
-                        const long m = m0 + r;
-                        const int k = kc * kBK + c8 * 8;
-                        packed[q] = make_uint4(0u, 0u, 0u, 0u);
-                        if (m < a.M && k < a.K)
-                            packed[q] = __ldcs(reinterpret_cast<const uint4 *>(
-                                static_cast<const __nv_bfloat16 *>(a.A) + (size_t)m * a.K + k));
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int item = lt + 128 * q, r = item >> 3, c8 = item & 7;
-                    const uint32_t dst = sA + kc * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
-                                 "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
-                                 : "memory");
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 bar_arrive(a_full(kc));
@@ -446,11 +429,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
     } else {
         // ---------------- epilogue ----------------
         const int ew = warp - kEpiWarp0, grp = ew >> 2, quarter = warp & 3;
-        const int row = quarter * 32 + lane, et = ew * 32 + lane;  // et and et + 128 share a row
+        const int row = quarter * 32 + lane, et = ew * 32 + lane;  // et mod 128 names the row's slot
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        // staged values [kChunk][256]; at the end of a band the group-1 thread
-        // on row r leaves its list in its own slots (entry q: value in row q,
-        // column in row kMaxTop + q) for the group-0 thread on that row
+        // staged values [kChunk][kEpiThreads]; at the end of a band the threads
+        // of groups 1-3 leave their lists in their own slots (entry q: value in
+        // row q, column in row kMaxTop + q) for the group-0 thread on that row
         float *cand = reinterpret_cast<float *>(smem + kOffCand);
         int j = 0, it = 0;
         bool ok = true;
@@ -465,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                 tn[q] = -1;
             }
             float thr = -INFINITY;  // k-th value so far
-            if (EPI == EPI_TOPK && grp == 1) {
+            if (EPI == EPI_TOPK && grp > 0) {
                 // group 0 has read this thread's list of the previous band
                 if (!(ok = bar_wait(mrg_empty, par ^ 1, abort, a.fault))) break;
             }
@@ -475,61 +458,49 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                 ok = bar_wait(acc_full(ab), use & 1, abort, a.fault);
                 if (!ok) break;
                 tc_fence_after();
-                if (EPI == EPI_TOPK) {
-                    for (int h = 0; h < 2; ++h) {
-                        const int colh = grp * 128 + h * 64;
-                        uint32_t v[64];
-                        tmem_ld64(tl + (uint32_t)(ab * kBN + colh), v);
-                        if (h == 1) {
-                            tc_fence_before();
-                            bar_arrive(acc_empty(ab));
+#pragma unroll 1
+                for (int h = 0; h < kGroupCols / 32; ++h) {
+                    const int col0 = grp * kGroupCols + h * 32;
+                    uint32_t v[32];
+                    tmem_ld32(tl + (uint32_t)(ab * kBN + col0), v);
+                    if (h == kGroupCols / 32 - 1) {
+                        tc_fence_before();
+                        bar_arrive(acc_empty(ab));
+                    }
+                    const int n0 = nt * kBN + col0;
+                    if (EPI == EPI_TOPK) {
+                        // candidates: values not below the k-th (ties are ranked
+                        // by grid index below)
+                        uint32_t mask = 0;
+                        if (n0 + 32 <= a.N) {
+#pragma unroll
+                            for (int q = 0; q < 32; ++q)
+                                asm("{ .reg .pred p; setp.ge.f32 p, %1, %2; @p or.b32 %0, %0, %3; }"
+                                    : "+r"(mask)
+                                    : "f"(__uint_as_float(v[q])), "f"(thr), "r"(1u << q));
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 32; ++q)
+                                mask |= (n0 + q < a.N && __uint_as_float(v[q]) >= thr) ? (1u << q) : 0u;
                         }
+                        if (__any_sync(0xffffffffu, mask != 0)) {
 #pragma unroll
-                        for (int b = 0; b < 2; ++b) {
-                            const int n0 = nt * kBN + colh + b * kChunk;
-                            // candidates: values not below the k-th (ties are
-                            // ranked by grid index below)
-                            uint32_t mask = 0;
-                            if (n0 + kChunk <= a.N) {
-#pragma unroll
-                                for (int q = 0; q < kChunk; ++q)
-                                    mask |= __uint_as_float(v[b * kChunk + q]) >= thr ? (1u << q) : 0u;
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < kChunk; ++q)
-                                    mask |= (n0 + q < a.N && __uint_as_float(v[b * kChunk + q]) >= thr) ? (1u << q)
-                                                                                                       : 0u;
-                            }
-                            if (__any_sync(0xffffffffu, mask != 0)) {
-#pragma unroll
-                                for (int q = 0; q < kChunk; ++q) cand[q * 256 + et] = __uint_as_float(v[b * kChunk + q]);
-                                // the warp drains its lanes' candidates together
-                                while (__any_sync(0xffffffffu, mask != 0)) {
-                                    if (mask) {
-                                        const int q = __ffs(mask) - 1;
-                                        mask &= mask - 1;
-                                        const float x = cand[q * 256 + et];
-                                        const int n = n0 + q;
-                                        if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, kth(tn, a.topk)))) {
-                                            reg_insert(tv, tn, x, n, a.order);
-                                            thr = kth(tv, a.topk);
-                                        }
+                            for (int q = 0; q < 32; ++q) cand[q * kEpiThreads + et] = __uint_as_float(v[q]);
+                            // the warp drains its lanes' candidates together
+                            while (__any_sync(0xffffffffu, mask != 0)) {
+                                if (mask) {
+                                    const int q = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    const float x = cand[q * kEpiThreads + et];
+                                    const int n = n0 + q;
+                                    if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, kth(tn, a.topk)))) {
+                                        reg_insert(tv, tn, x, n, a.order);
+                                        thr = kth(tv, a.topk);
                                     }
                                 }
                             }
                         }
-                    }
-                } else {
-                    for (int c = 0; c < 4; ++c) {
-                        const int col0 = grp * 128 + c * 32;
-                        uint32_t v[32];
-                        tmem_ld32(tl + (uint32_t)(ab * kBN + col0), v);
-                        if (c == 3) {
-                            tc_fence_before();
-                            bar_arrive(acc_empty(ab));
-                        }
-                        const int n0 = nt * kBN + col0;
-                        if (m >= a.M) continue;
+                    } else if (m < a.M) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
@@ -537,8 +508,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                             const float y0 = n < a.N ? gelu_f(__uint_as_float(v[2 * q]) + __ldg(a.bias + n)) : 0.f;
                             const float y1 =
                                 n + 1 < a.N ? gelu_f(__uint_as_float(v[2 * q + 1]) + __ldg(a.bias + n + 1)) : 0.f;
-                            __nv_bfloat162 h = __floats2bfloat162_rn(y0, y1);
-                            pk[q] = *reinterpret_cast<uint32_t *>(&h);
+                            __nv_bfloat162 hh = __floats2bfloat162_rn(y0, y1);
+                            pk[q] = *reinterpret_cast<uint32_t *>(&hh);
                         }
                         __nv_bfloat16 *o = a.out + (size_t)m * a.N + n0;
                         for (int q = 0; q < 4 && 8 * q < a.N - n0; ++q)
@@ -549,24 +520,25 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
             }
             if (!ok) break;
             if (EPI == EPI_TOPK) {
-                // group 0 merges the list of the group-1 thread on its row
-                if (grp == 1) {
+                // group 0 merges the lists of the other groups' threads on its row
+                if (grp > 0) {
 #pragma unroll
                     for (int q = 0; q < kMaxTop; ++q)
                         if (q < a.topk) {
-                            cand[q * 256 + et] = tv[q];
-                            cand[(kMaxTop + q) * 256 + et] = __int_as_float(tn[q]);
+                            cand[q * kEpiThreads + et] = tv[q];
+                            cand[(kMaxTop + q) * kEpiThreads + et] = __int_as_float(tn[q]);
                         }
                     bar_arrive(mrg_full);
                 } else {
                     ok = bar_wait(mrg_full, par, abort, a.fault);
                     if (!ok) break;
-                    for (int q = 0; q < a.topk; ++q) {
-                        const float x = cand[q * 256 + et + 128];
-                        const int n = __float_as_int(cand[(kMaxTop + q) * 256 + et + 128]);
-                        if (n >= 0 && ahead_of(x, gidx(a.order, n), kth(tv, a.topk), kth(tn, a.topk), a.order))
-                            reg_insert(tv, tn, x, n, a.order);
-                    }
+                    for (int g = 1; g < kEpiGroups; ++g)
+                        for (int q = 0; q < a.topk; ++q) {
+                            const float x = cand[q * kEpiThreads + et + 128 * g];
+                            const int n = __float_as_int(cand[(kMaxTop + q) * kEpiThreads + et + 128 * g]);
+                            if (n >= 0 && ahead_of(x, gidx(a.order, n), kth(tv, a.topk), kth(tn, a.topk), a.order))
+                                reg_insert(tv, tn, x, n, a.order);
+                        }
                     bar_arrive(mrg_empty);
                     if (m < a.M)
 #pragma unroll
