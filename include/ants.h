@@ -82,7 +82,9 @@ typedef enum {
 } ants_method;
 
 /* Signal element types. */
-typedef enum { ANTS_F32 = 0 } ants_dtype;
+/* Element type of signal arrays: FP32, or FP16 (IEEE binary16; widened to
+ * FP32 on the device before the search, exactly). */
+typedef enum { ANTS_F32 = 0, ANTS_F16 = 1 } ants_dtype;
 
 typedef struct ants_ctx ants_ctx;
 typedef struct ants_detector ants_detector;
@@ -293,7 +295,9 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf);
  *     ants_mlp_seeded_params* (no start_xyz_dev; trace_dev then records the
  *     refine grids).
  *   signals_dev: [n_events][n_sensors] row-major, element type signal_dtype
- *     (ANTS_F32); n_sensors must equal the LRF's.
+ *     (ANTS_F32, or ANTS_F16: widened to FP32 in library-owned device
+ *     chunks of up to 2^20 events, so the results equal those of the FP32
+ *     values); n_sensors must equal the LRF's.
  *   start_xyz_dev: nullable [n_events][3] FP32 start positions; NULL = the
  *     centroid (Sec. 5.1.1) clamped into the XY domain of an XY/XYZ LRF,
  *     with z = params->z0 (Sec. 5.1.2.1 start options).

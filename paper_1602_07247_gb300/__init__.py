@@ -30,6 +30,7 @@ ANTS_CGS_PLAIN = 0
 ANTS_GEMM_TOPK = 1
 ANTS_MLP_SEEDED = 2
 ANTS_F32 = 0
+ANTS_F16 = 1
 ANTS_NOALLOC_STAGE_BYTES = 33554432
 
 _STATUS_NAMES = {0: "ANTS_OK", -1: "ANTS_E_ARG", -2: "ANTS_E_CUDA", -3: "ANTS_E_OOM", -4: "ANTS_E_LRF",
@@ -654,7 +655,7 @@ class Result:
 
 def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=None, want_trace=False,
                 stream=None, method: int = ANTS_CGS_PLAIN) -> Result:
-    """Reconstruct device-resident signals [n, n_sensors] (torch, float32)."""
+    """Reconstruct device-resident signals [n, n_sensors] (torch float32 or float16)."""
     import torch
     n = int(signals.shape[0])
     dev = signals.device
@@ -665,8 +666,9 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     iters = params.refine.iters if isinstance(params, (SeededParams, GemmParams)) else params.iters
     trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
+    dtype = ANTS_F16 if signals.dtype == torch.float16 else ANTS_F32
     ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
-                     start_xyz=start_xyz, trace=trace, stream=stream)
+                     start_xyz=start_xyz, trace=trace, stream=stream, signal_dtype=dtype)
     return Result(xyz, E, logL, status, trace)
 
 
@@ -686,13 +688,14 @@ def reconstruct_host_noalloc(ctx: Context, lrf: Lrf, params: CgsParams, signals:
 
 def reconstruct_host(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndarray, start_xyz=None,
                      method: int = ANTS_CGS_PLAIN) -> Result:
-    """Reconstruct host-resident signals (numpy float32 or pinned torch CPU tensor); synchronous."""
+    """Reconstruct host-resident signals (numpy float32/float16 or pinned torch CPU tensor); synchronous."""
     n = int(signals.shape[0])
     xyz = np.empty((n, 3), dtype=np.float32)
     E = np.empty(n, dtype=np.float32)
     logL = np.empty(n, dtype=np.float32)
     status = np.empty(n, dtype=np.int32)
     n_s = int(signals.shape[1]) if signals.ndim == 2 else -1
+    dtype = ANTS_F16 if str(signals.dtype) in ("float16", "torch.float16") else ANTS_F32
     ants_reconstruct_host(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
-                          start_xyz=start_xyz)
+                          start_xyz=start_xyz, signal_dtype=dtype)
     return Result(xyz, E, logL, status)

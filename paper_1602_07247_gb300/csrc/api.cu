@@ -4,6 +4,8 @@
 #include <cstring>
 #include <new>
 
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 #include "bspline.cuh"
 
@@ -57,6 +59,23 @@ void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
     }
     ctx->scratch_cap[slot] = want;
     return ctx->scratch[slot];
+}
+
+__global__ void widen_half_kernel(const __half *__restrict__ h, size_t n, float *__restrict__ f)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        f[i] = __half2float(h[i]);
+}
+
+int widen_half(const __half *h, size_t n, float *f, cudaStream_t s)
+{
+    if (n == 0) return ANTS_OK;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    widen_half_kernel<<<(unsigned)blocks, 256, 0, s>>>(h, n, f);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ANTS_OK : cuda_fail(e, "widen FP16 signals");
 }
 
 }  // namespace ants
@@ -437,11 +456,26 @@ static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const vo
     if (n_events < 0) return fail(ANTS_E_ARG, "ants_reconstruct: n_events < 0");
     if (n_sensors != lrf->n_s)
         return fail(ANTS_E_SHAPE, "ants_reconstruct: n_sensors %d but the LRF has %d", n_sensors, lrf->n_s);
-    if (signal_dtype != ANTS_F32) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: dtype %d", signal_dtype);
+    if (signal_dtype != ANTS_F32 && signal_dtype != ANTS_F16)
+        return fail(ANTS_E_ARG, "ants_reconstruct: signal dtype %d", signal_dtype);
     if (method == ANTS_MLP_SEEDED) return check_seeded_params(lrf, (const ants_mlp_seeded_params *)params);
     if (method == ANTS_GEMM_TOPK) return check_gemm_params(lrf, (const ants_gemm_params *)params);
     if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
     return check_cgs_params(lrf, (const ants_cgs_params *)params);
+}
+
+static int reconstruct_f32(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params, const float *sig,
+                           long n_events, const float *start_xyz_dev, float *xyz_dev, float *E_dev, float *logL_dev,
+                           int32_t *status_dev, int16_t *trace_dev, cudaStream_t stream)
+{
+    if (method == ANTS_GEMM_TOPK)
+        return reconstruct_gemm_topk(ctx, lrf, *(const ants_gemm_params *)params, sig, n_events, xyz_dev, E_dev,
+                                     logL_dev, status_dev, stream);
+    if (method == ANTS_MLP_SEEDED)
+        return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, sig, n_events, xyz_dev,
+                                      E_dev, logL_dev, status_dev, trace_dev, stream);
+    return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, sig, n_events, start_xyz_dev, xyz_dev, E_dev,
+                            logL_dev, status_dev, trace_dev, stream);
 }
 
 ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
@@ -455,21 +489,33 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
     if (n_events == 0) return ANTS_OK;
     if (!signals_dev || !xyz_dev || !E_dev || !logL_dev || !status_dev)
         return fail(ANTS_E_ARG, "ants_reconstruct: NULL signal or output buffer");
+    if (method == ANTS_GEMM_TOPK && (start_xyz_dev || trace_dev))
+        return fail(ANTS_E_ARG, "ants_reconstruct: the precision form takes no start or trace");
+    if (method == ANTS_MLP_SEEDED && start_xyz_dev)
+        return fail(ANTS_E_ARG, "ants_reconstruct: the learned form proposes its own start");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if (method == ANTS_GEMM_TOPK) {
-        if (start_xyz_dev || trace_dev) return fail(ANTS_E_ARG, "ants_reconstruct: the precision form takes no start or trace");
-        return reconstruct_gemm_topk(ctx, lrf, *(const ants_gemm_params *)params, (const float *)signals_dev, n_events,
-                                     xyz_dev, E_dev, logL_dev, status_dev, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (signal_dtype == ANTS_F32)
+        return reconstruct_f32(ctx, lrf, method, params, (const float *)signals_dev, n_events, start_xyz_dev, xyz_dev,
+                               E_dev, logL_dev, status_dev, trace_dev, s);
+    // FP16 signals: widen chunk by chunk into scratch slot 7 (no other user)
+    const int iters = method == ANTS_CGS_PLAIN ? ((const ants_cgs_params *)params)->iters
+                      : method == ANTS_MLP_SEEDED ? ((const ants_mlp_seeded_params *)params)->refine.iters
+                                                  : 0;
+    const long chunk = n_events < (1L << 20) ? n_events : (1L << 20);
+    float *wide = (float *)ctx_scratch(ctx, 7, (size_t)chunk * n_sensors * sizeof(float));
+    if (!wide) return ANTS_E_OOM;
+    const __half *h = (const __half *)signals_dev;
+    for (long off = 0; off < n_events; off += chunk) {
+        const long n = n_events - off < chunk ? n_events - off : chunk;
+        rc = widen_half(h + (size_t)off * n_sensors, (size_t)n * n_sensors, wide, s);
+        if (rc != ANTS_OK) return rc;
+        rc = reconstruct_f32(ctx, lrf, method, params, wide, n, start_xyz_dev ? start_xyz_dev + 3 * off : nullptr,
+                             xyz_dev + 3 * off, E_dev + off, logL_dev + off, status_dev + off,
+                             trace_dev ? trace_dev + (size_t)off * iters : nullptr, s);
+        if (rc != ANTS_OK) return rc;
     }
-    if (method == ANTS_MLP_SEEDED) {
-        if (start_xyz_dev) return fail(ANTS_E_ARG, "ants_reconstruct: the learned form proposes its own start");
-        return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, (const float *)signals_dev,
-                                      n_events, xyz_dev, E_dev, logL_dev, status_dev, trace_dev,
-                                      (cudaStream_t)stream);
-    }
-    return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, (const float *)signals_dev,
-                            n_events, start_xyz_dev, xyz_dev, E_dev, logL_dev, status_dev, trace_dev,
-                            (cudaStream_t)stream);
+    return ANTS_OK;
 }
 
 ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
@@ -491,7 +537,8 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
     if (ctx->host_cap_events < (size_t)chunk || ctx->host_cap_sensors < n_sensors) {
         free_host_buffers(ctx);
         for (int k = 0; k < 2; ++k) {
-            cudaError_t e = cudaMalloc(&ctx->d_sig[k], (size_t)chunk * n_sensors * sizeof(float));
+            // FP32 chunk, then room for the FP16 copy that is widened into it
+            cudaError_t e = cudaMalloc(&ctx->d_sig[k], (size_t)chunk * n_sensors * (sizeof(float) + sizeof(__half)));
             if (e == cudaSuccess) e = cudaMalloc(&ctx->d_start[k], (size_t)chunk * 3 * sizeof(float));
             if (e == cudaSuccess) e = cudaMalloc(&ctx->d_out[k], (size_t)chunk * 5 * sizeof(float));
             if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status[k], (size_t)chunk * sizeof(int32_t));
@@ -507,9 +554,18 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
         int k = (int)(c & 1);
         cudaStream_t s = ctx->stream[k];
         long n = n_events - off < chunk ? n_events - off : chunk;
-        const float *sig = (const float *)signals_host + off * n_sensors;
-        ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_sig[k], sig, (size_t)n * n_sensors * sizeof(float),
-                                      cudaMemcpyHostToDevice, s), "H2D signals");
+        if (signal_dtype == ANTS_F32) {
+            const float *sig = (const float *)signals_host + off * n_sensors;
+            ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_sig[k], sig, (size_t)n * n_sensors * sizeof(float),
+                                          cudaMemcpyHostToDevice, s), "H2D signals");
+        } else {
+            const __half *sig = (const __half *)signals_host + off * n_sensors;
+            __half *stage = (__half *)((float *)ctx->d_sig[k] + (size_t)chunk * n_sensors);
+            ANTS_CUDA_TRY(cudaMemcpyAsync(stage, sig, (size_t)n * n_sensors * sizeof(__half), cudaMemcpyHostToDevice,
+                                          s), "H2D signals");
+            rc = widen_half(stage, (size_t)n * n_sensors, (float *)ctx->d_sig[k], s);
+            if (rc != ANTS_OK) return rc;
+        }
         if (start_xyz_host)
             ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_start[k], start_xyz_host + off * 3, (size_t)n * 3 * sizeof(float),
                                           cudaMemcpyHostToDevice, s), "H2D start");

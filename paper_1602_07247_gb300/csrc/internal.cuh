@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -102,6 +103,8 @@ int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
 // Growing a slot frees the old buffer, so the caller must not have work in
 // flight that uses it.
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
+// f[i] = h[i] for n FP16 values (exact widening), on stream s
+int widen_half(const __half *h, size_t n, float *f, cudaStream_t s);
 // learned proposal (mlp.cu)
 int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s);
 int mlp_decode(const ants_mlp *M, const float *O, long n, float *xyz, float *E, cudaStream_t s);

@@ -145,3 +145,27 @@ def test_topk_many_bands_16x16(setup16):
     sc1, ix1 = table.topk(sig[-300:], 8)
     assert np.array_equal(ix1.cpu().numpy(), ix[-300:]) and np.array_equal(sc1.cpu().numpy(), sc[-300:])
     assert ants.ants_ctx_fault(ctx.handle) == 0
+
+
+def test_fp16_signals_equal_their_fp32_values(setup16):
+    """FP16 signals (the precision workload's storage type) give bit-identical
+    results to the same values passed as FP32, for all three methods and the
+    host-buffer path, across the 2^20-event conversion chunks' boundary logic."""
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    ev = w.events(1531, seed=95)
+    h = torch.from_numpy(ev.signals).cuda().to(torch.float16)
+    f = h.float()
+    gp = table.params(ants.CgsParams(n_xy=7, iters=5, step_xy=0.8 / 3), top_k=8, nms_cells=1.5)
+    for params, method in ((plain, ants.ANTS_CGS_PLAIN), (gp, ants.ANTS_GEMM_TOPK)):
+        a = to_numpy(ants.reconstruct(ctx, lrf, params, h, method=method))
+        b = to_numpy(ants.reconstruct(ctx, lrf, params, f, method=method))
+        for k in ("xyz", "E", "logL", "status"):
+            assert np.array_equal(a[k], b[k], equal_nan=True), (method, k)
+    hh = h.cpu().numpy()
+    rh = ants.reconstruct_host(ctx, lrf, plain, hh)
+    rf = ants.reconstruct_host(ctx, lrf, plain, hh.astype(np.float32))
+    assert np.array_equal(rh.xyz, rf.xyz, equal_nan=True) and np.array_equal(rh.logL, rf.logL, equal_nan=True)
+    with pytest.raises(ants.AntsError):
+        ants.ants_reconstruct(ctx.handle, lrf.handle, ants.ANTS_CGS_PLAIN, plain, f, 256, *[torch.empty(
+            s, device="cuda") for s in ((1531, 3), 1531, 1531)], torch.empty(1531, dtype=torch.int32, device="cuda"),
+            signal_dtype=7)
