@@ -89,6 +89,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Event seed of a rank: every rank reconstructs its own events."""
+    return base + 7919 * rank
+
+
+def max_over_ranks(x: float, device="cuda") -> float:
+    """The largest x over all ranks (the job's wall time); x itself on one rank."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(n_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job events/s: the events all ranks processed over the slowest rank's time."""
+    return n_per_rank * world * steps / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -317,7 +338,7 @@ def run_ours(args):
     pts, vals = w.fit_samples()
     lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)  # FP64 fit on the GPU
     p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
-    ev = w.events(n, seed=w.event_seed + 7919 * rank)
+    ev = w.events(n, seed=rank_seed(w.event_seed, rank))
     sig = torch.from_numpy(ev.signals).cuda()
     xyz = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     E = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -352,13 +373,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    dt = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
-    value = n * world * args.steps / dt
+    dt = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    value = job_rate(n, world, args.steps, dt)
     kernel_s = dt / args.steps  # one kernel launch per step
 
     # accuracy of this run (not timed): RMS |dxy| against the true positions
@@ -382,17 +398,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         step_host()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": n * world * e2e_steps / t_e2e, "unit": "events/s",
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": job_rate(n, world, e2e_steps, t_e2e), "unit": "events/s",
            "h2d_bytes_per_step": int(sig_host.numel() * 4),
            "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
 
     if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()  # rank 0 prints after the others are done with the GPU collectives
+            dist.destroy_process_group()
         return 0
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
@@ -428,6 +443,7 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
+        dist.barrier()
         dist.destroy_process_group()
     return 0
 
