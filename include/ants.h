@@ -210,6 +210,15 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx);
  * undefined) and returns ANTS_E_TIMEOUT; otherwise stores 0, returns ANTS_OK. */
 ANTS_API int ants_ctx_fault(ants_ctx *ctx, int *fault);
 
+/* Self-test of that mechanism (no counterpart in the paper): launches a small
+ * tensor-core top-K product whose TMA producer is held back, so that its MMA
+ * thread's wait runs out after 1 s; the kernel must stop, drain, free its
+ * tensor memory and set the fault word, and a normal launch on the same
+ * context must then give the right answer.  Synchronous (about 1 s); faults,
+ * traps and hangs nothing.  Returns ANTS_OK when all of that holds,
+ * ANTS_E_INTERNAL otherwise; it clears the fault word. */
+ANTS_API int ants_selftest_stalled_product(ants_ctx *ctx);
+
 /* ------------------------------------------------------------------------ */
 /* Detector definition (Sec. 2 "detector definitions"; Sec. 5.1.1 gains)      */
 /* ------------------------------------------------------------------------ */

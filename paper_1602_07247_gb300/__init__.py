@@ -128,6 +128,7 @@ def lib() -> C.CDLL:
         L.ants_ctx_destroy.argtypes = [_VP]
         L.ants_ctx_destroy.restype = None
         L.ants_ctx_fault.argtypes = [_VP, C.POINTER(C.c_int)]
+        L.ants_selftest_stalled_product.argtypes = [_VP]
         L.ants_detector_create.argtypes = [C.c_int, _DP, _DP, C.POINTER(_VP)]
         L.ants_detector_free.argtypes = [_VP]
         L.ants_detector_free.restype = None
@@ -240,6 +241,11 @@ def ants_ctx_fault(ctx: int) -> int:
     f = C.c_int(0)
     _check(lib().ants_ctx_fault(ctx, C.byref(f)))
     return f.value
+
+
+def ants_selftest_stalled_product(ctx: int) -> None:
+    """Run the bounded-wait self-test of the tensor-core kernels (raises on failure)."""
+    _check(lib().ants_selftest_stalled_product(ctx))
 
 
 def ants_detector_create(sensor_xy, rel_gain=None) -> int:

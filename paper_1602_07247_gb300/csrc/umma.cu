@@ -30,6 +30,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "internal.cuh"
 
 namespace ants {
@@ -68,6 +70,7 @@ struct UmmaArgs {
     const float *bias;
     __nv_bfloat16 *out;
     int *fault;
+    int hold_producer;  // self-test only: the TMA producer issues nothing
 };
 
 // ---- PTX wrappers -----------------------------------------------------------
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0, issued = 0, issued_ph = 0;
-            bool ok = true;
+            bool ok = !a.hold_producer;
             for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x)
                 for (int nt = 0; nt < n_nt && ok; ++nt)
                     for (int kc = 0; kc < n_kc && ok; ++kc) {
@@ -670,3 +673,83 @@ int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfl
 }
 
 }  // namespace ants
+
+using namespace ants;
+
+// Self-test of the bounded waits (no counterpart in the paper): a top-K
+// product whose producer is held back must give up after its 1 s wait limit,
+// report through the fault word, and leave the context usable.
+extern "C" ANTS_API int ants_selftest_stalled_product(ants_ctx *ctx)
+{
+    begin_call();
+    if (!ctx) return fail(ANTS_E_ARG, "ants_selftest_stalled_product: NULL context");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int M = 256, N = 256, K = 64;
+    float *A = nullptr, *val = nullptr;
+    __nv_bfloat16 *B = nullptr;
+    int *order = nullptr, *idx = nullptr;
+    cudaError_t e = cudaMalloc(&A, (size_t)M * K * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&B, (size_t)N * K * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&order, N * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&val, (size_t)M * 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&idx, (size_t)M * 8 * sizeof(int));
+    int rc = ANTS_OK;
+    if (e != cudaSuccess) rc = cuda_fail(e, "self-test buffers");
+    std::vector<int> ho(N);
+    for (int i = 0; i < N; ++i) ho[i] = i;
+    // A = 1, B = 0 except B[n][0] = n/256: every row's best column is N-1
+    std::vector<float> hA((size_t)M * K, 1.0f);
+    std::vector<__nv_bfloat16> hB((size_t)N * K, __float2bfloat16_rn(0.0f));
+    for (int n = 0; n < N; ++n) hB[(size_t)n * K] = __float2bfloat16_rn((float)n / 256.0f);
+    if (rc == ANTS_OK) {
+        e = cudaMemcpy(A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(B, hB.data(), hB.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(order, ho.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(ctx->d_fault, 0, sizeof(int));
+        if (e != cudaSuccess) rc = cuda_fail(e, "self-test upload");
+    }
+    CUtensorMap map;
+    if (rc == ANTS_OK) rc = encode_b(&map, B, N, K);
+    int fault_stalled = 0, fault_after = 0;
+    if (rc == ANTS_OK) {
+        UmmaArgs a{};
+        a.M = M;
+        a.N = N;
+        a.K = K;
+        a.A = A;
+        a.topk = 8;
+        a.order = order;
+        a.top_val = val;
+        a.top_idx = idx;
+        a.fault = ctx->d_fault;
+        a.hold_producer = 1;
+        rc = launch<EPI_TOPK, true>(ctx, map, a, nullptr);
+        if (rc == ANTS_OK) {
+            e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) e = cudaMemcpy(&fault_stalled, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemset(ctx->d_fault, 0, sizeof(int));
+            if (e != cudaSuccess) rc = cuda_fail(e, "self-test (stalled launch)");
+        }
+        if (rc == ANTS_OK) {
+            a.hold_producer = 0;
+            rc = launch<EPI_TOPK, true>(ctx, map, a, nullptr);
+        }
+        if (rc == ANTS_OK) {
+            e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) e = cudaMemcpy(&fault_after, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost);
+            int best = -1;
+            if (e == cudaSuccess) e = cudaMemcpy(&best, idx, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = cuda_fail(e, "self-test (normal launch)");
+            else if (!fault_stalled) rc = fail(ANTS_E_INTERNAL, "self-test: the stalled product did not report");
+            else if (fault_after || best != N - 1)
+                rc = fail(ANTS_E_INTERNAL, "self-test: the context is not usable after the timeout (%d, %d)",
+                          fault_after, best);
+        }
+    }
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(order);
+    cudaFree(val);
+    cudaFree(idx);
+    return rc;
+}

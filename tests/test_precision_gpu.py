@@ -169,3 +169,16 @@ def test_fp16_signals_equal_their_fp32_values(setup16):
         ants.ants_reconstruct(ctx.handle, lrf.handle, ants.ANTS_CGS_PLAIN, plain, f, 256, *[torch.empty(
             s, device="cuda") for s in ((1531, 3), 1531, 1531)], torch.empty(1531, dtype=torch.int32, device="cuda"),
             signal_dtype=7)
+
+
+def test_stalled_product_gives_up_and_the_context_recovers(setup16):
+    """A tensor-core product whose producer never delivers stops after its
+    bounded wait, reports through the fault word, and the next launch on the
+    same context is correct (no GPU fault, trap or hang involved)."""
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    ants.ants_selftest_stalled_product(ctx.handle)
+    assert ants.ants_ctx_fault(ctx.handle) == 0
+    ev = w.events(300, seed=97)
+    sc, ix = table.topk(torch.from_numpy(ev.signals).cuda(), 8)
+    T, _ = table.values()
+    _check_topk(ev.signals, T, sc.cpu().numpy(), ix.cpu().numpy(), 8)
