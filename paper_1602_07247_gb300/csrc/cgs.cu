@@ -910,6 +910,15 @@ ANTS_API int ants_batch_autotune(ants_batch_plan *P, const char *cache_path, lon
             for (int b : blocks) {
                 if (rc != ANTS_OK) break;
                 if (w * b > 64) continue;  // at most 64 warps per SM
+                // blocks beyond what one SM holds at once only wait for an
+                // empty queue: skip shapes whose blocks cannot all be resident
+                int resident = 0;
+                const size_t smem_b = (size_t)w * P->warp_floats * sizeof(float);
+                if (smem_b <= P->ctx->smem_optin) {
+                    cudaFuncSetAttribute(cgs_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cgs_batched_kernel, 32 * w, smem_b);
+                }
+                if (resident < b) continue;
                 P->cfg = ants_batch_config{u, w, b};
                 rc = build_plan(P, events_per_item);
                 if (rc != ANTS_OK) break;
