@@ -30,6 +30,10 @@ if ROOT not in sys.path:
 METRIC = "events/s of ML position reconstruction, plain CGS vs chosen form, same error"
 SM_COUNT = 152
 MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
+# DRAM bytes (read + write) per event of the headline kernel, from the ncu
+# capture summarised in profiles/cgs_xy_sipm8x8_xy.md (600 000 events:
+# 155.88 MB read + 10.37 MB written); None once the kernel changes.
+XY_TRAFFIC_PER_EVENT = (155.879936e6 + 10.371328e6) / 600_000
 
 
 def peaks():
@@ -414,8 +418,9 @@ def run_ours(args):
     evals = n * w.iters * w.n_xy * w.n_xy * w.n_sensors
     peak_evals = SM_COUNT * MUFU_PER_CLK_SM * sm_mhz * 1e6
     achieved = evals / kernel_s
+    traffic = None if XY_TRAFFIC_PER_EVENT is None else XY_TRAFFIC_PER_EVENT * n
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_evals / 1e12, "unit": "Teval/s",
-                "frac": achieved / peak_evals, "traffic": None,
+                "frac": achieved / peak_evals, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_kind": f"derived: {SM_COUNT} SMs x {MUFU_PER_CLK_SM} log2/clk x {sm_mhz:.0f} MHz "
                              f"({pk_kind} max clock); one eval = one LRF value + one log2 per (node, sensor)"}
     cpu = None
