@@ -234,12 +234,20 @@ def forms_comparison(args, ants, torch, ctx, stream):
         d = res.xyz[:, :2].double().cpu().numpy() - true_xy
         err = np.sqrt((d ** 2).sum(1))
         st = res.status.cpu().numpy()
-        out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt, "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
+        fb_frac = float((st == ants.ANTS_EVT_FALLBACK).mean())
+        evals = n * {"plain": plain.n_xy ** 2 * plain.iters,
+                     "learned": refine.n_xy ** 2 * refine.iters + fb_frac * plain.n_xy ** 2 * plain.iters,
+                     "precision": 8 * 7 * 7 * 5}[name] * w.n_sensors  # precision: up to 8 refines
+        roof = SM_COUNT * MUFU_PER_CLK_SM * 2070.0e6
+        out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt,
+                     "evals_per_s": evals / dt, "frac_of_log2_roof": evals / dt / roof,
+                     "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
                      "median_dxy_mm": float(np.median(err)), "p95_dxy_mm": float(np.quantile(err, 0.95)),
-                     "fallback_frac": float((st == ants.ANTS_EVT_FALLBACK).mean())}
+                     "fallback_frac": fb_frac}
     for k in ("learned", "precision"):
         out[k]["speedup_vs_plain"] = out[k]["events_per_s"] / out["plain"]["events_per_s"]
         out[k]["rms_ratio_vs_plain"] = out[k]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
+    out["precision"]["evals_note"] = "upper bound: counts 8 refines per event; suppressed candidates do none"
     # the precision form's tensor-core scan on its own (tcgen05 product + top-8)
     sc = torch.empty((n, 8), device="cuda")
     ix = torch.empty((n, 8), dtype=torch.int32, device="cuda")
@@ -312,9 +320,14 @@ def batched_run(args, ants, torch, ctx, stream):
         per.append({"detector": w.name, "events": int(o.xyz.shape[0]),
                     "rms_dxy_mm": float(d[:, :2].pow(2).sum(1).mean().sqrt()),
                     "rms_dz_mm": float(d[:, 2].pow(2).mean().sqrt())})
+    pk, pk_kind = peaks()
+    roof = SM_COUNT * MUFU_PER_CLK_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     return {"workload": f"8 detectors, XYZ LRFs 16x16x8, {n_tot} events, grid 7x7x5 x 7, one persistent launch "
                         f"per step (CUDA graph)", "events_per_s": n_tot / dt, "ms_per_step": 1e3 * dt,
-            "evals_per_s": evals / dt, "steps": args.batch_steps, "setup_s": setup_s,
+            "evals_per_s": evals / dt,
+            "roofline": {"bound": "alu", "achieved": evals / dt / 1e12, "peak": roof / 1e12, "unit": "Teval/s",
+                         "frac": evals / dt / roof, "peak_kind": f"{pk_kind} max clock, 16 log2/clk/SM"},
+            "steps": args.batch_steps, "setup_s": setup_s,
             "autotuned": {"unit_events": cfg.unit_events, "warps_per_block": cfg.warps_per_block,
                           "blocks_per_sm": cfg.blocks_per_sm}, "detectors": per}
 
