@@ -599,7 +599,7 @@ int launch_cgs_rows(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_par
                     int16_t *trace, cudaStream_t stream)
 {
     if (cgs_xy_supported(lrf, p))
-        return launch_cgs_xy(ctx, lrf, p, sig, row_div, n_e, start, xyz, E, logL, status, trace, stream);
+        return launch_cgs_xy(ctx, lrf, p, sig, row_div, nullptr, n_e, start, xyz, E, logL, status, trace, stream);
     CgsArgs a;
     a.row_div = row_div;
     a.L = lrf->dev;

@@ -40,7 +40,8 @@ struct XyArgs {
     float shrink, step_xy;
     const float *sig;
     long n_e;
-    int row_div;  // event e reads signal row e / row_div
+    int row_div;      // event e reads signal row e / row_div ...
+    const int *rows;  // ... or rows[e] when given
     const float *start;
     float *xyz, *E, *logL;
     int32_t *status;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
 
     for (long e = (long)blockIdx.x * teams_per_block + team; e < a.n_e; e += team_stride) {
         // ---- prologue: signals, S, centroid, status ----------------------------
-        const float *sg = a.sig + (e / a.row_div) * n_s;
+        const float *sg = a.sig + (size_t)(a.rows ? (long)a.rows[e] : e / a.row_div) * n_s;
         float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
         int bad = 0;
         for (int i = t; i < n_pad; i += LT) {
@@ -547,11 +548,13 @@ bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p)
 }
 
 int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, int row_div,
+                  const int *rows,
                   long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                   cudaStream_t stream)
 {
     XyArgs a;
     a.row_div = row_div;
+    a.rows = rows;
     a.L = lrf->dev;
     a.iters = p.iters;
     a.shrink = p.shrink;

@@ -125,7 +125,9 @@ int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_se
                            long n, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                            cudaStream_t s);
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
+// event e reads signal row rows[e] when rows is given, else row e / row_div
 int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, int row_div,
+                  const int *rows,
                   long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                   cudaStream_t stream);
 // as launch_cgs_plain, with event e reading signal row e / row_div

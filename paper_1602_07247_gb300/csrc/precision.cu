@@ -11,9 +11,9 @@
 //              (BF16 x BF16 -> FP32 tensor-core product), keeping the top-K
 //              grid points per event without storing L.
 // p3  refine   a local contracting-grid search (Sec. 5.1.2.2) from each
-//              candidate not within `nms_cells` cells of a better one; the
-//              result with the largest log-likelihood wins (ties: better
-//              candidate rank).
+//              candidate not within `nms_cells` cells of a better one (only
+//              those are launched); the result with the largest
+//              log-likelihood wins (ties: better candidate rank).
 #include <cuda_bf16.h>
 
 #include <new>
@@ -132,6 +132,46 @@ __global__ void pick_best(long n, int K, const float *xyz_c, const float *E_c, c
 
 unsigned nb(long n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// Candidates that survived the suppression (and every event's first, whose
+// search also reports the event's signal status) are listed for the refine;
+// the others are marked as not searched.  The order of the list does not
+// matter: results go back to each candidate's own slot.
+__global__ void compact_candidates(const float *starts, long nv, int K, int *count, int *cidx, int *crow,
+                                   float *cstart, float *xyz_c, float *E_c, float *logL_c, int32_t *st_c)
+{
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const bool kept = (v % K) == 0 || !isnan(starts[3 * v]);
+    if (kept) {
+        const int r = atomicAdd(count, 1);
+        cidx[r] = (int)v;
+        crow[r] = (int)(v / K);
+        cstart[3 * r] = starts[3 * v];
+        cstart[3 * r + 1] = starts[3 * v + 1];
+        cstart[3 * r + 2] = starts[3 * v + 2];
+    } else {
+        const float qnan = __int_as_float(0x7fc00000);
+        xyz_c[3 * v] = xyz_c[3 * v + 1] = xyz_c[3 * v + 2] = qnan;
+        E_c[v] = logL_c[v] = qnan;
+        st_c[v] = ANTS_EVT_OUT_OF_DOMAIN;
+    }
+}
+
+__global__ void scatter_candidates(const int *count, const int *cidx, const float *o_xyz, const float *o_E,
+                                   const float *o_logL, const int32_t *o_st, float *xyz_c, float *E_c, float *logL_c,
+                                   int32_t *st_c)
+{
+    const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= *count) return;
+    const long v = cidx[r];
+    xyz_c[3 * v] = o_xyz[3 * r];
+    xyz_c[3 * v + 1] = o_xyz[3 * r + 1];
+    xyz_c[3 * v + 2] = o_xyz[3 * r + 2];
+    E_c[v] = o_E[r];
+    logL_c[v] = o_logL[r];
+    st_c[v] = o_st[r];
+}
+
 // Tp[r] = T[order[r]]
 __global__ void permute_rows(const __nv_bfloat16 *T, const int *order, long G, int n_s, __nv_bfloat16 *Tp)
 {
@@ -194,8 +234,37 @@ int reconstruct_gemm_topk(ants_ctx *ctx, const ants_lrf *lrf, const ants_gemm_pa
     }
     candidate_starts<<<nb(n, 256), 256, 0, s>>>(idx, n, K, T->nx, T->x0, T->y0, T->dx, T->dy, P.nms_cells, starts);
     count_launch();
-    int rc = launch_cgs_rows(ctx, lrf, P.refine, sig, K, nv, starts, xyz_c, E_c, logL_c, st_c, nullptr, s);
-    if (rc != ANTS_OK) return rc;
+    int rc = ANTS_OK;
+    if (!cgs_xy_supported(lrf, P.refine) || nv > 0x7fffffffL) {
+        // every candidate searched (suppressed ones stop at their NaN start)
+        rc = launch_cgs_rows(ctx, lrf, P.refine, sig, K, nv, starts, xyz_c, E_c, logL_c, st_c, nullptr, s);
+        if (rc != ANTS_OK) return rc;
+    } else {
+        // only the kept candidates are searched
+        unsigned char *lst = (unsigned char *)ctx_scratch(ctx, 5, 256 + (size_t)nv * 5 * sizeof(float));
+        unsigned char *res = (unsigned char *)ctx_scratch(ctx, 6, (size_t)nv * 6 * sizeof(float) + 1024);
+        if (!lst || !res) return ANTS_E_OOM;
+        int *d_count = (int *)lst;
+        int *cidx = (int *)(lst + 256), *crow = cidx + nv;
+        float *cstart = (float *)(crow + nv);
+        float *o_xyz = (float *)res, *o_E = o_xyz + 3 * nv, *o_logL = o_E + nv;
+        int32_t *o_st = (int32_t *)(o_logL + nv);
+        ANTS_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int), s), "candidate count");
+        compact_candidates<<<nb(nv, 256), 256, 0, s>>>(starts, nv, K, d_count, cidx, crow, cstart, xyz_c, E_c, logL_c,
+                                                       st_c);
+        count_launch();
+        int h_count = 0;
+        ANTS_CUDA_TRY(cudaMemcpyAsync(&h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, s), "candidate count");
+        ANTS_CUDA_TRY(cudaStreamSynchronize(s), "candidate count");
+        if (h_count > 0) {
+            rc = launch_cgs_xy(ctx, lrf, P.refine, sig, 1, crow, h_count, cstart, o_xyz, o_E, o_logL, o_st, nullptr,
+                               s);
+            if (rc != ANTS_OK) return rc;
+            scatter_candidates<<<nb(h_count, 256), 256, 0, s>>>(d_count, cidx, o_xyz, o_E, o_logL, o_st, xyz_c, E_c,
+                                                                logL_c, st_c);
+            count_launch();
+        }
+    }
     pick_best<<<nb(n, 256), 256, 0, s>>>(n, K, xyz_c, E_c, logL_c, st_c, xyz, E, logL, status, nullptr);
     count_launch();
     ANTS_CUDA_TRY(cudaGetLastError(), "precision form launch");
