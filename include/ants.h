@@ -330,10 +330,12 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
 
 /* The same reconstruction with HOST buffers (signals_host [n_events]
  * [n_sensors], outputs xyz_host [n_events][3], E_host, logL_host,
- * status_host; nullable start_xyz_host).  The library streams the events
- * through device buffers owned by the context in chunks, overlapping the
- * host-to-device copy, the search and the device-to-host copy on two
- * internal streams.  Page-locked host memory gives full copy bandwidth.
+ * status_host; nullable start_xyz_host, plain search only), any method.
+ * The library streams the events through device buffers owned by the
+ * context in chunks; for the plain search it overlaps the host-to-device
+ * copy, the search and the device-to-host copy on two internal streams, for
+ * the two forms (which use the context's scratch buffers) the chunks run in
+ * turn.  Page-locked host memory gives full copy bandwidth.
  * Synchronous: returns when the outputs are in host memory.
  * Errors: as ants_reconstruct, plus ANTS_E_OOM. */
 ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int method,

@@ -526,12 +526,15 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
     begin_call();
     int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
     if (rc != ANTS_OK) return rc;
-    if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct_host: method %d", method);
     if (n_events == 0) return ANTS_OK;
     if (!signals_host || !xyz_host || !E_host || !logL_host || !status_host)
         return fail(ANTS_E_ARG, "ants_reconstruct_host: NULL signal or output buffer");
+    if (method != ANTS_CGS_PLAIN && start_xyz_host)
+        return fail(ANTS_E_ARG, "ants_reconstruct_host: the learned and precision forms take no start");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const ants_cgs_params &p = *(const ants_cgs_params *)params;
+    // the plain search overlaps chunks on two streams; the two forms use the
+    // context's scratch buffers, so their chunks run one after the other
+    const bool overlap = method == ANTS_CGS_PLAIN;
     // chunk large enough to fill the GPU, small enough to pipeline
     const long chunk = 1L << 17;
     if (ctx->host_cap_events < (size_t)chunk || ctx->host_cap_sensors < n_sensors) {
@@ -551,7 +554,7 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
         ctx->host_cap_sensors = n_sensors;
     }
     for (long off = 0, c = 0; off < n_events; off += chunk, ++c) {
-        int k = (int)(c & 1);
+        int k = overlap ? (int)(c & 1) : 0;
         cudaStream_t s = ctx->stream[k];
         long n = n_events - off < chunk ? n_events - off : chunk;
         if (signal_dtype == ANTS_F32) {
@@ -570,9 +573,9 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
             ANTS_CUDA_TRY(cudaMemcpyAsync(ctx->d_start[k], start_xyz_host + off * 3, (size_t)n * 3 * sizeof(float),
                                           cudaMemcpyHostToDevice, s), "H2D start");
         float *o = ctx->d_out[k];
-        rc = launch_cgs_plain(ctx, lrf, p, (const float *)ctx->d_sig[k], n,
-                              start_xyz_host ? ctx->d_start[k] : nullptr, o, o + 3 * chunk, o + 4 * chunk,
-                              ctx->d_status[k], nullptr, s);
+        rc = reconstruct_f32(ctx, lrf, method, params, (const float *)ctx->d_sig[k], n,
+                             start_xyz_host ? ctx->d_start[k] : nullptr, o, o + 3 * chunk, o + 4 * chunk,
+                             ctx->d_status[k], nullptr, s);
         if (rc != ANTS_OK) return rc;
         ANTS_CUDA_TRY(cudaMemcpyAsync(xyz_host + off * 3, o, (size_t)n * 3 * sizeof(float),
                                       cudaMemcpyDeviceToHost, s), "D2H xyz");

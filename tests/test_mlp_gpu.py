@@ -173,4 +173,7 @@ def test_seeded_pipeline_consistency_and_gain(env):
     print("rms: learned form", rms(res), "refine from network", rms(ref), "refine from centroid", rms(cog),
           "plain", rms(full))
     assert rms(ref) < 0.5 * rms(cog)
+    # the same form through host buffers
+    host = ants.reconstruct_host(ctx, lrf, sp, ev.signals, method=ants.ANTS_MLP_SEEDED)
+    assert np.array_equal(host.xyz, res["xyz"], equal_nan=True) and np.array_equal(host.status, res["status"])
     assert rms(res) <= 1.10 * rms(full)

@@ -182,3 +182,19 @@ def test_stalled_product_gives_up_and_the_context_recovers(setup16):
     sc, ix = table.topk(torch.from_numpy(ev.signals).cuda(), 8)
     T, _ = table.values()
     _check_topk(ev.signals, T, sc.cpu().numpy(), ix.cpu().numpy(), 8)
+
+
+def test_host_buffer_path_precision_form(setup16):
+    """The precision form through host buffers (chunks of 2^17 events run in
+    turn) equals the device path bit for bit, also for FP16 host signals."""
+    torch, ants, ctx, w, L, det, lrf, plain, table = setup16
+    gp = table.params(ants.CgsParams(n_xy=7, iters=5, step_xy=0.8 / 3), top_k=8, nms_cells=1.5)
+    ev = w.events(2500, seed=98)
+    dev = to_numpy(ants.reconstruct(ctx, lrf, gp, torch.from_numpy(ev.signals).cuda(), method=ants.ANTS_GEMM_TOPK))
+    host = ants.reconstruct_host(ctx, lrf, gp, ev.signals, method=ants.ANTS_GEMM_TOPK)
+    for k in ("xyz", "E", "logL", "status"):
+        assert np.array_equal(getattr(host, k), dev[k], equal_nan=True), k
+    h16 = ants.reconstruct_host(ctx, lrf, gp, ev.signals.astype(np.float16), method=ants.ANTS_GEMM_TOPK)
+    d16 = to_numpy(ants.reconstruct(ctx, lrf, gp, torch.from_numpy(ev.signals).cuda().half(),
+                                    method=ants.ANTS_GEMM_TOPK))
+    assert np.array_equal(h16.xyz, d16["xyz"], equal_nan=True)
