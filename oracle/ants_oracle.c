@@ -1022,7 +1022,11 @@ void or_simulate(const or_lrf *L, const or_sim_params *P, uint64_t seed, long fi
         double u0 = or_u01(ev[0]), u1 = or_u01(ev[1]), u2 = or_u01(ev[2]), u3 = or_u01(ev[3]);
         double x, y;
         if (P->region == 0) {
+#if OR_MUTANT == 12
+            double rad = P->extent * u0, th = 6.283185307179586 * u1;
+#else
             double rad = P->extent * sqrt(u0), th = 6.283185307179586 * u1;
+#endif
             x = P->cx + rad * cos(th);
             y = P->cy + rad * sin(th);
         } else {

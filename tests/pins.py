@@ -541,6 +541,38 @@ def pin_uniform_stream(mutant=0):
     assert not np.array_equal(oracle.philox(1, (0, 0, 0, 0)), oracle.philox(2, (0, 0, 0, 0)))
 
 
+def pin_simulator(mutant=0):
+    """Event simulation: sources uniform in the square (mean, variance a^2/3)
+    and in the disk (r^2 uniform), energies uniform in e0 (1 +- spread), counts
+    with mean E eta_i(source) and Poisson variance, plus N(1, sigma^2) per
+    photo-electron when a single-p.e. spread is given (variance E eta (1 +
+    sigma^2)); different first_event values continue one stream."""
+    L, _ = _small_xy_lrf()
+    a, e0, sp = 4.0, 800.0, 0.1
+    sig, tr = oracle.simulate(L, 99, 0, 20000, region="square", extent=a, e0=e0, e_spread=sp, mutant=mutant)
+    n = len(tr)
+    for c in (0, 1):
+        assert abs(tr[:, c].mean()) < 4 * a / np.sqrt(3 * n)
+        assert abs(tr[:, c].var() / (a * a / 3) - 1) < 0.05
+    assert tr[:, 0].min() >= -a and tr[:, 0].max() <= a
+    assert tr[:, 3].min() >= e0 * (1 - sp) and tr[:, 3].max() <= e0 * (1 + sp)
+    assert abs(tr[:, 3].mean() / e0 - 1) < 4 * sp / np.sqrt(3 * n)
+    mu = tr[:, 3:4] * oracle.lrf_eval(L, tr[:, :2])
+    z = (sig - mu) / np.sqrt(mu)
+    assert np.all(np.abs(z.mean(0)) < 4 / np.sqrt(n)), z.mean(0)
+    assert np.all(np.abs(z.var(0) - 1) < 0.05), z.var(0)
+    assert np.array_equal(sig, np.round(sig))
+    sd, td = oracle.simulate(L, 99, 0, 20000, region="disk", extent=a, e0=e0, e_spread=sp, mutant=mutant)
+    r2 = (td[:, 0] ** 2 + td[:, 1] ** 2) / (a * a)
+    assert r2.max() <= 1 + 1e-12 and abs(r2.mean() - 0.5) < 4 * np.sqrt(1 / 12 / n)
+    ss, ts = oracle.simulate(L, 99, 0, 20000, region="square", extent=a, e0=e0, e_spread=sp, spe_sigma=0.3,
+                             mutant=mutant)
+    mu = ts[:, 3:4] * oracle.lrf_eval(L, ts[:, :2])
+    assert np.all(np.abs((ss - mu).var(0) / (mu * 1.09).mean(0) - 1) < 0.08)
+    s2, t2 = oracle.simulate(L, 99, 5000, 100, region="square", extent=a, e0=e0, e_spread=sp, mutant=mutant)
+    assert np.array_equal(s2, sig[5000:5100]) and np.array_equal(t2, tr[5000:5100])
+
+
 def pin_logtable_ranks_like_likelihood(mutant=0):
     """The table scores sum_i s_i T[g][i] differ from the profiled
     log-likelihood F(g) = sum s ln eta - S ln H by a constant per event, and
@@ -564,5 +596,5 @@ ALL_PINS = [
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
     pin_noise_free_recovery, pin_noise_free_recovery_3d, pin_cg_matches_brute_force, pin_ties_go_to_lowest_index, pin_domain,
     pin_event_status, pin_replay, pin_gelu, pin_mlp_forward, pin_mlp_gradient, pin_adam, pin_deviance,
-    pin_poisson_sampler, pin_uniform_stream, pin_logtable_ranks_like_likelihood,
+    pin_poisson_sampler, pin_uniform_stream, pin_simulator, pin_logtable_ranks_like_likelihood,
 ]

@@ -17,6 +17,7 @@ MUTANTS = {
     9: "wrong knot in the local Cox-de Boor recursion",
     10: "GELU with erf(x) instead of erf(x / sqrt 2)",
     11: "loss gradient missing the factor 2",
+    12: "disk sources with radius extent*u instead of extent*sqrt(u)",
 }
 
 
