@@ -291,6 +291,39 @@ def forms_comparison(args, ants, torch, ctx, stream):
             "setup_s": setup_s, "deviance_max": thr, **out}
 
 
+def radial_run(args, ants, torch, ctx, stream):
+    """19-PMT hexagonal detector with one radial LRF (9x9 grid, 6 grids):
+    throughput on 10^6 events (the workload's 10^4 events take under a
+    millisecond, too short to time) and accuracy against the true positions."""
+    import synth.workloads
+    w = synth.workloads.get("hex19_radial")
+    det = ants.Detector(w.sensor_xy, w.gains)
+    pts, vals = w.fit_samples()
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_RADIAL, w.n_int, w.lo, w.hi, pts, vals, shared=True)
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    out = {}
+    for n in (w.n_events, 1_000_000):
+        ev = w.events(n, seed=w.event_seed)
+        sig = torch.from_numpy(ev.signals).cuda()
+        for _ in range(3):
+            res = ants.reconstruct(ctx, lrf, p, sig, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            res = ants.reconstruct(ctx, lrf, p, sig, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / reps
+        d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+        evals = n * w.n_xy * w.n_xy * w.iters * w.n_sensors
+        out[str(n)] = {"events_per_s": n / dt, "ms_per_launch": 1e3 * dt, "evals_per_s": evals / dt,
+                       "rms_dxy_mm": float(np.sqrt((d ** 2).sum(1).mean()))}
+    return {"workload": "hex19_radial: 19 PMTs, hexagonal, pitch 30 mm, one radial LRF (20 intervals on [0,150] mm), "
+                        "contracting grid 9x9 x 6 grids, plain FP32", **out}
+
+
 def batched_run(args, ants, torch, ctx, stream):
     """Eight detectors with 3D LRFs (19..256 sensors, 3e6 events) in one
     persistent launch per step (CUDA graph), launch shape autotuned."""
@@ -463,6 +496,7 @@ def run_ours(args):
         except Exception as exc:  # the headline line must still be printed
             return {"error": f"{type(exc).__name__}: {exc}"}
 
+    radial = optional(radial_run, args.no_forms)
     forms = optional(forms_comparison, args.no_forms)
     batched = optional(batched_run, args.no_batched)
     line = {
@@ -470,7 +504,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-        "rms_dxy_mm": rms, "forms_16x16": forms, "batched_3d": batched,
+        "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
