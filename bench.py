@@ -30,6 +30,24 @@ if ROOT not in sys.path:
 METRIC = "events/s of ML position reconstruction, plain CGS vs chosen form, same error"
 SM_COUNT = 152
 MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
+FMA_PER_CLK_SM = 128  # FP32 fused multiply-adds per clock per SM
+# canonical FP32 multiply-adds per (node, sensor) evaluation of each search:
+# B-spline tensor product, likelihood term and energy sum
+F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9}
+
+
+def alu_roofline(evals_per_s: float, kind: str) -> dict:
+    """Evaluation rate against min(FP32 FMA peak / F, log2 peak / 1)."""
+    pk, pk_kind = peaks()
+    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    fma_ceiling = SM_COUNT * FMA_PER_CLK_SM * clk / F_FMA[kind]
+    log_ceiling = SM_COUNT * MUFU_PER_CLK_SM * clk
+    peak = min(fma_ceiling, log_ceiling)
+    return {"bound": "alu", "achieved": evals_per_s / 1e12, "peak": peak / 1e12, "unit": "Teval/s",
+            "frac": evals_per_s / peak, "frac_of_log2_peak": evals_per_s / log_ceiling,
+            "peak_kind": f"min({SM_COUNT} SMs x {FMA_PER_CLK_SM} FMA/clk x {clk / 1e6:.0f} MHz / {F_FMA[kind]} FMA "
+                         f"per evaluation, {SM_COUNT} x {MUFU_PER_CLK_SM} log2/clk x {clk / 1e6:.0f} MHz); "
+                         f"{pk_kind} max clock"}
 # DRAM bytes (read + write) per event of the headline kernel, from the ncu
 # capture summarised in profiles/cgs_xy_sipm8x8_xy.md (600 000 events:
 # 155.88 MB read + 10.37 MB written); None once the kernel changes.
@@ -252,9 +270,9 @@ def forms_comparison(args, ants, torch, ctx, stream):
         evals = n * {"plain": plain.n_xy ** 2 * plain.iters,
                      "learned": refine.n_xy ** 2 * refine.iters + fb_frac * plain.n_xy ** 2 * plain.iters,
                      "precision": kept_per_event * 7 * 7 * 5}[name] * w.n_sensors
-        roof = SM_COUNT * MUFU_PER_CLK_SM * 2070.0e6
         out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt,
-                     "evals_per_s": evals / dt, "frac_of_log2_roof": evals / dt / roof,
+                     "evals_per_s": evals / dt,
+                     "roofline": alu_roofline(evals / dt, "xy" if name == "plain" else "local"),
                      "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
                      "median_dxy_mm": float(np.median(err)), "p95_dxy_mm": float(np.quantile(err, 0.95)),
                      "fallback_frac": fb_frac}
@@ -319,6 +337,7 @@ def radial_run(args, ants, torch, ctx, stream):
         d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
         evals = n * w.n_xy * w.n_xy * w.iters * w.n_sensors
         out[str(n)] = {"events_per_s": n / dt, "ms_per_launch": 1e3 * dt, "evals_per_s": evals / dt,
+                       "roofline": alu_roofline(evals / dt, "radial"),
                        "rms_dxy_mm": float(np.sqrt((d ** 2).sum(1).mean()))}
     return {"workload": "hex19_radial: 19 PMTs, hexagonal, pitch 30 mm, one radial LRF (20 intervals on [0,150] mm), "
                         "contracting grid 9x9 x 6 grids, plain FP32", **out}
@@ -367,13 +386,9 @@ def batched_run(args, ants, torch, ctx, stream):
         per.append({"detector": w.name, "events": int(o.xyz.shape[0]),
                     "rms_dxy_mm": float(d[:, :2].pow(2).sum(1).mean().sqrt()),
                     "rms_dz_mm": float(d[:, 2].pow(2).mean().sqrt())})
-    pk, pk_kind = peaks()
-    roof = SM_COUNT * MUFU_PER_CLK_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     return {"workload": f"8 detectors, XYZ LRFs 16x16x8, {n_tot} events, grid 7x7x5 x 7, one persistent launch "
                         f"per step (CUDA graph)", "events_per_s": n_tot / dt, "ms_per_step": 1e3 * dt,
-            "evals_per_s": evals / dt,
-            "roofline": {"bound": "alu", "achieved": evals / dt / 1e12, "peak": roof / 1e12, "unit": "Teval/s",
-                         "frac": evals / dt / roof, "peak_kind": f"{pk_kind} max clock, 16 log2/clk/SM"},
+            "evals_per_s": evals / dt, "roofline": alu_roofline(evals / dt, "xyz"),
             "steps": args.batch_steps, "setup_s": setup_s,
             "autotuned": {"unit_events": cfg.unit_events, "warps_per_block": cfg.warps_per_block,
                           "blocks_per_sm": cfg.blocks_per_sm}, "detectors": per}
@@ -473,16 +488,9 @@ def run_ours(args):
             dist.barrier()  # rank 0 prints after the others are done with the GPU collectives
             dist.destroy_process_group()
         return 0
-    pk, pk_kind = peaks()
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     evals = n * w.iters * w.n_xy * w.n_xy * w.n_sensors
-    peak_evals = SM_COUNT * MUFU_PER_CLK_SM * sm_mhz * 1e6
-    achieved = evals / kernel_s
     traffic = None if XY_TRAFFIC_PER_EVENT is None else XY_TRAFFIC_PER_EVENT * n
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_evals / 1e12, "unit": "Teval/s",
-                "frac": achieved / peak_evals, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_kind": f"derived: {SM_COUNT} SMs x {MUFU_PER_CLK_SM} log2/clk x {sm_mhz:.0f} MHz "
-                             f"({pk_kind} max clock); one eval = one LRF value + one log2 per (node, sensor)"}
+    roofline = {**alu_roofline(evals / kernel_s, "xy"), "traffic": traffic, "traffic_unit": "bytes per launch"}
     cpu = None
     if not args.no_cpu_baseline:
         rate, secs, cores, _ = cpu_oracle_rate(w, args.cpu_events, seed=w.event_seed)
