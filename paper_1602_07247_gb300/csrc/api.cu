@@ -242,6 +242,26 @@ static int upload_lrf(ants_lrf *L)
         D.coef2 = L->d_coef2;
         D.pair_stride = ps;
     }
+    D.rpoly = nullptr;
+    if (L->type == ANTS_LRF_RADIAL) {
+        // uniform cubic B-spline on interval j: sum_a c[j+a] B_a(t) expanded in
+        // powers of t (FP64, then rounded once to FP32)
+        const int ni = L->n_int[0];
+        std::vector<float4> rp((size_t)L->n_sets * ni);
+        for (int set = 0; set < L->n_sets; ++set)
+            for (int j = 0; j < ni; ++j) {
+                const double *c = L->coef.data() + (size_t)set * L->n_coef + j;
+                const double p0 = (c[0] + 4.0 * c[1] + c[2]) / 6.0;
+                const double p1 = (c[2] - c[0]) / 2.0;
+                const double p2 = (c[0] - 2.0 * c[1] + c[2]) / 2.0;
+                const double p3 = (-c[0] + 3.0 * c[1] - 3.0 * c[2] + c[3]) / 6.0;
+                rp[(size_t)set * ni + j] = make_float4((float)p0, (float)p1, (float)p2, (float)p3);
+            }
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_rpoly, rp.size() * sizeof(float4)), "cudaMalloc(lrf radial polynomials)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_rpoly, rp.data(), rp.size() * sizeof(float4), cudaMemcpyHostToDevice),
+                      "upload radial polynomials");
+        D.rpoly = L->d_rpoly;
+    }
     D.type = L->type;
     D.n_s = L->n_s;
     D.shared = L->shared;
@@ -271,6 +291,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_gain);
     cudaFree(lrf->d_cogw);
     cudaFree(lrf->d_coef2);
+    cudaFree(lrf->d_rpoly);
     delete lrf;
 }
 

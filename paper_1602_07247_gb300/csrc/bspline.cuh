@@ -39,18 +39,15 @@ __device__ __forceinline__ bool in_box(const LrfDev &L, float x, float y, float 
     return ok;
 }
 
-// axial LRF of sensor i at distance r (caller checks r <= hi)
+// axial LRF of sensor i at distance r (caller checks r <= hi): the span's
+// cubic in the power basis of its local parameter, by Horner's rule
 __device__ __forceinline__ float radial_eta(const LrfDev &L, int i, float r)
 {
-    float t, w[4];
-    int j = bs_span(r, 0.0f, L.inv_h[0], L.n_int[0], t);
-    bs_weights(t, w);
-    const float *c = L.coef + (L.shared ? 0 : i * L.n_coef) + j;
-    float f = c[0] * w[0];
-    f = fmaf(c[1], w[1], f);
-    f = fmaf(c[2], w[2], f);
-    f = fmaf(c[3], w[3], f);
-    return L.gain[i] * f;
+    float t;
+    const int j = bs_span(r, 0.0f, L.inv_h[0], L.n_int[0], t);
+    const float4 p = __ldg(L.rpoly + (L.shared ? 0 : i * L.n_int[0]) + j);
+    const float f = fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
+    return __ldg(L.gain + i) * f;
 }
 
 // eta_i at one point; ok = false outside the domain (used by the evaluation

@@ -272,6 +272,55 @@ __device__ __forceinline__ void event_epilogue(const CgsArgs &a, long e, const f
     __syncwarp();
 }
 
+// Scores of a radial-LRF grid, NPL nodes per lane at a time sharing each
+// sensor's data; per (node, sensor) the same operations in the same order as
+// node_score.  Updates the lane's best (score, node).
+template <int NPL>
+__device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, const float *s_sig, const float *s_ic,
+                                             const float *s_ec, float S, float inv_hc, float cx, float cy, float sxy,
+                                             int nodes, int lane, float &bestF, int &bestk)
+{
+    const int c_xy = (a.n_xy - 1) / 2;
+    const float hi = L.hi[0];
+    for (int k0 = 0; k0 < nodes; k0 += 32 * NPL) {
+        float xs[NPL], ys[NPL], acc[NPL], dh[NPL];
+        bool ok[NPL];
+#pragma unroll
+        for (int m = 0; m < NPL; ++m) {
+            const int k = k0 + lane + 32 * m;
+            const int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy;
+            xs[m] = fmaf((float)(ix - c_xy), sxy, cx);
+            ys[m] = fmaf((float)(iy - c_xy), sxy, cy);
+            acc[m] = dh[m] = 0.0f;
+            ok[m] = true;
+        }
+        for (int i = 0; i < L.n_s; ++i) {
+            const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
+            const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) {
+                const float dx = xs[m] - sx, dy = ys[m] - sy;
+                const float r = sqrtf(fmaf(dx, dx, dy * dy));
+                ok[m] = ok[m] && r <= hi;
+                const float eta = fmaxf(radial_eta(L, i, fminf(r, hi)), kEtaFloor);
+                acc[m] = fmaf(si, __log2f(eta * ici), acc[m]);
+                dh[m] += eta - eci;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NPL; ++m) {
+            const int k = k0 + lane + 32 * m;
+            if (k < nodes) {
+                const float F = ok[m] ? acc[m] - S * (log1pf(dh[m] * inv_hc) * 1.4426950408889634f) : -INFINITY;
+                if (F > bestF) {
+                    bestF = F;
+                    bestk = k;
+                }
+            }
+        }
+    }
+}
+
 // Reconstruct event e of a (one warp; s_sig, s_ic, s_ec: 3 n_s floats of
 // this warp's shared memory), every node evaluated on its own.  Shared by the
 // plain and the batched kernels.
@@ -289,15 +338,24 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
         const float inv_hc = centre_values<TYPE>(L, s_ic, s_ec, cx, cy, cz, lane);
         float bestF = -INFINITY;
         int bestk = 0x7fffffff;
-        for (int k = lane; k < nodes; k += 32) {
-            int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
-            float x = fmaf((float)(ix - c_xy), sxy, cx);
-            float y = fmaf((float)(iy - c_xy), sxy, cy);
-            float z = fmaf((float)(iz - c_z), sz, cz);
-            float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
-            if (F > bestF) {
-                bestF = F;
-                bestk = k;
+        if (TYPE == ANTS_LRF_RADIAL) {
+            // a lane's nodes share each sensor's data (3 per lane covers a
+            // 9 x 9 grid in one pass, 4 per lane larger grids)
+            if (nodes <= 96)
+                radial_nodes<3>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk);
+            else
+                radial_nodes<4>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk);
+        } else {
+            for (int k = lane; k < nodes; k += 32) {
+                int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
+                float x = fmaf((float)(ix - c_xy), sxy, cx);
+                float y = fmaf((float)(iy - c_xy), sxy, cy);
+                float z = fmaf((float)(iz - c_z), sz, cz);
+                float F = node_score<TYPE>(L, s_sig, s_ic, s_ec, S, inv_hc, x, y, z);
+                if (F > bestF) {
+                    bestF = F;
+                    bestk = k;
+                }
             }
         }
         pick_and_move(a, e, it, bestF, bestk, cx, cy, cz, sxy, sz, lane);
