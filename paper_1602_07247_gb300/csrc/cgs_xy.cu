@@ -31,7 +31,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
 constexpr float kInvLn2 = 1.4426950408889634f;
-constexpr int kXyThreads = 384;  // 12 warps per block, one block per SM
+constexpr int kXyThreads = 512;  // 16 warps per block, one block per SM
 constexpr int kPPL = 3;          // sensor pairs in flight per lane
 
 struct XyArgs {
@@ -127,14 +127,20 @@ __device__ __forceinline__ void team_sync(int team)
 
 // per-team shared-memory layout (floats): signals, 1/eta_c, eta_c [n_pad each],
 // row bases as duplicated pairs [N][8] (16-byte aligned) and iy [N], partial
-// sums acc [N][LT+N] then dH [N][LT+N] (row stride = N mod 32: a warp of node
-// threads reads 32 different banks), reduction scratch [32]
+// sums acc then dH, reduction scratch [32].  Teams of several warps keep one
+// partial per grid row, warp and grid column ([N][warps][N]: the lanes of a
+// warp that share a column are summed by shuffles first); one-warp teams keep
+// one per grid row and lane ([N][LT+N]: row stride N mod 32, so a warp of node
+// threads reads 32 different banks)
 // (disjoint slots per phase: argmax 0..7, centre H 8..11, final H 12..15,
 // prologue sums 16..31, final logL 16..19)
 struct TeamSmem {
     int n_pad, part_stride;
     // the one place the layout is defined, for the launcher and the kernel
-    __device__ __host__ static TeamSmem make(int n_pad, int lt, int n) { return TeamSmem{n_pad, lt + n}; }
+    __device__ __host__ static TeamSmem make(int n_pad, int lt, int n)
+    {
+        return TeamSmem{n_pad, lt > 32 ? (lt / 32) * n : lt + n};
+    }
     __device__ __host__ int sig() const { return 0; }
     __device__ __host__ int ic() const { return n_pad; }
     __device__ __host__ int ec() const { return 2 * n_pad; }  // holds -eta_c
@@ -183,6 +189,9 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     const int q = t / N, j = t - q * N;
     const bool active = q < Q;
     const int pairs_mine = active ? (n_pairs - q + Q - 1) / Q : 0;  // pairs q, q+Q, ... below n_pairs
+    // every lane runs the same number of pair groups (the shuffles of the
+    // partial sums need the whole warp); missing pairs contribute zero
+    const int group_end = ((n_pairs + Q - 1) / Q + kPPL - 1) / kPPL * kPPL;
     const float qnan = __int_as_float(0x7fc00000);
     const long team_stride = (long)gridDim.x * teams_per_block;
 
@@ -301,14 +310,8 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             for (int b = 0; b < 4; ++b) wx2[b] = make_float2(wxs[b], wxs[b]);
             const int ps = lay.part_stride;
             const int sy = L.stride_y;
-            if (active && pairs_mine == 0) {
-                for (int k = 0; k < N; ++k) {
-                    s_part[k * ps + t] = 0.0f;
-                    s_part[(N + k) * ps + t] = 0.0f;
-                }
-            }
             const unsigned rowb = (unsigned)sy * 8u;  // bytes per table row
-            for (int g = 0; g < pairs_mine; g += kPPL) {
+            for (int g = 0; g < group_end; g += kPPL) {
                 const float2 *gb[kPPL];
                 unsigned sb[kPPL];
                 float2 sp[kPPL], ic[kPPL], nec[kPPL];
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
 #pragma unroll
                 for (int m = 0; m < kPPL; ++m) {
                     on[m] = g + m < pairs_mine;
-                    const int p = q + (on[m] ? g + m : g) * Q;
+                    const int p = on[m] ? q + (g + m) * Q : 0;  // any valid pair when missing
                     gb[m] = coef2 + (size_t)p * L.pair_stride + ix;
                     sb[m] = SMEM ? (unsigned)__cvta_generic_to_shared(gb[m]) : 0u;
                     sp[m] = on[m] ? s_sig2[p] : make_float2(0.0f, 0.0f);
@@ -387,13 +390,29 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                         if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
                     }
                     float va = acc.x + acc.y, vd = dh.x + dh.y;
-                    float *pa = s_part + k * ps + t, *pd = s_part + (N + k) * ps + t;
-                    if (g > 0) {
-                        va += *pa;
-                        vd += *pd;
+                    if (TEAM > 1) {
+                        // lanes l, l+N, l+2N, ... of a warp share grid column j:
+                        // lane l < N adds the lanes' own values
+                        const float a0 = va, d0 = vd;
+#pragma unroll
+                        for (int o = N; o < 32; o += N) {
+                            const float xa = __shfl_down_sync(kFull, a0, o), xd = __shfl_down_sync(kFull, d0, o);
+                            if (lane + o < 32) {
+                                va += xa;
+                                vd += xd;
+                            }
+                        }
                     }
-                    *pa = va;
-                    *pd = vd;
+                    if (TEAM == 1 || lane < N) {
+                        const int slot = TEAM > 1 ? wit * N + j : t;
+                        float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
+                        if (g > 0) {
+                            va += *pa;
+                            vd += *pd;
+                        }
+                        *pa = va;
+                        *pd = vd;
+                    }
                 }
             }
             team_sync<TEAM>(team);
@@ -404,10 +423,13 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             for (int node = t; node < N * N; node += LT) {
                 const int k = node / N, jj = node - k * N;
                 float sa = 0.0f, sd = 0.0f;
+                // the partials of the warps (teams of several warps) or of the
+                // sensor slots (one-warp teams) of this node's column
+                constexpr int NPART = TEAM > 1 ? TEAM : Q;
 #pragma unroll 4
-                for (int qq = 0; qq < Q; ++qq) {
-                    sa += s_part[k * lay.part_stride + qq * N + jj];
-                    sd += s_part[(N + k) * lay.part_stride + qq * N + jj];
+                for (int w = 0; w < NPART; ++w) {
+                    sa += s_part[k * lay.part_stride + w * N + jj];
+                    sd += s_part[(N + k) * lay.part_stride + w * N + jj];
                 }
                 const float xn = fmaf((float)(jj - C), sxy, cx);
                 const float yn = fmaf((float)(k - C), sxy, cy);
