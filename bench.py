@@ -48,10 +48,10 @@ def alu_roofline(evals_per_s: float, kind: str) -> dict:
             "peak_kind": f"min({SM_COUNT} SMs x {FMA_PER_CLK_SM} FMA/clk x {clk / 1e6:.0f} MHz / {F_FMA[kind]} FMA "
                          f"per evaluation, {SM_COUNT} x {MUFU_PER_CLK_SM} log2/clk x {clk / 1e6:.0f} MHz); "
                          f"{pk_kind} max clock"}
-# DRAM bytes (read + write) per event of the headline kernel, from the ncu
-# capture summarised in profiles/cgs_xy_sipm8x8_xy.md (600 000 events:
-# 155.88 MB read + 10.37 MB written); None once the kernel changes.
-XY_TRAFFIC_PER_EVENT = (155.879936e6 + 10.371328e6) / 600_000
+# DRAM bytes (read + write) per event of the headline kernel, from one ncu
+# capture of it on 600 000 events of the same workload (156.07 MB read +
+# 9.98 MB written); None once the kernel changes.
+XY_TRAFFIC_PER_EVENT = (156.071680e6 + 9.976064e6) / 600_000
 
 
 def peaks():
