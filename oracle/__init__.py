@@ -494,3 +494,160 @@ def logtable(lrf: Lrf, nx: int, ny: int, mutant: int = 0):
     m = np.empty(lrf.n_sensors)
     L.or_logtable(C.byref(s), int(nx), int(ny), _d(T), _d(m))
     return T, m
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.2 event filters and Sec. 8 iterative LRF reconstruction
+# --------------------------------------------------------------------------
+
+
+class _Filter(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("chi2_max", "e_lo", "e_hi", "sum_lo", "sum_hi", "r_max", "cx", "cy")]
+
+
+@dataclass
+class EventCuts:
+    """The cuts of Sec. 5.2 used between cycles.  chi2_max and r_max are off
+    when <= 0; an energy or signal-sum window is off when its upper bound is
+    not above its lower bound."""
+
+    chi2_max: float = 0.0
+    e_lo: float = 0.0
+    e_hi: float = 0.0
+    sum_lo: float = 0.0
+    sum_hi: float = 0.0
+    r_max: float = 0.0
+    cx: float = 0.0
+    cy: float = 0.0
+
+    def _struct(self) -> _Filter:
+        return _Filter(self.chi2_max, self.e_lo, self.e_hi, self.sum_lo, self.sum_hi, self.r_max, self.cx, self.cy)
+
+
+def _ilib(mutant=0):
+    L = _slib(mutant)
+    if not getattr(L, "_it_declared", False):
+        L.or_chi2_at.argtypes = [C.POINTER(_Lrf), C.c_long, _D, _D, _D, _D]
+        L.or_event_filter.argtypes = [C.c_long, _I, _D, _D, _D, _D, C.POINTER(_Filter), _I]
+        L.or_shift_xy.argtypes = [C.c_uint64, C.c_int, C.c_long, C.POINTER(C.c_long), C.c_double, _D]
+        L.or_gain_refit.argtypes = [C.c_int, C.c_double, C.c_double, _D, C.c_long, C.c_int, _D, _D, _D]
+        L._it_declared = True
+    return L
+
+
+def chi2_at(lrf: Lrf, sig, xyz, E, mutant: int = 0) -> np.ndarray:
+    """Reduced Pearson chi-squared of each event at (xyz, E) (Sec. 5.2)."""
+    sig, xyz, E = _f64(sig), _f64(xyz), _f64(E)
+    s = lrf._struct()
+    out = np.empty(sig.shape[0])
+    _ilib(mutant).or_chi2_at(C.byref(s), sig.shape[0], _d(sig), _d(xyz), _d(E), _d(out))
+    return out
+
+
+def event_filter(status, xyz, E, chi2, ssum, cuts: EventCuts, mutant: int = 0) -> np.ndarray:
+    """Boolean keep mask of the Sec. 5.2 cuts."""
+    st = np.ascontiguousarray(np.asarray(status, dtype=np.int32))
+    xyz, E, chi2, ssum = _f64(xyz), _f64(E), _f64(chi2), _f64(ssum)
+    keep = np.empty(st.shape[0], dtype=np.int32)
+    f = cuts._struct()
+    _ilib(mutant).or_event_filter(st.shape[0], _i(st), _d(xyz), _d(E), _d(chi2), _d(ssum), C.byref(f), _i(keep))
+    return keep.astype(bool)
+
+
+def shift_xy(seed: int, cycle: int, events, sigma: float, mutant: int = 0) -> np.ndarray:
+    """Seeded normal offsets [k, 2] of standard deviation sigma for the given
+    event indices (Sec. 8 random shift)."""
+    ev = np.ascontiguousarray(np.asarray(events, dtype=np.int64))
+    out = np.empty((ev.shape[0], 2))
+    _ilib(mutant).or_shift_xy(int(seed), int(cycle), ev.shape[0], ev.ctypes.data_as(C.POINTER(C.c_long)),
+                              float(sigma), _d(out))
+    return out
+
+
+def gain_refit(n_int: int, lo: float, hi: float, coef, r, v, mutant: int = 0) -> np.ndarray:
+    """Least-squares relative gains with a fixed radial profile (Sec. 6.3);
+    r, v: [n_e, n_s]."""
+    r, v, coef = _f64(r), _f64(v), _f64(coef).ravel()
+    g = np.empty(r.shape[1])
+    _ilib(mutant).or_gain_refit(int(n_int), float(lo), float(hi), _d(coef), r.shape[0], r.shape[1], _d(r), _d(v),
+                                _d(g))
+    return g
+
+
+def lrf_refit(lrf: Lrf, sig, xyz, E, shared=None, refit_gains: bool = False, ridge: float = 0.0,
+              mutant: int = 0) -> Lrf:
+    """LRFs refitted to the signals of reconstructed events (Sec. 6: LRFs
+    from (position, signal) data; Sec. 8: the positions are reconstructed).
+    Each event e gives, for every sensor i, the value v_ei = s_ei / E_e at its
+    position.  XY / XYZ: one least-squares fit with the points (x, y[, z]) and
+    one value column per sensor.  RADIAL grouped (Sec. 6.2): one fit of the
+    profile to every (r_ei, v_ei / g_i), g_i the group's current gains; with
+    refit_gains the gains are then refitted with the new profile fixed
+    (Sec. 6.3) and scaled to mean 1, the profile taking the inverse factor so
+    that g_i f is unchanged.  RADIAL per sensor: one fit of (r_ei, v_ei) per
+    sensor, gains 1.  The knot grid is the input's; `shared` (default: the
+    input's) selects grouped or per-sensor output for RADIAL."""
+    sig, xyz, E = _f64(sig), _f64(xyz), _f64(E)
+    shared = lrf.shared if shared is None else bool(shared)
+    v = sig / E[:, None]
+    n_s = lrf.n_sensors
+    if lrf.type != RADIAL:
+        dims = 2 if lrf.type == XY else 3
+        coef, _, _ = lrf_fit(lrf.n_int, lrf.lo, lrf.hi, xyz[:, :dims], v, ridge, mutant)
+        return Lrf(lrf.type, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, coef)
+    d = xyz[:, None, :2] - lrf.sensor_xy[None, :, :]
+    r = np.sqrt(d[..., 0] ** 2 + d[..., 1] ** 2)
+    if not shared:
+        coef = np.concatenate([lrf_fit(lrf.n_int, lrf.lo, lrf.hi, r[:, i], v[:, i], ridge, mutant)[0]
+                               for i in range(n_s)])
+        return Lrf(RADIAL, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, coef, shared=False)
+    g = np.ones(n_s) if lrf.gain is None or not lrf.shared else _f64(lrf.gain)
+    coef, _, _ = lrf_fit(lrf.n_int, lrf.lo, lrf.hi, r.reshape(-1), (v / g[None, :]).reshape(-1), ridge, mutant)
+    if refit_gains:
+        g = gain_refit(lrf.n_int[0], lrf.lo[0], lrf.hi[0], coef, r, v, mutant)
+        gm = g.mean()
+        g = g / gm
+        coef = coef * gm
+    return Lrf(RADIAL, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, coef, shared=True, gain=g.copy())
+
+
+def centroid_lrf(lrf: Lrf, sig, gain_cog=None, shared=None, ridge: float = 0.0, mutant: int = 0) -> Lrf:
+    """Initial LRFs without a known response (Sec. 8): every event at its
+    centroid position (Sec. 5.1.1) with E = the sum of its signals, refitted
+    on `lrf`'s knot grid (gains of a radial group start at 1)."""
+    sig = _f64(sig)
+    xy = cog(sig, lrf.sensor_xy, gain_cog, mutant)
+    S = sig.sum(axis=1)
+    ok = np.isfinite(xy).all(axis=1) & (S > 0)
+    xyz = np.concatenate([xy, np.zeros((xy.shape[0], 1))], axis=1)
+    base = Lrf(lrf.type, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, lrf.coef, shared=lrf.shared,
+               gain=np.ones(lrf.n_sensors) if lrf.type == RADIAL else None)
+    return lrf_refit(base, sig[ok], xyz[ok], S[ok], shared, False, ridge, mutant)
+
+
+def lrf_iterate(lrf0: Lrf, params: CgsParams, sig, cycles: int, cuts: EventCuts, shift_sigma: float = 0.0,
+                shift_cycles: int = 0, seed: int = 0, refit_gains: bool = False, gain_cog=None,
+                ridge: float = 0.0, mutant: int = 0):
+    """Iterative LRF reconstruction from flood data (Sec. 8).  Each cycle:
+    reconstruct every event with the current LRFs (contracting grids,
+    Sec. 5.1.2.2), keep the events that pass the cuts (Sec. 5.2), offset the
+    kept positions by seeded normal shifts during the first shift_cycles
+    cycles, and refit the LRFs from the kept events (lrf_refit).  Returns the
+    final LRFs and per-cycle statistics (events kept, their mean chi2 and
+    mean energy)."""
+    sig = _f64(sig)
+    L = lrf0
+    stats = []
+    ssum = sig.sum(axis=1)
+    for c in range(cycles):
+        r = cgs(L, params, sig, gain_cog=gain_cog, mutant=mutant)
+        chi2 = chi2_at(L, sig, r["xyz"], r["E"], mutant)
+        keep = event_filter(r["status"], r["xyz"], r["E"], chi2, ssum, cuts, mutant)
+        idx = np.nonzero(keep)[0]
+        xyz = r["xyz"][idx].copy()
+        if c < shift_cycles and shift_sigma > 0.0:
+            xyz[:, :2] += shift_xy(seed, c, idx, shift_sigma, mutant)
+        stats.append(dict(n_kept=int(idx.size), mean_chi2=float(chi2[idx].mean()) if idx.size else float("nan"),
+                          mean_E=float(r["E"][idx].mean()) if idx.size else float("nan")))
+        L = lrf_refit(L, sig[idx], xyz, r["E"][idx], None, refit_gains, ridge, mutant)
+    return L, stats

@@ -1094,3 +1094,121 @@ void or_logtable(const or_lrf *L, int nx, int ny, double *T, double *m)
         for (long g = 0; g < G; ++g) T[g * n + i] -= m[i];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Event filters (Sec. 5.2) and the steps of iterative LRF reconstruction    */
+/* (Sec. 8: reconstruct a flood dataset, discard badly reconstructed events, */
+/* refit the LRFs from the reconstructed positions, repeat; Sec. 6.3: refit  */
+/* the relative gains of a group with its LRF profile fixed)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Chi-squared of a reconstruction, one of the quantities Sec. 5.2 filters
+ * on.  Reading: Pearson's statistic of the signals against the mean counts
+ * mu_i = E eta_i(x, y, z) at the reconstructed point, over the sensors with
+ * mu_i > 0, divided by the degrees of freedom n_s - 3 (x, y and E fitted;
+ * 1 when n_s <= 3).  NaN when the position or E is not finite. */
+void or_chi2_at(const or_lrf *L, long n_e, const double *sig, const double *xyz, const double *E, double *chi2)
+{
+    int n = L->n_sensors;
+    double dof = n > 3 ? (double)(n - 3) : 1.0;
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < n_e; ++e) {
+        double x = xyz[3 * e], y = xyz[3 * e + 1], z = xyz[3 * e + 2], En = E[e];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(En)) {
+            chi2[e] = NAN;
+            continue;
+        }
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            int ok;
+            double mu = En * or_lrf_eta(L, i, x, y, z, &ok);
+            if (!ok || !(mu > 0.0)) continue;
+            double d = sig[e * n + i] - mu;
+#if OR_MUTANT == 13
+            acc += d * d;
+#else
+            acc += d * d / mu;
+#endif
+        }
+        chi2[e] = acc / dof;
+    }
+}
+
+/* The cuts of Sec. 5.2 used by the iterative procedure; a cut whose upper
+ * bound is not above its lower bound (or whose maximum is <= 0) is off. */
+typedef struct {
+    double chi2_max;       /* chi2 <= chi2_max */
+    double e_lo, e_hi;     /* e_lo <= E <= e_hi */
+    double sum_lo, sum_hi; /* sum_lo <= sum of signals <= sum_hi */
+    double r_max, cx, cy;  /* (x - cx)^2 + (y - cy)^2 <= r_max^2 */
+} or_filter;
+
+/* keep[e] = 1 when event e was reconstructed (status OK, finite position,
+ * energy and chi2) and passes every active cut. */
+void or_event_filter(long n_e, const int *status, const double *xyz, const double *E, const double *chi2,
+                     const double *sum, const or_filter *F, int *keep)
+{
+    for (long e = 0; e < n_e; ++e) {
+        double x = xyz[3 * e], y = xyz[3 * e + 1], z = xyz[3 * e + 2];
+        int k = status[e] == OR_EVT_OK && isfinite(x) && isfinite(y) && isfinite(z) && isfinite(E[e]) &&
+                isfinite(chi2[e]);
+        if (k && F->chi2_max > 0.0) k = chi2[e] <= F->chi2_max;
+        if (k && F->e_hi > F->e_lo) k = E[e] >= F->e_lo && E[e] <= F->e_hi;
+        if (k && F->sum_hi > F->sum_lo) k = sum[e] >= F->sum_lo && sum[e] <= F->sum_hi;
+        if (k && F->r_max > 0.0) {
+            double dx = x - F->cx, dy = y - F->cy;
+            k = dx * dx + dy * dy <= F->r_max * F->r_max;
+        }
+        keep[e] = k;
+    }
+}
+
+/* Random shift of reconstructed positions before a refit (Sec. 8: a small
+ * random shift helps the first iterations).  Reading: a normal pair of
+ * standard deviation sigma per event, by the Box-Muller transform of the
+ * first two uniforms of the Philox block at counter (e_lo, e_hi, 0xFFFFFFFE,
+ * cycle) under key `seed`; e is the event's index in the flood dataset. */
+void or_shift_xy(uint64_t seed, int cycle, long n, const long *event, double sigma, double *dxy)
+{
+    for (long k = 0; k < n; ++k) {
+        uint64_t e = (uint64_t)event[k];
+        uint32_t w[4];
+        or_philox_block(seed, (uint32_t)e, (uint32_t)(e >> 32), 0xFFFFFFFEu, (uint32_t)cycle, w);
+        double ua = or_u01(w[0]), ub = or_u01(w[1]);
+        double rho = sqrt(-2.0 * log(ua)), th = 6.283185307179586 * ub;
+        dxy[2 * k] = sigma * rho * cos(th);
+#if OR_MUTANT == 14
+        dxy[2 * k + 1] = sigma * rho * cos(th);
+#else
+        dxy[2 * k + 1] = sigma * rho * sin(th);
+#endif
+    }
+}
+
+/* Relative gains of one group with its profile f fixed (Sec. 6.3): g_i
+ * minimises sum_e (v_ei - g_i f(r_ei))^2 over the samples of sensor i with
+ * r_ei inside the profile's domain, so g_i = sum f v / sum f^2.
+ * r, v: [n_e][n_s]; coef: the profile's n_int + 3 coefficients.  A sensor
+ * without samples (sum f^2 = 0) gets g_i = NaN. */
+void or_gain_refit(int n_int, double lo, double hi, const double *coef, long n_e, int n_s, const double *r,
+                   const double *v, double *g)
+{
+    for (int i = 0; i < n_s; ++i) {
+        double fv = 0.0, ff = 0.0;
+        for (long e = 0; e < n_e; ++e) {
+            double B[4];
+            int j0 = or_bspline_basis4(n_int, lo, hi, r[e * n_s + i], B);
+            if (j0 < 0) continue;
+            double f = 0.0;
+            for (int a = 0; a < 4; ++a) f += coef[j0 + a] * B[a];
+#if OR_MUTANT == 15
+            fv += f * v[e * n_s + i];
+            ff += f;
+#else
+            fv += f * v[e * n_s + i];
+            ff += f * f;
+#endif
+        }
+        g[i] = ff > 0.0 ? fv / ff : NAN;
+    }
+}

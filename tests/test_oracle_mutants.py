@@ -18,6 +18,9 @@ MUTANTS = {
     10: "GELU with erf(x) instead of erf(x / sqrt 2)",
     11: "loss gradient missing the factor 2",
     12: "disk sources with radius extent*u instead of extent*sqrt(u)",
+    13: "chi-squared terms without the division by the mean count",
+    14: "random shift with cos for both components",
+    15: "gain refit dividing by sum f instead of sum f^2",
 }
 
 
