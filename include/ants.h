@@ -183,6 +183,51 @@ typedef struct {
     int border_fallback;
 } ants_mlp_seeded_params;
 
+/* Event cuts (Sec. 5.2: events are filtered on the reconstruction's
+ * chi-squared, its energy, the sum of the signals and the position; Sec. 8:
+ * the iterative procedure discards badly reconstructed events with them).
+ * A cut is off when chi2_max <= 0, r_max <= 0, or a window's upper bound is
+ * not above its lower bound.  Bounds are inclusive; comparisons are made in
+ * FP64 on the FP32 values. */
+typedef struct {
+    double chi2_max;       /* chi2 <= chi2_max */
+    double e_lo, e_hi;     /* e_lo <= E <= e_hi */
+    double sum_lo, sum_hi; /* sum_lo <= sum of the signals <= sum_hi */
+    double r_max, cx, cy;  /* (x - cx)^2 + (y - cy)^2 <= r_max^2 */
+} ants_event_cuts;
+
+/* LRF refit from reconstructed events (ants_lrf_refit). */
+typedef struct {
+    int shared;          /* RADIAL: 1 one group (a profile times per-sensor gains, Sec. 6.2), 0 per sensor */
+    int refit_gains;     /* RADIAL group: refit the gains with the new profile fixed (Sec. 6.3) */
+    double shift_sigma;  /* > 0: add normal offsets of this standard deviation (mm) to x and y (Sec. 8) */
+    uint64_t seed;       /* Philox key of the offsets */
+    int cycle;           /* counter word of the offsets (the cycle number of an iteration) */
+    double ridge;        /* as ants_lrf_fit */
+} ants_refit_params;
+
+/* Iterative LRF reconstruction (ants_lrf_iterate, Sec. 8). */
+typedef struct {
+    ants_cgs_params cgs;   /* the reconstruction of every cycle (plain contracting grids) */
+    int cycles;            /* >= 1 */
+    ants_event_cuts cuts;
+    int refit_gains;       /* RADIAL group: refit the gains every cycle */
+    double shift_sigma;    /* random shift (mm) of the kept positions ... */
+    int shift_cycles;      /* ... during the first shift_cycles cycles */
+    uint64_t seed;
+    double ridge;
+} ants_iter_params;
+
+/* Per-cycle record of ants_lrf_iterate. */
+typedef struct {
+    long n_kept;            /* events that passed the cuts and entered the refit */
+    double mean_chi2;       /* their mean chi-squared (under the cycle's input LRFs) */
+    double mean_E;          /* their mean energy */
+    double rel_change;      /* relative RMS change of the LRFs where the data are:
+                               sqrt(sum (eta_new - eta_old)^2 / sum eta_old^2) over the kept
+                               events (at their reconstructed positions) and all sensors */
+} ants_iter_stats;
+
 /* ------------------------------------------------------------------------ */
 /* Library and context                                                        */
 /* ------------------------------------------------------------------------ */
@@ -275,6 +320,11 @@ ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, con
  * *n_coef_out (nullable) receive the shape.  Errors: ANTS_E_ARG. */
 ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_t count,
                                    int *n_sets_out, int *n_coef_out);
+
+/* Copy the per-sensor gain factors ([n_sensors]: a RADIAL LRF's factors,
+ * 1 otherwise) to gain_host; `count` is the capacity in doubles and must be
+ * >= n_sensors.  Errors: ANTS_E_ARG. */
+ANTS_API int ants_lrf_gains(const ants_lrf *lrf, double *gain_host, size_t count);
 
 /* Evaluate eta_i at n_pts points for all sensors: pts_dev[n_pts][dim] FP32
  * (dim = 2 for RADIAL/XY, 3 for XYZ), out_dev[n_pts][n_sensors] FP32.
@@ -536,6 +586,75 @@ ANTS_API int ants_reconstruct_host_noalloc(ants_ctx *ctx, const ants_lrf *lrf, i
                                            int signal_dtype, long n_events, int n_sensors,
                                            const float *start_xyz_host, float *xyz_host,
                                            float *E_host, float *logL_host, int32_t *status_host);
+
+/* ------------------------------------------------------------------------ */
+/* Event filters (Sec. 5.2) and iterative LRF reconstruction (Sec. 8)         */
+/* ------------------------------------------------------------------------ */
+
+/* Centroid position (Sec. 5.1.1: x = sum X_i s_i/g_i / sum s_i/g_i with the
+ * detector's relative gains g_i, sensor positions X_i) and the sum of the
+ * signals of each event, as the start of an iterative reconstruction when no
+ * LRF is known yet.  signals_dev [n_events][n_s] FP32; xyz_dev [n_events][3]
+ * receives (x, y, 0) (NaN when the weighted sum is not > 0); sum_dev
+ * [n_events] (nullable).  Accumulates in FP64.  Asynchronous on `stream`.
+ * Errors: ANTS_E_ARG, ANTS_E_CUDA. */
+ANTS_API int ants_event_centroid(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
+                                 float *xyz_dev, float *sum_dev, void *stream);
+
+/* Chi-squared of each event's reconstruction (Sec. 5.2): Pearson's
+ * statistic sum_i (s_i - mu_i)^2 / mu_i with mu_i = E eta_i(xyz), over the
+ * sensors with mu_i > 0, divided by n_s - 3 (x, y, E fitted; 1 when
+ * n_s <= 3); NaN when the position or E is not finite.  eta in FP32, the sum
+ * in FP64, stored as FP32.  sum_dev (nullable) receives the sum of the
+ * signals.  Asynchronous on `stream`.  Errors: ANTS_E_ARG, ANTS_E_CUDA. */
+ANTS_API int ants_event_chi2(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
+                             const float *xyz_dev, const float *E_dev, float *chi2_dev, float *sum_dev,
+                             void *stream);
+
+/* Select the events that were reconstructed (status ANTS_EVT_OK, finite
+ * position, E and chi2) and pass every active cut.  index_dev (capacity
+ * n_events) receives the kept event indices in increasing order and
+ * *n_kept_host their number.  sum_dev may be NULL when the signal-sum cut is
+ * off.  Waits for the count (synchronises `stream`).
+ * Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_event_filter(ants_ctx *ctx, long n_events, const int32_t *status_dev, const float *xyz_dev,
+                               const float *E_dev, const float *chi2_dev, const float *sum_dev,
+                               const ants_event_cuts *cuts, int32_t *index_dev, long *n_kept_host, void *stream);
+
+/* Refit `lrf` from reconstructed events (Sec. 6: LRFs from (position,
+ * signal) data; Sec. 8: the positions are reconstructed ones).  The events
+ * are index_dev[0..n_kept) (NULL: all n_events in order); event e gives the
+ * value v_ei = s_ei / E_e of sensor i at its position, after adding the
+ * seeded normal offset of (seed, cycle, e) to x and y when shift_sigma > 0
+ * (Philox4x32-10 block at counter (e_lo, e_hi, 0xFFFFFFFE, cycle), Box-Muller
+ * of its first two words, FP64).
+ *   XY / XYZ: one FP64 least-squares fit, points (x, y[, z]), one value
+ *     column per sensor.
+ *   RADIAL with p->shared: one fit of the profile to every (r_ei, v_ei/g_i),
+ *     r_ei the distance to sensor i, g_i the input's gains; with
+ *     p->refit_gains the gains are then refitted with the new profile fixed,
+ *     g_i = sum f(r) v / sum f(r)^2 (Sec. 6.3), and scaled to mean 1, the
+ *     profile taking the inverse factor.
+ *   RADIAL without p->shared: one fit of (r_ei, v_ei) per sensor, gains 1.
+ * The output has the input's knot grid, sensors and relative gains.
+ * Synchronous.  Errors: ANTS_E_ARG, ANTS_E_LRF (a fit stayed singular, e.g.
+ * no events), ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_refit(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
+                            const float *xyz_dev, const float *E_dev, const int32_t *index_dev, long n_kept,
+                            const ants_refit_params *p, ants_lrf **out);
+
+/* Iterative LRF reconstruction from flood data (Sec. 8): starting from
+ * lrf_init, each of p->cycles cycles reconstructs all events with the current
+ * LRFs (ants_reconstruct, ANTS_CGS_PLAIN, p->cgs), computes their
+ * chi-squared, keeps the events that pass p->cuts and refits the LRFs from
+ * them (ants_lrf_refit with the input's grouping, p->refit_gains, the shift
+ * during the first p->shift_cycles cycles with cycle = the cycle number, and
+ * p->ridge).  stats_host (nullable) receives p->cycles records.  *out is a
+ * new LRF set; lrf_init is not modified.  Synchronous; all work runs on the
+ * context's first stream.  Errors: as the calls above; ANTS_E_LRF when a
+ * cycle keeps no event. */
+ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init, const float *signals_dev, long n_events,
+                              const ants_iter_params *p, ants_iter_stats *stats_host, ants_lrf **out);
 
 /* Number of kernels the calling thread's last successful ants_* call
  * launched (for accounting in benchmarks). */

@@ -82,7 +82,10 @@ class SimParams(C.Structure):
 
     def __init__(self, region="square", extent=10.0, cx=0.0, cy=0.0, z_lo=0.0, z_hi=0.0, e0=1000.0, e_spread=0.05,
                  spe_sigma=0.0):
-        super().__init__(0 if region == "disk" else 1, extent, cx, cy, z_lo, z_hi, e0, e_spread, spe_sigma)
+        codes = {"disk": 0, "square": 1, 0: 0, 1: 1}
+        if region not in codes:
+            raise ValueError(f"region must be 'disk' (0) or 'square' (1), not {region!r}")
+        super().__init__(codes[region], extent, cx, cy, z_lo, z_hi, e0, e_spread, spe_sigma)
 
 
 class BatchItem(C.Structure):
@@ -106,6 +109,29 @@ class SeededParams(C.Structure):
     """ants_mlp_seeded_params: network start, local refine, plain fallback."""
     _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
                 ("deviance_max", C.c_float), ("border_fallback", C.c_int)]
+
+
+class EventCuts(C.Structure):
+    """ants_event_cuts (Sec. 5.2): a cut is off when chi2_max <= 0, r_max <= 0
+    or its window's upper bound is not above its lower bound."""
+    _fields_ = [(n, C.c_double) for n in ("chi2_max", "e_lo", "e_hi", "sum_lo", "sum_hi", "r_max", "cx", "cy")]
+
+
+class RefitParams(C.Structure):
+    """ants_refit_params: grouping, gain refit, seeded shift, ridge."""
+    _fields_ = [("shared", C.c_int), ("refit_gains", C.c_int), ("shift_sigma", C.c_double), ("seed", C.c_uint64),
+                ("cycle", C.c_int), ("ridge", C.c_double)]
+
+
+class IterParams(C.Structure):
+    """ants_iter_params: the cycles of Sec. 8."""
+    _fields_ = [("cgs", CgsParams), ("cycles", C.c_int), ("cuts", EventCuts), ("refit_gains", C.c_int),
+                ("shift_sigma", C.c_double), ("shift_cycles", C.c_int), ("seed", C.c_uint64), ("ridge", C.c_double)]
+
+
+class IterStats(C.Structure):
+    _fields_ = [("n_kept", C.c_long), ("mean_chi2", C.c_double), ("mean_E", C.c_double),
+                ("rel_change", C.c_double)]
 
 
 _lib: C.CDLL | None = None
@@ -175,6 +201,15 @@ def lib() -> C.CDLL:
                                      C.POINTER(TrainReport)]
         L.ants_mlp_save.argtypes = [_VP, C.c_char_p]
         L.ants_mlp_load.argtypes = [_VP, C.c_char_p, C.POINTER(_VP)]
+        L.ants_lrf_gains.argtypes = [_VP, _DP, C.c_size_t]
+        L.ants_event_centroid.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP]
+        L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
+        L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
+                                        C.POINTER(C.c_long), _VP]
+        L.ants_lrf_refit.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, C.c_long, C.POINTER(RefitParams),
+                                     C.POINTER(_VP)]
+        L.ants_lrf_iterate.argtypes = [_VP, _VP, _VP, C.c_long, C.POINTER(IterParams), C.POINTER(IterStats),
+                                       C.POINTER(_VP)]
         _lib = L
     return _lib
 
@@ -294,6 +329,44 @@ def ants_lrf_coefficients(lrf: int) -> np.ndarray:
     out = np.empty((ns.value, nc.value))
     _check(lib().ants_lrf_coefficients(lrf, _dptr(out), out.size, None, None))
     return out
+
+
+def ants_lrf_gains(lrf: int, n_sensors: int) -> np.ndarray:
+    g = np.empty(n_sensors)
+    _check(lib().ants_lrf_gains(lrf, _dptr(g), n_sensors))
+    return g
+
+
+def ants_event_centroid(ctx: int, lrf: int, signals, xyz, ssum=None, stream=None) -> None:
+    _check(lib().ants_event_centroid(ctx, lrf, _tptr(signals), signals.shape[0], _tptr(xyz), _tptr(ssum),
+                                     _stream_handle(stream)))
+
+
+def ants_event_chi2(ctx: int, lrf: int, signals, xyz, E, chi2, ssum=None, stream=None) -> None:
+    _check(lib().ants_event_chi2(ctx, lrf, _tptr(signals), signals.shape[0], _tptr(xyz), _tptr(E), _tptr(chi2),
+                                 _tptr(ssum), _stream_handle(stream)))
+
+
+def ants_event_filter(ctx: int, status, xyz, E, chi2, ssum, cuts: EventCuts, index, stream=None) -> int:
+    n = C.c_long(0)
+    _check(lib().ants_event_filter(ctx, status.shape[0], _tptr(status), _tptr(xyz), _tptr(E), _tptr(chi2),
+                                   _tptr(ssum), C.byref(cuts), _tptr(index), C.byref(n), _stream_handle(stream)))
+    return int(n.value)
+
+
+def ants_lrf_refit(ctx: int, lrf: int, signals, xyz, E, index, n_kept: int, params: RefitParams) -> int:
+    h = _VP()
+    _check(lib().ants_lrf_refit(ctx, lrf, _tptr(signals), signals.shape[0], _tptr(xyz), _tptr(E), _tptr(index),
+                                n_kept, C.byref(params), C.byref(h)))
+    return h.value
+
+
+def ants_lrf_iterate(ctx: int, lrf: int, signals, params: IterParams):
+    stats = (IterStats * params.cycles)()
+    h = _VP()
+    _check(lib().ants_lrf_iterate(ctx, lrf, _tptr(signals), signals.shape[0], C.byref(params), stats, C.byref(h)))
+    return h.value, [dict(n_kept=s.n_kept, mean_chi2=s.mean_chi2, mean_E=s.mean_E, rel_change=s.rel_change)
+                     for s in stats]
 
 
 def ants_lrf_eval(lrf: int, pts, out, stream=None) -> None:
@@ -565,16 +638,20 @@ class Lrf:
     def __init__(self, ctx: Context, det: Detector, handle: int, type: int):
         self.ctx, self.det, self.handle, self.type = ctx, det, handle, type
         self.n_sensors = det.n_sensors
+        self.shared = False
 
     @classmethod
     def from_coefficients(cls, ctx, det, type, n_int, lo, hi, coef, shared=False, gain=None):
-        return cls(ctx, det, ants_lrf_create(ctx.handle, det.handle, type, n_int, lo, hi, shared, coef, gain), type)
+        L = cls(ctx, det, ants_lrf_create(ctx.handle, det.handle, type, n_int, lo, hi, shared, coef, gain), type)
+        L.shared = bool(shared)
+        return L
 
     @classmethod
     def fit(cls, ctx, det, type, n_int, lo, hi, pts, vals, shared=False, ridge=0.0):
         h, lam = ants_lrf_fit(ctx.handle, det.handle, type, n_int, lo, hi, shared, pts, vals, ridge)
         L = cls(ctx, det, h, type)
         L.ridge_used = lam
+        L.shared = bool(shared)
         return L
 
     @classmethod
@@ -588,6 +665,31 @@ class Lrf:
 
     def coefficients(self) -> np.ndarray:
         return ants_lrf_coefficients(self.handle)
+
+    def gains(self) -> np.ndarray:
+        return ants_lrf_gains(self.handle, self.n_sensors)
+
+    def refit(self, signals, xyz, E, index=None, n_kept=None, shared=None, refit_gains=False, shift_sigma=0.0,
+              seed=0, cycle=0, ridge=0.0) -> "Lrf":
+        """A new LRF set fitted to reconstructed events (ants_lrf_refit);
+        shared=None keeps this set's grouping."""
+        sh = self.shared if shared is None else bool(shared)
+        p = RefitParams(int(sh), int(refit_gains), float(shift_sigma), int(seed), int(cycle), float(ridge))
+        n = signals.shape[0] if index is None else (index.shape[0] if n_kept is None else n_kept)
+        L = Lrf(self.ctx, self.det, ants_lrf_refit(self.ctx.handle, self.handle, signals, xyz, E, index, n, p),
+                self.type)
+        L.shared = sh
+        return L
+
+    def iterate(self, signals, cgs: CgsParams, cycles: int, cuts: EventCuts | None = None, refit_gains=False,
+                shift_sigma=0.0, shift_cycles=0, seed=0, ridge=0.0):
+        """Iterative LRF reconstruction (ants_lrf_iterate): (new Lrf, per-cycle stats)."""
+        p = IterParams(cgs, int(cycles), cuts if cuts is not None else EventCuts(), int(refit_gains),
+                       float(shift_sigma), int(shift_cycles), int(seed), float(ridge))
+        h, stats = ants_lrf_iterate(self.ctx.handle, self.handle, signals, p)
+        L = Lrf(self.ctx, self.det, h, self.type)
+        L.shared = self.shared
+        return L, stats
 
     def eval(self, pts, stream=None):
         import torch

@@ -34,6 +34,9 @@ void begin_call()
 {
     t_err.clear();
     t_launches = 0;
+    // a failed runtime call outside any entry point (or in a free function)
+    // must not surface as this call's error; sticky errors persist anyway
+    (void)cudaGetLastError();
 }
 
 void count_launch(long n) { t_launches += n; }
@@ -285,7 +288,7 @@ static int upload_lrf(ants_lrf *L)
 ANTS_API void ants_lrf_free(ants_lrf *lrf)
 {
     if (!lrf) return;
-    if (lrf->ctx) cudaSetDevice(lrf->ctx->device);
+    cudaSetDevice(lrf->device);
     cudaFree(lrf->d_coef);
     cudaFree(lrf->d_sxy);
     cudaFree(lrf->d_gain);
@@ -293,6 +296,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_coef2);
     cudaFree(lrf->d_rpoly);
     delete lrf;
+    (void)cudaGetLastError();
 }
 
 ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
@@ -314,6 +318,7 @@ ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, 
     ants_lrf *L = new (std::nothrow) ants_lrf();
     if (!L) return fail(ANTS_E_OOM, "ants_lrf_create: out of host memory");
     L->ctx = ctx;
+    L->device = ctx->device;
     L->type = type;
     L->n_s = det->n_s;
     L->shared = shared ? 1 : 0;
@@ -367,6 +372,15 @@ ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_
     if (count < lrf->coef.size())
         return fail(ANTS_E_ARG, "ants_lrf_coefficients: capacity %zu < %zu", count, lrf->coef.size());
     std::memcpy(coef_host, lrf->coef.data(), lrf->coef.size() * sizeof(double));
+    return ANTS_OK;
+}
+
+ANTS_API int ants_lrf_gains(const ants_lrf *lrf, double *gain_host, size_t count)
+{
+    begin_call();
+    if (!lrf || !gain_host) return fail(ANTS_E_ARG, "ants_lrf_gains: NULL argument");
+    if (count < (size_t)lrf->n_s) return fail(ANTS_E_ARG, "ants_lrf_gains: capacity %zu < %d", count, lrf->n_s);
+    std::memcpy(gain_host, lrf->gain.data(), lrf->n_s * sizeof(double));
     return ANTS_OK;
 }
 

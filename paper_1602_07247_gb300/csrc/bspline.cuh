@@ -21,6 +21,17 @@ __device__ __forceinline__ void bs_weights(float t, float w[4])
     w[3] = k * t3;
 }
 
+// the same weights in FP64 (LRF fits and the gain refit)
+__device__ __forceinline__ void bs_weights_f64(double t, double w[4])
+{
+    const double k = 1.0 / 6.0;
+    double t2 = t * t, t3 = t2 * t, u = 1.0 - t;
+    w[0] = k * u * u * u;
+    w[1] = k * (3.0 * t3 - 6.0 * t2 + 4.0);
+    w[2] = k * (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0);
+    w[3] = k * t3;
+}
+
 // span index j in [0, n-1] of x and its local parameter t; x == hi falls in
 // the last span with t = 1
 __device__ __forceinline__ int bs_span(float x, float lo, float inv_h, int n, float &t)

@@ -740,6 +740,7 @@ __global__ void __launch_bounds__(256) cgs_batched_kernel(const CgsArgs *__restr
 
 struct ants_batch_plan {
     ants_ctx *ctx = nullptr;
+    int device = 0;
     std::vector<ants_batch_item> items;
     ants_batch_config cfg{};
     ants::CgsArgs *d_items = nullptr;
@@ -894,6 +895,7 @@ ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch
     ants_batch_plan *P = new (std::nothrow) ants_batch_plan();
     if (!P) return fail(ANTS_E_OOM, "ants_batch_plan_create: out of host memory");
     P->ctx = ctx;
+    P->device = ctx->device;
     P->items.assign(items, items + n_items);
     P->cfg = c;
     rc = build_plan(P, 0);
@@ -1017,10 +1019,11 @@ ANTS_API int ants_batch_autotune(ants_batch_plan *P, const char *cache_path, lon
 ANTS_API void ants_batch_plan_free(ants_batch_plan *P)
 {
     if (!P) return;
-    cudaSetDevice(P->ctx->device);
+    cudaSetDevice(P->device);
     ants::release_plan_device(P);
     if (P->cap) cudaStreamDestroy(P->cap);
     delete P;
+    (void)cudaGetLastError();
 }
 
 }  // extern "C"

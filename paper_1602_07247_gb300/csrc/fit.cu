@@ -8,15 +8,21 @@
 // Every sum is taken in a fixed order, so the result is bitwise
 // reproducible:
 //   1. per sample: knot span and the 4 weights per axis, cell id
-//   2. samples bucketed per cell (counting sort; each bucket then sorted by
-//      sample index)
-//   3. A(u, v) = sum over the cells both basis functions cover, over the
-//      samples of each cell, of B_u B_v  (one thread per band entry)
-//      r(u, s) = sum over u's cells and their samples of B_u v_s
-//   4. right-looking elimination on the band, one launch per column
-//   5. forward / diagonal / backward substitution, one block per value set
+//   2. the samples inside the domain sorted by cell with a stable LSD radix
+//      sort (8-bit digits; one warp ranks a chunk of 2048 samples in index
+//      order), so each cell's samples stay in index order
+//   3. each cell's samples cut into work items of a fixed size; per item the
+//      local normal matrix of the 4^d basis functions that are non-zero on
+//      the cell (upper triangle) and the local right-hand sides, each entry
+//      summed by one thread over the item's samples in order
+//   4. A(u, v) and r(u, s): over the cells that cover them, in cell order,
+//      the entries of their items, in order
+//   5. right-looking elimination on the band, one launch per column
+//   6. forward / diagonal / backward substitution, one block per value set
+#include <algorithm>
 #include <cmath>
 
+#include "bspline.cuh"
 #include "internal.cuh"
 
 namespace ants {
@@ -29,19 +35,10 @@ struct FitGrid {
     int nb[3];       // basis functions per axis: n + 3 (1 for unused axes)
     double lo[3], hi[3], h[3];
     int n_coef, n_cells, bw;
+    int nloc;        // basis functions non-zero on one cell: 4^dims
 };
 
-__device__ __forceinline__ void seg_weights(double t, double w[4])
-{
-    const double k = 1.0 / 6.0;
-    double t2 = t * t, t3 = t2 * t, u = 1.0 - t;
-    w[0] = k * u * u * u;
-    w[1] = k * (3.0 * t3 - 6.0 * t2 + 4.0);
-    w[2] = k * (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0);
-    w[3] = k * t3;
-}
-
-__global__ void fit_point_basis(FitGrid g, const double *pts, long n_pts, int *cell, int *span,
+__global__ void fit_point_basis(FitGrid g, const double *pts, long n_pts, int *cell, int *valid, int *span,
                                 double *wts)
 {
     long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,7 +54,7 @@ __global__ void fit_point_basis(FitGrid g, const double *pts, long n_pts, int *c
             double u = (x - g.lo[a]) / g.h[a];
             j = (int)floor(u);
             j = j < 0 ? 0 : (j > g.n[a] - 1 ? g.n[a] - 1 : j);
-            if (ok) seg_weights(u - (double)j, w);
+            if (ok) bs_weights_f64(u - (double)j, w);
         }
         span[p * 3 + a] = j;
         for (int q = 0; q < 4; ++q) wts[(p * 3 + a) * 4 + q] = w[q];
@@ -65,49 +62,169 @@ __global__ void fit_point_basis(FitGrid g, const double *pts, long n_pts, int *c
         mult *= g.n[a];
     }
     cell[p] = ok ? c : -1;
+    valid[p] = ok ? 1 : 0;
 }
 
-__global__ void fit_count(const int *cell, long n_pts, int *count)
-{
-    long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n_pts && cell[p] >= 0) atomicAdd(&count[cell[p]], 1);
-}
-
-// exclusive scan of n_cells counts (small: one block, serial chunks)
-__global__ void fit_scan(const int *count, int n_cells, int *offset)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int acc = 0;
-        for (int c = 0; c < n_cells; ++c) {
-            offset[c] = acc;
-            acc += count[c];
-        }
-        offset[n_cells] = acc;
-    }
-}
-
-__global__ void fit_scatter(const int *cell, long n_pts, const int *offset, int *cursor, int *list)
+// the samples inside the domain, in index order: key = cell, idx = sample
+__global__ void fit_compact(const int *cell, long n_pts, const int *pos, int *key, int *idx)
 {
     long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n_pts && cell[p] >= 0) {
-        int pos = atomicAdd(&cursor[cell[p]], 1);
-        list[offset[cell[p]] + pos] = (int)p;
+        key[pos[p]] = cell[p];
+        idx[pos[p]] = (int)p;
     }
 }
 
-// order every bucket by sample index (insertion sort; buckets are small)
-__global__ void fit_sort_buckets(const int *offset, int n_cells, int *list)
+// --- stable LSD radix sort of (key, idx) by key, 8 bits per pass ------------
+constexpr int kRadixChunk = 2048;  // keys ranked in order by one warp
+constexpr int kRadixWarps = 4;     // chunks per block
+
+// count[d][chunk]: keys of the chunk whose digit is d
+__global__ void __launch_bounds__(32 * kRadixWarps) radix_count(const int *key, long n, int shift, long n_chunks,
+                                                                 int *count)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cells) return;
-    int b = offset[c], e = offset[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = list[i], k = i - 1;
-        while (k >= b && list[k] > v) {
-            list[k + 1] = list[k];
-            --k;
+    __shared__ int s_cnt[kRadixWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long chunk = (long)blockIdx.x * kRadixWarps + w;
+    if (chunk >= n_chunks) return;  // warp-uniform; only warp-level synchronisation follows
+    for (int d = lane; d < 256; d += 32) s_cnt[w][d] = 0;
+    __syncwarp();
+    const long b = chunk * kRadixChunk, e = b + kRadixChunk < n ? b + kRadixChunk : n;
+    for (long i = b + lane; i < e; i += 32) atomicAdd(&s_cnt[w][(key[i] >> shift) & 255], 1);
+    __syncwarp();
+    for (int d = lane; d < 256; d += 32) count[(long)d * n_chunks + chunk] = s_cnt[w][d];
+}
+
+// offset[d][chunk] = exclusive scan of count in (digit, chunk) order; each
+// warp places its chunk's keys in index order (equal digits ranked by lane)
+__global__ void __launch_bounds__(32 * kRadixWarps) radix_scatter(const int *key_in, const int *idx_in, long n,
+                                                                   int shift, long n_chunks, const int *offset,
+                                                                   int *key_out, int *idx_out)
+{
+    __shared__ int s_cnt[kRadixWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long chunk = (long)blockIdx.x * kRadixWarps + w;
+    if (chunk >= n_chunks) return;  // warp-uniform
+    for (int d = lane; d < 256; d += 32) s_cnt[w][d] = offset[(long)d * n_chunks + chunk];
+    __syncwarp();
+    const long b = chunk * kRadixChunk, e = b + kRadixChunk < n ? b + kRadixChunk : n;
+    for (long i0 = b; i0 < e; i0 += 32) {
+        const long i = i0 + lane;
+        const bool ok = i < e;
+        const int k = ok ? key_in[i] : 0;
+        const int d = ok ? (k >> shift) & 255 : 256 + lane;  // idle lanes match only themselves
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int base = ok ? s_cnt[w][d] : 0;
+        __syncwarp();
+        if (ok) {
+            const int pos = base + __popc(peers & ((1u << lane) - 1u));
+            key_out[pos] = k;
+            idx_out[pos] = idx_in[i];
+            if ((peers >> lane) == 1u) s_cnt[w][d] = base + __popc(peers);  // the highest lane of the digit
         }
-        list[k + 1] = v;
+        __syncwarp();
+    }
+}
+
+// offset[c] = first sorted position whose cell is >= c, c = 0..n_cells
+__global__ void fit_cell_offsets(const int *key, long n, int n_cells, int *offset)
+{
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_cells) return;
+    long lo = 0, hi = n;
+    while (lo < hi) {
+        long mid = (lo + hi) >> 1;
+        if (key[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    offset[c] = (int)lo;
+}
+
+__global__ void fit_items_per_cell(const int *offset, int n_cells, int per_item, int *items)
+{
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_cells) items[c] = (offset[c + 1] - offset[c] + per_item - 1) / per_item;
+}
+
+// --- per-item local normal matrices and right-hand sides ---------------------
+constexpr int kPartThreads = 128;
+constexpr int kPartR = 8;     // outputs per thread per pass
+constexpr int kPartTile = 32; // samples staged per round
+
+// index of (a, b), a <= b, in the row-major upper triangle of an n x n matrix
+__device__ __forceinline__ int tri_index(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
+
+// partial[item][o]: o < n_mat the local matrix entry (a, b) of tri_index;
+// o = n_mat + l * n_sets + s the local right-hand side (l, s)
+__global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int n_sets, int per_item,
+                                                                   const int *offset, const int *item_off,
+                                                                   const int *idx, const double *wts,
+                                                                   const double *vals, double *partial)
+{
+    __shared__ double s_b[kPartTile][64];
+    __shared__ long s_p[kPartTile];
+    const long item = blockIdx.x;
+    // the cell holding this item: the last cell whose first item is <= item
+    int lo = 0, hi = g.n_cells - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = lo;
+    const long k0 = offset[c] + (item - item_off[c]) * (long)per_item;
+    const long kend = offset[c + 1] < k0 + per_item ? (long)offset[c + 1] : k0 + per_item;
+    const int nloc = g.nloc, n_mat = nloc * (nloc + 1) / 2, n_out = n_mat + nloc * n_sets;
+    double *out = partial + item * (long)n_out;
+    for (int pass = 0; pass < n_out; pass += kPartThreads * kPartR) {
+        int la[kPartR], lb[kPartR];  // lb < 0: right-hand side of set -1 - lb
+        double acc[kPartR];
+#pragma unroll
+        for (int r = 0; r < kPartR; ++r) {
+            const int o = pass + (int)threadIdx.x + r * kPartThreads;
+            acc[r] = 0.0;
+            la[r] = 0;
+            lb[r] = 0;
+            if (o < n_mat) {
+                int a = 0, rem = o;
+                while (rem >= nloc - a) {
+                    rem -= nloc - a;
+                    ++a;
+                }
+                la[r] = a;
+                lb[r] = a + rem;
+            } else if (o < n_out) {
+                la[r] = (o - n_mat) / n_sets;
+                lb[r] = -1 - (o - n_mat) % n_sets;
+            }
+        }
+        for (long t0 = k0; t0 < kend; t0 += kPartTile) {
+            const int nt = kend - t0 < kPartTile ? (int)(kend - t0) : kPartTile;
+            __syncthreads();  // the previous tile is consumed
+            for (int q = threadIdx.x; q < nt * nloc; q += kPartThreads) {
+                const int ts = q / nloc, l = q - ts * nloc;
+                const long p = idx[t0 + ts];
+                s_b[ts][l] = wts[(p * 3 + 0) * 4 + (l & 3)] * wts[(p * 3 + 1) * 4 + ((l >> 2) & 3)] *
+                             wts[(p * 3 + 2) * 4 + (l >> 4)];
+                if (l == 0) s_p[ts] = p;
+            }
+            __syncthreads();
+            for (int ts = 0; ts < nt; ++ts) {
+#pragma unroll
+                for (int r = 0; r < kPartR; ++r) {
+                    const int o = pass + (int)threadIdx.x + r * kPartThreads;
+                    if (o < n_out) {
+                        const double bb = lb[r] >= 0 ? s_b[ts][lb[r]] : vals[s_p[ts] * n_sets + (-1 - lb[r])];
+                        acc[r] += s_b[ts][la[r]] * bb;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kPartR; ++r) {
+            const int o = pass + (int)threadIdx.x + r * kPartThreads;
+            if (o < n_out) out[o] = acc[r];
+        }
     }
 }
 
@@ -118,26 +235,21 @@ __device__ __forceinline__ void decode(const FitGrid &g, int u, int q[3])
     q[2] = u / (g.nb[0] * g.nb[1]);
 }
 
-// B_u at sample p (given u's per-axis index q)
-__device__ __forceinline__ double basis_at(const int *span, const double *wts, long p, const int q[3])
+// local index of basis u (per-axis index q) on the cell with spans (cx, cy, cz)
+__device__ __forceinline__ int local_index(const int q[3], int cx, int cy, int cz)
 {
-    double b = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        int r = q[a] - span[p * 3 + a];
-        if (r < 0 || r > 3) return 0.0;
-        b *= wts[(p * 3 + a) * 4 + r];
-    }
-    return b;
+    return (q[0] - cx) + 4 * ((q[1] - cy) + 4 * (q[2] - cz));
 }
 
 // band storage of the lower triangle: A(i, k), 0 <= i - k <= bw, at i*(bw+1) + (i-k)
-__global__ void fit_assemble_band(FitGrid g, const int *offset, const int *list, const int *span,
-                                  const double *wts, double lambda, double *band)
+__global__ void fit_band_from_partials(FitGrid g, int n_sets, const int *item_off, const double *partial,
+                                       double *band)
 {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long total = (long)g.n_coef * (g.bw + 1);
     if (t >= total) return;
     int u = (int)(t / (g.bw + 1)), d = (int)(t % (g.bw + 1)), v = u - d;
+    const int n_out = g.nloc * (g.nloc + 1) / 2 + g.nloc * n_sets;
     double acc = 0.0;
     if (v >= 0) {
         int qu[3], qv[3], lo[3], hi[3];
@@ -154,26 +266,25 @@ __global__ void fit_assemble_band(FitGrid g, const int *offset, const int *list,
             for (int cz = lo[2]; cz <= hi[2]; ++cz)
                 for (int cy = lo[1]; cy <= hi[1]; ++cy)
                     for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                        int c = (cz * g.n[1] + cy) * g.n[0] + cx;
-                        for (int k = offset[c]; k < offset[c + 1]; ++k) {
-                            long p = list[k];
-                            acc += basis_at(span, wts, p, qu) * basis_at(span, wts, p, qv);
-                        }
+                        const int c = (cz * g.n[1] + cy) * g.n[0] + cx;
+                        const int lu = local_index(qu, cx, cy, cz), lv = local_index(qv, cx, cy, cz);
+                        const int o = tri_index(min(lu, lv), max(lu, lv), g.nloc);
+                        for (int it = item_off[c]; it < item_off[c + 1]; ++it) acc += partial[(long)it * n_out + o];
                     }
         }
-        if (d == 0) acc += lambda;
     }
     band[t] = acc;
 }
 
-// r[u][s] = sum over u's cells and their samples of B_u(p) v[p][s]
-__global__ void fit_rhs(FitGrid g, int n_sets, const int *offset, const int *list, const int *span,
-                        const double *wts, const double *vals, double *rhs)
+// r[u][s] = sum over u's cells and their items of the local right-hand side
+__global__ void fit_rhs_from_partials(FitGrid g, int n_sets, const int *item_off, const double *partial,
+                                      double *rhs)
 {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long total = (long)g.n_coef * n_sets;
     if (t >= total) return;
     int u = (int)(t / n_sets), s = (int)(t % n_sets);
+    const int n_mat = g.nloc * (g.nloc + 1) / 2, n_out = n_mat + g.nloc * n_sets;
     int q[3], lo[3], hi[3];
     decode(g, u, q);
     for (int a = 0; a < 3; ++a) {
@@ -184,11 +295,9 @@ __global__ void fit_rhs(FitGrid g, int n_sets, const int *offset, const int *lis
     for (int cz = lo[2]; cz <= hi[2]; ++cz)
         for (int cy = lo[1]; cy <= hi[1]; ++cy)
             for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                int c = (cz * g.n[1] + cy) * g.n[0] + cx;
-                for (int k = offset[c]; k < offset[c + 1]; ++k) {
-                    long p = list[k];
-                    acc += basis_at(span, wts, p, q) * vals[p * n_sets + s];
-                }
+                const int c = (cz * g.n[1] + cy) * g.n[0] + cx;
+                const int o = n_mat + local_index(q, cx, cy, cz) * n_sets + s;
+                for (int it = item_off[c]; it < item_off[c + 1]; ++it) acc += partial[(long)it * n_out + o];
             }
     rhs[t] = acc;
 }
@@ -276,15 +385,17 @@ int dalloc(DevBuf &b, size_t count, const char *what)
 
 }  // namespace
 
-// Fit on the device; coef_out[n_sets][n_coef] on the host.
-int lrf_fit_device(const ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
-                   long n_pts, const double *pts_host, int n_sets, const double *vals_host, double ridge,
-                   double *coef_out, double *ridge_used)
+// Fit on the device from device-resident samples: pts [n_pts][dims] and
+// vals [n_pts][n_sets] FP64; coef_out[n_sets][n_coef] on the host.
+int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
+                    long n_pts, const double *pts, int n_sets, const double *vals, double ridge, double *coef_out,
+                    double *ridge_used, cudaStream_t st)
 {
     FitGrid g{};
     g.dims = dims;
     g.n_coef = 1;
     g.n_cells = 1;
+    g.nloc = 1;
     for (int a = 0; a < 3; ++a) {
         bool used = a < dims;
         g.n[a] = used ? n_int[a] : 1;
@@ -294,59 +405,92 @@ int lrf_fit_device(const ants_ctx *ctx, int dims, const int *n_int, const double
         g.h[a] = (g.hi[a] - g.lo[a]) / (double)g.n[a];
         g.n_coef *= g.nb[a];
         g.n_cells *= g.n[a];
+        if (used) g.nloc *= 4;
     }
     // largest flat-index distance between two basis functions sharing a cell
     g.bw = 3 * (1 + (dims > 1 ? g.nb[0] : 0) + (dims > 2 ? g.nb[0] * g.nb[1] : 0));
     if (g.bw > g.n_coef - 1) g.bw = g.n_coef - 1;
     const int nc = g.n_coef, W = g.bw + 1;
-    cudaStream_t st = ctx->stream[0];
+    const int n_mat = g.nloc * (g.nloc + 1) / 2;
+    const long n_out = n_mat + (long)g.nloc * n_sets;
+    const int per_item = n_out <= 64 ? 1024 : 2048;
+    const long n_chunks = (n_pts + kRadixChunk - 1) / kRadixChunk;
+    int bits = 0;
+    while ((1L << bits) < (long)g.n_cells) ++bits;
+    const int passes = (bits + 7) / 8;
+    const long n_scan = std::max({n_pts, 256L * n_chunks, (long)g.n_cells});
 
-    DevBuf d_pts, d_vals, d_cell, d_span, d_wts, d_count, d_off, d_cur, d_list, d_band, d_band0, d_rhs, d_x,
-        d_flag;
-    FIT_TRY(dalloc<double>(d_pts, (size_t)n_pts * dims, "points"));
-    FIT_TRY(dalloc<double>(d_vals, (size_t)n_pts * n_sets, "values"));
+    DevBuf d_cell, d_valid, d_pos, d_span, d_wts, d_key0, d_idx0, d_key1, d_idx1, d_count, d_off, d_items, d_itoff,
+        d_tmp, d_tot, d_band, d_band0, d_rhs, d_x, d_flag, d_part;
     FIT_TRY(dalloc<int>(d_cell, (size_t)n_pts, "cells"));
+    FIT_TRY(dalloc<int>(d_valid, (size_t)n_pts, "flags"));
+    FIT_TRY(dalloc<int>(d_pos, (size_t)n_pts, "positions"));
     FIT_TRY(dalloc<int>(d_span, (size_t)n_pts * 3, "spans"));
     FIT_TRY(dalloc<double>(d_wts, (size_t)n_pts * 12, "weights"));
-    FIT_TRY(dalloc<int>(d_count, (size_t)g.n_cells, "counts"));
-    FIT_TRY(dalloc<int>(d_off, (size_t)g.n_cells + 1, "offsets"));
-    FIT_TRY(dalloc<int>(d_cur, (size_t)g.n_cells, "cursors"));
-    FIT_TRY(dalloc<int>(d_list, (size_t)n_pts, "buckets"));
+    FIT_TRY(dalloc<int>(d_key0, (size_t)n_pts, "keys"));
+    FIT_TRY(dalloc<int>(d_idx0, (size_t)n_pts, "indices"));
+    FIT_TRY(dalloc<int>(d_key1, (size_t)n_pts, "keys"));
+    FIT_TRY(dalloc<int>(d_idx1, (size_t)n_pts, "indices"));
+    FIT_TRY(dalloc<int>(d_count, (size_t)256 * (n_chunks > 0 ? n_chunks : 1), "digit counts"));
+    FIT_TRY(dalloc<int>(d_off, (size_t)g.n_cells + 1, "cell offsets"));
+    FIT_TRY(dalloc<int>(d_items, (size_t)g.n_cells, "items"));
+    FIT_TRY(dalloc<int>(d_itoff, (size_t)g.n_cells + 1, "item offsets"));
+    FIT_TRY(dalloc<char>(d_tmp, exclusive_scan_tmp_bytes(n_scan), "scan scratch"));
+    FIT_TRY(dalloc<int>(d_tot, 1, "total"));
     FIT_TRY(dalloc<double>(d_band, (size_t)nc * W, "band"));
     FIT_TRY(dalloc<double>(d_band0, (size_t)nc * W, "band copy"));
     FIT_TRY(dalloc<double>(d_rhs, (size_t)nc * n_sets, "rhs"));
     FIT_TRY(dalloc<double>(d_x, (size_t)nc * n_sets, "solution"));
     FIT_TRY(dalloc<int>(d_flag, 1, "flag"));
-    double *pts = (double *)d_pts.p, *vals = (double *)d_vals.p, *wts = (double *)d_wts.p;
-    int *cell = (int *)d_cell.p, *span = (int *)d_span.p, *count = (int *)d_count.p, *off = (int *)d_off.p;
-    int *cur = (int *)d_cur.p, *list = (int *)d_list.p, *flag = (int *)d_flag.p;
-    double *band = (double *)d_band.p, *band0 = (double *)d_band0.p, *rhs = (double *)d_rhs.p, *x = (double *)d_x.p;
+    int *cell = (int *)d_cell.p, *valid = (int *)d_valid.p, *pos = (int *)d_pos.p, *span = (int *)d_span.p;
+    int *key = (int *)d_key0.p, *idx = (int *)d_idx0.p, *key2 = (int *)d_key1.p, *idx2 = (int *)d_idx1.p;
+    int *count = (int *)d_count.p, *off = (int *)d_off.p, *items = (int *)d_items.p, *itoff = (int *)d_itoff.p;
+    int *tot = (int *)d_tot.p, *flag = (int *)d_flag.p;
+    double *wts = (double *)d_wts.p, *band = (double *)d_band.p, *band0 = (double *)d_band0.p;
+    double *rhs = (double *)d_rhs.p, *x = (double *)d_x.p;
 
-    ANTS_CUDA_TRY(cudaMemcpyAsync(pts, pts_host, (size_t)n_pts * dims * sizeof(double), cudaMemcpyHostToDevice, st),
-                  "fit: upload points");
-    ANTS_CUDA_TRY(cudaMemcpyAsync(vals, vals_host, (size_t)n_pts * n_sets * sizeof(double), cudaMemcpyHostToDevice,
-                                  st), "fit: upload values");
-    ANTS_CUDA_TRY(cudaMemsetAsync(count, 0, g.n_cells * sizeof(int), st), "fit: memset");
-    ANTS_CUDA_TRY(cudaMemsetAsync(cur, 0, g.n_cells * sizeof(int), st), "fit: memset");
-    ANTS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "fit: memset");
     const int T = 256;
-    unsigned bp = (unsigned)((n_pts + T - 1) / T);
     long launches = 0;
+    int n_valid = 0;
     if (n_pts > 0) {
-        fit_point_basis<<<bp, T, 0, st>>>(g, pts, n_pts, cell, span, wts);
-        fit_count<<<bp, T, 0, st>>>(cell, n_pts, count);
-        launches += 2;
+        unsigned bp = (unsigned)((n_pts + T - 1) / T);
+        fit_point_basis<<<bp, T, 0, st>>>(g, pts, n_pts, cell, valid, span, wts);
+        ++launches;
+        FIT_TRY(exclusive_scan(valid, pos, n_pts, tot, d_tmp.p, st));
+        fit_compact<<<bp, T, 0, st>>>(cell, n_pts, pos, key, idx);
+        ++launches;
+        ANTS_CUDA_TRY(cudaMemcpyAsync(&n_valid, tot, sizeof(int), cudaMemcpyDeviceToHost, st), "fit: count");
+        ANTS_CUDA_TRY(cudaStreamSynchronize(st), "fit: basis");
     }
-    fit_scan<<<1, 32, 0, st>>>(count, g.n_cells, off);
-    ++launches;
-    if (n_pts > 0) {
-        fit_scatter<<<bp, T, 0, st>>>(cell, n_pts, off, cur, list);
+    const long nv_chunks = ((long)n_valid + kRadixChunk - 1) / kRadixChunk;
+    const unsigned rb = (unsigned)((nv_chunks + kRadixWarps - 1) / kRadixWarps);
+    for (int pass = 0; pass < passes && n_valid > 1; ++pass) {
+        radix_count<<<rb, 32 * kRadixWarps, 0, st>>>(key, n_valid, 8 * pass, nv_chunks, count);
+        FIT_TRY(exclusive_scan(count, count, 256 * nv_chunks, nullptr, d_tmp.p, st));
+        radix_scatter<<<rb, 32 * kRadixWarps, 0, st>>>(key, idx, n_valid, 8 * pass, nv_chunks, count, key2, idx2);
+        launches += 2;
+        std::swap(key, key2);
+        std::swap(idx, idx2);
+    }
+    const unsigned bcell = (unsigned)((g.n_cells + 1 + T - 1) / T);
+    fit_cell_offsets<<<bcell, T, 0, st>>>(key, n_valid, g.n_cells, off);
+    fit_items_per_cell<<<bcell, T, 0, st>>>(off, g.n_cells, per_item, items);
+    launches += 2;
+    FIT_TRY(exclusive_scan(items, itoff, g.n_cells, itoff + g.n_cells, d_tmp.p, st));
+    int n_items = 0;
+    ANTS_CUDA_TRY(cudaMemcpyAsync(&n_items, itoff + g.n_cells, sizeof(int), cudaMemcpyDeviceToHost, st),
+                  "fit: items");
+    ANTS_CUDA_TRY(cudaStreamSynchronize(st), "fit: sort");
+    FIT_TRY(dalloc<double>(d_part, (size_t)(n_items > 0 ? n_items : 1) * n_out, "partial sums"));
+    double *part = (double *)d_part.p;
+    if (n_items > 0) {
+        fit_cell_partials<<<(unsigned)n_items, kPartThreads, 0, st>>>(g, n_sets, per_item, off, itoff, idx, wts, vals,
+                                                                       part);
         ++launches;
     }
-    fit_sort_buckets<<<(g.n_cells + T - 1) / T, T, 0, st>>>(off, g.n_cells, list);
-    fit_assemble_band<<<(unsigned)(((long)nc * W + T - 1) / T), T, 0, st>>>(g, off, list, span, wts, 0.0, band0);
-    fit_rhs<<<(unsigned)(((long)nc * n_sets + T - 1) / T), T, 0, st>>>(g, n_sets, off, list, span, wts, vals, rhs);
-    launches += 3;
+    fit_band_from_partials<<<(unsigned)(((long)nc * W + T - 1) / T), T, 0, st>>>(g, n_sets, itoff, part, band0);
+    fit_rhs_from_partials<<<(unsigned)(((long)nc * n_sets + T - 1) / T), T, 0, st>>>(g, n_sets, itoff, part, rhs);
+    launches += 2;
     ANTS_CUDA_TRY(cudaGetLastError(), "fit: assembly launch");
     // trace of B^T B for the ridge fallback
     std::vector<double> band_host((size_t)nc * W);
@@ -421,9 +565,20 @@ extern "C" ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, in
     }
     int n_sets = shared ? 1 : det->n_s;
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = ctx->stream[0];
+    DevBuf d_pts, d_vals;
+    FIT_TRY(dalloc<double>(d_pts, (size_t)n_pts * dims, "points"));
+    FIT_TRY(dalloc<double>(d_vals, (size_t)n_pts * n_sets, "values"));
+    if (n_pts > 0) {
+        ANTS_CUDA_TRY(cudaMemcpyAsync(d_pts.p, pts_host, (size_t)n_pts * dims * sizeof(double),
+                                      cudaMemcpyHostToDevice, st), "fit: upload points");
+        ANTS_CUDA_TRY(cudaMemcpyAsync(d_vals.p, vals_host, (size_t)n_pts * n_sets * sizeof(double),
+                                      cudaMemcpyHostToDevice, st), "fit: upload values");
+    }
     std::vector<double> coef((size_t)nc * n_sets);
     double lam = 0.0;
-    int rc = lrf_fit_device(ctx, dims, n_int, lo, hi, n_pts, pts_host, n_sets, vals_host, ridge, coef.data(), &lam);
+    int rc = lrf_fit_samples(ctx, dims, n_int, lo, hi, n_pts, (const double *)d_pts.p, n_sets,
+                             (const double *)d_vals.p, ridge, coef.data(), &lam, st);
     if (rc != ANTS_OK) return rc;
     long launches = ants_last_launch_count();
     if (ridge_used) *ridge_used = lam;

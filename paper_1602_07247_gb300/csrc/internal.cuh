@@ -84,6 +84,7 @@ struct ants_detector {
 
 struct ants_lrf {
     ants_ctx *ctx = nullptr;
+    int device = 0;  // the context's device (freeing does not read the context)
     int type = 0, n_s = 0, shared = 0, n_sets = 0, n_coef = 0;
     int n_int[3] = {0, 0, 0};
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -108,6 +109,15 @@ int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
 // Growing a slot frees the old buffer, so the caller must not have work in
 // flight that uses it.
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
+// exclusive prefix sum of n int32 values (in == out allowed); *total_dev
+// (nullable) receives the sum; tmp holds exclusive_scan_tmp_bytes(n) bytes
+size_t exclusive_scan_tmp_bytes(long n);
+int exclusive_scan(const int *in, int *out, long n, int *total_dev, void *tmp, cudaStream_t s);
+// FP64 least-squares B-spline fit from device samples pts [n_pts][dims],
+// vals [n_pts][n_sets]; coefficients [n_sets][n_coef] to the host (fit.cu)
+int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
+                    long n_pts, const double *pts, int n_sets, const double *vals, double ridge, double *coef_out,
+                    double *ridge_used, cudaStream_t st);
 // f[i] = h[i] for n FP16 values (exact widening), on stream s
 int widen_half(const __half *h, size_t n, float *f, cudaStream_t s);
 // learned proposal (mlp.cu)

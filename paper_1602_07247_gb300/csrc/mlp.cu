@@ -27,6 +27,7 @@
 
 struct ants_mlp {
     ants_ctx *ctx = nullptr;
+    int device = 0;
     int n_in = 0, H = 0;
     ants_mlp_config cfg{};
     size_t n_par = 0;
@@ -517,6 +518,7 @@ ANTS_API int ants_mlp_create(ants_ctx *ctx, int n_in, const ants_mlp_config *cfg
     ants_mlp *M = new (std::nothrow) ants_mlp();
     if (!M) return fail(ANTS_E_OOM, "ants_mlp_create: out of host memory");
     M->ctx = ctx;
+    M->device = ctx->device;
     M->n_in = n_in;
     M->H = cfg->n_hidden;
     M->cfg = *cfg;
@@ -547,7 +549,7 @@ ANTS_API int ants_mlp_create(ants_ctx *ctx, int n_in, const ants_mlp_config *cfg
 ANTS_API void ants_mlp_free(ants_mlp *M)
 {
     if (!M) return;
-    if (M->ctx) cudaSetDevice(M->ctx->device);
+    cudaSetDevice(M->device);
     cudaFree(M->d_par);
     cudaFree(M->d_m);
     cudaFree(M->d_v);
@@ -555,6 +557,7 @@ ANTS_API void ants_mlp_free(ants_mlp *M)
     cudaFree(M->d_w2b);
     cudaFree(M->d_bpad);
     delete M;
+    (void)cudaGetLastError();
 }
 
 ANTS_API int ants_mlp_shape(const ants_mlp *M, int *n_in, int *n_hidden, long *n_params)

@@ -25,6 +25,7 @@
 
 struct ants_logtable {
     ants_ctx *ctx = nullptr;
+    int device = 0;
     const ants_lrf *lrf = nullptr;
     int nx = 0, ny = 0, n_s = 0;
     float x0 = 0, y0 = 0, dx = 0, dy = 0;  // centre of cell (0, 0) and spacing
@@ -290,6 +291,7 @@ ANTS_API int ants_logtable_create(ants_ctx *ctx, const ants_lrf *lrf, int nx, in
     ants_logtable *T = new (std::nothrow) ants_logtable();
     if (!T) return fail(ANTS_E_OOM, "ants_logtable_create: out of host memory");
     T->ctx = ctx;
+    T->device = ctx->device;
     T->lrf = lrf;
     T->nx = nx;
     T->ny = ny;
@@ -359,12 +361,13 @@ ANTS_API int ants_logtable_topk(ants_ctx *ctx, const ants_logtable *T, const flo
 ANTS_API void ants_logtable_free(ants_logtable *T)
 {
     if (!T) return;
-    cudaSetDevice(T->ctx->device);
+    cudaSetDevice(T->device);
     cudaFree(T->d_T);
     cudaFree(T->d_m);
     cudaFree(T->d_Tp);
     cudaFree(T->d_order);
     delete T;
+    (void)cudaGetLastError();
 }
 
 }  // extern "C"

@@ -4,15 +4,16 @@
 // optical transport of Sec. 4.2.3 is summarised by the LRFs), optionally with
 // a normal single-photo-electron response.
 //
-// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) keyed
-// by the seed.  Event e draws its source from the block at counter
-// (e_lo, e_hi, 0xFFFFFFFF, 0); sensor i of event e consumes the blocks at
+// Random numbers: Philox4x32-10 (philox.cuh) keyed by the seed.  Event e
+// draws its source from the block at counter (e_lo, e_hi, 0xFFFFFFFF, 0);
+// sensor i of event e consumes the blocks at
 // (e_lo, e_hi, i, 0), (e_lo, e_hi, i, 1), ...  Poisson counts: CDF inversion
 // below rate 10, Hormann's transformed rejection with squeeze (PTRS, 1993)
 // above.  One thread per (event, sensor); results are independent of the
 // launch shape.
 #include "bspline.cuh"
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace ants {
 
@@ -23,24 +24,6 @@ struct Philox {
     uint32_t buf[4];
     int pos;
 };
-
-__device__ __forceinline__ void philox10(uint32_t k0, uint32_t k1, uint32_t c[4])
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-}
-
-__device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
 
 __device__ __forceinline__ float next_u(Philox &s)
 {

@@ -1,0 +1,360 @@
+"""GPU parity of the event filters (Sec. 5.2), the refit from reconstructed
+events (Sec. 6, 6.2, 6.3) and the iterative LRF reconstruction (Sec. 8)
+against the FP64 oracle, on the same seeded inputs, plus the fit's scaling
+to flood-sized sample sets."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import synth.workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1602_07247_gb300 as ants
+    return ants.Context(0)
+
+
+def _hex19(gain_sigma=0.1):
+    w = synth.workloads.get("hex19_radial")
+    gains = synth.sensor_gains(19, gain_sigma, 5)
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    L = oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), coef, shared=True,
+                   gain=gains)
+    return w, L, gains
+
+
+def _gpu_lrf(ctx, L, w, det_gains=None, gain=None):
+    import paper_1602_07247_gb300 as ants
+    det = ants.Detector(L.sensor_xy, det_gains)
+    dims = {oracle.RADIAL: 1, oracle.XY: 2, oracle.XYZ: 3}[L.type]
+    return ants.Lrf.from_coefficients(ctx, det, L.type, L.n_int[:dims], L.lo[:dims], L.hi[:dims], L.coef,
+                                      shared=L.shared, gain=L.gain if gain is None else gain)
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def _profile(coef, w, r):
+    return oracle.spline_eval(w.n_int[:1], w.lo[:1], w.hi[:1], np.asarray(coef).ravel(), r[:, None])
+
+
+# --------------------------------------------------------------------------
+# the fit at flood sizes
+# --------------------------------------------------------------------------
+
+
+def test_fit_two_million_samples(ctx):
+    """A radial profile fitted to 2e6 scattered samples (the size of one
+    refit of 10^5 events x 19 sensors): the new cell-sorted assembly matches
+    the oracle's normal equations and is bitwise reproducible."""
+    import paper_1602_07247_gb300 as ants
+    rng = np.random.default_rng(41)
+    n = 2_000_000
+    r = rng.uniform(0.0, 150.0, n) ** 1.0
+    v = synth.eta_axial(r) * rng.normal(1.0, 0.05, n)
+    want, _, _ = oracle.lrf_fit((20,), (0.0,), (150.0,), r[:, None], v[:, None])
+    det = ants.Detector(synth.hex_array(2, 30.0))
+    a = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_RADIAL, (20,), (0.0,), (150.0,), r[:, None], v[:, None], shared=True)
+    got = a.coefficients()
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-9, err
+    b = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_RADIAL, (20,), (0.0,), (150.0,), r[:, None], v[:, None], shared=True)
+    assert np.array_equal(b.coefficients(), got)
+
+
+def test_fit_xy_many_samples_many_sets(ctx):
+    """64 value columns on a 24 x 24 grid from 3e5 scattered points (cells
+    with thousands of samples, several work items each) against the oracle."""
+    import paper_1602_07247_gb300 as ants
+    w = synth.workloads.get("sipm8x8_xy")
+    rng = np.random.default_rng(42)
+    pts = rng.uniform(-24.0, 24.0, (300_000, 2))
+    vals = synth.truth_eta(w.sensor_xy, w.gains, pts) * rng.normal(1.0, 0.02, (300_000, 64))
+    want, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    det = ants.Detector(w.sensor_xy, w.gains)
+    got = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals).coefficients()
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-9, err
+
+
+# --------------------------------------------------------------------------
+# centroid, chi-squared, cuts
+# --------------------------------------------------------------------------
+
+
+def test_centroid_matches_oracle(ctx):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, L, gains = _hex19()
+    sig, _ = oracle.simulate(L, 5, 0, 3000, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+    sig[7] = 0.0  # no light: NaN position
+    lrf = _gpu_lrf(ctx, L, w, det_gains=gains)
+    s = torch.from_numpy(_f32(sig)).cuda()
+    xyz = torch.empty((3000, 3), device="cuda")
+    S = torch.empty(3000, device="cuda")
+    ants.ants_event_centroid(ctx.handle, lrf.handle, s, xyz, S)
+    torch.cuda.synchronize()
+    want = oracle.cog(_f32(sig).astype(np.float64), w.sensor_xy, gains)
+    got = xyz.cpu().numpy()
+    ok = np.isfinite(want).all(axis=1)
+    assert not ok[7] and np.isnan(got[7, :2]).all()
+    assert np.abs(got[ok, :2] - want[ok]).max() < 1e-5
+    assert np.all(got[:, 2] == 0.0)
+    assert np.allclose(S.cpu().numpy(), _f32(sig).astype(np.float64).sum(1), rtol=1e-7)
+
+
+@pytest.mark.parametrize("kind", ["radial_group", "xy"])
+def test_chi2_matches_oracle(ctx, kind):
+    """Pearson chi2 at given positions and energies (FP32 values on both
+    sides), including non-finite positions and points where some sensors are
+    out of reach; the GPU evaluates eta in FP32, so the agreement is to
+    ~1e-5 relative."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    if kind == "radial_group":
+        w, L, gains = _hex19()
+        sig, tr = oracle.simulate(L, 6, 0, 4000, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+        lrf = _gpu_lrf(ctx, L, w, det_gains=gains)
+        shift = 1.5
+    else:
+        w = synth.workloads.get("sipm8x8_xy")
+        pts, vals = w.fit_samples()
+        coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+        L = oracle.Lrf(oracle.XY, w.sensor_xy, w.n_int + (0,), w.lo + (0.0,), w.hi + (0.0,), coef)
+        sig, tr = oracle.simulate(L, 6, 0, 4000, region="square", extent=24.0, e0=3000.0, e_spread=0.05)
+        lrf = _gpu_lrf(ctx, L, w)
+        shift = 0.5
+    rng = np.random.default_rng(9)
+    xyz = _f32(np.concatenate([tr[:, :2] + rng.normal(0.0, shift, (4000, 2)), np.zeros((4000, 1))], axis=1))
+    if kind == "xy":
+        xyz[:, :2] = np.clip(xyz[:, :2], -24.0, 24.0)
+    E = _f32(tr[:, 3] * rng.uniform(0.9, 1.1, 4000))
+    xyz[3, 0] = np.nan
+    E[5] = np.inf
+    sig = _f32(sig)
+    want = oracle.chi2_at(L, sig.astype(np.float64), xyz.astype(np.float64), E.astype(np.float64))
+    c = torch.empty(4000, device="cuda")
+    S = torch.empty(4000, device="cuda")
+    ants.ants_event_chi2(ctx.handle, lrf.handle, torch.from_numpy(sig).cuda(), torch.from_numpy(xyz).cuda(),
+                         torch.from_numpy(E).cuda(), c, S)
+    torch.cuda.synchronize()
+    got = c.cpu().numpy().astype(np.float64)
+    assert np.isnan(got[3]) and np.isnan(got[5]) and np.isnan(want[3]) and np.isnan(want[5])
+    ok = np.isfinite(want)
+    assert np.all(np.isfinite(got[ok]))
+    rel = np.abs(got[ok] - want[ok]) / (np.abs(want[ok]) + 1e-3)
+    assert rel.max() < 2e-4, rel.max()
+    assert np.median(rel) < 2e-6
+
+
+@pytest.mark.parametrize("cut", [dict(), dict(chi2_max=1.5), dict(e_lo=950.0, e_hi=1050.0),
+                                 dict(sum_lo=200.0, sum_hi=800.0), dict(r_max=30.0, cx=2.0, cy=-1.0),
+                                 dict(chi2_max=2.0, e_lo=900.0, e_hi=1100.0, r_max=40.0)])
+def test_filter_matches_oracle(ctx, cut):
+    """The same FP32 inputs on both sides give the same kept list, bit for
+    bit (comparisons in FP64 on both), for every cut alone and combined."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    rng = np.random.default_rng(3)
+    n = 50_001
+    xyz = _f32(np.concatenate([rng.uniform(-50, 50, (n, 2)), np.zeros((n, 1))], axis=1))
+    E = _f32(rng.normal(1000.0, 60.0, n))
+    chi2 = _f32(rng.gamma(4.0, 0.3, n))
+    ssum = _f32(rng.uniform(0.0, 1000.0, n))
+    status = rng.choice([0, 0, 0, 0, 2, 3, 4], n).astype(np.int32)
+    xyz[::97, 1] = np.nan
+    chi2[::89] = np.inf
+    # values exactly on the bounds are kept
+    E[10] = 950.0
+    E[11] = 1050.0
+    chi2[12] = 1.5
+    status[10:13] = 0
+    want = np.nonzero(oracle.event_filter(status, xyz, E, chi2, ssum, oracle.EventCuts(**cut)))[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    k = ants.ants_event_filter(ctx.handle, torch.from_numpy(status).cuda(), torch.from_numpy(xyz).cuda(),
+                               torch.from_numpy(E).cuda(), torch.from_numpy(chi2).cuda(),
+                               torch.from_numpy(ssum).cuda(), ants.EventCuts(**cut), idx)
+    assert k == want.size
+    assert np.array_equal(idx[:k].cpu().numpy(), want)
+
+
+# --------------------------------------------------------------------------
+# refit from reconstructed events
+# --------------------------------------------------------------------------
+
+
+def _flood_refit_inputs(L, n, seed, extent=60.0, region="disk", e0=1e4, jitter=0.7):
+    sig, tr = oracle.simulate(L, seed, 0, n, region=region, extent=extent, e0=e0, e_spread=0.05)
+    rng = np.random.default_rng(seed)
+    xyz = _f32(np.concatenate([tr[:, :2] + rng.normal(0.0, jitter, (n, 2)), np.zeros((n, 1))], axis=1))
+    E = _f32(tr[:, 3] * rng.uniform(0.97, 1.03, n))
+    keep = np.sort(rng.choice(n, size=int(0.8 * n), replace=False)).astype(np.int32)
+    return _f32(sig), xyz, E, keep
+
+
+@pytest.mark.parametrize("mode", ["group", "group_gains", "per_sensor"])
+def test_radial_refit_matches_oracle(ctx, mode):
+    """Radial refit of the kept events with a seeded shift: profile (and
+    gains) against the oracle's FP64 refit of the same samples."""
+    import torch
+    w, L, gains = _hex19()
+    sig, xyz, E, keep = _flood_refit_inputs(L, 20000, 11)
+    lrf = _gpu_lrf(ctx, L, w, det_gains=gains)
+    shared = mode != "per_sensor"
+    rg = mode == "group_gains"
+    out = lrf.refit(torch.from_numpy(sig).cuda(), torch.from_numpy(xyz).cuda(), torch.from_numpy(E).cuda(),
+                    index=torch.from_numpy(keep).cuda(), shared=shared, refit_gains=rg, shift_sigma=1.2, seed=77,
+                    cycle=3)
+    x = xyz[keep].astype(np.float64)
+    x[:, :2] += oracle.shift_xy(77, 3, keep, 1.2)
+    want = oracle.lrf_refit(L, sig[keep].astype(np.float64), x, E[keep].astype(np.float64), shared=shared,
+                            refit_gains=rg)
+    got = out.coefficients()
+    r = np.linspace(0.0, 120.0, 61)
+    if shared:
+        gp, wp = _profile(got[0], w, r), _profile(want.coef[0], w, r)
+        assert np.abs(gp - wp).max() < 1e-9 * np.abs(wp).max()
+        assert np.abs(out.gains() - want.gain).max() < 1e-10
+    else:
+        for i in range(19):
+            gp, wp = _profile(got[i], w, r), _profile(want.coef[i], w, r)
+            assert np.abs(gp - wp).max() < 1e-9 * np.abs(wp).max(), i
+        assert np.all(out.gains() == 1.0)
+
+
+def test_xy_refit_matches_oracle(ctx):
+    import torch
+    w = synth.workloads.get("sipm8x8_xy")
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    L = oracle.Lrf(oracle.XY, w.sensor_xy, w.n_int + (0,), w.lo + (0.0,), w.hi + (0.0,), coef)
+    sig, xyz, E, keep = _flood_refit_inputs(L, 60000, 12, extent=23.0, region="square", e0=3000.0, jitter=0.3)
+    lrf = _gpu_lrf(ctx, L, w)
+    out = lrf.refit(torch.from_numpy(sig).cuda(), torch.from_numpy(xyz).cuda(), torch.from_numpy(E).cuda(),
+                    index=torch.from_numpy(keep).cuda(), shift_sigma=0.4, seed=5, cycle=0)
+    x = xyz[keep].astype(np.float64)
+    x[:, :2] += oracle.shift_xy(5, 0, keep, 0.4)
+    want = oracle.lrf_refit(L, sig[keep].astype(np.float64), x, E[keep].astype(np.float64))
+    got = out.coefficients()
+    assert np.abs(got - want.coef).max() < 1e-8 * np.abs(want.coef).max()
+
+
+def test_refit_errors(ctx):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, L, gains = _hex19()
+    lrf = _gpu_lrf(ctx, L, w)
+    sig = torch.zeros((4, 19), device="cuda")
+    xyz = torch.zeros((4, 3), device="cuda")
+    E = torch.ones(4, device="cuda")
+    idx = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(ants.AntsError):  # no events: the fit stays singular
+        lrf.refit(sig, xyz, E, index=idx, n_kept=0)
+    wx = synth.workloads.get("sipm8x8_xy")
+    Lx = oracle.Lrf(oracle.XY, wx.sensor_xy, wx.n_int + (0,), wx.lo + (0.0,), wx.hi + (0.0,),
+                    np.ones((64, 27 * 27)))
+    lx = _gpu_lrf(ctx, Lx, wx)
+    with pytest.raises(ants.AntsError):  # gains belong to radial groups
+        lx.refit(torch.zeros((4, 64), device="cuda"), xyz, E, refit_gains=True)
+
+
+# --------------------------------------------------------------------------
+# the iterative procedure
+# --------------------------------------------------------------------------
+
+
+def _start_guess(w, gains, r0=55.0):
+    pts, _ = w.fit_samples()
+    c0, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, synth.eta_axial(pts[:, 0], r0=r0)[:, None])
+    return oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), c0, shared=True,
+                      gain=gains.copy())
+
+
+def test_iterate_matches_oracle(ctx):
+    """Four cycles from a too-wide simulated guess on 2000 flood events, with
+    a chi2 cut and a shift in the first cycle: the GPU procedure and the
+    oracle's keep the same events every cycle and end with the same profile
+    up to the FP32-vs-FP64 differences of the reconstructed positions."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, Lt, gains = _hex19()
+    sig, tr = oracle.simulate(Lt, 78, 0, 2000, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+    sig = _f32(sig)
+    L0 = _start_guess(w, gains)
+    P = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    cuts = dict(chi2_max=25.0)
+    want, st_o = oracle.lrf_iterate(L0, P, sig.astype(np.float64), 4, oracle.EventCuts(**cuts), shift_sigma=1.0,
+                                    shift_cycles=1, seed=9, gain_cog=gains)
+    lrf0 = _gpu_lrf(ctx, L0, w, det_gains=gains)
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    got, st_g = lrf0.iterate(torch.from_numpy(sig).cuda(), p, 4, ants.EventCuts(**cuts), shift_sigma=1.0,
+                             shift_cycles=1, seed=9)
+    for a, b in zip(st_g, st_o):
+        assert abs(a["n_kept"] - b["n_kept"]) <= 2, (a, b)
+        assert abs(a["mean_E"] / b["mean_E"] - 1) < 1e-4
+    r = np.linspace(0.0, 110.0, 56)
+    gp, wp = _profile(got.coefficients()[0], w, r), _profile(want.coef[0], w, r)
+    assert np.abs(gp - wp).max() < 2e-3 * np.abs(wp).max()
+    # bitwise reproducible
+    again, _ = lrf0.iterate(torch.from_numpy(sig).cuda(), p, 4, ants.EventCuts(**cuts), shift_sigma=1.0,
+                            shift_cycles=1, seed=9)
+    assert np.array_equal(again.coefficients(), got.coefficients())
+
+
+def test_iterate_converges_and_equals_its_steps(ctx):
+    """10^5 flood events: four GPU cycles bring the position error within 3 %
+    of that with the true LRFs; the last cycle equals an explicit
+    reconstruct - chi2 - filter - refit sequence through the C ABI."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, Lt, gains = _hex19()
+    lt = _gpu_lrf(ctx, Lt, w, det_gains=gains)
+    n = 100_000
+    sp = ants.SimParams("disk", 60.0, 0.0, 0.0, 0.0, 0.0, 1e4, 0.05, 0.1)
+    sig = torch.empty((n, 19), device="cuda")
+    truth = torch.empty((n, 4), device="cuda")
+    ants.ants_simulate_events(ctx.handle, lt.handle, sp, 1234, 0, sig, truth)
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+
+    def rms(lrf):
+        res = ants.reconstruct(ctx, lrf, p, sig)
+        return float(((res.xyz[:, :2] - truth[:, :2]) ** 2).sum(1).mean().sqrt())
+
+    lrf0 = _gpu_lrf(ctx, _start_guess(w, gains), w, det_gains=gains)
+    e_true, e0 = rms(lt), rms(lrf0)
+    cuts = ants.EventCuts(chi2_max=25.0)
+    l3, st3 = lrf0.iterate(sig, p, 3, cuts)
+    l4, st4 = lrf0.iterate(sig, p, 4, cuts)
+    e4 = rms(l4)
+    assert e0 > 4 * e_true and e4 < 1.03 * e_true, (e_true, e0, e4)
+    assert st4[-1]["n_kept"] > 0.99 * n and st4[-1]["rel_change"] < 0.02
+    # the fourth cycle by hand from the third cycle's output
+    res = ants.reconstruct(ctx, l3, p, sig)
+    chi2 = torch.empty(n, device="cuda")
+    ssum = torch.empty(n, device="cuda")
+    ants.ants_event_chi2(ctx.handle, l3.handle, sig, res.xyz, res.E, chi2, ssum)
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    k = ants.ants_event_filter(ctx.handle, res.status, res.xyz, res.E, chi2, ssum, cuts, idx)
+    assert k == st4[-1]["n_kept"]
+    manual = l3.refit(sig, res.xyz, res.E, index=idx, n_kept=k)
+    assert np.array_equal(manual.coefficients(), l4.coefficients())
+    assert np.array_equal(manual.gains(), l4.gains())
+
+
+def test_iterate_rejects_empty_cycles(ctx):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, Lt, gains = _hex19()
+    lt = _gpu_lrf(ctx, Lt, w, det_gains=gains)
+    sig, _ = oracle.simulate(Lt, 3, 0, 500, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    with pytest.raises(ants.AntsError, match="kept no event"):
+        lt.iterate(torch.from_numpy(_f32(sig)).cuda(), p, 2, ants.EventCuts(e_lo=1.0, e_hi=2.0))
