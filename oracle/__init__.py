@@ -14,6 +14,11 @@ Functions follow the paper (Morozov et al., arXiv:1602.07247):
   lrf_fit        Sec. 6 B-spline LRFs fitted to (position, value) data
   lrf_eval       Sec. 6.1.1 / 6.1.2 axial, XY and XYZ LRFs, Sec. 6.2 grouping
   bspline_*      uniform cubic B-spline basis (Cox-de Boor)
+  chi2_at, event_filter
+                 Sec. 5.2 reconstruction chi-squared and event cuts
+  shift_xy, lrf_refit, gain_refit, centroid_lrf, lrf_iterate
+                 Sec. 8 iterative LRF reconstruction, Sec. 6.2 / 6.3 groups
+                 and their relative gains
 Parity pins live in tests/test_oracle_*.py.
 """
 from __future__ import annotations

@@ -18,7 +18,11 @@
  *   - Sec. 6 / 6.1.1 / 6.1.2, LRFs are B-spline parameterised functions of
  *     1 (axial), 2 (XY) or 3 (XYZ) coordinates, computed from datasets of
  *     (position, signal) pairs; Sec. 6.2, one group = one shared LRF times a
- *     per-sensor relative gain.
+ *     per-sensor relative gain; Sec. 6.3, the gains of a group refitted with
+ *     its profile fixed.
+ *   - Sec. 5.2, event filters on chi-squared, energy, signal sum and
+ *     position; Sec. 8, iterative LRF reconstruction (reconstruct, filter,
+ *     optionally shift the positions at random, refit, repeat).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - B-spline: uniform cubic on [lo,hi] with n intervals, n+3 basis
@@ -39,6 +43,9 @@
  *     domain of an XY/XYZ LRF; z starts at a given z0.
  *   - Reported logL: sum_i [ s_i ln mu_i - mu_i - lgamma(s_i+1) ] at the
  *     result, with s_i = 0 terms equal to -mu_i.
+ *   - Chi-squared: Pearson's sum over sensors with mu_i > 0 of
+ *     (s_i - mu_i)^2 / mu_i, divided by n_s - 3.
+ *   - Random shift: normal, sigma given, Box-Muller of a Philox4x32-10 block.
  *
  * Every function is a direct transcription of a definition; no blocking,
  * fusion or reordering is done beyond what the definition states.

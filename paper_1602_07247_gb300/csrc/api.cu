@@ -45,7 +45,7 @@ int lrf_dims(int type) { return type == ANTS_LRF_RADIAL ? 1 : (type == ANTS_LRF_
 
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
 {
-    if (slot < 0 || slot >= 8) {
+    if (slot < 0 || slot >= 12) {
         fail(ANTS_E_INTERNAL, "scratch slot %d", slot);
         return nullptr;
     }
@@ -147,7 +147,7 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_host_buffers(ctx);
-    for (int k = 0; k < 8; ++k) cudaFree(ctx->scratch[k]);
+    for (int k = 0; k < 12; ++k) cudaFree(ctx->scratch[k]);
     cudaFree(ctx->d_fault);
     for (int k = 0; k < 2; ++k)
         if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);

@@ -7,18 +7,20 @@
 //   factorisation (A = L D L^T) of the banded normal matrix.
 // Every sum is taken in a fixed order, so the result is bitwise
 // reproducible:
-//   1. per sample: knot span and the 4 weights per axis, cell id
+//   1. per sample: its cell (knot span per axis)
 //   2. the samples inside the domain sorted by cell with a stable LSD radix
 //      sort (8-bit digits; one warp ranks a chunk of 2048 samples in index
 //      order), so each cell's samples stay in index order
 //   3. each cell's samples cut into work items of a fixed size; per item the
 //      local normal matrix of the 4^d basis functions that are non-zero on
 //      the cell (upper triangle) and the local right-hand sides, each entry
-//      summed by one thread over the item's samples in order
-//   4. A(u, v) and r(u, s): over the cells that cover them, in cell order,
-//      the entries of their items, in order
-//   5. right-looking elimination on the band, one launch per column
-//   6. forward / diagonal / backward substitution, one block per value set
+//      summed by one thread over the item's samples in order (weights and
+//      values staged in shared memory tile by tile)
+//   4. per cell, the sum of its items' entries (8 interleaved lanes, then
+//      the lanes in order)
+//   5. A(u, v) and r(u, s): over the cells that cover them, in cell order
+//   6. right-looking elimination on the band, one launch per column
+//   7. forward / diagonal / backward substitution, one block per value set
 #include <algorithm>
 #include <cmath>
 
@@ -38,28 +40,30 @@ struct FitGrid {
     int nloc;        // basis functions non-zero on one cell: 4^dims
 };
 
-__global__ void fit_point_basis(FitGrid g, const double *pts, long n_pts, int *cell, int *valid, int *span,
-                                double *wts)
+// the span of axis a at coordinate x (clamped) and its local parameter
+__device__ __forceinline__ int axis_span(const FitGrid &g, int a, double x, double &t)
+{
+    double u = (x - g.lo[a]) / g.h[a];
+    int j = (int)floor(u);
+    j = j < 0 ? 0 : (j > g.n[a] - 1 ? g.n[a] - 1 : j);
+    t = u - (double)j;
+    return j;
+}
+
+__global__ void fit_point_cells(FitGrid g, const double *pts, long n_pts, int *cell, int *valid)
 {
     long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pts) return;
     int c = 0, mult = 1;
     bool ok = true;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double w[4] = {1.0, 0.0, 0.0, 0.0};
-        int j = 0;
         if (a < g.dims) {
-            double x = pts[p * g.dims + a];
+            double x = pts[p * g.dims + a], t;
             ok = ok && x >= g.lo[a] && x <= g.hi[a];
-            double u = (x - g.lo[a]) / g.h[a];
-            j = (int)floor(u);
-            j = j < 0 ? 0 : (j > g.n[a] - 1 ? g.n[a] - 1 : j);
-            if (ok) bs_weights_f64(u - (double)j, w);
+            c += axis_span(g, a, x, t) * mult;
+            mult *= g.n[a];
         }
-        span[p * 3 + a] = j;
-        for (int q = 0; q < 4; ++q) wts[(p * 3 + a) * 4 + q] = w[q];
-        c += j * mult;
-        mult *= g.n[a];
     }
     cell[p] = ok ? c : -1;
     valid[p] = ok ? 1 : 0;
@@ -148,21 +152,41 @@ __global__ void fit_items_per_cell(const int *offset, int n_cells, int per_item,
 
 // --- per-item local normal matrices and right-hand sides ---------------------
 constexpr int kPartThreads = 128;
-constexpr int kPartR = 8;     // outputs per thread per pass
-constexpr int kPartTile = 32; // samples staged per round
+constexpr int kPartR = 8;           // outputs per thread per pass
+constexpr int kPartMaxTile = 32;    // samples staged per round
+constexpr int kPartSmem = 40 * 1024;  // dynamic; plus 4160 B static, under the 48 KB default
+
+// samples per staged tile for nloc local functions and n_sets values
+__host__ __device__ inline int part_tile(int nloc, int n_sets)
+{
+    const int per = 8 * (12 + nloc + n_sets) + 8;
+    const int t = kPartSmem / per;
+    return t < 1 ? 1 : (t > kPartMaxTile ? kPartMaxTile : t);
+}
 
 // index of (a, b), a <= b, in the row-major upper triangle of an n x n matrix
 __device__ __forceinline__ int tri_index(int a, int b, int n) { return a * n - a * (a - 1) / 2 + (b - a); }
 
 // partial[item][o]: o < n_mat the local matrix entry (a, b) of tri_index;
-// o = n_mat + l * n_sets + s the local right-hand side (l, s)
-__global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int n_sets, int per_item,
+// o = n_mat + l * n_sets + s the local right-hand side (l, s).  Each tile of
+// samples is staged in shared memory (weights computed from the points,
+// values gathered), so the per-output loops read shared memory only.
+// Dynamic shared memory: weights [tile][3][4], local basis values
+// [tile][nloc], values [tile][n_sets] (FP64), sample indices [tile].
+__global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int n_sets, int per_item, int tile,
                                                                    const int *offset, const int *item_off,
-                                                                   const int *idx, const double *wts,
+                                                                   const int *idx, const double *pts,
                                                                    const double *vals, double *partial)
 {
-    __shared__ double s_b[kPartTile][64];
-    __shared__ long s_p[kPartTile];
+    extern __shared__ double smem[];
+    __shared__ unsigned short s_tri[64 * 65 / 2];  // (a << 8) | b of each upper-triangle entry
+    const int nloc = g.nloc, n_mat = nloc * (nloc + 1) / 2, n_out = n_mat + nloc * n_sets;
+    for (int q = threadIdx.x; q < nloc; q += kPartThreads)
+        for (int b = q; b < nloc; ++b) s_tri[tri_index(q, b, nloc)] = (unsigned short)((q << 8) | b);
+    double *s_w = smem;
+    double *s_b = s_w + tile * 12;
+    double *s_v = s_b + tile * nloc;
+    long *s_p = (long *)(s_v + (size_t)tile * n_sets);
     const long item = blockIdx.x;
     // the cell holding this item: the last cell whose first item is <= item
     int lo = 0, hi = g.n_cells - 1;
@@ -174,8 +198,8 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
     const int c = lo;
     const long k0 = offset[c] + (item - item_off[c]) * (long)per_item;
     const long kend = offset[c + 1] < k0 + per_item ? (long)offset[c + 1] : k0 + per_item;
-    const int nloc = g.nloc, n_mat = nloc * (nloc + 1) / 2, n_out = n_mat + nloc * n_sets;
     double *out = partial + item * (long)n_out;
+    __syncthreads();  // s_tri is complete
     for (int pass = 0; pass < n_out; pass += kPartThreads * kPartR) {
         int la[kPartR], lb[kPartR];  // lb < 0: right-hand side of set -1 - lb
         double acc[kPartR];
@@ -186,27 +210,40 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
             la[r] = 0;
             lb[r] = 0;
             if (o < n_mat) {
-                int a = 0, rem = o;
-                while (rem >= nloc - a) {
-                    rem -= nloc - a;
-                    ++a;
-                }
-                la[r] = a;
-                lb[r] = a + rem;
+                la[r] = s_tri[o] >> 8;
+                lb[r] = s_tri[o] & 255;
             } else if (o < n_out) {
                 la[r] = (o - n_mat) / n_sets;
                 lb[r] = -1 - (o - n_mat) % n_sets;
             }
         }
-        for (long t0 = k0; t0 < kend; t0 += kPartTile) {
-            const int nt = kend - t0 < kPartTile ? (int)(kend - t0) : kPartTile;
+        for (long t0 = k0; t0 < kend; t0 += tile) {
+            const int nt = kend - t0 < tile ? (int)(kend - t0) : tile;
             __syncthreads();  // the previous tile is consumed
+            for (int q = threadIdx.x; q < nt; q += kPartThreads) s_p[q] = idx[t0 + q];
+            __syncthreads();
+            for (int ts = threadIdx.x; ts < nt; ts += kPartThreads) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {  // static axis index: the grid stays in registers
+                    double w[4] = {1.0, 0.0, 0.0, 0.0};
+                    if (a < g.dims) {
+                        double t;
+                        axis_span(g, a, pts[s_p[ts] * g.dims + a], t);
+                        bs_weights_f64(t, w);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) s_w[(ts * 3 + a) * 4 + b] = w[b];
+                }
+            }
+            for (int q = threadIdx.x; q < nt * n_sets; q += kPartThreads) {
+                const int ts = q / n_sets, sidx = q - ts * n_sets;
+                s_v[q] = vals[s_p[ts] * n_sets + sidx];
+            }
+            __syncthreads();
             for (int q = threadIdx.x; q < nt * nloc; q += kPartThreads) {
                 const int ts = q / nloc, l = q - ts * nloc;
-                const long p = idx[t0 + ts];
-                s_b[ts][l] = wts[(p * 3 + 0) * 4 + (l & 3)] * wts[(p * 3 + 1) * 4 + ((l >> 2) & 3)] *
-                             wts[(p * 3 + 2) * 4 + (l >> 4)];
-                if (l == 0) s_p[ts] = p;
+                s_b[q] = s_w[(ts * 3 + 0) * 4 + (l & 3)] * s_w[(ts * 3 + 1) * 4 + ((l >> 2) & 3)] *
+                         s_w[(ts * 3 + 2) * 4 + (l >> 4)];
             }
             __syncthreads();
             for (int ts = 0; ts < nt; ++ts) {
@@ -214,8 +251,8 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
                 for (int r = 0; r < kPartR; ++r) {
                     const int o = pass + (int)threadIdx.x + r * kPartThreads;
                     if (o < n_out) {
-                        const double bb = lb[r] >= 0 ? s_b[ts][lb[r]] : vals[s_p[ts] * n_sets + (-1 - lb[r])];
-                        acc[r] += s_b[ts][la[r]] * bb;
+                        const double bb = lb[r] >= 0 ? s_b[ts * nloc + lb[r]] : s_v[ts * n_sets + (-1 - lb[r])];
+                        acc[r] += s_b[ts * nloc + la[r]] * bb;
                     }
                 }
             }
@@ -226,6 +263,36 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
             if (o < n_out) out[o] = acc[r];
         }
     }
+}
+
+// cellsum[c][o] = the sum over cell c's items of partial[item][o]: lane l of
+// kRedLanes sums the items l, l + kRedLanes, ... in order, then the lanes
+// are added in order
+constexpr int kRedOut = 32, kRedLanes = 8;
+
+__global__ void __launch_bounds__(kRedOut * kRedLanes) fit_cell_sums(int n_out, const int *item_off,
+                                                                      const double *partial, double *cellsum)
+{
+    __shared__ double s[kRedLanes][kRedOut];
+    const int c = blockIdx.x;
+    const int ol = threadIdx.x % kRedOut, lane = threadIdx.x / kRedOut;
+    const long o = (long)blockIdx.y * kRedOut + ol;
+    double acc = 0.0;
+    if (o < n_out)
+        for (int it = item_off[c] + lane; it < item_off[c + 1]; it += kRedLanes) acc += partial[(long)it * n_out + o];
+    s[lane][ol] = acc;
+    __syncthreads();
+    if (lane == 0 && o < n_out) {
+        double t = s[0][ol];
+        for (int l = 1; l < kRedLanes; ++l) t += s[l][ol];
+        cellsum[(long)c * n_out + o] = t;
+    }
+}
+
+__global__ void fit_iota(int n, int *v)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) v[i] = (int)i;
 }
 
 __device__ __forceinline__ void decode(const FitGrid &g, int u, int q[3])
@@ -386,9 +453,11 @@ int dalloc(DevBuf &b, size_t count, const char *what)
 }  // namespace
 
 // Fit on the device from device-resident samples: pts [n_pts][dims] and
-// vals [n_pts][n_sets] FP64; coef_out[n_sets][n_coef] on the host.
-int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
-                    long n_pts, const double *pts, int n_sets, const double *vals, double ridge, double *coef_out,
+// vals [n_pts][n_sets] FP64; coef_out[n_sets][n_coef] on the host.  Work
+// buffers come from the context's scratch slots 8 and 9 (the call is
+// synchronous, so nothing else can be using them when it returns).
+int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi, long n_pts,
+                    const double *pts, int n_sets, const double *vals, double ridge, double *coef_out,
                     double *ridge_used, cudaStream_t st)
 {
     FitGrid g{};
@@ -414,59 +483,54 @@ int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const doubl
     const int n_mat = g.nloc * (g.nloc + 1) / 2;
     const long n_out = n_mat + (long)g.nloc * n_sets;
     const int per_item = n_out <= 64 ? 1024 : 2048;
+    const int tile = part_tile(g.nloc, n_sets);
     const long n_chunks = (n_pts + kRadixChunk - 1) / kRadixChunk;
     int bits = 0;
     while ((1L << bits) < (long)g.n_cells) ++bits;
     const int passes = (bits + 7) / 8;
     const long n_scan = std::max({n_pts, 256L * n_chunks, (long)g.n_cells});
 
-    DevBuf d_cell, d_valid, d_pos, d_span, d_wts, d_key0, d_idx0, d_key1, d_idx1, d_count, d_off, d_items, d_itoff,
-        d_tmp, d_tot, d_band, d_band0, d_rhs, d_x, d_flag, d_part;
-    FIT_TRY(dalloc<int>(d_cell, (size_t)n_pts, "cells"));
-    FIT_TRY(dalloc<int>(d_valid, (size_t)n_pts, "flags"));
-    FIT_TRY(dalloc<int>(d_pos, (size_t)n_pts, "positions"));
-    FIT_TRY(dalloc<int>(d_span, (size_t)n_pts * 3, "spans"));
-    FIT_TRY(dalloc<double>(d_wts, (size_t)n_pts * 12, "weights"));
-    FIT_TRY(dalloc<int>(d_key0, (size_t)n_pts, "keys"));
-    FIT_TRY(dalloc<int>(d_idx0, (size_t)n_pts, "indices"));
-    FIT_TRY(dalloc<int>(d_key1, (size_t)n_pts, "keys"));
-    FIT_TRY(dalloc<int>(d_idx1, (size_t)n_pts, "indices"));
-    FIT_TRY(dalloc<int>(d_count, (size_t)256 * (n_chunks > 0 ? n_chunks : 1), "digit counts"));
-    FIT_TRY(dalloc<int>(d_off, (size_t)g.n_cells + 1, "cell offsets"));
-    FIT_TRY(dalloc<int>(d_items, (size_t)g.n_cells, "items"));
-    FIT_TRY(dalloc<int>(d_itoff, (size_t)g.n_cells + 1, "item offsets"));
-    FIT_TRY(dalloc<char>(d_tmp, exclusive_scan_tmp_bytes(n_scan), "scan scratch"));
-    FIT_TRY(dalloc<int>(d_tot, 1, "total"));
-    FIT_TRY(dalloc<double>(d_band, (size_t)nc * W, "band"));
-    FIT_TRY(dalloc<double>(d_band0, (size_t)nc * W, "band copy"));
-    FIT_TRY(dalloc<double>(d_rhs, (size_t)nc * n_sets, "rhs"));
-    FIT_TRY(dalloc<double>(d_x, (size_t)nc * n_sets, "solution"));
-    FIT_TRY(dalloc<int>(d_flag, 1, "flag"));
-    int *cell = (int *)d_cell.p, *valid = (int *)d_valid.p, *pos = (int *)d_pos.p, *span = (int *)d_span.p;
-    int *key = (int *)d_key0.p, *idx = (int *)d_idx0.p, *key2 = (int *)d_key1.p, *idx2 = (int *)d_idx1.p;
-    int *count = (int *)d_count.p, *off = (int *)d_off.p, *items = (int *)d_items.p, *itoff = (int *)d_itoff.p;
-    int *tot = (int *)d_tot.p, *flag = (int *)d_flag.p;
-    double *wts = (double *)d_wts.p, *band = (double *)d_band.p, *band0 = (double *)d_band0.p;
-    double *rhs = (double *)d_rhs.p, *x = (double *)d_x.p;
+    Carve cv;
+    const size_t o_cell = cv.take<int>(n_pts), o_valid = cv.take<int>(n_pts), o_pos = cv.take<int>(n_pts);
+    const size_t o_key0 = cv.take<int>(n_pts), o_idx0 = cv.take<int>(n_pts);
+    const size_t o_key1 = cv.take<int>(n_pts), o_idx1 = cv.take<int>(n_pts);
+    const size_t o_count = cv.take<int>(256 * (size_t)(n_chunks > 0 ? n_chunks : 1));
+    const size_t o_off = cv.take<int>(g.n_cells + 1), o_items = cv.take<int>(g.n_cells);
+    const size_t o_itoff = cv.take<int>(g.n_cells + 1), o_iota = cv.take<int>(g.n_cells + 1);
+    const size_t o_tmp = cv.take<char>(exclusive_scan_tmp_bytes(n_scan)), o_tot = cv.take<int>(1);
+    const size_t o_band = cv.take<double>((size_t)nc * W), o_band0 = cv.take<double>((size_t)nc * W);
+    const size_t o_rhs = cv.take<double>((size_t)nc * n_sets), o_x = cv.take<double>((size_t)nc * n_sets);
+    const size_t o_flag = cv.take<int>(1);
+    char *base = (char *)ctx_scratch(ctx, 8, cv.off);
+    if (!base) return ANTS_E_OOM;
+    int *cell = (int *)(base + o_cell), *valid = (int *)(base + o_valid), *pos = (int *)(base + o_pos);
+    int *key = (int *)(base + o_key0), *idx = (int *)(base + o_idx0);
+    int *key2 = (int *)(base + o_key1), *idx2 = (int *)(base + o_idx1);
+    int *count = (int *)(base + o_count), *off = (int *)(base + o_off), *items = (int *)(base + o_items);
+    int *itoff = (int *)(base + o_itoff), *iota = (int *)(base + o_iota), *tot = (int *)(base + o_tot);
+    int *flag = (int *)(base + o_flag);
+    void *tmp = base + o_tmp;
+    double *band = (double *)(base + o_band), *band0 = (double *)(base + o_band0);
+    double *rhs = (double *)(base + o_rhs), *x = (double *)(base + o_x);
 
     const int T = 256;
     long launches = 0;
     int n_valid = 0;
     if (n_pts > 0) {
         unsigned bp = (unsigned)((n_pts + T - 1) / T);
-        fit_point_basis<<<bp, T, 0, st>>>(g, pts, n_pts, cell, valid, span, wts);
+        fit_point_cells<<<bp, T, 0, st>>>(g, pts, n_pts, cell, valid);
         ++launches;
-        FIT_TRY(exclusive_scan(valid, pos, n_pts, tot, d_tmp.p, st));
+        FIT_TRY(exclusive_scan(valid, pos, n_pts, tot, tmp, st));
         fit_compact<<<bp, T, 0, st>>>(cell, n_pts, pos, key, idx);
         ++launches;
         ANTS_CUDA_TRY(cudaMemcpyAsync(&n_valid, tot, sizeof(int), cudaMemcpyDeviceToHost, st), "fit: count");
-        ANTS_CUDA_TRY(cudaStreamSynchronize(st), "fit: basis");
+        ANTS_CUDA_TRY(cudaStreamSynchronize(st), "fit: cells");
     }
     const long nv_chunks = ((long)n_valid + kRadixChunk - 1) / kRadixChunk;
     const unsigned rb = (unsigned)((nv_chunks + kRadixWarps - 1) / kRadixWarps);
     for (int pass = 0; pass < passes && n_valid > 1; ++pass) {
         radix_count<<<rb, 32 * kRadixWarps, 0, st>>>(key, n_valid, 8 * pass, nv_chunks, count);
-        FIT_TRY(exclusive_scan(count, count, 256 * nv_chunks, nullptr, d_tmp.p, st));
+        FIT_TRY(exclusive_scan(count, count, 256 * nv_chunks, nullptr, tmp, st));
         radix_scatter<<<rb, 32 * kRadixWarps, 0, st>>>(key, idx, n_valid, 8 * pass, nv_chunks, count, key2, idx2);
         launches += 2;
         std::swap(key, key2);
@@ -476,20 +540,39 @@ int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const doubl
     fit_cell_offsets<<<bcell, T, 0, st>>>(key, n_valid, g.n_cells, off);
     fit_items_per_cell<<<bcell, T, 0, st>>>(off, g.n_cells, per_item, items);
     launches += 2;
-    FIT_TRY(exclusive_scan(items, itoff, g.n_cells, itoff + g.n_cells, d_tmp.p, st));
+    FIT_TRY(exclusive_scan(items, itoff, g.n_cells, itoff + g.n_cells, tmp, st));
     int n_items = 0;
     ANTS_CUDA_TRY(cudaMemcpyAsync(&n_items, itoff + g.n_cells, sizeof(int), cudaMemcpyDeviceToHost, st),
                   "fit: items");
     ANTS_CUDA_TRY(cudaStreamSynchronize(st), "fit: sort");
-    FIT_TRY(dalloc<double>(d_part, (size_t)(n_items > 0 ? n_items : 1) * n_out, "partial sums"));
-    double *part = (double *)d_part.p;
+    // per-cell sums of the items unless that table would be large (huge
+    // grids): then the band sums the items directly
+    const bool by_cell = (double)g.n_cells * (double)n_out <= (double)(1L << 27);
+    Carve cp;
+    const size_t o_part = cp.take<double>((size_t)(n_items > 0 ? n_items : 1) * n_out);
+    const size_t o_csum = by_cell ? cp.take<double>((size_t)g.n_cells * n_out) : 0;
+    char *pbase = (char *)ctx_scratch(ctx, 9, cp.off);
+    if (!pbase) return ANTS_E_OOM;
+    double *part = (double *)(pbase + o_part);
     if (n_items > 0) {
-        fit_cell_partials<<<(unsigned)n_items, kPartThreads, 0, st>>>(g, n_sets, per_item, off, itoff, idx, wts, vals,
-                                                                       part);
+        const size_t smem = (size_t)tile * (12 + g.nloc + n_sets) * sizeof(double) + (size_t)tile * sizeof(long);
+        fit_cell_partials<<<(unsigned)n_items, kPartThreads, smem, st>>>(g, n_sets, per_item, tile, off, itoff, idx,
+                                                                         pts, vals, part);
         ++launches;
     }
-    fit_band_from_partials<<<(unsigned)(((long)nc * W + T - 1) / T), T, 0, st>>>(g, n_sets, itoff, part, band0);
-    fit_rhs_from_partials<<<(unsigned)(((long)nc * n_sets + T - 1) / T), T, 0, st>>>(g, n_sets, itoff, part, rhs);
+    const int *sum_off = itoff;
+    const double *sums = part;
+    if (by_cell) {
+        double *csum = (double *)(pbase + o_csum);
+        dim3 grid((unsigned)g.n_cells, (unsigned)((n_out + kRedOut - 1) / kRedOut));
+        fit_cell_sums<<<grid, kRedOut * kRedLanes, 0, st>>>((int)n_out, itoff, part, csum);
+        fit_iota<<<bcell, T, 0, st>>>(g.n_cells, iota);
+        launches += 2;
+        sum_off = iota;  // one "item" per cell
+        sums = csum;
+    }
+    fit_band_from_partials<<<(unsigned)(((long)nc * W + T - 1) / T), T, 0, st>>>(g, n_sets, sum_off, sums, band0);
+    fit_rhs_from_partials<<<(unsigned)(((long)nc * n_sets + T - 1) / T), T, 0, st>>>(g, n_sets, sum_off, sums, rhs);
     launches += 2;
     ANTS_CUDA_TRY(cudaGetLastError(), "fit: assembly launch");
     // trace of B^T B for the ridge fallback

@@ -69,9 +69,11 @@ struct ants_ctx {
     float *d_start[2] = {nullptr, nullptr};
     float *d_out[2] = {nullptr, nullptr};   // xyz(3) E logL per event
     int32_t *d_status[2] = {nullptr, nullptr};
-    // general device scratch slots (grown on demand by ants::ctx_scratch)
-    void *scratch[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t scratch_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // general device scratch slots (grown on demand by ants::ctx_scratch):
+    // 0 network activations, 1-6 precision and learned forms, 7 FP16
+    // widening, 8-9 LRF fit, 10 refit samples, 11 event filter
+    void *scratch[12] = {};
+    size_t scratch_cap[12] = {};
     // device word set by a kernel whose bounded wait ran out (ants_ctx_fault)
     int *d_fault = nullptr;
 };
@@ -105,7 +107,18 @@ int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_pa
                      const float *sig, long n_e, const float *start, float *xyz, float *E,
                      float *logL, int32_t *status, int16_t *trace, cudaStream_t stream);
 int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p);
-// device scratch slot `slot` (0..7) of at least `bytes`; NULL (error recorded) on failure.
+// offsets of consecutive 256-byte aligned pieces of one scratch arena
+struct Carve {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count)
+    {
+        const size_t at = off;
+        off += (count * sizeof(T) + 255) & ~(size_t)255;
+        return at;
+    }
+};
+// device scratch slot `slot` (0..11) of at least `bytes`; NULL (error recorded) on failure.
 // Growing a slot frees the old buffer, so the caller must not have work in
 // flight that uses it.
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);
@@ -115,7 +128,7 @@ size_t exclusive_scan_tmp_bytes(long n);
 int exclusive_scan(const int *in, int *out, long n, int *total_dev, void *tmp, cudaStream_t s);
 // FP64 least-squares B-spline fit from device samples pts [n_pts][dims],
 // vals [n_pts][n_sets]; coefficients [n_sets][n_coef] to the host (fit.cu)
-int lrf_fit_samples(const ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
+int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo, const double *hi,
                     long n_pts, const double *pts, int n_sets, const double *vals, double ridge, double *coef_out,
                     double *ridge_used, cudaStream_t st);
 // f[i] = h[i] for n FP16 values (exact widening), on stream s

@@ -349,39 +349,39 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
     const ShiftArgs sh{p.shift_sigma, (uint32_t)p.seed, (uint32_t)(p.seed >> 32), (uint32_t)p.cycle};
     const long total = n_kept * (long)n_s;
     const int T = 256;
+    const int nc = lrf->n_coef;
+    // the samples and the small per-call tables live in scratch slot 10
+    Carve cv;
+    const size_t o_a = cv.take<double>(lrf->type == ANTS_LRF_RADIAL ? total : (size_t)n_kept * dims);
+    const size_t o_b = cv.take<double>(total);
+    const size_t o_sxy = cv.take<double>(2 * (size_t)n_s), o_g = cv.take<double>(n_s);
+    const size_t o_coef = cv.take<double>(nc), o_graw = cv.take<double>(n_s);
+    char *base = (char *)ctx_scratch(ctx, 10, cv.off);
+    if (!base) return ANTS_E_OOM;
+    double *A = (double *)(base + o_a), *B = (double *)(base + o_b);
     if (lrf->type != ANTS_LRF_RADIAL) {
-        DBuf d_pts, d_vals;
-        IT_TRY(dmalloc<double>(d_pts, (size_t)n_kept * dims, "refit points"));
-        IT_TRY(dmalloc<double>(d_vals, (size_t)total, "refit values"));
         if (total > 0) {
-            samples_box<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, dims, n_s, xyz, sig, E, sh,
-                                                             (double *)d_pts.p, (double *)d_vals.p);
+            samples_box<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, dims, n_s, xyz, sig, E, sh, A, B);
             ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
             count_launch();
         }
-        std::vector<double> coef((size_t)n_s * lrf->n_coef);
-        IT_TRY(lrf_fit_samples(ctx, dims, lrf->n_int, lrf->lo, lrf->hi, n_kept, (const double *)d_pts.p, n_s,
-                               (const double *)d_vals.p, p.ridge, coef.data(), nullptr, st));
+        std::vector<double> coef((size_t)n_s * nc);
+        IT_TRY(lrf_fit_samples(ctx, dims, lrf->n_int, lrf->lo, lrf->hi, n_kept, A, n_s, B, p.ridge, coef.data(),
+                               nullptr, st));
         return make_like(ctx, lrf, 0, coef, nullptr, out);
     }
-    DBuf d_sxy, d_g, d_r, d_v;
-    IT_TRY(dmalloc<double>(d_sxy, (size_t)2 * n_s, "sensor positions"));
-    IT_TRY(dmalloc<double>(d_g, (size_t)n_s, "gains"));
-    IT_TRY(dmalloc<double>(d_r, (size_t)total, "refit distances"));
-    IT_TRY(dmalloc<double>(d_v, (size_t)total, "refit values"));
-    ANTS_CUDA_TRY(cudaMemcpyAsync(d_sxy.p, lrf->sxy.data(), 2 * n_s * sizeof(double), cudaMemcpyHostToDevice, st),
+    double *d_sxy = (double *)(base + o_sxy), *d_g = (double *)(base + o_g);
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_sxy, lrf->sxy.data(), 2 * n_s * sizeof(double), cudaMemcpyHostToDevice, st),
                   "refit: upload sensors");
     // a per-sensor input has no group gains: its values are divided by 1
     std::vector<double> g_in(n_s, 1.0);
     if (lrf->shared) g_in = lrf->gain;
-    ANTS_CUDA_TRY(cudaMemcpyAsync(d_g.p, g_in.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_g, g_in.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
                   "refit: upload gains");
-    double *r = (double *)d_r.p, *v = (double *)d_v.p;
-    const int nc = lrf->n_coef;
+    double *r = A, *v = B;
     if (total > 0) {
-        samples_radial<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, n_s, xyz, sig, E, (const double *)d_sxy.p,
-                                                            p.shared ? (const double *)d_g.p : nullptr, sh,
-                                                            p.shared ? 0 : 1, r, v);
+        samples_radial<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, n_s, xyz, sig, E, d_sxy,
+                                                            p.shared ? d_g : nullptr, sh, p.shared ? 0 : 1, r, v);
         ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
         count_launch();
     }
@@ -396,16 +396,14 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
     IT_TRY(lrf_fit_samples(ctx, 1, lrf->n_int, lrf->lo, lrf->hi, total, r, 1, v, p.ridge, coef.data(), nullptr, st));
     std::vector<double> gains = g_in;
     if (p.refit_gains) {
-        DBuf d_coef, d_graw;
-        IT_TRY(dmalloc<double>(d_coef, (size_t)nc, "profile"));
-        IT_TRY(dmalloc<double>(d_graw, (size_t)n_s, "gain sums"));
-        ANTS_CUDA_TRY(cudaMemcpyAsync(d_coef.p, coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st),
+        double *d_coef = (double *)(base + o_coef), *d_graw = (double *)(base + o_graw);
+        ANTS_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st),
                       "refit: upload profile");
-        gain_sums<<<n_s, kGainThreads, 0, st>>>((const double *)d_coef.p, lrf->n_int[0], lrf->hi[0], n_kept, n_s, r,
-                                                index, sig, E, (double *)d_graw.p);
+        gain_sums<<<n_s, kGainThreads, 0, st>>>(d_coef, lrf->n_int[0], lrf->hi[0], n_kept, n_s, r, index, sig, E,
+                                                d_graw);
         ANTS_CUDA_TRY(cudaGetLastError(), "gain refit launch");
         count_launch();
-        ANTS_CUDA_TRY(cudaMemcpyAsync(gains.data(), d_graw.p, n_s * sizeof(double), cudaMemcpyDeviceToHost, st),
+        ANTS_CUDA_TRY(cudaMemcpyAsync(gains.data(), d_graw, n_s * sizeof(double), cudaMemcpyDeviceToHost, st),
                       "refit: download gains");
         ANTS_CUDA_TRY(cudaStreamSynchronize(st), "gain refit");
         double gm = 0.0;
@@ -415,7 +413,7 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
             gm += gains[i];
         }
         gm /= (double)n_s;
-        for (auto &g : gains) g /= gm;
+        for (auto &gg : gains) gg /= gm;
         for (auto &c : coef) c *= gm;
     }
     return make_like(ctx, lrf, 1, coef, &gains, out);
@@ -430,23 +428,26 @@ int check_cuts(const ants_event_cuts *c)
     return ANTS_OK;
 }
 
-int filter_events(long n_e, const int32_t *status, const float *xyz, const float *E, const float *chi2,
+int filter_events(ants_ctx *ctx, long n_e, const int32_t *status, const float *xyz, const float *E, const float *chi2,
                   const float *ssum, const ants_event_cuts &c, int32_t *index, long *n_kept, cudaStream_t st)
 {
-    DBuf d_flag, d_pos, d_tmp, d_tot;
-    IT_TRY(dmalloc<int>(d_flag, (size_t)n_e, "filter flags"));
-    IT_TRY(dmalloc<int>(d_pos, (size_t)n_e, "filter positions"));
-    IT_TRY(dmalloc<char>(d_tmp, exclusive_scan_tmp_bytes(n_e), "scan scratch"));
-    IT_TRY(dmalloc<int>(d_tot, 1, "count"));
+    // flags, positions, scan scratch and the count live in scratch slot 11;
+    // the call waits for the count, so nothing is in flight on return
+    Carve cv;
+    const size_t o_flag = cv.take<int>(n_e), o_pos = cv.take<int>(n_e);
+    const size_t o_tmp = cv.take<char>(exclusive_scan_tmp_bytes(n_e)), o_tot = cv.take<int>(1);
+    char *base = (char *)ctx_scratch(ctx, 11, cv.off);
+    if (!base) return ANTS_E_OOM;
+    int *flag = (int *)(base + o_flag), *pos = (int *)(base + o_pos), *tot = (int *)(base + o_tot);
     const int T = 256;
-    filter_flags<<<blocks_for(n_e, T), T, 0, st>>>(n_e, status, xyz, E, chi2, ssum, c, (int *)d_flag.p);
+    filter_flags<<<blocks_for(n_e, T), T, 0, st>>>(n_e, status, xyz, E, chi2, ssum, c, flag);
     count_launch();
-    IT_TRY(exclusive_scan((const int *)d_flag.p, (int *)d_pos.p, n_e, (int *)d_tot.p, d_tmp.p, st));
-    compact_kernel<<<blocks_for(n_e, T), T, 0, st>>>((const int *)d_flag.p, (const int *)d_pos.p, n_e, index);
+    IT_TRY(exclusive_scan(flag, pos, n_e, tot, base + o_tmp, st));
+    compact_kernel<<<blocks_for(n_e, T), T, 0, st>>>(flag, pos, n_e, index);
     count_launch();
     ANTS_CUDA_TRY(cudaGetLastError(), "filter launch");
     int h = 0;
-    ANTS_CUDA_TRY(cudaMemcpyAsync(&h, d_tot.p, sizeof(int), cudaMemcpyDeviceToHost, st), "filter: count");
+    ANTS_CUDA_TRY(cudaMemcpyAsync(&h, tot, sizeof(int), cudaMemcpyDeviceToHost, st), "filter: count");
     ANTS_CUDA_TRY(cudaStreamSynchronize(st), "filter");
     *n_kept = h;
     return ANTS_OK;
@@ -527,7 +528,7 @@ extern "C" ANTS_API int ants_event_filter(ants_ctx *ctx, long n_events, const in
     if (cuts->sum_hi > cuts->sum_lo && !sum_dev)
         return fail(ANTS_E_ARG, "ants_event_filter: the signal-sum cut needs sum_dev");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
-    return filter_events(n_events, status_dev, xyz_dev, E_dev, chi2_dev, sum_dev, *cuts, index_dev, n_kept_host,
+    return filter_events(ctx, n_events, status_dev, xyz_dev, E_dev, chi2_dev, sum_dev, *cuts, index_dev, n_kept_host,
                          (cudaStream_t)stream);
 }
 
@@ -589,7 +590,7 @@ extern "C" ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init
         chi2_kernel<<<blocks_for(n, kEvWarps), 32 * kEvWarps, 0, st>>>(cur->dev, signals_dev, n, xyz, E, chi2, ssum);
         count_launch();
         long n_kept = 0;
-        rc = filter_events(n, status, xyz, E, chi2, ssum, p->cuts, index, &n_kept, st);
+        rc = filter_events(ctx, n, status, xyz, E, chi2, ssum, p->cuts, index, &n_kept, st);
         if (rc != ANTS_OK) break;
         if (n_kept == 0) {
             rc = fail(ANTS_E_LRF, "ants_lrf_iterate: cycle %d kept no event", c);
