@@ -50,15 +50,36 @@ __device__ __forceinline__ bool in_box(const LrfDev &L, float x, float y, float 
     return ok;
 }
 
-// axial LRF of sensor i at distance r (caller checks r <= hi): the span's
-// cubic in the power basis of its local parameter, by Horner's rule
+// distance in the sensor plane as r^2 times the reciprocal square root of
+// r^2 (rsqrtf: within 2 ulp), 0 at the sensor itself
+__device__ __forceinline__ float plane_dist(float dx, float dy)
+{
+    const float r2 = fmaf(dx, dx, dy * dy);
+    return r2 > 1e-30f ? r2 * rsqrtf(r2) : 0.0f;
+}
+
+// an axial profile at 0 <= r <= hi: its span (the same span and local
+// parameter as bs_span with lo = 0, since r >= 0), the span's cubic in the
+// power basis of the local parameter, Horner's rule
+__device__ __forceinline__ float radial_profile(const float4 *poly, float inv_h, int n, float r)
+{
+    const float u = r * inv_h;
+    const int j = min((int)u, n - 1);
+    const float t = u - (float)j;
+    const float4 p = __ldg(poly + j);
+    return fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
+}
+
+// the power-basis cubics of sensor i's axial LRF
+__device__ __forceinline__ const float4 *radial_poly(const LrfDev &L, int i)
+{
+    return L.rpoly + (L.shared ? 0 : i * L.n_int[0]);
+}
+
+// axial LRF of sensor i at distance r (caller checks r <= hi)
 __device__ __forceinline__ float radial_eta(const LrfDev &L, int i, float r)
 {
-    float t;
-    const int j = bs_span(r, 0.0f, L.inv_h[0], L.n_int[0], t);
-    const float4 p = __ldg(L.rpoly + (L.shared ? 0 : i * L.n_int[0]) + j);
-    const float f = fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
-    return __ldg(L.gain + i) * f;
+    return __ldg(L.gain + i) * radial_profile(radial_poly(L, i), L.inv_h[0], L.n_int[0], r);
 }
 
 // eta_i at one point; ok = false outside the domain (used by the evaluation
@@ -66,8 +87,7 @@ __device__ __forceinline__ float radial_eta(const LrfDev &L, int i, float r)
 __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, float y, float z, bool &ok)
 {
     if (L.type == ANTS_LRF_RADIAL) {
-        float dx = x - L.sxy[2 * i], dy = y - L.sxy[2 * i + 1];
-        float r = sqrtf(fmaf(dx, dx, dy * dy));
+        const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
         ok = r <= L.hi[0];
         return ok ? radial_eta(L, i, r) : 0.0f;
     }

@@ -67,8 +67,7 @@ __device__ __forceinline__ bool node_in_domain_radial(const LrfDev &L, float x, 
 {
     bool ok = true;
     for (int i = 0; i < L.n_s; ++i) {
-        float dx = x - L.sxy[2 * i], dy = y - L.sxy[2 * i + 1];
-        ok = ok && sqrtf(fmaf(dx, dx, dy * dy)) <= L.hi[0];
+        ok = ok && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) <= L.hi[0];
     }
     return ok;
 }
@@ -93,8 +92,7 @@ __device__ __forceinline__ float node_score(const LrfDev &L, const float *s_sig,
     if (TYPE == ANTS_LRF_RADIAL) {
         bool ok = true;
         for (int i = 0; i < n_s; ++i) {
-            float dx = x - L.sxy[2 * i], dy = y - L.sxy[2 * i + 1];
-            float r = sqrtf(fmaf(dx, dx, dy * dy));
+            const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
             ok = ok && r <= L.hi[0];
             float eta = fmaxf(radial_eta(L, i, fminf(r, L.hi[0])), kEtaFloor);
             acc = fmaf(s_sig[i], __log2f(eta * s_ic[i]), acc);
@@ -294,15 +292,18 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
             acc[m] = dh[m] = 0.0f;
             ok[m] = true;
         }
+        const float inv_h = L.inv_h[0];
+        const int n_int = L.n_int[0];
         for (int i = 0; i < L.n_s; ++i) {
             const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
             const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
+            const float gi = __ldg(L.gain + i);
 #pragma unroll
             for (int m = 0; m < NPL; ++m) {
-                const float dx = xs[m] - sx, dy = ys[m] - sy;
-                const float r = sqrtf(fmaf(dx, dx, dy * dy));
+                const float r = plane_dist(xs[m] - sx, ys[m] - sy);
                 ok[m] = ok[m] && r <= hi;
-                const float eta = fmaxf(radial_eta(L, i, fminf(r, hi)), kEtaFloor);
+                const float eta =
+                    fmaxf(gi * radial_profile(radial_poly(L, i), inv_h, n_int, fminf(r, hi)), kEtaFloor);
                 acc[m] = fmaf(si, __log2f(eta * ici), acc[m]);
                 dh[m] += eta - eci;
             }
@@ -580,7 +581,7 @@ __host__ inline void setup_sep(CgsArgs &a)
 }
 
 template <int TYPE>
-__global__ void __launch_bounds__(256) cgs_plain_kernel(CgsArgs a, int warp_floats)
+__global__ void __launch_bounds__(256, TYPE == ANTS_LRF_XYZ ? 2 : 3) cgs_plain_kernel(CgsArgs a, int warp_floats)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
