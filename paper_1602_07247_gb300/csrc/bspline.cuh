@@ -51,11 +51,12 @@ __device__ __forceinline__ bool in_box(const LrfDev &L, float x, float y, float 
 }
 
 // distance in the sensor plane as r^2 times the reciprocal square root of
-// r^2 (rsqrtf: within 2 ulp), 0 at the sensor itself
+// r^2 (rsqrtf: within 2 ulp); the floor on the argument makes it 0 at the
+// sensor itself
 __device__ __forceinline__ float plane_dist(float dx, float dy)
 {
     const float r2 = fmaf(dx, dx, dy * dy);
-    return r2 > 1e-30f ? r2 * rsqrtf(r2) : 0.0f;
+    return r2 * rsqrtf(fmaxf(r2, 1e-30f));
 }
 
 // an axial profile at 0 <= r <= hi: its span (the same span and local

@@ -298,12 +298,12 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
             const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
             const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
             const float gi = __ldg(L.gain + i);
+            const float4 *poly = radial_poly(L, i);
 #pragma unroll
             for (int m = 0; m < NPL; ++m) {
                 const float r = plane_dist(xs[m] - sx, ys[m] - sy);
                 ok[m] = ok[m] && r <= hi;
-                const float eta =
-                    fmaxf(gi * radial_profile(radial_poly(L, i), inv_h, n_int, fminf(r, hi)), kEtaFloor);
+                const float eta = fmaxf(gi * radial_profile(poly, inv_h, n_int, fminf(r, hi)), kEtaFloor);
                 acc[m] = fmaf(si, __log2f(eta * ici), acc[m]);
                 dh[m] += eta - eci;
             }

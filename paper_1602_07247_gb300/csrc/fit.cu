@@ -35,15 +35,16 @@ struct FitGrid {
     int dims;
     int n[3];        // intervals per axis (1 for unused axes)
     int nb[3];       // basis functions per axis: n + 3 (1 for unused axes)
-    double lo[3], hi[3], h[3];
+    double lo[3], hi[3], h[3], inv_h[3];
     int n_coef, n_cells, bw;
     int nloc;        // basis functions non-zero on one cell: 4^dims
 };
 
-// the span of axis a at coordinate x (clamped) and its local parameter
+// the span of axis a at coordinate x (clamped) and its local parameter;
+// the cell of a sample and its weights both come from here, so they agree
 __device__ __forceinline__ int axis_span(const FitGrid &g, int a, double x, double &t)
 {
-    double u = (x - g.lo[a]) / g.h[a];
+    double u = (x - g.lo[a]) * g.inv_h[a];
     int j = (int)floor(u);
     j = j < 0 ? 0 : (j > g.n[a] - 1 ? g.n[a] - 1 : j);
     t = u - (double)j;
@@ -242,8 +243,12 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
             __syncthreads();
             for (int q = threadIdx.x; q < nt * nloc; q += kPartThreads) {
                 const int ts = q / nloc, l = q - ts * nloc;
-                s_b[q] = s_w[(ts * 3 + 0) * 4 + (l & 3)] * s_w[(ts * 3 + 1) * 4 + ((l >> 2) & 3)] *
-                         s_w[(ts * 3 + 2) * 4 + (l >> 4)];
+                const double *w = s_w + ts * 12;
+                // FP64 is scarce: no products with the unit weights of unused axes
+                double b = w[l & 3];
+                if (g.dims > 1) b *= w[4 + ((l >> 2) & 3)];
+                if (g.dims > 2) b *= w[8 + (l >> 4)];
+                s_b[q] = b;
             }
             __syncthreads();
             for (int ts = 0; ts < nt; ++ts) {
@@ -472,6 +477,7 @@ int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo,
         g.lo[a] = used ? lo[a] : 0.0;
         g.hi[a] = used ? hi[a] : 1.0;
         g.h[a] = (g.hi[a] - g.lo[a]) / (double)g.n[a];
+        g.inv_h[a] = (double)g.n[a] / (g.hi[a] - g.lo[a]);
         g.n_coef *= g.nb[a];
         g.n_cells *= g.n[a];
         if (used) g.nloc *= 4;

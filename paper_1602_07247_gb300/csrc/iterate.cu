@@ -245,45 +245,46 @@ __device__ __forceinline__ void shift_of(long e, const ShiftArgs &sh, double &dx
     dy = sh.sigma * rho * sn;
 }
 
-// XY / XYZ samples: pts [k][dims], vals [k][n_s] = s / E
+// XY / XYZ samples, one thread per kept event: pts [k][dims], vals [k][n_s]
+// = s / E (FP64 is scarce: one division per event, a product per sensor)
 __global__ void samples_box(const int32_t *index, long n_kept, int dims, int n_s, const float *xyz, const float *sig,
                             const float *E, ShiftArgs sh, double *pts, double *vals)
 {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_kept * n_s) return;
-    const long k = t / n_s;
-    const int i = (int)(t - k * n_s);
-    const long e = index ? index[k] : k;
-    vals[t] = (double)sig[e * n_s + i] / (double)E[e];
-    if (i == 0) {
-        double dx, dy;
-        shift_of(e, sh, dx, dy);
-        pts[k * dims] = (double)xyz[3 * e] + dx;
-        pts[k * dims + 1] = (double)xyz[3 * e + 1] + dy;
-        if (dims == 3) pts[k * 3 + 2] = (double)xyz[3 * e + 2];
-    }
-}
-
-// RADIAL samples: r = distance to sensor i, v = s / E (divided by gdiv[i]
-// when given); by_sensor stores [i][k], otherwise [k][i]
-__global__ void samples_radial(const int32_t *index, long n_kept, int n_s, const float *xyz, const float *sig,
-                               const float *E, const double *sxy, const double *gdiv, ShiftArgs sh, int by_sensor,
-                               double *r, double *v)
-{
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_kept * n_s) return;
-    const long k = t / n_s;
-    const int i = (int)(t - k * n_s);
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_kept) return;
     const long e = index ? index[k] : k;
     double dx, dy;
     shift_of(e, sh, dx, dy);
-    const double ddx = ((double)xyz[3 * e] + dx) - sxy[2 * i], ddy = ((double)xyz[3 * e + 1] + dy) - sxy[2 * i + 1];
-    const double rr = sqrt(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
-    double vv = (double)sig[e * n_s + i] / (double)E[e];
-    if (gdiv) vv = vv / gdiv[i];
-    const long o = by_sensor ? (long)i * n_kept + k : t;
-    r[o] = rr;
-    v[o] = vv;
+    pts[k * dims] = (double)xyz[3 * e] + dx;
+    pts[k * dims + 1] = (double)xyz[3 * e + 1] + dy;
+    if (dims == 3) pts[k * 3 + 2] = (double)xyz[3 * e + 2];
+    const double inv_e = 1.0 / (double)E[e];
+    for (int i = 0; i < n_s; ++i) vals[k * n_s + i] = (double)sig[e * n_s + i] * inv_e;
+}
+
+// RADIAL samples, one thread per kept event: r = distance to sensor i,
+// v = s / E (times inv_g[i] when given); by_sensor stores [i][k], otherwise
+// [k][i]
+__global__ void samples_radial(const int32_t *index, long n_kept, int n_s, const float *xyz, const float *sig,
+                               const float *E, const double *sxy, const double *inv_g, ShiftArgs sh, int by_sensor,
+                               double *r, double *v)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_kept) return;
+    const long e = index ? index[k] : k;
+    double dx, dy;
+    shift_of(e, sh, dx, dy);
+    const double x = (double)xyz[3 * e] + dx, y = (double)xyz[3 * e + 1] + dy;
+    const double inv_e = 1.0 / (double)E[e];
+    for (int i = 0; i < n_s; ++i) {
+        const double ddx = x - sxy[2 * i], ddy = y - sxy[2 * i + 1];
+        const double rr = sqrt(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
+        double vv = (double)sig[e * n_s + i] * inv_e;
+        if (inv_g) vv *= inv_g[i];
+        const long o = by_sensor ? (long)i * n_kept + k : k * n_s + i;
+        r[o] = rr;
+        v[o] = vv;
+    }
 }
 
 // Sec. 6.3 gain of sensor i with the profile fixed: sum f(r) v / sum f(r)^2
@@ -296,19 +297,19 @@ __global__ void __launch_bounds__(kGainThreads) gain_sums(const double *coef, in
 {
     __shared__ double s_a[kGainThreads], s_b[kGainThreads];
     const int i = blockIdx.x;
-    const double h = hi / (double)n_int;
+    const double inv_h = (double)n_int / hi;
     double fv = 0.0, ff = 0.0;
     for (long k = threadIdx.x; k < n_kept; k += kGainThreads) {
         const double rr = r[k * n_s + i];
         if (!(rr >= 0.0 && rr <= hi)) continue;
-        const double u = rr / h;
+        const double u = rr * inv_h;
         int j = (int)floor(u);
         j = j < 0 ? 0 : (j > n_int - 1 ? n_int - 1 : j);
         double w[4];
         bs_weights_f64(u - (double)j, w);
         const double f = coef[j] * w[0] + coef[j + 1] * w[1] + coef[j + 2] * w[2] + coef[j + 3] * w[3];
         const long e = index ? index[k] : k;
-        const double vv = (double)sig[e * n_s + i] / (double)E[e];
+        const double vv = (double)sig[e * n_s + i] * (1.0 / (double)E[e]);
         fv += f * vv;
         ff += f * f;
     }
@@ -361,7 +362,7 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
     double *A = (double *)(base + o_a), *B = (double *)(base + o_b);
     if (lrf->type != ANTS_LRF_RADIAL) {
         if (total > 0) {
-            samples_box<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, dims, n_s, xyz, sig, E, sh, A, B);
+            samples_box<<<blocks_for(n_kept, T), T, 0, st>>>(index, n_kept, dims, n_s, xyz, sig, E, sh, A, B);
             ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
             count_launch();
         }
@@ -374,13 +375,14 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
     ANTS_CUDA_TRY(cudaMemcpyAsync(d_sxy, lrf->sxy.data(), 2 * n_s * sizeof(double), cudaMemcpyHostToDevice, st),
                   "refit: upload sensors");
     // a per-sensor input has no group gains: its values are divided by 1
-    std::vector<double> g_in(n_s, 1.0);
+    std::vector<double> g_in(n_s, 1.0), inv_g(n_s);
     if (lrf->shared) g_in = lrf->gain;
-    ANTS_CUDA_TRY(cudaMemcpyAsync(d_g, g_in.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
+    for (int i = 0; i < n_s; ++i) inv_g[i] = 1.0 / g_in[i];
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_g, inv_g.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
                   "refit: upload gains");
     double *r = A, *v = B;
     if (total > 0) {
-        samples_radial<<<blocks_for(total, T), T, 0, st>>>(index, n_kept, n_s, xyz, sig, E, d_sxy,
+        samples_radial<<<blocks_for(n_kept, T), T, 0, st>>>(index, n_kept, n_s, xyz, sig, E, d_sxy,
                                                             p.shared ? d_g : nullptr, sh, p.shared ? 0 : 1, r, v);
         ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
         count_launch();
