@@ -144,8 +144,9 @@ def workload():
     return synth.workloads.get("sipm8x8_xy")
 
 
-def cpu_oracle_rate(w, n_sample: int, seed: int):
-    """Events/s of the FP64 oracle (as it stands) on a sample of the workload."""
+def cpu_oracle_rate(w, n_sample: int, seed: int, threads: int = 0):
+    """Events/s of the FP64 oracle (as it stands) on a sample of the workload,
+    on all host cores (threads = 0) or on `threads` threads."""
     import oracle
     pts, vals = w.fit_samples()
     coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
@@ -153,10 +154,18 @@ def cpu_oracle_rate(w, n_sample: int, seed: int):
     P = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
     ev = w.events(n_sample, seed=seed)
     sig = ev.signals.astype(np.float64)
-    t0 = time.perf_counter()
-    oracle.cgs(L, P, sig, gain_cog=w.gains)
-    dt = time.perf_counter() - t0
-    return n_sample / dt, dt, oracle.num_threads(), (L, P, sig)
+    all_cores = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        used = oracle.num_threads()
+        t0 = time.perf_counter()
+        oracle.cgs(L, P, sig, gain_cog=w.gains)
+        dt = time.perf_counter() - t0
+    finally:
+        if threads:
+            oracle.set_num_threads(all_cores)
+    return n_sample / dt, dt, used, (L, P, sig)
 
 
 def run_reference(args):
@@ -561,8 +570,12 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         rate, secs, cores, _ = cpu_oracle_rate(w, args.cpu_events, seed=w.event_seed)
+        n1 = max(64, args.cpu_events // 8)
+        rate1, secs1, _, _ = cpu_oracle_rate(w, n1, seed=w.event_seed, threads=1)
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_events} events of this workload ({secs:.1f} s), FP64 C oracle, OpenMP"}
+               "sample": f"{args.cpu_events} events of this workload ({secs:.1f} s), FP64 C oracle, OpenMP",
+               "single_thread": {"value": rate1, "unit": "events/s", "cores": 1,
+                                 "sample": f"{n1} events ({secs1:.1f} s), one thread"}}
     def optional(fn, skip):
         if skip or world > 1:
             return None

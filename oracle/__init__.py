@@ -348,6 +348,13 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Threads of the following oracle calls (for timing it single-threaded)."""
+    L = lib()
+    L.or_set_num_threads.argtypes = [C.c_int]
+    L.or_set_num_threads(int(n))
+
+
 # --------------------------------------------------------------------------
 # learned proposal (multilayer perceptron) and deviance
 # --------------------------------------------------------------------------

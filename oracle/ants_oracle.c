@@ -737,6 +737,18 @@ int or_num_threads(void)
 #endif
 }
 
+/* Run the following calls on n threads (timing the oracle single-threaded
+ * and on all cores); no effect without OpenMP. */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Learned proposal: multilayer perceptron (the ANN role of Sec. 5.1.3)      */
 /* ------------------------------------------------------------------------ */
