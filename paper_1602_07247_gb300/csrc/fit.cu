@@ -15,7 +15,9 @@
 //      local normal matrix of the 4^d basis functions that are non-zero on
 //      the cell (upper triangle) and the local right-hand sides, each entry
 //      summed by one thread over the item's samples in order (weights and
-//      values staged in shared memory tile by tile)
+//      values staged in shared memory tile by tile); for one-dimensional
+//      single-set fits each thread sums all entries over its share of the
+//      item's samples and a fixed tree adds the threads' sums
 //   4. per cell, the sum of its items' entries (8 interleaved lanes, then
 //      the lanes in order)
 //   5. A(u, v) and r(u, s): over the cells that cover them, in cell order
@@ -270,6 +272,61 @@ __global__ void __launch_bounds__(kPartThreads) fit_cell_partials(FitGrid g, int
     }
 }
 
+// The same partial sums for one-dimensional fits of one value set (radial
+// profiles: 10 matrix entries and 4 right-hand sides), sample-parallel:
+// thread t accumulates all 14 entries over the item's samples t, t + T, ...
+// in order, then the threads' sums are added by a fixed tree per entry (an
+// FP64 instruction costs the same whatever its active lanes, so every lane
+// works).
+constexpr int kOut1 = 14;
+constexpr int kPer1 = 4096;  // samples per work item
+
+__global__ void __launch_bounds__(kPartThreads) fit_cell_partials_1d(FitGrid g, const int *offset,
+                                                                      const int *item_off, const int *idx,
+                                                                      const double *pts, const double *vals,
+                                                                      double *partial)
+{
+    __shared__ double s_red[kOut1][kPartThreads];
+    const long item = blockIdx.x;
+    int lo = 0, hi = g.n_cells - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = lo;
+    const long k0 = offset[c] + (item - item_off[c]) * (long)kPer1;
+    const long kend = offset[c + 1] < k0 + kPer1 ? (long)offset[c + 1] : k0 + kPer1;
+    double acc[kOut1];
+#pragma unroll
+    for (int o = 0; o < kOut1; ++o) acc[o] = 0.0;
+    for (long k = k0 + threadIdx.x; k < kend; k += kPartThreads) {
+        const long p = idx[k];
+        double t, w[4];
+        axis_span(g, 0, pts[p], t);
+        bs_weights_f64(t, w);
+        const double v = vals[p];
+        int o = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a; b < 4; ++b) acc[o++] += w[a] * w[b];  // o = tri_index(a, b, 4)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[10 + a] += w[a] * v;
+    }
+#pragma unroll
+    for (int o = 0; o < kOut1; ++o) s_red[o][threadIdx.x] = acc[o];
+    __syncthreads();
+    for (int half = kPartThreads / 2; half > 0; half >>= 1) {
+        for (int q = threadIdx.x; q < kOut1 * half; q += kPartThreads) {
+            const int o = q / half, j = q - o * half;
+            s_red[o][j] += s_red[o][j + half];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kOut1) partial[item * kOut1 + threadIdx.x] = s_red[threadIdx.x][0];
+}
+
 // cellsum[c][o] = the sum over cell c's items of partial[item][o]: lane l of
 // kRedLanes sums the items l, l + kRedLanes, ... in order, then the lanes
 // are added in order
@@ -488,7 +545,8 @@ int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo,
     const int nc = g.n_coef, W = g.bw + 1;
     const int n_mat = g.nloc * (g.nloc + 1) / 2;
     const long n_out = n_mat + (long)g.nloc * n_sets;
-    const int per_item = n_out <= 64 ? 1024 : 2048;
+    const bool one_d = dims == 1 && n_sets == 1;  // n_out == kOut1: the sample-parallel kernel
+    const int per_item = one_d ? kPer1 : (n_out <= 64 ? 1024 : 2048);
     const int tile = part_tile(g.nloc, n_sets);
     const long n_chunks = (n_pts + kRadixChunk - 1) / kRadixChunk;
     int bits = 0;
@@ -560,7 +618,10 @@ int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo,
     char *pbase = (char *)ctx_scratch(ctx, 9, cp.off);
     if (!pbase) return ANTS_E_OOM;
     double *part = (double *)(pbase + o_part);
-    if (n_items > 0) {
+    if (n_items > 0 && one_d) {
+        fit_cell_partials_1d<<<(unsigned)n_items, kPartThreads, 0, st>>>(g, off, itoff, idx, pts, vals, part);
+        ++launches;
+    } else if (n_items > 0) {
         const size_t smem = (size_t)tile * (12 + g.nloc + n_sets) * sizeof(double) + (size_t)tile * sizeof(long);
         fit_cell_partials<<<(unsigned)n_items, kPartThreads, smem, st>>>(g, n_sets, per_item, tile, off, itoff, idx,
                                                                          pts, vals, part);

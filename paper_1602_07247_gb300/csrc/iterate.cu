@@ -103,8 +103,10 @@ __global__ void chi2_kernel(LrfDev L, const float *sig, long n_e, const float *x
             bool ok;
             const float mu = En * lrf_eta_point(L, i, x, y, z, ok);
             if (ok && mu > 0.0f) {
+                // the difference is exact in FP64; the term in FP32 (FP64
+                // division is scarce), the sum in FP64
                 const double d = (double)si - (double)mu;
-                acc += d * d / (double)mu;
+                acc += (double)__fdividef((float)(d * d), mu);
             }
         }
     }
