@@ -14,6 +14,9 @@ Functions follow the paper (Morozov et al., arXiv:1602.07247):
   lrf_fit        Sec. 6 B-spline LRFs fitted to (position, value) data
   lrf_eval       Sec. 6.1.1 / 6.1.2 axial, XY and XYZ LRFs, Sec. 6.2 grouping
   bspline_*      uniform cubic B-spline basis (Cox-de Boor)
+  cgs_variant(_replay)
+                 Sec. 5.1.2 / 5.3 search variants: least squares, strongest-
+                 sensor start, sensor cuts, passive sensors
   chi2_at, event_filter
                  Sec. 5.2 reconstruction chi-squared and event cuts
   shift_xy, lrf_refit, gain_refit, centroid_lrf, lrf_iterate
@@ -330,6 +333,74 @@ def cgs_replay(lrf: Lrf, params: CgsParams, sig, trace, gain_cog=None, start_xyz
     g, st = _opt(gain_cog), _opt(start_xyz)
     lib(mutant).or_cgs_replay(C.byref(s), C.byref(p), _p(g), _p(st), n, _d(sig), _i(tr), float(tau_rel), _d(xyz), _d(E), _d(logL), _i(status),
                               _i(n_tie), _i(n_bad))
+    return dict(xyz=xyz, E=E, logL=logL, status=status, n_tie=n_tie, n_bad=n_bad)
+
+
+class _Variant(C.Structure):
+    _fields_ = [("criterion", C.c_int), ("start", C.c_int), ("min_signal", C.c_double),
+                ("max_distance", C.c_double), ("passive", _I)]
+
+
+@dataclass
+class Variant:
+    """Search variant (Sec. 5.1.2, 5.3): criterion 0 maximum likelihood / 1
+    least squares; start 0 centroid / 1 strongest sensor; sensors below
+    min_signal or farther than max_distance from the start (when > 0) and
+    passive ones are left out of the match."""
+
+    criterion: int = 0
+    start: int = 0
+    min_signal: float = 0.0
+    max_distance: float = 0.0
+    passive: np.ndarray | None = None
+    _keep: list = field(default_factory=list, repr=False)
+
+    def _struct(self) -> _Variant:
+        pas = None if self.passive is None else np.ascontiguousarray(np.asarray(self.passive, dtype=np.int32))
+        self._keep[:] = [pas]
+        return _Variant(int(self.criterion), int(self.start), float(self.min_signal), float(self.max_distance),
+                        _i(pas) if pas is not None else C.cast(None, _I))
+
+
+def _vlib(mutant=0):
+    L = lib(mutant)
+    if not getattr(L, "_var_declared", False):
+        L.or_cgs_variant.argtypes = [C.POINTER(_Lrf), C.POINTER(_Cgs), C.POINTER(_Variant), _D, C.c_long, _D, _D,
+                                     _D, _D, _I, _I]
+        L.or_cgs_variant_replay.argtypes = [C.POINTER(_Lrf), C.POINTER(_Cgs), C.POINTER(_Variant), _D, C.c_long,
+                                            _D, _I, C.c_double, _D, _D, _D, _I, _I, _I]
+        L._var_declared = True
+    return L
+
+
+def cgs_variant(lrf: Lrf, params: CgsParams, sig, variant: Variant, gain=None, mutant: int = 0):
+    """Contracting grids with a search variant; gain: the relative gains used
+    by the start (centroid weights, strongest-sensor comparison)."""
+    sig = _f64(sig)
+    n = sig.shape[0]
+    s, p, v = lrf._struct(), params._struct(), variant._struct()
+    xyz, E, logL = np.empty((n, 3)), np.empty(n), np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    trace = np.empty((n, params.iters), dtype=np.int32)
+    g = _opt(gain)
+    _vlib(mutant).or_cgs_variant(C.byref(s), C.byref(p), C.byref(v), _p(g), n, _d(sig), _d(xyz), _d(E), _d(logL),
+                                 _i(status), _i(trace))
+    return dict(xyz=xyz, E=E, logL=logL, status=status, trace=trace)
+
+
+def cgs_variant_replay(lrf: Lrf, params: CgsParams, sig, variant: Variant, trace, gain=None,
+                       tau_rel: float = TAU_REL, mutant: int = 0):
+    sig = _f64(sig)
+    n = sig.shape[0]
+    tr = np.ascontiguousarray(np.asarray(trace, dtype=np.int32))
+    s, p, v = lrf._struct(), params._struct(), variant._struct()
+    xyz, E, logL = np.empty((n, 3)), np.empty(n), np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    n_tie = np.empty(n, dtype=np.int32)
+    n_bad = np.empty(n, dtype=np.int32)
+    g = _opt(gain)
+    _vlib(mutant).or_cgs_variant_replay(C.byref(s), C.byref(p), C.byref(v), _p(g), n, _d(sig), _i(tr),
+                                        float(tau_rel), _d(xyz), _d(E), _d(logL), _i(status), _i(n_tie), _i(n_bad))
     return dict(xyz=xyz, E=E, logL=logL, status=status, n_tie=n_tie, n_bad=n_bad)
 
 

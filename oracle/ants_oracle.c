@@ -701,6 +701,251 @@ void or_cgs_replay(const or_lrf *L, const or_cgs_params *P, const double *gain_c
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Search variants.  Sec. 5.1.2: the match is either maximum likelihood or   */
+/* least squares, and sensors whose signal is below a threshold or that lie  */
+/* farther than a given distance from the start position can be ignored;    */
+/* Sec. 5.1.2.1 / 5.1.2.2: the start is the centroid or the position of the  */
+/* sensor with the strongest signal; Sec. 5.3: passive sensors are ignored.  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int criterion;        /* 0: maximum likelihood, 1: least squares */
+    int start;            /* 0: centroid, 1: sensor with the strongest signal */
+    double min_signal;    /* > 0: sensors with s_i < min_signal are ignored */
+    double max_distance;  /* > 0: sensors farther than this from the start are ignored */
+    const int *passive;   /* nullable [n_sensors]: nonzero = passive */
+} or_variant;
+
+static int or_passive(const or_variant *V, int i) { return V->passive && V->passive[i]; }
+
+/* A node is inside the domain when the LRF of every sensor in the match is
+ * defined there (radial: within reach of each; XY / XYZ: inside the box). */
+static int or_variant_valid(const or_lrf *L, const int *act, double x, double y, double z)
+{
+    if (L->type == OR_RADIAL) {
+        for (int i = 0; i < L->n_sensors; ++i) {
+            if (!act[i]) continue;
+            double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r >= L->lo[0] && r <= L->hi[0])) return 0;
+        }
+        return 1;
+    }
+    return or_node_valid(L, x, y, z);
+}
+
+/* Start position, the sensors in the match (act) and their signal sum. */
+static int or_variant_start(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const double *gain,
+                            const double *s, double *cx, double *cy, double *cz, double *S_out, int *act)
+{
+    int n = L->n_sensors;
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+        act[i] = 0;
+        if (or_passive(V, i)) continue;
+        if (!isfinite(s[i]) || s[i] < 0.0) return OR_EVT_BAD_SIGNAL;
+        tot += s[i];
+    }
+    *S_out = 0.0;
+    if (!(tot > 0.0)) return OR_EVT_ZERO_SIGNAL;
+    if (V->start == 1) {
+        int best = -1;
+        double bv = -1.0;
+        for (int i = 0; i < n; ++i) {
+            if (or_passive(V, i)) continue;
+            double v = s[i] / (gain ? gain[i] : 1.0);
+#if OR_MUTANT == 17
+            if (best < 0 || v < bv) {
+#else
+            if (v > bv) {
+#endif
+                bv = v;
+                best = i;
+            }
+        }
+        *cx = L->sensor_xy[2 * best];
+        *cy = L->sensor_xy[2 * best + 1];
+    } else {
+        double nx = 0.0, ny = 0.0, den = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (or_passive(V, i)) continue;
+            double w = s[i] / (gain ? gain[i] : 1.0);
+            nx += L->sensor_xy[2 * i] * w;
+            ny += L->sensor_xy[2 * i + 1] * w;
+            den += w;
+        }
+        *cx = nx / den;
+        *cy = ny / den;
+    }
+    *cz = (L->type == OR_XYZ) ? P->z0 : 0.0;
+    if (L->type != OR_RADIAL) {
+        if (*cx < L->lo[0]) *cx = L->lo[0];
+        if (*cx > L->hi[0]) *cx = L->hi[0];
+        if (*cy < L->lo[1]) *cy = L->lo[1];
+        if (*cy > L->hi[1]) *cy = L->hi[1];
+    }
+    double S = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (or_passive(V, i)) continue;
+        int a = 1;
+        if (V->min_signal > 0.0 && s[i] < V->min_signal) a = 0;
+        if (V->max_distance > 0.0) {
+#if OR_MUTANT == 18
+            double dx = L->sensor_xy[2 * i], dy = L->sensor_xy[2 * i + 1];
+#else
+            double dx = L->sensor_xy[2 * i] - *cx, dy = L->sensor_xy[2 * i + 1] - *cy;
+#endif
+            if (sqrt(dx * dx + dy * dy) > V->max_distance) a = 0;
+        }
+        act[i] = a;
+        if (a) S += s[i];
+    }
+    *S_out = S;
+    if (!(S > 0.0)) return OR_EVT_ZERO_SIGNAL;
+    if (!or_variant_valid(L, act, *cx, *cy, *cz)) return OR_EVT_OUT_OF_DOMAIN;
+    return OR_EVT_OK;
+}
+
+/* The match at a node, larger is better.  Maximum likelihood: F = sum_A s
+ * ln eta - S ln H (the profiled objective over the sensors A in the match).
+ * Least squares (reading: Poisson variances as weights): minus Pearson's
+ * sum_A (s - E eta)^2 / (E eta) with E = S / H, the node's energy ratio. */
+static double or_variant_score(const or_lrf *L, const or_variant *V, const int *act, const double *s, double S,
+                               double x, double y, double z)
+{
+    if (!or_variant_valid(L, act, x, y, z)) return -INFINITY;
+    double H = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i)
+        if (act[i]) H += or_eta_floored(L, i, x, y, z);
+    if (V->criterion == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < L->n_sensors; ++i)
+            if (act[i] && s[i] != 0.0) acc += s[i] * log(or_eta_floored(L, i, x, y, z));
+        return acc - S * log(H);
+    }
+    double E = S / H, chi = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        if (!act[i]) continue;
+        double mu = E * or_eta_floored(L, i, x, y, z), d = s[i] - mu;
+#if OR_MUTANT == 16
+        chi += d * d;
+#else
+        chi += d * d / mu;
+#endif
+    }
+    return -chi;
+}
+
+/* E = S / H and the full Poisson log-likelihood over the sensors in the match. */
+static void or_variant_energy_logl(const or_lrf *L, const int *act, const double *s, double S, double x, double y,
+                                   double z, double *E_out, double *logL_out)
+{
+    double H = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i)
+        if (act[i]) H += or_eta_floored(L, i, x, y, z);
+    double E = S / H, ll = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i) {
+        if (!act[i]) continue;
+        double mu = E * or_eta_floored(L, i, x, y, z);
+        ll += (s[i] != 0.0 ? s[i] * log(mu) : 0.0) - mu - lgamma(s[i] + 1.0);
+    }
+    *E_out = E;
+    *logL_out = ll;
+}
+
+/* Magnitude of the terms summed at a node, for the tie tolerance of the
+ * replay: sum_A |s ln p| (maximum likelihood, p = eta / H) or sum_A (s +
+ * E eta) (least squares). */
+static double or_variant_mag(const or_lrf *L, const or_variant *V, const int *act, const double *s, double S,
+                             double x, double y, double z)
+{
+    double H = 0.0, mag = 0.0;
+    for (int i = 0; i < L->n_sensors; ++i)
+        if (act[i]) H += or_eta_floored(L, i, x, y, z);
+    for (int i = 0; i < L->n_sensors; ++i) {
+        if (!act[i]) continue;
+        double eta = or_eta_floored(L, i, x, y, z);
+        mag += V->criterion == 0 ? fabs(s[i] * log(eta / H)) : s[i] + S / H * eta;
+    }
+    return mag;
+}
+
+/* The contracting-grid search of or_cgs with the variant's criterion, start
+ * and sensor selection; with trace_in (not NULL) the replay of another
+ * implementation's path under the tie rule of or_cgs_replay (tau = tau_rel
+ * times or_variant_mag at the grid's centre). */
+static void or_cgs_variant_run(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const double *gain,
+                               long n_e, const double *sig, const int *trace_in, double tau_rel, double *xyz,
+                               double *E, double *logL, int *status, int *trace, int *n_tie, int *n_bad)
+{
+    int nodes = P->n_xy * P->n_xy * P->n_z;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        int *act = (int *)malloc(sizeof(int) * (size_t)L->n_sensors);
+        double cx, cy, cz, S;
+        int st = or_variant_start(L, P, V, gain, s, &cx, &cy, &cz, &S, act);
+        status[e] = st;
+        if (n_tie) n_tie[e] = 0;
+        if (n_bad) n_bad[e] = 0;
+        if (st != OR_EVT_OK) {
+            or_set_nan(&xyz[3 * e], &E[e], &logL[e]);
+            if (trace) for (int it = 0; it < P->iters; ++it) trace[e * P->iters + it] = -1;
+            free(act);
+            continue;
+        }
+        double sxy = P->step_xy, sz = P->step_z;
+        for (int it = 0; it < P->iters; ++it) {
+            double best = -INFINITY;
+            int best_k = -1;
+            for (int k = 0; k < nodes; ++k) {
+                double x, y, z;
+                or_node(P, cx, cy, cz, sxy, sz, k, &x, &y, &z);
+                double F = or_variant_score(L, V, act, s, S, x, y, z);
+                if (F > best) { best = F; best_k = k; }
+            }
+            int g = best_k;
+            if (trace_in) {
+                g = trace_in[e * P->iters + it];
+                if (g < 0 || g >= nodes) { n_bad[e]++; g = best_k; }
+                if (g != best_k) {
+                    double gx, gy, gz;
+                    or_node(P, cx, cy, cz, sxy, sz, g, &gx, &gy, &gz);
+                    double Fg = or_variant_score(L, V, act, s, S, gx, gy, gz);
+                    double tau = tau_rel * or_variant_mag(L, V, act, s, S, cx, cy, cz);
+                    if (isfinite(Fg) && Fg >= best - tau) n_tie[e]++;
+                    else n_bad[e]++;
+                }
+            }
+            double x, y, z;
+            or_node(P, cx, cy, cz, sxy, sz, g, &x, &y, &z);
+            cx = x; cy = y; cz = z;
+            if (trace) trace[e * P->iters + it] = g;
+            sxy *= P->shrink;
+            sz *= P->shrink;
+        }
+        xyz[3 * e] = cx;
+        xyz[3 * e + 1] = cy;
+        xyz[3 * e + 2] = cz;
+        or_variant_energy_logl(L, act, s, S, cx, cy, cz, &E[e], &logL[e]);
+        free(act);
+    }
+}
+
+void or_cgs_variant(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const double *gain, long n_e,
+                    const double *sig, double *xyz, double *E, double *logL, int *status, int *trace)
+{
+    or_cgs_variant_run(L, P, V, gain, n_e, sig, NULL, 0.0, xyz, E, logL, status, trace, NULL, NULL);
+}
+
+void or_cgs_variant_replay(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const double *gain,
+                           long n_e, const double *sig, const int *trace_in, double tau_rel, double *xyz, double *E,
+                           double *logL, int *status, int *n_tie, int *n_bad)
+{
+    or_cgs_variant_run(L, P, V, gain, n_e, sig, trace_in, tau_rel, xyz, E, logL, status, NULL, n_tie, n_bad);
+}
+
 /* Exhaustive search: the best node of a regular nx x ny grid over
  * [x_lo, x_hi] x [y_lo, y_hi] at height z (ties to the lowest index). */
 void or_brute_force(const or_lrf *L, long n_e, const double *sig, double x_lo, double x_hi,

@@ -743,6 +743,109 @@ def pin_iterative_lrf_converges(mutant=0):
     ft = oracle.spline_eval(Lt.n_int[:1], Lt.lo[:1], Lt.hi[:1], Lt.coef[0], rr)
     assert np.abs(f / f[0] - ft / ft[0]).max() < 0.03
 
+# --------------------------------------------------------------------------
+# search variants (Sec. 5.1.2, 5.3)
+# --------------------------------------------------------------------------
+
+
+def _variant_events(L, g, n, seed, extent=12.0, e0=2500.0):
+    return synth.draw_events(L.sensor_xy, g, n, seed, region="square", extent=extent, e0=e0).signals
+
+
+def pin_variant_defaults_and_passive(mutant=0):
+    """With no option set the variant search is the plain search, bit for
+    bit; a passive sensor (Sec. 5.3) gives exactly the search on the detector
+    without that sensor (its LRF, signal and gain removed)."""
+    L, g = _small_xy_lrf(mutant)
+    P = oracle.CgsParams(n_xy=9, iters=6, step_xy=1.5)
+    sig = _variant_events(L, g, 60, 5)
+    a = oracle.cgs(L, P, sig, gain_cog=g, mutant=mutant)
+    b = oracle.cgs_variant(L, P, sig, oracle.Variant(), gain=g, mutant=mutant)
+    for k in ("xyz", "E", "logL", "status", "trace"):
+        assert np.array_equal(a[k], b[k]), k
+    keep = np.array([i for i in range(9) if i != 4])
+    L2 = oracle.Lrf(oracle.XY, L.sensor_xy[keep], L.n_int, L.lo, L.hi, L.coef[keep])
+    c = oracle.cgs(L2, P, sig[:, keep], gain_cog=g[keep], mutant=mutant)
+    pas = np.zeros(9, dtype=int)
+    pas[4] = 1
+    sig_bad = sig.copy()
+    sig_bad[:, 4] = -7.0  # a passive sensor's signal is never read
+    d = oracle.cgs_variant(L, P, sig_bad, oracle.Variant(passive=pas), gain=g, mutant=mutant)
+    for k in ("xyz", "E", "logL", "status", "trace"):
+        assert np.array_equal(c[k], d[k]), k
+
+
+def pin_variant_start_and_cuts(mutant=0):
+    """The strongest-sensor start (Sec. 5.1.2.1) is the plain search started
+    at the sensor with the largest s_i / g_i; the signal cut and the distance
+    cut (Sec. 5.1.2) equal, event by event, the search with the cut sensors
+    made passive, whenever the cut keeps the start sensor (the distance cut
+    always does; the start is chosen before any cut)."""
+    L, g = _small_xy_lrf(mutant)
+    P = oracle.CgsParams(n_xy=9, iters=6, step_xy=1.5)
+    sig = _variant_events(L, g, 40, 6)
+    best = np.argmax(sig / g[None, :], axis=1)
+    start = np.concatenate([L.sensor_xy[best], np.zeros((40, 1))], axis=1)
+    a = oracle.cgs(L, P, sig, start_xyz=start, mutant=mutant)
+    b = oracle.cgs_variant(L, P, sig, oracle.Variant(start=1), gain=g, mutant=mutant)
+    for k in ("xyz", "E", "logL", "trace"):
+        assert np.array_equal(a[k], b[k]), k
+    thr, R = 100.0, 9.0
+    n_sig = 0
+    for e in range(40):
+        s1 = sig[e:e + 1]
+        cuts = [(dict(max_distance=R), np.hypot(*(L.sensor_xy - start[e, :2]).T) > R)]
+        if s1[0, best[e]] >= thr:
+            cuts.append((dict(min_signal=thr), s1[0] < thr))
+            n_sig += 1
+        for cut, pas in cuts:
+            x = oracle.cgs_variant(L, P, s1, oracle.Variant(start=1, **cut), gain=g, mutant=mutant)
+            y = oracle.cgs_variant(L, P, s1, oracle.Variant(start=1, passive=pas.astype(int)), gain=g, mutant=mutant)
+            for k in ("xyz", "E", "logL", "trace"):
+                assert np.array_equal(x[k], y[k], equal_nan=k != "trace"), (e, cut, k)
+    assert n_sig >= 10, n_sig
+
+
+def pin_least_squares(mutant=0):
+    """Least-squares criterion (Sec. 5.1.2), read as Pearson's statistic with
+    E = S / H: noise-free signals are recovered exactly (the statistic is 0
+    only at the source; the strongest-sensor start puts the source on a node
+    of the first grid), and on a tiny detector the contracting-grid result is
+    the minimum of (H / S) sum s_i^2 / eta_i - S (the same statistic in
+    another algebraic form) over an exhaustive fine grid."""
+    L, g = _small_xy_lrf(mutant)
+    P = oracle.CgsParams(n_xy=9, iters=6, step_xy=1.5)
+    xt = np.array([[3.0, -1.5]])
+    s = np.array([[2500.0]]) * oracle.lrf_eval(L, xt, mutant=mutant)
+    assert np.argmax(s[0] / g) == 4  # the centre sensor, at (0, 0)
+    v = oracle.cgs_variant(L, P, s, oracle.Variant(criterion=1, start=1), gain=g, mutant=mutant)
+    assert v["status"][0] == 0
+    assert np.abs(v["xyz"][0, :2] - xt[0]).max() < 1e-12 and abs(v["E"][0] / 2500.0 - 1) < 1e-12, v["xyz"]
+    sxy = synth.square_array(2, 10.0)
+    g4 = np.array([1.0, 0.95, 1.05, 1.02])
+    n_int, lo, hi = (10, 10), (-15.0, -15.0), (15.0, 15.0)
+    pts = synth.grid_samples(n_int, lo, hi, 4)
+    coef, _, _ = oracle.lrf_fit(n_int, lo, hi, pts, synth.truth_eta(sxy, g4, pts, r0=20.0), mutant=mutant)
+    L4 = oracle.Lrf(oracle.XY, sxy, n_int + (0,), lo + (0,), hi + (0,), coef)
+    ev = synth.draw_events(sxy, g4, 60, 78, region="square", extent=6.0, e0=4000.0, r0=20.0)
+    P4 = oracle.CgsParams(n_xy=9, iters=8, step_xy=3.75)
+    x = oracle.cgs_variant(L4, P4, ev.signals, oracle.Variant(criterion=1), gain=g4, mutant=mutant)
+    fine = 0.05
+    gx = np.linspace(-15, 15, int(30 / fine) + 1)
+    X, Y = np.meshgrid(gx, gx)
+    grid = np.stack([X.ravel(), Y.ravel()], axis=1)
+    eta = oracle.lrf_eval(L4, grid, mutant=mutant)
+    H = eta.sum(1)
+    ok = 0
+    for e in range(60):
+        sv = ev.signals[e]
+        S = sv.sum()
+        stat = H / S * (sv[None, :] ** 2 / eta).sum(1) - S
+        bxy = grid[np.argmin(stat)]
+        d = np.hypot(*(x["xyz"][e, :2] - bxy))
+        ok += d <= 2.0 * (fine + P4.step_xy * P4.shrink ** (P4.iters - 1))
+    assert ok / 60 >= 0.95, ok
+
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
@@ -750,4 +853,5 @@ ALL_PINS = [
     pin_event_status, pin_replay, pin_gelu, pin_mlp_forward, pin_mlp_gradient, pin_adam, pin_deviance,
     pin_poisson_sampler, pin_uniform_stream, pin_simulator, pin_logtable_ranks_like_likelihood,
     pin_chi2, pin_event_filter, pin_shift, pin_lrf_refit_exact, pin_iterative_lrf_converges,
+    pin_variant_defaults_and_passive, pin_variant_start_and_cuts, pin_least_squares,
 ]

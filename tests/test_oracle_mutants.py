@@ -21,6 +21,9 @@ MUTANTS = {
     13: "chi-squared terms without the division by the mean count",
     14: "random shift with cos for both components",
     15: "gain refit dividing by sum f instead of sum f^2",
+    16: "least-squares terms without the Poisson weight",
+    17: "strongest-sensor start picking the weakest sensor",
+    18: "distance cut measured from the origin instead of the start",
 }
 
 
