@@ -352,6 +352,49 @@ def radial_run(args, ants, torch, ctx, stream):
                         "contracting grid 9x9 x 6 grids, plain FP32", **out}
 
 
+def variants_run(args, ants, torch, ctx, stream):
+    """Search variants (Sec. 5.1.2, 5.3) on the 8x8 SiPM workload, 10^6
+    events: maximum likelihood through the per-node variant kernel, least
+    squares, and maximum likelihood with the strongest-sensor start, signal
+    and distance cuts and a passive sensor; events/s and the XY roofline."""
+    import synth.workloads
+    w = workload()
+    det = ants.Detector(w.sensor_xy, w.gains)
+    pts, vals = w.fit_samples()
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    n = 1_000_000
+    ev = w.events(n, seed=w.event_seed)
+    sig = torch.from_numpy(ev.signals).cuda()
+    pas = np.zeros(w.n_sensors, dtype=np.uint8)
+    pas[27] = 1
+    cases = {"ml": ants.VariantParams(p),
+             "ls": ants.VariantParams(p, criterion=ants.ANTS_CRIT_LS),
+             "ml_max_sensor_cuts_passive": ants.VariantParams(p, start=ants.ANTS_START_MAX_SENSOR, min_signal=60.0,
+                                                              max_distance=25.0, passive=pas)}
+    out = {}
+    evals = n * w.n_xy * w.n_xy * w.iters * w.n_sensors
+    for name, vp in cases.items():
+        for _ in range(2):
+            res = ants.reconstruct(ctx, lrf, vp, sig, stream=stream, method=ants.ANTS_CGS_VARIANT)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            res = ants.reconstruct(ctx, lrf, vp, sig, stream=stream, method=ants.ANTS_CGS_VARIANT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / 2
+        d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+        ok = res.status.cpu().numpy() == 0
+        out[name] = {"events_per_s": n / dt, "ms_per_launch": 1e3 * dt,
+                     "roofline": alu_roofline(evals / dt, "xy"),
+                     "rms_dxy_mm": float(np.sqrt((d[ok] ** 2).sum(1).mean())), "ok_frac": float(ok.mean())}
+    return {"workload": f"{w.name}: 64 sensors, XY LRF, {n} events, 11x11 x 8 grids; per-node variant kernel "
+                        "(least squares evaluates every node twice); cuts: signal >= 60, within 25 mm of the "
+                        "strongest sensor, sensor 27 passive", **out}
+
+
 def iterative_run(args, ants, torch, ctx, stream):
     """Iterative LRF reconstruction (Sec. 8) from a flood of 10^6 events of the
     19-PMT detector (relative gains N(1, 0.1^2), known): from a too-wide
@@ -588,13 +631,14 @@ def run_ours(args):
     forms = optional(forms_comparison, args.no_forms)
     batched = optional(batched_run, args.no_batched)
     iterative = optional(iterative_run, args.no_iterative)
+    variants = optional(variants_run, args.no_variants)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
-        "iterative_lrf": iterative,
+        "iterative_lrf": iterative, "variants_8x8": variants,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -620,6 +664,7 @@ def main():
     ap.add_argument("--train-events", type=int, default=1_000_000)
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-detector 3D batched run")
     ap.add_argument("--no-iterative", action="store_true", help="skip the iterative LRF reconstruction")
+    ap.add_argument("--no-variants", action="store_true", help="skip the search variants")
     ap.add_argument("--iter-events", type=int, default=1_000_000)
     ap.add_argument("--iter-cycles", type=int, default=6)
     ap.add_argument("--batch-steps", type=int, default=1)

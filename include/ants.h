@@ -78,8 +78,15 @@ typedef enum {
 typedef enum {
     ANTS_CGS_PLAIN = 0, /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
     ANTS_GEMM_TOPK = 1, /* global-grid tensor-core scores, top-K, local contracting grids */
-    ANTS_MLP_SEEDED = 2 /* network proposal + local contracting grids + plain fallback */
+    ANTS_MLP_SEEDED = 2, /* network proposal + local contracting grids + plain fallback */
+    ANTS_CGS_VARIANT = 3 /* contracting grids with another criterion, start or sensor selection */
 } ants_method;
+
+/* Match criterion of ANTS_CGS_VARIANT (Sec. 5.1.2). */
+typedef enum { ANTS_CRIT_ML = 0, ANTS_CRIT_LS = 1 } ants_criterion;
+
+/* Start position of ANTS_CGS_VARIANT (Sec. 5.1.2.1, 5.1.2.2). */
+typedef enum { ANTS_START_COG = 0, ANTS_START_MAX_SENSOR = 1 } ants_start_mode;
 
 /* Signal element types. */
 /* Element type of signal arrays: FP32, or FP16 (IEEE binary16; widened to
@@ -165,6 +172,36 @@ typedef struct {
     float nms_cells;
     ants_cgs_params refine;
 } ants_gemm_params;
+
+/* Parameters of ANTS_CGS_VARIANT: the contracting grids of `grid` with
+ *   criterion: ANTS_CRIT_ML, maximum likelihood (the score of ANTS_CGS_PLAIN
+ *     over the sensors in the match), or ANTS_CRIT_LS, least squares read as
+ *     Pearson's statistic sum (s_i - E eta_i)^2 / (E eta_i) with the node's
+ *     energy ratio E = sum s / sum eta over the sensors in the match
+ *     (smallest wins);
+ *   start: ANTS_START_COG, the centroid of the non-passive sensors with the
+ *     detector's relative gains, or ANTS_START_MAX_SENSOR, the position of the
+ *     non-passive sensor with the largest s_i / g_i (ties: lowest index);
+ *     clamped into the XY box of an XY / XYZ LRF;
+ *   the sensors in the match: the non-passive ones (passive_host[i] != 0,
+ *     Sec. 5.3: never read, not even for the status), without those whose
+ *     signal is below min_signal (when > 0) or whose distance from the start
+ *     exceeds max_distance (when > 0) (Sec. 5.1.2).
+ * E is S / H and logL the full Poisson log-likelihood over the sensors in the
+ * match.  Status: BAD_SIGNAL for a negative or non-finite non-passive
+ * signal, ZERO_SIGNAL when the non-passive or the matched signals sum to 0,
+ * OUT_OF_DOMAIN when an LRF in the match is undefined at the start.  At most
+ * 1024 sensors; every LRF type; no start_xyz (the variant picks its start);
+ * the trace is supported.  Every node is evaluated on its own (no separable
+ * form), so variants run slower than ANTS_CGS_PLAIN. */
+typedef struct {
+    ants_cgs_params grid;
+    int criterion;
+    int start;
+    float min_signal;
+    float max_distance;
+    const unsigned char *passive_host; /* nullable, [n_sensors], read during the call */
+} ants_cgs_variant_params;
 
 /* Parameters of ANTS_MLP_SEEDED: the network's (x, y), clamped into the LRF's
  * XY box, starts the `refine` search; events whose Poisson deviance

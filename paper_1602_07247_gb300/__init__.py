@@ -29,6 +29,9 @@ ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
 ANTS_CGS_PLAIN = 0
 ANTS_GEMM_TOPK = 1
 ANTS_MLP_SEEDED = 2
+ANTS_CGS_VARIANT = 3
+ANTS_CRIT_ML, ANTS_CRIT_LS = 0, 1
+ANTS_START_COG, ANTS_START_MAX_SENSOR = 0, 1
 ANTS_F32 = 0
 ANTS_F16 = 1
 ANTS_NOALLOC_STAGE_BYTES = 33554432
@@ -109,6 +112,17 @@ class SeededParams(C.Structure):
     """ants_mlp_seeded_params: network start, local refine, plain fallback."""
     _fields_ = [("mlp", C.c_void_p), ("bf16", C.c_int), ("refine", CgsParams), ("fallback", CgsParams),
                 ("deviance_max", C.c_float), ("border_fallback", C.c_int)]
+
+
+class VariantParams(C.Structure):
+    """ants_cgs_variant_params: grid, criterion, start, sensor cuts, passive mask."""
+    _fields_ = [("grid", CgsParams), ("criterion", C.c_int), ("start", C.c_int), ("min_signal", C.c_float),
+                ("max_distance", C.c_float), ("passive_host", C.c_void_p)]
+
+    def __init__(self, grid, criterion=0, start=0, min_signal=0.0, max_distance=0.0, passive=None):
+        self._passive = None if passive is None else np.ascontiguousarray(np.asarray(passive, dtype=np.uint8))
+        super().__init__(grid, int(criterion), int(start), float(min_signal), float(max_distance),
+                         None if self._passive is None else self._passive.ctypes.data)
 
 
 class EventCuts(C.Structure):
@@ -771,7 +785,8 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     E = torch.empty(n, dtype=torch.float32, device=dev)
     logL = torch.empty(n, dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
-    iters = params.refine.iters if isinstance(params, (SeededParams, GemmParams)) else params.iters
+    iters = (params.refine.iters if isinstance(params, (SeededParams, GemmParams))
+             else params.grid.iters if isinstance(params, VariantParams) else params.iters)
     trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
     dtype = ANTS_F16 if signals.dtype == torch.float16 else ANTS_F32

@@ -495,6 +495,7 @@ static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const vo
         return fail(ANTS_E_ARG, "ants_reconstruct: signal dtype %d", signal_dtype);
     if (method == ANTS_MLP_SEEDED) return check_seeded_params(lrf, (const ants_mlp_seeded_params *)params);
     if (method == ANTS_GEMM_TOPK) return check_gemm_params(lrf, (const ants_gemm_params *)params);
+    if (method == ANTS_CGS_VARIANT) return check_variant_params(lrf, (const ants_cgs_variant_params *)params);
     if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
     return check_cgs_params(lrf, (const ants_cgs_params *)params);
 }
@@ -509,6 +510,9 @@ static int reconstruct_f32(ants_ctx *ctx, const ants_lrf *lrf, int method, const
     if (method == ANTS_MLP_SEEDED)
         return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, sig, n_events, xyz_dev,
                                       E_dev, logL_dev, status_dev, trace_dev, stream);
+    if (method == ANTS_CGS_VARIANT)
+        return reconstruct_variant(ctx, lrf, *(const ants_cgs_variant_params *)params, sig, n_events, xyz_dev, E_dev,
+                                   logL_dev, status_dev, trace_dev, stream);
     return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, sig, n_events, start_xyz_dev, xyz_dev, E_dev,
                             logL_dev, status_dev, trace_dev, stream);
 }
@@ -528,15 +532,18 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
         return fail(ANTS_E_ARG, "ants_reconstruct: the precision form takes no start or trace");
     if (method == ANTS_MLP_SEEDED && start_xyz_dev)
         return fail(ANTS_E_ARG, "ants_reconstruct: the learned form proposes its own start");
+    if (method == ANTS_CGS_VARIANT && start_xyz_dev)
+        return fail(ANTS_E_ARG, "ants_reconstruct: a search variant picks its own start");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     if (signal_dtype == ANTS_F32)
         return reconstruct_f32(ctx, lrf, method, params, (const float *)signals_dev, n_events, start_xyz_dev, xyz_dev,
                                E_dev, logL_dev, status_dev, trace_dev, s);
     // FP16 signals: widen chunk by chunk into scratch slot 7 (no other user)
-    const int iters = method == ANTS_CGS_PLAIN ? ((const ants_cgs_params *)params)->iters
-                      : method == ANTS_MLP_SEEDED ? ((const ants_mlp_seeded_params *)params)->refine.iters
-                                                  : 0;
+    const int iters = method == ANTS_CGS_PLAIN     ? ((const ants_cgs_params *)params)->iters
+                      : method == ANTS_MLP_SEEDED  ? ((const ants_mlp_seeded_params *)params)->refine.iters
+                      : method == ANTS_CGS_VARIANT ? ((const ants_cgs_variant_params *)params)->grid.iters
+                                                   : 0;
     const long chunk = n_events < (1L << 20) ? n_events : (1L << 20);
     float *wide = (float *)ctx_scratch(ctx, 7, (size_t)chunk * n_sensors * sizeof(float));
     if (!wide) return ANTS_E_OOM;
@@ -569,7 +576,7 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     // the plain search overlaps chunks on two streams; the two forms use the
     // context's scratch buffers, so their chunks run one after the other
-    const bool overlap = method == ANTS_CGS_PLAIN;
+    const bool overlap = method == ANTS_CGS_PLAIN || method == ANTS_CGS_VARIANT;  // no shared scratch
     // chunk large enough to fill the GPU, small enough to pipeline
     const long chunk = 1L << 17;
     if (ctx->host_cap_events < (size_t)chunk || ctx->host_cap_sensors < n_sensors) {

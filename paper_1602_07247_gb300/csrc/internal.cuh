@@ -153,6 +153,11 @@ int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_se
                            long n, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
                            cudaStream_t s);
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
+// search variants (variant.cu)
+int check_variant_params(const ants_lrf *lrf, const ants_cgs_variant_params *P);
+int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_variant_params &P, const float *sig,
+                        long n_e, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
+                        cudaStream_t s);
 // event e reads signal row rows[e] when rows is given, else row e / row_div
 int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, int row_div,
                   const int *rows,
