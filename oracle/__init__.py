@@ -37,6 +37,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ants_oracle.c")
 
 RADIAL, XY, XYZ = 1, 2, 3
+COMPOSITE, AXIAL_Z, SLICED = 4, 5, 6   # Sec. 6.1.1, 6.1.2 parameterisation schemes
 EVT_OK, EVT_ZERO_SIGNAL, EVT_BAD_SIGNAL, EVT_OUT_OF_DOMAIN = 0, 2, 3, 4
 TAU_REL = 8.0 * 2.0 ** -24
 
@@ -86,6 +87,9 @@ class _Lrf(C.Structure):
         ("coef", C.POINTER(C.c_double)),
         ("gain", C.POINTER(C.c_double)),
         ("sensor_xy", C.POINTER(C.c_double)),
+        ("n_int_r", C.c_int),
+        ("hi_r", C.c_double),
+        ("n_planes", C.c_int),
     ]
 
 
@@ -151,6 +155,11 @@ class Lrf:
     coef has shape [n_sets, n_coef]; n_sets is 1 for a shared radial LRF
     (Sec. 6.2 "one group"), else n_sensors.  Coefficients are stored x
     fastest, then y, then z.  gain multiplies a radial LRF per sensor.
+    COMPOSITE (Sec. 6.1.1): per sensor the n_int_r + 3 coefficients of the
+    axial part on [0, hi_r], then those of the XY part on the n_int / lo / hi
+    box.  AXIAL_Z (Sec. 6.1.2): one spline of (r, z), axis 0 = r on [0,
+    hi[0]], axis 1 = z.  SLICED (Sec. 6.1.2): per sensor n_planes XY LRFs on
+    the box, planes evenly spaced from lo[2] to hi[2].
     """
 
     type: int
@@ -161,6 +170,9 @@ class Lrf:
     coef: np.ndarray
     shared: bool = False
     gain: np.ndarray | None = None
+    n_int_r: int = 0
+    hi_r: float = 0.0
+    n_planes: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -171,9 +183,10 @@ class Lrf:
         s = _Lrf()
         s.type = self.type
         s.n_sensors = self.n_sensors
-        dims = 1 if self.type == RADIAL else (2 if self.type == XY else 3)
+        dims = {RADIAL: 1, XY: 2, XYZ: 3, COMPOSITE: 2, AXIAL_Z: 2, SLICED: 3}[self.type]
+        s.n_int_r, s.hi_r, s.n_planes = int(self.n_int_r), float(self.hi_r), int(self.n_planes)
         for a in range(3):
-            s.n_int[a] = int(self.n_int[a]) if a < dims else 0
+            s.n_int[a] = int(self.n_int[a]) if a < dims and not (self.type == SLICED and a == 2) else 0
             s.lo[a] = float(self.lo[a]) if a < dims else 0.0
             s.hi[a] = float(self.hi[a]) if a < dims else 0.0
         s.shared = 1 if self.shared else 0
@@ -734,3 +747,60 @@ def lrf_iterate(lrf0: Lrf, params: CgsParams, sig, cycles: int, cuts: EventCuts,
                           mean_E=float(r["E"][idx].mean()) if idx.size else float("nan")))
         L = lrf_refit(L, sig[idx], xyz, r["E"][idx], None, refit_gains, ridge, mutant)
     return L, stats
+
+
+
+# --------------------------------------------------------------------------
+# Sec. 6.1.1 / 6.1.2 parameterisation schemes: fits
+# --------------------------------------------------------------------------
+
+
+def _dist(sensor_xy, pts):
+    d = pts[:, None, :2] - sensor_xy[None, :, :]
+    return np.sqrt(d[..., 0] ** 2 + d[..., 1] ** 2)
+
+
+def lrf_fit_composite(sensor_xy, pts, vals, n_int_r, hi_r, n_int, lo, hi, ridge=0.0, mutant: int = 0) -> Lrf:
+    """Composite LRFs (Sec. 6.1.1): per sensor the axial part is fitted first
+    to (r_i, v_i); the XY part is then fitted to the residual v_i - A_i(r_i)
+    on the n_int / lo / hi box (one value column per sensor; a sample beyond
+    the axial part's reach, r_i > hi_r, gives a zero residual).  pts [n, 2],
+    vals [n, n_s]."""
+    pts, vals = _f64(pts), _f64(vals)
+    r = _dist(_f64(sensor_xy), pts)
+    n_s = vals.shape[1]
+    ca = np.concatenate([lrf_fit((n_int_r,), (0.0,), (hi_r,), r[:, i], vals[:, i], ridge, mutant)[0]
+                         for i in range(n_s)])
+    res = np.stack([vals[:, i] - spline_eval((n_int_r,), (0.0,), (hi_r,), ca[i], r[:, i:i + 1], mutant)
+                    for i in range(n_s)], axis=1)
+    res[~np.isfinite(res)] = 0.0
+    cxy, _, _ = lrf_fit(n_int[:2], lo[:2], hi[:2], pts[:, :2], res, ridge, mutant)
+    coef = np.concatenate([ca, cxy], axis=1)
+    return Lrf(COMPOSITE, _f64(sensor_xy), tuple(n_int[:2]) + (0,), tuple(lo[:2]) + (0.0,), tuple(hi[:2]) + (0.0,),
+               coef, n_int_r=n_int_r, hi_r=hi_r)
+
+
+def lrf_fit_axial_z(sensor_xy, pts, vals, n_int_rz, hi_r, z_lo, z_hi, ridge=0.0, mutant: int = 0) -> Lrf:
+    """Axial+Z LRFs (Sec. 6.1.2): per sensor one spline of (r_i, z) fitted to
+    its values.  pts [n, 3], vals [n, n_s]."""
+    pts, vals = _f64(pts), _f64(vals)
+    r = _dist(_f64(sensor_xy), pts)
+    coef = np.concatenate([lrf_fit(n_int_rz, (0.0, z_lo), (hi_r, z_hi), np.stack([r[:, i], pts[:, 2]], axis=1),
+                                   vals[:, i], ridge, mutant)[0] for i in range(vals.shape[1])])
+    return Lrf(AXIAL_Z, _f64(sensor_xy), tuple(n_int_rz) + (0,), (0.0, z_lo, 0.0), (hi_r, z_hi, 0.0), coef)
+
+
+def lrf_fit_sliced(sensor_xy, pts, vals, n_int, lo, hi, n_planes, z_lo, z_hi, ridge=0.0, mutant: int = 0) -> Lrf:
+    """Sliced LRFs (Sec. 6.1.2): the XY LRFs of plane j (z_j = z_lo + j dz)
+    are fitted to the samples whose nearest plane is j (reading: the paper
+    names the planes, not how their samples are chosen).  pts [n, 3]."""
+    pts, vals = _f64(pts), _f64(vals)
+    dz = (z_hi - z_lo) / (n_planes - 1)
+    plane = np.clip(np.floor((pts[:, 2] - z_lo) / dz + 0.5), 0, n_planes - 1).astype(int)
+    parts = []
+    for j in range(n_planes):
+        sel = plane == j
+        parts.append(lrf_fit(n_int[:2], lo[:2], hi[:2], pts[sel, :2], vals[sel], ridge, mutant)[0])
+    coef = np.concatenate(parts, axis=1)  # [n_s, n_planes * n_coef_xy]
+    return Lrf(SLICED, _f64(sensor_xy), tuple(n_int[:2]) + (0,), tuple(lo[:2]) + (z_lo,), tuple(hi[:2]) + (z_hi,),
+               coef, n_planes=n_planes)

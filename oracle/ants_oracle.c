@@ -57,6 +57,9 @@
 #define OR_RADIAL 1
 #define OR_XY 2
 #define OR_XYZ 3
+#define OR_COMPOSITE 4 /* Sec. 6.1.1: an axial LRF plus an XY LRF */
+#define OR_AXIAL_Z 5   /* Sec. 6.1.2: axial in the XY plane, varying along z */
+#define OR_SLICED 6    /* Sec. 6.1.2: XY LRFs on z planes, linear in z between them */
 
 #define OR_EVT_OK 0
 #define OR_EVT_ZERO_SIGNAL 2
@@ -173,21 +176,51 @@ int or_bspline_basis4(int n_int, double lo, double hi, double x, double B[4])
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    int type;               /* OR_RADIAL, OR_XY, OR_XYZ */
+    int type;               /* OR_RADIAL .. OR_SLICED */
     int n_sensors;
-    int n_int[3];           /* intervals per axis (radial: axis 0 = r) */
-    double lo[3], hi[3];    /* domain per axis */
+    int n_int[3];           /* intervals per axis (radial: axis 0 = r; axial+z: r, z) */
+    double lo[3], hi[3];    /* domain per axis (sliced: z planes span lo[2]..hi[2]) */
     int shared;             /* radial only: one coefficient set for all sensors */
     const double *coef;     /* [n_sets][n_coef], x fastest, then y, then z */
     const double *gain;     /* [n_sensors] relative gain on a radial LRF; NULL = 1 */
     const double *sensor_xy;/* [n_sensors][2] sensor centres (mm) */
+    int n_int_r;            /* composite: intervals of the axial part on [0, hi_r] */
+    double hi_r;
+    int n_planes;           /* sliced: number of z planes (>= 2) */
 } or_lrf;
+
+/* LRF types with a z coordinate, and with an XY box as domain */
+static int or_is_3d(int type) { return type == OR_XYZ || type == OR_AXIAL_Z || type == OR_SLICED; }
+static int or_has_box(int type) { return type == OR_XY || type == OR_XYZ || type == OR_COMPOSITE || type == OR_SLICED; }
 
 static int or_n_coef(const or_lrf *L)
 {
     if (L->type == OR_RADIAL) return L->n_int[0] + 3;
-    if (L->type == OR_XY) return (L->n_int[0] + 3) * (L->n_int[1] + 3);
+    if (L->type == OR_XY || L->type == OR_AXIAL_Z) return (L->n_int[0] + 3) * (L->n_int[1] + 3);
+    if (L->type == OR_COMPOSITE) return (L->n_int_r + 3) + (L->n_int[0] + 3) * (L->n_int[1] + 3);
+    if (L->type == OR_SLICED) return L->n_planes * (L->n_int[0] + 3) * (L->n_int[1] + 3);
     return (L->n_int[0] + 3) * (L->n_int[1] + 3) * (L->n_int[2] + 3);
+}
+
+/* A two-dimensional tensor spline (axis u fastest in c) at (u, v); *ok = 0
+ * outside its box. */
+static double or_spline2(int n0, double lo0, double hi0, int n1, double lo1, double hi1, const double *c, double u,
+                         double v, int *ok)
+{
+    double B0[4], B1[4];
+    int j0 = or_bspline_basis4(n0, lo0, hi0, u, B0);
+    int j1 = or_bspline_basis4(n1, lo1, hi1, v, B1);
+    *ok = j0 >= 0 && j1 >= 0;
+    if (!*ok) return 0.0;
+    double f = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a)
+#if OR_MUTANT == 20
+            f += c[(size_t)(j0 + a) * (n1 + 3) + (size_t)(j1 + b)] * B0[a] * B1[b];
+#else
+            f += c[(size_t)(j1 + b) * (n0 + 3) + (size_t)(j0 + a)] * B0[a] * B1[b];
+#endif
+    return f;
 }
 
 /* eta_i at (x, y, z) from the B-spline expansion.  *ok = 0 when the point
@@ -196,6 +229,48 @@ static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, i
 {
     int nc = or_n_coef(L);
     *ok = 1;
+    if (L->type == OR_COMPOSITE) {
+        /* the axial part at the distance r, plus the XY part */
+        const double *c = L->coef + (size_t)i * nc;
+        double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+        double B[4];
+        int j0 = or_bspline_basis4(L->n_int_r, 0.0, L->hi_r, sqrt(dx * dx + dy * dy), B);
+        int okxy;
+        double fxy = or_spline2(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                                c + L->n_int_r + 3, x, y, &okxy);
+        if (j0 < 0 || !okxy) { *ok = 0; return 0.0; }
+        double fa = 0.0;
+        for (int a = 0; a < 4; ++a) fa += c[j0 + a] * B[a];
+        return fa + fxy;
+    }
+    if (L->type == OR_AXIAL_Z) {
+        /* one spline of (r, z), r the distance in the XY plane */
+        double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+        return or_spline2(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                          L->coef + (size_t)i * nc, sqrt(dx * dx + dy * dy), z, ok);
+    }
+    if (L->type == OR_SLICED) {
+        /* linear interpolation between the XY LRFs of the two closest planes */
+        if (!(z >= L->lo[2] && z <= L->hi[2])) { *ok = 0; return 0.0; }
+        int m = L->n_planes, ncxy = nc / m;
+        double dz = (L->hi[2] - L->lo[2]) / (double)(m - 1), u = (z - L->lo[2]) / dz;
+        int j = (int)floor(u);
+        if (j > m - 2) j = m - 2;
+        if (j < 0) j = 0;
+        double w = u - (double)j;
+        const double *c = L->coef + (size_t)i * nc;
+        int ok0, ok1;
+        double f0 = or_spline2(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                               c + (size_t)j * ncxy, x, y, &ok0);
+        double f1 = or_spline2(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                               c + (size_t)(j + 1) * ncxy, x, y, &ok1);
+        if (!ok0 || !ok1) { *ok = 0; return 0.0; }
+#if OR_MUTANT == 19
+        return w * f0 + (1.0 - w) * f1;
+#else
+        return (1.0 - w) * f0 + w * f1;
+#endif
+    }
     if (L->type == OR_RADIAL) {
         const double *c = L->coef + (size_t)(L->shared ? 0 : i) * nc;
         double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
@@ -428,20 +503,32 @@ void or_cog(long n_e, int n_s, const double *sig, const double *sensor_xy, const
 /* Likelihood (Sec. 5.1.2, energy ratio of Sec. 5.1.2.2)                     */
 /* ------------------------------------------------------------------------ */
 
+/* Whether every LRF of the sensors with act[i] (all when act is NULL) is
+ * defined at a node: within reach of each sensor for the axial parts
+ * (radial, composite, axial+z), inside the XY box, inside the z range. */
+static int or_valid_act(const or_lrf *L, const int *act, double x, double y, double z)
+{
+    if (L->type == OR_RADIAL || L->type == OR_COMPOSITE || L->type == OR_AXIAL_Z) {
+        double rlo = L->type == OR_COMPOSITE ? 0.0 : L->lo[0];
+        double rhi = L->type == OR_COMPOSITE ? L->hi_r : L->hi[0];
+        for (int i = 0; i < L->n_sensors; ++i) {
+            if (act && !act[i]) continue;
+            double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r >= rlo && r <= rhi)) return 0;
+        }
+    }
+    if (or_has_box(L->type) && !(x >= L->lo[0] && x <= L->hi[0] && y >= L->lo[1] && y <= L->hi[1])) return 0;
+    if (L->type == OR_XYZ && !(z >= L->lo[2] && z <= L->hi[2])) return 0;
+    if (L->type == OR_SLICED && !(z >= L->lo[2] && z <= L->hi[2])) return 0;
+    if (L->type == OR_AXIAL_Z && !(z >= L->lo[1] && z <= L->hi[1])) return 0;
+    return 1;
+}
+
 /* Whether a node is inside the LRF's domain. */
 static int or_node_valid(const or_lrf *L, double x, double y, double z)
 {
-    if (L->type == OR_RADIAL) {
-        for (int i = 0; i < L->n_sensors; ++i) {
-            double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
-            double r = sqrt(dx * dx + dy * dy);
-            if (!(r >= L->lo[0] && r <= L->hi[0])) return 0;
-        }
-        return 1;
-    }
-    if (!(x >= L->lo[0] && x <= L->hi[0] && y >= L->lo[1] && y <= L->hi[1])) return 0;
-    if (L->type == OR_XYZ && !(z >= L->lo[2] && z <= L->hi[2])) return 0;
-    return 1;
+    return or_valid_act(L, NULL, x, y, z);
 }
 
 static double or_eta_floored(const or_lrf *L, int i, double x, double y, double z)
@@ -566,8 +653,8 @@ static int or_start(const or_lrf *L, const or_cgs_params *P, const double *gain_
         return OR_EVT_OK;
     }
     or_cog1(L->n_sensors, s, L->sensor_xy, gain_cog, cx, cy);
-    *cz = (L->type == OR_XYZ) ? P->z0 : 0.0;
-    if (L->type != OR_RADIAL) {
+    *cz = or_is_3d(L->type) ? P->z0 : 0.0;
+    if (or_has_box(L->type)) {
         if (*cx < L->lo[0]) *cx = L->lo[0];
         if (*cx > L->hi[0]) *cx = L->hi[0];
         if (*cy < L->lo[1]) *cy = L->lo[1];
@@ -723,16 +810,7 @@ static int or_passive(const or_variant *V, int i) { return V->passive && V->pass
  * defined there (radial: within reach of each; XY / XYZ: inside the box). */
 static int or_variant_valid(const or_lrf *L, const int *act, double x, double y, double z)
 {
-    if (L->type == OR_RADIAL) {
-        for (int i = 0; i < L->n_sensors; ++i) {
-            if (!act[i]) continue;
-            double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
-            double r = sqrt(dx * dx + dy * dy);
-            if (!(r >= L->lo[0] && r <= L->hi[0])) return 0;
-        }
-        return 1;
-    }
-    return or_node_valid(L, x, y, z);
+    return or_valid_act(L, act, x, y, z);
 }
 
 /* Start position, the sensors in the match (act) and their signal sum. */
@@ -778,8 +856,8 @@ static int or_variant_start(const or_lrf *L, const or_cgs_params *P, const or_va
         *cx = nx / den;
         *cy = ny / den;
     }
-    *cz = (L->type == OR_XYZ) ? P->z0 : 0.0;
-    if (L->type != OR_RADIAL) {
+    *cz = or_is_3d(L->type) ? P->z0 : 0.0;
+    if (or_has_box(L->type)) {
         if (*cx < L->lo[0]) *cx = L->lo[0];
         if (*cx > L->hi[0]) *cx = L->hi[0];
         if (*cy < L->lo[1]) *cy = L->lo[1];
@@ -1299,7 +1377,7 @@ void or_simulate(const or_lrf *L, const or_sim_params *P, uint64_t seed, long fi
         }
         double E = P->e0 * (1.0 + P->e_spread * (2.0 * u2 - 1.0));
         double z = P->z_lo + (P->z_hi - P->z_lo) * u3;
-        if (L->type != OR_XYZ) z = 0.0;
+        if (!or_is_3d(L->type)) z = 0.0;
         if (truth) {
             truth[4 * r] = x;
             truth[4 * r + 1] = y;

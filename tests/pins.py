@@ -846,6 +846,107 @@ def pin_least_squares(mutant=0):
         ok += d <= 2.0 * (fine + P4.step_xy * P4.shrink ** (P4.iters - 1))
     assert ok / 60 >= 0.95, ok
 
+# --------------------------------------------------------------------------
+# LRF parameterisation schemes (Sec. 6.1.1, 6.1.2)
+# --------------------------------------------------------------------------
+
+
+def _scheme_lrfs(mutant=0, seed=4):
+    """Small composite, axial+z and sliced LRF sets on a 2 x 2 array with
+    random smooth coefficients (positive, order 1)."""
+    rng = np.random.default_rng(seed)
+    sxy = synth.square_array(2, 10.0)
+    ca = np.stack([0.04 / (1 + (np.linspace(-7.5, 37.5, 10) / 20.0) ** 2) ** 1.5 for _ in range(4)])
+    cxy = rng.uniform(-0.002, 0.002, (4, 9 * 9))
+    comp = oracle.Lrf(oracle.COMPOSITE, sxy, (6, 6, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 0.0),
+                      np.concatenate([ca, cxy], axis=1), n_int_r=7, hi_r=35.0)
+    # axial+z: the closed-form 3D response (its width changes with z, so z is
+    # identifiable) fitted on the (r, z) grid, times a per-sensor factor
+    rz = synth.grid_samples((6, 5), (0.0, 0.0), (30.0, 20.0), 4)
+    c1, _, _ = oracle.lrf_fit((6, 5), (0.0, 0.0), (30.0, 20.0), rz, synth.eta_3d(rz[:, 0], rz[:, 1], r0=15.0),
+                              mutant=mutant)
+    caz = c1 * rng.uniform(0.9, 1.1, (4, 1))
+    az = oracle.Lrf(oracle.AXIAL_Z, sxy, (6, 5, 0), (0.0, 0.0, 0.0), (30.0, 20.0, 0.0), caz)
+    csl = rng.uniform(0.5, 1.5, (4, 3 * 49)) * 0.01
+    sl = oracle.Lrf(oracle.SLICED, sxy, (4, 4, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 20.0), csl, n_planes=3)
+    return sxy, comp, az, sl
+
+
+def pin_lrf_schemes_eval(mutant=0):
+    """Composite = its axial part (as per-sensor radial LRFs) plus its XY
+    part (as XY LRFs); axial+z = the two-dimensional spline of (r, z) evaluated
+    by the plain tensor routine; sliced = the plane's XY LRF on each plane and
+    the linear blend (1 - w) f_j + w f_{j+1} between planes."""
+    sxy, comp, az, sl = _scheme_lrfs(mutant)
+    rng = np.random.default_rng(9)
+    p2 = rng.uniform(-11.0, 11.0, (50, 2))
+    rad = oracle.Lrf(oracle.RADIAL, sxy, (7, 0, 0), (0.0, 0.0, 0.0), (35.0, 0.0, 0.0), comp.coef[:, :10])
+    xy = oracle.Lrf(oracle.XY, sxy, (6, 6, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 0.0), comp.coef[:, 10:])
+    want = oracle.lrf_eval(rad, p2, mutant) + oracle.lrf_eval(xy, p2, mutant)
+    assert np.abs(oracle.lrf_eval(comp, p2, mutant) - want).max() < 1e-15
+    p3 = np.concatenate([p2, rng.uniform(0.0, 20.0, (50, 1))], axis=1)
+    got = oracle.lrf_eval(az, p3, mutant)
+    d = p3[:, None, :2] - sxy[None]
+    r = np.sqrt((d ** 2).sum(-1))
+    for i in range(4):
+        ref = oracle.spline_eval((6, 5), (0.0, 0.0), (30.0, 20.0), az.coef[i], np.stack([r[:, i], p3[:, 2]], 1))
+        assert np.abs(got[:, i] - ref).max() < 1e-14
+    planes = [oracle.Lrf(oracle.XY, sxy, (4, 4, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 0.0),
+                         sl.coef[:, 49 * j:49 * (j + 1)]) for j in range(3)]
+    f = [oracle.lrf_eval(P, p2, mutant) for P in planes]
+    for z, w0, j in ((0.0, 1.0, 0), (10.0, 1.0, 1), (20.0, 1.0, 2), (2.5, 0.75, 0), (17.5, 0.25, 1)):
+        v = oracle.lrf_eval(sl, np.concatenate([p2, np.full((50, 1), z)], 1), mutant)
+        ref = w0 * f[j] + (1.0 - w0) * f[min(j + 1, 2)]
+        assert np.abs(v - ref).max() < 1e-15, (z, np.abs(v - ref).max())
+
+
+def pin_lrf_schemes_fit(mutant=0):
+    """Fits of the schemes recover LRFs that lie in their spline spaces:
+    axial+z from scattered (x, y, z) samples, sliced from samples on the
+    planes; a composite fit of purely axial data reproduces it with a
+    (numerically) zero XY part."""
+    sxy, comp, az, sl = _scheme_lrfs(mutant)
+    rng = np.random.default_rng(10)
+    p3 = np.stack([rng.uniform(-12, 12, 4000), rng.uniform(-12, 12, 4000), rng.uniform(0, 20, 4000)], 1)
+    F = oracle.lrf_fit_axial_z(sxy, p3, oracle.lrf_eval(az, p3, mutant), (6, 5), 30.0, 0.0, 20.0, mutant=mutant)
+    q = np.stack([rng.uniform(-10, 10, 300), rng.uniform(-10, 10, 300), rng.uniform(0, 20, 300)], 1)
+    # distances reach 24 of the profile's 30 mm: the unsampled tail takes the
+    # ridge fallback, which moves the values near 0.05 by ~5e-9
+    assert np.abs(oracle.lrf_eval(F, q, mutant) - oracle.lrf_eval(az, q, mutant)).max() < 5e-8
+    pz = np.concatenate([p3[:, :2], rng.integers(0, 3, (4000, 1)) * 10.0], 1)
+    G = oracle.lrf_fit_sliced(sxy, pz, oracle.lrf_eval(sl, pz, mutant), (4, 4), (-12.0, -12.0), (12.0, 12.0), 3,
+                              0.0, 20.0, mutant=mutant)
+    assert np.abs(oracle.lrf_eval(G, q, mutant) - oracle.lrf_eval(sl, q, mutant)).max() < 1e-9
+    ax = oracle.Lrf(oracle.COMPOSITE, sxy, comp.n_int, comp.lo, comp.hi,
+                    np.concatenate([comp.coef[:, :10], np.zeros((4, 81))], 1), n_int_r=7, hi_r=35.0)
+    p2 = p3[:, :2]
+    H = oracle.lrf_fit_composite(sxy, p2, oracle.lrf_eval(ax, p2, mutant), 7, 35.0, (6, 6), (-12.0, -12.0),
+                                 (12.0, 12.0), mutant=mutant)
+    # values where samples exist; the axial tail beyond r = 24 mm is set by
+    # the ridge fallback, which leaves the XY part at the 1e-8 level
+    q2 = q[:, :2]
+    assert np.abs(oracle.lrf_eval(H, q2, mutant) - oracle.lrf_eval(ax, q2, mutant)).max() < 1e-8
+    assert np.abs(H.coef[:, 10:]).max() < 1e-7
+
+
+def pin_lrf_schemes_search(mutant=0):
+    """Noise-free signals of a source on grid nodes are recovered exactly by
+    the contracting grids with each scheme (Gibbs' inequality), in 2D for
+    composite and in 3D for axial+z and sliced."""
+    sxy, comp, az, sl = _scheme_lrfs(mutant)
+    P2 = oracle.CgsParams(n_xy=7, iters=5, step_xy=1.0)
+    xt = np.array([[2.0, -1.0, 0.0]])
+    s = 3000.0 * oracle.lrf_eval(comp, xt[:, :2], mutant)
+    r = oracle.cgs(comp, P2, s, start_xyz=xt - np.array([[2.0, -1.0, 0.0]]), mutant=mutant)
+    assert np.abs(r["xyz"] - xt).max() < 1e-12, r["xyz"]
+    P3 = oracle.CgsParams(n_xy=7, iters=5, step_xy=1.0, n_z=5, step_z=2.0, z0=10.0)
+    for L in (az, sl):
+        xt = np.array([[1.0, 2.0, 12.0]])
+        s = 3000.0 * oracle.lrf_eval(L, xt, mutant)
+        r = oracle.cgs(L, P3, s, start_xyz=xt - np.array([[1.0, -1.0, 2.0]]), mutant=mutant)
+        assert np.abs(r["xyz"] - xt).max() < 1e-12, (L.type, r["xyz"])
+
+
 ALL_PINS = [
     pin_bspline_golden, pin_partition_of_unity, pin_fit_reproduces_cubics, pin_fit_h4_convergence,
     pin_lrf_matches_closed_form, pin_cog, pin_energy_is_ml, pin_logl_is_poisson, pin_profile_identity,
@@ -854,4 +955,5 @@ ALL_PINS = [
     pin_poisson_sampler, pin_uniform_stream, pin_simulator, pin_logtable_ranks_like_likelihood,
     pin_chi2, pin_event_filter, pin_shift, pin_lrf_refit_exact, pin_iterative_lrf_converges,
     pin_variant_defaults_and_passive, pin_variant_start_and_cuts, pin_least_squares,
+    pin_lrf_schemes_eval, pin_lrf_schemes_fit, pin_lrf_schemes_search,
 ]

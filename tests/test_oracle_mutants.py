@@ -24,6 +24,8 @@ MUTANTS = {
     16: "least-squares terms without the Poisson weight",
     17: "strongest-sensor start picking the weakest sensor",
     18: "distance cut measured from the origin instead of the start",
+    19: "sliced LRF interpolation weights swapped between the planes",
+    20: "two-dimensional spline coefficients indexed with the axes transposed",
 }
 
 
