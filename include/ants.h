@@ -61,7 +61,11 @@ typedef enum {
 typedef enum {
     ANTS_LRF_RADIAL = 1, /* eta_i(x,y) = g_i f(|(x,y) - (X_i,Y_i)|), f a cubic B-spline in r */
     ANTS_LRF_XY = 2,     /* eta_i(x,y) = sum_jk c_ijk B_j(x) B_k(y), one tensor spline per sensor */
-    ANTS_LRF_XYZ = 3     /* eta_i(x,y,z) = sum_jkl c_ijkl B_j(x) B_k(y) B_l(z) */
+    ANTS_LRF_XYZ = 3,    /* eta_i(x,y,z) = sum_jkl c_ijkl B_j(x) B_k(y) B_l(z) */
+    /* ants_lrf_create_scheme / ants_lrf_fit_scheme: */
+    ANTS_LRF_COMPOSITE = 4, /* Sec. 6.1.1: eta_i(x,y) = A_i(r_i) + X_i(x,y), an axial and an XY spline */
+    ANTS_LRF_AXIAL_Z = 5,   /* Sec. 6.1.2: eta_i(x,y,z) = one spline of (r_i, z) */
+    ANTS_LRF_SLICED = 6     /* Sec. 6.1.2: XY splines on z planes, linear in z between the two closest */
 } ants_lrf_type;
 
 /* Per-event status codes written by the reconstruction calls. */
@@ -351,6 +355,41 @@ ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, con
                           const double *lo, const double *hi, int shared, long n_pts,
                           const double *pts_host, const double *vals_host, double ridge,
                           double *ridge_used, ants_lrf **out);
+
+/* LRF sets of the other parameterisation schemes (Sec. 6.1.1, 6.1.2), one
+ * coefficient set per sensor, coef_host [n_sensors][n_coef]:
+ *   ANTS_LRF_COMPOSITE: the axial part, n_int_r + 3 coefficients of a cubic
+ *     B-spline in r on [0, hi_r], followed by the XY part, (n_int[0] + 3) *
+ *     (n_int[1] + 3) coefficients on the box lo[0..1] .. hi[0..1] (x
+ *     fastest).  Defined where r <= hi_r and (x, y) is inside the box.
+ *   ANTS_LRF_AXIAL_Z: one spline of (r, z): axis 0 = r on [0, hi[0]] (lo[0]
+ *     must be 0) with n_int[0] intervals, axis 1 = z on [lo[1], hi[1]]; (n_int[0]
+ *     + 3) * (n_int[1] + 3) coefficients, r fastest.
+ *   ANTS_LRF_SLICED: n_planes (2..64) XY splines on the box lo[0..1] .. hi[0..1]
+ *     with planes z_j = lo[2] + j (hi[2] - lo[2]) / (n_planes - 1); between
+ *     two planes the value is (1 - w) f_j + w f_{j+1}; n_planes * (n_int[0] +
+ *     3) * (n_int[1] + 3) coefficients, plane by plane.
+ * Reconstruction with these sets evaluates every node on its own (the
+ * per-node kernel of ANTS_CGS_VARIANT); the precision and learned forms, the
+ * batched run, the iterative refit and save / load take the first three
+ * types only.  Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_create_scheme(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                                    const double *lo, const double *hi, int n_int_r, double hi_r, int n_planes,
+                                    const double *coef_host, ants_lrf **out);
+
+/* Fit an LRF set of one of those schemes by FP64 least squares on the device
+ * (Sec. 6.1.1, 6.1.2).  pts_host [n_pts][d] (COMPOSITE: x, y; AXIAL_Z and
+ * SLICED: x, y, z), vals_host [n_pts][n_sensors].  COMPOSITE: per sensor the
+ * axial part is fitted first to (r_i, v_i), then the XY part to the residual
+ * v_i - A_i(r_i) (a sample beyond the axial part's reach gives a zero
+ * residual).  AXIAL_Z: per sensor one fit of (r_i, z).  SLICED: the XY
+ * splines of plane j are fitted to the samples whose nearest plane is j.
+ * Each fit retries with the ridge of ants_lrf_fit when singular.
+ * Synchronous.  Errors: as ants_lrf_fit. */
+ANTS_API int ants_lrf_fit_scheme(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                                 const double *lo, const double *hi, int n_int_r, double hi_r, int n_planes,
+                                 long n_pts, const double *pts_host, const double *vals_host, double ridge,
+                                 ants_lrf **out);
 
 /* Copy the FP64 coefficients ([n_sets][n_coef]) to coef_host; `count` is
  * the capacity in doubles and must be >= n_sets*n_coef.  *n_sets_out and

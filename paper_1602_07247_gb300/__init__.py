@@ -24,6 +24,7 @@ LIB_PATH = _build.LIB
 # enums of include/ants.h
 ANTS_OK = 0
 ANTS_LRF_RADIAL, ANTS_LRF_XY, ANTS_LRF_XYZ = 1, 2, 3
+ANTS_LRF_COMPOSITE, ANTS_LRF_AXIAL_Z, ANTS_LRF_SLICED = 4, 5, 6
 ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
 ANTS_EVT_BAD_SIGNAL, ANTS_EVT_OUT_OF_DOMAIN, ANTS_EVT_LOW_LOGL = 3, 4, 5
 ANTS_CGS_PLAIN = 0
@@ -216,6 +217,10 @@ def lib() -> C.CDLL:
         L.ants_mlp_save.argtypes = [_VP, C.c_char_p]
         L.ants_mlp_load.argtypes = [_VP, C.c_char_p, C.POINTER(_VP)]
         L.ants_lrf_gains.argtypes = [_VP, _DP, C.c_size_t]
+        L.ants_lrf_create_scheme.argtypes = [_VP, _VP, C.c_int, _IP, _DP, _DP, C.c_int, C.c_double, C.c_int, _DP,
+                                             C.POINTER(_VP)]
+        L.ants_lrf_fit_scheme.argtypes = [_VP, _VP, C.c_int, _IP, _DP, _DP, C.c_int, C.c_double, C.c_int, C.c_long,
+                                          _DP, _DP, C.c_double, C.POINTER(_VP)]
         L.ants_event_centroid.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP]
         L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
         L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
@@ -343,6 +348,36 @@ def ants_lrf_coefficients(lrf: int) -> np.ndarray:
     out = np.empty((ns.value, nc.value))
     _check(lib().ants_lrf_coefficients(lrf, _dptr(out), out.size, None, None))
     return out
+
+
+def _grid3(n_int, lo, hi):
+    ni = np.zeros(3, dtype=np.int32)
+    l3, h3 = np.zeros(3), np.zeros(3)
+    ni[:len(n_int)] = n_int
+    l3[:len(lo)] = lo
+    h3[:len(hi)] = hi
+    return ni, l3, h3
+
+
+def ants_lrf_create_scheme(ctx: int, det: int, type: int, n_int, lo, hi, coef, n_int_r: int = 0, hi_r: float = 0.0,
+                           n_planes: int = 0) -> int:
+    ni, l3, h3 = _grid3(n_int, lo, hi)
+    c = _f64(coef).ravel()
+    h = _VP()
+    _check(lib().ants_lrf_create_scheme(ctx, det, type, ni.ctypes.data_as(_IP), _dptr(l3), _dptr(h3), int(n_int_r),
+                                        float(hi_r), int(n_planes), _dptr(c), C.byref(h)))
+    return h.value
+
+
+def ants_lrf_fit_scheme(ctx: int, det: int, type: int, n_int, lo, hi, pts, vals, n_int_r: int = 0,
+                        hi_r: float = 0.0, n_planes: int = 0, ridge: float = 0.0) -> int:
+    ni, l3, h3 = _grid3(n_int, lo, hi)
+    p, v = _f64(pts), _f64(vals)
+    h = _VP()
+    _check(lib().ants_lrf_fit_scheme(ctx, det, type, ni.ctypes.data_as(_IP), _dptr(l3), _dptr(h3), int(n_int_r),
+                                     float(hi_r), int(n_planes), int(p.shape[0]), _dptr(p), _dptr(v), float(ridge),
+                                     C.byref(h)))
+    return h.value
 
 
 def ants_lrf_gains(lrf: int, n_sensors: int) -> np.ndarray:
@@ -667,6 +702,18 @@ class Lrf:
         L.ridge_used = lam
         L.shared = bool(shared)
         return L
+
+    @classmethod
+    def from_scheme(cls, ctx, det, type, n_int, lo, hi, coef, n_int_r=0, hi_r=0.0, n_planes=0):
+        """A composite, axial+z or sliced set from coefficients (ants_lrf_create_scheme)."""
+        return cls(ctx, det, ants_lrf_create_scheme(ctx.handle, det.handle, type, n_int, lo, hi, coef, n_int_r, hi_r,
+                                                    n_planes), type)
+
+    @classmethod
+    def fit_scheme(cls, ctx, det, type, n_int, lo, hi, pts, vals, n_int_r=0, hi_r=0.0, n_planes=0, ridge=0.0):
+        """A composite, axial+z or sliced set fitted on the device (ants_lrf_fit_scheme)."""
+        return cls(ctx, det, ants_lrf_fit_scheme(ctx.handle, det.handle, type, n_int, lo, hi, pts, vals, n_int_r, hi_r,
+                                                 n_planes, ridge), type)
 
     @classmethod
     def load(cls, ctx, det, path):

@@ -41,7 +41,12 @@ void begin_call()
 
 void count_launch(long n) { t_launches += n; }
 
-int lrf_dims(int type) { return type == ANTS_LRF_RADIAL ? 1 : (type == ANTS_LRF_XY ? 2 : 3); }
+int lrf_dims(int type)
+{
+    // spline axes: radial r; XY and composite (its box) x, y; axial+z r, z;
+    // sliced x, y (+ the plane range); XYZ x, y, z
+    return type == ANTS_LRF_RADIAL ? 1 : (type == ANTS_LRF_XYZ ? 3 : 2);
+}
 
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
 {
@@ -246,10 +251,11 @@ static int upload_lrf(ants_lrf *L)
         D.pair_stride = ps;
     }
     D.rpoly = nullptr;
-    if (L->type == ANTS_LRF_RADIAL) {
+    if (L->type == ANTS_LRF_RADIAL || L->type == ANTS_LRF_COMPOSITE) {
         // uniform cubic B-spline on interval j: sum_a c[j+a] B_a(t) expanded in
-        // powers of t (FP64, then rounded once to FP32)
-        const int ni = L->n_int[0];
+        // powers of t (FP64, then rounded once to FP32); a composite set's
+        // axial part leads its coefficients
+        const int ni = L->type == ANTS_LRF_COMPOSITE ? L->n_int_r : L->n_int[0];
         std::vector<float4> rp((size_t)L->n_sets * ni);
         for (int set = 0; set < L->n_sets; ++set)
             for (int j = 0; j < ni; ++j) {
@@ -277,6 +283,12 @@ static int upload_lrf(ants_lrf *L)
     }
     D.stride_y = L->n_int[0] + 3;
     D.stride_z = (L->n_int[0] + 3) * (L->type == ANTS_LRF_RADIAL ? 1 : L->n_int[1] + 3);
+    D.n_int_r = L->n_int_r;
+    D.hi_r = (float)L->hi_r;
+    D.inv_h_r = L->n_int_r > 0 ? (float)((double)L->n_int_r / L->hi_r) : 0.0f;
+    D.n_planes = L->n_planes;
+    D.n_coef_xy = (L->n_int[0] + 3) * (L->n_int[1] + 3);
+    if (L->type == ANTS_LRF_SLICED) D.inv_h[2] = (float)((double)(L->n_planes - 1) / (L->hi[2] - L->lo[2]));
     D.positive = positive;
     D.coef = L->d_coef;
     D.sxy = L->d_sxy;
@@ -299,22 +311,29 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     (void)cudaGetLastError();
 }
 
-ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
-                             const double *lo, const double *hi, int shared,
-                             const double *coef_host, const double *gain_host, ants_lrf **out)
+}  // extern "C"
+
+namespace ants {
+
+int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
+                    const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
+                    double hi_r, int n_planes, ants_lrf **out)
 {
-    begin_call();
-    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create: out is NULL");
     *out = nullptr;
     if (!ctx || !det || !n_int || !lo || !hi || !coef_host)
         return fail(ANTS_E_ARG, "ants_lrf_create: NULL argument");
-    if (type != ANTS_LRF_RADIAL && type != ANTS_LRF_XY && type != ANTS_LRF_XYZ)
+    if (type < ANTS_LRF_RADIAL || type > ANTS_LRF_SLICED)
         return fail(ANTS_E_ARG, "ants_lrf_create: unknown LRF type %d", type);
     if (shared && type != ANTS_LRF_RADIAL)
         return fail(ANTS_E_ARG, "ants_lrf_create: shared coefficients need a RADIAL LRF");
     if (gain_host && type != ANTS_LRF_RADIAL)
         return fail(ANTS_E_ARG, "ants_lrf_create: gains apply to RADIAL LRFs only");
     int dims = lrf_dims(type);
+    if (type == ANTS_LRF_COMPOSITE && (n_int_r < 1 || n_int_r > 256 || !(hi_r > 0.0) || !std::isfinite(hi_r)))
+        return fail(ANTS_E_ARG, "ants_lrf_create: a composite LRF needs 1 <= n_int_r <= 256 and hi_r > 0");
+    if (type == ANTS_LRF_SLICED &&
+        (n_planes < 2 || n_planes > 64 || !(lo[2] < hi[2]) || !std::isfinite(lo[2]) || !std::isfinite(hi[2])))
+        return fail(ANTS_E_ARG, "ants_lrf_create: a sliced LRF needs 2..64 planes and a z range lo[2] < hi[2]");
     ants_lrf *L = new (std::nothrow) ants_lrf();
     if (!L) return fail(ANTS_E_OOM, "ants_lrf_create: out of host memory");
     L->ctx = ctx;
@@ -334,9 +353,20 @@ ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, 
         L->hi[a] = hi[a];
         L->n_coef *= n_int[a] + 3;
     }
-    if (type == ANTS_LRF_RADIAL && lo[0] != 0.0) {
+    if ((type == ANTS_LRF_RADIAL || type == ANTS_LRF_AXIAL_Z) && lo[0] != 0.0) {
         delete L;
-        return fail(ANTS_E_ARG, "ants_lrf_create: a RADIAL LRF starts at r = 0");
+        return fail(ANTS_E_ARG, "ants_lrf_create: an axial LRF starts at r = 0");
+    }
+    if (type == ANTS_LRF_COMPOSITE) {
+        L->n_int_r = n_int_r;
+        L->hi_r = hi_r;
+        L->n_coef += n_int_r + 3;
+    }
+    if (type == ANTS_LRF_SLICED) {
+        L->n_planes = n_planes;
+        L->lo[2] = lo[2];
+        L->hi[2] = hi[2];
+        L->n_coef *= n_planes;
     }
     L->n_sets = L->shared ? 1 : L->n_s;
     size_t nc = (size_t)L->n_sets * L->n_coef;
@@ -359,6 +389,34 @@ ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, 
     }
     *out = L;
     return ANTS_OK;
+}
+
+}  // namespace ants
+
+extern "C" {
+
+ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                             const double *lo, const double *hi, int shared,
+                             const double *coef_host, const double *gain_host, ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create: out is NULL");
+    *out = nullptr;
+    if (type != ANTS_LRF_RADIAL && type != ANTS_LRF_XY && type != ANTS_LRF_XYZ)
+        return fail(ANTS_E_ARG, "ants_lrf_create: type %d (the other schemes: ants_lrf_create_scheme)", type);
+    return lrf_create_impl(ctx, det, type, n_int, lo, hi, shared, coef_host, gain_host, 0, 0.0, 0, out);
+}
+
+ANTS_API int ants_lrf_create_scheme(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
+                                    const double *lo, const double *hi, int n_int_r, double hi_r, int n_planes,
+                                    const double *coef_host, ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create_scheme: out is NULL");
+    *out = nullptr;
+    if (type != ANTS_LRF_COMPOSITE && type != ANTS_LRF_AXIAL_Z && type != ANTS_LRF_SLICED)
+        return fail(ANTS_E_ARG, "ants_lrf_create_scheme: type %d is not a composite, axial+z or sliced LRF", type);
+    return lrf_create_impl(ctx, det, type, n_int, lo, hi, 0, coef_host, nullptr, n_int_r, hi_r, n_planes, out);
 }
 
 ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_t count,
@@ -405,7 +463,7 @@ ANTS_API int ants_lrf_eval(const ants_lrf *lrf, const float *pts_dev, long n_pts
     begin_call();
     if (!lrf) return fail(ANTS_E_ARG, "ants_lrf_eval: lrf is NULL");
     if (n_pts < 0) return fail(ANTS_E_ARG, "ants_lrf_eval: n_pts < 0");
-    int need = lrf->type == ANTS_LRF_XYZ ? 3 : 2;
+    int need = lrf_is_3d(lrf->type) ? 3 : 2;
     if (dim != need) return fail(ANTS_E_SHAPE, "ants_lrf_eval: dim %d, LRF needs %d", dim, need);
     if (n_pts == 0) return ANTS_OK;
     if (!pts_dev || !out_dev) return fail(ANTS_E_ARG, "ants_lrf_eval: NULL buffer");
@@ -429,6 +487,7 @@ ANTS_API int ants_lrf_save(const ants_lrf *lrf, const char *path)
 {
     begin_call();
     if (!lrf || !path) return fail(ANTS_E_ARG, "ants_lrf_save: NULL argument");
+    if (lrf->type > ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "ants_lrf_save: RADIAL, XY and XYZ sets only");
     FILE *f = fopen(path, "wb");
     if (!f) return fail(ANTS_E_IO, "ants_lrf_save: cannot open %s", path);
     int32_t hdr[8] = {1, lrf->type, lrf->n_s, lrf->shared, lrf->n_int[0], lrf->n_int[1], lrf->n_int[2],
@@ -511,8 +570,8 @@ static int reconstruct_f32(ants_ctx *ctx, const ants_lrf *lrf, int method, const
         return reconstruct_mlp_seeded(ctx, lrf, *(const ants_mlp_seeded_params *)params, sig, n_events, xyz_dev,
                                       E_dev, logL_dev, status_dev, trace_dev, stream);
     if (method == ANTS_CGS_VARIANT)
-        return reconstruct_variant(ctx, lrf, *(const ants_cgs_variant_params *)params, sig, n_events, xyz_dev, E_dev,
-                                   logL_dev, status_dev, trace_dev, stream);
+        return reconstruct_variant(ctx, lrf, *(const ants_cgs_variant_params *)params, sig, n_events, nullptr,
+                                   xyz_dev, E_dev, logL_dev, status_dev, trace_dev, stream);
     return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, sig, n_events, start_xyz_dev, xyz_dev, E_dev,
                             logL_dev, status_dev, trace_dev, stream);
 }

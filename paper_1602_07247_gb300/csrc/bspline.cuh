@@ -46,8 +46,32 @@ __device__ __forceinline__ int bs_span(float x, float lo, float inv_h, int n, fl
 __device__ __forceinline__ bool in_box(const LrfDev &L, float x, float y, float z)
 {
     bool ok = x >= L.lo[0] && x <= L.hi[0] && y >= L.lo[1] && y <= L.hi[1];
-    if (L.type == ANTS_LRF_XYZ) ok = ok && z >= L.lo[2] && z <= L.hi[2];
+    if (L.type == ANTS_LRF_XYZ || L.type == ANTS_LRF_SLICED) ok = ok && z >= L.lo[2] && z <= L.hi[2];
     return ok;
+}
+
+// a tensor spline of two axes (axis 0 fastest in c, row stride n0 + 3) at
+// (u, v), both inside their ranges
+__device__ __forceinline__ float spline2(const float *c, float u, float lo0, float inv_h0, int n0, float v, float lo1,
+                                         float inv_h1, int n1)
+{
+    float tu, tv, wu[4], wv[4];
+    const int ju = bs_span(u, lo0, inv_h0, n0, tu);
+    const int jv = bs_span(v, lo1, inv_h1, n1, tv);
+    bs_weights(tu, wu);
+    bs_weights(tv, wv);
+    const int st = n0 + 3;
+    float f = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float *row = c + (jv + b) * st + ju;
+        float fr = row[0] * wu[0];
+        fr = fmaf(row[1], wu[1], fr);
+        fr = fmaf(row[2], wu[2], fr);
+        fr = fmaf(row[3], wu[3], fr);
+        f = fmaf(fr, wv[b], f);
+    }
+    return f;
 }
 
 // distance in the sensor plane as r^2 times the reciprocal square root of
@@ -92,6 +116,36 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
         ok = r <= L.hi[0];
         return ok ? radial_eta(L, i, r) : 0.0f;
     }
+    if (L.type == ANTS_LRF_COMPOSITE) {
+        // the axial part at r plus the XY part
+        const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
+        ok = r <= L.hi_r && in_box(L, x, y, z);
+        if (!ok) return 0.0f;
+        const float *c = L.coef + (size_t)i * L.n_coef + (L.n_int_r + 3);
+        return radial_profile(L.rpoly + i * L.n_int_r, L.inv_h_r, L.n_int_r, r) +
+               spline2(c, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1]);
+    }
+    if (L.type == ANTS_LRF_AXIAL_Z) {
+        // one spline of (r, z)
+        const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
+        ok = r <= L.hi[0] && z >= L.lo[1] && z <= L.hi[1];
+        if (!ok) return 0.0f;
+        return spline2(L.coef + (size_t)i * L.n_coef, r, 0.0f, L.inv_h[0], L.n_int[0], z, L.lo[1], L.inv_h[1],
+                       L.n_int[1]);
+    }
+    if (L.type == ANTS_LRF_SLICED) {
+        // the XY splines of the two closest planes, blended linearly in z
+        ok = in_box(L, x, y, z);
+        if (!ok) return 0.0f;
+        const float u = (z - L.lo[2]) * L.inv_h[2];
+        const int j = min(max((int)floorf(u), 0), L.n_planes - 2);
+        const float w = u - (float)j;
+        const float *c = L.coef + (size_t)i * L.n_coef + (size_t)j * L.n_coef_xy;
+        const float f0 = spline2(c, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1]);
+        const float f1 =
+            spline2(c + L.n_coef_xy, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1]);
+        return fmaf(w, f1, (1.0f - w) * f0);
+    }
     ok = in_box(L, x, y, z);
     if (!ok) return 0.0f;
     float tx, ty, tz = 0.0f, wx[4], wy[4], wz[4] = {1.0f, 0.0f, 0.0f, 0.0f};
@@ -120,6 +174,21 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
         f = fmaf(fz, wz[cz], f);
     }
     return f;
+}
+
+// every LRF of the sensors with s_act[i] != 0 (all sensors when s_act is
+// NULL) defined at the point: within reach of each sensor for the axial
+// parts, inside the XY box, inside the z range
+__device__ __forceinline__ bool lrf_defined(const LrfDev &L, const float *s_act, float x, float y, float z)
+{
+    if (L.type == ANTS_LRF_RADIAL || L.type == ANTS_LRF_COMPOSITE || L.type == ANTS_LRF_AXIAL_Z) {
+        const float rhi = L.type == ANTS_LRF_COMPOSITE ? L.hi_r : L.hi[0];
+        for (int i = 0; i < L.n_s; ++i)
+            if ((!s_act || s_act[i] != 0.0f) && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) > rhi) return false;
+    }
+    if (L.type == ANTS_LRF_AXIAL_Z) return z >= L.lo[1] && z <= L.hi[1];
+    if (L.type == ANTS_LRF_RADIAL) return true;
+    return in_box(L, x, y, z);
 }
 
 }  // namespace ants

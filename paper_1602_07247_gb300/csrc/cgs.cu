@@ -636,12 +636,12 @@ int check_cgs_params(const ants_lrf *lrf, const ants_cgs_params *p)
         return fail(ANTS_E_ARG, "cgs params: n_xy %d must be odd in [3, 15]", p->n_xy);
     if (p->n_z < 1 || p->n_z > 15 || !(p->n_z & 1))
         return fail(ANTS_E_ARG, "cgs params: n_z %d must be odd in [1, 15]", p->n_z);
-    if (p->n_z > 1 && lrf->type != ANTS_LRF_XYZ)
-        return fail(ANTS_E_ARG, "cgs params: n_z > 1 needs an XYZ LRF");
+    if (p->n_z > 1 && !lrf_is_3d(lrf->type))
+        return fail(ANTS_E_ARG, "cgs params: n_z > 1 needs an LRF with a z coordinate");
     if (p->iters < 1 || p->iters > 32) return fail(ANTS_E_ARG, "cgs params: iters %d not in [1, 32]", p->iters);
     if (!(p->shrink > 0.0f && p->shrink < 1.0f)) return fail(ANTS_E_ARG, "cgs params: shrink must be in (0, 1)");
     if (!(p->step_xy > 0.0f) || !isfinite(p->step_xy)) return fail(ANTS_E_ARG, "cgs params: step_xy must be > 0");
-    if (lrf->type == ANTS_LRF_XYZ && p->n_z > 1 && !(p->step_z > 0.0f))
+    if (lrf_is_3d(lrf->type) && p->n_z > 1 && !(p->step_z > 0.0f))
         return fail(ANTS_E_ARG, "cgs params: step_z must be > 0");
     return ANTS_OK;
 }
@@ -659,6 +659,14 @@ int launch_cgs_rows(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_par
 {
     if (cgs_xy_supported(lrf, p))
         return launch_cgs_xy(ctx, lrf, p, sig, row_div, nullptr, n_e, start, xyz, E, logL, status, trace, stream);
+    if (lrf->type > ANTS_LRF_XYZ) {
+        // composite, axial+z and sliced sets: the per-node kernel of the
+        // variants with no option set is this search
+        if (row_div != 1) return fail(ANTS_E_UNIMPLEMENTED, "cgs: shared signal rows need an XY LRF");
+        ants_cgs_variant_params v{};
+        v.grid = p;
+        return reconstruct_variant(ctx, lrf, v, sig, n_e, start, xyz, E, logL, status, trace, stream);
+    }
     CgsArgs a;
     a.row_div = row_div;
     a.L = lrf->dev;
@@ -883,6 +891,8 @@ ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch
     for (int k = 0; k < n_items; ++k) {
         const ants_batch_item &it = items[k];
         if (!it.lrf || it.lrf->ctx != ctx) return fail(ANTS_E_ARG, "batch item %d: LRF of another context", k);
+        if (it.lrf->type > ANTS_LRF_XYZ)
+            return fail(ANTS_E_UNIMPLEMENTED, "batch item %d: RADIAL, XY and XYZ LRFs only", k);
         if (it.n_events < 0) return fail(ANTS_E_ARG, "batch item %d: n_events < 0", k);
         if (it.n_events > 0 && (!it.signals_dev || !it.xyz_dev || !it.E_dev || !it.logL_dev || !it.status_dev))
             return fail(ANTS_E_ARG, "batch item %d: NULL buffer", k);

@@ -53,6 +53,13 @@ struct LrfDev {
     const float4 *rpoly;
     int n_pairs;
     int pair_stride;   // (n_int[1]+3) * (n_int[0]+3)
+    // COMPOSITE: the axial part's intervals on [0, hi_r] (its cubics in
+    // rpoly, [n_s][n_int_r]); the XY part follows n_int_r + 3 coefficients
+    // of each sensor's set in coef.  SLICED: planes over lo[2]..hi[2],
+    // inv_h[2] = (n_planes - 1) / (hi[2] - lo[2]).
+    int n_int_r;
+    float hi_r, inv_h_r;
+    int n_planes, n_coef_xy;
 };
 
 }  // namespace ants
@@ -94,6 +101,9 @@ struct ants_lrf {
     std::vector<double> gain;      // [n_s] (RADIAL factor; 1 otherwise)
     std::vector<double> sxy;       // [n_s][2]
     std::vector<double> rel_gain;  // [n_s] detector relative gains
+    int n_int_r = 0;               // COMPOSITE axial part
+    double hi_r = 0.0;
+    int n_planes = 0;              // SLICED
     float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
     float2 *d_coef2 = nullptr;
     float4 *d_rpoly = nullptr;
@@ -102,6 +112,19 @@ struct ants_lrf {
 
 namespace ants {
 int lrf_dims(int type);
+// the LRF types with a z coordinate / with an XY box as (part of) their domain
+__host__ __device__ inline bool lrf_is_3d(int type)
+{
+    return type == ANTS_LRF_XYZ || type == ANTS_LRF_AXIAL_Z || type == ANTS_LRF_SLICED;
+}
+__host__ __device__ inline bool lrf_has_box(int type)
+{
+    return type == ANTS_LRF_XY || type == ANTS_LRF_XYZ || type == ANTS_LRF_COMPOSITE || type == ANTS_LRF_SLICED;
+}
+// any LRF type: create from coefficients (api.cu)
+int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
+                    const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
+                    double hi_r, int n_planes, ants_lrf **out);
 // launches of the reconstruction kernels (cgs.cu)
 int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p,
                      const float *sig, long n_e, const float *start, float *xyz, float *E,
@@ -155,9 +178,10 @@ int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_se
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
 // search variants (variant.cu)
 int check_variant_params(const ants_lrf *lrf, const ants_cgs_variant_params *P);
+// start (nullable): given starts [n_e][3] instead of the variant's own
 int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_variant_params &P, const float *sig,
-                        long n_e, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
-                        cudaStream_t s);
+                        long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                        int16_t *trace, cudaStream_t s);
 // event e reads signal row rows[e] when rows is given, else row e / row_div
 int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p, const float *sig, int row_div,
                   const int *rows,

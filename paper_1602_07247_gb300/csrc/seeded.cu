@@ -139,7 +139,8 @@ int check_seeded_params(const ants_lrf *lrf, const ants_mlp_seeded_params *P)
     if (mlp_n_in(P->mlp) != lrf->n_s)
         return fail(ANTS_E_SHAPE, "learned form: network takes %d inputs, the LRF has %d sensors",
                     mlp_n_in(P->mlp), lrf->n_s);
-    if (lrf->type == ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "learned form: XYZ LRFs");
+    if (lrf->type != ANTS_LRF_XY && lrf->type != ANTS_LRF_RADIAL)
+        return fail(ANTS_E_UNIMPLEMENTED, "learned form: RADIAL and XY LRFs only");
     int rc = check_cgs_params(lrf, &P->refine);
     if (rc != ANTS_OK) return rc;
     return check_cgs_params(lrf, &P->fallback);

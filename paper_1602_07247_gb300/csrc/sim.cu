@@ -99,7 +99,7 @@ __global__ void simulate_kernel(SimArgs a)
             y = a.p.cy + a.p.extent * (2.0f * u1 - 1.0f);
         }
         const float E = a.p.e0 * (1.0f + a.p.e_spread * (2.0f * u2 - 1.0f));
-        const float z = a.L.type == ANTS_LRF_XYZ ? a.p.z_lo + (a.p.z_hi - a.p.z_lo) * u3 : 0.0f;
+        const float z = lrf_is_3d(a.L.type) ? a.p.z_lo + (a.p.z_hi - a.p.z_lo) * u3 : 0.0f;
         if (i == 0 && a.truth) {
             a.truth[4 * r] = x;
             a.truth[4 * r + 1] = y;

@@ -37,11 +37,13 @@ struct VarArgs {
     float min_signal, max_distance;
     const float *sig;
     long n_e;
+    const float *start_xyz;  // given starts [n_e][3] (nullable)
     float *xyz, *E, *logL;
     int32_t *status;
     int16_t *trace;
     double gain[kMaxVariantSensors];             // relative gains (start)
     unsigned char passive[kMaxVariantSensors];   // 1 = passive
+    __device__ bool start_xyz_given() const { return start_xyz != nullptr; }
 };
 
 __device__ __forceinline__ float vwarp_sum(float v)
@@ -77,12 +79,7 @@ __device__ __forceinline__ float eta_at(const LrfDev &L, int i, float x, float y
 template <int TYPE>
 __device__ __forceinline__ bool node_ok(const LrfDev &L, const float *s_act, float x, float y, float z)
 {
-    if (TYPE == ANTS_LRF_RADIAL) {
-        for (int i = 0; i < L.n_s; ++i)
-            if (s_act[i] != 0.0f && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) > L.hi[0]) return false;
-        return true;
-    }
-    return in_box(L, x, y, z);
+    return lrf_defined(L, s_act, x, y, z);
 }
 
 __device__ __forceinline__ void set_failed(const VarArgs &a, long e, int st, int lane)
@@ -141,8 +138,12 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
             set_failed(a, e, ANTS_EVT_ZERO_SIGNAL, lane);
             continue;
         }
-        float cx, cy, cz = TYPE == ANTS_LRF_XYZ ? a.z0 : 0.0f;
-        if (a.start == 1) {
+        float cx, cy, cz = lrf_is_3d(TYPE) ? a.z0 : 0.0f;
+        if (a.start_xyz_given()) {
+            cx = a.start_xyz[3 * e];
+            cy = a.start_xyz[3 * e + 1];
+            cz = a.start_xyz[3 * e + 2];
+        } else if (a.start == 1) {
             for (int o = 16; o; o >>= 1) {  // the largest s/g, ties to the lowest index
                 const double v2 = __shfl_xor_sync(kFull, bv, o);
                 const int i2 = __shfl_xor_sync(kFull, bi, o);
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
             cx = (float)(X / W);
             cy = (float)(Y / W);
         }
-        if (TYPE != ANTS_LRF_RADIAL) {
+        if (lrf_has_box(TYPE) && !a.start_xyz_given()) {
             cx = fminf(fmaxf(cx, L.lo[0]), L.hi[0]);
             cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
         }
@@ -300,8 +301,8 @@ int check_variant_params(const ants_lrf *lrf, const ants_cgs_variant_params *P)
 }
 
 int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_variant_params &P, const float *sig,
-                        long n_e, float *xyz, float *E, float *logL, int32_t *status, int16_t *trace,
-                        cudaStream_t s)
+                        long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                        int16_t *trace, cudaStream_t s)
 {
     VarArgs a;
     a.L = lrf->dev;
@@ -318,6 +319,7 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     a.max_distance = P.max_distance;
     a.sig = sig;
     a.n_e = n_e;
+    a.start_xyz = start;
     a.xyz = xyz;
     a.E = E;
     a.logL = logL;
@@ -338,7 +340,12 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     switch (lrf->type) {
     case ANTS_LRF_RADIAL: cgs_variant_kernel<ANTS_LRF_RADIAL><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
     case ANTS_LRF_XY: cgs_variant_kernel<ANTS_LRF_XY><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    default: cgs_variant_kernel<ANTS_LRF_XYZ><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_XYZ: cgs_variant_kernel<ANTS_LRF_XYZ><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_COMPOSITE:
+        cgs_variant_kernel<ANTS_LRF_COMPOSITE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        break;
+    case ANTS_LRF_AXIAL_Z: cgs_variant_kernel<ANTS_LRF_AXIAL_Z><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    default: cgs_variant_kernel<ANTS_LRF_SLICED><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "cgs_variant_kernel launch");
