@@ -33,7 +33,7 @@ MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
 FMA_PER_CLK_SM = 128  # FP32 fused multiply-adds per clock per SM
 # canonical FP32 multiply-adds per (node, sensor) evaluation of each search:
 # B-spline tensor product, likelihood term and energy sum
-F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9}
+F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9, "composite": 41, "axial_z": 25, "sliced": 46}
 
 
 def alu_roofline(evals_per_s: float, kind: str) -> dict:
@@ -395,6 +395,60 @@ def variants_run(args, ants, torch, ctx, stream):
                         "strongest sensor, sensor 27 passive", **out}
 
 
+def schemes_run(args, ants, torch, ctx, stream):
+    """The other LRF schemes (Sec. 6.1.1, 6.1.2) on a 4 x 4 SiPM array (pitch
+    6 mm), LRFs fitted on the GPU to the closed-form truth (composite: the
+    axial truth with a 5 % smooth XY term; axial+z and sliced: the 3D truth
+    over z in [0, 20] mm, 5 planes), 10^6 events simulated on the GPU from
+    each, reconstructed by the per-node kernel (composite 9x9 x 7 grids,
+    3D 7x7x5 x 5 grids)."""
+    import synth
+    sxy = synth.square_array(4, 6.0)
+    g = synth.sensor_gains(16, 0.05, 3)
+    det = ants.Detector(sxy)
+    rng = np.random.default_rng(2)
+    p2 = rng.uniform(-12.0, 12.0, (40000, 2))
+    v2 = synth.truth_eta(sxy, g, p2) * (1.0 + 0.05 * np.cos(p2[:, :1] / 7.0) * np.sin(p2[:, 1:] / 5.0))
+    p3 = np.concatenate([p2, rng.uniform(0.0, 20.0, (40000, 1))], 1)
+    p3s = np.concatenate([p2, rng.integers(0, 5, (40000, 1)) * 5.0], 1)
+    lrfs = {
+        "composite": ants.Lrf.fit_scheme(ctx, det, ants.ANTS_LRF_COMPOSITE, (8, 8), (-12.0, -12.0), (12.0, 12.0),
+                                         p2, v2, n_int_r=12, hi_r=40.0),
+        "axial_z": ants.Lrf.fit_scheme(ctx, det, ants.ANTS_LRF_AXIAL_Z, (12, 6), (0.0, 0.0), (40.0, 20.0), p3,
+                                       synth.truth_eta(sxy, g, p3)),
+        "sliced": ants.Lrf.fit_scheme(ctx, det, ants.ANTS_LRF_SLICED, (8, 8), (-12.0, -12.0, 0.0),
+                                      (12.0, 12.0, 20.0), p3s, synth.truth_eta(sxy, g, p3s), n_planes=5)}
+    n = 1_000_000
+    out = {}
+    for name, lrf in lrfs.items():
+        three = name != "composite"
+        src = ants.SimParams("square", 8.0, 0.0, 0.0, 0.0, 20.0 if three else 0.0, 4000.0, 0.05, 0.0)
+        sig, truth = ants.simulate(ctx, lrf, src, n, seed=77)
+        if three:
+            p = ants.CgsParams(n_xy=7, iters=5, step_xy=2.0, n_z=5, step_z=4.0, z0=10.0)
+            nodes = 7 * 7 * 5
+        else:
+            p = ants.CgsParams(n_xy=9, iters=7, step_xy=2.0)
+            nodes = 81
+        for _ in range(2):
+            res = ants.reconstruct(ctx, lrf, p, sig, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            res = ants.reconstruct(ctx, lrf, p, sig, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / 2
+        evals = n * nodes * p.iters * 16
+        d = (res.xyz - truth[:, :3]).double()
+        out[name] = {"events_per_s": n / dt, "ms_per_launch": 1e3 * dt, "roofline": alu_roofline(evals / dt, name),
+                     "rms_dxy_mm": float((d[:, :2] ** 2).sum(1).mean().sqrt()),
+                     "rms_dz_mm": float((d[:, 2] ** 2).mean().sqrt()) if three else None}
+    return {"workload": "4x4 SiPMs, pitch 6 mm; 10^6 events per scheme simulated from its own LRFs; composite "
+                        "9x9 x 7 grids, axial+z and sliced 7x7x5 x 5 grids; per-node kernel", **out}
+
+
 def iterative_run(args, ants, torch, ctx, stream):
     """Iterative LRF reconstruction (Sec. 8) from a flood of 10^6 events of the
     19-PMT detector (relative gains N(1, 0.1^2), known): from a too-wide
@@ -632,13 +686,14 @@ def run_ours(args):
     batched = optional(batched_run, args.no_batched)
     iterative = optional(iterative_run, args.no_iterative)
     variants = optional(variants_run, args.no_variants)
+    schemes = optional(schemes_run, args.no_schemes)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
-        "iterative_lrf": iterative, "variants_8x8": variants,
+        "iterative_lrf": iterative, "variants_8x8": variants, "lrf_schemes_4x4": schemes,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -665,6 +720,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-detector 3D batched run")
     ap.add_argument("--no-iterative", action="store_true", help="skip the iterative LRF reconstruction")
     ap.add_argument("--no-variants", action="store_true", help="skip the search variants")
+    ap.add_argument("--no-schemes", action="store_true", help="skip the composite, axial+z and sliced LRFs")
     ap.add_argument("--iter-events", type=int, default=1_000_000)
     ap.add_argument("--iter-cycles", type=int, default=6)
     ap.add_argument("--batch-steps", type=int, default=1)
