@@ -680,8 +680,8 @@ ANTS_API int ants_event_centroid(ants_ctx *ctx, const ants_lrf *lrf, const float
 /* Chi-squared of each event's reconstruction (Sec. 5.2): Pearson's
  * statistic sum_i (s_i - mu_i)^2 / mu_i with mu_i = E eta_i(xyz), over the
  * sensors with mu_i > 0, divided by n_s - 3 (x, y, E fitted; 1 when
- * n_s <= 3); NaN when the position or E is not finite.  eta in FP32, the sum
- * in FP64, stored as FP32.  sum_dev (nullable) receives the sum of the
+ * n_s <= 3); NaN when the position or E is not finite.  FP32 (the terms'
+ * differences are exact near the mean; a pairwise sum over the warp).  sum_dev (nullable) receives the sum of the
  * signals.  Asynchronous on `stream`.  Errors: ANTS_E_ARG, ANTS_E_CUDA. */
 ANTS_API int ants_event_chi2(ants_ctx *ctx, const ants_lrf *lrf, const float *signals_dev, long n_events,
                              const float *xyz_dev, const float *E_dev, float *chi2_dev, float *sum_dev,

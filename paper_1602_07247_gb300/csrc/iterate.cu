@@ -49,6 +49,13 @@ int dmalloc(DBuf &b, size_t count, const char *what)
 constexpr int kEvWarps = 8;  // events (one warp each) per block
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -95,27 +102,28 @@ __global__ void chi2_kernel(LrfDev L, const float *sig, long n_e, const float *x
     const float x = xyz[3 * e], y = xyz[3 * e + 1], z = xyz[3 * e + 2], En = E[e];
     const bool fin = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(En);
     const float *s = sig + e * L.n_s;
-    double acc = 0.0, S = 0.0;
+    // FP32 throughout (FP64 is scarce): s - mu is exact whenever s is within a
+    // factor 2 of mu (Sterbenz), so the terms carry the rounding of mu only,
+    // and the warp's butterfly sum is pairwise
+    float acc = 0.0f, S = 0.0f;
     for (int i = lane; i < L.n_s; i += 32) {
         const float si = s[i];
-        S += (double)si;
+        S += si;
         if (fin) {
             bool ok;
             const float mu = En * lrf_eta_point(L, i, x, y, z, ok);
             if (ok && mu > 0.0f) {
-                // the difference is exact in FP64; the term in FP32 (FP64
-                // division is scarce), the sum in FP64
-                const double d = (double)si - (double)mu;
-                acc += (double)__fdividef((float)(d * d), mu);
+                const float d = si - mu;
+                acc += __fdividef(d * d, mu);
             }
         }
     }
-    acc = warp_sum(acc);
-    S = warp_sum(S);
+    acc = warp_sum_f(acc);
+    S = warp_sum_f(S);
     if (lane == 0) {
-        const double dof = L.n_s > 3 ? (double)(L.n_s - 3) : 1.0;
-        chi2[e] = fin ? (float)(acc / dof) : __int_as_float(0x7fc00000);
-        if (ssum) ssum[e] = (float)S;
+        const float dof = L.n_s > 3 ? (float)(L.n_s - 3) : 1.0f;
+        chi2[e] = fin ? acc / dof : __int_as_float(0x7fc00000);
+        if (ssum) ssum[e] = S;
     }
 }
 
@@ -180,7 +188,8 @@ __global__ void __launch_bounds__(kStatThreads) change_sums(LrfDev A, LrfDev B, 
 {
     __shared__ double s_a[kStatThreads], s_b[kStatThreads];
     const long total = n_kept * A.n_s;
-    double d2 = 0.0, a2 = 0.0;
+    // a convergence monitor: FP32 partial sums per thread, the tree in FP64
+    float d2 = 0.0f, a2 = 0.0f;
     for (long t = (long)blockIdx.x * kStatThreads + threadIdx.x; t < total; t += (long)kStatBlocks * kStatThreads) {
         const long k = t / A.n_s;
         const int i = (int)(t - k * A.n_s);
@@ -189,13 +198,13 @@ __global__ void __launch_bounds__(kStatThreads) change_sums(LrfDev A, LrfDev B, 
         bool oka, okb;
         const float a = lrf_eta_point(A, i, x, y, z, oka), b = lrf_eta_point(B, i, x, y, z, okb);
         if (oka && okb) {
-            const double d = (double)b - (double)a;
-            d2 += d * d;
-            a2 += (double)a * (double)a;
+            const float d = b - a;
+            d2 = fmaf(d, d, d2);
+            a2 = fmaf(a, a, a2);
         }
     }
-    s_a[threadIdx.x] = d2;
-    s_b[threadIdx.x] = a2;
+    s_a[threadIdx.x] = (double)d2;
+    s_b[threadIdx.x] = (double)a2;
     __syncthreads();
     for (int o = kStatThreads / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) {
