@@ -109,14 +109,15 @@ __device__ __forceinline__ float radial_eta(const LrfDev &L, int i, float r)
 
 // eta_i at one point; ok = false outside the domain (used by the evaluation
 // entry point and by per-event prologue/epilogue code)
-__device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, float y, float z, bool &ok)
+template <int TYPE>
+__device__ __forceinline__ float lrf_eta_t(const LrfDev &L, int i, float x, float y, float z, bool &ok)
 {
-    if (L.type == ANTS_LRF_RADIAL) {
+    if (TYPE == ANTS_LRF_RADIAL) {
         const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
         ok = r <= L.hi[0];
         return ok ? radial_eta(L, i, r) : 0.0f;
     }
-    if (L.type == ANTS_LRF_COMPOSITE) {
+    if (TYPE == ANTS_LRF_COMPOSITE) {
         // the axial part at r plus the XY part
         const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
         ok = r <= L.hi_r && in_box(L, x, y, z);
@@ -125,7 +126,7 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
         return radial_profile(L.rpoly + i * L.n_int_r, L.inv_h_r, L.n_int_r, r) +
                spline2(c, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1]);
     }
-    if (L.type == ANTS_LRF_AXIAL_Z) {
+    if (TYPE == ANTS_LRF_AXIAL_Z) {
         // one spline of (r, z)
         const float r = plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]);
         ok = r <= L.hi[0] && z >= L.lo[1] && z <= L.hi[1];
@@ -133,7 +134,7 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
         return spline2(L.coef + (size_t)i * L.n_coef, r, 0.0f, L.inv_h[0], L.n_int[0], z, L.lo[1], L.inv_h[1],
                        L.n_int[1]);
     }
-    if (L.type == ANTS_LRF_SLICED) {
+    if (TYPE == ANTS_LRF_SLICED) {
         // the XY splines of the two closest planes, blended linearly in z
         ok = in_box(L, x, y, z);
         if (!ok) return 0.0f;
@@ -154,7 +155,7 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
     int jz = 0, nz = 1;
     bs_weights(tx, wx);
     bs_weights(ty, wy);
-    if (L.type == ANTS_LRF_XYZ) {
+    if (TYPE == ANTS_LRF_XYZ) {
         jz = bs_span(z, L.lo[2], L.inv_h[2], L.n_int[2], tz);
         bs_weights(tz, wz);
         nz = 4;
@@ -174,6 +175,19 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
         f = fmaf(fz, wz[cz], f);
     }
     return f;
+}
+
+// the same with the type read at run time
+__device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, float y, float z, bool &ok)
+{
+    switch (L.type) {
+    case ANTS_LRF_RADIAL: return lrf_eta_t<ANTS_LRF_RADIAL>(L, i, x, y, z, ok);
+    case ANTS_LRF_XY: return lrf_eta_t<ANTS_LRF_XY>(L, i, x, y, z, ok);
+    case ANTS_LRF_XYZ: return lrf_eta_t<ANTS_LRF_XYZ>(L, i, x, y, z, ok);
+    case ANTS_LRF_COMPOSITE: return lrf_eta_t<ANTS_LRF_COMPOSITE>(L, i, x, y, z, ok);
+    case ANTS_LRF_AXIAL_Z: return lrf_eta_t<ANTS_LRF_AXIAL_Z>(L, i, x, y, z, ok);
+    default: return lrf_eta_t<ANTS_LRF_SLICED>(L, i, x, y, z, ok);
+    }
 }
 
 // every LRF of the sensors with s_act[i] != 0 (all sensors when s_act is

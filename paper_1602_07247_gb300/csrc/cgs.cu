@@ -76,7 +76,7 @@ template <int TYPE>
 __device__ __forceinline__ float eta_floor(const LrfDev &L, int i, float x, float y, float z)
 {
     bool ok;
-    float v = lrf_eta_point(L, i, x, y, z, ok);
+    float v = lrf_eta_t<TYPE>(L, i, x, y, z, ok);
     return fmaxf(v, kEtaFloor);
 }
 
@@ -270,13 +270,29 @@ __device__ __forceinline__ void event_epilogue(const CgsArgs &a, long e, const f
     __syncwarp();
 }
 
+// one power-basis cubic of a radial table held in shared memory (32-bit
+// shared address) or read through the read-only path
+template <bool SPOLY>
+__device__ __forceinline__ float4 poly_at(const float4 *poly, unsigned saddr, int j)
+{
+    if (SPOLY) {
+        float4 v;
+        asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+            : "r"(saddr + 16u * (unsigned)j));
+        return v;
+    }
+    return __ldg(poly + j);
+}
+
 // Scores of a radial-LRF grid, NPL nodes per lane at a time sharing each
 // sensor's data; per (node, sensor) the same operations in the same order as
-// node_score.  Updates the lane's best (score, node).
-template <int NPL>
+// node_score.  Updates the lane's best (score, node).  With SPOLY the
+// cubics are read from the block's shared copy `polys`.
+template <int NPL, bool SPOLY>
 __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, const float *s_sig, const float *s_ic,
                                              const float *s_ec, float S, float inv_hc, float cx, float cy, float sxy,
-                                             int nodes, int lane, float &bestF, int &bestk)
+                                             int nodes, int lane, float &bestF, int &bestk, const float4 *polys)
 {
     const int c_xy = (a.n_xy - 1) / 2;
     const float hi = L.hi[0];
@@ -298,12 +314,19 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
             const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
             const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
             const float gi = __ldg(L.gain + i);
-            const float4 *poly = radial_poly(L, i);
+            const float4 *poly = polys + (L.shared ? 0 : i * n_int);
+            const unsigned sp = SPOLY ? (unsigned)__cvta_generic_to_shared(poly) : 0u;
 #pragma unroll
             for (int m = 0; m < NPL; ++m) {
                 const float r = plane_dist(xs[m] - sx, ys[m] - sy);
                 ok[m] = ok[m] && r <= hi;
-                const float eta = fmaxf(gi * radial_profile(poly, inv_h, n_int, fminf(r, hi)), kEtaFloor);
+                // the span and local parameter of radial_profile
+                const float u = fminf(r, hi) * inv_h;
+                const int j = min((int)u, n_int - 1);
+                const float t = u - (float)j;
+                const float4 pc = poly_at<SPOLY>(poly, sp, j);
+                const float f = fmaf(t, fmaf(t, fmaf(t, pc.w, pc.z), pc.y), pc.x);
+                const float eta = fmaxf(gi * f, kEtaFloor);
                 acc[m] = fmaf(si, __log2f(eta * ici), acc[m]);
                 dh[m] += eta - eci;
             }
@@ -325,9 +348,9 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
 // Reconstruct event e of a (one warp; s_sig, s_ic, s_ec: 3 n_s floats of
 // this warp's shared memory), every node evaluated on its own.  Shared by the
 // plain and the batched kernels.
-template <int TYPE>
+template <int TYPE, bool SPOLY = false>
 __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig, float *s_ic, float *s_ec,
-                                          int lane)
+                                          int lane, const float4 *s_poly = nullptr)
 {
     const LrfDev &L = a.L;
     const int nodes = a.n_xy * a.n_xy * a.n_z;
@@ -343,9 +366,11 @@ __device__ __forceinline__ void cgs_event(const CgsArgs &a, long e, float *s_sig
             // a lane's nodes share each sensor's data (3 per lane covers a
             // 9 x 9 grid in one pass, 4 per lane larger grids)
             if (nodes <= 96)
-                radial_nodes<3>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk);
+                radial_nodes<3, SPOLY>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk,
+                                       SPOLY ? s_poly : L.rpoly);
             else
-                radial_nodes<4>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk);
+                radial_nodes<4, SPOLY>(a, L, s_sig, s_ic, s_ec, S, inv_hc, cx, cy, sxy, nodes, lane, bestF, bestk,
+                                       SPOLY ? s_poly : L.rpoly);
         } else {
             for (int k = lane; k < nodes; k += 32) {
                 int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy, iz = k / (a.n_xy * a.n_xy);
@@ -580,8 +605,9 @@ __host__ inline void setup_sep(CgsArgs &a)
     a.rz_cap = sep_rows(a.n_z, a.step_z, a.L.inv_h[2], a.L.n_int[2]);
 }
 
-template <int TYPE>
-__global__ void __launch_bounds__(256, TYPE == ANTS_LRF_XYZ ? 2 : 3) cgs_plain_kernel(CgsArgs a, int warp_floats)
+template <int TYPE, bool SPOLY>
+__global__ void __launch_bounds__(256, TYPE == ANTS_LRF_XYZ ? 2 : 3) cgs_plain_kernel(CgsArgs a, int warp_floats,
+                                                                                     int n_poly)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -590,11 +616,18 @@ __global__ void __launch_bounds__(256, TYPE == ANTS_LRF_XYZ ? 2 : 3) cgs_plain_k
     float *s_ic = s_sig + n_s;  // 1 / eta_i(centre)
     float *s_ec = s_ic + n_s;   // eta_i(centre)
     float *sep = s_sig + ((3 * n_s + 3) & ~3);
+    // SPOLY (radial): the power-basis cubics copied once per block
+    float4 *s_poly = nullptr;
+    if (SPOLY) {
+        s_poly = (float4 *)(smem + (((size_t)wpb * warp_floats + 3) & ~(size_t)3));
+        for (int k = threadIdx.x; k < n_poly; k += blockDim.x) s_poly[k] = a.L.rpoly[k];
+        __syncthreads();
+    }
     for (long e = (long)blockIdx.x * wpb + wib; e < a.n_e; e += (long)gridDim.x * wpb) {
         if (TYPE == ANTS_LRF_XYZ && a.sep)
             cgs_event_xyz_sep(a, e, s_sig, s_ic, s_ec, sep, lane);
         else
-            cgs_event<TYPE>(a, e, s_sig, s_ic, s_ec, lane);
+            cgs_event<TYPE, SPOLY>(a, e, s_sig, s_ic, s_ec, lane, s_poly);
     }
 }
 
@@ -611,16 +644,34 @@ int launch_typed(const ants_ctx *ctx, CgsArgs a, cudaStream_t stream, bool allow
     }
     const int threads = 32 * wpb;
     size_t smem = (size_t)wpb * warp_floats * sizeof(float);
-    if (smem > ctx->smem_optin) return fail(ANTS_E_SHAPE, "cgs: %d sensors need too much shared memory", a.L.n_s);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(cgs_plain_kernel<TYPE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_plain)");
+    // radial cubics in shared memory when they take at most 32 KB
+    int n_poly = 0;
+    if (TYPE == ANTS_LRF_RADIAL) {
+        const long np = (long)(a.L.shared ? 1 : a.L.n_s) * a.L.n_int[0];
+        if (np * 16 <= 32 * 1024) {
+            n_poly = (int)np;
+            smem = ((smem + 15) & ~(size_t)15) + (size_t)np * 16;
+        }
     }
+    if (smem > ctx->smem_optin) return fail(ANTS_E_SHAPE, "cgs: %d sensors need too much shared memory", a.L.n_s);
     long blocks = (a.n_e + wpb - 1) / wpb;
     long cap = (long)ctx->n_sm * (64 / wpb);
     if (blocks > cap) blocks = cap;
-    cgs_plain_kernel<TYPE><<<(unsigned)blocks, threads, smem, stream>>>(a, warp_floats);
+    if (TYPE == ANTS_LRF_RADIAL && n_poly > 0) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(cgs_plain_kernel<ANTS_LRF_RADIAL, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_plain)");
+        }
+        cgs_plain_kernel<ANTS_LRF_RADIAL, true><<<(unsigned)blocks, threads, smem, stream>>>(a, warp_floats, n_poly);
+    } else {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(cgs_plain_kernel<TYPE, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_plain)");
+        }
+        cgs_plain_kernel<TYPE, false><<<(unsigned)blocks, threads, smem, stream>>>(a, warp_floats, 0);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cgs_plain_kernel launch");
     count_launch();

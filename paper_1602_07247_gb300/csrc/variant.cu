@@ -69,10 +69,11 @@ __device__ __forceinline__ float vpoisson_const(float s)
     return s * logf(s) - s - lgammaf(s + 1.0f);
 }
 
+template <int TYPE>
 __device__ __forceinline__ float eta_at(const LrfDev &L, int i, float x, float y, float z)
 {
     bool ok;
-    return fmaxf(lrf_eta_point(L, i, x, y, z, ok), kEtaFloor);
+    return fmaxf(lrf_eta_t<TYPE>(L, i, x, y, z, ok), kEtaFloor);
 }
 
 // every LRF in the match defined at the node
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
             if (a.criterion == 0) {
                 float hc = 0.0f;
                 for (int i = lane; i < n_s; i += 32) {
-                    const float eta = eta_at(L, i, cx, cy, cz);
+                    const float eta = eta_at<TYPE>(L, i, cx, cy, cz);
                     s_ec[i] = eta;
                     s_ic[i] = __frcp_rn(eta);
                     if (s_act[i] != 0.0f) hc += eta;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
                         float acc = 0.0f, dh = 0.0f;
                         for (int i = 0; i < n_s; ++i) {
                             if (s_act[i] == 0.0f) continue;  // the same sensor on every lane
-                            const float eta = eta_at(L, i, x, y, z);
+                            const float eta = eta_at<TYPE>(L, i, x, y, z);
                             acc = fmaf(s_sig[i], __log2f(eta * s_ic[i]), acc);
                             dh += eta - s_ec[i];
                         }
@@ -223,12 +224,12 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
                     } else {
                         float H = 0.0f;
                         for (int i = 0; i < n_s; ++i)
-                            if (s_act[i] != 0.0f) H += eta_at(L, i, x, y, z);
+                            if (s_act[i] != 0.0f) H += eta_at<TYPE>(L, i, x, y, z);
                         const float En = S / H;
                         float chi = 0.0f;
                         for (int i = 0; i < n_s; ++i) {
                             if (s_act[i] == 0.0f) continue;
-                            const float mu = En * eta_at(L, i, x, y, z), d = s_sig[i] - mu;
+                            const float mu = En * eta_at<TYPE>(L, i, x, y, z), d = s_sig[i] - mu;
                             chi = fmaf(d, d / mu, chi);
                         }
                         F = -chi;
@@ -260,13 +261,13 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
         // ---- energy and full Poisson log-likelihood over the match ----------
         float H = 0.0f;
         for (int i = lane; i < n_s; i += 32)
-            if (s_act[i] != 0.0f) H += eta_at(L, i, cx, cy, cz);
+            if (s_act[i] != 0.0f) H += eta_at<TYPE>(L, i, cx, cy, cz);
         H = vwarp_sum(H);
         const float En = S / H;
         float ll = 0.0f;
         for (int i = lane; i < n_s; i += 32) {
             if (s_act[i] == 0.0f) continue;
-            const float mu = En * eta_at(L, i, cx, cy, cz), s = s_sig[i];
+            const float mu = En * eta_at<TYPE>(L, i, cx, cy, cz), s = s_sig[i];
             ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + vpoisson_const(s) : -mu;
         }
         ll = vwarp_sum(ll);
