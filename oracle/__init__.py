@@ -417,6 +417,75 @@ def cgs_variant_replay(lrf: Lrf, params: CgsParams, sig, variant: Variant, trace
     return dict(xyz=xyz, E=E, logL=logL, status=status, n_tie=n_tie, n_bad=n_bad)
 
 
+class _MinParams(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("lambda0", C.c_double), ("fit_z", C.c_int)]
+
+
+@dataclass
+class Minimize:
+    """Continuous minimisation (Sec. 5.1.2.1): damped Fisher scoring
+    (Levenberg-Marquardt) of the variant's criterion over x, y (and z for a
+    3D LRF with fit_z), E profiled; at most max_iter trial steps, converged
+    when an accepted step is shorter than tol (mm)."""
+
+    max_iter: int = 30
+    tol: float = 1e-3
+    lambda0: float = 1e-3
+    fit_z: int = 1
+
+    def _struct(self) -> _MinParams:
+        return _MinParams(int(self.max_iter), float(self.tol), float(self.lambda0), int(self.fit_z))
+
+
+def _minlib(mutant=0):
+    L = _vlib(mutant)
+    if not getattr(L, "_min_declared", False):
+        L.or_lrf_grad.argtypes = [C.POINTER(_Lrf), C.c_long, _D, C.c_int, _D]
+        L.or_bspline_dbasis4.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _D, _D]
+        L.or_bspline_dbasis4.restype = C.c_int
+        L.or_minimize.argtypes = [C.POINTER(_Lrf), C.POINTER(_Cgs), C.POINTER(_Variant), C.POINTER(_MinParams), _D,
+                                  C.c_long, _D, _D, _D, _D, _D, _I, _I]
+        L._min_declared = True
+    return L
+
+
+def bspline_dbasis4(n_int: int, lo: float, hi: float, x: float, mutant: int = 0):
+    """(first index, B[4], dB/dx[4]) of the cubic basis at x; index -1 outside."""
+    B, D = np.empty(4), np.empty(4)
+    j = _minlib(mutant).or_bspline_dbasis4(int(n_int), float(lo), float(hi), float(x), _d(B), _d(D))
+    return j, B, D
+
+
+def lrf_grad(lrf: Lrf, pts, mutant: int = 0) -> np.ndarray:
+    """Gradients (d/dx, d/dy, d/dz) of every sensor's LRF at the points:
+    [n_pts, n_sensors, 3], NaN where undefined."""
+    pts = _f64(pts)
+    s = lrf._struct()
+    out = np.empty((pts.shape[0], lrf.n_sensors, 3))
+    _minlib(mutant).or_lrf_grad(C.byref(s), pts.shape[0], _d(pts), pts.shape[1], _d(out))
+    return out
+
+
+def minimize(lrf: Lrf, sig, variant: Variant, params: Minimize, z0: float = 0.0, start_xyz=None, gain=None,
+             mutant: int = 0):
+    """The continuous minimisation of every event from the variant's start
+    (or start_xyz [n, 3]); returns xyz, E, logL, status and n_iter (trials
+    used, negative when max_iter ran out)."""
+    sig = _f64(sig)
+    n = sig.shape[0]
+    s, v, m = lrf._struct(), variant._struct(), params._struct()
+    p = CgsParams(n_xy=1, iters=0, step_xy=0.0, z0=z0)._struct()
+    xyz, E, logL = np.empty((n, 3)), np.empty(n), np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    n_iter = np.empty(n, dtype=np.int32)
+    st = _f64(start_xyz) if start_xyz is not None else None
+    g = _opt(gain)
+    _minlib(mutant).or_minimize(C.byref(s), C.byref(p), C.byref(v), C.byref(m), _p(g), n, _d(sig),
+                              _d(st) if st is not None else C.cast(None, _D), _d(xyz), _d(E), _d(logL), _i(status),
+                              _i(n_iter))
+    return dict(xyz=xyz, E=E, logL=logL, status=status, n_iter=n_iter)
+
+
 def brute_force(lrf: Lrf, sig, x_rng, nx, y_rng, ny, z=0.0, mutant: int = 0):
     sig = _f64(sig)
     n = sig.shape[0]

@@ -813,9 +813,11 @@ static int or_variant_valid(const or_lrf *L, const int *act, double x, double y,
     return or_valid_act(L, act, x, y, z);
 }
 
-/* Start position, the sensors in the match (act) and their signal sum. */
+/* Start position, the sensors in the match (act) and their signal sum.
+ * given (nullable): a start position to use instead of the variant's own. */
 static int or_variant_start(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const double *gain,
-                            const double *s, double *cx, double *cy, double *cz, double *S_out, int *act)
+                            const double *s, const double *given, double *cx, double *cy, double *cz, double *S_out,
+                            int *act)
 {
     int n = L->n_sensors;
     double tot = 0.0;
@@ -827,7 +829,11 @@ static int or_variant_start(const or_lrf *L, const or_cgs_params *P, const or_va
     }
     *S_out = 0.0;
     if (!(tot > 0.0)) return OR_EVT_ZERO_SIGNAL;
-    if (V->start == 1) {
+    if (given) {
+        *cx = given[0];
+        *cy = given[1];
+        *cz = given[2];
+    } else if (V->start == 1) {
         int best = -1;
         double bv = -1.0;
         for (int i = 0; i < n; ++i) {
@@ -856,8 +862,8 @@ static int or_variant_start(const or_lrf *L, const or_cgs_params *P, const or_va
         *cx = nx / den;
         *cy = ny / den;
     }
-    *cz = or_is_3d(L->type) ? P->z0 : 0.0;
-    if (or_has_box(L->type)) {
+    if (!given) *cz = or_is_3d(L->type) ? P->z0 : 0.0;
+    if (!given && or_has_box(L->type)) {
         if (*cx < L->lo[0]) *cx = L->lo[0];
         if (*cx > L->hi[0]) *cx = L->hi[0];
         if (*cy < L->lo[1]) *cy = L->lo[1];
@@ -963,7 +969,7 @@ static void or_cgs_variant_run(const or_lrf *L, const or_cgs_params *P, const or
         const double *s = sig + e * L->n_sensors;
         int *act = (int *)malloc(sizeof(int) * (size_t)L->n_sensors);
         double cx, cy, cz, S;
-        int st = or_variant_start(L, P, V, gain, s, &cx, &cy, &cz, &S, act);
+        int st = or_variant_start(L, P, V, gain, s, NULL, &cx, &cy, &cz, &S, act);
         status[e] = st;
         if (n_tie) n_tie[e] = 0;
         if (n_bad) n_bad[e] = 0;
@@ -1022,6 +1028,398 @@ void or_cgs_variant_replay(const or_lrf *L, const or_cgs_params *P, const or_var
                            double *logL, int *status, int *n_tie, int *n_bad)
 {
     or_cgs_variant_run(L, P, V, gain, n_e, sig, trace_in, tau_rel, xyz, E, logL, status, NULL, n_tie, n_bad);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Continuous minimisation (Sec. 5.1.2.1: the match, maximum likelihood or   */
+/* least squares, minimised over the two or three coordinates by a gradient  */
+/* method from the centroid or strongest-sensor start; the paper uses        */
+/* Minuit2's Migrad).  Here: damped Fisher scoring (Levenberg-Marquardt)     */
+/* with the energy profiled out, E = S / H at every position.                */
+/* ------------------------------------------------------------------------ */
+
+/* The four non-zero cubic basis functions at x and their derivatives,
+ * dB_{j,3}/dx = 3 [B_{j,2}(x) / (t_{j+3} - t_j) - B_{j+1,2}(x) / (t_{j+4} -
+ * t_{j+1})] (the derivative of a B-spline as a difference of lower-degree
+ * ones), from the Cox-de Boor triangle of degrees 0..3.  Returns the index
+ * of the first one, or -1 outside [lo, hi]. */
+int or_bspline_dbasis4(int n_int, double lo, double hi, double x, double B[4], double dB[4])
+{
+    int m = or_span(n_int, lo, hi, x);
+    if (m < 0) return -1;
+    double N[4][4]; /* N[k][r] = B_{m-k+r, k}(x) */
+    N[0][0] = 1.0;
+    for (int k = 1; k <= 3; ++k) {
+        for (int r = 0; r <= k; ++r) {
+            int j = m - k + r;
+            double v = 0.0;
+            if (r >= 1)
+                v += (x - or_knot(n_int, lo, hi, j)) / (or_knot(n_int, lo, hi, j + k) - or_knot(n_int, lo, hi, j)) *
+                     N[k - 1][r - 1];
+            if (r <= k - 1)
+                v += (or_knot(n_int, lo, hi, j + k + 1) - x) /
+                     (or_knot(n_int, lo, hi, j + k + 1) - or_knot(n_int, lo, hi, j + 1)) * N[k - 1][r];
+            N[k][r] = v;
+        }
+    }
+    for (int r = 0; r < 4; ++r) {
+        int j = m - 3 + r;
+        double a = r >= 1 ? N[2][r - 1] / (or_knot(n_int, lo, hi, j + 3) - or_knot(n_int, lo, hi, j)) : 0.0;
+        double b = r <= 2 ? N[2][r] / (or_knot(n_int, lo, hi, j + 4) - or_knot(n_int, lo, hi, j + 1)) : 0.0;
+        B[r] = N[3][r];
+#if OR_MUTANT == 21
+        dB[r] = 3.0 * (a + b);
+#else
+        dB[r] = 3.0 * (a - b);
+#endif
+    }
+    return m - 3;
+}
+
+/* or_spline2 with its partial derivatives along u and v. */
+static double or_spline2_grad(int n0, double lo0, double hi0, int n1, double lo1, double hi1, const double *c,
+                              double u, double v, int *ok, double *du, double *dv)
+{
+    double B0[4], B1[4], D0[4], D1[4];
+    int j0 = or_bspline_dbasis4(n0, lo0, hi0, u, B0, D0);
+    int j1 = or_bspline_dbasis4(n1, lo1, hi1, v, B1, D1);
+    *ok = j0 >= 0 && j1 >= 0;
+    *du = *dv = 0.0;
+    if (!*ok) return 0.0;
+    double f = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            double cc = c[(size_t)(j1 + b) * (n0 + 3) + (size_t)(j0 + a)];
+            f += cc * B0[a] * B1[b];
+            *du += cc * D0[a] * B1[b];
+            *dv += cc * B0[a] * D1[b];
+        }
+    return f;
+}
+
+/* An axial part's derivative along x and y: df/dr times (dx, dy) / r
+ * (taken as 0 at r = 0, where the direction is undefined). */
+static void or_axial_dir(double dfdr, double dx, double dy, double r, double *gx, double *gy)
+{
+    *gx = r > 0.0 ? dfdr * dx / r : 0.0;
+    *gy = r > 0.0 ? dfdr * dy / r : 0.0;
+}
+
+/* eta_i at (x, y, z) as or_lrf_eta, and its gradient g = (d/dx, d/dy,
+ * d/dz) (d/dz = 0 for 2D LRFs). */
+static double or_lrf_eta_grad(const or_lrf *L, int i, double x, double y, double z, int *ok, double g[3])
+{
+    int nc = or_n_coef(L);
+    double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
+    double r = sqrt(dx * dx + dy * dy);
+    g[0] = g[1] = g[2] = 0.0;
+    *ok = 1;
+    if (L->type == OR_RADIAL || L->type == OR_COMPOSITE) {
+        const double *c = L->coef + (size_t)(L->type == OR_RADIAL && L->shared ? 0 : i) * nc;
+        int n = L->type == OR_RADIAL ? L->n_int[0] : L->n_int_r;
+        double lo = L->type == OR_RADIAL ? L->lo[0] : 0.0, hi = L->type == OR_RADIAL ? L->hi[0] : L->hi_r;
+        double B[4], D[4];
+        int j0 = or_bspline_dbasis4(n, lo, hi, r, B, D);
+        if (j0 < 0) { *ok = 0; return 0.0; }
+        double f = 0.0, fr = 0.0;
+        for (int a = 0; a < 4; ++a) {
+            f += c[j0 + a] * B[a];
+            fr += c[j0 + a] * D[a];
+        }
+        if (L->type == OR_RADIAL) {
+            double gn = L->gain ? L->gain[i] : 1.0;
+            or_axial_dir(gn * fr, dx, dy, r, &g[0], &g[1]);
+            return gn * f;
+        }
+        int okxy;
+        double fx, fy;
+        double fxy = or_spline2_grad(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                                     c + L->n_int_r + 3, x, y, &okxy, &fx, &fy);
+        if (!okxy) { *ok = 0; g[0] = g[1] = 0.0; return 0.0; }
+        or_axial_dir(fr, dx, dy, r, &g[0], &g[1]);
+        g[0] += fx;
+        g[1] += fy;
+        return f + fxy;
+    }
+    if (L->type == OR_AXIAL_Z) {
+        double fr, fz;
+        double f = or_spline2_grad(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                                   L->coef + (size_t)i * nc, r, z, ok, &fr, &fz);
+        if (!*ok) return 0.0;
+        or_axial_dir(fr, dx, dy, r, &g[0], &g[1]);
+        g[2] = fz;
+        return f;
+    }
+    if (L->type == OR_SLICED) {
+        if (!(z >= L->lo[2] && z <= L->hi[2])) { *ok = 0; return 0.0; }
+        int m = L->n_planes, ncxy = nc / m;
+        double dz = (L->hi[2] - L->lo[2]) / (double)(m - 1), u = (z - L->lo[2]) / dz;
+        int j = (int)floor(u);
+        if (j > m - 2) j = m - 2;
+        if (j < 0) j = 0;
+        double w = u - (double)j;
+        const double *c = L->coef + (size_t)i * nc;
+        int ok0, ok1;
+        double f0x, f0y, f1x, f1y;
+        double f0 = or_spline2_grad(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                                    c + (size_t)j * ncxy, x, y, &ok0, &f0x, &f0y);
+        double f1 = or_spline2_grad(L->n_int[0], L->lo[0], L->hi[0], L->n_int[1], L->lo[1], L->hi[1],
+                                    c + (size_t)(j + 1) * ncxy, x, y, &ok1, &f1x, &f1y);
+        if (!ok0 || !ok1) { *ok = 0; return 0.0; }
+        g[0] = (1.0 - w) * f0x + w * f1x;
+        g[1] = (1.0 - w) * f0y + w * f1y;
+        g[2] = (f1 - f0) / dz;
+        return (1.0 - w) * f0 + w * f1;
+    }
+    const double *c = L->coef + (size_t)i * nc;
+    double Bx[4], By[4], Bz[4] = {1.0, 0.0, 0.0, 0.0}, Dx[4], Dy[4], Dz[4] = {0.0, 0.0, 0.0, 0.0};
+    int jx = or_bspline_dbasis4(L->n_int[0], L->lo[0], L->hi[0], x, Bx, Dx);
+    int jy = or_bspline_dbasis4(L->n_int[1], L->lo[1], L->hi[1], y, By, Dy);
+    int jz = 0, nz = 1;
+    if (L->type == OR_XYZ) {
+        jz = or_bspline_dbasis4(L->n_int[2], L->lo[2], L->hi[2], z, Bz, Dz);
+        nz = 4;
+    }
+    if (jx < 0 || jy < 0 || jz < 0) { *ok = 0; return 0.0; }
+    int sx = L->n_int[0] + 3, sy = L->n_int[1] + 3;
+    double f = 0.0;
+    for (int cz = 0; cz < nz; ++cz)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                double cc = c[((size_t)(jz + cz) * sy + (size_t)(jy + b)) * sx + (size_t)(jx + a)];
+                f += cc * Bx[a] * By[b] * Bz[cz];
+                g[0] += cc * Dx[a] * By[b] * Bz[cz];
+                g[1] += cc * Bx[a] * Dy[b] * Bz[cz];
+                g[2] += cc * Bx[a] * By[b] * Dz[cz];
+            }
+    return f;
+}
+
+/* Gradients of every sensor's LRF at the points: out[(p n_s + i) 3 + k]; NaN
+ * where the LRF is undefined. */
+void or_lrf_grad(const or_lrf *L, long n_pts, const double *pts, int dim, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < n_pts; ++p) {
+        double x = pts[p * dim], y = dim > 1 ? pts[p * dim + 1] : 0.0;
+        double z = dim > 2 ? pts[p * dim + 2] : 0.0;
+        for (int i = 0; i < L->n_sensors; ++i) {
+            int ok;
+            double g[3];
+            or_lrf_eta_grad(L, i, x, y, z, &ok, g);
+            for (int k = 0; k < 3; ++k) out[(p * L->n_sensors + i) * 3 + k] = ok ? g[k] : NAN;
+        }
+    }
+}
+
+typedef struct {
+    int max_iter;   /* trial steps (accepted or not) */
+    double tol;     /* converged when an accepted step is shorter than tol (mm) */
+    double lambda0; /* initial damping */
+    int fit_z;      /* 3D LRFs: z is a free coordinate too */
+} or_min_params;
+
+#define OR_LAMBDA_MIN 1e-12
+#define OR_LAMBDA_MAX 1e8
+
+/* The match's value C (larger is better: F for maximum likelihood, minus
+ * Pearson's chi^2 for least squares) at p over the sensors in act, with the
+ * energy profiled (E = S / H, eta floored as everywhere).  With g and J (not
+ * NULL) also, over the first d coordinates:
+ *   J = E sum_A (grad eta_i - eta_i grad H / H)(...)^T / eta_i, the Fisher
+ *       information of the position with E profiled out (grad mu_i = E (grad
+ *       eta_i - eta_i grad H / H) for mu_i = E eta_i);
+ *   g = grad F = sum_A (s_i - E eta_i) grad eta_i / eta_i (maximum
+ *       likelihood), or -grad chi^2 / 2 = -(1/2) sum_A (1 - s_i^2 / mu_i^2)
+ *       grad mu_i (least squares, d chi^2 / d mu_i = 1 - s_i^2 / mu_i^2),
+ *   so that the scoring step solves J delta = g in both cases (chi^2's
+ *   Gauss-Newton curvature is 2 J). */
+static double or_min_value(const or_lrf *L, int crit, const int *act, const double *s, double S, const double p[3],
+                           int d, double g[3], double J[9])
+{
+    int n = L->n_sensors;
+    double H = 0.0, dH[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+        if (!act[i]) continue;
+        int ok;
+        double gi[3];
+        double eta = or_lrf_eta_grad(L, i, p[0], p[1], p[2], &ok, gi);
+        if (!(eta > OR_ETA_FLOOR)) { eta = OR_ETA_FLOOR; gi[0] = gi[1] = gi[2] = 0.0; }
+        H += eta;
+        for (int k = 0; k < 3; ++k) dH[k] += gi[k];
+    }
+    double E = S / H, C = 0.0;
+    if (g) {
+        for (int k = 0; k < 3; ++k) g[k] = 0.0;
+        for (int k = 0; k < 9; ++k) J[k] = 0.0;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!act[i]) continue;
+        int ok;
+        double gi[3];
+        double eta = or_lrf_eta_grad(L, i, p[0], p[1], p[2], &ok, gi);
+        if (!(eta > OR_ETA_FLOOR)) { eta = OR_ETA_FLOOR; gi[0] = gi[1] = gi[2] = 0.0; }
+        double mu = E * eta;
+        if (crit == 0) C += s[i] != 0.0 ? s[i] * log(eta) : 0.0;
+        else C -= (s[i] - mu) * (s[i] - mu) / mu;
+        if (!g) continue;
+        double dmu[3];
+        for (int k = 0; k < 3; ++k) dmu[k] = E * (gi[k] - eta * dH[k] / H);
+        for (int k = 0; k < d; ++k) {
+#if OR_MUTANT == 22
+            if (crit == 0) g[k] += s[i] * gi[k] / eta;
+#else
+            if (crit == 0) g[k] += (s[i] - mu) * gi[k] / eta;
+#endif
+#if OR_MUTANT == 23
+            else g[k] -= 0.5 * (1.0 + s[i] * s[i] / (mu * mu)) * dmu[k];
+#else
+            else g[k] -= 0.5 * (1.0 - s[i] * s[i] / (mu * mu)) * dmu[k];
+#endif
+            for (int l = 0; l < d; ++l) J[k * 3 + l] += dmu[k] * dmu[l] / mu;
+        }
+    }
+    if (crit == 0) C -= S * log(H);
+    return C;
+}
+
+/* Solve (J + lambda D) delta = g for d = 2 or 3, D = diag(J) with each entry
+ * floored at 1e-12 of the largest; Cramer's rule.  Returns 0 when the system
+ * is singular. */
+static int or_min_solve(const double J[9], double lambda, const double g[3], int d, double delta[3])
+{
+    double dmax = 0.0;
+    for (int k = 0; k < d; ++k) dmax = J[k * 4] > dmax ? J[k * 4] : dmax;
+    if (!(dmax > 0.0)) return 0;
+    double A[9];
+    for (int k = 0; k < 9; ++k) A[k] = J[k];
+    for (int k = 0; k < d; ++k) {
+        double dk = J[k * 4] > 1e-12 * dmax ? J[k * 4] : 1e-12 * dmax;
+        A[k * 4] += lambda * dk;
+    }
+    delta[0] = delta[1] = delta[2] = 0.0;
+    if (d == 2) {
+        double det = A[0] * A[4] - A[1] * A[3];
+        if (!(fabs(det) > 0.0)) return 0;
+        delta[0] = (g[0] * A[4] - A[1] * g[1]) / det;
+        delta[1] = (A[0] * g[1] - g[0] * A[3]) / det;
+        return 1;
+    }
+    double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (!(fabs(det) > 0.0)) return 0;
+    for (int c = 0; c < 3; ++c) {
+        double M[9];
+        for (int k = 0; k < 9; ++k) M[k] = A[k];
+        for (int r = 0; r < 3; ++r) M[r * 3 + c] = g[r];
+        delta[c] = (M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                    M[2] * (M[3] * M[7] - M[4] * M[6])) / det;
+    }
+    return 1;
+}
+
+/* A trial position moved onto the domain's box: x and y into the XY box
+ * (XY, XYZ, composite, sliced), z into the z range (XYZ, sliced, axial+z). */
+static void or_min_clamp(const or_lrf *L, double q[3])
+{
+    if (or_has_box(L->type)) {
+        q[0] = q[0] < L->lo[0] ? L->lo[0] : (q[0] > L->hi[0] ? L->hi[0] : q[0]);
+        q[1] = q[1] < L->lo[1] ? L->lo[1] : (q[1] > L->hi[1] ? L->hi[1] : q[1]);
+    }
+    int kz = L->type == OR_AXIAL_Z ? 1 : 2;
+    if (or_is_3d(L->type)) q[2] = q[2] < L->lo[kz] ? L->lo[kz] : (q[2] > L->hi[kz] ? L->hi[kz] : q[2]);
+}
+
+/* The minimisation of one event from p (already inside the domain):
+ *   each trial solves (J + lambda D) delta = g at p and moves to q = p +
+ *   delta moved onto the domain's box (or_min_clamp).  q is accepted when
+ *   every LRF in the match is defined there and the match improves: when
+ *   |C(q) - C(p)| > tau = 2^-18 S (beyond a bound on the single-precision
+ *   rounding of the difference, used by both implementations) by its sign,
+ *   else by the sign of (g(p) + g(q)) . (q - p), the trapezoid rule for the
+ *   change along the step (exact for a quadratic match, and computed from
+ *   gradients, which keep their precision near the optimum).  An accepted
+ *   trial sets lambda = max(lambda / 10, 1e-12) and ends the minimisation
+ *   when |q - p| < tol; a rejected one multiplies lambda by 10 and ends it
+ *   above 1e8.  At most max_iter trials.
+ * Returns the trials used, negative when max_iter ran out first. */
+static int or_min_run(const or_lrf *L, int crit, const or_min_params *M, const int *act, const double *s, double S,
+                      double p[3])
+{
+    int d = or_is_3d(L->type) && M->fit_z ? 3 : 2;
+    double tau = ldexp(S, -18);
+    double lambda = M->lambda0, g[3], J[9];
+    double C = or_min_value(L, crit, act, s, S, p, d, g, J);
+    for (int it = 1; it <= M->max_iter; ++it) {
+        double delta[3] = {0.0, 0.0, 0.0};
+        int okd = or_min_solve(J, lambda, g, d, delta);
+        double q[3] = {p[0] + delta[0], p[1] + delta[1], p[2] + delta[2]};
+        or_min_clamp(L, q);
+        int acc = okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && or_valid_act(L, act, q[0], q[1], q[2]);
+        double gq[3], Jq[9], Cq = 0.0;
+        if (acc) {
+            Cq = or_min_value(L, crit, act, s, S, q, d, gq, Jq);
+            double dC = Cq - C;
+            if (fabs(dC) > tau) {
+                acc = dC > 0.0;
+            } else {
+                double t = 0.0;
+                for (int k = 0; k < 3; ++k) t += (g[k] + gq[k]) * (q[k] - p[k]);
+#if OR_MUTANT == 24
+                acc = 1;
+#else
+                acc = t >= 0.0;
+#endif
+            }
+        }
+        if (acc) {
+            double step = sqrt((q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) +
+                               (q[2] - p[2]) * (q[2] - p[2]));
+            for (int k = 0; k < 3; ++k) {
+                p[k] = q[k];
+                g[k] = gq[k];
+            }
+            for (int k = 0; k < 9; ++k) J[k] = Jq[k];
+            C = Cq;
+            lambda = lambda * 0.1 > OR_LAMBDA_MIN ? lambda * 0.1 : OR_LAMBDA_MIN;
+            if (step < M->tol) return it;
+        } else {
+            lambda *= 10.0;
+            if (lambda > OR_LAMBDA_MAX) return it;
+        }
+    }
+    return -M->max_iter;
+}
+
+/* Minimisation of n_e events: the start and the sensors in the match as
+ * for the search variants (start_xyz, when not NULL, gives the start of
+ * every event instead), then or_min_run; E = S / H and the full Poisson
+ * logL over the match at the result; n_iter: the trials of or_min_run. */
+void or_minimize(const or_lrf *L, const or_cgs_params *P, const or_variant *V, const or_min_params *M,
+                 const double *gain, long n_e, const double *sig, const double *start_xyz, double *xyz, double *E,
+                 double *logL, int *status, int *n_iter)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long e = 0; e < n_e; ++e) {
+        const double *s = sig + e * L->n_sensors;
+        int *act = (int *)malloc(sizeof(int) * (size_t)L->n_sensors);
+        double p[3], S;
+        int st = or_variant_start(L, P, V, gain, s, start_xyz ? start_xyz + 3 * e : NULL, &p[0], &p[1], &p[2], &S,
+                                  act);
+        status[e] = st;
+        n_iter[e] = 0;
+        if (st != OR_EVT_OK) {
+            or_set_nan(&xyz[3 * e], &E[e], &logL[e]);
+            free(act);
+            continue;
+        }
+        n_iter[e] = or_min_run(L, V->criterion, M, act, s, S, p);
+        xyz[3 * e] = p[0];
+        xyz[3 * e + 1] = p[1];
+        xyz[3 * e + 2] = p[2];
+        or_variant_energy_logl(L, act, s, S, p[0], p[1], p[2], &E[e], &logL[e]);
+        free(act);
+    }
 }
 
 /* Exhaustive search: the best node of a regular nx x ny grid over

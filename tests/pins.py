@@ -957,3 +957,164 @@ ALL_PINS = [
     pin_variant_defaults_and_passive, pin_variant_start_and_cuts, pin_least_squares,
     pin_lrf_schemes_eval, pin_lrf_schemes_fit, pin_lrf_schemes_search,
 ]
+
+
+# --------------------------------------------------------------------------
+# Continuous minimisation (Sec. 5.1.2.1)
+# --------------------------------------------------------------------------
+
+
+def _all_type_lrfs(mutant=0, seed=6):
+    """One LRF set of each type: radial (per sensor, with gains), XY, XYZ,
+    axial+z and sliced (smooth responses sampled on the knot grids, random
+    factors) on a 3 x 3 array of pitch 8 mm, and the composite set of the
+    scheme pins (2 x 2 array)."""
+    sxy2, comp, az, sl = _scheme_lrfs(mutant)
+    sxy = synth.square_array(3, 8.0)
+    rng = np.random.default_rng(seed)
+    prof = 0.04 / (1 + (np.linspace(-5.0, 40.0, 10) / 20.0) ** 2) ** 1.5
+    rad = oracle.Lrf(oracle.RADIAL, sxy, (7, 0, 0), (0.0, 0.0, 0.0), (35.0, 0.0, 0.0),
+                     prof[None, :] * rng.uniform(0.95, 1.05, (9, 10)), gain=rng.uniform(0.9, 1.1, 9))
+    kx = np.linspace(-12.0 - 6.0, 12.0 + 6.0, 9)
+    X, Y = np.meshgrid(kx, kx)
+
+    def bump(w):
+        return np.stack([0.04 / (1 + ((X - sx) ** 2 + (Y - sy) ** 2) / w ** 2) ** 1.5 for sx, sy in sxy]).reshape(9, -1)
+
+    xy = oracle.Lrf(oracle.XY, sxy, (6, 6, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 0.0),
+                    bump(20.0) * rng.uniform(0.95, 1.05, (9, 81)))
+    # XYZ: the bump widens with z (a z that only scaled every sensor alike
+    # would be confounded with the energy)
+    kz = np.linspace(-5.0, 25.0, 7)
+    cxyz = np.stack([bump(15.0 + z) for z in kz], 1)  # [9][z][y*x]
+    xyz = oracle.Lrf(oracle.XYZ, sxy, (6, 6, 4), (-12.0, -12.0, 0.0), (12.0, 12.0, 20.0),
+                     cxyz.reshape(9, -1) * rng.uniform(0.95, 1.05, (9, 7 * 81)))
+    # axial+z: the closed-form 3D response on the (r, z) grid; sliced: the
+    # widening bump on the planes z = 0, 10, 20
+    rz = synth.grid_samples((6, 5), (0.0, 0.0), (30.0, 20.0), 4)
+    c1, _, _ = oracle.lrf_fit((6, 5), (0.0, 0.0), (30.0, 20.0), rz, synth.eta_3d(rz[:, 0], rz[:, 1], r0=15.0),
+                              mutant=mutant)
+    az3 = oracle.Lrf(oracle.AXIAL_Z, sxy, (6, 5, 0), (0.0, 0.0, 0.0), (30.0, 20.0, 0.0),
+                     c1 * rng.uniform(0.95, 1.05, (9, 1)))
+    csl = np.concatenate([bump(15.0 + z) for z in (0.0, 10.0, 20.0)], 1) * rng.uniform(0.95, 1.05, (9, 3 * 81))
+    sl3 = oracle.Lrf(oracle.SLICED, sxy, (6, 6, 0), (-12.0, -12.0, 0.0), (12.0, 12.0, 20.0), csl, n_planes=3)
+    return sxy, {"radial": rad, "xy": xy, "xyz": xyz, "composite": comp, "axial_z": az3, "sliced": sl3}
+
+
+def pin_lrf_grad(mutant=0):
+    """The analytic gradient of every LRF type equals central differences of
+    the LRF values (h = 1e-5 mm) at interior points away from the sliced
+    planes (where d/dz jumps) and from the sensors (where an axial LRF's
+    direction is undefined)."""
+    sxy, Ls = _all_type_lrfs(mutant)
+    rng = np.random.default_rng(12)
+    n = 60
+    p = np.stack([rng.uniform(-10.0, 10.0, n), rng.uniform(-10.0, 10.0, n), rng.uniform(1.0, 19.0, n)], 1)
+    p = p[np.abs(p[:, 2] - 10.0) > 0.5]
+    h = 1e-5
+    for name, L in Ls.items():
+        d = 3 if L.type in (oracle.XYZ, oracle.AXIAL_Z, oracle.SLICED) else 2
+        sx = L.sensor_xy
+        q = p[np.all(np.hypot(p[:, None, 0] - sx[None, :, 0], p[:, None, 1] - sx[None, :, 1]) > 0.5, axis=1), :d]
+        g = oracle.lrf_grad(L, q, mutant)
+        scale = np.abs(oracle.lrf_eval(L, q, mutant)).max()
+        for k in range(d):
+            e = np.zeros(d)
+            e[k] = h
+            fd = (oracle.lrf_eval(L, q + e, mutant) - oracle.lrf_eval(L, q - e, mutant)) / (2 * h)
+            err = np.abs(g[:, :, k] - fd).max()
+            assert err < 1e-7 * scale, (name, k, err, scale)
+        if d == 2:
+            assert np.all(g[:, :, 2] == 0.0)
+
+
+def _min_value(L, crit, s, p):
+    """The match at p from plain LRF values (all sensors): F = sum s ln eta -
+    S ln H, or minus Pearson's chi^2 with E = S / H."""
+    eta = oracle.lrf_eval(L, p[None, :L_dim(L)])[0]
+    S, H = s.sum(), eta.sum()
+    if crit == 0:
+        return float((s * np.log(eta)).sum() - S * np.log(H))
+    mu = S / H * eta
+    return float(-((s - mu) ** 2 / mu).sum())
+
+
+def L_dim(L):
+    return 3 if L.type in (oracle.XYZ, oracle.AXIAL_Z, oracle.SLICED) else 2
+
+
+def pin_minimize_noise_free(mutant=0):
+    """Noise-free signals s = E0 eta(p0) are matched exactly at p0 (Gibbs'
+    inequality for maximum likelihood, a zero chi^2 for least squares): the
+    minimisation from a start 1.8-2.7 mm away ends at p0 for every LRF type
+    and both criteria, and E = E0."""
+    sxy, Ls = _all_type_lrfs(mutant)
+    M = oracle.Minimize(max_iter=100, tol=1e-10, lambda0=1e-3)
+    for name, L in Ls.items():
+        d = L_dim(L)
+        p0 = np.array([[1.5, -2.0, 11.0]])[:, :d]
+        s = 3000.0 * oracle.lrf_eval(L, p0, mutant)
+        start = np.array([[0.0, -1.0, 13.0]]) if d == 3 else np.array([[0.0, -1.0, 0.0]])
+        for crit in (0, 1):
+            r = oracle.minimize(L, s, oracle.Variant(criterion=crit), M, start_xyz=start, mutant=mutant)
+            assert r["status"][0] == 0 and r["n_iter"][0] > 0, (name, crit, r["n_iter"])
+            err = np.abs(r["xyz"][0, :d] - p0[0]).max()
+            assert err < 1e-7, (name, crit, err, r["xyz"][0], r["n_iter"])
+            assert abs(r["E"][0] / 3000.0 - 1.0) < 1e-8, (name, crit, r["E"][0])
+
+
+def pin_minimize_stationary(mutant=0):
+    """On Poisson events the result is a local optimum of the match as
+    computed from plain LRF values: no probe 0.01 mm away along any axis
+    (inside the domain) is better, for the events that converged (at least
+    90 %; an optimum beyond the domain's edge is approached step by step;
+    sliced results on a plane, where the match has a kink, are left out),
+    and it is at least as good as the contracting grids' result it started
+    from (their last spacing is 0.0625 mm)."""
+    sxy, Ls = _all_type_lrfs(mutant)
+    rng = np.random.default_rng(21)
+    M = oracle.Minimize(max_iter=200, tol=1e-6)
+    for name in ("xy", "radial", "xyz", "sliced"):
+        L = Ls[name]
+        d = L_dim(L)
+        n = 12
+        p0 = np.stack([rng.uniform(-6, 6, n), rng.uniform(-6, 6, n), rng.uniform(6, 14, n)], 1)[:, :d]
+        sig = rng.poisson(5000.0 * oracle.lrf_eval(L, p0, mutant)).astype(np.float64)
+        P = oracle.CgsParams(n_xy=9, iters=7, step_xy=4.0, n_z=5 if d == 3 else 1, step_z=4.0 if d == 3 else 0.0,
+                             z0=10.0)
+        cg = oracle.cgs(L, P, sig, mutant=mutant)
+        for crit in (0, 1):
+            start = cg["xyz"] if crit == 0 else None
+            r = oracle.minimize(L, sig, oracle.Variant(criterion=crit), M, z0=10.0, start_xyz=start, mutant=mutant)
+            assert np.all(r["status"] == 0)
+            assert (r["n_iter"] > 0).mean() >= 0.9, (name, crit, r["n_iter"])
+            for e in np.nonzero(r["n_iter"] > 0)[0]:
+                p = r["xyz"][e]
+                if name == "sliced" and np.abs(p[2] - np.array([0.0, 10.0, 20.0])).min() < 0.05:
+                    continue  # on a plane the match has a kink along z: a gradient method stops at its edge
+                C0 = _min_value(L, crit, sig[e], p)
+                for k in range(d):
+                    for sgn in (-1.0, 1.0):
+                        q = p.copy()
+                        q[k] += sgn * 0.01
+                        Cq = _min_value(L, crit, sig[e], q)  # NaN outside the domain: no probe
+                        assert not (Cq > C0 + 1e-9), (name, crit, e, k, Cq - C0)
+                if crit == 0:
+                    assert C0 >= _min_value(L, 0, sig[e], cg["xyz"][e]) - 1e-9, (name, e)
+
+
+def pin_minimize_status(mutant=0):
+    """Status as for the search variants (bad or zero signals, a start
+    outside the domain) with NaN outputs; n_iter < 0 when max_iter runs out."""
+    sxy, Ls = _all_type_lrfs(mutant)
+    L = Ls["xy"]
+    s = 3000.0 * oracle.lrf_eval(L, np.array([[1.0, 1.0], [0.0, 0.0], [0.0, 0.0], [2.0, 2.0]]), mutant)
+    s[1] = 0.0
+    s[2, 1] = -1.0
+    start = np.array([[-5.0, -5.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [40.0, 0.0, 0.0]])
+    r = oracle.minimize(L, s, oracle.Variant(), oracle.Minimize(max_iter=1), start_xyz=start, mutant=mutant)
+    assert list(r["status"]) == [0, 2, 3, 4]
+    assert r["n_iter"][0] == -1 and np.all(np.isnan(r["xyz"][1:]))
+
+
+ALL_PINS += [pin_lrf_grad, pin_minimize_noise_free, pin_minimize_stationary, pin_minimize_status]

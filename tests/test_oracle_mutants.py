@@ -26,6 +26,10 @@ MUTANTS = {
     18: "distance cut measured from the origin instead of the start",
     19: "sliced LRF interpolation weights swapped between the planes",
     20: "two-dimensional spline coefficients indexed with the axes transposed",
+    21: "B-spline derivative with the two lower-degree terms added",
+    22: "maximum-likelihood gradient without the -E eta term",
+    23: "least-squares gradient weight 1 + s^2/mu^2 instead of 1 - s^2/mu^2",
+    24: "minimisation accepting every step inside the rounding band",
 }
 
 
