@@ -1284,18 +1284,26 @@ static double or_min_value(const or_lrf *L, int crit, const int *act, const doub
 }
 
 /* Solve (J + lambda D) delta = g for d = 2 or 3, D = diag(J) with each entry
- * floored at 1e-12 of the largest; Cramer's rule.  Returns 0 when the system
- * is singular. */
-static int or_min_solve(const double J[9], double lambda, const double g[3], int d, double delta[3])
+ * floored at 1e-12 of the largest; Cramer's rule.  Coordinates in the mask
+ * `fixed` (bit k) are held: their rows and columns become those of the
+ * identity and their right-hand side 0, so delta_k = 0 and the others solve
+ * the reduced system.  Returns 0 when the system is singular. */
+static int or_min_solve(const double J[9], double lambda, const double g_in[3], int d, int fixed, double delta[3])
 {
     double dmax = 0.0;
     for (int k = 0; k < d; ++k) dmax = J[k * 4] > dmax ? J[k * 4] : dmax;
     if (!(dmax > 0.0)) return 0;
-    double A[9];
+    double A[9], g[3] = {g_in[0], g_in[1], g_in[2]};
     for (int k = 0; k < 9; ++k) A[k] = J[k];
     for (int k = 0; k < d; ++k) {
         double dk = J[k * 4] > 1e-12 * dmax ? J[k * 4] : 1e-12 * dmax;
         A[k * 4] += lambda * dk;
+    }
+    for (int k = 0; k < d; ++k) {
+        if (!(fixed >> k & 1)) continue;
+        for (int l = 0; l < 3; ++l) A[k * 3 + l] = A[l * 3 + k] = 0.0;
+        A[k * 4] = 1.0;
+        g[k] = 0.0;
     }
     delta[0] = delta[1] = delta[2] = 0.0;
     if (d == 2) {
@@ -1318,29 +1326,63 @@ static int or_min_solve(const double J[9], double lambda, const double g[3], int
     return 1;
 }
 
-/* A trial position moved onto the domain's box: x and y into the XY box
- * (XY, XYZ, composite, sliced), z into the z range (XYZ, sliced, axial+z). */
+/* The box bounds of coordinate k (x and y: the XY box of XY, XYZ,
+ * composite and sliced LRFs; z: the z range of XYZ, sliced and axial+z
+ * ones); 0 when the coordinate has none. */
+static int or_min_bounds(const or_lrf *L, int k, double *lo, double *hi)
+{
+    if (k < 2) {
+        if (!or_has_box(L->type)) return 0;
+        *lo = L->lo[k];
+        *hi = L->hi[k];
+        return 1;
+    }
+    if (!or_is_3d(L->type)) return 0;
+    int kz = L->type == OR_AXIAL_Z ? 1 : 2;
+    *lo = L->lo[kz];
+    *hi = L->hi[kz];
+    return 1;
+}
+
+/* A trial position moved onto the domain's box. */
 static void or_min_clamp(const or_lrf *L, double q[3])
 {
-    if (or_has_box(L->type)) {
-        q[0] = q[0] < L->lo[0] ? L->lo[0] : (q[0] > L->hi[0] ? L->hi[0] : q[0]);
-        q[1] = q[1] < L->lo[1] ? L->lo[1] : (q[1] > L->hi[1] ? L->hi[1] : q[1]);
+    for (int k = 0; k < 3; ++k) {
+        double lo, hi;
+        if (or_min_bounds(L, k, &lo, &hi)) q[k] = q[k] < lo ? lo : (q[k] > hi ? hi : q[k]);
     }
-    int kz = L->type == OR_AXIAL_Z ? 1 : 2;
-    if (or_is_3d(L->type)) q[2] = q[2] < L->lo[kz] ? L->lo[kz] : (q[2] > L->hi[kz] ? L->hi[kz] : q[2]);
+}
+
+/* The coordinates (bit k) that lie on a bound of the box while the step
+ * delta points out of it: the active constraints, held in the next solve. */
+static int or_min_active(const or_lrf *L, const double p[3], const double delta[3], int d)
+{
+    int fixed = 0;
+    for (int k = 0; k < d; ++k) {
+        double lo, hi;
+        if (!or_min_bounds(L, k, &lo, &hi)) continue;
+        if ((p[k] == lo && delta[k] < 0.0) || (p[k] == hi && delta[k] > 0.0)) fixed |= 1 << k;
+    }
+    return fixed;
 }
 
 /* The minimisation of one event from p (already inside the domain):
- *   each trial solves (J + lambda D) delta = g at p and moves to q = p +
- *   delta moved onto the domain's box (or_min_clamp).  q is accepted when
+ *   each trial solves (J + lambda D) delta = g at p, again with the
+ *   coordinates held that lie on a bound of the domain's box while delta
+ *   points out of it (or_min_active; a projected step), and moves to q = p +
+ *   delta moved onto the box (or_min_clamp).  q is accepted when
  *   every LRF in the match is defined there and the match improves: when
  *   |C(q) - C(p)| > tau = 2^-18 S (beyond a bound on the single-precision
  *   rounding of the difference, used by both implementations) by its sign,
  *   else by the sign of (g(p) + g(q)) . (q - p), the trapezoid rule for the
  *   change along the step (exact for a quadratic match, and computed from
  *   gradients, which keep their precision near the optimum).  An accepted
- *   trial sets lambda = max(lambda / 10, 1e-12) and ends the minimisation
- *   when |q - p| < tol; a rejected one multiplies lambda by 10 and ends it
+ *   trial sets lambda = max(lambda / 10, 1e-12), or, when the slope along
+ *   the step changed sign (a0 = g(p) . (q - p) > 0 > a1 = g(q) . (q - p):
+ *   the step overshot the optimum along its line, which a quadratic places
+ *   at t* = a0 / (a0 - a1) of it), the larger 1 / t* - 1 (the damping that
+ *   shortens a step by t* when D = J), and ends the minimisation when
+ *   |q - p| < tol; a rejected trial multiplies lambda by 10 and ends it
  *   above 1e8.  At most max_iter trials.
  * Returns the trials used, negative when max_iter ran out first. */
 static int or_min_run(const or_lrf *L, int crit, const or_min_params *M, const int *act, const double *s, double S,
@@ -1352,7 +1394,9 @@ static int or_min_run(const or_lrf *L, int crit, const or_min_params *M, const i
     double C = or_min_value(L, crit, act, s, S, p, d, g, J);
     for (int it = 1; it <= M->max_iter; ++it) {
         double delta[3] = {0.0, 0.0, 0.0};
-        int okd = or_min_solve(J, lambda, g, d, delta);
+        int okd = or_min_solve(J, lambda, g, d, 0, delta);
+        int fixed = okd ? or_min_active(L, p, delta, d) : 0;
+        if (fixed) okd = or_min_solve(J, lambda, g, d, fixed, delta);
         double q[3] = {p[0] + delta[0], p[1] + delta[1], p[2] + delta[2]};
         or_min_clamp(L, q);
         int acc = okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && or_valid_act(L, act, q[0], q[1], q[2]);
@@ -1375,13 +1419,22 @@ static int or_min_run(const or_lrf *L, int crit, const or_min_params *M, const i
         if (acc) {
             double step = sqrt((q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) +
                                (q[2] - p[2]) * (q[2] - p[2]));
+            double a0 = 0.0, a1 = 0.0, next = lambda * 0.1 > OR_LAMBDA_MIN ? lambda * 0.1 : OR_LAMBDA_MIN;
+            for (int k = 0; k < 3; ++k) {
+                a0 += g[k] * (q[k] - p[k]);
+                a1 += gq[k] * (q[k] - p[k]);
+            }
+            if (a0 > 0.0 && a1 < 0.0) {
+                double ts = a0 / (a0 - a1);
+                if (1.0 / ts - 1.0 > next) next = 1.0 / ts - 1.0;
+            }
             for (int k = 0; k < 3; ++k) {
                 p[k] = q[k];
                 g[k] = gq[k];
             }
             for (int k = 0; k < 9; ++k) J[k] = Jq[k];
             C = Cq;
-            lambda = lambda * 0.1 > OR_LAMBDA_MIN ? lambda * 0.1 : OR_LAMBDA_MIN;
+            lambda = next;
             if (step < M->tol) return it;
         } else {
             lambda *= 10.0;
