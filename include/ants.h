@@ -83,7 +83,8 @@ typedef enum {
     ANTS_CGS_PLAIN = 0, /* contracting grids, FP32, all sensors (Sec. 5.1.2.2) */
     ANTS_GEMM_TOPK = 1, /* global-grid tensor-core scores, top-K, local contracting grids */
     ANTS_MLP_SEEDED = 2, /* network proposal + local contracting grids + plain fallback */
-    ANTS_CGS_VARIANT = 3 /* contracting grids with another criterion, start or sensor selection */
+    ANTS_CGS_VARIANT = 3, /* contracting grids with another criterion, start or sensor selection */
+    ANTS_MINIMIZE = 4     /* continuous minimisation of the match (Sec. 5.1.2.1) */
 } ants_method;
 
 /* Match criterion of ANTS_CGS_VARIANT (Sec. 5.1.2). */
@@ -206,6 +207,41 @@ typedef struct {
     float max_distance;
     const unsigned char *passive_host; /* nullable, [n_sensors], read during the call */
 } ants_cgs_variant_params;
+
+/* Parameters of ANTS_MINIMIZE (Sec. 5.1.2.1: the match is minimised over
+ * the two or three coordinates by a gradient method, from the centroid or the
+ * strongest sensor; the paper uses Minuit2's Migrad): damped Fisher scoring
+ * (Levenberg-Marquardt) with the energy profiled out, E = S / H at every
+ * position.  The criterion, the start and the sensors in the match are those
+ * of ants_cgs_variant_params; start_xyz_dev, when given, starts every event
+ * instead (e.g. from a contracting-grid result: a continuous refine).
+ * Each trial at p solves (J + lambda diag J) delta = g, with J = E sum_A
+ * (grad eta_i - eta_i grad H / H)(...)^T / eta_i the Fisher information of
+ * the position and g = grad F (maximum likelihood) or -grad chi^2 / 2 (least
+ * squares), over x, y and, for a 3D LRF with fit_z, z; q = p + delta is
+ * moved onto the domain's box (XY box, z range) and accepted when every LRF
+ * in the match is defined there and the match improves: by the sign of the
+ * change when it exceeds tau = 2^-18 S, else by the sign of (g(p) + g(q)) .
+ * (q - p).  An accepted trial divides lambda by 10 (floor 1e-12) and ends
+ * the minimisation when |q - p| < tol; a rejected one multiplies lambda by
+ * 10 and ends it above 1e8.  At most max_iter trials.
+ * Outputs as for the other methods; trace_dev, when given, is [n_events][1]
+ * int16: the trials used, negative when max_iter ran out first (0 for
+ * events that were not minimised).  Status as for ANTS_CGS_VARIANT (with a
+ * given start: OUT_OF_DOMAIN when an LRF in the match is undefined there).
+ * Every LRF type; at most 1024 sensors. */
+typedef struct {
+    int criterion;           /* ANTS_CRIT_ML or ANTS_CRIT_LS */
+    int start;               /* ANTS_START_COG or ANTS_START_MAX_SENSOR (no start_xyz_dev) */
+    float z0;                /* start z of a 3D LRF (no start_xyz_dev) */
+    int fit_z;               /* 3D LRFs: 1 = z is fitted, 0 = z stays at the start */
+    int max_iter;            /* >= 1 trials */
+    float tol;               /* > 0, mm */
+    float lambda0;           /* >= 0, initial damping (e.g. 1e-3) */
+    float min_signal;        /* as ants_cgs_variant_params */
+    float max_distance;
+    const unsigned char *passive_host; /* nullable, [n_sensors], read during the call */
+} ants_minimize_params;
 
 /* Parameters of ANTS_MLP_SEEDED: the network's (x, y), clamped into the LRF's
  * XY box, starts the `refine` search; events whose Poisson deviance
@@ -428,7 +464,9 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf);
  *     ANTS_GEMM_TOPK with params = const ants_gemm_params* (no start_xyz_dev,
  *     no trace_dev), or ANTS_MLP_SEEDED with params = const
  *     ants_mlp_seeded_params* (no start_xyz_dev; trace_dev then records the
- *     refine grids).
+ *     refine grids), ANTS_CGS_VARIANT with params = const
+ *     ants_cgs_variant_params* (no start_xyz_dev), or ANTS_MINIMIZE with
+ *     params = const ants_minimize_params* (trace_dev [n_events][1]).
  *   signals_dev: [n_events][n_sensors] row-major, element type signal_dtype
  *     (ANTS_F32, or ANTS_F16: widened to FP32 in library-owned device
  *     chunks of up to 2^20 events, so the results equal those of the FP32
@@ -456,7 +494,8 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
 
 /* The same reconstruction with HOST buffers (signals_host [n_events]
  * [n_sensors], outputs xyz_host [n_events][3], E_host, logL_host,
- * status_host; nullable start_xyz_host, plain search only), any method.
+ * status_host; nullable start_xyz_host, plain search and minimisation only),
+ * any method.
  * The library streams the events through device buffers owned by the
  * context in chunks; for the plain search it overlaps the host-to-device
  * copy, the search and the device-to-host copy on two internal streams, for

@@ -31,6 +31,7 @@ ANTS_CGS_PLAIN = 0
 ANTS_GEMM_TOPK = 1
 ANTS_MLP_SEEDED = 2
 ANTS_CGS_VARIANT = 3
+ANTS_MINIMIZE = 4
 ANTS_CRIT_ML, ANTS_CRIT_LS = 0, 1
 ANTS_START_COG, ANTS_START_MAX_SENSOR = 0, 1
 ANTS_F32 = 0
@@ -123,6 +124,22 @@ class VariantParams(C.Structure):
     def __init__(self, grid, criterion=0, start=0, min_signal=0.0, max_distance=0.0, passive=None):
         self._passive = None if passive is None else np.ascontiguousarray(np.asarray(passive, dtype=np.uint8))
         super().__init__(grid, int(criterion), int(start), float(min_signal), float(max_distance),
+                         None if self._passive is None else self._passive.ctypes.data)
+
+
+class MinimizeParams(C.Structure):
+    """ants_minimize_params (Sec. 5.1.2.1): continuous minimisation of the
+    match (damped Fisher scoring, E profiled) from the centroid, the strongest
+    sensor or given starts."""
+    _fields_ = [("criterion", C.c_int), ("start", C.c_int), ("z0", C.c_float), ("fit_z", C.c_int),
+                ("max_iter", C.c_int), ("tol", C.c_float), ("lambda0", C.c_float), ("min_signal", C.c_float),
+                ("max_distance", C.c_float), ("passive_host", C.c_void_p)]
+
+    def __init__(self, criterion=0, start=0, z0=0.0, fit_z=1, max_iter=30, tol=1e-3, lambda0=1e-3, min_signal=0.0,
+                 max_distance=0.0, passive=None):
+        self._passive = None if passive is None else np.ascontiguousarray(np.asarray(passive, dtype=np.uint8))
+        super().__init__(int(criterion), int(start), float(z0), int(fit_z), int(max_iter), float(tol),
+                         float(lambda0), float(min_signal), float(max_distance),
                          None if self._passive is None else self._passive.ctypes.data)
 
 
@@ -833,7 +850,8 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
     logL = torch.empty(n, dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
     iters = (params.refine.iters if isinstance(params, (SeededParams, GemmParams))
-             else params.grid.iters if isinstance(params, VariantParams) else params.iters)
+             else params.grid.iters if isinstance(params, VariantParams)
+             else 1 if isinstance(params, MinimizeParams) else params.iters)
     trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
     dtype = ANTS_F16 if signals.dtype == torch.float16 else ANTS_F32

@@ -555,6 +555,7 @@ static int check_common(ants_ctx *ctx, const ants_lrf *lrf, int method, const vo
     if (method == ANTS_MLP_SEEDED) return check_seeded_params(lrf, (const ants_mlp_seeded_params *)params);
     if (method == ANTS_GEMM_TOPK) return check_gemm_params(lrf, (const ants_gemm_params *)params);
     if (method == ANTS_CGS_VARIANT) return check_variant_params(lrf, (const ants_cgs_variant_params *)params);
+    if (method == ANTS_MINIMIZE) return check_minimize_params(lrf, (const ants_minimize_params *)params);
     if (method != ANTS_CGS_PLAIN) return fail(ANTS_E_UNIMPLEMENTED, "ants_reconstruct: method %d", method);
     return check_cgs_params(lrf, (const ants_cgs_params *)params);
 }
@@ -572,6 +573,9 @@ static int reconstruct_f32(ants_ctx *ctx, const ants_lrf *lrf, int method, const
     if (method == ANTS_CGS_VARIANT)
         return reconstruct_variant(ctx, lrf, *(const ants_cgs_variant_params *)params, sig, n_events, nullptr,
                                    xyz_dev, E_dev, logL_dev, status_dev, trace_dev, stream);
+    if (method == ANTS_MINIMIZE)
+        return reconstruct_minimize(ctx, lrf, *(const ants_minimize_params *)params, sig, n_events, start_xyz_dev,
+                                    xyz_dev, E_dev, logL_dev, status_dev, trace_dev, stream);
     return launch_cgs_plain(ctx, lrf, *(const ants_cgs_params *)params, sig, n_events, start_xyz_dev, xyz_dev, E_dev,
                             logL_dev, status_dev, trace_dev, stream);
 }
@@ -602,6 +606,7 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
     const int iters = method == ANTS_CGS_PLAIN     ? ((const ants_cgs_params *)params)->iters
                       : method == ANTS_MLP_SEEDED  ? ((const ants_mlp_seeded_params *)params)->refine.iters
                       : method == ANTS_CGS_VARIANT ? ((const ants_cgs_variant_params *)params)->grid.iters
+                      : method == ANTS_MINIMIZE    ? 1
                                                    : 0;
     const long chunk = n_events < (1L << 20) ? n_events : (1L << 20);
     float *wide = (float *)ctx_scratch(ctx, 7, (size_t)chunk * n_sensors * sizeof(float));
@@ -630,12 +635,12 @@ ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int metho
     if (n_events == 0) return ANTS_OK;
     if (!signals_host || !xyz_host || !E_host || !logL_host || !status_host)
         return fail(ANTS_E_ARG, "ants_reconstruct_host: NULL signal or output buffer");
-    if (method != ANTS_CGS_PLAIN && start_xyz_host)
-        return fail(ANTS_E_ARG, "ants_reconstruct_host: the learned and precision forms take no start");
+    if (method != ANTS_CGS_PLAIN && method != ANTS_MINIMIZE && start_xyz_host)
+        return fail(ANTS_E_ARG, "ants_reconstruct_host: only the plain search and the minimisation take a start");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     // the plain search overlaps chunks on two streams; the two forms use the
     // context's scratch buffers, so their chunks run one after the other
-    const bool overlap = method == ANTS_CGS_PLAIN || method == ANTS_CGS_VARIANT;  // no shared scratch
+    const bool overlap = method == ANTS_CGS_PLAIN || method == ANTS_CGS_VARIANT || method == ANTS_MINIMIZE;
     // chunk large enough to fill the GPU, small enough to pipeline
     const long chunk = 1L << 17;
     if (ctx->host_cap_events < (size_t)chunk || ctx->host_cap_sensors < n_sensors) {

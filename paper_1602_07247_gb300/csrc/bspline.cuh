@@ -190,6 +190,160 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
     }
 }
 
+// derivatives of the four weights along the local parameter t
+__device__ __forceinline__ void bs_dweights(float t, float d[4])
+{
+    const float u = 1.0f - t;
+    d[0] = -0.5f * u * u;
+    d[1] = 0.5f * t * fmaf(3.0f, t, -4.0f);
+    d[2] = 0.5f * fmaf(t, fmaf(-3.0f, t, 2.0f), 1.0f);
+    d[3] = 0.5f * t * t;
+}
+
+// spline2 with its partial derivatives along u and v
+__device__ __forceinline__ float spline2_grad(const float *c, float u, float lo0, float inv_h0, int n0, float v,
+                                              float lo1, float inv_h1, int n1, float &du, float &dv)
+{
+    float tu, tv, wu[4], wv[4], du4[4], dv4[4];
+    const int ju = bs_span(u, lo0, inv_h0, n0, tu);
+    const int jv = bs_span(v, lo1, inv_h1, n1, tv);
+    bs_weights(tu, wu);
+    bs_weights(tv, wv);
+    bs_dweights(tu, du4);
+    bs_dweights(tv, dv4);
+    const int st = n0 + 3;
+    float f = 0.0f, fu = 0.0f, fv = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float *row = c + (jv + b) * st + ju;
+        float fr = 0.0f, fru = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            fr = fmaf(row[a], wu[a], fr);
+            fru = fmaf(row[a], du4[a], fru);
+        }
+        f = fmaf(fr, wv[b], f);
+        fu = fmaf(fru, wv[b], fu);
+        fv = fmaf(fr, dv4[b], fv);
+    }
+    du = fu * inv_h0;
+    dv = fv * inv_h1;
+    return f;
+}
+
+// an axial profile and its derivative along r (power-basis cubic of the span)
+__device__ __forceinline__ float radial_profile_grad(const float4 *poly, float inv_h, int n, float r, float &dr)
+{
+    const float u = r * inv_h;
+    const int j = min((int)u, n - 1);
+    const float t = u - (float)j;
+    const float4 p = __ldg(poly + j);
+    dr = fmaf(t, fmaf(3.0f * t, p.w, 2.0f * p.z), p.y) * inv_h;
+    return fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
+}
+
+// eta_i at one point and its gradient (gx, gy, gz) = (d/dx, d/dy, d/dz),
+// gz = 0 for 2D LRFs; an axial part's direction (dx, dy) / r is 0 at the
+// sensor itself; ok = false outside the domain
+template <int TYPE>
+__device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x, float y, float z, bool &ok, float &gx,
+                                                float &gy, float &gz)
+{
+    gx = gy = gz = 0.0f;
+    const float dx = x - L.sxy[2 * i], dy = y - L.sxy[2 * i + 1];
+    const float r2 = fmaf(dx, dx, dy * dy), rinv = rsqrtf(fmaxf(r2, 1e-30f)), r = r2 * rinv;
+    if (TYPE == ANTS_LRF_RADIAL) {
+        ok = r <= L.hi[0];
+        if (!ok) return 0.0f;
+        float dr;
+        const float g = __ldg(L.gain + i);
+        const float f = radial_profile_grad(radial_poly(L, i), L.inv_h[0], L.n_int[0], r, dr);
+        gx = g * dr * dx * rinv;
+        gy = g * dr * dy * rinv;
+        return g * f;
+    }
+    if (TYPE == ANTS_LRF_COMPOSITE) {
+        ok = r <= L.hi_r && in_box(L, x, y, z);
+        if (!ok) return 0.0f;
+        float dr, fx, fy;
+        const float fa = radial_profile_grad(L.rpoly + i * L.n_int_r, L.inv_h_r, L.n_int_r, r, dr);
+        const float *c = L.coef + (size_t)i * L.n_coef + (L.n_int_r + 3);
+        const float fxy = spline2_grad(c, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1], fx, fy);
+        gx = fmaf(dr * dx, rinv, fx);
+        gy = fmaf(dr * dy, rinv, fy);
+        return fa + fxy;
+    }
+    if (TYPE == ANTS_LRF_AXIAL_Z) {
+        ok = r <= L.hi[0] && z >= L.lo[1] && z <= L.hi[1];
+        if (!ok) return 0.0f;
+        float fr, fz;
+        const float f = spline2_grad(L.coef + (size_t)i * L.n_coef, r, 0.0f, L.inv_h[0], L.n_int[0], z, L.lo[1],
+                                     L.inv_h[1], L.n_int[1], fr, fz);
+        gx = fr * dx * rinv;
+        gy = fr * dy * rinv;
+        gz = fz;
+        return f;
+    }
+    if (TYPE == ANTS_LRF_SLICED) {
+        ok = in_box(L, x, y, z);
+        if (!ok) return 0.0f;
+        const float u = (z - L.lo[2]) * L.inv_h[2];
+        const int j = min(max((int)floorf(u), 0), L.n_planes - 2);
+        const float w = u - (float)j;
+        const float *c = L.coef + (size_t)i * L.n_coef + (size_t)j * L.n_coef_xy;
+        float f0x, f0y, f1x, f1y;
+        const float f0 = spline2_grad(c, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1], f0x, f0y);
+        const float f1 = spline2_grad(c + L.n_coef_xy, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1],
+                                      L.n_int[1], f1x, f1y);
+        gx = fmaf(w, f1x, (1.0f - w) * f0x);
+        gy = fmaf(w, f1y, (1.0f - w) * f0y);
+        gz = (f1 - f0) * L.inv_h[2];
+        return fmaf(w, f1, (1.0f - w) * f0);
+    }
+    ok = in_box(L, x, y, z);
+    if (!ok) return 0.0f;
+    float tx, ty, tz = 0.0f, wx[4], wy[4], wz[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+    float ddx[4], ddy[4], ddz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int jx = bs_span(x, L.lo[0], L.inv_h[0], L.n_int[0], tx);
+    const int jy = bs_span(y, L.lo[1], L.inv_h[1], L.n_int[1], ty);
+    int jz = 0, nz = 1;
+    bs_weights(tx, wx);
+    bs_weights(ty, wy);
+    bs_dweights(tx, ddx);
+    bs_dweights(ty, ddy);
+    if (TYPE == ANTS_LRF_XYZ) {
+        jz = bs_span(z, L.lo[2], L.inv_h[2], L.n_int[2], tz);
+        bs_weights(tz, wz);
+        bs_dweights(tz, ddz);
+        nz = 4;
+    }
+    const float *c = L.coef + (size_t)i * L.n_coef;
+    float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    for (int cz = 0; cz < nz; ++cz) {
+        float a0 = 0.0f, ax = 0.0f, ay = 0.0f;
+        for (int b = 0; b < 4; ++b) {
+            const float *row = c + (jz + cz) * L.stride_z + (jy + b) * L.stride_y + jx;
+            float fr = 0.0f, frx = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                fr = fmaf(row[a], wx[a], fr);
+                frx = fmaf(row[a], ddx[a], frx);
+            }
+            a0 = fmaf(fr, wy[b], a0);
+            ax = fmaf(frx, wy[b], ax);
+            ay = fmaf(fr, ddy[b], ay);
+        }
+        f = fmaf(a0, wz[cz], f);
+        fx = fmaf(ax, wz[cz], fx);
+        fy = fmaf(ay, wz[cz], fy);
+        fz = fmaf(a0, ddz[cz], fz);
+    }
+    gx = fx * L.inv_h[0];
+    gy = fy * L.inv_h[1];
+    gz = TYPE == ANTS_LRF_XYZ ? fz * L.inv_h[2] : 0.0f;
+    return f;
+}
+
 // every LRF of the sensors with s_act[i] != 0 (all sensors when s_act is
 // NULL) defined at the point: within reach of each sensor for the axial
 // parts, inside the XY box, inside the z range

@@ -177,6 +177,10 @@ int reconstruct_mlp_seeded(ants_ctx *ctx, const ants_lrf *lrf, const ants_mlp_se
                            cudaStream_t s);
 bool cgs_xy_supported(const ants_lrf *lrf, const ants_cgs_params &p);
 // search variants (variant.cu)
+int check_minimize_params(const ants_lrf *lrf, const ants_minimize_params *P);
+int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_minimize_params &P, const float *sig,
+                         long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                         int16_t *n_iter, cudaStream_t s);
 int check_variant_params(const ants_lrf *lrf, const ants_cgs_variant_params *P);
 // start (nullable): given starts [n_e][3] instead of the variant's own
 int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_variant_params &P, const float *sig,

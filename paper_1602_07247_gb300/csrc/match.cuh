@@ -1,0 +1,112 @@
+// The per-event set-up shared by the search variants and the continuous
+// minimisation: signals, status, start position and the sensors in the
+// match (Sec. 5.1.2: sensors below a signal threshold or farther than a
+// given distance from the start can be left out; Sec. 5.1.2.1 / 5.1.2.2: the
+// start is the centroid or the strongest sensor; Sec. 5.3: passive sensors
+// are ignored).  One warp per event.
+#pragma once
+
+#include "bspline.cuh"
+#include "internal.cuh"
+
+namespace ants {
+
+constexpr int kMaxMatchSensors = 1024;
+
+struct MatchArgs {
+    int start;                                  // ANTS_START_COG / ANTS_START_MAX_SENSOR
+    float min_signal, max_distance, z0;
+    double gain[kMaxMatchSensors];              // relative gains (start)
+    unsigned char passive[kMaxMatchSensors];    // 1 = passive
+};
+
+__device__ __forceinline__ float match_warp_sum(float v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double match_warp_sum_d(double v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Loads event e's signals into s_sig (0 for passive sensors), picks the start
+// (given: start_xyz, nullable), marks the sensors in the match in s_act (1 /
+// 0) and returns ANTS_EVT_OK with their signal sum S and the start, or the
+// event's failure status.  Comparisons that pick the start or a sensor are
+// made in FP64.
+template <int TYPE>
+__device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &m, const float *sig, long e,
+                                              const float *start_xyz, float *s_sig, float *s_act, int lane, float &S,
+                                              float &cx, float &cy, float &cz)
+{
+    const int n_s = L.n_s;
+    bool bad = false;
+    double tot = 0.0, W = 0.0, X = 0.0, Y = 0.0, bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n_s; i += 32) {
+        float s = sig[e * n_s + i];
+        if (m.passive[i]) s = 0.0f;
+        else if (!isfinite(s) || s < 0.0f) bad = true;
+        s_sig[i] = s;
+        const double w = (double)s / m.gain[i];
+        tot += (double)s;
+        W += w;
+        X += (double)L.sxy[2 * i] * w;
+        Y += (double)L.sxy[2 * i + 1] * w;
+        if (!m.passive[i] && w > bv) {  // lanes visit increasing i: the first maximum
+            bv = w;
+            bi = i;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad)) return ANTS_EVT_BAD_SIGNAL;
+    tot = match_warp_sum_d(tot);
+    if (!(tot > 0.0)) return ANTS_EVT_ZERO_SIGNAL;
+    cz = lrf_is_3d(TYPE) ? m.z0 : 0.0f;
+    if (start_xyz) {
+        cx = start_xyz[3 * e];
+        cy = start_xyz[3 * e + 1];
+        cz = start_xyz[3 * e + 2];
+    } else if (m.start == 1) {
+        for (int o = 16; o; o >>= 1) {  // the largest s/g, ties to the lowest index
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (v2 > bv || (v2 == bv && i2 < bi)) {
+                bv = v2;
+                bi = i2;
+            }
+        }
+        cx = L.sxy[2 * bi];
+        cy = L.sxy[2 * bi + 1];
+    } else {
+        W = match_warp_sum_d(W);
+        X = match_warp_sum_d(X);
+        Y = match_warp_sum_d(Y);
+        cx = (float)(X / W);
+        cy = (float)(Y / W);
+    }
+    if (lrf_has_box(TYPE) && !start_xyz) {
+        cx = fminf(fmaxf(cx, L.lo[0]), L.hi[0]);
+        cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
+    }
+    float Sp = 0.0f;
+    for (int i = lane; i < n_s; i += 32) {
+        bool in = !m.passive[i];
+        if (m.min_signal > 0.0f && s_sig[i] < m.min_signal) in = false;
+        if (m.max_distance > 0.0f) {
+            const double dx = (double)L.sxy[2 * i] - (double)cx, dy = (double)L.sxy[2 * i + 1] - (double)cy;
+            if (sqrt(dx * dx + dy * dy) > (double)m.max_distance) in = false;
+        }
+        s_act[i] = in ? 1.0f : 0.0f;
+        if (in) Sp += s_sig[i];
+    }
+    S = match_warp_sum(Sp);
+    __syncwarp();
+    if (!(S > 0.0f)) return ANTS_EVT_ZERO_SIGNAL;
+    if (!lrf_defined(L, s_act, cx, cy, cz)) return ANTS_EVT_OUT_OF_DOMAIN;
+    return ANTS_EVT_OK;
+}
+
+}  // namespace ants

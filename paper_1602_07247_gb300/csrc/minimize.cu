@@ -1,0 +1,415 @@
+// Continuous minimisation of the match (Sec. 5.1.2.1: the match, maximum
+// likelihood or least squares, is minimised over the two or three source
+// coordinates by a gradient method, from the centroid or the strongest
+// sensor; the paper uses Minuit2's Migrad).  Here: damped Fisher scoring
+// (Levenberg-Marquardt) with the energy profiled out, E = S / H.
+//
+// One warp per event.  Each trial evaluates every sensor in the match at the
+// trial point in two passes over the lanes' sensors (eta and its gradient,
+// kept in shared memory; then, with H and grad H reduced, the Fisher
+// information J and the scoring direction g); the butterfly reductions
+// leave identical sums in every lane, so every lane solves the same 2 x 2 or
+// 3 x 3 system and takes the same decisions.  The change of the match
+// between the current point p and the trial q is formed relative to p: for
+// maximum likelihood sum s log2(eta_q / eta_p) - S log1p(sum (eta_q - eta_p)
+// / H_p), which keeps single precision near the optimum; inside a rounding
+// band tau = 2^-18 S the decision falls to the trapezoid rule on the
+// gradients, (g_p + g_q) . (q - p) >= 0.  Coordinates on a bound of the
+// domain's box whose step points out of it are held (a projected step), and
+// a step that overshot the optimum along its line raises the damping.
+#include <cmath>
+
+#include "bspline.cuh"
+#include "internal.cuh"
+#include "match.cuh"
+
+namespace ants {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kEtaFloor = 1e-30f;
+constexpr int kMinWarps = 8;
+constexpr float kLambdaMin = 1e-12f, kLambdaMax = 1e8f;
+
+struct MinArgs {
+    LrfDev L;
+    int criterion, fit_z, max_iter;
+    float tol, lambda0;
+    const float *sig;
+    long n_e;
+    const float *start_xyz;  // nullable [n_e][3]
+    float *xyz, *E, *logL;
+    int32_t *status;
+    int16_t *n_iter;  // nullable [n_e]
+    MatchArgs m;
+};
+
+// the sums of one trial point (identical in every lane after the reductions)
+struct PointSums {
+    float H, dH[3];
+    float g[3];
+    float J[6];   // J00, J01, J02, J11, J12, J22
+    float chi2;   // least squares: Pearson's chi^2
+    float lsum;   // maximum likelihood: sum s log2(eta / eta_p)
+    float dHrel;  // sum (eta - eta_p)
+};
+
+// s ln s - s - lgamma(s + 1) for s > 0 (Stirling series from s = 10)
+__device__ __forceinline__ float poisson_const(float s)
+{
+    if (s >= 10.0f) {
+        float r = 1.0f / s, r2 = r * r;
+        float series = r * (-1.0f / 12.0f + r2 * (1.0f / 360.0f - r2 * (1.0f / 1260.0f)));
+        return -0.5f * logf(6.283185307179586f * s) + series;
+    }
+    return s * logf(s) - s - lgammaf(s + 1.0f);
+}
+
+// every LRF in the match defined at (x, y, z), checked across the warp
+template <int TYPE>
+__device__ __forceinline__ bool defined_warp(const LrfDev &L, const float *s_act, float x, float y, float z, int lane)
+{
+    bool ok = true;
+    if (TYPE == ANTS_LRF_RADIAL || TYPE == ANTS_LRF_COMPOSITE || TYPE == ANTS_LRF_AXIAL_Z) {
+        const float rhi = TYPE == ANTS_LRF_COMPOSITE ? L.hi_r : L.hi[0];
+        for (int i = lane; i < L.n_s; i += 32)
+            if (s_act[i] != 0.0f && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) > rhi) ok = false;
+    }
+    ok = __all_sync(kFull, ok);
+    if (TYPE == ANTS_LRF_AXIAL_Z) return ok && z >= L.lo[1] && z <= L.hi[1];
+    if (TYPE == ANTS_LRF_RADIAL) return ok;
+    return ok && in_box(L, x, y, z);
+}
+
+// the box bounds of coordinate k: x and y in the XY box (XY, XYZ,
+// composite, sliced), z in the z range (XYZ, sliced, axial+z); false when
+// the coordinate has none
+template <int TYPE>
+__device__ __forceinline__ bool box_bounds(const LrfDev &L, int k, float &lo, float &hi)
+{
+    if (k < 2) {
+        if (!lrf_has_box(TYPE)) return false;
+        lo = L.lo[k];
+        hi = L.hi[k];
+        return true;
+    }
+    if (!lrf_is_3d(TYPE)) return false;
+    const int kz = TYPE == ANTS_LRF_AXIAL_Z ? 1 : 2;
+    lo = L.lo[kz];
+    hi = L.hi[kz];
+    return true;
+}
+
+// a trial point moved onto the domain's box
+template <int TYPE>
+__device__ __forceinline__ void clamp_box(const LrfDev &L, float q[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        float lo, hi;
+        if (box_bounds<TYPE>(L, k, lo, hi)) q[k] = fminf(fmaxf(q[k], lo), hi);
+    }
+}
+
+// the coordinates (bit k) on a bound of the box while the step points out
+// of it: held in the next solve (a projected step)
+template <int TYPE>
+__device__ __forceinline__ int active_set(const LrfDev &L, const float p[3], const float delta[3], int d)
+{
+    int fixed = 0;
+    for (int k = 0; k < d; ++k) {
+        float lo, hi;
+        if (!box_bounds<TYPE>(L, k, lo, hi)) continue;
+        if ((p[k] == lo && delta[k] < 0.0f) || (p[k] == hi && delta[k] > 0.0f)) fixed |= 1 << k;
+    }
+    return fixed;
+}
+
+// The two passes at point q over the sensors in the match: eta (floored,
+// gradient 0 where floored) into s_eq and its gradient into s_g, then J, g
+// and chi^2; rel: the sums relative to eta_p in s_ep as well.
+template <int TYPE>
+__device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s_sig, const float *s_act,
+                                                const float *s_ep, float *s_eq, float *s_g, const float q[3], int d,
+                                                float S, bool rel, int lane)
+{
+    const LrfDev &L = a.L;
+    const int n_s = L.n_s;
+    PointSums P;
+    float H = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, ls = 0.0f, dh = 0.0f;
+    for (int i = lane; i < n_s; i += 32) {
+        if (s_act[i] == 0.0f) continue;
+        bool ok;
+        float gx, gy, gz;
+        float eta = lrf_eta_grad_t<TYPE>(L, i, q[0], q[1], q[2], ok, gx, gy, gz);
+        if (!(eta > kEtaFloor)) {
+            eta = kEtaFloor;
+            gx = gy = gz = 0.0f;
+        }
+        s_eq[i] = eta;
+        s_g[3 * i] = gx;
+        s_g[3 * i + 1] = gy;
+        s_g[3 * i + 2] = gz;
+        H += eta;
+        d0 += gx;
+        d1 += gy;
+        d2 += gz;
+        if (rel) {
+            const float ep = s_ep[i];
+            if (s_sig[i] != 0.0f) ls = fmaf(s_sig[i], log2f(eta / ep), ls);
+            dh += eta - ep;
+        }
+    }
+    P.H = match_warp_sum(H);
+    P.dH[0] = match_warp_sum(d0);
+    P.dH[1] = match_warp_sum(d1);
+    P.dH[2] = match_warp_sum(d2);
+    P.lsum = rel ? match_warp_sum(ls) : 0.0f;
+    P.dHrel = rel ? match_warp_sum(dh) : 0.0f;
+    const float E = S / P.H, invH = 1.0f / P.H;
+    float g[3] = {0.0f, 0.0f, 0.0f}, J[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, chi = 0.0f;
+    for (int i = lane; i < n_s; i += 32) {
+        if (s_act[i] == 0.0f) continue;
+        const float eta = s_eq[i], s = s_sig[i], mu = E * eta;
+        float gi[3] = {s_g[3 * i], s_g[3 * i + 1], s_g[3 * i + 2]}, dmu[3];
+        for (int k = 0; k < 3; ++k) dmu[k] = E * fmaf(-eta * invH, P.dH[k], gi[k]);
+        const float imu = 1.0f / mu;
+        J[0] = fmaf(dmu[0] * imu, dmu[0], J[0]);
+        J[1] = fmaf(dmu[0] * imu, dmu[1], J[1]);
+        J[3] = fmaf(dmu[1] * imu, dmu[1], J[3]);
+        if (d == 3) {
+            J[2] = fmaf(dmu[0] * imu, dmu[2], J[2]);
+            J[4] = fmaf(dmu[1] * imu, dmu[2], J[4]);
+            J[5] = fmaf(dmu[2] * imu, dmu[2], J[5]);
+        }
+        const float r = s - mu;
+        if (a.criterion == 0) {
+            const float w = r / eta;
+            for (int k = 0; k < 3; ++k) g[k] = fmaf(w, gi[k], g[k]);
+        } else {
+            const float sm = s * imu, w = -0.5f * (1.0f - sm * sm);
+            for (int k = 0; k < 3; ++k) g[k] = fmaf(w, dmu[k], g[k]);
+            chi = fmaf(r * r, imu, chi);
+        }
+    }
+    for (int k = 0; k < 3; ++k) P.g[k] = k < d ? match_warp_sum(g[k]) : 0.0f;
+    P.J[0] = match_warp_sum(J[0]);
+    P.J[1] = match_warp_sum(J[1]);
+    P.J[3] = match_warp_sum(J[3]);
+    P.J[2] = d == 3 ? match_warp_sum(J[2]) : 0.0f;
+    P.J[4] = d == 3 ? match_warp_sum(J[4]) : 0.0f;
+    P.J[5] = d == 3 ? match_warp_sum(J[5]) : 0.0f;
+    P.chi2 = a.criterion == 0 ? 0.0f : match_warp_sum(chi);
+    return P;
+}
+
+// (J + lambda D) delta = g, D = diag(J) floored at 1e-12 of its largest
+// entry, by Cramer's rule; the coordinates in `fixed` are held (their rows
+// and columns those of the identity, right-hand side 0); false when singular
+__device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int d, int fixed, float delta[3])
+{
+    delta[0] = delta[1] = delta[2] = 0.0f;
+    float dmax = fmaxf(P.J[0], P.J[3]);
+    if (d == 3) dmax = fmaxf(dmax, P.J[5]);
+    if (!(dmax > 0.0f)) return false;
+    const float fl = 1e-12f * dmax;
+    const bool f0 = fixed & 1, f1 = fixed & 2, f2 = fixed & 4;
+    const float g0 = f0 ? 0.0f : P.g[0], g1 = f1 ? 0.0f : P.g[1], g2 = f2 ? 0.0f : P.g[2];
+    const float a00 = f0 ? 1.0f : fmaf(lambda, fmaxf(P.J[0], fl), P.J[0]);
+    const float a11 = f1 ? 1.0f : fmaf(lambda, fmaxf(P.J[3], fl), P.J[3]);
+    const float a01 = f0 || f1 ? 0.0f : P.J[1];
+    if (d == 2) {
+        const float det = a00 * a11 - a01 * a01;
+        if (!(fabsf(det) > 0.0f)) return false;
+        delta[0] = (g0 * a11 - a01 * g1) / det;
+        delta[1] = (a00 * g1 - g0 * a01) / det;
+        return true;
+    }
+    const float a22 = f2 ? 1.0f : fmaf(lambda, fmaxf(P.J[5], fl), P.J[5]);
+    const float a02 = f0 || f2 ? 0.0f : P.J[2], a12 = f1 || f2 ? 0.0f : P.J[4];
+    const float c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+    const float det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(fabsf(det) > 0.0f)) return false;
+    const float c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+    const float inv = 1.0f / det;
+    delta[0] = (c00 * g0 + c01 * g1 + c02 * g2) * inv;
+    delta[1] = (c01 * g0 + c11 * g1 + c12 * g2) * inv;
+    delta[2] = (c02 * g0 + c12 * g1 + c22 * g2) * inv;
+    return true;
+}
+
+template <int TYPE>
+__global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __grid_constant__ MinArgs a)
+{
+    extern __shared__ float smem[];
+    const LrfDev &L = a.L;
+    const int n_s = L.n_s;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *s_sig = smem + (size_t)wib * 7 * n_s;  // signals (0 for passive sensors)
+    float *s_act = s_sig + n_s;                   // 1 in the match, 0 out
+    float *s_ep = s_act + n_s;                    // eta at the current point
+    float *s_eq = s_ep + n_s;                     // eta at the trial point
+    float *s_g = s_eq + n_s;                      // its gradient [n_s][3]
+    const int d = lrf_is_3d(TYPE) && a.fit_z ? 3 : 2;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long e = (long)blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_e; e += warps) {
+        float S, p[3];
+        const int st = match_prologue<TYPE>(L, a.m, a.sig, e, a.start_xyz, s_sig, s_act, lane, S, p[0], p[1], p[2]);
+        if (st != ANTS_EVT_OK) {
+            if (lane == 0) {
+                const float nan = __int_as_float(0x7fc00000);
+                a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = nan;
+                a.E[e] = a.logL[e] = nan;
+                a.status[e] = st;
+                if (a.n_iter) a.n_iter[e] = 0;
+            }
+            __syncwarp();
+            continue;
+        }
+        const float tau = ldexpf(S, -18);
+        PointSums P = point_pass<TYPE>(a, s_sig, s_act, s_ep, s_eq, s_g, p, d, S, false, lane);
+        for (int i = lane; i < n_s; i += 32) s_ep[i] = s_eq[i];
+        float lambda = a.lambda0;
+        int used = -a.max_iter;
+        for (int it = 1; it <= a.max_iter; ++it) {
+            float delta[3];
+            bool okd = solve_step(P, lambda, d, 0, delta);
+            const int fixed = okd ? active_set<TYPE>(L, p, delta, d) : 0;
+            if (fixed) okd = solve_step(P, lambda, d, fixed, delta);
+            float q[3] = {p[0] + delta[0], p[1] + delta[1], p[2] + delta[2]};
+            clamp_box<TYPE>(L, q);
+            bool acc = okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
+                       defined_warp<TYPE>(L, s_act, q[0], q[1], q[2], lane);
+            PointSums Q;
+            if (acc) {
+                Q = point_pass<TYPE>(a, s_sig, s_act, s_ep, s_eq, s_g, q, d, S, true, lane);
+                const float dC = a.criterion == 0
+                                     ? 0.6931471805599453f * Q.lsum - S * log1pf(Q.dHrel / P.H)
+                                     : P.chi2 - Q.chi2;
+                if (fabsf(dC) > tau) {
+                    acc = dC > 0.0f;
+                } else {
+                    float t = 0.0f;
+                    for (int k = 0; k < 3; ++k) t = fmaf(P.g[k] + Q.g[k], q[k] - p[k], t);
+                    acc = t >= 0.0f;
+                }
+            }
+            if (acc) {
+                const float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+                const float step = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                // slopes along the step at both ends: when their sign changed
+                // the step overshot the line's optimum (at t* = a0 / (a0 - a1)
+                // for a quadratic), and the next damping shortens by t*
+                const float a0 = fmaf(P.g[0], dx, fmaf(P.g[1], dy, P.g[2] * dz));
+                const float a1 = fmaf(Q.g[0], dx, fmaf(Q.g[1], dy, Q.g[2] * dz));
+                float next = fmaxf(lambda * 0.1f, kLambdaMin);
+                if (a0 > 0.0f && a1 < 0.0f) next = fmaxf(next, (a0 - a1) / a0 - 1.0f);
+                p[0] = q[0];
+                p[1] = q[1];
+                p[2] = q[2];
+                P = Q;
+                for (int i = lane; i < n_s; i += 32) s_ep[i] = s_eq[i];
+                lambda = next;
+                if (step < a.tol) {
+                    used = it;
+                    break;
+                }
+            } else {
+                lambda *= 10.0f;
+                if (lambda > kLambdaMax) {
+                    used = it;
+                    break;
+                }
+            }
+        }
+        // energy and full Poisson log-likelihood over the match at p
+        const float En = S / P.H;
+        float ll = 0.0f;
+        for (int i = lane; i < n_s; i += 32) {
+            if (s_act[i] == 0.0f) continue;
+            const float mu = En * s_ep[i], s = s_sig[i];
+            ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
+        }
+        ll = match_warp_sum(ll);
+        if (lane == 0) {
+            a.xyz[3 * e] = p[0];
+            a.xyz[3 * e + 1] = p[1];
+            a.xyz[3 * e + 2] = p[2];
+            a.E[e] = En;
+            a.logL[e] = ll;
+            a.status[e] = ANTS_EVT_OK;
+            if (a.n_iter) a.n_iter[e] = (int16_t)used;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int check_minimize_params(const ants_lrf *lrf, const ants_minimize_params *P)
+{
+    if (!P) return fail(ANTS_E_ARG, "minimize parameters are NULL");
+    if (P->criterion != ANTS_CRIT_ML && P->criterion != ANTS_CRIT_LS)
+        return fail(ANTS_E_ARG, "minimize: unknown criterion %d", P->criterion);
+    if (P->start != ANTS_START_COG && P->start != ANTS_START_MAX_SENSOR)
+        return fail(ANTS_E_ARG, "minimize: unknown start %d", P->start);
+    if (P->max_iter < 1 || P->max_iter > 32767) return fail(ANTS_E_ARG, "minimize: max_iter must be in 1..32767");
+    if (!(P->tol > 0.0f) || !(P->lambda0 >= 0.0f)) return fail(ANTS_E_ARG, "minimize: tol must be > 0, lambda0 >= 0");
+    if (!(P->min_signal >= 0.0f) || !(P->max_distance >= 0.0f))
+        return fail(ANTS_E_ARG, "minimize: min_signal and max_distance must be >= 0");
+    if (P->fit_z != 0 && P->fit_z != 1) return fail(ANTS_E_ARG, "minimize: fit_z must be 0 or 1");
+    if (lrf->n_s > kMaxMatchSensors)
+        return fail(ANTS_E_UNIMPLEMENTED, "minimize: at most %d sensors", kMaxMatchSensors);
+    return ANTS_OK;
+}
+
+int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_minimize_params &P, const float *sig,
+                         long n_e, const float *start, float *xyz, float *E, float *logL, int32_t *status,
+                         int16_t *n_iter, cudaStream_t s)
+{
+    MinArgs a;
+    a.L = lrf->dev;
+    a.criterion = P.criterion;
+    a.fit_z = P.fit_z;
+    a.max_iter = P.max_iter;
+    a.tol = P.tol;
+    a.lambda0 = P.lambda0;
+    a.sig = sig;
+    a.n_e = n_e;
+    a.start_xyz = start;
+    a.xyz = xyz;
+    a.E = E;
+    a.logL = logL;
+    a.status = status;
+    a.n_iter = n_iter;
+    a.m.start = P.start;
+    a.m.min_signal = P.min_signal;
+    a.m.max_distance = P.max_distance;
+    a.m.z0 = P.z0;
+    const int n_s = lrf->n_s;
+    for (int i = 0; i < kMaxMatchSensors; ++i) {
+        a.m.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
+        a.m.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
+    }
+    // as many warps per block as fit 7 n_s floats each in 48 KB
+    int wpb = (int)(48 * 1024 / (28 * (size_t)n_s));
+    wpb = wpb < 1 ? 1 : (wpb > kMinWarps ? kMinWarps : wpb);
+    const size_t smem = (size_t)wpb * 28 * n_s;
+    long blocks = (n_e + wpb - 1) / wpb;
+    const long cap = (long)ctx->n_sm * 16;
+    if (blocks > cap) blocks = cap;
+    switch (lrf->type) {
+    case ANTS_LRF_RADIAL: minimize_kernel<ANTS_LRF_RADIAL><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_XY: minimize_kernel<ANTS_LRF_XY><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_XYZ: minimize_kernel<ANTS_LRF_XYZ><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_COMPOSITE: minimize_kernel<ANTS_LRF_COMPOSITE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_AXIAL_Z: minimize_kernel<ANTS_LRF_AXIAL_Z><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    default: minimize_kernel<ANTS_LRF_SLICED><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "minimize_kernel launch");
+    count_launch();
+    return ANTS_OK;
+}
+
+}  // namespace ants

@@ -19,6 +19,7 @@
 
 #include "bspline.cuh"
 #include "internal.cuh"
+#include "match.cuh"
 
 namespace ants {
 
@@ -26,37 +27,24 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
-constexpr int kMaxVariantSensors = 1024;
+constexpr int kMaxVariantSensors = kMaxMatchSensors;
 constexpr int kVarWarps = 8;
 
 struct VarArgs {
     LrfDev L;
     int n_xy, n_z, iters;
-    float shrink, step_xy, step_z, z0;
-    int criterion, start;
-    float min_signal, max_distance;
+    float shrink, step_xy, step_z;
+    int criterion;
     const float *sig;
     long n_e;
     const float *start_xyz;  // given starts [n_e][3] (nullable)
     float *xyz, *E, *logL;
     int32_t *status;
     int16_t *trace;
-    double gain[kMaxVariantSensors];             // relative gains (start)
-    unsigned char passive[kMaxVariantSensors];   // 1 = passive
-    __device__ bool start_xyz_given() const { return start_xyz != nullptr; }
+    MatchArgs m;
 };
 
-__device__ __forceinline__ float vwarp_sum(float v)
-{
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double vwarp_sum_d(double v)
-{
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
+__device__ __forceinline__ float vwarp_sum(float v) { return match_warp_sum(v); }
 
 // s ln s - s - lgamma(s + 1) for s > 0 (Stirling series from s = 10)
 __device__ __forceinline__ float vpoisson_const(float s)
@@ -111,81 +99,11 @@ __global__ void __launch_bounds__(32 * kVarWarps, 2) cgs_variant_kernel(const __
     const int c_xy = (a.n_xy - 1) / 2, c_z = (a.n_z - 1) / 2;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     for (long e = (long)blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_e; e += warps) {
-        // ---- signals, status, start ------------------------------------
-        bool bad = false;
-        double tot = 0.0, W = 0.0, X = 0.0, Y = 0.0, bv = -1.0;
-        int bi = 0x7fffffff;
-        for (int i = lane; i < n_s; i += 32) {
-            float s = a.sig[e * n_s + i];
-            if (a.passive[i]) s = 0.0f;
-            else if (!isfinite(s) || s < 0.0f) bad = true;
-            s_sig[i] = s;
-            const double w = (double)s / a.gain[i];
-            tot += (double)s;
-            W += w;
-            X += (double)L.sxy[2 * i] * w;
-            Y += (double)L.sxy[2 * i + 1] * w;
-            if (!a.passive[i] && w > bv) {  // lanes visit increasing i: the first maximum
-                bv = w;
-                bi = i;
-            }
-        }
-        if (__any_sync(kFull, bad)) {
-            set_failed(a, e, ANTS_EVT_BAD_SIGNAL, lane);
-            continue;
-        }
-        tot = vwarp_sum_d(tot);
-        if (!(tot > 0.0)) {
-            set_failed(a, e, ANTS_EVT_ZERO_SIGNAL, lane);
-            continue;
-        }
-        float cx, cy, cz = lrf_is_3d(TYPE) ? a.z0 : 0.0f;
-        if (a.start_xyz_given()) {
-            cx = a.start_xyz[3 * e];
-            cy = a.start_xyz[3 * e + 1];
-            cz = a.start_xyz[3 * e + 2];
-        } else if (a.start == 1) {
-            for (int o = 16; o; o >>= 1) {  // the largest s/g, ties to the lowest index
-                const double v2 = __shfl_xor_sync(kFull, bv, o);
-                const int i2 = __shfl_xor_sync(kFull, bi, o);
-                if (v2 > bv || (v2 == bv && i2 < bi)) {
-                    bv = v2;
-                    bi = i2;
-                }
-            }
-            cx = L.sxy[2 * bi];
-            cy = L.sxy[2 * bi + 1];
-        } else {
-            W = vwarp_sum_d(W);
-            X = vwarp_sum_d(X);
-            Y = vwarp_sum_d(Y);
-            cx = (float)(X / W);
-            cy = (float)(Y / W);
-        }
-        if (lrf_has_box(TYPE) && !a.start_xyz_given()) {
-            cx = fminf(fmaxf(cx, L.lo[0]), L.hi[0]);
-            cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
-        }
-        // ---- sensors in the match -------------------------------------------
-        float Sp = 0.0f;
-        for (int i = lane; i < n_s; i += 32) {
-            bool in = !a.passive[i];
-            if (a.min_signal > 0.0f && s_sig[i] < a.min_signal) in = false;
-            if (a.max_distance > 0.0f) {
-                const double dx = (double)L.sxy[2 * i] - (double)cx, dy = (double)L.sxy[2 * i + 1] - (double)cy;
-                if (sqrt(dx * dx + dy * dy) > (double)a.max_distance) in = false;
-            }
-            s_act[i] = in ? 1.0f : 0.0f;
-            if (in) Sp += s_sig[i];
-        }
-        const float S = vwarp_sum(Sp);
-        __syncwarp();
-        if (!(S > 0.0f)) {
-            set_failed(a, e, ANTS_EVT_ZERO_SIGNAL, lane);
-            continue;
-        }
-        if (!node_ok<TYPE>(L, s_act, cx, cy, cz)) {
-            set_failed(a, e, ANTS_EVT_OUT_OF_DOMAIN, lane);
+        // ---- signals, status, start, the sensors in the match ---------------
+        float S, cx, cy, cz;
+        const int st = match_prologue<TYPE>(L, a.m, a.sig, e, a.start_xyz, s_sig, s_act, lane, S, cx, cy, cz);
+        if (st != ANTS_EVT_OK) {
+            set_failed(a, e, st, lane);
             continue;
         }
         // ---- contracting grids ------------------------------------------------
@@ -313,11 +231,11 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     a.shrink = P.grid.shrink;
     a.step_xy = P.grid.step_xy;
     a.step_z = P.grid.step_z;
-    a.z0 = P.grid.z0;
+    a.m.z0 = P.grid.z0;
     a.criterion = P.criterion;
-    a.start = P.start;
-    a.min_signal = P.min_signal;
-    a.max_distance = P.max_distance;
+    a.m.start = P.start;
+    a.m.min_signal = P.min_signal;
+    a.m.max_distance = P.max_distance;
     a.sig = sig;
     a.n_e = n_e;
     a.start_xyz = start;
@@ -328,8 +246,8 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     a.trace = trace;
     const int n_s = lrf->n_s;
     for (int i = 0; i < kMaxVariantSensors; ++i) {
-        a.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
-        a.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
+        a.m.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
+        a.m.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
     }
     // as many warps per block as fit 4 n_s floats each in 48 KB
     int wpb = (int)(48 * 1024 / (16 * (size_t)n_s));

@@ -1,0 +1,176 @@
+"""Continuous minimisation of the match (Sec. 5.1.2.1) on the GPU against
+the FP64 oracle: the same damped Fisher scoring from the same starts, for
+every LRF type and both criteria; results compared at convergence, where
+the optimum itself is the common reference."""
+import numpy as np
+import pytest
+
+import oracle
+import pins
+import synth
+import synth.workloads
+from parity import gpu_objects, oracle_lrf
+
+pytestmark = pytest.mark.gpu
+
+TYPES = ["radial", "xy", "xyz", "composite", "axial_z", "sliced"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1602_07247_gb300 as ants
+    return ants.Context(0)
+
+
+@pytest.fixture(scope="module")
+def lrfs():
+    return pins._all_type_lrfs()[1]
+
+
+def _gpu_lrf(ctx, L):
+    import paper_1602_07247_gb300 as ants
+    det = ants.Detector(L.sensor_xy)
+    if L.type in (oracle.RADIAL, oracle.XY, oracle.XYZ):
+        d = {oracle.RADIAL: 1, oracle.XY: 2, oracle.XYZ: 3}[L.type]
+        return ants.Lrf.from_coefficients(ctx, det, L.type, L.n_int[:d], L.lo[:d], L.hi[:d], L.coef,
+                                          gain=L.gain)
+    if L.type == oracle.COMPOSITE:
+        return ants.Lrf.from_scheme(ctx, det, L.type, L.n_int[:2], L.lo[:2], L.hi[:2], L.coef, n_int_r=L.n_int_r,
+                                    hi_r=L.hi_r)
+    if L.type == oracle.AXIAL_Z:
+        return ants.Lrf.from_scheme(ctx, det, L.type, L.n_int[:2], L.lo[:2], L.hi[:2], L.coef)
+    return ants.Lrf.from_scheme(ctx, det, L.type, L.n_int[:2], L.lo, L.hi, L.coef, n_planes=L.n_planes)
+
+
+def _events(L, n, seed):
+    rng = np.random.default_rng(seed)
+    d = pins.L_dim(L)
+    half = 5.0 if L.type == oracle.COMPOSITE else 7.0
+    p0 = np.stack([rng.uniform(-half, half, n), rng.uniform(-half, half, n), rng.uniform(4.0, 16.0, n)], 1)[:, :d]
+    return rng.poisson(4000.0 * oracle.lrf_eval(L, p0)).astype(np.float32), p0
+
+
+def _run_gpu(ctx, lrf, sig, mp, start=None):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    st = None if start is None else torch.from_numpy(np.ascontiguousarray(start, dtype=np.float32)).cuda()
+    r = ants.reconstruct(ctx, lrf, mp, torch.from_numpy(sig).cuda(), start_xyz=st, want_trace=True,
+                         method=ants.ANTS_MINIMIZE)
+    torch.cuda.synchronize()
+    return {k: getattr(r, k).cpu().numpy() for k in ("xyz", "E", "logL", "status", "trace")}
+
+
+@pytest.mark.parametrize("crit", [0, 1], ids=["ml", "ls"])
+@pytest.mark.parametrize("name", TYPES)
+def test_minimize_matches_oracle(ctx, lrfs, name, crit):
+    import paper_1602_07247_gb300 as ants
+    L = lrfs[name]
+    lrf = _gpu_lrf(ctx, L)
+    sig, p0 = _events(L, 600, seed=3 + crit)
+    mp = ants.MinimizeParams(criterion=crit, z0=10.0, max_iter=60, tol=1e-4)
+    g = _run_gpu(ctx, lrf, sig, mp)
+    o = oracle.minimize(L, sig.astype(np.float64), oracle.Variant(criterion=crit),
+                        oracle.Minimize(max_iter=60, tol=1e-4), z0=10.0)
+    assert np.array_equal(g["status"], o["status"])
+    conv = (g["status"] == 0) & (g["trace"][:, 0] > 0) & (o["n_iter"] > 0)
+    assert conv.mean() > 0.9, conv.mean()
+    d = pins.L_dim(L)
+    dx = np.abs(g["xyz"][conv, :d] - o["xyz"][conv, :d]).max(axis=1)
+    rl = np.abs(g["logL"][conv] / o["logL"][conv] - 1.0)
+    rE = np.abs(g["E"][conv] / o["E"][conv] - 1.0)
+    print(name, crit, "converged", conv.mean(), "max |dxyz|", dx.max(), "p99", np.quantile(dx, 0.99), "rel dlogL",
+          rl.max(), "rel dE", rE.max(), "trials gpu/oracle", g["trace"][conv, 0].mean(), o["n_iter"][conv].mean())
+    # single precision moves the optimum through the gradient's rounding
+    # (~2^-23 sum |s grad eta / eta|) over the curvature: ~1e-5 mm in x, y,
+    # up to a few 1e-4 mm along the weakly curved z of the 3D sets
+    assert np.quantile(dx, 0.99) <= 1e-3 and dx.max() <= 5e-3
+    assert rl.max() <= 1e-5 and rE.max() <= 1e-4
+
+
+def test_refine_from_contracting_grids(ctx):
+    """The 8x8 SiPM workload: contracting grids, then the continuous refine
+    from their result; both sides start from the GPU's grid result."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w = synth.workloads.get("sipm8x8_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    ev = w.events(4000, seed=17)
+    sig = ev.signals.astype(np.float32)
+    cg = ants.reconstruct(ctx, lrf, p, torch.from_numpy(sig).cuda())
+    start = cg.xyz.cpu().numpy()
+    g = _run_gpu(ctx, lrf, sig, ants.MinimizeParams(max_iter=30, tol=1e-4), start=start)
+    pick = np.random.default_rng(2).choice(4000, 400, replace=False)
+    o = oracle.minimize(L, sig[pick].astype(np.float64), oracle.Variant(), oracle.Minimize(max_iter=30, tol=1e-4),
+                        start_xyz=start[pick].astype(np.float64), gain=w.gains)
+    assert np.array_equal(g["status"][pick], o["status"])
+    ok = (o["status"] == 0) & (o["n_iter"] > 0) & (g["trace"][pick, 0] > 0)
+    assert ok.mean() > 0.95
+    dx = np.abs(g["xyz"][pick][ok] - o["xyz"][ok]).max()
+    print("refine max |dxyz|", dx, "trials", g["trace"][pick][ok, 0].mean())
+    assert dx <= 2e-3
+    # the refine never loses likelihood against the grid result
+    assert np.all(g["logL"] >= cg.logL.cpu().numpy() - 1e-5 * np.abs(g["logL"]))
+
+
+def test_noise_free_recovery(ctx, lrfs):
+    import paper_1602_07247_gb300 as ants
+    for name in TYPES:
+        L = lrfs[name]
+        d = pins.L_dim(L)
+        p0 = np.array([[1.5, -2.0, 11.0]])[:, :d]
+        s = (3000.0 * oracle.lrf_eval(L, p0)).astype(np.float32)
+        start = np.array([[0.0, -1.0, 13.0]])
+        for crit in (0, 1):
+            g = _run_gpu(ctx, _gpu_lrf(ctx, L), s, ants.MinimizeParams(criterion=crit, max_iter=60, tol=1e-5),
+                         start=start)
+            assert g["status"][0] == 0
+            err = np.abs(g["xyz"][0, :d] - p0[0]).max()
+            assert err < 2e-3, (name, crit, err, g["xyz"][0], g["trace"][0])
+
+
+def test_status_and_errors(ctx, lrfs):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    L = lrfs["xy"]
+    lrf = _gpu_lrf(ctx, L)
+    s = (3000.0 * oracle.lrf_eval(L, np.array([[1.0, 1.0], [0.0, 0.0], [0.0, 0.0], [2.0, 2.0]]))).astype(np.float32)
+    s[1] = 0.0
+    s[2, 1] = -1.0
+    start = np.array([[-5.0, -5.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [40.0, 0.0, 0.0]])
+    g = _run_gpu(ctx, lrf, s, ants.MinimizeParams(max_iter=1), start=start)
+    assert list(g["status"]) == [0, 2, 3, 4]
+    assert g["trace"][0, 0] == -1 and np.all(np.isnan(g["xyz"][1:]))
+    sig = torch.from_numpy(s).cuda()
+    for bad in (dict(criterion=7), dict(max_iter=0), dict(tol=0.0), dict(lambda0=-1.0), dict(fit_z=2)):
+        with pytest.raises(ants.AntsError):
+            ants.reconstruct(ctx, lrf, ants.MinimizeParams(**bad), sig, method=ants.ANTS_MINIMIZE)
+
+
+def test_full_size_sampled(ctx):
+    """10^6 events of the 8x8 SiPM workload minimised from the centroid; 64
+    sampled events against the oracle."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w = synth.workloads.get("sipm8x8_xy")
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    n = 1_000_000
+    ev = w.events(n, seed=w.event_seed)
+    mp = ants.MinimizeParams(max_iter=40, tol=1e-3)
+    r = ants.reconstruct(ctx, lrf, mp, torch.from_numpy(ev.signals).cuda(), want_trace=True,
+                         method=ants.ANTS_MINIMIZE)
+    torch.cuda.synchronize()
+    pick = np.random.default_rng(5).choice(n, 64, replace=False)
+    o = oracle.minimize(L, ev.signals[pick].astype(np.float64), oracle.Variant(), oracle.Minimize(max_iter=40, tol=1e-3),
+                        gain=w.gains)
+    st = r.status.cpu().numpy()[pick]
+    tr = r.trace.cpu().numpy()[pick, 0]
+    assert np.array_equal(st, o["status"])
+    ok = (st == 0) & (tr > 0) & (o["n_iter"] > 0)
+    assert ok.mean() > 0.9
+    dx = np.abs(r.xyz.cpu().numpy()[pick][ok] - o["xyz"][ok]).max()
+    print("full size: max |dxyz|", dx, "converged", (r.trace.cpu().numpy()[:, 0] > 0).mean())
+    assert dx <= 1e-2
