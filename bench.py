@@ -33,7 +33,8 @@ MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
 FMA_PER_CLK_SM = 128  # FP32 fused multiply-adds per clock per SM
 # canonical FP32 multiply-adds per (node, sensor) evaluation of each search:
 # B-spline tensor product, likelihood term and energy sum
-F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9, "composite": 41, "axial_z": 25, "sliced": 46}
+F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9, "composite": 41, "axial_z": 25, "sliced": 46,
+         "xy_minimize": 70}
 
 
 def alu_roofline(evals_per_s: float, kind: str) -> dict:
@@ -258,17 +259,20 @@ def forms_comparison(args, ants, torch, ctx, stream):
     # 2048 are exact in FP16, so all three forms see the same events)
     sig16 = sig.half()
     assert bool((sig16.float() == sig).all())
+    mp = ants.MinimizeParams(max_iter=40, tol=1e-3)
     for name, method, params, s_in in (("plain", ants.ANTS_CGS_PLAIN, plain, sig),
                                        ("learned", ants.ANTS_MLP_SEEDED, sp, sig),
-                                       ("precision", ants.ANTS_GEMM_TOPK, gp, sig16)):
-        res = ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream)
+                                       ("precision", ants.ANTS_GEMM_TOPK, gp, sig16),
+                                       ("minimize", ants.ANTS_MINIMIZE, mp, sig)):
+        tr = name == "minimize"
+        res = ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream, want_trace=tr)
         for _ in range(2):
-            ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream)
+            ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream, want_trace=tr)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.forms_steps):
-            res = ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream)
+            res = ants.reconstruct(ctx, lrf, params, s_in, method=method, stream=stream, want_trace=tr)
         e1.record(stream)
         torch.cuda.synchronize()
         dt = e0.elapsed_time(e1) / 1e3 / args.forms_steps
@@ -276,16 +280,19 @@ def forms_comparison(args, ants, torch, ctx, stream):
         err = np.sqrt((d ** 2).sum(1))
         st = res.status.cpu().numpy()
         fb_frac = float((st == ants.ANTS_EVT_FALLBACK).mean())
+        trials = float(np.abs(res.trace[:, 0].cpu().numpy().astype(np.int64)).mean()) + 1.0 if tr else 0.0
         evals = n * {"plain": plain.n_xy ** 2 * plain.iters,
                      "learned": refine.n_xy ** 2 * refine.iters + fb_frac * plain.n_xy ** 2 * plain.iters,
-                     "precision": kept_per_event * 7 * 7 * 5}[name] * w.n_sensors
+                     "precision": kept_per_event * 7 * 7 * 5, "minimize": trials}[name] * w.n_sensors
+        kind = {"plain": "xy", "minimize": "xy_minimize"}.get(name, "local")
         out[name] = {"events_per_s": n / dt, "ms_per_step": 1e3 * dt,
                      "evals_per_s": evals / dt,
-                     "roofline": alu_roofline(evals / dt, "xy" if name == "plain" else "local"),
+                     "roofline": alu_roofline(evals / dt, kind),
                      "rms_dxy_mm": float(np.sqrt((err ** 2).mean())),
                      "median_dxy_mm": float(np.median(err)), "p95_dxy_mm": float(np.quantile(err, 0.95)),
                      "fallback_frac": fb_frac}
-    for k in ("learned", "precision"):
+    out["minimize"]["mean_trials"] = trials - 1.0
+    for k in ("learned", "precision", "minimize"):
         out[k]["speedup_vs_plain"] = out[k]["events_per_s"] / out["plain"]["events_per_s"]
         out[k]["rms_ratio_vs_plain"] = out[k]["rms_dxy_mm"] / out["plain"]["rms_dxy_mm"]
     out["precision"]["refines_per_event"] = kept_per_event
@@ -314,7 +321,7 @@ def forms_comparison(args, ants, torch, ctx, stream):
                         f"MLP 256-256-256-3 (BF16, trained on the GPU on {args.train_events} events, "
                         f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile; precision form: "
                         f"FP16 signals, 64x64 BF16 log-response table, tcgen05 top-8, suppression 1.5 cells, "
-                        f"refine 7x7x5",
+                        f"refine 7x7x5; continuous minimisation from the centroid (at most 40 trials, tol 1e-3 mm)",
             "setup_s": setup_s, "deviance_max": thr, **out}
 
 
@@ -393,6 +400,73 @@ def variants_run(args, ants, torch, ctx, stream):
     return {"workload": f"{w.name}: 64 sensors, XY LRF, {n} events, 11x11 x 8 grids; per-node variant kernel "
                         "(least squares evaluates every node twice); cuts: signal >= 60, within 25 mm of the "
                         "strongest sensor, sensor 27 passive", **out}
+
+
+def minimize_run(args, ants, torch, ctx, stream):
+    """The continuous minimisation (Sec. 5.1.2.1) on the 8x8 SiPM workload,
+    10^6 events: from the centroid (maximum likelihood), and as a refine of
+    shorter contracting grids (11x11 x 4 grids, then the minimisation from
+    their result) beside the plain 11x11 x 8 search; events/s, RMS error,
+    trials, and the rate of sensor evaluations with gradient against the ALU
+    ceiling (70 FMA per evaluation: value and gradient of the tensor spline,
+    the weights and their derivatives, the Fisher and gradient sums)."""
+    w = workload()
+    det = ants.Detector(w.sensor_xy, w.gains)
+    pts, vals = w.fit_samples()
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, w.n_int, w.lo, w.hi, pts, vals)
+    n = 1_000_000
+    ev = w.events(n, seed=w.event_seed)
+    sig = torch.from_numpy(ev.signals).cuda()
+    mp = ants.MinimizeParams(max_iter=40, tol=1e-3)
+    short = ants.CgsParams(n_xy=w.n_xy, iters=4, step_xy=w.step_xy, shrink=w.shrink)
+    plain = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    trace = torch.empty((n, 1), dtype=torch.int16, device="cuda")
+    xyz0 = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    E0, L0 = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    st0 = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def minimize(start=None):
+        r = ants.Result(torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
+                        torch.empty(n, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"), trace)
+        ants.ants_reconstruct(ctx.handle, lrf.handle, ants.ANTS_MINIMIZE, mp, sig, w.n_sensors, r.xyz, r.E, r.logL,
+                              r.status, start_xyz=start, trace=trace, stream=stream)
+        return r
+
+    def refine():
+        ants.ants_reconstruct(ctx.handle, lrf.handle, ants.ANTS_CGS_PLAIN, short, sig, w.n_sensors, xyz0, E0, L0, st0,
+                              stream=stream)
+        return minimize(xyz0)
+
+    def grid():
+        return ants.reconstruct(ctx, lrf, plain, sig, stream=stream)
+
+    out = {}
+    for name, fn in (("from_centroid", minimize), ("grids_11x11x4_then_refine", refine), ("plain_11x11x8", grid)):
+        for _ in range(2):
+            res = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / reps
+        ok = res.status.cpu().numpy() == 0
+        d = res.xyz[:, :2].double().cpu().numpy() - ev.xyz[:, :2]
+        o = {"events_per_s": n / dt, "ms_per_launch": 1e3 * dt, "ok_frac": float(ok.mean()),
+             "rms_dxy_mm": float(np.sqrt((d[ok] ** 2).sum(1).mean()))}
+        if name != "plain_11x11x8":
+            t = trace[:, 0].cpu().numpy().astype(np.int64)
+            o["mean_trials"] = float(np.abs(t[ok]).mean())
+            o["converged_frac"] = float((t[ok] > 0).mean())
+            if name == "from_centroid":
+                evals = float(np.abs(t[ok]).sum() + ok.sum()) * w.n_sensors  # the start's pass and one per trial
+                o["roofline"] = alu_roofline(evals / dt, "xy_minimize")
+        out[name] = o
+    return {"workload": f"{w.name}: 64 sensors, XY LRF, {n} events; damped Fisher scoring (maximum likelihood, "
+                        "E profiled), at most 40 trials, tol 1e-3 mm", **out}
 
 
 def schemes_run(args, ants, torch, ctx, stream):
@@ -687,6 +761,7 @@ def run_ours(args):
     iterative = optional(iterative_run, args.no_iterative)
     variants = optional(variants_run, args.no_variants)
     schemes = optional(schemes_run, args.no_schemes)
+    minim = optional(minimize_run, args.no_minimize)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -694,6 +769,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
         "iterative_lrf": iterative, "variants_8x8": variants, "lrf_schemes_4x4": schemes,
+        "minimize_8x8": minim,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -721,6 +797,7 @@ def main():
     ap.add_argument("--no-iterative", action="store_true", help="skip the iterative LRF reconstruction")
     ap.add_argument("--no-variants", action="store_true", help="skip the search variants")
     ap.add_argument("--no-schemes", action="store_true", help="skip the composite, axial+z and sliced LRFs")
+    ap.add_argument("--no-minimize", action="store_true", help="skip the continuous minimisation")
     ap.add_argument("--iter-events", type=int, default=1_000_000)
     ap.add_argument("--iter-cycles", type=int, default=6)
     ap.add_argument("--batch-steps", type=int, default=1)

@@ -34,7 +34,7 @@ constexpr float kLambdaMin = 1e-12f, kLambdaMax = 1e8f;
 
 struct MinArgs {
     LrfDev L;
-    int criterion, fit_z, max_iter;
+    int criterion, max_iter;
     float tol, lambda0;
     const float *sig;
     long n_e;
@@ -113,11 +113,12 @@ __device__ __forceinline__ void clamp_box(const LrfDev &L, float q[3])
 
 // the coordinates (bit k) on a bound of the box while the step points out
 // of it: held in the next solve (a projected step)
-template <int TYPE>
-__device__ __forceinline__ int active_set(const LrfDev &L, const float p[3], const float delta[3], int d)
+template <int TYPE, int D>
+__device__ __forceinline__ int active_set(const LrfDev &L, const float p[3], const float delta[3])
 {
     int fixed = 0;
-    for (int k = 0; k < d; ++k) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
         float lo, hi;
         if (!box_bounds<TYPE>(L, k, lo, hi)) continue;
         if ((p[k] == lo && delta[k] < 0.0f) || (p[k] == hi && delta[k] > 0.0f)) fixed |= 1 << k;
@@ -128,10 +129,10 @@ __device__ __forceinline__ int active_set(const LrfDev &L, const float p[3], con
 // The two passes at point q over the sensors in the match: eta (floored,
 // gradient 0 where floored) into s_eq and its gradient into s_g, then J, g
 // and chi^2; rel: the sums relative to eta_p in s_ep as well.
-template <int TYPE>
+template <int TYPE, int D>
 __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s_sig, const float *s_act,
-                                                const float *s_ep, float *s_eq, float *s_g, const float q[3], int d,
-                                                float S, bool rel, int lane)
+                                                const float *s_ep, float *s_eq, float *s_g, const float q[3], float S,
+                                                bool rel, int lane)
 {
     const LrfDev &L = a.L;
     const int n_s = L.n_s;
@@ -153,7 +154,7 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
         H += eta;
         d0 += gx;
         d1 += gy;
-        d2 += gz;
+        if (D == 3) d2 += gz;
         if (rel) {
             const float ep = s_ep[i];
             if (s_sig[i] != 0.0f) ls = fmaf(s_sig[i], log2f(eta / ep), ls);
@@ -163,7 +164,7 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
     P.H = match_warp_sum(H);
     P.dH[0] = match_warp_sum(d0);
     P.dH[1] = match_warp_sum(d1);
-    P.dH[2] = match_warp_sum(d2);
+    P.dH[2] = D == 3 ? match_warp_sum(d2) : 0.0f;
     P.lsum = rel ? match_warp_sum(ls) : 0.0f;
     P.dHrel = rel ? match_warp_sum(dh) : 0.0f;
     const float E = S / P.H, invH = 1.0f / P.H;
@@ -171,13 +172,14 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
     for (int i = lane; i < n_s; i += 32) {
         if (s_act[i] == 0.0f) continue;
         const float eta = s_eq[i], s = s_sig[i], mu = E * eta;
-        float gi[3] = {s_g[3 * i], s_g[3 * i + 1], s_g[3 * i + 2]}, dmu[3];
-        for (int k = 0; k < 3; ++k) dmu[k] = E * fmaf(-eta * invH, P.dH[k], gi[k]);
+        float gi[3] = {s_g[3 * i], s_g[3 * i + 1], D == 3 ? s_g[3 * i + 2] : 0.0f}, dmu[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 0; k < D; ++k) dmu[k] = E * fmaf(-eta * invH, P.dH[k], gi[k]);
         const float imu = 1.0f / mu;
         J[0] = fmaf(dmu[0] * imu, dmu[0], J[0]);
         J[1] = fmaf(dmu[0] * imu, dmu[1], J[1]);
         J[3] = fmaf(dmu[1] * imu, dmu[1], J[3]);
-        if (d == 3) {
+        if (D == 3) {
             J[2] = fmaf(dmu[0] * imu, dmu[2], J[2]);
             J[4] = fmaf(dmu[1] * imu, dmu[2], J[4]);
             J[5] = fmaf(dmu[2] * imu, dmu[2], J[5]);
@@ -185,20 +187,23 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
         const float r = s - mu;
         if (a.criterion == 0) {
             const float w = r / eta;
-            for (int k = 0; k < 3; ++k) g[k] = fmaf(w, gi[k], g[k]);
+#pragma unroll
+            for (int k = 0; k < D; ++k) g[k] = fmaf(w, gi[k], g[k]);
         } else {
             const float sm = s * imu, w = -0.5f * (1.0f - sm * sm);
-            for (int k = 0; k < 3; ++k) g[k] = fmaf(w, dmu[k], g[k]);
+#pragma unroll
+            for (int k = 0; k < D; ++k) g[k] = fmaf(w, dmu[k], g[k]);
             chi = fmaf(r * r, imu, chi);
         }
     }
-    for (int k = 0; k < 3; ++k) P.g[k] = k < d ? match_warp_sum(g[k]) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P.g[k] = k < D ? match_warp_sum(g[k]) : 0.0f;
     P.J[0] = match_warp_sum(J[0]);
     P.J[1] = match_warp_sum(J[1]);
     P.J[3] = match_warp_sum(J[3]);
-    P.J[2] = d == 3 ? match_warp_sum(J[2]) : 0.0f;
-    P.J[4] = d == 3 ? match_warp_sum(J[4]) : 0.0f;
-    P.J[5] = d == 3 ? match_warp_sum(J[5]) : 0.0f;
+    P.J[2] = D == 3 ? match_warp_sum(J[2]) : 0.0f;
+    P.J[4] = D == 3 ? match_warp_sum(J[4]) : 0.0f;
+    P.J[5] = D == 3 ? match_warp_sum(J[5]) : 0.0f;
     P.chi2 = a.criterion == 0 ? 0.0f : match_warp_sum(chi);
     return P;
 }
@@ -206,11 +211,12 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
 // (J + lambda D) delta = g, D = diag(J) floored at 1e-12 of its largest
 // entry, by Cramer's rule; the coordinates in `fixed` are held (their rows
 // and columns those of the identity, right-hand side 0); false when singular
-__device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int d, int fixed, float delta[3])
+template <int D>
+__device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int fixed, float delta[3])
 {
     delta[0] = delta[1] = delta[2] = 0.0f;
     float dmax = fmaxf(P.J[0], P.J[3]);
-    if (d == 3) dmax = fmaxf(dmax, P.J[5]);
+    if (D == 3) dmax = fmaxf(dmax, P.J[5]);
     if (!(dmax > 0.0f)) return false;
     const float fl = 1e-12f * dmax;
     const bool f0 = fixed & 1, f1 = fixed & 2, f2 = fixed & 4;
@@ -218,7 +224,7 @@ __device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int
     const float a00 = f0 ? 1.0f : fmaf(lambda, fmaxf(P.J[0], fl), P.J[0]);
     const float a11 = f1 ? 1.0f : fmaf(lambda, fmaxf(P.J[3], fl), P.J[3]);
     const float a01 = f0 || f1 ? 0.0f : P.J[1];
-    if (d == 2) {
+    if (D == 2) {
         const float det = a00 * a11 - a01 * a01;
         if (!(fabsf(det) > 0.0f)) return false;
         delta[0] = (g0 * a11 - a01 * g1) / det;
@@ -238,7 +244,7 @@ __device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int
     return true;
 }
 
-template <int TYPE>
+template <int TYPE, int D>
 __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __grid_constant__ MinArgs a)
 {
     extern __shared__ float smem[];
@@ -250,7 +256,6 @@ __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __gri
     float *s_ep = s_act + n_s;                    // eta at the current point
     float *s_eq = s_ep + n_s;                     // eta at the trial point
     float *s_g = s_eq + n_s;                      // its gradient [n_s][3]
-    const int d = lrf_is_3d(TYPE) && a.fit_z ? 3 : 2;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     for (long e = (long)blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_e; e += warps) {
         float S, p[3];
@@ -267,22 +272,22 @@ __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __gri
             continue;
         }
         const float tau = ldexpf(S, -18);
-        PointSums P = point_pass<TYPE>(a, s_sig, s_act, s_ep, s_eq, s_g, p, d, S, false, lane);
+        PointSums P = point_pass<TYPE, D>(a, s_sig, s_act, s_ep, s_eq, s_g, p, S, false, lane);
         for (int i = lane; i < n_s; i += 32) s_ep[i] = s_eq[i];
         float lambda = a.lambda0;
         int used = -a.max_iter;
         for (int it = 1; it <= a.max_iter; ++it) {
             float delta[3];
-            bool okd = solve_step(P, lambda, d, 0, delta);
-            const int fixed = okd ? active_set<TYPE>(L, p, delta, d) : 0;
-            if (fixed) okd = solve_step(P, lambda, d, fixed, delta);
+            bool okd = solve_step<D>(P, lambda, 0, delta);
+            const int fixed = okd ? active_set<TYPE, D>(L, p, delta) : 0;
+            if (fixed) okd = solve_step<D>(P, lambda, fixed, delta);
             float q[3] = {p[0] + delta[0], p[1] + delta[1], p[2] + delta[2]};
             clamp_box<TYPE>(L, q);
             bool acc = okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
                        defined_warp<TYPE>(L, s_act, q[0], q[1], q[2], lane);
             PointSums Q;
             if (acc) {
-                Q = point_pass<TYPE>(a, s_sig, s_act, s_ep, s_eq, s_g, q, d, S, true, lane);
+                Q = point_pass<TYPE, D>(a, s_sig, s_act, s_ep, s_eq, s_g, q, S, true, lane);
                 const float dC = a.criterion == 0
                                      ? 0.6931471805599453f * Q.lsum - S * log1pf(Q.dHrel / P.H)
                                      : P.chi2 - Q.chi2;
@@ -370,7 +375,6 @@ int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_mi
     MinArgs a;
     a.L = lrf->dev;
     a.criterion = P.criterion;
-    a.fit_z = P.fit_z;
     a.max_iter = P.max_iter;
     a.tol = P.tol;
     a.lambda0 = P.lambda0;
@@ -398,13 +402,24 @@ int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_mi
     long blocks = (n_e + wpb - 1) / wpb;
     const long cap = (long)ctx->n_sm * 16;
     if (blocks > cap) blocks = cap;
+    const bool z = P.fit_z != 0;
+    const unsigned g = (unsigned)blocks, t = 32u * wpb;
     switch (lrf->type) {
-    case ANTS_LRF_RADIAL: minimize_kernel<ANTS_LRF_RADIAL><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    case ANTS_LRF_XY: minimize_kernel<ANTS_LRF_XY><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    case ANTS_LRF_XYZ: minimize_kernel<ANTS_LRF_XYZ><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    case ANTS_LRF_COMPOSITE: minimize_kernel<ANTS_LRF_COMPOSITE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    case ANTS_LRF_AXIAL_Z: minimize_kernel<ANTS_LRF_AXIAL_Z><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    default: minimize_kernel<ANTS_LRF_SLICED><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_RADIAL: minimize_kernel<ANTS_LRF_RADIAL, 2><<<g, t, smem, s>>>(a); break;
+    case ANTS_LRF_XY: minimize_kernel<ANTS_LRF_XY, 2><<<g, t, smem, s>>>(a); break;
+    case ANTS_LRF_COMPOSITE: minimize_kernel<ANTS_LRF_COMPOSITE, 2><<<g, t, smem, s>>>(a); break;
+    case ANTS_LRF_XYZ:
+        if (z) minimize_kernel<ANTS_LRF_XYZ, 3><<<g, t, smem, s>>>(a);
+        else minimize_kernel<ANTS_LRF_XYZ, 2><<<g, t, smem, s>>>(a);
+        break;
+    case ANTS_LRF_AXIAL_Z:
+        if (z) minimize_kernel<ANTS_LRF_AXIAL_Z, 3><<<g, t, smem, s>>>(a);
+        else minimize_kernel<ANTS_LRF_AXIAL_Z, 2><<<g, t, smem, s>>>(a);
+        break;
+    default:
+        if (z) minimize_kernel<ANTS_LRF_SLICED, 3><<<g, t, smem, s>>>(a);
+        else minimize_kernel<ANTS_LRF_SLICED, 2><<<g, t, smem, s>>>(a);
+        break;
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "minimize_kernel launch");
