@@ -486,6 +486,122 @@ def minimize(lrf: Lrf, sig, variant: Variant, params: Minimize, z0: float = 0.0,
     return dict(xyz=xyz, E=E, logL=logL, status=status, n_iter=n_iter)
 
 
+_ML = 8  # layers of an optical stack, at most
+
+
+class _Optics(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("z", C.c_double * (_ML + 1)), ("n", C.c_double * _ML),
+                ("abs_len", C.c_double * _ML), ("ray_len", C.c_double * _ML), ("n_below", C.c_double),
+                ("n_above", C.c_double), ("half_x", C.c_double), ("half_y", C.c_double),
+                ("p_abs", C.c_double * (_ML + 1)), ("p_spec", C.c_double * (_ML + 1)),
+                ("p_diff", C.c_double * (_ML + 1)), ("n_sensors", C.c_int), ("sensor_xy", _D),
+                ("sensor_size", C.c_double), ("n_sensor", C.c_double), ("qe", _D), ("n_ang", C.c_int), ("ang", _D),
+                ("max_cycles", C.c_int), ("pre_reject", C.c_int)]
+
+
+# photon outcomes (>= 0: the detecting sensor)
+PH_ABSORBED, PH_ESCAPED, PH_MAX_CYCLES, PH_UNDETECTED, PH_REJECTED = -1, -2, -3, -4, -5
+
+
+@dataclass
+class Optics:
+    """A stack of horizontal slabs (Sec. 4.2.3, 4.2.4, 4.2.6, 3.5): boundaries
+    z[0] < ... < z[K], per layer the refractive index and the absorption and
+    Rayleigh lengths (0 = none), the media below and above, the lateral
+    extent, custom interface probabilities per boundary (absorb, specular,
+    diffuse), square sensor windows of side sensor_size on z[0] with their
+    index, QE and a relative angular response, the cycle limit and the
+    pre-rejection switch."""
+
+    z: tuple
+    n: tuple
+    abs_len: tuple
+    ray_len: tuple
+    sensor_xy: np.ndarray
+    sensor_size: float
+    qe: np.ndarray
+    n_below: float = 1.0
+    n_above: float = 1.0
+    half_x: float = 1e9
+    half_y: float = 1e9
+    p_abs: tuple = ()
+    p_spec: tuple = ()
+    p_diff: tuple = ()
+    n_sensor: float = 1.5
+    ang: np.ndarray | None = None
+    max_cycles: int = 1000
+    pre_reject: int = 0
+    _keep: list = field(default_factory=list, repr=False)
+
+    def _struct(self) -> _Optics:
+        K = len(self.n)
+        o = _Optics()
+        o.n_layers = K
+        pad = lambda v, m: list(v) + [0.0] * (m - len(v))
+        o.z[:] = pad(self.z, _ML + 1)
+        o.n[:] = pad(self.n, _ML)
+        o.abs_len[:] = pad(self.abs_len, _ML)
+        o.ray_len[:] = pad(self.ray_len, _ML)
+        o.n_below, o.n_above, o.half_x, o.half_y = self.n_below, self.n_above, self.half_x, self.half_y
+        o.p_abs[:] = pad(self.p_abs, _ML + 1)
+        o.p_spec[:] = pad(self.p_spec, _ML + 1)
+        o.p_diff[:] = pad(self.p_diff, _ML + 1)
+        sxy = _f64(self.sensor_xy)
+        qe = _f64(self.qe)
+        ang = _f64(self.ang) if self.ang is not None else None
+        self._keep[:] = [sxy, qe, ang]
+        o.n_sensors = sxy.shape[0]
+        o.sensor_xy, o.qe = _d(sxy), _d(qe)
+        o.sensor_size, o.n_sensor = self.sensor_size, self.n_sensor
+        o.n_ang = 0 if ang is None else ang.shape[0]
+        o.ang = _d(ang) if ang is not None else C.cast(None, _D)
+        o.max_cycles, o.pre_reject = int(self.max_cycles), int(self.pre_reject)
+        return o
+
+
+def _olib(mutant=0):
+    L = lib(mutant)
+    if not getattr(L, "_opt_declared", False):
+        L.or_fresnel.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_fresnel.restype = C.c_double
+        L.or_rayleigh_mu.argtypes = [C.c_double]
+        L.or_rayleigh_mu.restype = C.c_double
+        L.or_trace_photons.argtypes = [C.POINTER(_Optics), C.c_long, _D, C.c_long, C.c_uint64, _I, _I]
+        L.or_turn_dir.argtypes = [_D, C.c_double, C.c_double, _D]
+        L._opt_declared = True
+    return L
+
+
+def fresnel(n1: float, n2: float, ci: float, mutant: int = 0) -> float:
+    """Unpolarised Fresnel reflection coefficient from n1 into n2 at incidence cosine ci."""
+    return _olib(mutant).or_fresnel(float(n1), float(n2), float(ci))
+
+
+def rayleigh_mu(u: float, mutant: int = 0) -> float:
+    """cos(theta) of the Rayleigh phase function at the CDF value u."""
+    return _olib(mutant).or_rayleigh_mu(float(u))
+
+
+def turn_dir(d, mu: float, phi: float, mutant: int = 0) -> np.ndarray:
+    """The unit direction at angle acos(mu) from d and azimuth phi about it."""
+    d = _f64(d)
+    out = np.empty(3)
+    _olib(mutant).or_turn_dir(_d(d), float(mu), float(phi), _d(out))
+    return out
+
+
+def trace_photons(optics: Optics, src_xyz, n_photons: int, seed: int, want_outcome: bool = False, mutant: int = 0):
+    """n_photons photons from each source [n_src, 3]: counts [n_src, n_sensors]
+    and, with want_outcome, every photon's outcome [n_src, n_photons]."""
+    src = _f64(np.atleast_2d(src_xyz))
+    o = optics._struct()
+    counts = np.empty((src.shape[0], o.n_sensors), dtype=np.int32)
+    out = np.empty((src.shape[0], n_photons), dtype=np.int32) if want_outcome else None
+    _olib(mutant).or_trace_photons(C.byref(o), src.shape[0], _d(src), int(n_photons), int(seed), _i(counts),
+                                   _i(out) if out is not None else C.cast(None, _I))
+    return (counts, out) if want_outcome else counts
+
+
 def brute_force(lrf: Lrf, sig, x_rng, nx, y_rng, ny, z=0.0, mutant: int = 0):
     sig = _f64(sig)
     n = sig.shape[0]

@@ -1762,6 +1762,258 @@ static double or_next_u(or_stream *s)
     return or_u01(s->buf[s->pos++]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Optical photon transport in a stack of horizontal slabs (Sec. 4.2.3     */
+/* photon tracing, 4.2.4 detection, 4.2.6 pre-rejection; Sec. 3.5 custom    */
+/* interface properties).  Photons are emitted isotropically from a point; */
+/* each tracing cycle finds the next interface, draws absorption and        */
+/* Rayleigh ranges, and at an interface applies the custom properties, then */
+/* Fresnel reflection (unpolarised) or Snell refraction.  Sensors are       */
+/* square windows on the bottom boundary.                                   */
+/* ------------------------------------------------------------------------ */
+
+#define OR_OPT_MAX_LAYERS 8
+#define OR_PI 3.14159265358979323846
+#define OR_OPT_TAG 0x0F7105u
+
+typedef struct {
+    int n_layers;
+    double z[OR_OPT_MAX_LAYERS + 1];    /* boundaries, increasing */
+    double n[OR_OPT_MAX_LAYERS];        /* refractive index per layer */
+    double abs_len[OR_OPT_MAX_LAYERS];  /* absorption length, 0 = none */
+    double ray_len[OR_OPT_MAX_LAYERS];  /* Rayleigh mean free path, 0 = none */
+    double n_below, n_above;            /* media outside the stack */
+    double half_x, half_y;              /* lateral extent of the stack */
+    double p_abs[OR_OPT_MAX_LAYERS + 1], p_spec[OR_OPT_MAX_LAYERS + 1], p_diff[OR_OPT_MAX_LAYERS + 1];
+    int n_sensors;
+    const double *sensor_xy;            /* [n_sensors][2] window centres on z[0] */
+    double sensor_size;                 /* side of the square windows */
+    double n_sensor;                    /* window index */
+    const double *qe;                   /* [n_sensors] */
+    int n_ang;                          /* angular response samples (0: none) */
+    const double *ang;                  /* [n_ang] at theta_j = j (pi/2) / (n_ang - 1) */
+    int max_cycles;
+    int pre_reject;
+} or_optics;
+
+/* outcome codes of a photon (>= 0: the detecting sensor) */
+#define OR_PH_ABSORBED -1
+#define OR_PH_ESCAPED -2
+#define OR_PH_MAX_CYCLES -3
+#define OR_PH_UNDETECTED -4 /* entered a sensor, failed the detection test */
+#define OR_PH_REJECTED -5   /* discarded before tracing (pre-rejection) */
+
+/* Fresnel reflection coefficient for unpolarised light, the mean of the s
+ * and p coefficients, from medium n1 into n2 at incidence cosine ci; 1
+ * beyond the critical angle. */
+double or_fresnel(double n1, double n2, double ci)
+{
+    double si2 = 1.0 - ci * ci;
+    double st2 = (n1 / n2) * (n1 / n2) * si2;
+    if (st2 >= 1.0) return 1.0;
+    double ct = sqrt(1.0 - st2);
+#if OR_MUTANT == 25
+    double rs = (n1 * ci - n2 * ct) / (n1 * ct + n2 * ci);
+#else
+    double rs = (n1 * ci - n2 * ct) / (n1 * ci + n2 * ct);
+#endif
+    double rp = (n1 * ct - n2 * ci) / (n1 * ct + n2 * ci);
+    return 0.5 * (rs * rs + rp * rp);
+}
+
+/* cos(theta) drawn from the Rayleigh phase function, density (3/8)(1 +
+ * mu^2) on [-1, 1]: the CDF (mu^3 + 3 mu + 4) / 8 = u inverted by Cardano's
+ * formula for the depressed cubic mu^3 + 3 mu + (4 - 8u) = 0. */
+double or_rayleigh_mu(double u)
+{
+    double q = 4.0 * u - 2.0, r = sqrt(q * q + 1.0);
+    return cbrt(q + r) + cbrt(q - r);
+}
+
+/* a unit direction at angle acos(mu) from d and azimuth phi about it */
+static void or_turn(double d[3], double mu, double phi)
+{
+    double s = sqrt(fmax(0.0, 1.0 - mu * mu)), cp = cos(phi), sp = sin(phi);
+    double nx, ny, nz;
+    if (fabs(d[2]) > 0.99999) {
+        double sg = d[2] > 0.0 ? 1.0 : -1.0;
+        nx = s * cp;
+        ny = s * sp;
+        nz = sg * mu;
+    } else {
+        double a = sqrt(1.0 - d[2] * d[2]);
+        nx = mu * d[0] + s * (d[0] * d[2] * cp - d[1] * sp) / a;
+        ny = mu * d[1] + s * (d[1] * d[2] * cp + d[0] * sp) / a;
+        nz = mu * d[2] - s * a * cp;
+    }
+    d[0] = nx;
+    d[1] = ny;
+    d[2] = nz;
+}
+
+/* or_turn on a copy of d (exported for the pins) */
+void or_turn_dir(const double d_in[3], double mu, double phi, double out[3])
+{
+    for (int c = 0; c < 3; ++c) out[c] = d_in[c];
+    or_turn(out, mu, phi);
+}
+
+/* relative angular response at incidence cosine ci (linear in the angle) */
+static double or_ang_resp(const or_optics *O, double ci)
+{
+    if (O->n_ang < 2) return 1.0;
+    double th = acos(fmin(1.0, fmax(0.0, ci))) / (0.5 * OR_PI) * (double)(O->n_ang - 1);
+    int j = (int)floor(th);
+    if (j >= O->n_ang - 1) return O->ang[O->n_ang - 1];
+    double w = th - (double)j;
+    return (1.0 - w) * O->ang[j] + w * O->ang[j + 1];
+}
+
+/* the sensor whose window contains (x, y) on the bottom boundary, or -1 */
+static int or_sensor_at(const or_optics *O, double x, double y)
+{
+    double h = 0.5 * O->sensor_size;
+    for (int i = 0; i < O->n_sensors; ++i) {
+#if OR_MUTANT == 26
+        if (fabs(x - O->sensor_xy[2 * i]) <= O->sensor_size && fabs(y - O->sensor_xy[2 * i + 1]) <= O->sensor_size)
+#else
+        if (fabs(x - O->sensor_xy[2 * i]) <= h && fabs(y - O->sensor_xy[2 * i + 1]) <= h)
+#endif
+            return i;
+    }
+    return -1;
+}
+
+/* the largest detection probability of any sensor (pre-rejection) */
+static double or_pmax(const or_optics *O)
+{
+    double a = 0.0, q = 0.0;
+    for (int i = 0; i < O->n_sensors; ++i) q = O->qe[i] > q ? O->qe[i] : q;
+    if (O->n_ang < 2) a = 1.0;
+    for (int j = 0; j < O->n_ang; ++j) a = O->ang[j] > a ? O->ang[j] : a;
+    return q * a;
+}
+
+/* One photon of source src_index from (x, y, z), photon index ph. */
+static int or_trace_photon(const or_optics *O, uint64_t seed, long src_index, long ph, double x, double y, double z)
+{
+    or_stream st;
+    or_stream_init(&st, seed, (long)(((uint64_t)src_index << 32) | (uint64_t)ph), OR_OPT_TAG);
+    double u_det = -1.0;
+    if (O->pre_reject) {
+        u_det = or_next_u(&st);
+#if OR_MUTANT == 27
+        if (u_det < or_pmax(O)) return OR_PH_REJECTED;
+#else
+        if (!(u_det < or_pmax(O))) return OR_PH_REJECTED;
+#endif
+    }
+    /* layer of the source: z[k] <= z < z[k+1] (the top boundary belongs to the top layer) */
+    int k = 0;
+    while (k < O->n_layers - 1 && z >= O->z[k + 1]) ++k;
+    double r[3] = {x, y, z}, d[3];
+    {
+        double mu = 2.0 * or_next_u(&st) - 1.0, phi = 2.0 * OR_PI * or_next_u(&st);
+        double s = sqrt(fmax(0.0, 1.0 - mu * mu));
+        d[0] = s * cos(phi);
+        d[1] = s * sin(phi);
+        d[2] = mu;
+    }
+    for (int cyc = 0; cyc < O->max_cycles; ++cyc) {
+        /* distance to the next interface: the layer's boundaries, the lateral walls */
+        double tz = INFINITY, tw = INFINITY;
+        int b = -1;
+        if (d[2] > 0.0) { tz = (O->z[k + 1] - r[2]) / d[2]; b = k + 1; }
+        else if (d[2] < 0.0) { tz = (O->z[k] - r[2]) / d[2]; b = k; }
+        if (d[0] != 0.0) tw = ((d[0] > 0.0 ? O->half_x : -O->half_x) - r[0]) / d[0];
+        if (d[1] != 0.0) {
+            double ty = ((d[1] > 0.0 ? O->half_y : -O->half_y) - r[1]) / d[1];
+            tw = ty < tw ? ty : tw;
+        }
+        /* random ranges of absorption and Rayleigh scattering */
+        double ua = or_next_u(&st), ur = or_next_u(&st);
+#if OR_MUTANT == 28
+        double sa = O->abs_len[k] > 0.0 ? O->abs_len[k] * ua : INFINITY;
+#else
+        double sa = O->abs_len[k] > 0.0 ? -O->abs_len[k] * log(ua) : INFINITY;
+#endif
+        double sr = O->ray_len[k] > 0.0 ? -O->ray_len[k] * log(ur) : INFINITY;
+        double t = tz < tw ? tz : tw, s = sa < sr ? sa : sr;
+        if (s < t) {
+            for (int c = 0; c < 3; ++c) r[c] += s * d[c];
+            if (sa <= sr) return OR_PH_ABSORBED;
+            double mu = or_rayleigh_mu(or_next_u(&st)), phi = 2.0 * OR_PI * or_next_u(&st);
+            or_turn(d, mu, phi);
+            continue;
+        }
+        if (tw <= tz) return OR_PH_ESCAPED; /* through a lateral wall */
+        for (int c = 0; c < 3; ++c) r[c] += tz * d[c];
+        r[2] = O->z[b]; /* on the boundary */
+        double ci = fabs(d[2]);
+        int sens = b == 0 ? or_sensor_at(O, r[0], r[1]) : -1;
+        if (sens >= 0) {
+            /* into the sensor's window (Fresnel), then the detection test */
+            if (or_next_u(&st) < or_fresnel(O->n[k], O->n_sensor, ci)) {
+                d[2] = -d[2];
+                continue;
+            }
+            double pd = O->qe[sens] * or_ang_resp(O, ci);
+            if (u_det < 0.0) u_det = or_next_u(&st);
+            return u_det < pd ? sens : OR_PH_UNDETECTED;
+        }
+        double pa = O->p_abs[b], ps = O->p_spec[b], pf = O->p_diff[b];
+        if (pa + ps + pf > 0.0) {
+            double u = or_next_u(&st);
+            if (u < pa) return OR_PH_ABSORBED;
+            if (u < pa + ps) {
+                d[2] = -d[2];
+                continue;
+            }
+            if (u < pa + ps + pf) {
+                /* Lambertian: cosine-weighted about the normal into layer k */
+                double mu = sqrt(or_next_u(&st)), phi = 2.0 * OR_PI * or_next_u(&st);
+                double sn = sqrt(fmax(0.0, 1.0 - mu * mu));
+                d[0] = sn * cos(phi);
+                d[1] = sn * sin(phi);
+                d[2] = b == k + 1 ? -mu : mu;
+                continue;
+            }
+        }
+        /* Fresnel reflection or Snell refraction into the next medium */
+        double n1 = O->n[k];
+        double n2 = b == k + 1 ? (b == O->n_layers ? O->n_above : O->n[k + 1]) : (b == 0 ? O->n_below : O->n[k - 1]);
+        if (or_next_u(&st) < or_fresnel(n1, n2, ci)) {
+            d[2] = -d[2];
+            continue;
+        }
+        if (b == 0 || b == O->n_layers) return OR_PH_ESCAPED; /* out of the stack */
+        double eta = n1 / n2, ct = sqrt(fmax(0.0, 1.0 - eta * eta * (1.0 - ci * ci)));
+        d[0] *= eta;
+        d[1] *= eta;
+        d[2] = d[2] > 0.0 ? ct : -ct;
+        k = b == k + 1 ? k + 1 : k - 1;
+    }
+    return OR_PH_MAX_CYCLES;
+}
+
+/* Photons of n_src point sources, n_ph each: detected counts per sensor
+ * counts[src][sensor] and, when outcome is not NULL, every photon's
+ * outcome[src][photon]. */
+void or_trace_photons(const or_optics *O, long n_src, const double *src_xyz, long n_ph, uint64_t seed, int *counts,
+                      int *outcome)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long q = 0; q < n_src; ++q) {
+        int *c = counts + q * O->n_sensors;
+        for (int i = 0; i < O->n_sensors; ++i) c[i] = 0;
+        for (long p = 0; p < n_ph; ++p) {
+            int o = or_trace_photon(O, seed, q, p, src_xyz[3 * q], src_xyz[3 * q + 1], src_xyz[3 * q + 2]);
+            if (o >= 0) c[o]++;
+            if (outcome) outcome[q * n_ph + p] = o;
+        }
+    }
+}
+
 /* Poisson(lam): inversion of the CDF for lam < 10; Hormann's transformed
  * rejection with squeeze (PTRS, Insurance: Mathematics and Economics 12,
  * 1993) otherwise. */

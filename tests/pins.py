@@ -1118,3 +1118,154 @@ def pin_minimize_status(mutant=0):
 
 
 ALL_PINS += [pin_lrf_grad, pin_minimize_noise_free, pin_minimize_stationary, pin_minimize_status]
+
+
+# --------------------------------------------------------------------------
+# Optical photon transport (Sec. 4.2.3, 4.2.4, 4.2.6, 3.5)
+# --------------------------------------------------------------------------
+
+
+def _corner_solid_angle(x, y, d):
+    """Solid angle of the rectangle [0, x] x [0, y] seen from height d above
+    its corner (x, y >= 0)."""
+    return np.arctan(x * y / (d * np.sqrt(x * x + y * y + d * d)))
+
+
+def _rect_solid_angle(x0, x1, y0, y1, d):
+    """Solid angle of [x0, x1] x [y0, y1] seen from (0, 0, d): signed sums of
+    corner rectangles."""
+    def c(x, y):
+        return np.sign(x) * np.sign(y) * _corner_solid_angle(abs(x), abs(y), d)
+    return c(x1, y1) - c(x0, y1) - c(x1, y0) + c(x0, y0)
+
+
+def _bare_optics(**kw):
+    """One vacuum-like layer (n = 1 everywhere, no reflection) over a 2 x 2
+    array of 6 mm windows, pitch 8 mm, QE 1."""
+    sxy = np.array([[-4.0, -4.0], [4.0, -4.0], [-4.0, 4.0], [4.0, 4.0]])
+    args = dict(z=(0.0, 30.0), n=(1.0,), abs_len=(0.0,), ray_len=(0.0,), sensor_xy=sxy, sensor_size=6.0,
+                qe=np.ones(4), n_sensor=1.0)
+    args.update(kw)
+    return oracle.Optics(**args)
+
+
+def _binomial_ok(k, n, p, sig=5.0):
+    return abs(k - n * p) <= sig * np.sqrt(n * p * (1 - p)) + 1.0
+
+
+def pin_optics_solid_angle(mutant=0):
+    """Without refraction, reflection or attenuation a window detects the
+    fraction Omega / 4 pi of the photons, Omega the closed-form solid angle of
+    the rectangle (sums of corner terms arctan(x y / (d sqrt(x^2 + y^2 +
+    d^2)))); within 5 binomial sigmas for two source positions."""
+    O = _bare_optics()
+    n = 200_000
+    for src in ((1.5, -0.5, 7.0), (-6.0, 3.0, 12.0)):
+        c = oracle.trace_photons(O, [src], n, seed=11, mutant=mutant)[0]
+        for i, (sx, sy) in enumerate(O.sensor_xy):
+            om = _rect_solid_angle(sx - 3.0 - src[0], sx + 3.0 - src[0], sy - 3.0 - src[1], sy + 3.0 - src[1],
+                                   src[2])
+            assert _binomial_ok(c[i], n, om / (4 * np.pi)), (src, i, c[i], n * om / (4 * np.pi))
+
+
+def pin_optics_absorption(mutant=0):
+    """With an absorption length L the detected fraction is (1 / 4 pi) times
+    the integral over the window of d exp(-r / L) / r^3 (midpoint rule on a
+    400 x 400 grid); within 5 binomial sigmas."""
+    L = 15.0
+    O = _bare_optics(abs_len=(L,))
+    n = 200_000
+    src = (2.0, 1.0, 10.0)
+    c = oracle.trace_photons(O, [src], n, seed=12, mutant=mutant)[0]
+    m = 400
+    for i, (sx, sy) in enumerate(O.sensor_xy):
+        u = (np.arange(m) + 0.5) / m * 6.0 - 3.0
+        X, Y = np.meshgrid(sx + u - src[0], sy + u - src[1])
+        r = np.sqrt(X ** 2 + Y ** 2 + src[2] ** 2)
+        frac = (src[2] * np.exp(-r / L) / r ** 3).sum() * (6.0 / m) ** 2 / (4 * np.pi)
+        assert _binomial_ok(c[i], n, frac), (i, c[i], n * frac)
+    # every photon ends in exactly one class
+    _, o = oracle.trace_photons(O, [src], 5000, seed=12, want_outcome=True, mutant=mutant)
+    assert np.all((o >= -2) & (o < 4))
+
+
+def pin_fresnel(mutant=0):
+    """The unpolarised Fresnel coefficient: ((n1 - n2) / (n1 + n2))^2 at normal
+    incidence, 0 between equal media, 1 beyond the critical angle, half the s
+    term sin^2(ti - tt) at Brewster's angle (p term 0), the same for the
+    reversed ray (n2 into n1 at the refracted angle), 1 at grazing incidence."""
+    f = lambda a, b, c: oracle.fresnel(a, b, c, mutant)
+    for n1, n2 in ((1.0, 1.5), (1.5, 1.0), (1.33, 1.8)):
+        assert abs(f(n1, n2, 1.0) - ((n1 - n2) / (n1 + n2)) ** 2) < 1e-15
+        assert abs(f(n1, n1, 0.3)) < 1e-15
+        tb = np.arctan(n2 / n1)
+        tt = np.arcsin(n1 / n2 * np.sin(tb))
+        assert abs(f(n1, n2, np.cos(tb)) - 0.5 * np.sin(tb - tt) ** 2) < 1e-12
+        for ti in (0.2, 0.5, 0.7):
+            st = n1 / n2 * np.sin(ti)
+            if st < 1:
+                assert abs(f(n1, n2, np.cos(ti)) - f(n2, n1, np.sqrt(1 - st * st))) < 1e-12
+        assert abs(f(n1, n2, 1e-9) - 1.0) < 1e-6
+    assert f(1.5, 1.0, np.cos(0.75)) == 1.0  # beyond asin(1 / 1.5) = 0.7297
+
+
+def pin_rayleigh_and_turn(mutant=0):
+    """The Rayleigh sampler inverts the CDF (mu^3 + 3 mu + 4) / 8 and has the
+    moments E[mu] = 0, E[mu^2] = 2/5 (midpoint grid of 20001 u values); a
+    turned direction is a unit vector at cosine mu from the old one."""
+    u = (np.arange(20001) + 0.5) / 20001
+    mu = np.array([oracle.rayleigh_mu(x, mutant) for x in u])
+    assert np.abs((mu ** 3 + 3 * mu + 4) / 8 - u).max() < 1e-12
+    assert abs(mu.mean()) < 1e-6 and abs((mu ** 2).mean() - 0.4) < 1e-6
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        m, ph = rng.uniform(-1, 1), rng.uniform(0, 2 * np.pi)
+        t = oracle.turn_dir(d, m, ph, mutant)
+        assert abs(np.linalg.norm(t) - 1) < 1e-12 and abs(t @ d - m) < 1e-12
+    t = oracle.turn_dir(np.array([0.0, 0.0, 1.0]), 0.3, 0.0, mutant)
+    assert abs(t[2] - 0.3) < 1e-12
+
+
+def pin_optics_fresnel_mc(mutant=0):
+    """A source in a layer of index 1.5 over one window of index 1 that
+    covers the whole floor, an absorbing ceiling: photons going down enter
+    the window with probability 1 - R(mu) (none beyond the critical angle),
+    reflected ones are absorbed above, so the detected fraction is (1/2)
+    int_0^1 (1 - R(mu)) d mu (Simpson, 4001 points); within 5 sigmas."""
+    O = oracle.Optics(z=(0.0, 10.0), n=(1.5,), abs_len=(0.0,), ray_len=(0.0,), sensor_xy=np.array([[0.0, 0.0]]),
+                      sensor_size=1e7, qe=np.ones(1), n_sensor=1.0, p_abs=(0.0, 1.0))
+    n = 200_000
+    c = oracle.trace_photons(O, [(0.0, 0.0, 5.0)], n, seed=13, mutant=mutant)[0, 0]
+    mu = np.linspace(0.0, 1.0, 4001)
+    T = np.array([1.0 - oracle.fresnel(1.5, 1.0, m) for m in mu])
+    w = np.ones(4001)
+    w[1:-1:2], w[2:-1:2] = 4, 2
+    frac = 0.5 * (w * T).sum() / (3 * 4000)
+    assert _binomial_ok(c, n, frac), (c, n * frac)
+
+
+def pin_optics_diffuse_and_prereject(mutant=0):
+    """A Lambertian ceiling that reflects half of the photons and absorbs the
+    rest over a floor-wide window (n = 1 everywhere): 3/4 are detected. With
+    QE 0.25 the pre-rejection mode detects as many as plain tracing (5
+    sigmas), and rejects 3/4 of the photons before tracing."""
+    sxy = np.array([[0.0, 0.0]])
+    O = oracle.Optics(z=(0.0, 10.0), n=(1.0,), abs_len=(0.0,), ray_len=(0.0,), sensor_xy=sxy, sensor_size=1e7,
+                      qe=np.ones(1), n_sensor=1.0, p_abs=(0.0, 0.5), p_diff=(0.0, 0.5))
+    n = 100_000
+    c = oracle.trace_photons(O, [(0.0, 0.0, 5.0)], n, seed=14, mutant=mutant)[0, 0]
+    assert _binomial_ok(c, n, 0.75), c
+    O2 = _bare_optics(qe=np.full(4, 0.25))
+    O3 = _bare_optics(qe=np.full(4, 0.25), pre_reject=1)
+    src = [(1.0, 2.0, 6.0)]
+    a = oracle.trace_photons(O2, src, n, seed=15, mutant=mutant)[0].sum()
+    b, o = oracle.trace_photons(O3, src, n, seed=16, want_outcome=True, mutant=mutant)
+    p = a / n
+    assert abs(b[0].sum() - a) <= 5 * np.sqrt(2 * n * p * (1 - p)), (a, b[0].sum())
+    assert _binomial_ok((o == oracle.PH_REJECTED).sum(), n, 0.75)
+
+
+ALL_PINS += [pin_optics_solid_angle, pin_optics_absorption, pin_fresnel, pin_rayleigh_and_turn, pin_optics_fresnel_mc,
+             pin_optics_diffuse_and_prereject]

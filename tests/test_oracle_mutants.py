@@ -30,6 +30,10 @@ MUTANTS = {
     22: "maximum-likelihood gradient without the -E eta term",
     23: "least-squares gradient weight 1 + s^2/mu^2 instead of 1 - s^2/mu^2",
     24: "minimisation accepting every step inside the rounding band",
+    25: "Fresnel s coefficient with the cosines swapped in its denominator",
+    26: "sensor window test with the full side as half-width",
+    27: "pre-rejection discarding the photons it should trace",
+    28: "absorption range L u instead of -L ln u",
 }
 
 
