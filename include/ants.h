@@ -96,7 +96,7 @@ typedef enum { ANTS_START_COG = 0, ANTS_START_MAX_SENSOR = 1 } ants_start_mode;
 /* Signal element types. */
 /* Element type of signal arrays: FP32, or FP16 (IEEE binary16; widened to
  * FP32 on the device before the search, exactly). */
-typedef enum { ANTS_F32 = 0, ANTS_F16 = 1 } ants_dtype;
+typedef enum { ANTS_F32 = 0, ANTS_F16 = 1, ANTS_F64 = 2 } ants_dtype;
 
 typedef struct ants_ctx ants_ctx;
 typedef struct ants_detector ants_detector;
@@ -774,6 +774,81 @@ ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init, const flo
 /* Number of kernels the calling thread's last successful ants_* call
  * launched (for accounting in benchmarks). */
 ANTS_API long ants_last_launch_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* Optical photon transport (Sec. 4.2.3 photon tracing, 4.2.4 detection,     */
+/* 4.2.6 pre-rejection, Sec. 3.5 custom interface properties)                */
+/* ------------------------------------------------------------------------ */
+
+#define ANTS_OPT_MAX_LAYERS 8
+
+/* A stack of horizontal slabs, laterally bounded by |x| <= half_x, |y| <=
+ * half_y (photons crossing those walls leave the geometry).  Layer k lies
+ * between z[k] < z[k+1] (mm) and has refractive index n[k], absorption
+ * length abs_len[k] and Rayleigh mean free path ray_len[k] (mm; 0 = none).
+ * Below z[0] and above z[n_layers] are media of index n_below and n_above
+ * (photons refracted into them leave the stack).  Boundary b (0..n_layers)
+ * has custom probabilities p_abs[b] (absorption), p_spec[b] (specular
+ * reflection) and p_diff[b] (Lambertian reflection), applied before Fresnel
+ * (sum <= 1; the rest goes to Fresnel).  Sensors: square windows of side
+ * sensor_size centred at sensor_xy_host[i] on the bottom boundary z[0], of
+ * index n_sensor, with quantum efficiency qe_host[i] and, when n_ang >= 2, a
+ * relative angular response ang_host[j] at incidence theta_j = j (pi/2) /
+ * (n_ang - 1), linear in the angle (detection probability QE times the
+ * response).  max_cycles bounds the tracing cycles of a photon; pre_reject
+ * = 1 discards a photon before tracing when its detection uniform is not
+ * below the largest detection probability, and uses that uniform for the
+ * detection test (the same distribution of counts).  Host arrays are read
+ * during the call. */
+typedef struct {
+    int n_layers;
+    double z[ANTS_OPT_MAX_LAYERS + 1];
+    double n[ANTS_OPT_MAX_LAYERS];
+    double abs_len[ANTS_OPT_MAX_LAYERS];
+    double ray_len[ANTS_OPT_MAX_LAYERS];
+    double n_below, n_above;
+    double half_x, half_y;
+    double p_abs[ANTS_OPT_MAX_LAYERS + 1];
+    double p_spec[ANTS_OPT_MAX_LAYERS + 1];
+    double p_diff[ANTS_OPT_MAX_LAYERS + 1];
+    int n_sensors;                 /* 1..256 */
+    const double *sensor_xy_host;  /* [n_sensors][2] */
+    double sensor_size;
+    double n_sensor;
+    const double *qe_host;         /* [n_sensors], 0..1 */
+    int n_ang;                     /* 0 or 2..64 */
+    const double *ang_host;        /* [n_ang], 0..1 */
+    int max_cycles;
+    int pre_reject;
+} ants_optics_params;
+
+/* The outcome of a traced photon: >= 0 the index of the detecting sensor. */
+typedef enum {
+    ANTS_PH_ABSORBED = -1,    /* in a layer or by an interface */
+    ANTS_PH_ESCAPED = -2,     /* out of the stack or through a lateral wall */
+    ANTS_PH_MAX_CYCLES = -3,  /* cycle limit reached */
+    ANTS_PH_UNDETECTED = -4,  /* entered a window, failed the detection test */
+    ANTS_PH_REJECTED = -5     /* discarded before tracing (pre_reject) */
+} ants_photon_outcome;
+
+/* Trace n_photons photons from each of n_src point sources
+ * src_xyz_dev[n_src][3] (FP32, mm; the source's layer: z[k] <= z < z[k+1]).
+ * Each photon draws its uniforms from its own Philox4x32-10 stream with key
+ * seed and counter (photon, source, 0x0F7105, block) in a fixed order:
+ * [pre-rejection uniform], emission cos(theta) = 2u - 1 and phi = 2 pi u,
+ * then per cycle the absorption and Rayleigh uniforms (ranges -L ln u), a
+ * Rayleigh scatter's cos(theta) (phase function 1 + cos^2) and azimuth, at an
+ * interface one uniform for the custom properties (when any is non-zero) and
+ * two for a Lambertian direction, one for Fresnel, and one for the detection
+ * test.  precision ANTS_F64 takes every decision in double precision,
+ * ANTS_F32 in single.  Outputs: counts_dev[n_src][n_sensors] int32 detected
+ * photons (zeroed by the call); outcome_dev (nullable) [n_src][n_photons]
+ * int16 outcomes; eta_dev (nullable) [n_src][n_sensors] FP32 counts /
+ * n_photons (the light response at the source positions, e.g. to fit LRFs).
+ * Asynchronous on `stream`.  Errors: ANTS_E_ARG, ANTS_E_CUDA. */
+ANTS_API int ants_trace_photons(ants_ctx *ctx, const ants_optics_params *params, const float *src_xyz_dev,
+                                long n_src, long n_photons, uint64_t seed, int precision, int32_t *counts_dev,
+                                int16_t *outcome_dev, float *eta_dev, void *stream);
 
 #ifdef __cplusplus
 }

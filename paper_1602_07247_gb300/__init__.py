@@ -32,6 +32,8 @@ ANTS_GEMM_TOPK = 1
 ANTS_MLP_SEEDED = 2
 ANTS_CGS_VARIANT = 3
 ANTS_MINIMIZE = 4
+ANTS_F64 = 2
+ANTS_PH_ABSORBED, ANTS_PH_ESCAPED, ANTS_PH_MAX_CYCLES, ANTS_PH_UNDETECTED, ANTS_PH_REJECTED = -1, -2, -3, -4, -5
 ANTS_CRIT_ML, ANTS_CRIT_LS = 0, 1
 ANTS_START_COG, ANTS_START_MAX_SENSOR = 0, 1
 ANTS_F32 = 0
@@ -143,6 +145,37 @@ class MinimizeParams(C.Structure):
                          None if self._passive is None else self._passive.ctypes.data)
 
 
+_OML = 8  # ANTS_OPT_MAX_LAYERS
+
+
+class OpticsParams(C.Structure):
+    """ants_optics_params (Sec. 4.2.3, 4.2.4, 4.2.6, 3.5): a slab stack over
+    square sensor windows on its bottom boundary."""
+    _fields_ = [("n_layers", C.c_int), ("z", C.c_double * (_OML + 1)), ("n", C.c_double * _OML),
+                ("abs_len", C.c_double * _OML), ("ray_len", C.c_double * _OML), ("n_below", C.c_double),
+                ("n_above", C.c_double), ("half_x", C.c_double), ("half_y", C.c_double),
+                ("p_abs", C.c_double * (_OML + 1)), ("p_spec", C.c_double * (_OML + 1)),
+                ("p_diff", C.c_double * (_OML + 1)), ("n_sensors", C.c_int), ("sensor_xy_host", C.c_void_p),
+                ("sensor_size", C.c_double), ("n_sensor", C.c_double), ("qe_host", C.c_void_p), ("n_ang", C.c_int),
+                ("ang_host", C.c_void_p), ("max_cycles", C.c_int), ("pre_reject", C.c_int)]
+
+    def __init__(self, z, n, abs_len, ray_len, sensor_xy, sensor_size, qe, n_below=1.0, n_above=1.0, half_x=1e9,
+                 half_y=1e9, p_abs=(), p_spec=(), p_diff=(), n_sensor=1.5, ang=None, max_cycles=1000, pre_reject=0):
+        pad = lambda v, m: [float(x) for x in v] + [0.0] * (m - len(v))
+        self._sxy = np.ascontiguousarray(np.asarray(sensor_xy, dtype=np.float64))
+        self._qe = np.ascontiguousarray(np.asarray(qe, dtype=np.float64))
+        self._ang = None if ang is None else np.ascontiguousarray(np.asarray(ang, dtype=np.float64))
+        super().__init__(len(n), (C.c_double * (_OML + 1))(*pad(z, _OML + 1)), (C.c_double * _OML)(*pad(n, _OML)),
+                         (C.c_double * _OML)(*pad(abs_len, _OML)), (C.c_double * _OML)(*pad(ray_len, _OML)),
+                         float(n_below), float(n_above), float(half_x), float(half_y),
+                         (C.c_double * (_OML + 1))(*pad(p_abs, _OML + 1)),
+                         (C.c_double * (_OML + 1))(*pad(p_spec, _OML + 1)),
+                         (C.c_double * (_OML + 1))(*pad(p_diff, _OML + 1)), self._sxy.shape[0],
+                         self._sxy.ctypes.data, float(sensor_size), float(n_sensor), self._qe.ctypes.data,
+                         0 if self._ang is None else self._ang.shape[0],
+                         None if self._ang is None else self._ang.ctypes.data, int(max_cycles), int(pre_reject))
+
+
 class EventCuts(C.Structure):
     """ants_event_cuts (Sec. 5.2): a cut is off when chi2_max <= 0, r_max <= 0
     or its window's upper bound is not above its lower bound."""
@@ -239,6 +272,7 @@ def lib() -> C.CDLL:
         L.ants_lrf_fit_scheme.argtypes = [_VP, _VP, C.c_int, _IP, _DP, _DP, C.c_int, C.c_double, C.c_int, C.c_long,
                                           _DP, _DP, C.c_double, C.POINTER(_VP)]
         L.ants_event_centroid.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP]
+        L.ants_trace_photons.argtypes = [_VP, _VP, _VP, C.c_long, C.c_long, C.c_uint64, C.c_int, _VP, _VP, _VP, _VP]
         L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
         L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
                                         C.POINTER(C.c_long), _VP]
@@ -837,6 +871,29 @@ class Result:
     logL: object
     status: object
     trace: object = None
+
+
+def ants_trace_photons(ctx: int, params: OpticsParams, src_xyz, n_photons: int, seed: int, precision: int, counts,
+                       outcome=None, eta=None, stream=None) -> None:
+    _check(lib().ants_trace_photons(ctx, C.addressof(params), _tptr(src_xyz), int(src_xyz.shape[0]), int(n_photons),
+                                    int(seed), int(precision), _tptr(counts), _tptr(outcome), _tptr(eta),
+                                    _stream_handle(stream)))
+
+
+def trace_photons(ctx: Context, params: OpticsParams, src_xyz, n_photons: int, seed: int, fp64: bool = False,
+                  want_outcome: bool = False, want_eta: bool = False, stream=None):
+    """ants_trace_photons: photons from every source of src_xyz (torch [n_src, 3]
+    float32 on the device); returns counts [n_src, n_sensors] int32 and, on
+    request, the outcomes [n_src, n_photons] int16 and eta = counts / n_photons."""
+    import torch
+    n_src = int(src_xyz.shape[0])
+    dev = src_xyz.device
+    counts = torch.empty((n_src, params.n_sensors), dtype=torch.int32, device=dev)
+    outcome = torch.empty((n_src, n_photons), dtype=torch.int16, device=dev) if want_outcome else None
+    eta = torch.empty((n_src, params.n_sensors), dtype=torch.float32, device=dev) if want_eta else None
+    ants_trace_photons(ctx.handle, params, src_xyz, n_photons, seed, ANTS_F64 if fp64 else ANTS_F32, counts, outcome,
+                       eta, stream)
+    return counts, outcome, eta
 
 
 def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=None, want_trace=False,
