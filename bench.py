@@ -469,6 +469,75 @@ def minimize_run(args, ants, torch, ctx, stream):
                         "E profiled), at most 40 trials, tol 1e-3 mm", **out}
 
 
+def _optics_stack(ants, pre_reject=0):
+    """A 4 x 4 SiPM array (pitch 8 mm, 6 mm windows) under a 2 mm light guide
+    (n 1.5), a 10 mm scintillator (n 1.8, absorption 100 mm, Rayleigh 40 mm)
+    and a 2 mm window (n 1.5) with a diffuse reflector on top; lateral walls
+    at 20 mm, a partly absorbing, partly specular floor between the windows."""
+    g = np.arange(4) * 8.0 - 12.0
+    sxy = np.array([(x, y) for y in g for x in g])
+    qe = 0.2 + 0.1 * np.random.default_rng(4).uniform(size=16)
+    return ants.OpticsParams(z=(0.0, 2.0, 12.0, 14.0), n=(1.5, 1.8, 1.5), abs_len=(200.0, 100.0, 0.0),
+                             ray_len=(0.0, 40.0, 0.0), sensor_xy=sxy, sensor_size=6.0, qe=qe, n_below=1.0,
+                             n_above=1.0, half_x=20.0, half_y=20.0, p_abs=(0.3, 0.0, 0.0, 0.1),
+                             p_spec=(0.2, 0.0, 0.0, 0.0), p_diff=(0.0, 0.0, 0.0, 0.9), n_sensor=1.5,
+                             ang=[1.0, 0.98, 0.9, 0.7, 0.3], max_cycles=200, pre_reject=pre_reject), sxy
+
+
+def optics_run(args, ants, torch, ctx, stream):
+    """Optical photon transport (Sec. 4.2.3-4.2.6): photons/s of the FP32 and
+    FP64 kernels (64 sources x 10^6 photons in the scintillator, with and
+    without pre-rejection), then the chain the simulation serves: light
+    response on a 17 x 17 grid of sources (2 x 10^5 photons each) -> XY LRFs
+    fitted on the device -> 20000 events of 4000 photons traced by the same
+    simulator and reconstructed (plain 11 x 11 x 8) with those LRFs."""
+    P, sxy = _optics_stack(ants)
+    Pr, _ = _optics_stack(ants, pre_reject=1)
+    rng = np.random.default_rng(5)
+    src = torch.tensor(np.stack([rng.uniform(-15, 15, 64), rng.uniform(-15, 15, 64), rng.uniform(2.5, 11.5, 64)],
+                                1).astype(np.float32)).cuda()
+    n_ph = 1_000_000
+    counts = torch.empty((64, 16), dtype=torch.int32, device="cuda")
+    out = {}
+    for name, params, prec in (("fp32", P, ants.ANTS_F32), ("fp64", P, ants.ANTS_F64),
+                               ("fp32_prereject", Pr, ants.ANTS_F32)):
+        ants.ants_trace_photons(ctx.handle, params, src, n_ph, 1, prec, counts, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for r in range(reps):
+            ants.ants_trace_photons(ctx.handle, params, src, n_ph, 2 + r, prec, counts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"photons_per_s": 64 * n_ph / dt, "ms_per_launch": 1e3 * dt,
+                     "detected_frac": float(counts.sum()) / (64 * n_ph)}
+    # light response on a grid -> LRFs -> reconstruction of traced events
+    t0 = time.perf_counter()
+    gx = np.linspace(-16.0, 16.0, 17)
+    grid = np.array([(x, y, 7.0) for y in gx for x in gx], dtype=np.float32)
+    _, _, eta = ants.trace_photons(ctx, P, torch.from_numpy(grid).cuda(), 200_000, 11, want_eta=True)
+    det = ants.Detector(sxy)
+    lrf = ants.Lrf.fit(ctx, det, ants.ANTS_LRF_XY, (8, 8), (-16.0, -16.0), (16.0, 16.0), grid[:, :2].astype(np.float64),
+                       eta.double().cpu().numpy())
+    n_ev = 20000
+    truth = np.stack([rng.uniform(-12, 12, n_ev), rng.uniform(-12, 12, n_ev), np.full(n_ev, 7.0)], 1).astype(np.float32)
+    sig, _, _ = ants.trace_photons(ctx, P, torch.from_numpy(truth).cuda(), 4000, 12)
+    res = ants.reconstruct(ctx, lrf, ants.CgsParams(n_xy=11, iters=8, step_xy=4.0, shrink=0.5), sig.float())
+    torch.cuda.synchronize()
+    ok = res.status.cpu().numpy() == 0
+    d = res.xyz[:, :2].double().cpu().numpy() - truth[:, :2]
+    out["physical_lrf_chain"] = {"grid_sources": int(grid.shape[0]), "photons_per_grid_source": 200_000,
+                                 "events": n_ev, "photons_per_event": 4000,
+                                 "mean_detected_per_event": float(sig.float().sum(1).mean()),
+                                 "ok_frac": float(ok.mean()), "rms_dxy_mm": float(np.sqrt((d[ok] ** 2).sum(1).mean())),
+                                 "seconds": time.perf_counter() - t0}
+    return {"workload": "slab stack over 4 x 4 SiPMs (guide n 1.5 / scintillator n 1.8, absorption 100 mm, "
+                        "Rayleigh 40 mm / window n 1.5, diffuse reflector), 64 sources x 10^6 photons per launch",
+            **out}
+
+
 def schemes_run(args, ants, torch, ctx, stream):
     """The other LRF schemes (Sec. 6.1.1, 6.1.2) on a 4 x 4 SiPM array (pitch
     6 mm), LRFs fitted on the GPU to the closed-form truth (composite: the
@@ -762,6 +831,7 @@ def run_ours(args):
     variants = optional(variants_run, args.no_variants)
     schemes = optional(schemes_run, args.no_schemes)
     minim = optional(minimize_run, args.no_minimize)
+    optics = optional(optics_run, args.no_optics)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -769,7 +839,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
         "iterative_lrf": iterative, "variants_8x8": variants, "lrf_schemes_4x4": schemes,
-        "minimize_8x8": minim,
+        "minimize_8x8": minim, "optics_4x4": optics,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -798,6 +868,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the search variants")
     ap.add_argument("--no-schemes", action="store_true", help="skip the composite, axial+z and sliced LRFs")
     ap.add_argument("--no-minimize", action="store_true", help="skip the continuous minimisation")
+    ap.add_argument("--no-optics", action="store_true", help="skip the optical photon transport")
     ap.add_argument("--iter-events", type=int, default=1_000_000)
     ap.add_argument("--iter-cycles", type=int, default=6)
     ap.add_argument("--batch-steps", type=int, default=1)
