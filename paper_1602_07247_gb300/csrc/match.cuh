@@ -32,21 +32,54 @@ __device__ __forceinline__ double match_warp_sum_d(double v)
     return v;
 }
 
-// Loads event e's signals into s_sig (0 for passive sensors), picks the start
-// (given: start_xyz, nullable), marks the sensors in the match in s_act (1 /
-// 0) and returns ANTS_EVT_OK with their signal sum S and the start, or the
-// event's failure status.  Comparisons that pick the start or a sensor are
-// made in FP64.
-template <int TYPE>
-__device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &m, const float *sig, long e,
-                                              const float *start_xyz, float *s_sig, float *s_act, int lane, float &S,
-                                              float &cx, float &cy, float &cz)
+// Collectives of a group of G lanes (G = 8, 16 or 32; groups are aligned
+// blocks of the warp).  Every lane of the warp calls them together (the
+// callers keep the groups in lockstep), so the full mask is used; butterfly
+// offsets below G stay inside the group, and every lane of a group ends with
+// the same sum.
+template <int G> struct Group {
+    static __device__ __forceinline__ unsigned mask(int lane)
+    {
+        return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    }
+    static __device__ __forceinline__ float sum(float v)
+    {
+        for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+    static __device__ __forceinline__ double sumd(double v)
+    {
+        for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+    static __device__ __forceinline__ bool any(bool p, int lane)
+    {
+        return (__ballot_sync(0xffffffffu, p) & mask(lane)) != 0u;
+    }
+    static __device__ __forceinline__ bool all(bool p, int lane)
+    {
+        const unsigned m = mask(lane);
+        return (__ballot_sync(0xffffffffu, p) & m) == m;
+    }
+};
+
+// The set-up of event e by a group of G lanes (glane = lane within the
+// group): loads the signals into s_sig (0 for passive sensors), picks the
+// start (given: start_xyz, nullable), marks the sensors in the match in
+// s_act (1 / 0) and returns ANTS_EVT_OK with their signal sum S and the
+// start, or the event's failure status.  Comparisons that pick the start or
+// a sensor are made in FP64.  Every lane of the warp runs every collective;
+// an inactive group (no event) reads nothing and returns ANTS_EVT_ZERO_SIGNAL.
+template <int TYPE, int G>
+__device__ __forceinline__ int match_prologue_g(const LrfDev &L, const MatchArgs &m, const float *sig, long e,
+                                                bool active, const float *start_xyz, float *s_sig, float *s_act,
+                                                int lane, float &S, float &cx, float &cy, float &cz)
 {
-    const int n_s = L.n_s;
+    const int n_s = L.n_s, glane = lane & (G - 1);
     bool bad = false;
     double tot = 0.0, W = 0.0, X = 0.0, Y = 0.0, bv = -1.0;
     int bi = 0x7fffffff;
-    for (int i = lane; i < n_s; i += 32) {
+    for (int i = glane; active && i < n_s; i += G) {
         float s = sig[e * n_s + i];
         if (m.passive[i]) s = 0.0f;
         else if (!isfinite(s) || s < 0.0f) bad = true;
@@ -61,29 +94,30 @@ __device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &
             bi = i;
         }
     }
-    if (__any_sync(0xffffffffu, bad)) return ANTS_EVT_BAD_SIGNAL;
-    tot = match_warp_sum_d(tot);
-    if (!(tot > 0.0)) return ANTS_EVT_ZERO_SIGNAL;
+    bad = Group<G>::any(bad, lane);
+    tot = Group<G>::sumd(tot);
+    int st = !active ? ANTS_EVT_ZERO_SIGNAL : bad ? ANTS_EVT_BAD_SIGNAL : !(tot > 0.0) ? ANTS_EVT_ZERO_SIGNAL
+                                                                                     : ANTS_EVT_OK;
     cz = lrf_is_3d(TYPE) ? m.z0 : 0.0f;
-    if (start_xyz) {
+    for (int o = G / 2; o; o >>= 1) {  // the largest s/g, ties to the lowest index
+        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > bv || (v2 == bv && i2 < bi)) {
+            bv = v2;
+            bi = i2;
+        }
+    }
+    W = Group<G>::sumd(W);
+    X = Group<G>::sumd(X);
+    Y = Group<G>::sumd(Y);
+    if (start_xyz && active) {
         cx = start_xyz[3 * e];
         cy = start_xyz[3 * e + 1];
         cz = start_xyz[3 * e + 2];
     } else if (m.start == 1) {
-        for (int o = 16; o; o >>= 1) {  // the largest s/g, ties to the lowest index
-            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (v2 > bv || (v2 == bv && i2 < bi)) {
-                bv = v2;
-                bi = i2;
-            }
-        }
-        cx = L.sxy[2 * bi];
-        cy = L.sxy[2 * bi + 1];
+        cx = bi < n_s ? L.sxy[2 * bi] : 0.0f;
+        cy = bi < n_s ? L.sxy[2 * bi + 1] : 0.0f;
     } else {
-        W = match_warp_sum_d(W);
-        X = match_warp_sum_d(X);
-        Y = match_warp_sum_d(Y);
         cx = (float)(X / W);
         cy = (float)(Y / W);
     }
@@ -92,7 +126,7 @@ __device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &
         cy = fminf(fmaxf(cy, L.lo[1]), L.hi[1]);
     }
     float Sp = 0.0f;
-    for (int i = lane; i < n_s; i += 32) {
+    for (int i = glane; st == ANTS_EVT_OK && i < n_s; i += G) {
         bool in = !m.passive[i];
         if (m.min_signal > 0.0f && s_sig[i] < m.min_signal) in = false;
         if (m.max_distance > 0.0f) {
@@ -102,11 +136,21 @@ __device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &
         s_act[i] = in ? 1.0f : 0.0f;
         if (in) Sp += s_sig[i];
     }
-    S = match_warp_sum(Sp);
+    S = Group<G>::sum(Sp);
     __syncwarp();
+    if (st != ANTS_EVT_OK) return st;
     if (!(S > 0.0f)) return ANTS_EVT_ZERO_SIGNAL;
     if (!lrf_defined(L, s_act, cx, cy, cz)) return ANTS_EVT_OUT_OF_DOMAIN;
     return ANTS_EVT_OK;
+}
+
+// the same for one event per warp (G = 32)
+template <int TYPE>
+__device__ __forceinline__ int match_prologue(const LrfDev &L, const MatchArgs &m, const float *sig, long e,
+                                              const float *start_xyz, float *s_sig, float *s_act, int lane, float &S,
+                                              float &cx, float &cy, float &cz)
+{
+    return match_prologue_g<TYPE, 32>(L, m, sig, e, true, start_xyz, s_sig, s_act, lane, S, cx, cy, cz);
 }
 
 }  // namespace ants

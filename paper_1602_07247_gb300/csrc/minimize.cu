@@ -27,7 +27,6 @@ namespace ants {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
 constexpr int kMinWarps = 8;
 constexpr float kLambdaMin = 1e-12f, kLambdaMax = 1e8f;
@@ -66,17 +65,19 @@ __device__ __forceinline__ float poisson_const(float s)
     return s * logf(s) - s - lgammaf(s + 1.0f);
 }
 
-// every LRF in the match defined at (x, y, z), checked across the warp
-template <int TYPE>
-__device__ __forceinline__ bool defined_warp(const LrfDev &L, const float *s_act, float x, float y, float z, int lane)
+// every LRF in the match defined at (x, y, z), checked across the group
+// (every lane of the warp calls it; a lane with live = false checks nothing)
+template <int TYPE, int G>
+__device__ __forceinline__ bool defined_group(const LrfDev &L, const float *s_act, float x, float y, float z, int lane,
+                                              bool live)
 {
     bool ok = true;
     if (TYPE == ANTS_LRF_RADIAL || TYPE == ANTS_LRF_COMPOSITE || TYPE == ANTS_LRF_AXIAL_Z) {
         const float rhi = TYPE == ANTS_LRF_COMPOSITE ? L.hi_r : L.hi[0];
-        for (int i = lane; i < L.n_s; i += 32)
+        for (int i = lane & (G - 1); live && i < L.n_s; i += G)
             if (s_act[i] != 0.0f && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) > rhi) ok = false;
     }
-    ok = __all_sync(kFull, ok);
+    ok = Group<G>::all(ok, lane);
     if (TYPE == ANTS_LRF_AXIAL_Z) return ok && z >= L.lo[1] && z <= L.hi[1];
     if (TYPE == ANTS_LRF_RADIAL) return ok;
     return ok && in_box(L, x, y, z);
@@ -129,20 +130,54 @@ __device__ __forceinline__ int active_set(const LrfDev &L, const float p[3], con
 // The two passes at point q over the sensors in the match: eta (floored,
 // gradient 0 where floored) into s_eq and its gradient into s_g, then J, g
 // and chi^2; rel: the sums relative to eta_p in s_ep as well.
-template <int TYPE, int D>
+template <int TYPE, int D, int G>
 __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s_sig, const float *s_act,
                                                 const float *s_ep, float *s_eq, float *s_g, const float q[3], float S,
-                                                bool rel, int lane)
+                                                bool rel, int lane, bool live)
 {
     const LrfDev &L = a.L;
-    const int n_s = L.n_s;
+    const int n_s = L.n_s, glane = lane & (G - 1);
     PointSums P;
     float H = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, ls = 0.0f, dh = 0.0f;
-    for (int i = lane; i < n_s; i += 32) {
+    // XY sets share the knot grid: the span and the weights of the point are
+    // computed once, not per sensor (the same arithmetic as lrf_eta_grad_t)
+    int jx = 0, jy = 0;
+    float wx[4], wy[4], dwx[4], dwy[4];
+    if (TYPE == ANTS_LRF_XY) {
+        float tx, ty;
+        jx = bs_span(q[0], L.lo[0], L.inv_h[0], L.n_int[0], tx);
+        jy = bs_span(q[1], L.lo[1], L.inv_h[1], L.n_int[1], ty);
+        bs_weights(tx, wx);
+        bs_weights(ty, wy);
+        bs_dweights(tx, dwx);
+        bs_dweights(ty, dwy);
+    }
+    for (int i = glane; live && i < n_s; i += G) {
         if (s_act[i] == 0.0f) continue;
         bool ok;
-        float gx, gy, gz;
-        float eta = lrf_eta_grad_t<TYPE>(L, i, q[0], q[1], q[2], ok, gx, gy, gz);
+        float gx, gy, gz = 0.0f, eta;
+        if (TYPE == ANTS_LRF_XY) {
+            const float *c = L.coef + (size_t)i * L.n_coef + jy * L.stride_y + jx;
+            float f = 0.0f, fx = 0.0f, fy = 0.0f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float *row = c + b * L.stride_y;
+                float fr = 0.0f, frx = 0.0f;
+#pragma unroll
+                for (int a2 = 0; a2 < 4; ++a2) {
+                    fr = fmaf(row[a2], wx[a2], fr);
+                    frx = fmaf(row[a2], dwx[a2], frx);
+                }
+                f = fmaf(fr, wy[b], f);
+                fx = fmaf(frx, wy[b], fx);
+                fy = fmaf(fr, dwy[b], fy);
+            }
+            eta = f;
+            gx = fx * L.inv_h[0];
+            gy = fy * L.inv_h[1];
+        } else {
+            eta = lrf_eta_grad_t<TYPE>(L, i, q[0], q[1], q[2], ok, gx, gy, gz);
+        }
         if (!(eta > kEtaFloor)) {
             eta = kEtaFloor;
             gx = gy = gz = 0.0f;
@@ -161,15 +196,15 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
             dh += eta - ep;
         }
     }
-    P.H = match_warp_sum(H);
-    P.dH[0] = match_warp_sum(d0);
-    P.dH[1] = match_warp_sum(d1);
-    P.dH[2] = D == 3 ? match_warp_sum(d2) : 0.0f;
-    P.lsum = rel ? match_warp_sum(ls) : 0.0f;
-    P.dHrel = rel ? match_warp_sum(dh) : 0.0f;
+    P.H = Group<G>::sum(H);
+    P.dH[0] = Group<G>::sum(d0);
+    P.dH[1] = Group<G>::sum(d1);
+    P.dH[2] = D == 3 ? Group<G>::sum(d2) : 0.0f;
+    P.lsum = rel ? Group<G>::sum(ls) : 0.0f;
+    P.dHrel = rel ? Group<G>::sum(dh) : 0.0f;
     const float E = S / P.H, invH = 1.0f / P.H;
     float g[3] = {0.0f, 0.0f, 0.0f}, J[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, chi = 0.0f;
-    for (int i = lane; i < n_s; i += 32) {
+    for (int i = glane; live && i < n_s; i += G) {
         if (s_act[i] == 0.0f) continue;
         const float eta = s_eq[i], s = s_sig[i], mu = E * eta;
         float gi[3] = {s_g[3 * i], s_g[3 * i + 1], D == 3 ? s_g[3 * i + 2] : 0.0f}, dmu[3] = {0.0f, 0.0f, 0.0f};
@@ -197,14 +232,14 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
         }
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) P.g[k] = k < D ? match_warp_sum(g[k]) : 0.0f;
-    P.J[0] = match_warp_sum(J[0]);
-    P.J[1] = match_warp_sum(J[1]);
-    P.J[3] = match_warp_sum(J[3]);
-    P.J[2] = D == 3 ? match_warp_sum(J[2]) : 0.0f;
-    P.J[4] = D == 3 ? match_warp_sum(J[4]) : 0.0f;
-    P.J[5] = D == 3 ? match_warp_sum(J[5]) : 0.0f;
-    P.chi2 = a.criterion == 0 ? 0.0f : match_warp_sum(chi);
+    for (int k = 0; k < 3; ++k) P.g[k] = k < D ? Group<G>::sum(g[k]) : 0.0f;
+    P.J[0] = Group<G>::sum(J[0]);
+    P.J[1] = Group<G>::sum(J[1]);
+    P.J[3] = Group<G>::sum(J[3]);
+    P.J[2] = D == 3 ? Group<G>::sum(J[2]) : 0.0f;
+    P.J[4] = D == 3 ? Group<G>::sum(J[4]) : 0.0f;
+    P.J[5] = D == 3 ? Group<G>::sum(J[5]) : 0.0f;
+    P.chi2 = a.criterion == 0 ? 0.0f : Group<G>::sum(chi);
     return P;
 }
 
@@ -244,53 +279,56 @@ __device__ __forceinline__ bool solve_step(const PointSums &P, float lambda, int
     return true;
 }
 
-template <int TYPE, int D>
+// G lanes per event, 32 / G events per warp in lockstep: every lane runs
+// every collective; groups whose event is finished (or absent) keep running
+// the loop without evaluating sensors or changing their state
+template <int TYPE, int D, int G>
 __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __grid_constant__ MinArgs a)
 {
     extern __shared__ float smem[];
+    constexpr int EPW = 32 / G;
     const LrfDev &L = a.L;
     const int n_s = L.n_s;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *s_sig = smem + (size_t)wib * 7 * n_s;  // signals (0 for passive sensors)
-    float *s_act = s_sig + n_s;                   // 1 in the match, 0 out
-    float *s_ep = s_act + n_s;                    // eta at the current point
-    float *s_eq = s_ep + n_s;                     // eta at the trial point
-    float *s_g = s_eq + n_s;                      // its gradient [n_s][3]
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, grp = lane / G, glane = lane & (G - 1);
+    float *s_sig = smem + ((size_t)wib * EPW + grp) * 7 * n_s;  // signals (0 for passive sensors)
+    float *s_act = s_sig + n_s;                                  // 1 in the match, 0 out
+    float *s_ep = s_act + n_s;                                   // eta at the current point
+    float *s_eq = s_ep + n_s;                                    // eta at the trial point
+    float *s_g = s_eq + n_s;                                     // its gradient [n_s][3]
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
-    for (long e = (long)blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_e; e += warps) {
+    for (long base = ((long)blockIdx.x * (blockDim.x >> 5) + wib) * EPW; base < a.n_e; base += warps * EPW) {
+        const long e = base + grp;
+        const bool active = e < a.n_e;
         float S, p[3];
-        const int st = match_prologue<TYPE>(L, a.m, a.sig, e, a.start_xyz, s_sig, s_act, lane, S, p[0], p[1], p[2]);
-        if (st != ANTS_EVT_OK) {
-            if (lane == 0) {
-                const float nan = __int_as_float(0x7fc00000);
-                a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = nan;
-                a.E[e] = a.logL[e] = nan;
-                a.status[e] = st;
-                if (a.n_iter) a.n_iter[e] = 0;
-            }
-            __syncwarp();
-            continue;
+        const int st = match_prologue_g<TYPE, G>(L, a.m, a.sig, e, active, a.start_xyz, s_sig, s_act, lane, S, p[0],
+                                                 p[1], p[2]);
+        bool done = st != ANTS_EVT_OK;
+        if (active && done && glane == 0) {
+            const float nan = __int_as_float(0x7fc00000);
+            a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = nan;
+            a.E[e] = a.logL[e] = nan;
+            a.status[e] = st;
+            if (a.n_iter) a.n_iter[e] = 0;
         }
         const float tau = ldexpf(S, -18);
-        PointSums P = point_pass<TYPE, D>(a, s_sig, s_act, s_ep, s_eq, s_g, p, S, false, lane);
-        for (int i = lane; i < n_s; i += 32) s_ep[i] = s_eq[i];
+        PointSums P = point_pass<TYPE, D, G>(a, s_sig, s_act, s_ep, s_eq, s_g, p, S, false, lane, !done);
+        for (int i = glane; !done && i < n_s; i += G) s_ep[i] = s_eq[i];
         float lambda = a.lambda0;
         int used = -a.max_iter;
         for (int it = 1; it <= a.max_iter; ++it) {
+            if (__all_sync(0xffffffffu, done)) break;
             float delta[3];
             bool okd = solve_step<D>(P, lambda, 0, delta);
             const int fixed = okd ? active_set<TYPE, D>(L, p, delta) : 0;
             if (fixed) okd = solve_step<D>(P, lambda, fixed, delta);
             float q[3] = {p[0] + delta[0], p[1] + delta[1], p[2] + delta[2]};
             clamp_box<TYPE>(L, q);
-            bool acc = okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) &&
-                       defined_warp<TYPE>(L, s_act, q[0], q[1], q[2], lane);
-            PointSums Q;
+            const bool cand = !done && okd && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]);
+            bool acc = defined_group<TYPE, G>(L, s_act, q[0], q[1], q[2], lane, cand) && cand;
+            PointSums Q = point_pass<TYPE, D, G>(a, s_sig, s_act, s_ep, s_eq, s_g, q, S, true, lane, acc);
             if (acc) {
-                Q = point_pass<TYPE, D>(a, s_sig, s_act, s_ep, s_eq, s_g, q, S, true, lane);
-                const float dC = a.criterion == 0
-                                     ? 0.6931471805599453f * Q.lsum - S * log1pf(Q.dHrel / P.H)
-                                     : P.chi2 - Q.chi2;
+                const float dC = a.criterion == 0 ? 0.6931471805599453f * Q.lsum - S * log1pf(Q.dHrel / P.H)
+                                                  : P.chi2 - Q.chi2;
                 if (fabsf(dC) > tau) {
                     acc = dC > 0.0f;
                 } else {
@@ -299,6 +337,7 @@ __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __gri
                     acc = t >= 0.0f;
                 }
             }
+            if (done) continue;
             if (acc) {
                 const float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
                 const float step = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -313,30 +352,31 @@ __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __gri
                 p[1] = q[1];
                 p[2] = q[2];
                 P = Q;
-                for (int i = lane; i < n_s; i += 32) s_ep[i] = s_eq[i];
+                for (int i = glane; i < n_s; i += G) s_ep[i] = s_eq[i];
                 lambda = next;
                 if (step < a.tol) {
                     used = it;
-                    break;
+                    done = true;
                 }
             } else {
                 lambda *= 10.0f;
                 if (lambda > kLambdaMax) {
                     used = it;
-                    break;
+                    done = true;
                 }
             }
         }
         // energy and full Poisson log-likelihood over the match at p
+        const bool ok = st == ANTS_EVT_OK;
         const float En = S / P.H;
         float ll = 0.0f;
-        for (int i = lane; i < n_s; i += 32) {
+        for (int i = glane; ok && i < n_s; i += G) {
             if (s_act[i] == 0.0f) continue;
             const float mu = En * s_ep[i], s = s_sig[i];
             ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
         }
-        ll = match_warp_sum(ll);
-        if (lane == 0) {
+        ll = Group<G>::sum(ll);
+        if (ok && glane == 0) {
             a.xyz[3 * e] = p[0];
             a.xyz[3 * e + 1] = p[1];
             a.xyz[3 * e + 2] = p[2];
@@ -395,32 +435,40 @@ int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_mi
         a.m.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
         a.m.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
     }
-    // as many warps per block as fit 7 n_s floats each in 48 KB
-    int wpb = (int)(48 * 1024 / (28 * (size_t)n_s));
+    // 8 lanes per event (4 events per warp) up to 96 sensors, else a warp
+    // per event; as many warps per block as fit 7 n_s floats per event in 48 KB
+    const int G = n_s <= 96 ? 8 : 32, epw = 32 / G;
+    int wpb = (int)(48 * 1024 / (28 * (size_t)n_s * epw));
     wpb = wpb < 1 ? 1 : (wpb > kMinWarps ? kMinWarps : wpb);
-    const size_t smem = (size_t)wpb * 28 * n_s;
-    long blocks = (n_e + wpb - 1) / wpb;
+    const size_t smem = (size_t)wpb * epw * 28 * n_s;
+    const long per_block = (long)wpb * epw;
+    long blocks = (n_e + per_block - 1) / per_block;
     const long cap = (long)ctx->n_sm * 16;
     if (blocks > cap) blocks = cap;
     const bool z = P.fit_z != 0;
     const unsigned g = (unsigned)blocks, t = 32u * wpb;
+#define ANTS_MIN_LAUNCH(T, D)                                                         \
+    (G == 8    ? minimize_kernel<T, D, 8><<<g, t, smem, s>>>(a)                                \
+     : G == 16 ? minimize_kernel<T, D, 16><<<g, t, smem, s>>>(a)                              \
+               : minimize_kernel<T, D, 32><<<g, t, smem, s>>>(a))
     switch (lrf->type) {
-    case ANTS_LRF_RADIAL: minimize_kernel<ANTS_LRF_RADIAL, 2><<<g, t, smem, s>>>(a); break;
-    case ANTS_LRF_XY: minimize_kernel<ANTS_LRF_XY, 2><<<g, t, smem, s>>>(a); break;
-    case ANTS_LRF_COMPOSITE: minimize_kernel<ANTS_LRF_COMPOSITE, 2><<<g, t, smem, s>>>(a); break;
+    case ANTS_LRF_RADIAL: ANTS_MIN_LAUNCH(ANTS_LRF_RADIAL, 2); break;
+    case ANTS_LRF_XY: ANTS_MIN_LAUNCH(ANTS_LRF_XY, 2); break;
+    case ANTS_LRF_COMPOSITE: ANTS_MIN_LAUNCH(ANTS_LRF_COMPOSITE, 2); break;
     case ANTS_LRF_XYZ:
-        if (z) minimize_kernel<ANTS_LRF_XYZ, 3><<<g, t, smem, s>>>(a);
-        else minimize_kernel<ANTS_LRF_XYZ, 2><<<g, t, smem, s>>>(a);
+        if (z) ANTS_MIN_LAUNCH(ANTS_LRF_XYZ, 3);
+        else ANTS_MIN_LAUNCH(ANTS_LRF_XYZ, 2);
         break;
     case ANTS_LRF_AXIAL_Z:
-        if (z) minimize_kernel<ANTS_LRF_AXIAL_Z, 3><<<g, t, smem, s>>>(a);
-        else minimize_kernel<ANTS_LRF_AXIAL_Z, 2><<<g, t, smem, s>>>(a);
+        if (z) ANTS_MIN_LAUNCH(ANTS_LRF_AXIAL_Z, 3);
+        else ANTS_MIN_LAUNCH(ANTS_LRF_AXIAL_Z, 2);
         break;
     default:
-        if (z) minimize_kernel<ANTS_LRF_SLICED, 3><<<g, t, smem, s>>>(a);
-        else minimize_kernel<ANTS_LRF_SLICED, 2><<<g, t, smem, s>>>(a);
+        if (z) ANTS_MIN_LAUNCH(ANTS_LRF_SLICED, 3);
+        else ANTS_MIN_LAUNCH(ANTS_LRF_SLICED, 2);
         break;
     }
+#undef ANTS_MIN_LAUNCH
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "minimize_kernel launch");
     count_launch();
