@@ -234,6 +234,7 @@ static int upload_lrf(ants_lrf *L)
                   "upload cog weights");
     LrfDev &D = L->dev;
     D.coef2 = nullptr;
+    D.coef_t = nullptr;
     D.n_pairs = (L->n_s + 1) / 2;
     D.pair_stride = 0;
     if (L->type == ANTS_LRF_XY) {
@@ -249,6 +250,13 @@ static int upload_lrf(ants_lrf *L)
                       "upload coef pairs");
         D.coef2 = L->d_coef2;
         D.pair_stride = ps;
+        std::vector<float> ct(c.size());
+        for (int i = 0; i < L->n_s; ++i)
+            for (int k = 0; k < ps; ++k) ct[(size_t)k * L->n_s + i] = c[(size_t)i * ps + k];
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_coeft, ct.size() * sizeof(float)), "cudaMalloc(lrf coef sensor-minor)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_coeft, ct.data(), ct.size() * sizeof(float), cudaMemcpyHostToDevice),
+                      "upload coef sensor-minor");
+        D.coef_t = L->d_coeft;
     }
     D.rpoly = nullptr;
     if (L->type == ANTS_LRF_RADIAL || L->type == ANTS_LRF_COMPOSITE) {
@@ -306,6 +314,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_gain);
     cudaFree(lrf->d_cogw);
     cudaFree(lrf->d_coef2);
+    cudaFree(lrf->d_coeft);
     cudaFree(lrf->d_rpoly);
     delete lrf;
     (void)cudaGetLastError();

@@ -47,6 +47,7 @@ struct LrfDev {
     // XY LRFs: sensors interleaved in pairs, [n_pairs][n_int[1]+3][n_int[0]+3]
     // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
     const float2 *coef2;
+    const float *coef_t;   // XY: the coefficients sensor-minor, [k][n_s] (per-point loops over sensors)
     // RADIAL LRFs: each interval's cubic in the power basis of its local
     // parameter t, (p0, p1, p2, p3) with f = p0 + t (p1 + t (p2 + t p3)),
     // [n_sets][n_int[0]]
@@ -106,6 +107,7 @@ struct ants_lrf {
     int n_planes = 0;              // SLICED
     float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
     float2 *d_coef2 = nullptr;
+    float *d_coeft = nullptr;
     float4 *d_rpoly = nullptr;
     ants::LrfDev dev{};
 };

@@ -6,6 +6,8 @@
 // are ignored).  One warp per event.
 #pragma once
 
+#include <type_traits>
+
 #include "bspline.cuh"
 #include "internal.cuh"
 
@@ -17,6 +19,7 @@ struct MatchArgs {
     int start;                                  // ANTS_START_COG / ANTS_START_MAX_SENSOR
     float min_signal, max_distance, z0;
     double gain[kMaxMatchSensors];              // relative gains (start)
+    float inv_gain[kMaxMatchSensors];           // their reciprocals (single-precision start)
     unsigned char passive[kMaxMatchSensors];    // 1 = passive
 };
 
@@ -52,6 +55,8 @@ template <int G> struct Group {
         for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     }
+    static __device__ __forceinline__ double sum_any(double v) { return sumd(v); }
+    static __device__ __forceinline__ float sum_any(float v) { return sum(v); }
     static __device__ __forceinline__ bool any(bool p, int lane)
     {
         return (__ballot_sync(0xffffffffu, p) & mask(lane)) != 0u;
@@ -67,49 +72,53 @@ template <int G> struct Group {
 // group): loads the signals into s_sig (0 for passive sensors), picks the
 // start (given: start_xyz, nullable), marks the sensors in the match in
 // s_act (1 / 0) and returns ANTS_EVT_OK with their signal sum S and the
-// start, or the event's failure status.  Comparisons that pick the start or
-// a sensor are made in FP64.  Every lane of the warp runs every collective;
-// an inactive group (no event) reads nothing and returns ANTS_EVT_ZERO_SIGNAL.
-template <int TYPE, int G>
+// start, or the event's failure status.  EXACT: the sums and comparisons
+// that pick the start or a sensor are made in FP64 (s / g as the oracle
+// forms it, for searches whose path depends on the start's last bit); else
+// in FP32 with s times 1 / g (a minimisation converges to the same optimum).
+// Every lane of the warp runs every collective; an inactive group (no
+// event) reads nothing and returns ANTS_EVT_ZERO_SIGNAL.
+template <int TYPE, int G, bool EXACT = true>
 __device__ __forceinline__ int match_prologue_g(const LrfDev &L, const MatchArgs &m, const float *sig, long e,
                                                 bool active, const float *start_xyz, float *s_sig, float *s_act,
                                                 int lane, float &S, float &cx, float &cy, float &cz)
 {
+    using A = typename std::conditional<EXACT, double, float>::type;
     const int n_s = L.n_s, glane = lane & (G - 1);
     bool bad = false;
-    double tot = 0.0, W = 0.0, X = 0.0, Y = 0.0, bv = -1.0;
+    A tot = 0, W = 0, X = 0, Y = 0, bv = -1;
     int bi = 0x7fffffff;
     for (int i = glane; active && i < n_s; i += G) {
         float s = sig[e * n_s + i];
         if (m.passive[i]) s = 0.0f;
         else if (!isfinite(s) || s < 0.0f) bad = true;
         s_sig[i] = s;
-        const double w = (double)s / m.gain[i];
-        tot += (double)s;
+        const A w = EXACT ? (A)((double)s / m.gain[i]) : (A)(s * m.inv_gain[i]);
+        tot += (A)s;
         W += w;
-        X += (double)L.sxy[2 * i] * w;
-        Y += (double)L.sxy[2 * i + 1] * w;
+        X += (A)L.sxy[2 * i] * w;
+        Y += (A)L.sxy[2 * i + 1] * w;
         if (!m.passive[i] && w > bv) {  // lanes visit increasing i: the first maximum
             bv = w;
             bi = i;
         }
     }
     bad = Group<G>::any(bad, lane);
-    tot = Group<G>::sumd(tot);
-    int st = !active ? ANTS_EVT_ZERO_SIGNAL : bad ? ANTS_EVT_BAD_SIGNAL : !(tot > 0.0) ? ANTS_EVT_ZERO_SIGNAL
-                                                                                     : ANTS_EVT_OK;
+    tot = Group<G>::sum_any(tot);
+    int st = !active ? ANTS_EVT_ZERO_SIGNAL : bad ? ANTS_EVT_BAD_SIGNAL : !(tot > A(0)) ? ANTS_EVT_ZERO_SIGNAL
+                                                                                       : ANTS_EVT_OK;
     cz = lrf_is_3d(TYPE) ? m.z0 : 0.0f;
     for (int o = G / 2; o; o >>= 1) {  // the largest s/g, ties to the lowest index
-        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const A v2 = __shfl_xor_sync(0xffffffffu, bv, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
         if (v2 > bv || (v2 == bv && i2 < bi)) {
             bv = v2;
             bi = i2;
         }
     }
-    W = Group<G>::sumd(W);
-    X = Group<G>::sumd(X);
-    Y = Group<G>::sumd(Y);
+    W = Group<G>::sum_any(W);
+    X = Group<G>::sum_any(X);
+    Y = Group<G>::sum_any(Y);
     if (start_xyz && active) {
         cx = start_xyz[3 * e];
         cy = start_xyz[3 * e + 1];

@@ -157,16 +157,19 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
         bool ok;
         float gx, gy, gz = 0.0f, eta;
         if (TYPE == ANTS_LRF_XY) {
-            const float *c = L.coef + (size_t)i * L.n_coef + jy * L.stride_y + jx;
+            // sensor-minor copy: the group's lanes read neighbouring sensors
+            const float *c = L.coef_t + (size_t)(jy * L.stride_y + jx) * n_s + i;
+            const size_t rs = (size_t)L.stride_y * n_s;
             float f = 0.0f, fx = 0.0f, fy = 0.0f;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const float *row = c + b * L.stride_y;
+                const float *row = c + b * rs;
                 float fr = 0.0f, frx = 0.0f;
 #pragma unroll
                 for (int a2 = 0; a2 < 4; ++a2) {
-                    fr = fmaf(row[a2], wx[a2], fr);
-                    frx = fmaf(row[a2], dwx[a2], frx);
+                    const float cv = __ldg(row + (size_t)a2 * n_s);
+                    fr = fmaf(cv, wx[a2], fr);
+                    frx = fmaf(cv, dwx[a2], frx);
                 }
                 f = fmaf(fr, wy[b], f);
                 fx = fmaf(frx, wy[b], fx);
@@ -300,8 +303,8 @@ __global__ void __launch_bounds__(32 * kMinWarps, 2) minimize_kernel(const __gri
         const long e = base + grp;
         const bool active = e < a.n_e;
         float S, p[3];
-        const int st = match_prologue_g<TYPE, G>(L, a.m, a.sig, e, active, a.start_xyz, s_sig, s_act, lane, S, p[0],
-                                                 p[1], p[2]);
+        const int st = match_prologue_g<TYPE, G, false>(L, a.m, a.sig, e, active, a.start_xyz, s_sig, s_act, lane, S,
+                                                        p[0], p[1], p[2]);
         bool done = st != ANTS_EVT_OK;
         if (active && done && glane == 0) {
             const float nan = __int_as_float(0x7fc00000);
@@ -433,6 +436,7 @@ int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_mi
     const int n_s = lrf->n_s;
     for (int i = 0; i < kMaxMatchSensors; ++i) {
         a.m.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
+        a.m.inv_gain[i] = (float)(1.0 / a.m.gain[i]);
         a.m.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
     }
     // 8 lanes per event (4 events per warp) up to 96 sensors, else a warp

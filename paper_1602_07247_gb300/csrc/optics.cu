@@ -27,14 +27,17 @@ constexpr int kMaxAng = 64;
 constexpr uint32_t kTag = 0x0F7105u;
 constexpr int kOptThreads = 256;
 
+// the geometry in the kernel's arithmetic type (converted once on the host,
+// so the FP32 kernel does no double-precision work)
+template <typename R>
 struct OptArgs {
     int n_layers, n_s, n_ang, max_cycles, pre_reject;
-    double z[kMaxLayers + 1], n[kMaxLayers], abs_len[kMaxLayers], ray_len[kMaxLayers];
-    double n_below, n_above, half_x, half_y;
-    double p_abs[kMaxLayers + 1], p_spec[kMaxLayers + 1], p_diff[kMaxLayers + 1];
-    double sensor_half, n_sensor, p_max;
-    double sx[kMaxOptSensors], sy[kMaxOptSensors], qe[kMaxOptSensors];
-    double ang[kMaxAng];
+    R z[kMaxLayers + 1], n[kMaxLayers], abs_len[kMaxLayers], ray_len[kMaxLayers];
+    R n_below, n_above, half_x, half_y;
+    R p_abs[kMaxLayers + 1], p_spec[kMaxLayers + 1], p_diff[kMaxLayers + 1];
+    R sensor_half, n_sensor, p_max;
+    R sx[kMaxOptSensors], sy[kMaxOptSensors], qe[kMaxOptSensors];
+    R ang[kMaxAng];
     uint32_t k0, k1;
     const float *src;
     long n_src, n_ph;
@@ -119,7 +122,7 @@ __device__ __forceinline__ void turn(R d[3], R mu, R phi)
 }
 
 template <typename R>
-__device__ __forceinline__ R ang_resp(const OptArgs &a, R ci)
+__device__ __forceinline__ R ang_resp(const OptArgs<R> &a, R ci)
 {
     if (a.n_ang < 2) return R(1);
     const R th = M<R>::acos(fmin(R(1), fmax(R(0), ci))) / R(0.5 * 3.14159265358979323846) * R(a.n_ang - 1);
@@ -130,7 +133,7 @@ __device__ __forceinline__ R ang_resp(const OptArgs &a, R ci)
 }
 
 template <typename R>
-__device__ int trace_photon(const OptArgs &a, const R *s_sx, const R *s_sy, uint32_t q, uint32_t p)
+__device__ int trace_photon(const OptArgs<R> &a, const R *s_sx, const R *s_sy, uint32_t q, uint32_t p)
 {
     PhotonStream st{a.k0, a.k1, p, q, 0u, {0u, 0u, 0u, 0u}, 4};
     R u_det = R(-1);
@@ -168,8 +171,8 @@ __device__ int trace_photon(const OptArgs &a, const R *s_sx, const R *s_sy, uint
             tw = ty < tw ? ty : tw;
         }
         const R ua = st.next<R>(), ur = st.next<R>();
-        const R sa = a.abs_len[k] > 0.0 ? -R(a.abs_len[k]) * M<R>::log(ua) : inf;
-        const R sr = a.ray_len[k] > 0.0 ? -R(a.ray_len[k]) * M<R>::log(ur) : inf;
+        const R sa = a.abs_len[k] > R(0) ? -a.abs_len[k] * M<R>::log(ua) : inf;
+        const R sr = a.ray_len[k] > R(0) ? -a.ray_len[k] * M<R>::log(ur) : inf;
         const R t = tz < tw ? tz : tw, s = sa < sr ? sa : sr;
         if (s < t) {
             for (int c = 0; c < 3; ++c) r[c] += s * d[c];
@@ -238,7 +241,7 @@ __device__ int trace_photon(const OptArgs &a, const R *s_sx, const R *s_sy, uint
 // grid (photon blocks, sources): each block traces a strided share of one
 // source's photons and adds its per-sensor counts once
 template <typename R>
-__global__ void __launch_bounds__(kOptThreads) trace_kernel(const __grid_constant__ OptArgs a)
+__global__ void __launch_bounds__(kOptThreads) trace_kernel(const __grid_constant__ OptArgs<R> a)
 {
     __shared__ int hist[kMaxOptSensors];
     __shared__ R s_sx[kMaxOptSensors], s_sy[kMaxOptSensors];
@@ -264,6 +267,49 @@ __global__ void counts_to_eta(const int32_t *counts, long n, float inv_ph, float
 {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         eta[i] = (float)counts[i] * inv_ph;
+}
+
+// the FP32 kernel's arguments: every geometry value rounded to float
+OptArgs<float> to_float(const OptArgs<double> &d)
+{
+    OptArgs<float> f;
+    f.n_layers = d.n_layers;
+    f.n_s = d.n_s;
+    f.n_ang = d.n_ang;
+    f.max_cycles = d.max_cycles;
+    f.pre_reject = d.pre_reject;
+    for (int b = 0; b <= kMaxLayers; ++b) {
+        f.z[b] = (float)d.z[b];
+        f.p_abs[b] = (float)d.p_abs[b];
+        f.p_spec[b] = (float)d.p_spec[b];
+        f.p_diff[b] = (float)d.p_diff[b];
+    }
+    for (int k = 0; k < kMaxLayers; ++k) {
+        f.n[k] = (float)d.n[k];
+        f.abs_len[k] = (float)d.abs_len[k];
+        f.ray_len[k] = (float)d.ray_len[k];
+    }
+    f.n_below = (float)d.n_below;
+    f.n_above = (float)d.n_above;
+    f.half_x = (float)d.half_x;
+    f.half_y = (float)d.half_y;
+    f.sensor_half = (float)d.sensor_half;
+    f.n_sensor = (float)d.n_sensor;
+    f.p_max = (float)d.p_max;
+    for (int i = 0; i < kMaxOptSensors; ++i) {
+        f.sx[i] = (float)d.sx[i];
+        f.sy[i] = (float)d.sy[i];
+        f.qe[i] = (float)d.qe[i];
+    }
+    for (int j = 0; j < kMaxAng; ++j) f.ang[j] = (float)d.ang[j];
+    f.k0 = d.k0;
+    f.k1 = d.k1;
+    f.src = d.src;
+    f.n_src = d.n_src;
+    f.n_ph = d.n_ph;
+    f.counts = d.counts;
+    f.outcome = d.outcome;
+    return f;
 }
 
 }  // namespace
@@ -301,7 +347,7 @@ extern "C" ANTS_API int ants_trace_photons(ants_ctx *ctx, const ants_optics_para
     if (P->max_cycles < 1) return fail(ANTS_E_ARG, "ants_trace_photons: max_cycles must be >= 1");
     if (n_src > 0 && n_photons > 0 && (!src_xyz_dev || !counts_dev))
         return fail(ANTS_E_ARG, "ants_trace_photons: NULL source or count buffer");
-    OptArgs a;
+    OptArgs<double> a;
     a.n_layers = K;
     a.n_s = P->n_sensors;
     a.n_ang = P->n_ang;
@@ -357,8 +403,11 @@ extern "C" ANTS_API int ants_trace_photons(ants_ctx *ctx, const ants_optics_para
         const long need = (n_photons + kOptThreads - 1) / kOptThreads;
         per = per < 1 ? 1 : (per > need ? need : per);
         const dim3 grid((unsigned)per, (unsigned)n_src);
-        if (precision == ANTS_F64) trace_kernel<double><<<grid, kOptThreads, 0, s>>>(a);
-        else trace_kernel<float><<<grid, kOptThreads, 0, s>>>(a);
+        if (precision == ANTS_F64) {
+            trace_kernel<double><<<grid, kOptThreads, 0, s>>>(a);
+        } else {
+            trace_kernel<float><<<grid, kOptThreads, 0, s>>>(to_float(a));
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "trace_kernel launch");
         count_launch();

@@ -247,6 +247,7 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     const int n_s = lrf->n_s;
     for (int i = 0; i < kMaxVariantSensors; ++i) {
         a.m.gain[i] = i < n_s ? lrf->rel_gain[i] : 1.0;
+        a.m.inv_gain[i] = (float)(1.0 / a.m.gain[i]);
         a.m.passive[i] = i < n_s && P.passive_host && P.passive_host[i] ? 1 : 0;
     }
     // as many warps per block as fit 4 n_s floats each in 48 KB
