@@ -10,7 +10,8 @@
 // (photon, source, tag, block), in a fixed order, so the results do not depend
 // on the launch shape.  Templated on the arithmetic type: the FP64 instance
 // takes every decision in the precision of the CPU oracle, the FP32 one is the
-// fast mode.  Detections are counted per block in shared memory and added to
+// fast mode.  A lane whose photon ends starts its next one in the same loop
+// iteration.  Detections are counted per block in shared memory and added to
 // the global counts once per block and sensor.
 #include <cmath>
 
@@ -132,110 +133,134 @@ __device__ __forceinline__ R ang_resp(const OptArgs<R> &a, R ci)
     return (R(1) - w) * R(a.ang[j]) + w * R(a.ang[j + 1]);
 }
 
+constexpr int kGoOn = 1000;  // a photon still in flight
+
+// the state of a photon in flight
 template <typename R>
-__device__ int trace_photon(const OptArgs<R> &a, const R *s_sx, const R *s_sy, uint32_t q, uint32_t p)
+struct Photon {
+    PhotonStream st;
+    R r[3], d[3], u_det;
+    int k, cyc;
+};
+
+// emission of photon p of source q: ANTS_PH_REJECTED or kGoOn
+template <typename R>
+__device__ __forceinline__ int photon_start(const OptArgs<R> &a, Photon<R> &ph, uint32_t q, uint32_t p)
 {
-    PhotonStream st{a.k0, a.k1, p, q, 0u, {0u, 0u, 0u, 0u}, 4};
-    R u_det = R(-1);
+    ph.st = PhotonStream{a.k0, a.k1, p, q, 0u, {0u, 0u, 0u, 0u}, 4};
+    ph.u_det = R(-1);
+    ph.cyc = 0;
     if (a.pre_reject) {
-        u_det = st.next<R>();
-        if (!(u_det < R(a.p_max))) return ANTS_PH_REJECTED;
+        ph.u_det = ph.st.template next<R>();
+        if (!(ph.u_det < a.p_max)) return ANTS_PH_REJECTED;
     }
     const R x0 = R(a.src[3 * (size_t)q]), y0 = R(a.src[3 * (size_t)q + 1]), z0 = R(a.src[3 * (size_t)q + 2]);
     int k = 0;
-    while (k < a.n_layers - 1 && z0 >= R(a.z[k + 1])) ++k;
-    R r[3] = {x0, y0, z0}, d[3];
-    {
-        const R mu = R(2) * st.next<R>() - R(1), phi = R(2 * 3.14159265358979323846) * st.next<R>();
-        R sp, cp;
-        M<R>::sincos(phi, &sp, &cp);
-        const R s = M<R>::sqrt(fmax(R(0), R(1) - mu * mu));
-        d[0] = s * cp;
-        d[1] = s * sp;
-        d[2] = mu;
+    while (k < a.n_layers - 1 && z0 >= a.z[k + 1]) ++k;
+    ph.k = k;
+    ph.r[0] = x0;
+    ph.r[1] = y0;
+    ph.r[2] = z0;
+    const R mu = R(2) * ph.st.template next<R>() - R(1), phi = R(2 * 3.14159265358979323846) * ph.st.template next<R>();
+    R sp, cp;
+    M<R>::sincos(phi, &sp, &cp);
+    const R s = M<R>::sqrt(fmax(R(0), R(1) - mu * mu));
+    ph.d[0] = s * cp;
+    ph.d[1] = s * sp;
+    ph.d[2] = mu;
+    return kGoOn;
+}
+
+// one tracing cycle of a photon in flight: its outcome, or kGoOn
+template <typename R>
+__device__ __forceinline__ int photon_cycle(const OptArgs<R> &a, const R *s_sx, const R *s_sy, Photon<R> &ph)
+{
+    if (ph.cyc >= a.max_cycles) return ANTS_PH_MAX_CYCLES;
+    ++ph.cyc;
+    R *r = ph.r, *d = ph.d;
+    int &k = ph.k;
+    PhotonStream &st = ph.st;
+    R &u_det = ph.u_det;
+    const R hx = a.half_x, hy = a.half_y, inf = R(INFINITY), half = a.sensor_half;
+    R tz = inf, tw = inf;
+    int b = -1;
+    if (d[2] > R(0)) {
+        tz = (R(a.z[k + 1]) - r[2]) / d[2];
+        b = k + 1;
+    } else if (d[2] < R(0)) {
+        tz = (R(a.z[k]) - r[2]) / d[2];
+        b = k;
     }
-    const R hx = R(a.half_x), hy = R(a.half_y), inf = R(INFINITY), half = R(a.sensor_half);
-    for (int cyc = 0; cyc < a.max_cycles; ++cyc) {
-        R tz = inf, tw = inf;
-        int b = -1;
-        if (d[2] > R(0)) {
-            tz = (R(a.z[k + 1]) - r[2]) / d[2];
-            b = k + 1;
-        } else if (d[2] < R(0)) {
-            tz = (R(a.z[k]) - r[2]) / d[2];
-            b = k;
-        }
-        if (d[0] != R(0)) tw = ((d[0] > R(0) ? hx : -hx) - r[0]) / d[0];
-        if (d[1] != R(0)) {
-            const R ty = ((d[1] > R(0) ? hy : -hy) - r[1]) / d[1];
-            tw = ty < tw ? ty : tw;
-        }
-        const R ua = st.next<R>(), ur = st.next<R>();
-        const R sa = a.abs_len[k] > R(0) ? -a.abs_len[k] * M<R>::log(ua) : inf;
-        const R sr = a.ray_len[k] > R(0) ? -a.ray_len[k] * M<R>::log(ur) : inf;
-        const R t = tz < tw ? tz : tw, s = sa < sr ? sa : sr;
-        if (s < t) {
-            for (int c = 0; c < 3; ++c) r[c] += s * d[c];
-            if (sa <= sr) return ANTS_PH_ABSORBED;
-            const R uq = st.next<R>();
-            const R qq = R(4) * uq - R(2), rr = M<R>::sqrt(qq * qq + R(1));
-            const R mu = M<R>::cbrt(qq + rr) + M<R>::cbrt(qq - rr);
-            turn<R>(d, mu, R(2 * 3.14159265358979323846) * st.next<R>());
-            continue;
-        }
-        if (tw <= tz) return ANTS_PH_ESCAPED;
-        for (int c = 0; c < 3; ++c) r[c] += tz * d[c];
-        r[2] = R(a.z[b]);
-        const R ci = fabs(d[2]);
-        int sens = -1;
-        if (b == 0)
-            for (int i = 0; i < a.n_s; ++i)
-                if (fabs(r[0] - s_sx[i]) <= half && fabs(r[1] - s_sy[i]) <= half) {
-                    sens = i;
-                    break;
-                }
-        if (sens >= 0) {
-            if (st.next<R>() < fresnel<R>(R(a.n[k]), R(a.n_sensor), ci)) {
-                d[2] = -d[2];
-                continue;
+    if (d[0] != R(0)) tw = ((d[0] > R(0) ? hx : -hx) - r[0]) / d[0];
+    if (d[1] != R(0)) {
+        const R ty = ((d[1] > R(0) ? hy : -hy) - r[1]) / d[1];
+        tw = ty < tw ? ty : tw;
+    }
+    const R ua = st.next<R>(), ur = st.next<R>();
+    const R sa = a.abs_len[k] > R(0) ? -a.abs_len[k] * M<R>::log(ua) : inf;
+    const R sr = a.ray_len[k] > R(0) ? -a.ray_len[k] * M<R>::log(ur) : inf;
+    const R t = tz < tw ? tz : tw, s = sa < sr ? sa : sr;
+    if (s < t) {
+        for (int c = 0; c < 3; ++c) r[c] += s * d[c];
+        if (sa <= sr) return ANTS_PH_ABSORBED;
+        const R uq = st.next<R>();
+        const R qq = R(4) * uq - R(2), rr = M<R>::sqrt(qq * qq + R(1));
+        const R mu = M<R>::cbrt(qq + rr) + M<R>::cbrt(qq - rr);
+        turn<R>(d, mu, R(2 * 3.14159265358979323846) * st.next<R>());
+        return kGoOn;
+    }
+    if (tw <= tz) return ANTS_PH_ESCAPED;
+    for (int c = 0; c < 3; ++c) r[c] += tz * d[c];
+    r[2] = R(a.z[b]);
+    const R ci = fabs(d[2]);
+    int sens = -1;
+    if (b == 0)
+        for (int i = 0; i < a.n_s; ++i)
+            if (fabs(r[0] - s_sx[i]) <= half && fabs(r[1] - s_sy[i]) <= half) {
+                sens = i;
+                break;
             }
-            const R pd = R(a.qe[sens]) * ang_resp<R>(a, ci);
-            if (u_det < R(0)) u_det = st.next<R>();
-            return u_det < pd ? sens : ANTS_PH_UNDETECTED;
-        }
-        const R pa = R(a.p_abs[b]), ps = R(a.p_spec[b]), pf = R(a.p_diff[b]);
-        if (pa + ps + pf > R(0)) {
-            const R u = st.next<R>();
-            if (u < pa) return ANTS_PH_ABSORBED;
-            if (u < pa + ps) {
-                d[2] = -d[2];
-                continue;
-            }
-            if (u < pa + ps + pf) {
-                const R mu = M<R>::sqrt(st.next<R>()), phi = R(2 * 3.14159265358979323846) * st.next<R>();
-                R sp, cp;
-                M<R>::sincos(phi, &sp, &cp);
-                const R sn = M<R>::sqrt(fmax(R(0), R(1) - mu * mu));
-                d[0] = sn * cp;
-                d[1] = sn * sp;
-                d[2] = b == k + 1 ? -mu : mu;
-                continue;
-            }
-        }
-        const R n1 = R(a.n[k]);
-        const R n2 = b == k + 1 ? (b == a.n_layers ? R(a.n_above) : R(a.n[k + 1])) : (b == 0 ? R(a.n_below) : R(a.n[k - 1]));
-        if (st.next<R>() < fresnel<R>(n1, n2, ci)) {
+    if (sens >= 0) {
+        if (st.next<R>() < fresnel<R>(R(a.n[k]), R(a.n_sensor), ci)) {
             d[2] = -d[2];
-            continue;
+            return kGoOn;
         }
-        if (b == 0 || b == a.n_layers) return ANTS_PH_ESCAPED;
-        const R eta = n1 / n2, ct = M<R>::sqrt(fmax(R(0), R(1) - eta * eta * (R(1) - ci * ci)));
-        d[0] *= eta;
-        d[1] *= eta;
-        d[2] = d[2] > R(0) ? ct : -ct;
-        k = b == k + 1 ? k + 1 : k - 1;
+        const R pd = R(a.qe[sens]) * ang_resp<R>(a, ci);
+        if (u_det < R(0)) u_det = st.next<R>();
+        return u_det < pd ? sens : ANTS_PH_UNDETECTED;
     }
-    return ANTS_PH_MAX_CYCLES;
+    const R pa = R(a.p_abs[b]), ps = R(a.p_spec[b]), pf = R(a.p_diff[b]);
+    if (pa + ps + pf > R(0)) {
+        const R u = st.next<R>();
+        if (u < pa) return ANTS_PH_ABSORBED;
+        if (u < pa + ps) {
+            d[2] = -d[2];
+            return kGoOn;
+        }
+        if (u < pa + ps + pf) {
+            const R mu = M<R>::sqrt(st.next<R>()), phi = R(2 * 3.14159265358979323846) * st.next<R>();
+            R sp, cp;
+            M<R>::sincos(phi, &sp, &cp);
+            const R sn = M<R>::sqrt(fmax(R(0), R(1) - mu * mu));
+            d[0] = sn * cp;
+            d[1] = sn * sp;
+            d[2] = b == k + 1 ? -mu : mu;
+            return kGoOn;
+        }
+    }
+    const R n1 = R(a.n[k]);
+    const R n2 = b == k + 1 ? (b == a.n_layers ? R(a.n_above) : R(a.n[k + 1])) : (b == 0 ? R(a.n_below) : R(a.n[k - 1]));
+    if (st.next<R>() < fresnel<R>(n1, n2, ci)) {
+        d[2] = -d[2];
+        return kGoOn;
+    }
+    if (b == 0 || b == a.n_layers) return ANTS_PH_ESCAPED;
+    const R eta = n1 / n2, ct = M<R>::sqrt(fmax(R(0), R(1) - eta * eta * (R(1) - ci * ci)));
+    d[0] *= eta;
+    d[1] *= eta;
+    d[2] = d[2] > R(0) ? ct : -ct;
+    k = b == k + 1 ? k + 1 : k - 1;
+    return kGoOn;
 }
 
 // grid (photon blocks, sources): each block traces a strided share of one
@@ -252,11 +277,22 @@ __global__ void __launch_bounds__(kOptThreads) trace_kernel(const __grid_constan
         s_sy[i] = R(a.sy[i]);
     }
     __syncthreads();
+    // a lane whose photon ends starts its next one at once, so the lanes of a
+    // warp stay busy however long the individual paths are
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_ph; p += stride) {
-        const int o = trace_photon<R>(a, s_sx, s_sy, q, (uint32_t)p);
-        if (o >= 0) atomicAdd(&hist[o], 1);
-        if (a.outcome) a.outcome[(size_t)q * a.n_ph + p] = (int16_t)o;
+    long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    Photon<R> ph;
+    bool have = p < a.n_ph;
+    int o = have ? photon_start<R>(a, ph, q, (uint32_t)p) : kGoOn;
+    while (have) {
+        if (o == kGoOn) o = photon_cycle<R>(a, s_sx, s_sy, ph);
+        if (o != kGoOn) {
+            if (o >= 0) atomicAdd(&hist[o], 1);
+            if (a.outcome) a.outcome[(size_t)q * a.n_ph + p] = (int16_t)o;
+            p += stride;
+            have = p < a.n_ph;
+            if (have) o = photon_start<R>(a, ph, q, (uint32_t)p);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < a.n_s; i += blockDim.x)
