@@ -293,6 +293,8 @@ typedef struct {
     int shift_cycles;      /* ... during the first shift_cycles cycles */
     uint64_t seed;
     double ridge;
+    int method;                    /* the reconstruction of every cycle: ANTS_CGS_PLAIN (cgs) or ANTS_MINIMIZE */
+    ants_minimize_params minimize; /* with ANTS_MINIMIZE (from its own start, no start_xyz) */
 } ants_iter_params;
 
 /* Per-cycle record of ants_lrf_iterate. */
@@ -760,7 +762,9 @@ ANTS_API int ants_lrf_refit(ants_ctx *ctx, const ants_lrf *lrf, const float *sig
 
 /* Iterative LRF reconstruction from flood data (Sec. 8): starting from
  * lrf_init, each of p->cycles cycles reconstructs all events with the current
- * LRFs (ants_reconstruct, ANTS_CGS_PLAIN, p->cgs), computes their
+ * LRFs (ants_reconstruct with p->method: ANTS_CGS_PLAIN and p->cgs, or
+ * ANTS_MINIMIZE and p->minimize; the paper's procedure uses whichever
+ * reconstruction is configured), computes their
  * chi-squared, keeps the events that pass p->cuts and refits the LRFs from
  * them (ants_lrf_refit with the input's grouping, p->refit_gains, the shift
  * during the first p->shift_cycles cycles with cycle = the cycle number, and

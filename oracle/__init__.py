@@ -906,12 +906,14 @@ def centroid_lrf(lrf: Lrf, sig, gain_cog=None, shared=None, ridge: float = 0.0, 
     return lrf_refit(base, sig[ok], xyz[ok], S[ok], shared, False, ridge, mutant)
 
 
-def lrf_iterate(lrf0: Lrf, params: CgsParams, sig, cycles: int, cuts: EventCuts, shift_sigma: float = 0.0,
+def lrf_iterate(lrf0: Lrf, params, sig, cycles: int, cuts: EventCuts, shift_sigma: float = 0.0,
                 shift_cycles: int = 0, seed: int = 0, refit_gains: bool = False, gain_cog=None,
                 ridge: float = 0.0, mutant: int = 0):
     """Iterative LRF reconstruction from flood data (Sec. 8).  Each cycle:
-    reconstruct every event with the current LRFs (contracting grids,
-    Sec. 5.1.2.2), keep the events that pass the cuts (Sec. 5.2), offset the
+    reconstruct every event with the current LRFs (params: CgsParams for the
+    contracting grids, Sec. 5.1.2.2, or Minimize for the continuous
+    minimisation from the centroid, Sec. 5.1.2.1), keep the events that pass
+    the cuts (Sec. 5.2), offset the
     kept positions by seeded normal shifts during the first shift_cycles
     cycles, and refit the LRFs from the kept events (lrf_refit).  Returns the
     final LRFs and per-cycle statistics (events kept, their mean chi2 and
@@ -921,7 +923,10 @@ def lrf_iterate(lrf0: Lrf, params: CgsParams, sig, cycles: int, cuts: EventCuts,
     stats = []
     ssum = sig.sum(axis=1)
     for c in range(cycles):
-        r = cgs(L, params, sig, gain_cog=gain_cog, mutant=mutant)
+        if isinstance(params, Minimize):
+            r = minimize(L, sig, Variant(), params, gain=gain_cog, mutant=mutant)
+        else:
+            r = cgs(L, params, sig, gain_cog=gain_cog, mutant=mutant)
         chi2 = chi2_at(L, sig, r["xyz"], r["E"], mutant)
         keep = event_filter(r["status"], r["xyz"], r["E"], chi2, ssum, cuts, mutant)
         idx = np.nonzero(keep)[0]

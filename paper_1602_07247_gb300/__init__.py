@@ -191,7 +191,8 @@ class RefitParams(C.Structure):
 class IterParams(C.Structure):
     """ants_iter_params: the cycles of Sec. 8."""
     _fields_ = [("cgs", CgsParams), ("cycles", C.c_int), ("cuts", EventCuts), ("refit_gains", C.c_int),
-                ("shift_sigma", C.c_double), ("shift_cycles", C.c_int), ("seed", C.c_uint64), ("ridge", C.c_double)]
+                ("shift_sigma", C.c_double), ("shift_cycles", C.c_int), ("seed", C.c_uint64), ("ridge", C.c_double),
+                ("method", C.c_int), ("minimize", MinimizeParams)]
 
 
 class IterStats(C.Structure):
@@ -793,11 +794,15 @@ class Lrf:
         L.shared = sh
         return L
 
-    def iterate(self, signals, cgs: CgsParams, cycles: int, cuts: EventCuts | None = None, refit_gains=False,
+    def iterate(self, signals, cgs, cycles: int, cuts: EventCuts | None = None, refit_gains=False,
                 shift_sigma=0.0, shift_cycles=0, seed=0, ridge=0.0):
-        """Iterative LRF reconstruction (ants_lrf_iterate): (new Lrf, per-cycle stats)."""
-        p = IterParams(cgs, int(cycles), cuts if cuts is not None else EventCuts(), int(refit_gains),
-                       float(shift_sigma), int(shift_cycles), int(seed), float(ridge))
+        """Iterative LRF reconstruction (ants_lrf_iterate): (new Lrf, per-cycle stats).  cgs: CgsParams
+        (contracting grids every cycle) or MinimizeParams (the continuous minimisation)."""
+        mini = isinstance(cgs, MinimizeParams)
+        p = IterParams(CgsParams() if mini else cgs, int(cycles), cuts if cuts is not None else EventCuts(),
+                       int(refit_gains), float(shift_sigma), int(shift_cycles), int(seed), float(ridge),
+                       ANTS_MINIMIZE if mini else ANTS_CGS_PLAIN, cgs if mini else MinimizeParams())
+        p._keep = cgs
         h, stats = ants_lrf_iterate(self.ctx.handle, self.handle, signals, p)
         L = Lrf(self.ctx, self.det, h, self.type)
         L.shared = self.shared

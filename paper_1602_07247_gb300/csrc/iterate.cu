@@ -574,7 +574,13 @@ extern "C" ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init
     if (p->cycles < 1 || p->shift_cycles < 0 || n_events < 1 || n_events > 0x7fffffffL || !signals_dev)
         return fail(ANTS_E_ARG, "ants_lrf_iterate: cycles >= 1, shift_cycles >= 0, 1 <= n_events < 2^31");
     IT_TRY(check_cuts(&p->cuts));
-    IT_TRY(check_cgs_params(lrf_init, &p->cgs));
+    if (p->method == ANTS_MINIMIZE) {
+        IT_TRY(check_minimize_params(lrf_init, &p->minimize));
+    } else if (p->method == ANTS_CGS_PLAIN) {
+        IT_TRY(check_cgs_params(lrf_init, &p->cgs));
+    } else {
+        return fail(ANTS_E_ARG, "ants_lrf_iterate: method must be ANTS_CGS_PLAIN or ANTS_MINIMIZE");
+    }
     ants_refit_params rp{lrf_init->shared, p->refit_gains, p->shift_sigma, p->seed, 0, p->ridge};
     IT_TRY(check_refit(lrf_init, &rp));
     if ((long)lrf_init->n_s * n_events > (1L << 30))
@@ -598,8 +604,11 @@ extern "C" ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init
     int rc = ANTS_OK;
     std::vector<double> part(2 * kStatBlocks);
     for (int c = 0; c < p->cycles && rc == ANTS_OK; ++c) {
-        rc = launch_cgs_plain(ctx, cur, p->cgs, signals_dev, n, nullptr, xyz, E, (float *)d_logL.p, status, nullptr,
-                              st);
+        rc = p->method == ANTS_MINIMIZE
+                 ? reconstruct_minimize(ctx, cur, p->minimize, signals_dev, n, nullptr, xyz, E, (float *)d_logL.p,
+                                        status, nullptr, st)
+                 : launch_cgs_plain(ctx, cur, p->cgs, signals_dev, n, nullptr, xyz, E, (float *)d_logL.p, status,
+                                    nullptr, st);
         if (rc != ANTS_OK) break;
         chi2_kernel<<<blocks_for(n, kEvWarps), 32 * kEvWarps, 0, st>>>(cur->dev, signals_dev, n, xyz, E, chi2, ssum);
         count_launch();

@@ -309,6 +309,30 @@ def test_iterate_matches_oracle(ctx):
     assert np.array_equal(again.coefficients(), got.coefficients())
 
 
+def test_iterate_with_minimisation_matches_oracle(ctx):
+    """The same procedure with the continuous minimisation as each cycle's
+    reconstruction (Sec. 5.1.2.1): GPU and oracle keep the same events and
+    end with the same profile."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    w, Lt, gains = _hex19()
+    sig, tr = oracle.simulate(Lt, 79, 0, 2000, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+    sig = _f32(sig)
+    L0 = _start_guess(w, gains)
+    cuts = dict(chi2_max=25.0)
+    want, st_o = oracle.lrf_iterate(L0, oracle.Minimize(max_iter=40, tol=1e-4), sig.astype(np.float64), 4,
+                                    oracle.EventCuts(**cuts), shift_sigma=1.0, shift_cycles=1, seed=9, gain_cog=gains)
+    lrf0 = _gpu_lrf(ctx, L0, w, det_gains=gains)
+    got, st_g = lrf0.iterate(torch.from_numpy(sig).cuda(), ants.MinimizeParams(max_iter=40, tol=1e-4), 4,
+                             ants.EventCuts(**cuts), shift_sigma=1.0, shift_cycles=1, seed=9)
+    for a, b in zip(st_g, st_o):
+        assert abs(a["n_kept"] - b["n_kept"]) <= 2, (a, b)
+        assert abs(a["mean_E"] / b["mean_E"] - 1) < 1e-4
+    r = np.linspace(0.0, 110.0, 56)
+    gp, wp = _profile(got.coefficients()[0], w, r), _profile(want.coef[0], w, r)
+    assert np.abs(gp - wp).max() < 2e-3 * np.abs(wp).max()
+
+
 def test_iterate_converges_and_equals_its_steps(ctx):
     """10^5 flood events: four GPU cycles bring the position error within 3 %
     of that with the true LRFs; the last cycle equals an explicit
