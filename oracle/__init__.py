@@ -90,6 +90,7 @@ class _Lrf(C.Structure):
         ("n_int_r", C.c_int),
         ("hi_r", C.c_double),
         ("n_planes", C.c_int),
+        ("group", C.POINTER(C.c_int)),
     ]
 
 
@@ -173,6 +174,7 @@ class Lrf:
     n_int_r: int = 0
     hi_r: float = 0.0
     n_planes: int = 0
+    group: np.ndarray | None = None
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -193,10 +195,12 @@ class Lrf:
         coef = _f64(self.coef)
         sxy = _f64(self.sensor_xy)
         gain = _f64(self.gain) if self.gain is not None else None
-        self._keep[:] = [coef, sxy, gain]
+        grp = np.ascontiguousarray(np.asarray(self.group, dtype=np.int32)) if self.group is not None else None
+        self._keep[:] = [coef, sxy, gain, grp]
         s.coef = _d(coef)
         s.sensor_xy = _d(sxy)
         s.gain = _d(gain) if gain is not None else C.cast(None, _D)
+        s.group = _i(grp) if grp is not None else C.cast(None, _I)
         return s
 
 
@@ -270,6 +274,18 @@ def lrf_eval(lrf: Lrf, pts, mutant: int = 0) -> np.ndarray:
     out = np.empty((pts.shape[0], lrf.n_sensors))
     lib(mutant).or_lrf_eval(C.byref(s), pts.shape[0], _d(pts), pts.shape[1], _d(out))
     return out
+
+
+def sensor_rings(sensor_xy, tol: float, mutant: int = 0):
+    """Sec. 6.2 grouping by distance from the array's centre: (group of each
+    sensor, number of groups); groups ordered outwards."""
+    sxy = _f64(sensor_xy)
+    g = np.empty(sxy.shape[0], dtype=np.int32)
+    L = lib(mutant)
+    L.or_sensor_rings.argtypes = [C.c_int, _D, C.c_double, _I]
+    L.or_sensor_rings.restype = C.c_int
+    k = L.or_sensor_rings(sxy.shape[0], _d(sxy), float(tol), _i(g))
+    return g, k
 
 
 def cog(sig, sensor_xy, gain=None, mutant: int = 0) -> np.ndarray:

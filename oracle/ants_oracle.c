@@ -187,7 +187,20 @@ typedef struct {
     int n_int_r;            /* composite: intervals of the axial part on [0, hi_r] */
     double hi_r;
     int n_planes;           /* sliced: number of z planes (>= 2) */
+    const int *group;       /* radial, not shared: nullable [n_sensors] coefficient set of each sensor (Sec. 6.2 groups) */
 } or_lrf;
+
+/* the coefficient set of sensor i of a radial LRF: one for all (shared), its
+ * group's (grouped) or its own */
+static int or_set_of(const or_lrf *L, int i)
+{
+    if (L->shared) return 0;
+#if OR_MUTANT == 29
+    return i;
+#else
+    return L->group ? L->group[i] : i;
+#endif
+}
 
 /* LRF types with a z coordinate, and with an XY box as domain */
 static int or_is_3d(int type) { return type == OR_XYZ || type == OR_AXIAL_Z || type == OR_SLICED; }
@@ -272,7 +285,7 @@ static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, i
 #endif
     }
     if (L->type == OR_RADIAL) {
-        const double *c = L->coef + (size_t)(L->shared ? 0 : i) * nc;
+        const double *c = L->coef + (size_t)or_set_of(L, i) * nc;
         double dx = x - L->sensor_xy[2 * i], dy = y - L->sensor_xy[2 * i + 1];
         double r = sqrt(dx * dx + dy * dy);
         double B[4];
@@ -306,6 +319,51 @@ static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, i
                 f += c[idx] * Bx[a] * By[b] * Bz[cz];
             }
     return f;
+}
+
+/* Sensor groups by distance from the array's centre (Sec. 6.2): the centre
+ * is the mean sensor position; sensors are taken in order of increasing
+ * distance d (ties by index) and a new group starts when d exceeds the
+ * distance of the current group's first sensor by more than tol.  group[i]
+ * receives the group of sensor i (0 = the innermost); returns the number of
+ * groups. */
+int or_sensor_rings(int n, const double *sensor_xy, double tol, int *group)
+{
+    double cx = 0.0, cy = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cx += sensor_xy[2 * i];
+        cy += sensor_xy[2 * i + 1];
+    }
+    cx /= n;
+    cy /= n;
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    int *order = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        d[i] = hypot(sensor_xy[2 * i] - cx, sensor_xy[2 * i + 1] - cy);
+        order[i] = i;
+    }
+    /* insertion sort by (d, index) */
+    for (int a = 1; a < n; ++a) {
+        int v = order[a], b = a - 1;
+        while (b >= 0 && (d[order[b]] > d[v] || (d[order[b]] == d[v] && order[b] > v))) {
+            order[b + 1] = order[b];
+            --b;
+        }
+        order[b + 1] = v;
+    }
+    int g = -1;
+    double first = 0.0;
+    for (int a = 0; a < n; ++a) {
+        int i = order[a];
+        if (g < 0 || d[i] - first > tol) {
+            ++g;
+            first = d[i];
+        }
+        group[i] = g;
+    }
+    free(d);
+    free(order);
+    return g + 1;
 }
 
 /* eta for every (point, sensor): out[p * n_sensors + i]; NaN outside. */
@@ -1115,7 +1173,7 @@ static double or_lrf_eta_grad(const or_lrf *L, int i, double x, double y, double
     g[0] = g[1] = g[2] = 0.0;
     *ok = 1;
     if (L->type == OR_RADIAL || L->type == OR_COMPOSITE) {
-        const double *c = L->coef + (size_t)(L->type == OR_RADIAL && L->shared ? 0 : i) * nc;
+        const double *c = L->coef + (size_t)(L->type == OR_RADIAL ? or_set_of(L, i) : i) * nc;
         int n = L->type == OR_RADIAL ? L->n_int[0] : L->n_int_r;
         double lo = L->type == OR_RADIAL ? L->lo[0] : 0.0, hi = L->type == OR_RADIAL ? L->hi[0] : L->hi_r;
         double B[4], D[4];

@@ -1269,3 +1269,50 @@ def pin_optics_diffuse_and_prereject(mutant=0):
 
 ALL_PINS += [pin_optics_solid_angle, pin_optics_absorption, pin_fresnel, pin_rayleigh_and_turn, pin_optics_fresnel_mc,
              pin_optics_diffuse_and_prereject]
+
+
+# --------------------------------------------------------------------------
+# Sensor groups (Sec. 6.2)
+# --------------------------------------------------------------------------
+
+
+def pin_sensor_groups(mutant=0):
+    """A grouped radial LRF evaluates sensor i with its group's profile times
+    its gain: equal to the per-sensor LRF whose rows are the groups' rows,
+    to the shared LRF when there is one group. Grouping by distance from
+    the centre: the 19-PMT hexagon has rings of 1, 6, 6 and 6 sensors at 0,
+    p, sqrt(3) p and 2 p; an 8 x 8 square array has one group per distinct
+    distance |(a, b)|, a, b in {3, 9, 15, 21} mm, whose sizes count the
+    sensors at that distance."""
+    w = synth.workloads.get("hex19_radial")
+    g, k = oracle.sensor_rings(w.sensor_xy, 1.0, mutant)
+    assert k == 4 and list(np.bincount(g)) == [1, 6, 6, 6], (k, np.bincount(g))
+    d = np.hypot(*(w.sensor_xy - w.sensor_xy.mean(0)).T)
+    for j, r in enumerate((0.0, 30.0, 30.0 * np.sqrt(3.0), 60.0)):
+        assert np.allclose(d[g == j], r, atol=1e-9)
+    sq = synth.square_array(8, 6.0)
+    g8, k8 = oracle.sensor_rings(sq, 0.01, mutant)
+    a = np.array([3.0, 9.0, 15.0, 21.0])
+    dist = sorted({round(float(np.hypot(x, y)), 6) for x in a for y in a})
+    assert k8 == len(dist)
+    dd = np.hypot(*(sq - sq.mean(0)).T)
+    for j, r in enumerate(dist):
+        assert np.all(np.abs(dd[g8 == j] - r) < 1e-6)
+    # evaluation with groups
+    rng = np.random.default_rng(8)
+    prof = 0.04 / (1 + (np.linspace(-7.5, 157.5, 23) / 40.0) ** 2) ** 1.5
+    rows = prof[None, :] * rng.uniform(0.9, 1.1, (k, 23))
+    gains = rng.uniform(0.9, 1.1, 19)
+    G = oracle.Lrf(oracle.RADIAL, w.sensor_xy, (20, 0, 0), (0.0, 0.0, 0.0), (150.0, 0.0, 0.0), rows, gain=gains,
+                   group=g)
+    P = oracle.Lrf(oracle.RADIAL, w.sensor_xy, (20, 0, 0), (0.0, 0.0, 0.0), (150.0, 0.0, 0.0), rows[g], gain=gains)
+    pts = rng.uniform(-50.0, 50.0, (200, 2))
+    assert np.array_equal(oracle.lrf_eval(G, pts, mutant), oracle.lrf_eval(P, pts, mutant))
+    one = oracle.Lrf(oracle.RADIAL, w.sensor_xy, (20, 0, 0), (0.0, 0.0, 0.0), (150.0, 0.0, 0.0), rows[:1],
+                     gain=gains, group=np.zeros(19, dtype=np.int32))
+    sh = oracle.Lrf(oracle.RADIAL, w.sensor_xy, (20, 0, 0), (0.0, 0.0, 0.0), (150.0, 0.0, 0.0), rows[:1],
+                    gain=gains, shared=True)
+    assert np.array_equal(oracle.lrf_eval(one, pts, mutant), oracle.lrf_eval(sh, pts, mutant))
+
+
+ALL_PINS += [pin_sensor_groups]

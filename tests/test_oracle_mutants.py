@@ -34,6 +34,7 @@ MUTANTS = {
     26: "sensor window test with the full side as half-width",
     27: "pre-rejection discarding the photons it should trace",
     28: "absorption range L u instead of -L ln u",
+    29: "grouped radial LRFs reading each sensor's own coefficient row",
 }
 
 
