@@ -394,6 +394,26 @@ ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, con
                           const double *pts_host, const double *vals_host, double ridge,
                           double *ridge_used, ants_lrf **out);
 
+/* A grouped RADIAL LRF set (Sec. 6.2: sensors of a group share one LRF
+ * profile; each keeps its relative gain): group_host[i] in [0, n_groups) is
+ * the group of sensor i, coef_host [n_groups][n_int[0] + 3] the groups'
+ * profiles (FP64, uploaded as FP32), gain_host (nullable, default 1) the
+ * per-sensor gains multiplying them.  Knot grid as ants_lrf_create.  Usable
+ * wherever a RADIAL set is (search, simulation, evaluation, forms); not
+ * saved or refitted (ANTS_E_UNIMPLEMENTED).  Errors: ANTS_E_ARG, ANTS_E_OOM,
+ * ANTS_E_CUDA. */
+ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
+                                     const double *hi, int n_groups, const int *group_host, const double *coef_host,
+                                     const double *gain_host, ants_lrf **out);
+
+/* Groups by distance from the array's centre (Sec. 6.2): the centre is the
+ * mean sensor position; sensors in order of increasing distance d (ties by
+ * index) start a new group when d exceeds the distance of the current
+ * group's first sensor by more than tol (mm).  group_host [n_sensors]
+ * receives each sensor's group (0 = innermost), *n_groups_out their count.
+ * Host only.  Errors: ANTS_E_ARG. */
+ANTS_API int ants_sensor_rings(const ants_detector *det, double tol, int *group_host, int *n_groups_out);
+
 /* LRF sets of the other parameterisation schemes (Sec. 6.1.1, 6.1.2), one
  * coefficient set per sensor, coef_host [n_sensors][n_coef]:
  *   ANTS_LRF_COMPOSITE: the axial part, n_int_r + 3 coefficients of a cubic

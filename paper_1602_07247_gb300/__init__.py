@@ -274,6 +274,8 @@ def lib() -> C.CDLL:
                                           _DP, _DP, C.c_double, C.POINTER(_VP)]
         L.ants_event_centroid.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP]
         L.ants_trace_photons.argtypes = [_VP, _VP, _VP, C.c_long, C.c_long, C.c_uint64, C.c_int, _VP, _VP, _VP, _VP]
+        L.ants_lrf_create_grouped.argtypes = [_VP, _VP, _IP, _DP, _DP, C.c_int, _IP, _DP, _DP, C.POINTER(_VP)]
+        L.ants_sensor_rings.argtypes = [_VP, C.c_double, _IP, _IP]
         L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
         L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
                                         C.POINTER(C.c_long), _VP]
@@ -727,6 +729,10 @@ class Detector:
         self.n_sensors = int(self.sensor_xy.shape[0])
         self.handle = ants_detector_create(self.sensor_xy, rel_gain)
 
+    def rings(self, tol: float = 1e-3):
+        """Sec. 6.2 grouping by distance from the array's centre: (group of each sensor, number of groups)."""
+        return ants_sensor_rings(self.handle, self.n_sensors, tol)
+
     def __del__(self):
         if getattr(self, "handle", None):
             ants_detector_free(self.handle)
@@ -746,6 +752,12 @@ class Lrf:
         L = cls(ctx, det, ants_lrf_create(ctx.handle, det.handle, type, n_int, lo, hi, shared, coef, gain), type)
         L.shared = bool(shared)
         return L
+
+    @classmethod
+    def from_groups(cls, ctx, det, n_int, lo, hi, group, coef, gain=None):
+        """A grouped RADIAL set (ants_lrf_create_grouped): one profile per group, per-sensor gains."""
+        return cls(ctx, det, ants_lrf_create_grouped(ctx.handle, det.handle, n_int, lo, hi, group, coef, gain),
+                   ANTS_LRF_RADIAL)
 
     @classmethod
     def fit(cls, ctx, det, type, n_int, lo, hi, pts, vals, shared=False, ridge=0.0):
@@ -876,6 +888,28 @@ class Result:
     logL: object
     status: object
     trace: object = None
+
+
+def ants_lrf_create_grouped(ctx: int, det: int, n_int, lo, hi, group, coef, gain=None) -> int:
+    g = np.ascontiguousarray(np.asarray(group, dtype=np.int32))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
+    gn = None if gain is None else np.ascontiguousarray(np.asarray(gain, dtype=np.float64))
+    ni = (C.c_int * 1)(int(n_int[0]))
+    lo_ = (C.c_double * 1)(float(lo[0]))
+    hi_ = (C.c_double * 1)(float(hi[0]))
+    h = _VP()
+    _check(lib().ants_lrf_create_grouped(ctx, det, ni, lo_, hi_, int(c.shape[0]), g.ctypes.data_as(_IP),
+                                         c.ctypes.data_as(_DP), None if gn is None else gn.ctypes.data_as(_DP),
+                                         C.byref(h)))
+    return h.value
+
+
+def ants_sensor_rings(det: int, n_sensors: int, tol: float):
+    """(group of each sensor, number of groups) by distance from the array's centre."""
+    g = np.empty(n_sensors, dtype=np.int32)
+    k = C.c_int()
+    _check(lib().ants_sensor_rings(det, float(tol), g.ctypes.data_as(_IP), C.byref(k)))
+    return g, k.value
 
 
 def ants_trace_photons(ctx: int, params: OpticsParams, src_xyz, n_photons: int, seed: int, precision: int, counts,

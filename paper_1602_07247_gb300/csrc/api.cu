@@ -1,4 +1,5 @@
 // libants: handles, errors, LRF storage and evaluation, host-buffer driver.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -235,6 +236,14 @@ static int upload_lrf(ants_lrf *L)
     LrfDev &D = L->dev;
     D.coef2 = nullptr;
     D.coef_t = nullptr;
+    D.set_of = nullptr;
+    D.n_sets = L->n_sets;
+    if (!L->groups.empty()) {
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_set_of, L->groups.size() * sizeof(int)), "cudaMalloc(lrf groups)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_set_of, L->groups.data(), L->groups.size() * sizeof(int), cudaMemcpyHostToDevice),
+                      "upload groups");
+        D.set_of = L->d_set_of;
+    }
     D.n_pairs = (L->n_s + 1) / 2;
     D.pair_stride = 0;
     if (L->type == ANTS_LRF_XY) {
@@ -315,6 +324,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_cogw);
     cudaFree(lrf->d_coef2);
     cudaFree(lrf->d_coeft);
+    cudaFree(lrf->d_set_of);
     cudaFree(lrf->d_rpoly);
     delete lrf;
     (void)cudaGetLastError();
@@ -326,9 +336,18 @@ namespace ants {
 
 int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
                     const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
-                    double hi_r, int n_planes, ants_lrf **out)
+                    double hi_r, int n_planes, ants_lrf **out, int n_groups, const int *group)
 {
     *out = nullptr;
+    if (group) {
+        if (type != ANTS_LRF_RADIAL || shared || !det)
+            return fail(ANTS_E_ARG, "ants_lrf_create_grouped: groups need a RADIAL LRF that is not shared");
+        if (n_groups < 1 || n_groups > det->n_s)
+            return fail(ANTS_E_ARG, "ants_lrf_create_grouped: 1 <= n_groups <= n_sensors");
+        for (int i = 0; i < det->n_s; ++i)
+            if (group[i] < 0 || group[i] >= n_groups)
+                return fail(ANTS_E_ARG, "ants_lrf_create_grouped: sensor %d in group %d of %d", i, group[i], n_groups);
+    }
     if (!ctx || !det || !n_int || !lo || !hi || !coef_host)
         return fail(ANTS_E_ARG, "ants_lrf_create: NULL argument");
     if (type < ANTS_LRF_RADIAL || type > ANTS_LRF_SLICED)
@@ -377,7 +396,8 @@ int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int
         L->hi[2] = hi[2];
         L->n_coef *= n_planes;
     }
-    L->n_sets = L->shared ? 1 : L->n_s;
+    L->n_sets = L->shared ? 1 : group ? n_groups : L->n_s;
+    if (group) L->groups.assign(group, group + L->n_s);
     size_t nc = (size_t)L->n_sets * L->n_coef;
     L->coef.assign(coef_host, coef_host + nc);
     for (size_t k = 0; k < nc; ++k)
@@ -414,6 +434,51 @@ ANTS_API int ants_lrf_create(ants_ctx *ctx, const ants_detector *det, int type, 
     if (type != ANTS_LRF_RADIAL && type != ANTS_LRF_XY && type != ANTS_LRF_XYZ)
         return fail(ANTS_E_ARG, "ants_lrf_create: type %d (the other schemes: ants_lrf_create_scheme)", type);
     return lrf_create_impl(ctx, det, type, n_int, lo, hi, shared, coef_host, gain_host, 0, 0.0, 0, out);
+}
+
+ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
+                                     const double *hi, int n_groups, const int *group_host, const double *coef_host,
+                                     const double *gain_host, ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create_grouped: out is NULL");
+    *out = nullptr;
+    if (!group_host) return fail(ANTS_E_ARG, "ants_lrf_create_grouped: group_host is NULL");
+    return lrf_create_impl(ctx, det, ANTS_LRF_RADIAL, n_int, lo, hi, 0, coef_host, gain_host, 0, 0.0, 0, out, n_groups,
+                           group_host);
+}
+
+ANTS_API int ants_sensor_rings(const ants_detector *det, double tol, int *group_host, int *n_groups_out)
+{
+    begin_call();
+    if (!det || !group_host || !n_groups_out) return fail(ANTS_E_ARG, "ants_sensor_rings: NULL argument");
+    if (!(tol >= 0.0)) return fail(ANTS_E_ARG, "ants_sensor_rings: tol must be >= 0");
+    const int n = det->n_s;
+    double cx = 0.0, cy = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cx += det->xy[2 * i];
+        cy += det->xy[2 * i + 1];
+    }
+    cx /= n;
+    cy /= n;
+    std::vector<double> d(n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) {
+        d[i] = std::hypot(det->xy[2 * i] - cx, det->xy[2 * i + 1] - cy);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
+    int g = -1;
+    double first = 0.0;
+    for (int i : order) {
+        if (g < 0 || d[i] - first > tol) {
+            ++g;
+            first = d[i];
+        }
+        group_host[i] = g;
+    }
+    *n_groups_out = g + 1;
+    return ANTS_OK;
 }
 
 ANTS_API int ants_lrf_create_scheme(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
@@ -496,7 +561,8 @@ ANTS_API int ants_lrf_save(const ants_lrf *lrf, const char *path)
 {
     begin_call();
     if (!lrf || !path) return fail(ANTS_E_ARG, "ants_lrf_save: NULL argument");
-    if (lrf->type > ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "ants_lrf_save: RADIAL, XY and XYZ sets only");
+    if (lrf->type > ANTS_LRF_XYZ || !lrf->groups.empty())
+        return fail(ANTS_E_UNIMPLEMENTED, "ants_lrf_save: ungrouped RADIAL, XY and XYZ sets only");
     FILE *f = fopen(path, "wb");
     if (!f) return fail(ANTS_E_IO, "ants_lrf_save: cannot open %s", path);
     int32_t hdr[8] = {1, lrf->type, lrf->n_s, lrf->shared, lrf->n_int[0], lrf->n_int[1], lrf->n_int[2],

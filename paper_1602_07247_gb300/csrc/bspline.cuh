@@ -98,7 +98,7 @@ __device__ __forceinline__ float radial_profile(const float4 *poly, float inv_h,
 // the power-basis cubics of sensor i's axial LRF
 __device__ __forceinline__ const float4 *radial_poly(const LrfDev &L, int i)
 {
-    return L.rpoly + (L.shared ? 0 : i * L.n_int[0]);
+    return L.rpoly + (L.shared ? 0 : (L.set_of ? __ldg(L.set_of + i) : i)) * L.n_int[0];
 }
 
 // axial LRF of sensor i at distance r (caller checks r <= hi)

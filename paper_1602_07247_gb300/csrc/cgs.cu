@@ -314,7 +314,7 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
             const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
             const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
             const float gi = __ldg(L.gain + i);
-            const float4 *poly = polys + (L.shared ? 0 : i * n_int);
+            const float4 *poly = polys + (L.shared ? 0 : (L.set_of ? __ldg(L.set_of + i) : i)) * n_int;
             const unsigned sp = SPOLY ? (unsigned)__cvta_generic_to_shared(poly) : 0u;
 #pragma unroll
             for (int m = 0; m < NPL; ++m) {
@@ -647,7 +647,7 @@ int launch_typed(const ants_ctx *ctx, CgsArgs a, cudaStream_t stream, bool allow
     // radial cubics in shared memory when they take at most 32 KB
     int n_poly = 0;
     if (TYPE == ANTS_LRF_RADIAL) {
-        const long np = (long)(a.L.shared ? 1 : a.L.n_s) * a.L.n_int[0];
+        const long np = (long)a.L.n_sets * a.L.n_int[0];
         if (np * 16 <= 32 * 1024) {
             n_poly = (int)np;
             smem = ((smem + 15) & ~(size_t)15) + (size_t)np * 16;

@@ -48,6 +48,8 @@ struct LrfDev {
     // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
     const float2 *coef2;
     const float *coef_t;   // XY: the coefficients sensor-minor, [k][n_s] (per-point loops over sensors)
+    const int *set_of;     // RADIAL grouped (Sec. 6.2): the coefficient set of each sensor; nullable
+    int n_sets;            // coefficient sets
     // RADIAL LRFs: each interval's cubic in the power basis of its local
     // parameter t, (p0, p1, p2, p3) with f = p0 + t (p1 + t (p2 + t p3)),
     // [n_sets][n_int[0]]
@@ -108,6 +110,8 @@ struct ants_lrf {
     float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
     float2 *d_coef2 = nullptr;
     float *d_coeft = nullptr;
+    int *d_set_of = nullptr;
+    std::vector<int> groups;       // RADIAL grouped: the group of each sensor (empty otherwise)
     float4 *d_rpoly = nullptr;
     ants::LrfDev dev{};
 };
@@ -126,7 +130,8 @@ __host__ __device__ inline bool lrf_has_box(int type)
 // any LRF type: create from coefficients (api.cu)
 int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
                     const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
-                    double hi_r, int n_planes, ants_lrf **out);
+                    double hi_r, int n_planes, ants_lrf **out, int n_groups = 0,
+                    const int *group = nullptr);
 // launches of the reconstruction kernels (cgs.cu)
 int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p,
                      const float *sig, long n_e, const float *start, float *xyz, float *E,
