@@ -882,8 +882,10 @@ def lrf_refit(lrf: Lrf, sig, xyz, E, shared=None, refit_gains: bool = False, rid
     refit_gains the gains are then refitted with the new profile fixed
     (Sec. 6.3) and scaled to mean 1, the profile taking the inverse factor so
     that g_i f is unchanged.  RADIAL per sensor: one fit of (r_ei, v_ei) per
-    sensor, gains 1.  The knot grid is the input's; `shared` (default: the
-    input's) selects grouped or per-sensor output for RADIAL."""
+    sensor, gains 1.  RADIAL with sensor groups (lrf.group): one profile per
+    group, gains refitted within each group.  The knot grid is the input's;
+    `shared` (default: the input's) selects grouped or per-sensor output for
+    RADIAL without groups."""
     sig, xyz, E = _f64(sig), _f64(xyz), _f64(E)
     shared = lrf.shared if shared is None else bool(shared)
     v = sig / E[:, None]
@@ -894,6 +896,24 @@ def lrf_refit(lrf: Lrf, sig, xyz, E, shared=None, refit_gains: bool = False, rid
         return Lrf(lrf.type, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, coef)
     d = xyz[:, None, :2] - lrf.sensor_xy[None, :, :]
     r = np.sqrt(d[..., 0] ** 2 + d[..., 1] ** 2)
+    if lrf.group is not None:
+        # groups (Sec. 6.2): one profile per group from its sensors' samples
+        # divided by their gains; with refit_gains each sensor's gain against
+        # its group's new profile, scaled to mean 1 within the group
+        grp = np.asarray(lrf.group)
+        k = int(grp.max()) + 1
+        g = np.ones(n_s) if lrf.gain is None else _f64(lrf.gain).copy()
+        coef = np.zeros((k, lrf.n_int[0] + 3))
+        for j in range(k):
+            m = np.nonzero(grp == j)[0]
+            coef[j], _, _ = lrf_fit(lrf.n_int, lrf.lo, lrf.hi, r[:, m].reshape(-1), (v[:, m] / g[None, m]).reshape(-1),
+                                    ridge, mutant)
+            if refit_gains:
+                gj = gain_refit(lrf.n_int[0], lrf.lo[0], lrf.hi[0], coef[j], r[:, m], v[:, m], mutant)
+                gm = gj.mean()
+                g[m] = gj / gm
+                coef[j] = coef[j] * gm
+        return Lrf(RADIAL, lrf.sensor_xy, lrf.n_int, lrf.lo, lrf.hi, coef, gain=g, group=grp.copy())
     if not shared:
         coef = np.concatenate([lrf_fit(lrf.n_int, lrf.lo, lrf.hi, r[:, i], v[:, i], ridge, mutant)[0]
                                for i in range(n_s)])

@@ -1316,3 +1316,45 @@ def pin_sensor_groups(mutant=0):
 
 
 ALL_PINS += [pin_sensor_groups]
+
+
+def pin_grouped_refit_exact(mutant=0):
+    """Noise-free signals E g_i f_{group(i)}(r) of the hexagon's four rings:
+    the grouped refit recovers each ring's profile where it is sampled, and
+    with the gain refit the planted gains scaled to mean 1 within each ring
+    (the ring's profile taking the mean), eta = g f unchanged."""
+    rng = np.random.default_rng(14)
+    w = synth.workloads.get("hex19_radial")
+    g, k = oracle.sensor_rings(w.sensor_xy, 1.0, mutant)
+    pts, vals = w.fit_samples()
+    base, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals, mutant=mutant)
+    rows = base[0][None, :] * rng.uniform(0.8, 1.2, (k, 1))
+    gains = rng.uniform(0.85, 1.15, 19)
+    Lt = oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), rows, gain=gains,
+                    group=g)
+    xy = rng.uniform(-60, 60, (3000, 2))
+    xyz = np.concatenate([xy, np.zeros((3000, 1))], axis=1)
+    E = rng.uniform(5000, 15000, 3000)
+    s = E[:, None] * np.nan_to_num(oracle.lrf_eval(Lt, xy, mutant))
+    # each ring's profile is compared where its sensors have samples (the
+    # unsampled tail is set by the ridge fallback)
+    dist = np.hypot(xy[:, None, 0] - w.sensor_xy[None, :, 0], xy[:, None, 1] - w.sensor_xy[None, :, 1])
+    reach = [0.95 * dist[:, g == j].max() for j in range(k)]
+    prof = lambda c, j: oracle.spline_eval(w.n_int, w.lo, w.hi, c, np.linspace(0.0, reach[j], 60)[:, None], mutant)
+    R = oracle.lrf_refit(Lt, s, xyz, E, mutant=mutant)
+    for j in range(k):
+        # 1e-6: the innermost ring is one sensor with few samples near r = 0
+        assert np.abs(prof(R.coef[j], j) - prof(rows[j], j)).max() < 1e-6 * prof(rows[j], j).max(), j
+    # from unit gains: the gain refit recovers the planted ones up to each ring's scale
+    L1 = oracle.Lrf(oracle.RADIAL, w.sensor_xy, w.n_int + (0, 0), w.lo + (0, 0), w.hi + (0, 0), rows, gain=gains,
+                    group=g)
+    R2 = oracle.lrf_refit(L1, s, xyz, E, refit_gains=True, mutant=mutant)
+    for j in range(k):
+        m = g == j
+        want = gains[m] / gains[m].mean()
+        assert np.abs(R2.gain[m] - want).max() < 1e-7, j
+        want_p = prof(rows[j], j) * gains[m].mean()
+        assert np.abs(prof(R2.coef[j], j) - want_p).max() < 1e-6 * want_p.max(), j
+
+
+ALL_PINS += [pin_grouped_refit_exact]
