@@ -399,9 +399,9 @@ ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, con
  * the group of sensor i, coef_host [n_groups][n_int[0] + 3] the groups'
  * profiles (FP64, uploaded as FP32), gain_host (nullable, default 1) the
  * per-sensor gains multiplying them.  Knot grid as ants_lrf_create.  Usable
- * wherever a RADIAL set is (search, simulation, evaluation, forms); not
- * saved or refitted (ANTS_E_UNIMPLEMENTED).  Errors: ANTS_E_ARG, ANTS_E_OOM,
- * ANTS_E_CUDA. */
+ * wherever a RADIAL set is (search, simulation, evaluation, forms, refit and
+ * iteration); not saved (ANTS_E_UNIMPLEMENTED).  Errors: ANTS_E_ARG,
+ * ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
                                      const double *hi, int n_groups, const int *group_host, const double *coef_host,
                                      const double *gain_host, ants_lrf **out);
@@ -773,6 +773,11 @@ ANTS_API int ants_event_filter(ants_ctx *ctx, long n_events, const int32_t *stat
  *     g_i = sum f(r) v / sum f(r)^2 (Sec. 6.3), and scaled to mean 1, the
  *     profile taking the inverse factor.
  *   RADIAL without p->shared: one fit of (r_ei, v_ei) per sensor, gains 1.
+ *   RADIAL with sensor groups (ants_lrf_create_grouped; p->shared ignored):
+ *     one fit per group of its sensors' (r_ei, v_ei/g_i); with
+ *     p->refit_gains each sensor's gain against its group's new profile,
+ *     scaled to mean 1 within the group (the group's profile taking the
+ *     factor).  The output keeps the groups.
  * The output has the input's knot grid, sensors and relative gains.
  * Synchronous.  Errors: ANTS_E_ARG, ANTS_E_LRF (a fit stayed singular, e.g.
  * no events), ANTS_E_OOM, ANTS_E_CUDA. */

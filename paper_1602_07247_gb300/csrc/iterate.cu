@@ -278,7 +278,7 @@ __global__ void samples_box(const int32_t *index, long n_kept, int dims, int n_s
 // [k][i]
 __global__ void samples_radial(const int32_t *index, long n_kept, int n_s, const float *xyz, const float *sig,
                                const float *E, const double *sxy, const double *inv_g, ShiftArgs sh, int by_sensor,
-                               double *r, double *v)
+                               const int *row_of, double *r, double *v)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_kept) return;
@@ -292,7 +292,7 @@ __global__ void samples_radial(const int32_t *index, long n_kept, int n_s, const
         const double rr = sqrt(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
         double vv = (double)sig[e * n_s + i] * inv_e;
         if (inv_g) vv *= inv_g[i];
-        const long o = by_sensor ? (long)i * n_kept + k : k * n_s + i;
+        const long o = by_sensor ? (long)(row_of ? row_of[i] : i) * n_kept + k : k * n_s + i;
         r[o] = rr;
         v[o] = vv;
     }
@@ -302,16 +302,20 @@ __global__ void samples_radial(const int32_t *index, long n_kept, int n_s, const
 // over the samples with r inside [0, hi]; one block per sensor
 constexpr int kGainThreads = 256;
 
-__global__ void __launch_bounds__(kGainThreads) gain_sums(const double *coef, int n_int, double hi, long n_kept, int n_s,
-                                                          const double *r, const int32_t *index, const float *sig,
-                                                          const float *E, double *g)
+// (samples event-major, or by sensor in rows row_of[i] when row_of is given;
+// sensor i's profile at coef + set_of[i] * nc when set_of is given)
+__global__ void __launch_bounds__(kGainThreads) gain_sums(const double *coef_all, int n_int, double hi, long n_kept,
+                                                          int n_s, const double *r, const int32_t *index,
+                                                          const float *sig, const float *E, const int *row_of,
+                                                          const int *set_of, int nc, double *g)
 {
     __shared__ double s_a[kGainThreads], s_b[kGainThreads];
     const int i = blockIdx.x;
+    const double *coef = coef_all + (set_of ? (size_t)set_of[i] * nc : 0);
     const double inv_h = (double)n_int / hi;
     double fv = 0.0, ff = 0.0;
     for (long k = threadIdx.x; k < n_kept; k += kGainThreads) {
-        const double rr = r[k * n_s + i];
+        const double rr = row_of ? r[(long)row_of[i] * n_kept + k] : r[k * n_s + i];
         if (!(rr >= 0.0 && rr <= hi)) continue;
         const double u = rr * inv_h;
         int j = (int)floor(u);
@@ -348,8 +352,12 @@ int make_like(ants_ctx *ctx, const ants_lrf *like, int shared, const std::vector
     det.xy = like->sxy;
     det.gain = like->rel_gain;
     const long launches = ants_last_launch_count();
-    const int rc = ants_lrf_create(ctx, &det, like->type, like->n_int, like->lo, like->hi, shared, coef.data(),
-                                   gain ? gain->data() : nullptr, out);
+    const int rc = like->groups.empty()
+                       ? ants_lrf_create(ctx, &det, like->type, like->n_int, like->lo, like->hi, shared, coef.data(),
+                                         gain ? gain->data() : nullptr, out)
+                       : lrf_create_impl(ctx, &det, ANTS_LRF_RADIAL, like->n_int, like->lo, like->hi, 0, coef.data(),
+                                         gain ? gain->data() : nullptr, 0, 0.0, 0, out, like->n_sets,
+                                         like->groups.data());
     count_launch(launches);
     return rc;
 }
@@ -367,7 +375,10 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
     const size_t o_a = cv.take<double>(lrf->type == ANTS_LRF_RADIAL ? total : (size_t)n_kept * dims);
     const size_t o_b = cv.take<double>(total);
     const size_t o_sxy = cv.take<double>(2 * (size_t)n_s), o_g = cv.take<double>(n_s);
-    const size_t o_coef = cv.take<double>(nc), o_graw = cv.take<double>(n_s);
+    const bool grouped = !lrf->groups.empty();
+    const int n_sets = lrf->n_sets;
+    const size_t o_coef = cv.take<double>((size_t)nc * n_sets), o_graw = cv.take<double>(n_s);
+    const size_t o_row = cv.take<int>(n_s), o_set = cv.take<int>(n_s);
     char *base = (char *)ctx_scratch(ctx, 10, cv.off);
     if (!base) return ANTS_E_OOM;
     double *A = (double *)(base + o_a), *B = (double *)(base + o_b);
@@ -387,16 +398,66 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
                   "refit: upload sensors");
     // a per-sensor input has no group gains: its values are divided by 1
     std::vector<double> g_in(n_s, 1.0), inv_g(n_s);
-    if (lrf->shared) g_in = lrf->gain;
+    if (lrf->shared || grouped) g_in = lrf->gain;
+    // grouped: the samples of each group's sensors in consecutive rows
+    std::vector<int> row(n_s), first(n_sets + 1, 0);
+    int *d_row = (int *)(base + o_row), *d_set = (int *)(base + o_set);
+    if (grouped) {
+        for (int i = 0; i < n_s; ++i) first[lrf->groups[i] + 1]++;
+        for (int j = 0; j < n_sets; ++j) first[j + 1] += first[j];
+        std::vector<int> fill(first.begin(), first.end() - 1);
+        for (int i = 0; i < n_s; ++i) row[i] = fill[lrf->groups[i]]++;
+        ANTS_CUDA_TRY(cudaMemcpyAsync(d_row, row.data(), n_s * sizeof(int), cudaMemcpyHostToDevice, st),
+                      "refit: upload rows");
+        ANTS_CUDA_TRY(cudaMemcpyAsync(d_set, lrf->groups.data(), n_s * sizeof(int), cudaMemcpyHostToDevice, st),
+                      "refit: upload groups");
+    }
     for (int i = 0; i < n_s; ++i) inv_g[i] = 1.0 / g_in[i];
     ANTS_CUDA_TRY(cudaMemcpyAsync(d_g, inv_g.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
                   "refit: upload gains");
     double *r = A, *v = B;
     if (total > 0) {
         samples_radial<<<blocks_for(n_kept, T), T, 0, st>>>(index, n_kept, n_s, xyz, sig, E, d_sxy,
-                                                            p.shared ? d_g : nullptr, sh, p.shared ? 0 : 1, r, v);
+                                                            p.shared || grouped ? d_g : nullptr, sh,
+                                                            p.shared && !grouped ? 0 : 1, grouped ? d_row : nullptr,
+                                                            r, v);
         ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
         count_launch();
+    }
+    if (grouped) {
+        std::vector<double> coef((size_t)n_sets * nc);
+        for (int j = 0; j < n_sets; ++j) {
+            const long np = (long)(first[j + 1] - first[j]) * n_kept;
+            if (np == 0) return fail(ANTS_E_LRF, "refit: group %d has no sensor", j);
+            IT_TRY(lrf_fit_samples(ctx, 1, lrf->n_int, lrf->lo, lrf->hi, np, r + (size_t)first[j] * n_kept, 1,
+                                   v + (size_t)first[j] * n_kept, p.ridge, coef.data() + (size_t)j * nc, nullptr,
+                                   st));
+        }
+        std::vector<double> gains = g_in;
+        if (p.refit_gains) {
+            double *d_coef = (double *)(base + o_coef), *d_graw = (double *)(base + o_graw);
+            ANTS_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                          st),
+                          "refit: upload profiles");
+            gain_sums<<<n_s, kGainThreads, 0, st>>>(d_coef, lrf->n_int[0], lrf->hi[0], n_kept, n_s, r, index, sig, E,
+                                                    d_row, d_set, nc, d_graw);
+            ANTS_CUDA_TRY(cudaGetLastError(), "gain refit launch");
+            count_launch();
+            ANTS_CUDA_TRY(cudaMemcpyAsync(gains.data(), d_graw, n_s * sizeof(double), cudaMemcpyDeviceToHost, st),
+                          "refit: download gains");
+            ANTS_CUDA_TRY(cudaStreamSynchronize(st), "gain refit");
+            std::vector<double> gm(n_sets, 0.0);
+            for (int i = 0; i < n_s; ++i) {
+                if (!std::isfinite(gains[i]) || !(gains[i] > 0.0))
+                    return fail(ANTS_E_LRF, "gain refit: sensor %d has no usable samples", i);
+                gm[lrf->groups[i]] += gains[i];
+            }
+            for (int j = 0; j < n_sets; ++j) gm[j] /= (double)(first[j + 1] - first[j]);
+            for (int i = 0; i < n_s; ++i) gains[i] /= gm[lrf->groups[i]];
+            for (int j = 0; j < n_sets; ++j)
+                for (int c = 0; c < nc; ++c) coef[(size_t)j * nc + c] *= gm[j];
+        }
+        return make_like(ctx, lrf, 0, coef, &gains, out);
     }
     if (!p.shared) {
         std::vector<double> coef((size_t)n_s * nc);
@@ -413,7 +474,7 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
         ANTS_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st),
                       "refit: upload profile");
         gain_sums<<<n_s, kGainThreads, 0, st>>>(d_coef, lrf->n_int[0], lrf->hi[0], n_kept, n_s, r, index, sig, E,
-                                                d_graw);
+                                                nullptr, nullptr, nc, d_graw);
         ANTS_CUDA_TRY(cudaGetLastError(), "gain refit launch");
         count_launch();
         ANTS_CUDA_TRY(cudaMemcpyAsync(gains.data(), d_graw, n_s * sizeof(double), cudaMemcpyDeviceToHost, st),
@@ -471,11 +532,10 @@ int check_refit(const ants_lrf *lrf, const ants_refit_params *p)
     if (!p) return fail(ANTS_E_ARG, "refit parameters are NULL");
     if (!(p->shift_sigma >= 0.0) || !(p->ridge >= 0.0)) return fail(ANTS_E_ARG, "refit: shift_sigma, ridge >= 0");
     if (p->cycle < 0) return fail(ANTS_E_ARG, "refit: cycle < 0");
-    if (lrf->type > ANTS_LRF_XYZ || !lrf->groups.empty())
-        return fail(ANTS_E_UNIMPLEMENTED, "refit: ungrouped RADIAL, XY and XYZ LRFs only");
+    if (lrf->type > ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "refit: RADIAL, XY and XYZ LRFs only");
     if (lrf->type != ANTS_LRF_RADIAL && p->shared) return fail(ANTS_E_ARG, "refit: groups are RADIAL only");
-    if (p->refit_gains && !(lrf->type == ANTS_LRF_RADIAL && p->shared))
-        return fail(ANTS_E_ARG, "refit: gains are refitted for a RADIAL group only");
+    if (p->refit_gains && !(lrf->type == ANTS_LRF_RADIAL && (p->shared || !lrf->groups.empty())))
+        return fail(ANTS_E_ARG, "refit: gains are refitted for RADIAL groups only");
     return ANTS_OK;
 }
 

@@ -83,3 +83,37 @@ def test_grouped_simulation_and_limits(setup):
         lrf.save("/tmp/ants_grouped.lrf")
     with pytest.raises(ants.AntsError):
         ants.Lrf.from_groups(ctx, det, w.n_int, w.lo, w.hi, np.full(19, 4), np.ones((4, 23)))
+
+
+def test_grouped_refit_and_iteration(setup):
+    """The refit of the rings from reconstructed events equals the oracle's
+    FP64 refit of the same samples (profiles per ring, gains within rings);
+    three cycles of the iteration from the true rings keep the events and
+    stay at the truth's position error."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    ctx, w, det, g, k, L, lrf = setup
+    sig, tr = oracle.simulate(L, 33, 0, 3000, region="disk", extent=60.0, e0=1e4, e_spread=0.05)
+    sd = torch.from_numpy(sig.astype(np.float32)).cuda()
+    p = ants.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    res = ants.reconstruct(ctx, lrf, p, sd)
+    keep = np.nonzero(res.status.cpu().numpy() == 0)[0].astype(np.int32)
+    R = lrf.refit(sd, res.xyz, res.E, index=torch.from_numpy(keep).cuda(), refit_gains=True)
+    want = oracle.lrf_refit(L, sig[keep], res.xyz.cpu().numpy()[keep].astype(np.float64),
+                            res.E.cpu().numpy()[keep].astype(np.float64), refit_gains=True)
+    c = R.coefficients()
+    assert c.shape == want.coef.shape == (k, w.n_int[0] + 3)
+    assert np.abs(c - want.coef).max() <= 1e-9 * np.abs(want.coef).max()
+    assert np.abs(R.gains() - want.gain).max() <= 1e-9
+    # the iteration on 10^5 simulated flood events (the ring of one sensor
+    # needs the statistics)
+    n = 100_000
+    sp = ants.SimParams("disk", 60.0, 0.0, 0.0, 0.0, 0.0, 1e4, 0.05, 0.1)
+    s2 = torch.empty((n, 19), device="cuda")
+    truth = torch.empty((n, 4), device="cuda")
+    ants.ants_simulate_events(ctx.handle, lrf.handle, sp, 77, 0, s2, truth)
+    it, stats = lrf.iterate(s2, p, 3, ants.EventCuts(chi2_max=25.0), refit_gains=True)
+    assert stats[-1]["n_kept"] > 0.95 * n
+    err = lambda L: float(((ants.reconstruct(ctx, L, p, s2).xyz[:, :2] - truth[:, :2]) ** 2).sum(1).mean().sqrt())
+    e_true, e_it = err(lrf), err(it)
+    assert e_it < 1.03 * e_true, (e_it, e_true)
