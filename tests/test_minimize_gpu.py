@@ -174,3 +174,37 @@ def test_full_size_sampled(ctx):
     dx = np.abs(r.xyz.cpu().numpy()[pick][ok] - o["xyz"][ok]).max()
     print("full size: max |dxyz|", dx, "converged", (r.trace.cpu().numpy()[:, 0] > 0).mean())
     assert dx <= 1e-2
+
+
+def test_minimize_many_sensors(ctx):
+    """A 12 x 12 array (144 sensors: one event per warp) against the oracle."""
+    import paper_1602_07247_gb300 as ants
+    sxy = synth.square_array(12, 4.0)
+    kx = np.linspace(-24.0 - 8.0, 24.0 + 8.0, 11)
+    X, Y = np.meshgrid(kx, kx)
+    rng = np.random.default_rng(12)
+    coef = np.stack([0.02 / (1 + ((X - sx) ** 2 + (Y - sy) ** 2) / 100.0) ** 1.5 for sx, sy in sxy]).reshape(144, -1)
+    coef *= rng.uniform(0.95, 1.05, coef.shape)
+    L = oracle.Lrf(oracle.XY, sxy, (8, 8, 0), (-24.0, -24.0, 0.0), (24.0, 24.0, 0.0), coef)
+    lrf = _gpu_lrf(ctx, L)
+    p0 = rng.uniform(-18, 18, (400, 2))
+    sig = rng.poisson(3000.0 * oracle.lrf_eval(L, p0)).astype(np.float32)
+    for crit in (0, 1):
+        g = _run_gpu(ctx, lrf, sig, ants.MinimizeParams(criterion=crit, max_iter=60, tol=1e-4))
+        o = oracle.minimize(L, sig.astype(np.float64), oracle.Variant(criterion=crit),
+                            oracle.Minimize(max_iter=60, tol=1e-4))
+        assert np.array_equal(g["status"], o["status"])
+        conv = (g["status"] == 0) & (g["trace"][:, 0] > 0) & (o["n_iter"] > 0)
+        assert conv.mean() > 0.95
+        dx = np.abs(g["xyz"][conv, :2] - o["xyz"][conv, :2]).max()
+        print("144 sensors", crit, "max |dxyz|", dx)
+        assert dx <= 1e-3
+
+
+def test_minimize_no_events(ctx, lrfs):
+    import torch
+    import paper_1602_07247_gb300 as ants
+    lrf = _gpu_lrf(ctx, lrfs["xy"])
+    r = ants.reconstruct(ctx, lrf, ants.MinimizeParams(), torch.zeros((0, 9), device="cuda"),
+                         method=ants.ANTS_MINIMIZE)
+    assert r.xyz.shape == (0, 3)

@@ -127,3 +127,20 @@ def test_errors(ctx):
     with pytest.raises(ants.AntsError):
         c = torch.empty((1, 4), dtype=torch.int32, device="cuda")
         ants.ants_trace_photons(ctx.handle, ants.OpticsParams(**_bare()), s, 10, 1, 7, c)
+
+
+def test_empty_calls(ctx):
+    """No photons: zero counts (the buffer is cleared) and zero light
+    response; no sources: nothing to do."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    P = ants.OpticsParams(**_bare())
+    s = torch.zeros((2, 3), device="cuda")
+    s[:, 2] = 5.0
+    counts = torch.full((2, 4), 7, dtype=torch.int32, device="cuda")
+    eta = torch.full((2, 4), 7.0, device="cuda")
+    ants.ants_trace_photons(ctx.handle, P, s, 0, 1, ants.ANTS_F32, counts, eta=eta)
+    torch.cuda.synchronize()
+    assert int(counts.abs().sum()) == 0 and float(eta.abs().sum()) == 0.0
+    c, _, _ = ants.trace_photons(ctx, P, torch.zeros((0, 3), device="cuda"), 100, 1)
+    assert c.shape == (0, 4)
