@@ -91,6 +91,8 @@ class _Lrf(C.Structure):
         ("hi_r", C.c_double),
         ("n_planes", C.c_int),
         ("group", C.POINTER(C.c_int)),
+        ("op", C.POINTER(C.c_int)),
+        ("sym_c", C.c_double * 2),
     ]
 
 
@@ -175,6 +177,8 @@ class Lrf:
     hi_r: float = 0.0
     n_planes: int = 0
     group: np.ndarray | None = None
+    op: np.ndarray | None = None
+    sym_c: tuple = (0.0, 0.0)
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -196,11 +200,14 @@ class Lrf:
         sxy = _f64(self.sensor_xy)
         gain = _f64(self.gain) if self.gain is not None else None
         grp = np.ascontiguousarray(np.asarray(self.group, dtype=np.int32)) if self.group is not None else None
-        self._keep[:] = [coef, sxy, gain, grp]
+        op = np.ascontiguousarray(np.asarray(self.op, dtype=np.int32)) if self.op is not None else None
+        self._keep[:] = [coef, sxy, gain, grp, op]
         s.coef = _d(coef)
         s.sensor_xy = _d(sxy)
         s.gain = _d(gain) if gain is not None else C.cast(None, _D)
         s.group = _i(grp) if grp is not None else C.cast(None, _I)
+        s.op = _i(op) if op is not None else C.cast(None, _I)
+        s.sym_c[0], s.sym_c[1] = float(self.sym_c[0]), float(self.sym_c[1])
         return s
 
 
@@ -274,6 +281,29 @@ def lrf_eval(lrf: Lrf, pts, mutant: int = 0) -> np.ndarray:
     out = np.empty((pts.shape[0], lrf.n_sensors))
     lib(mutant).or_lrf_eval(C.byref(s), pts.shape[0], _d(pts), pts.shape[1], _d(out))
     return out
+
+
+def sensor_symmetry(sensor_xy, tol: float, mutant: int = 0):
+    """Sec. 6.2 grouping by the rotation and reflection symmetry of the array:
+    (class of each sensor, its symmetry operation, number of classes,
+    centre)."""
+    sxy = _f64(sensor_xy)
+    g = np.empty(sxy.shape[0], dtype=np.int32)
+    op = np.empty(sxy.shape[0], dtype=np.int32)
+    c = np.empty(2)
+    L = lib(mutant)
+    L.or_sensor_symmetry.argtypes = [C.c_int, _D, C.c_double, _I, _I, _D]
+    L.or_sensor_symmetry.restype = C.c_int
+    k = L.or_sensor_symmetry(sxy.shape[0], _d(sxy), float(tol), _i(g), _i(op), _d(c))
+    return g, op, k, (float(c[0]), float(c[1]))
+
+
+def sym_matrix(k: int) -> np.ndarray:
+    """The 2 x 2 matrix of symmetry operation k (rotation by (k mod 12) x 30
+    degrees, after the reflection y -> -y for k >= 12)."""
+    t = (k % 12) * np.pi / 6
+    f = -1.0 if k >= 12 else 1.0
+    return np.array([[np.cos(t), -np.sin(t) * f], [np.sin(t), np.cos(t) * f]])
 
 
 def sensor_rings(sensor_xy, tol: float, mutant: int = 0):

@@ -62,6 +62,7 @@
 #define OR_SLICED 6    /* Sec. 6.1.2: XY LRFs on z planes, linear in z between them */
 
 #define OR_EVT_OK 0
+#define OR_PI_SYM 3.14159265358979323846
 #define OR_EVT_ZERO_SIGNAL 2
 #define OR_EVT_BAD_SIGNAL 3
 #define OR_EVT_OUT_OF_DOMAIN 4
@@ -187,8 +188,46 @@ typedef struct {
     int n_int_r;            /* composite: intervals of the axial part on [0, hi_r] */
     double hi_r;
     int n_planes;           /* sliced: number of z planes (>= 2) */
-    const int *group;       /* radial, not shared: nullable [n_sensors] coefficient set of each sensor (Sec. 6.2 groups) */
+    const int *group;       /* radial, not shared: nullable [n_sensors] coefficient set of each sensor (Sec. 6.2
+                               groups); XY: the symmetry class of each sensor */
+    const int *op;          /* XY with groups: [n_sensors] the symmetry operation of each sensor (or_sym_op) */
+    double sym_c[2];        /* XY with groups: the centre of the operations */
 } or_lrf;
+
+/* Symmetry operation k of the plane about a centre (Sec. 6.2 groups by the
+ * rotation and reflection symmetry of the array): the rotation by (k mod 12)
+ * x 30 degrees, preceded for k >= 12 by the reflection y -> -y; M is the
+ * 2 x 2 matrix, row-major. */
+static void or_sym_op(int k, double M[4])
+{
+    double t = (double)(k % 12) * (OR_PI_SYM / 6.0), c = cos(t), s = sin(t);
+    /* exact values at multiples of 90 degrees */
+    if (k % 3 == 0) {
+        int q = (k % 12) / 3;
+        c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+        s = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+    }
+    double f = k >= 12 ? -1.0 : 1.0;
+    M[0] = c;
+    M[1] = -s * f;
+    M[2] = s;
+    M[3] = c * f;
+}
+
+/* (x, y) mapped into the frame of sensor i's class representative:
+ * M^T ((x, y) - c) + c */
+static void or_sym_point(const or_lrf *L, int i, double *x, double *y)
+{
+    double M[4], dx = *x - L->sym_c[0], dy = *y - L->sym_c[1];
+    or_sym_op(L->op[i], M);
+#if OR_MUTANT == 30
+    *x = M[0] * dx + M[1] * dy + L->sym_c[0];
+    *y = M[2] * dx + M[3] * dy + L->sym_c[1];
+#else
+    *x = M[0] * dx + M[2] * dy + L->sym_c[0];
+    *y = M[1] * dx + M[3] * dy + L->sym_c[1];
+#endif
+}
 
 /* the coefficient set of sensor i of a radial LRF: one for all (shared), its
  * group's (grouped) or its own */
@@ -297,6 +336,13 @@ static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, i
         return g * f;
     }
     const double *c = L->coef + (size_t)i * nc;
+    double gs = 1.0;
+    if (L->type == OR_XY && L->group) {
+        /* symmetry class: the representative's LRF at the mapped point, times the gain */
+        c = L->coef + (size_t)L->group[i] * nc;
+        or_sym_point(L, i, &x, &y);
+        gs = L->gain ? L->gain[i] : 1.0;
+    }
     double Bx[4], By[4], Bz[4] = {1.0, 0.0, 0.0, 0.0};
     int jx = or_bspline_basis4(L->n_int[0], L->lo[0], L->hi[0], x, Bx);
     int jy = or_bspline_basis4(L->n_int[1], L->lo[1], L->hi[1], y, By);
@@ -318,7 +364,60 @@ static double or_lrf_eta(const or_lrf *L, int i, double x, double y, double z, i
 #endif
                 f += c[idx] * Bx[a] * By[b] * Bz[cz];
             }
-    return f;
+    return gs * f;
+}
+
+/* Sensor classes by the rotation and reflection symmetry of the array (Sec.
+ * 6.2): the centre is the mean sensor position; an operation of or_sym_op is
+ * a symmetry when it maps every sensor onto a sensor (within tol); sensors
+ * taken in index order open a class unless already reached, and every
+ * symmetry (in table order) maps the class's first sensor onto the members
+ * it reaches first, recording that operation.  Returns the number of
+ * classes; group[i], op[i] and the centre c receive the result. */
+int or_sensor_symmetry(int n, const double *sensor_xy, double tol, int *group, int *op, double *c)
+{
+    double cx = 0.0, cy = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cx += sensor_xy[2 * i];
+        cy += sensor_xy[2 * i + 1];
+    }
+    cx /= n;
+    cy /= n;
+    c[0] = cx;
+    c[1] = cy;
+    int valid[24], n_valid = 0;
+    for (int k = 0; k < 24; ++k) {
+        double M[4];
+        or_sym_op(k, M);
+        int ok = 1;
+        for (int i = 0; i < n && ok; ++i) {
+            double dx = sensor_xy[2 * i] - cx, dy = sensor_xy[2 * i + 1] - cy;
+            double x = M[0] * dx + M[1] * dy + cx, y = M[2] * dx + M[3] * dy + cy;
+            int hit = 0;
+            for (int j = 0; j < n && !hit; ++j) hit = hypot(sensor_xy[2 * j] - x, sensor_xy[2 * j + 1] - y) <= tol;
+            ok = hit;
+        }
+        if (ok) valid[n_valid++] = k;
+    }
+    for (int i = 0; i < n; ++i) group[i] = -1;
+    int g = 0;
+    for (int r = 0; r < n; ++r) {
+        if (group[r] >= 0) continue;
+        double dx = sensor_xy[2 * r] - cx, dy = sensor_xy[2 * r + 1] - cy;
+        for (int v = 0; v < n_valid; ++v) {
+            double M[4];
+            or_sym_op(valid[v], M);
+            double x = M[0] * dx + M[1] * dy + cx, y = M[2] * dx + M[3] * dy + cy;
+            for (int j = 0; j < n; ++j)
+                if (group[j] < 0 && hypot(sensor_xy[2 * j] - x, sensor_xy[2 * j + 1] - y) <= tol) {
+                    group[j] = g;
+                    op[j] = valid[v];
+                    break;
+                }
+        }
+        ++g;
+    }
+    return g;
 }
 
 /* Sensor groups by distance from the array's centre (Sec. 6.2): the centre
@@ -575,6 +674,16 @@ static int or_valid_act(const or_lrf *L, const int *act, double x, double y, dou
             double r = sqrt(dx * dx + dy * dy);
             if (!(r >= rlo && r <= rhi)) return 0;
         }
+    }
+    if (L->type == OR_XY && L->group) {
+        /* symmetry classes: every sensor's mapped point inside the box */
+        for (int i = 0; i < L->n_sensors; ++i) {
+            if (act && !act[i]) continue;
+            double u = x, v = y;
+            or_sym_point(L, i, &u, &v);
+            if (!(u >= L->lo[0] && u <= L->hi[0] && v >= L->lo[1] && v <= L->hi[1])) return 0;
+        }
+        return 1;
     }
     if (or_has_box(L->type) && !(x >= L->lo[0] && x <= L->hi[0] && y >= L->lo[1] && y <= L->hi[1])) return 0;
     if (L->type == OR_XYZ && !(z >= L->lo[2] && z <= L->hi[2])) return 0;
@@ -1230,6 +1339,13 @@ static double or_lrf_eta_grad(const or_lrf *L, int i, double x, double y, double
         return (1.0 - w) * f0 + w * f1;
     }
     const double *c = L->coef + (size_t)i * nc;
+    double gs = 1.0, M[4] = {1.0, 0.0, 0.0, 1.0};
+    if (L->type == OR_XY && L->group) {
+        c = L->coef + (size_t)L->group[i] * nc;
+        or_sym_point(L, i, &x, &y);
+        or_sym_op(L->op[i], M);
+        gs = L->gain ? L->gain[i] : 1.0;
+    }
     double Bx[4], By[4], Bz[4] = {1.0, 0.0, 0.0, 0.0}, Dx[4], Dy[4], Dz[4] = {0.0, 0.0, 0.0, 0.0};
     int jx = or_bspline_dbasis4(L->n_int[0], L->lo[0], L->hi[0], x, Bx, Dx);
     int jy = or_bspline_dbasis4(L->n_int[1], L->lo[1], L->hi[1], y, By, Dy);
@@ -1250,7 +1366,12 @@ static double or_lrf_eta_grad(const or_lrf *L, int i, double x, double y, double
                 g[1] += cc * Bx[a] * Dy[b] * Bz[cz];
                 g[2] += cc * Bx[a] * By[b] * Dz[cz];
             }
-    return f;
+    /* the gradient of F(M^T (p - c) + c) is M grad F */
+    double gx = M[0] * g[0] + M[1] * g[1], gy = M[2] * g[0] + M[3] * g[1];
+    g[0] = gs * gx;
+    g[1] = gs * gy;
+    g[2] *= gs;
+    return gs * f;
 }
 
 /* Gradients of every sensor's LRF at the points: out[(p n_s + i) 3 + k]; NaN

@@ -1358,3 +1358,56 @@ def pin_grouped_refit_exact(mutant=0):
 
 
 ALL_PINS += [pin_grouped_refit_exact]
+
+
+def pin_symmetry_groups(mutant=0):
+    """Sec. 6.2 classes by the array's symmetry: the 8 x 8 square has the 8
+    operations of the square's group and 10 classes (4 of 4 sensors on the
+    diagonals, 6 of 8); the 19-PMT hexagon 4 classes (1, 6, 6, 6); a 4 x 2
+    rectangle 2 classes of 4. A class LRF evaluated at the mapped point
+    M^T (p - c) + c equals, on a knot grid symmetric about the centre, the
+    per-sensor LRF whose coefficient grid is the class's with its indices
+    transformed by M (B_j(-x) = B_{N-j}(x) on symmetric knots), and its
+    analytic gradient equals central differences."""
+    sq = synth.square_array(8, 6.0)
+    g, op, k, c = oracle.sensor_symmetry(sq, 1e-6, mutant)
+    assert k == 10 and sorted(np.bincount(g)) == [4] * 4 + [8] * 6
+    assert sorted(set(op.tolist())) == [0, 3, 6, 9, 12, 15, 18, 21]
+    gh, _, kh, _ = oracle.sensor_symmetry(synth.workloads.get("hex19_radial").sensor_xy, 1e-6, mutant)
+    assert kh == 4 and sorted(np.bincount(gh)) == [1, 6, 6, 6]
+    rect = np.array([[x, y] for y in (-2.0, 2.0) for x in (-6.0, -2.0, 2.0, 6.0)])
+    gr, _, kr, _ = oracle.sensor_symmetry(rect, 1e-6, mutant)
+    assert kr == 2 and list(np.bincount(gr)) == [4, 4]
+    # class LRFs with random coefficients on a symmetric 6 x 6 grid over [-24, 24]^2
+    rng = np.random.default_rng(30)
+    n = 6
+    N = n + 2
+    cls = rng.uniform(0.5, 1.5, (k, (n + 3) * (n + 3)))
+    gains = rng.uniform(0.9, 1.1, 64)
+    G = oracle.Lrf(oracle.XY, sq, (n, n, 0), (-24.0, -24.0, 0.0), (24.0, 24.0, 0.0), cls, gain=gains, group=g, op=op,
+                   sym_c=c)
+    per = np.empty((64, (n + 3) * (n + 3)))
+    for i in range(64):
+        M = np.rint(oracle.sym_matrix(int(op[i]))).astype(int)
+        F = cls[g[i]].reshape(n + 3, n + 3)  # [jy][jx]
+        P = np.empty_like(F)
+        for jy in range(n + 3):
+            for jx in range(n + 3):
+                u = np.array([2 * jx - N, 2 * jy - N])  # twice the centred index
+                w = M.T @ u
+                P[jy, jx] = F[(w[1] + N) // 2, (w[0] + N) // 2]
+        per[i] = P.ravel() * gains[i]
+    Lp = oracle.Lrf(oracle.XY, sq, (n, n, 0), (-24.0, -24.0, 0.0), (24.0, 24.0, 0.0), per)
+    pts = rng.uniform(-23.0, 23.0, (300, 2))
+    a, b = oracle.lrf_eval(G, pts, mutant), oracle.lrf_eval(Lp, pts, mutant)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    gr_ = oracle.lrf_grad(G, pts, mutant)
+    h = 1e-5
+    for kk in range(2):
+        e = np.zeros(2)
+        e[kk] = h
+        fd = (oracle.lrf_eval(G, pts + e, mutant) - oracle.lrf_eval(G, pts - e, mutant)) / (2 * h)
+        assert np.abs(gr_[:, :, kk] - fd).max() < 1e-7 * np.abs(a).max()
+
+
+ALL_PINS += [pin_symmetry_groups]

@@ -35,6 +35,7 @@ MUTANTS = {
     27: "pre-rejection discarding the photons it should trace",
     28: "absorption range L u instead of -L ln u",
     29: "grouped radial LRFs reading each sensor's own coefficient row",
+    30: "symmetry classes mapping points with M instead of M^T",
 }
 
 
