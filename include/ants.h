@@ -406,6 +406,33 @@ ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, co
                                      const double *hi, int n_groups, const int *group_host, const double *coef_host,
                                      const double *gain_host, ants_lrf **out);
 
+/* An XY LRF set with symmetry classes (Sec. 6.2: sensors related by a
+ * rotation or reflection of the array share one LRF): class_host[i] in [0,
+ * n_classes) is sensor i's class, op_host[i] in [0, 24) its operation M
+ * (the rotation by (op mod 12) x 30 degrees, preceded for op >= 12 by the
+ * reflection y -> -y) about centre[2]; coef_host [n_classes][n_coef] the
+ * classes' XY LRFs in their representatives' frames, gain_host (nullable)
+ * per-sensor gains.  eta_i(p) = g_i F_class(i)(M_i^T (p - c) + c); a point is
+ * inside the domain when every mapped point lies in the XY box.  Used by the
+ * plain search (through the per-node kernel), the variants, the
+ * minimisation, the simulator and evaluation; not by the precision and
+ * learned forms or batches, not saved or refitted (ANTS_E_UNIMPLEMENTED).
+ * Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
+ANTS_API int ants_lrf_create_symmetric(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
+                                       const double *hi, int n_classes, const int *class_host, const int *op_host,
+                                       const double *centre, const double *coef_host, const double *gain_host,
+                                       ants_lrf **out);
+
+/* Classes by the rotation and reflection symmetry of the array (Sec. 6.2):
+ * the centre is the mean sensor position; an operation (as above) is a
+ * symmetry when it maps every sensor within tol of a sensor; sensors in index
+ * order open a class unless already reached, and each symmetry (in table
+ * order) maps the class's first sensor onto the unassigned sensor it reaches,
+ * recording that operation.  Outputs class_host[n], op_host[n], centre_out[2],
+ * *n_classes_out.  Host only.  Errors: ANTS_E_ARG. */
+ANTS_API int ants_sensor_symmetry(const ants_detector *det, double tol, int *class_host, int *op_host,
+                                  double *centre_out, int *n_classes_out);
+
 /* Groups by distance from the array's centre (Sec. 6.2): the centre is the
  * mean sensor position; sensors in order of increasing distance d (ties by
  * index) start a new group when d exceeds the distance of the current

@@ -276,6 +276,9 @@ def lib() -> C.CDLL:
         L.ants_trace_photons.argtypes = [_VP, _VP, _VP, C.c_long, C.c_long, C.c_uint64, C.c_int, _VP, _VP, _VP, _VP]
         L.ants_lrf_create_grouped.argtypes = [_VP, _VP, _IP, _DP, _DP, C.c_int, _IP, _DP, _DP, C.POINTER(_VP)]
         L.ants_sensor_rings.argtypes = [_VP, C.c_double, _IP, _IP]
+        L.ants_lrf_create_symmetric.argtypes = [_VP, _VP, _IP, _DP, _DP, C.c_int, _IP, _IP, _DP, _DP, _DP,
+                                                C.POINTER(_VP)]
+        L.ants_sensor_symmetry.argtypes = [_VP, C.c_double, _IP, _IP, _DP, _IP]
         L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
         L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
                                         C.POINTER(C.c_long), _VP]
@@ -729,6 +732,10 @@ class Detector:
         self.n_sensors = int(self.sensor_xy.shape[0])
         self.handle = ants_detector_create(self.sensor_xy, rel_gain)
 
+    def symmetry(self, tol: float = 1e-3):
+        """Sec. 6.2 classes by rotation and reflection symmetry: (class, operation, n_classes, centre)."""
+        return ants_sensor_symmetry(self.handle, self.n_sensors, tol)
+
     def rings(self, tol: float = 1e-3):
         """Sec. 6.2 grouping by distance from the array's centre: (group of each sensor, number of groups)."""
         return ants_sensor_rings(self.handle, self.n_sensors, tol)
@@ -758,6 +765,12 @@ class Lrf:
         """A grouped RADIAL set (ants_lrf_create_grouped): one profile per group, per-sensor gains."""
         return cls(ctx, det, ants_lrf_create_grouped(ctx.handle, det.handle, n_int, lo, hi, group, coef, gain),
                    ANTS_LRF_RADIAL)
+
+    @classmethod
+    def from_symmetry(cls, ctx, det, n_int, lo, hi, classes, ops, centre, coef, gain=None):
+        """An XY set with symmetry classes (ants_lrf_create_symmetric)."""
+        return cls(ctx, det, ants_lrf_create_symmetric(ctx.handle, det.handle, n_int, lo, hi, classes, ops, centre,
+                                                       coef, gain), ANTS_LRF_XY)
 
     @classmethod
     def fit(cls, ctx, det, type, n_int, lo, hi, pts, vals, shared=False, ridge=0.0):
@@ -902,6 +915,33 @@ def ants_lrf_create_grouped(ctx: int, det: int, n_int, lo, hi, group, coef, gain
                                          c.ctypes.data_as(_DP), None if gn is None else gn.ctypes.data_as(_DP),
                                          C.byref(h)))
     return h.value
+
+
+def ants_lrf_create_symmetric(ctx: int, det: int, n_int, lo, hi, classes, ops, centre, coef, gain=None) -> int:
+    cl = np.ascontiguousarray(np.asarray(classes, dtype=np.int32))
+    op = np.ascontiguousarray(np.asarray(ops, dtype=np.int32))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
+    ce = np.ascontiguousarray(np.asarray(centre, dtype=np.float64))
+    gn = None if gain is None else np.ascontiguousarray(np.asarray(gain, dtype=np.float64))
+    ni = (C.c_int * 2)(int(n_int[0]), int(n_int[1]))
+    lo_ = (C.c_double * 2)(float(lo[0]), float(lo[1]))
+    hi_ = (C.c_double * 2)(float(hi[0]), float(hi[1]))
+    h = _VP()
+    _check(lib().ants_lrf_create_symmetric(ctx, det, ni, lo_, hi_, int(c.shape[0]), cl.ctypes.data_as(_IP),
+                                           op.ctypes.data_as(_IP), ce.ctypes.data_as(_DP), c.ctypes.data_as(_DP),
+                                           None if gn is None else gn.ctypes.data_as(_DP), C.byref(h)))
+    return h.value
+
+
+def ants_sensor_symmetry(det: int, n_sensors: int, tol: float):
+    """(class of each sensor, its operation, number of classes, centre)."""
+    cl = np.empty(n_sensors, dtype=np.int32)
+    op = np.empty(n_sensors, dtype=np.int32)
+    ce = np.empty(2)
+    k = C.c_int()
+    _check(lib().ants_sensor_symmetry(det, float(tol), cl.ctypes.data_as(_IP), op.ctypes.data_as(_IP),
+                                      ce.ctypes.data_as(_DP), C.byref(k)))
+    return cl, op, k.value, (float(ce[0]), float(ce[1]))
 
 
 def ants_sensor_rings(det: int, n_sensors: int, tol: float):

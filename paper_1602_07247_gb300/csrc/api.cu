@@ -237,7 +237,31 @@ static int upload_lrf(ants_lrf *L)
     D.coef2 = nullptr;
     D.coef_t = nullptr;
     D.set_of = nullptr;
+    D.op_of = nullptr;
     D.n_sets = L->n_sets;
+    D.sym_c[0] = (float)L->sym_c[0];
+    D.sym_c[1] = (float)L->sym_c[1];
+    for (int k = 0; k < 24; ++k) {
+        // rotation by (k mod 12) x 30 degrees after the reflection y -> -y for k >= 12
+        const double t = (double)(k % 12) * (3.14159265358979323846 / 6.0);
+        double c = std::cos(t), sn = std::sin(t);
+        if (k % 3 == 0) {
+            const int q = (k % 12) / 3;
+            c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+            sn = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        }
+        const double f = k >= 12 ? -1.0 : 1.0;
+        D.op_m[k][0] = (float)c;
+        D.op_m[k][1] = (float)(-sn * f);
+        D.op_m[k][2] = (float)sn;
+        D.op_m[k][3] = (float)(c * f);
+    }
+    if (!L->ops.empty()) {
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_op_of, L->ops.size() * sizeof(int)), "cudaMalloc(lrf operations)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_op_of, L->ops.data(), L->ops.size() * sizeof(int), cudaMemcpyHostToDevice),
+                      "upload operations");
+        D.op_of = L->d_op_of;
+    }
     if (!L->groups.empty()) {
         ANTS_CUDA_TRY(cudaMalloc(&L->d_set_of, L->groups.size() * sizeof(int)), "cudaMalloc(lrf groups)");
         ANTS_CUDA_TRY(cudaMemcpy(L->d_set_of, L->groups.data(), L->groups.size() * sizeof(int), cudaMemcpyHostToDevice),
@@ -246,7 +270,7 @@ static int upload_lrf(ants_lrf *L)
     }
     D.n_pairs = (L->n_s + 1) / 2;
     D.pair_stride = 0;
-    if (L->type == ANTS_LRF_XY) {
+    if (L->type == ANTS_LRF_XY && L->ops.empty()) {
         const int ps = L->n_coef;
         std::vector<float2> c2((size_t)D.n_pairs * ps);
         for (int p = 0; p < D.n_pairs; ++p)
@@ -325,6 +349,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_coef2);
     cudaFree(lrf->d_coeft);
     cudaFree(lrf->d_set_of);
+    cudaFree(lrf->d_op_of);
     cudaFree(lrf->d_rpoly);
     delete lrf;
     (void)cudaGetLastError();
@@ -336,12 +361,18 @@ namespace ants {
 
 int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
                     const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
-                    double hi_r, int n_planes, ants_lrf **out, int n_groups, const int *group)
+                    double hi_r, int n_planes, ants_lrf **out, int n_groups, const int *group, const int *op,
+                    const double *centre)
 {
     *out = nullptr;
+    if (op && (type != ANTS_LRF_XY || !group || !centre))
+        return fail(ANTS_E_ARG, "ants_lrf_create_symmetric: symmetry classes need an XY LRF, classes and a centre");
+    if (op)
+        for (int i = 0; det && i < det->n_s; ++i)
+            if (op[i] < 0 || op[i] > 23) return fail(ANTS_E_ARG, "ants_lrf_create_symmetric: operation %d", op[i]);
     if (group) {
-        if (type != ANTS_LRF_RADIAL || shared || !det)
-            return fail(ANTS_E_ARG, "ants_lrf_create_grouped: groups need a RADIAL LRF that is not shared");
+        if ((type != ANTS_LRF_RADIAL && !op) || shared || !det)
+            return fail(ANTS_E_ARG, "groups need a RADIAL LRF that is not shared, or XY symmetry classes");
         if (n_groups < 1 || n_groups > det->n_s)
             return fail(ANTS_E_ARG, "ants_lrf_create_grouped: 1 <= n_groups <= n_sensors");
         for (int i = 0; i < det->n_s; ++i)
@@ -354,8 +385,8 @@ int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int
         return fail(ANTS_E_ARG, "ants_lrf_create: unknown LRF type %d", type);
     if (shared && type != ANTS_LRF_RADIAL)
         return fail(ANTS_E_ARG, "ants_lrf_create: shared coefficients need a RADIAL LRF");
-    if (gain_host && type != ANTS_LRF_RADIAL)
-        return fail(ANTS_E_ARG, "ants_lrf_create: gains apply to RADIAL LRFs only");
+    if (gain_host && type != ANTS_LRF_RADIAL && !op)
+        return fail(ANTS_E_ARG, "ants_lrf_create: gains apply to RADIAL LRFs and XY symmetry classes only");
     int dims = lrf_dims(type);
     if (type == ANTS_LRF_COMPOSITE && (n_int_r < 1 || n_int_r > 256 || !(hi_r > 0.0) || !std::isfinite(hi_r)))
         return fail(ANTS_E_ARG, "ants_lrf_create: a composite LRF needs 1 <= n_int_r <= 256 and hi_r > 0");
@@ -398,6 +429,11 @@ int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int
     }
     L->n_sets = L->shared ? 1 : group ? n_groups : L->n_s;
     if (group) L->groups.assign(group, group + L->n_s);
+    if (op) {
+        L->ops.assign(op, op + L->n_s);
+        L->sym_c[0] = centre[0];
+        L->sym_c[1] = centre[1];
+    }
     size_t nc = (size_t)L->n_sets * L->n_coef;
     L->coef.assign(coef_host, coef_host + nc);
     for (size_t k = 0; k < nc; ++k)
@@ -446,6 +482,88 @@ ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, co
     if (!group_host) return fail(ANTS_E_ARG, "ants_lrf_create_grouped: group_host is NULL");
     return lrf_create_impl(ctx, det, ANTS_LRF_RADIAL, n_int, lo, hi, 0, coef_host, gain_host, 0, 0.0, 0, out, n_groups,
                            group_host);
+}
+
+ANTS_API int ants_lrf_create_symmetric(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
+                                       const double *hi, int n_classes, const int *class_host, const int *op_host,
+                                       const double *centre, const double *coef_host, const double *gain_host,
+                                       ants_lrf **out)
+{
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_create_symmetric: out is NULL");
+    *out = nullptr;
+    if (!class_host || !op_host || !centre) return fail(ANTS_E_ARG, "ants_lrf_create_symmetric: NULL argument");
+    return lrf_create_impl(ctx, det, ANTS_LRF_XY, n_int, lo, hi, 0, coef_host, gain_host, 0, 0.0, 0, out, n_classes,
+                           class_host, op_host, centre);
+}
+
+ANTS_API int ants_sensor_symmetry(const ants_detector *det, double tol, int *class_host, int *op_host,
+                                  double *centre_out, int *n_classes_out)
+{
+    begin_call();
+    if (!det || !class_host || !op_host || !centre_out || !n_classes_out)
+        return fail(ANTS_E_ARG, "ants_sensor_symmetry: NULL argument");
+    if (!(tol >= 0.0)) return fail(ANTS_E_ARG, "ants_sensor_symmetry: tol must be >= 0");
+    const int n = det->n_s;
+    double cx = 0.0, cy = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cx += det->xy[2 * i];
+        cy += det->xy[2 * i + 1];
+    }
+    cx /= n;
+    cy /= n;
+    double M[24][4];
+    for (int k = 0; k < 24; ++k) {
+        const double t = (double)(k % 12) * (3.14159265358979323846 / 6.0);
+        double c = std::cos(t), sn = std::sin(t);
+        if (k % 3 == 0) {
+            const int q = (k % 12) / 3;
+            c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+            sn = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        }
+        const double f = k >= 12 ? -1.0 : 1.0;
+        M[k][0] = c;
+        M[k][1] = -sn * f;
+        M[k][2] = sn;
+        M[k][3] = c * f;
+    }
+    auto image = [&](int k, int i, double &x, double &y) {
+        const double dx = det->xy[2 * i] - cx, dy = det->xy[2 * i + 1] - cy;
+        x = M[k][0] * dx + M[k][1] * dy + cx;
+        y = M[k][2] * dx + M[k][3] * dy + cy;
+    };
+    std::vector<int> valid;
+    for (int k = 0; k < 24; ++k) {
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) {
+            double x, y;
+            image(k, i, x, y);
+            bool hit = false;
+            for (int j = 0; j < n && !hit; ++j) hit = std::hypot(det->xy[2 * j] - x, det->xy[2 * j + 1] - y) <= tol;
+            ok = hit;
+        }
+        if (ok) valid.push_back(k);
+    }
+    for (int i = 0; i < n; ++i) class_host[i] = -1;
+    int g = 0;
+    for (int r = 0; r < n; ++r) {
+        if (class_host[r] >= 0) continue;
+        for (int k : valid) {
+            double x, y;
+            image(k, r, x, y);
+            for (int j = 0; j < n; ++j)
+                if (class_host[j] < 0 && std::hypot(det->xy[2 * j] - x, det->xy[2 * j + 1] - y) <= tol) {
+                    class_host[j] = g;
+                    op_host[j] = k;
+                    break;
+                }
+        }
+        ++g;
+    }
+    centre_out[0] = cx;
+    centre_out[1] = cy;
+    *n_classes_out = g;
+    return ANTS_OK;
 }
 
 ANTS_API int ants_sensor_rings(const ants_detector *det, double tol, int *group_host, int *n_groups_out)

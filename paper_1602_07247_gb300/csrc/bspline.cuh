@@ -147,6 +147,17 @@ __device__ __forceinline__ float lrf_eta_t(const LrfDev &L, int i, float x, floa
             spline2(c + L.n_coef_xy, x, L.lo[0], L.inv_h[0], L.n_int[0], y, L.lo[1], L.inv_h[1], L.n_int[1]);
         return fmaf(w, f1, (1.0f - w) * f0);
     }
+    const float *c = L.coef + (size_t)i * L.n_coef;
+    float gs = 1.0f;
+    if (TYPE == ANTS_LRF_XY && L.set_of) {
+        // a symmetry class: the representative's LRF at M^T (p - c) + c, times the gain
+        const int k = __ldg(L.op_of + i);
+        const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
+        x = fmaf(L.op_m[k][0], dx, fmaf(L.op_m[k][2], dy, L.sym_c[0]));
+        y = fmaf(L.op_m[k][1], dx, fmaf(L.op_m[k][3], dy, L.sym_c[1]));
+        c = L.coef + (size_t)__ldg(L.set_of + i) * L.n_coef;
+        gs = __ldg(L.gain + i);
+    }
     ok = in_box(L, x, y, z);
     if (!ok) return 0.0f;
     float tx, ty, tz = 0.0f, wx[4], wy[4], wz[4] = {1.0f, 0.0f, 0.0f, 0.0f};
@@ -160,7 +171,6 @@ __device__ __forceinline__ float lrf_eta_t(const LrfDev &L, int i, float x, floa
         bs_weights(tz, wz);
         nz = 4;
     }
-    const float *c = L.coef + (size_t)i * L.n_coef;
     float f = 0.0f;
     for (int cz = 0; cz < nz; ++cz) {
         float fz = 0.0f;
@@ -174,7 +184,7 @@ __device__ __forceinline__ float lrf_eta_t(const LrfDev &L, int i, float x, floa
         }
         f = fmaf(fz, wz[cz], f);
     }
-    return f;
+    return gs * f;
 }
 
 // the same with the type read at run time
@@ -300,6 +310,17 @@ __device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x,
         gz = (f1 - f0) * L.inv_h[2];
         return fmaf(w, f1, (1.0f - w) * f0);
     }
+    const float *c = L.coef + (size_t)i * L.n_coef;
+    float gs = 1.0f;
+    int kop = -1;
+    if (TYPE == ANTS_LRF_XY && L.set_of) {
+        kop = __ldg(L.op_of + i);
+        const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
+        x = fmaf(L.op_m[kop][0], dx, fmaf(L.op_m[kop][2], dy, L.sym_c[0]));
+        y = fmaf(L.op_m[kop][1], dx, fmaf(L.op_m[kop][3], dy, L.sym_c[1]));
+        c = L.coef + (size_t)__ldg(L.set_of + i) * L.n_coef;
+        gs = __ldg(L.gain + i);
+    }
     ok = in_box(L, x, y, z);
     if (!ok) return 0.0f;
     float tx, ty, tz = 0.0f, wx[4], wy[4], wz[4] = {1.0f, 0.0f, 0.0f, 0.0f};
@@ -317,7 +338,6 @@ __device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x,
         bs_dweights(tz, ddz);
         nz = 4;
     }
-    const float *c = L.coef + (size_t)i * L.n_coef;
     float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
     for (int cz = 0; cz < nz; ++cz) {
         float a0 = 0.0f, ax = 0.0f, ay = 0.0f;
@@ -341,7 +361,13 @@ __device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x,
     gx = fx * L.inv_h[0];
     gy = fy * L.inv_h[1];
     gz = TYPE == ANTS_LRF_XYZ ? fz * L.inv_h[2] : 0.0f;
-    return f;
+    if (TYPE == ANTS_LRF_XY && kop >= 0) {
+        // the gradient of F(M^T (p - c) + c) is M grad F
+        const float ux = gx, uy = gy;
+        gx = gs * fmaf(L.op_m[kop][0], ux, L.op_m[kop][1] * uy);
+        gy = gs * fmaf(L.op_m[kop][2], ux, L.op_m[kop][3] * uy);
+    }
+    return gs * f;
 }
 
 // every LRF of the sensors with s_act[i] != 0 (all sensors when s_act is
@@ -356,6 +382,18 @@ __device__ __forceinline__ bool lrf_defined(const LrfDev &L, const float *s_act,
     }
     if (L.type == ANTS_LRF_AXIAL_Z) return z >= L.lo[1] && z <= L.hi[1];
     if (L.type == ANTS_LRF_RADIAL) return true;
+    if (L.type == ANTS_LRF_XY && L.set_of) {
+        // symmetry classes: every sensor's mapped point inside the box
+        for (int i = 0; i < L.n_s; ++i) {
+            if (s_act && s_act[i] == 0.0f) continue;
+            const int k = __ldg(L.op_of + i);
+            const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
+            const float u = fmaf(L.op_m[k][0], dx, fmaf(L.op_m[k][2], dy, L.sym_c[0]));
+            const float v = fmaf(L.op_m[k][1], dx, fmaf(L.op_m[k][3], dy, L.sym_c[1]));
+            if (!in_box(L, u, v, z)) return false;
+        }
+        return true;
+    }
     return in_box(L, x, y, z);
 }
 

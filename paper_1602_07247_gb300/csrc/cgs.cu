@@ -710,9 +710,9 @@ int launch_cgs_rows(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_par
 {
     if (cgs_xy_supported(lrf, p))
         return launch_cgs_xy(ctx, lrf, p, sig, row_div, nullptr, n_e, start, xyz, E, logL, status, trace, stream);
-    if (lrf->type > ANTS_LRF_XYZ) {
-        // composite, axial+z and sliced sets: the per-node kernel of the
-        // variants with no option set is this search
+    if (lrf->type > ANTS_LRF_XYZ || !lrf->ops.empty()) {
+        // composite, axial+z, sliced and XY symmetry-class sets: the per-node
+        // kernel of the variants with no option set is this search
         if (row_div != 1) return fail(ANTS_E_UNIMPLEMENTED, "cgs: shared signal rows need an XY LRF");
         ants_cgs_variant_params v{};
         v.grid = p;
@@ -942,8 +942,8 @@ ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch
     for (int k = 0; k < n_items; ++k) {
         const ants_batch_item &it = items[k];
         if (!it.lrf || it.lrf->ctx != ctx) return fail(ANTS_E_ARG, "batch item %d: LRF of another context", k);
-        if (it.lrf->type > ANTS_LRF_XYZ)
-            return fail(ANTS_E_UNIMPLEMENTED, "batch item %d: RADIAL, XY and XYZ LRFs only", k);
+        if (it.lrf->type > ANTS_LRF_XYZ || !it.lrf->ops.empty())
+            return fail(ANTS_E_UNIMPLEMENTED, "batch item %d: RADIAL, XY and XYZ LRFs only (no XY classes)", k);
         if (it.n_events < 0) return fail(ANTS_E_ARG, "batch item %d: n_events < 0", k);
         if (it.n_events > 0 && (!it.signals_dev || !it.xyz_dev || !it.E_dev || !it.logL_dev || !it.status_dev))
             return fail(ANTS_E_ARG, "batch item %d: NULL buffer", k);

@@ -48,8 +48,11 @@ struct LrfDev {
     // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
     const float2 *coef2;
     const float *coef_t;   // XY: the coefficients sensor-minor, [k][n_s] (per-point loops over sensors)
-    const int *set_of;     // RADIAL grouped (Sec. 6.2): the coefficient set of each sensor; nullable
+    const int *set_of;     // RADIAL grouped / XY symmetry classes (Sec. 6.2): the coefficient set of each sensor; nullable
     int n_sets;            // coefficient sets
+    const int *op_of;      // XY symmetry classes: the operation of each sensor (index into op_m)
+    float sym_c[2];        // XY symmetry classes: the centre of the operations
+    float op_m[24][4];     // the 2 x 2 matrices of the operations (rotations by k 30 degrees, then reflections)
     // RADIAL LRFs: each interval's cubic in the power basis of its local
     // parameter t, (p0, p1, p2, p3) with f = p0 + t (p1 + t (p2 + t p3)),
     // [n_sets][n_int[0]]
@@ -111,7 +114,10 @@ struct ants_lrf {
     float2 *d_coef2 = nullptr;
     float *d_coeft = nullptr;
     int *d_set_of = nullptr;
-    std::vector<int> groups;       // RADIAL grouped: the group of each sensor (empty otherwise)
+    std::vector<int> groups;       // RADIAL grouped / XY classes: the group of each sensor (empty otherwise)
+    std::vector<int> ops;          // XY classes: the symmetry operation of each sensor
+    double sym_c[2] = {0.0, 0.0};
+    int *d_op_of = nullptr;
     float4 *d_rpoly = nullptr;
     ants::LrfDev dev{};
 };
@@ -131,7 +137,7 @@ __host__ __device__ inline bool lrf_has_box(int type)
 int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,
                     const double *hi, int shared, const double *coef_host, const double *gain_host, int n_int_r,
                     double hi_r, int n_planes, ants_lrf **out, int n_groups = 0,
-                    const int *group = nullptr);
+                    const int *group = nullptr, const int *op = nullptr, const double *centre = nullptr);
 // launches of the reconstruction kernels (cgs.cu)
 int launch_cgs_plain(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_params &p,
                      const float *sig, long n_e, const float *start, float *xyz, float *E,

@@ -532,7 +532,8 @@ int check_refit(const ants_lrf *lrf, const ants_refit_params *p)
     if (!p) return fail(ANTS_E_ARG, "refit parameters are NULL");
     if (!(p->shift_sigma >= 0.0) || !(p->ridge >= 0.0)) return fail(ANTS_E_ARG, "refit: shift_sigma, ridge >= 0");
     if (p->cycle < 0) return fail(ANTS_E_ARG, "refit: cycle < 0");
-    if (lrf->type > ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "refit: RADIAL, XY and XYZ LRFs only");
+    if (lrf->type > ANTS_LRF_XYZ || !lrf->ops.empty())
+        return fail(ANTS_E_UNIMPLEMENTED, "refit: RADIAL, XY and XYZ LRFs only (no XY symmetry classes)");
     if (lrf->type != ANTS_LRF_RADIAL && p->shared) return fail(ANTS_E_ARG, "refit: groups are RADIAL only");
     if (p->refit_gains && !(lrf->type == ANTS_LRF_RADIAL && (p->shared || !lrf->groups.empty())))
         return fail(ANTS_E_ARG, "refit: gains are refitted for RADIAL groups only");
