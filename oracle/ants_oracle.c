@@ -23,6 +23,13 @@
  *   - Sec. 5.2, event filters on chi-squared, energy, signal sum and
  *     position; Sec. 8, iterative LRF reconstruction (reconstruct, filter,
  *     optionally shift the positions at random, refit, repeat).
+ *   - Sec. 5.1.2 / 5.1.2.1 / 5.3, search variants (least squares, the
+ *     strongest-sensor start, sensor cuts, passive sensors) and the
+ *     continuous minimisation of the match (Migrad in the paper; here damped
+ *     Fisher scoring with the energy profiled out).
+ *   - Sec. 6.1.1 / 6.1.2, composite, axial+z and sliced LRFs; Sec. 6.2,
+ *     sensor groups by distance and XY classes by symmetry.
+ *   - Sec. 4.2.3 - 4.2.6 and 3.5, optical photon transport in a slab stack.
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - B-spline: uniform cubic on [lo,hi] with n intervals, n+3 basis
