@@ -302,8 +302,40 @@ def sym_matrix(k: int) -> np.ndarray:
     """The 2 x 2 matrix of symmetry operation k (rotation by (k mod 12) x 30
     degrees, after the reflection y -> -y for k >= 12)."""
     t = (k % 12) * np.pi / 6
+    c, s = np.cos(t), np.sin(t)
+    if k % 3 == 0:  # exact at multiples of 90 degrees
+        q = (k % 12) // 3
+        c, s = (1.0, 0.0, -1.0, 0.0)[q], (0.0, 1.0, 0.0, -1.0)[q]
     f = -1.0 if k >= 12 else 1.0
-    return np.array([[np.cos(t), -np.sin(t) * f], [np.sin(t), np.cos(t) * f]])
+    return np.array([[c, -s * f], [s, c * f]])
+
+
+def lrf_fit_symmetric(sensor_xy, classes, ops, centre, n_int, lo, hi, pts, vals, gain=None, ridge: float = 0.0,
+                      mutant: int = 0) -> Lrf:
+    """XY LRFs of symmetry classes (Sec. 6.2) from samples: each class's LRF
+    is fitted to its members' samples mapped into the representative's frame,
+    M_i^T (p - c) + c, with values v_i / g_i; mapped points outside the box
+    are left out.  pts [n, 2], vals [n, n_s]."""
+    pts, vals = _f64(pts), _f64(vals)
+    cl, op = np.asarray(classes), np.asarray(ops)
+    g = np.ones(len(cl)) if gain is None else _f64(gain)
+    k = int(cl.max()) + 1
+    c = np.asarray(centre, dtype=np.float64)
+    rows = []
+    for j in range(k):
+        P, V = [], []
+        for i in np.nonzero(cl == j)[0]:
+            M = sym_matrix(int(op[i]))
+            q = (pts - c) @ M + c  # rows: M^T (p - c) + c
+            inside = (q[:, 0] >= lo[0]) & (q[:, 0] <= hi[0]) & (q[:, 1] >= lo[1]) & (q[:, 1] <= hi[1])
+            P.append(q[inside])
+            V.append(vals[inside, i] / g[i])
+        coef, _, _ = lrf_fit(tuple(n_int[:2]), tuple(lo[:2]), tuple(hi[:2]), np.concatenate(P),
+                             np.concatenate(V)[:, None], ridge, mutant)
+        rows.append(coef[0])
+    return Lrf(XY, _f64(sensor_xy), (n_int[0], n_int[1], 0), (lo[0], lo[1], 0.0), (hi[0], hi[1], 0.0),
+               np.stack(rows), gain=None if gain is None else g, group=cl.astype(np.int32), op=op.astype(np.int32),
+               sym_c=(float(c[0]), float(c[1])))
 
 
 def sensor_rings(sensor_xy, tol: float, mutant: int = 0):

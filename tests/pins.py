@@ -1411,3 +1411,25 @@ def pin_symmetry_groups(mutant=0):
 
 
 ALL_PINS += [pin_symmetry_groups]
+
+
+def pin_symmetric_fit_exact(mutant=0):
+    """Noise-free samples of a symmetry-class XY LRF set on the 8 x 8 array
+    (random class coefficients, gains): the class fit from the members'
+    mapped samples recovers every class's coefficients."""
+    sq = synth.square_array(8, 6.0)
+    g, op, k, c = oracle.sensor_symmetry(sq, 1e-6, mutant)
+    rng = np.random.default_rng(31)
+    n = 6
+    cls = rng.uniform(0.5, 1.5, (k, (n + 3) * (n + 3)))
+    gains = rng.uniform(0.9, 1.1, 64)
+    G = oracle.Lrf(oracle.XY, sq, (n, n, 0), (-24.0, -24.0, 0.0), (24.0, 24.0, 0.0), cls, gain=gains, group=g, op=op,
+                   sym_c=c)
+    pts = rng.uniform(-24.0, 24.0, (1500, 2))
+    vals = oracle.lrf_eval(G, pts, mutant)
+    F = oracle.lrf_fit_symmetric(sq, g, op, c, (n, n), (-24.0, -24.0), (24.0, 24.0), pts, vals, gain=gains,
+                                 mutant=mutant)
+    assert np.abs(F.coef - cls).max() < 1e-8 * np.abs(cls).max()
+
+
+ALL_PINS += [pin_symmetric_fit_exact]
