@@ -423,6 +423,18 @@ ANTS_API int ants_lrf_create_symmetric(ants_ctx *ctx, const ants_detector *det, 
                                        const double *centre, const double *coef_host, const double *gain_host,
                                        ants_lrf **out);
 
+/* Fit an XY LRF set with symmetry classes from samples (Sec. 6.2): each
+ * class's LRF by FP64 least squares (as ants_lrf_fit) to its members'
+ * samples mapped into the representative's frame, M_i^T (p - c) + c, with
+ * values vals_host[e][i] / gain_host[i] (gains nullable = 1); mapped points
+ * outside the XY box are left out.  pts_host [n_pts][2], vals_host
+ * [n_pts][n_sensors]; classes and operations as ants_sensor_symmetry gives
+ * them.  Errors: as ants_lrf_fit. */
+ANTS_API int ants_lrf_fit_symmetric(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
+                                    const double *hi, int n_classes, const int *class_host, const int *op_host,
+                                    const double *centre, long n_pts, const double *pts_host,
+                                    const double *vals_host, const double *gain_host, double ridge, ants_lrf **out);
+
 /* Classes by the rotation and reflection symmetry of the array (Sec. 6.2):
  * the centre is the mean sensor position; an operation (as above) is a
  * symmetry when it maps every sensor within tol of a sensor; sensors in index

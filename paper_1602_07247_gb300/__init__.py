@@ -279,6 +279,8 @@ def lib() -> C.CDLL:
         L.ants_lrf_create_symmetric.argtypes = [_VP, _VP, _IP, _DP, _DP, C.c_int, _IP, _IP, _DP, _DP, _DP,
                                                 C.POINTER(_VP)]
         L.ants_sensor_symmetry.argtypes = [_VP, C.c_double, _IP, _IP, _DP, _IP]
+        L.ants_lrf_fit_symmetric.argtypes = [_VP, _VP, _IP, _DP, _DP, C.c_int, _IP, _IP, _DP, C.c_long, _DP, _DP,
+                                             _DP, C.c_double, C.POINTER(_VP)]
         L.ants_event_chi2.argtypes = [_VP, _VP, _VP, C.c_long, _VP, _VP, _VP, _VP, _VP]
         L.ants_event_filter.argtypes = [_VP, C.c_long, _VP, _VP, _VP, _VP, _VP, C.POINTER(EventCuts), _VP,
                                         C.POINTER(C.c_long), _VP]
@@ -773,6 +775,12 @@ class Lrf:
                                                        coef, gain), ANTS_LRF_XY)
 
     @classmethod
+    def fit_symmetric(cls, ctx, det, n_int, lo, hi, classes, ops, centre, pts, vals, gain=None, ridge=0.0):
+        """XY symmetry-class LRFs fitted on the device (ants_lrf_fit_symmetric)."""
+        return cls(ctx, det, ants_lrf_fit_symmetric(ctx.handle, det.handle, n_int, lo, hi, classes, ops, centre, pts,
+                                                    vals, gain, ridge), ANTS_LRF_XY)
+
+    @classmethod
     def fit(cls, ctx, det, type, n_int, lo, hi, pts, vals, shared=False, ridge=0.0):
         h, lam = ants_lrf_fit(ctx.handle, det.handle, type, n_int, lo, hi, shared, pts, vals, ridge)
         L = cls(ctx, det, h, type)
@@ -930,6 +938,25 @@ def ants_lrf_create_symmetric(ctx: int, det: int, n_int, lo, hi, classes, ops, c
     _check(lib().ants_lrf_create_symmetric(ctx, det, ni, lo_, hi_, int(c.shape[0]), cl.ctypes.data_as(_IP),
                                            op.ctypes.data_as(_IP), ce.ctypes.data_as(_DP), c.ctypes.data_as(_DP),
                                            None if gn is None else gn.ctypes.data_as(_DP), C.byref(h)))
+    return h.value
+
+
+def ants_lrf_fit_symmetric(ctx: int, det: int, n_int, lo, hi, classes, ops, centre, pts, vals, gain=None,
+                           ridge=0.0) -> int:
+    cl = np.ascontiguousarray(np.asarray(classes, dtype=np.int32))
+    op = np.ascontiguousarray(np.asarray(ops, dtype=np.int32))
+    ce = np.ascontiguousarray(np.asarray(centre, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(pts, dtype=np.float64))
+    v = np.ascontiguousarray(np.asarray(vals, dtype=np.float64))
+    gn = None if gain is None else np.ascontiguousarray(np.asarray(gain, dtype=np.float64))
+    ni = (C.c_int * 2)(int(n_int[0]), int(n_int[1]))
+    lo_ = (C.c_double * 2)(float(lo[0]), float(lo[1]))
+    hi_ = (C.c_double * 2)(float(hi[0]), float(hi[1]))
+    h = _VP()
+    _check(lib().ants_lrf_fit_symmetric(ctx, det, ni, lo_, hi_, int(cl.max()) + 1, cl.ctypes.data_as(_IP),
+                                        op.ctypes.data_as(_IP), ce.ctypes.data_as(_DP), p.shape[0],
+                                        p.ctypes.data_as(_DP), v.ctypes.data_as(_DP),
+                                        None if gn is None else gn.ctypes.data_as(_DP), float(ridge), C.byref(h)))
     return h.value
 
 

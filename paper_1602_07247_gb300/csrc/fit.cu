@@ -689,6 +689,83 @@ int lrf_fit_samples(ants_ctx *ctx, int dims, const int *n_int, const double *lo,
 
 }  // namespace ants
 
+extern "C" ANTS_API int ants_lrf_fit_symmetric(ants_ctx *ctx, const ants_detector *det, const int *n_int,
+                                               const double *lo, const double *hi, int n_classes,
+                                               const int *class_host, const int *op_host, const double *centre,
+                                               long n_pts, const double *pts_host, const double *vals_host,
+                                               const double *gain_host, double ridge, ants_lrf **out)
+{
+    using namespace ants;
+    begin_call();
+    if (!out) return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: out is NULL");
+    *out = nullptr;
+    if (!ctx || !det || !n_int || !lo || !hi || !class_host || !op_host || !centre ||
+        (n_pts > 0 && (!pts_host || !vals_host)))
+        return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: NULL argument");
+    if (n_pts < 0 || n_pts > (1L << 30) / (det->n_s > 0 ? det->n_s : 1))
+        return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: n_pts out of range");
+    if (!(ridge >= 0.0)) return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: ridge must be >= 0");
+    if (n_classes < 1 || n_classes > det->n_s) return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: n_classes");
+    const int n_s = det->n_s;
+    for (int i = 0; i < n_s; ++i) {
+        if (class_host[i] < 0 || class_host[i] >= n_classes || op_host[i] < 0 || op_host[i] > 23)
+            return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: sensor %d class or operation out of range", i);
+        if (gain_host && !(gain_host[i] > 0.0)) return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: gains must be > 0");
+    }
+    for (int a = 0; a < 2; ++a)
+        if (n_int[a] < 1 || n_int[a] > 256 || !(lo[a] < hi[a]))
+            return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: axis %d needs 1 <= n_int <= 256, lo < hi", a);
+    const long nc = (long)(n_int[0] + 3) * (n_int[1] + 3);
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = ctx->stream[0];
+    std::vector<double> coef((size_t)nc * n_classes);
+    for (int j = 0; j < n_classes; ++j) {
+        // the members' samples mapped into the representative's frame,
+        // M^T (p - c) + c, values over the gains; points outside the box left out
+        std::vector<double> P, V;
+        for (int i = 0; i < n_s; ++i) {
+            if (class_host[i] != j) continue;
+            const int k = op_host[i];
+            const double t = (double)(k % 12) * (3.14159265358979323846 / 6.0);
+            double c = std::cos(t), sn = std::sin(t);
+            if (k % 3 == 0) {
+                const int q = (k % 12) / 3;
+                c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+                sn = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+            }
+            const double f = k >= 12 ? -1.0 : 1.0;
+            const double m00 = c, m01 = -sn * f, m10 = sn, m11 = c * f;
+            const double g = gain_host ? gain_host[i] : 1.0;
+            for (long e = 0; e < n_pts; ++e) {
+                const double dx = pts_host[2 * e] - centre[0], dy = pts_host[2 * e + 1] - centre[1];
+                const double x = m00 * dx + m10 * dy + centre[0], y = m01 * dx + m11 * dy + centre[1];
+                if (!(x >= lo[0] && x <= hi[0] && y >= lo[1] && y <= hi[1])) continue;
+                P.push_back(x);
+                P.push_back(y);
+                V.push_back(vals_host[e * n_s + i] / g);
+            }
+        }
+        const long np = (long)V.size();
+        DevBuf d_pts, d_vals;
+        FIT_TRY(dalloc<double>(d_pts, (size_t)np * 2, "points"));
+        FIT_TRY(dalloc<double>(d_vals, (size_t)np, "values"));
+        if (np > 0) {
+            ANTS_CUDA_TRY(cudaMemcpyAsync(d_pts.p, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                          "fit: upload points");
+            ANTS_CUDA_TRY(cudaMemcpyAsync(d_vals.p, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                          "fit: upload values");
+        }
+        int rc = lrf_fit_samples(ctx, 2, n_int, lo, hi, np, (const double *)d_pts.p, 1, (const double *)d_vals.p,
+                                 ridge, coef.data() + (size_t)j * nc, nullptr, st);
+        if (rc != ANTS_OK) return rc;
+    }
+    long launches = ants_last_launch_count();
+    int rc = ants_lrf_create_symmetric(ctx, det, n_int, lo, hi, n_classes, class_host, op_host, centre, coef.data(),
+                                       gain_host, out);
+    count_launch(launches);
+    return rc;
+}
+
 extern "C" ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int,
                                      const double *lo, const double *hi, int shared, long n_pts,
                                      const double *pts_host, const double *vals_host, double ridge,

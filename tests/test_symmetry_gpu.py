@@ -77,3 +77,20 @@ def test_symmetric_search_minimise_simulate(setup):
     assert (s.cpu().numpy() == os_).mean() > 0.999
     with pytest.raises(ants.AntsError):
         lrf.save("/tmp/ants_sym.lrf")
+
+
+def test_symmetric_fit_matches_oracle(setup):
+    """The class fit from samples (device FP64 fit of the mapped samples)
+    against the oracle's."""
+    import paper_1602_07247_gb300 as ants
+    ctx, det, L, lrf, k = setup
+    rng = np.random.default_rng(41)
+    pts = rng.uniform(-24.0, 24.0, (4000, 2))
+    vals = oracle.lrf_eval(L, pts) * rng.uniform(0.98, 1.02, (4000, 64))
+    cl, op, _, c = det.symmetry(1e-6)
+    got = ants.Lrf.fit_symmetric(ctx, det, (12, 12), (-24.0, -24.0), (24.0, 24.0), cl, op, c, pts, vals, L.gain)
+    want = oracle.lrf_fit_symmetric(L.sensor_xy, cl, op, c, (12, 12), (-24.0, -24.0), (24.0, 24.0), pts, vals,
+                                    gain=L.gain)
+    cg = got.coefficients()
+    assert cg.shape == want.coef.shape
+    assert np.abs(cg - want.coef).max() <= 1e-9 * np.abs(want.coef).max()
