@@ -952,6 +952,10 @@ def lrf_refit(lrf: Lrf, sig, xyz, E, shared=None, refit_gains: bool = False, rid
     shared = lrf.shared if shared is None else bool(shared)
     v = sig / E[:, None]
     n_s = lrf.n_sensors
+    if lrf.type == XY and lrf.op is not None:
+        # symmetry classes: each class refitted to its members' mapped samples, gains kept
+        return lrf_fit_symmetric(lrf.sensor_xy, lrf.group, lrf.op, lrf.sym_c, lrf.n_int[:2], lrf.lo[:2], lrf.hi[:2],
+                                 xyz[:, :2], v, gain=lrf.gain, ridge=ridge, mutant=mutant)
     if lrf.type != RADIAL:
         dims = 2 if lrf.type == XY else 3
         coef, _, _ = lrf_fit(lrf.n_int, lrf.lo, lrf.hi, xyz[:, :dims], v, ridge, mutant)

@@ -51,7 +51,7 @@ int lrf_dims(int type)
 
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
 {
-    if (slot < 0 || slot >= 12) {
+    if (slot < 0 || slot >= 13) {
         fail(ANTS_E_INTERNAL, "scratch slot %d", slot);
         return nullptr;
     }
@@ -153,7 +153,7 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_host_buffers(ctx);
-    for (int k = 0; k < 12; ++k) cudaFree(ctx->scratch[k]);
+    for (int k = 0; k < 13; ++k) cudaFree(ctx->scratch[k]);
     cudaFree(ctx->d_fault);
     for (int k = 0; k < 2; ++k)
         if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);

@@ -84,9 +84,10 @@ struct ants_ctx {
     int32_t *d_status[2] = {nullptr, nullptr};
     // general device scratch slots (grown on demand by ants::ctx_scratch):
     // 0 network activations, 1-6 precision and learned forms, 7 FP16
-    // widening, 8-9 LRF fit, 10 refit samples, 11 event filter
-    void *scratch[12] = {};
-    size_t scratch_cap[12] = {};
+    // widening, 8-9 LRF fit, 10 refit samples, 11 event filter, 12 mapped
+    // samples of symmetry classes
+    void *scratch[13] = {};
+    size_t scratch_cap[13] = {};
     // device word set by a kernel whose bounded wait ran out (ants_ctx_fault)
     int *d_fault = nullptr;
 };
@@ -154,7 +155,7 @@ struct Carve {
         return at;
     }
 };
-// device scratch slot `slot` (0..11) of at least `bytes`; NULL (error recorded) on failure.
+// device scratch slot `slot` (0..12) of at least `bytes`; NULL (error recorded) on failure.
 // Growing a slot frees the old buffer, so the caller must not have work in
 // flight that uses it.
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes);

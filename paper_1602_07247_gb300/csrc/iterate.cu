@@ -273,6 +273,27 @@ __global__ void samples_box(const int32_t *index, long n_kept, int dims, int n_s
     for (int i = 0; i < n_s; ++i) vals[k * n_s + i] = (double)sig[e * n_s + i] * inv_e;
 }
 
+// XY symmetry-class samples, one thread per kept event: for every sensor i
+// its row row_of[i] (the members of a class in consecutive rows) receives
+// the event's position mapped into the class representative's frame, M^T (p
+// - c) + c (opm: the operations' 2 x 2 matrices, row-major), and the value
+// v / g_i
+__global__ void samples_sym(const double *pts, const double *vals, long n_kept, int n_s, const int *row_of,
+                            const int *op_of, const double *opm, double cx, double cy, const double *inv_g, double *P,
+                            double *V)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_kept) return;
+    const double dx = pts[2 * k] - cx, dy = pts[2 * k + 1] - cy;
+    for (int i = 0; i < n_s; ++i) {
+        const double *M = opm + 4 * op_of[i];
+        const long o = (long)row_of[i] * n_kept + k;
+        P[2 * o] = M[0] * dx + M[2] * dy + cx;
+        P[2 * o + 1] = M[1] * dx + M[3] * dy + cy;
+        V[o] = vals[k * n_s + i] * inv_g[i];
+    }
+}
+
 // RADIAL samples, one thread per kept event: r = distance to sensor i,
 // v = s / E (times inv_g[i] when given); by_sensor stores [i][k], otherwise
 // [k][i]
@@ -362,6 +383,73 @@ int make_like(ants_ctx *ctx, const ants_lrf *like, int shared, const std::vector
     return rc;
 }
 
+// XY symmetry classes: one fit per class to its members' mapped samples
+// (the points outside the box are left out by the fit), gains kept
+int refit_symmetric(ants_ctx *ctx, const ants_lrf *lrf, const double *A, const double *B, long n_kept,
+                    const ants_refit_params &p, cudaStream_t st, ants_lrf **out)
+{
+    const int n_s = lrf->n_s, n_sets = lrf->n_sets, nc = lrf->n_coef;
+    std::vector<int> row(n_s), first(n_sets + 1, 0);
+    for (int i = 0; i < n_s; ++i) first[lrf->groups[i] + 1]++;
+    for (int j = 0; j < n_sets; ++j) first[j + 1] += first[j];
+    std::vector<int> fill(first.begin(), first.end() - 1);
+    for (int i = 0; i < n_s; ++i) row[i] = fill[lrf->groups[i]]++;
+    std::vector<double> opm(24 * 4), inv_g(n_s);
+    for (int k = 0; k < 24; ++k) {
+        const double t = (double)(k % 12) * (3.14159265358979323846 / 6.0);
+        double c = std::cos(t), sn = std::sin(t);
+        if (k % 3 == 0) {
+            const int q = (k % 12) / 3;
+            c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+            sn = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        }
+        const double f = k >= 12 ? -1.0 : 1.0;
+        opm[4 * k] = c;
+        opm[4 * k + 1] = -sn * f;
+        opm[4 * k + 2] = sn;
+        opm[4 * k + 3] = c * f;
+    }
+    for (int i = 0; i < n_s; ++i) inv_g[i] = 1.0 / lrf->gain[i];
+    const long total = n_kept * (long)n_s;
+    Carve cv;
+    const size_t o_p = cv.take<double>(2 * (size_t)total), o_v = cv.take<double>(total);
+    const size_t o_row = cv.take<int>(n_s), o_op = cv.take<int>(n_s), o_m = cv.take<double>(96),
+                 o_g = cv.take<double>(n_s);
+    char *base = (char *)ctx_scratch(ctx, 12, cv.off);  // not a slot of the fit
+    if (!base) return ANTS_E_OOM;
+    double *P = (double *)(base + o_p), *V = (double *)(base + o_v), *d_m = (double *)(base + o_m);
+    double *d_g = (double *)(base + o_g);
+    int *d_row = (int *)(base + o_row), *d_op = (int *)(base + o_op);
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_row, row.data(), n_s * sizeof(int), cudaMemcpyHostToDevice, st), "refit: rows");
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_op, lrf->ops.data(), n_s * sizeof(int), cudaMemcpyHostToDevice, st),
+                  "refit: operations");
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_m, opm.data(), 96 * sizeof(double), cudaMemcpyHostToDevice, st),
+                  "refit: matrices");
+    ANTS_CUDA_TRY(cudaMemcpyAsync(d_g, inv_g.data(), n_s * sizeof(double), cudaMemcpyHostToDevice, st),
+                  "refit: gains");
+    if (n_kept > 0) {
+        samples_sym<<<blocks_for(n_kept, 256), 256, 0, st>>>(A, B, n_kept, n_s, d_row, d_op, d_m, lrf->sym_c[0],
+                                                             lrf->sym_c[1], d_g, P, V);
+        ANTS_CUDA_TRY(cudaGetLastError(), "refit class samples launch");
+        count_launch();
+    }
+    std::vector<double> coef((size_t)n_sets * nc);
+    for (int j = 0; j < n_sets; ++j) {
+        const long np = (long)(first[j + 1] - first[j]) * n_kept;
+        IT_TRY(lrf_fit_samples(ctx, 2, lrf->n_int, lrf->lo, lrf->hi, np, P + 2 * (size_t)first[j] * n_kept, 1,
+                               V + (size_t)first[j] * n_kept, p.ridge, coef.data() + (size_t)j * nc, nullptr, st));
+    }
+    ants_detector det;
+    det.n_s = n_s;
+    det.xy = lrf->sxy;
+    det.gain = lrf->rel_gain;
+    const long launches = ants_last_launch_count();
+    const int rc = ants_lrf_create_symmetric(ctx, &det, lrf->n_int, lrf->lo, lrf->hi, n_sets, lrf->groups.data(),
+                                             lrf->ops.data(), lrf->sym_c, coef.data(), lrf->gain.data(), out);
+    count_launch(launches);
+    return rc;
+}
+
 int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float *xyz, const float *E,
               const int32_t *index, long n_kept, const ants_refit_params &p, cudaStream_t st, ants_lrf **out)
 {
@@ -388,6 +476,7 @@ int refit_lrf(ants_ctx *ctx, const ants_lrf *lrf, const float *sig, const float 
             ANTS_CUDA_TRY(cudaGetLastError(), "refit samples launch");
             count_launch();
         }
+        if (!lrf->ops.empty()) return refit_symmetric(ctx, lrf, A, B, n_kept, p, st, out);
         std::vector<double> coef((size_t)n_s * nc);
         IT_TRY(lrf_fit_samples(ctx, dims, lrf->n_int, lrf->lo, lrf->hi, n_kept, A, n_s, B, p.ridge, coef.data(),
                                nullptr, st));
@@ -532,8 +621,7 @@ int check_refit(const ants_lrf *lrf, const ants_refit_params *p)
     if (!p) return fail(ANTS_E_ARG, "refit parameters are NULL");
     if (!(p->shift_sigma >= 0.0) || !(p->ridge >= 0.0)) return fail(ANTS_E_ARG, "refit: shift_sigma, ridge >= 0");
     if (p->cycle < 0) return fail(ANTS_E_ARG, "refit: cycle < 0");
-    if (lrf->type > ANTS_LRF_XYZ || !lrf->ops.empty())
-        return fail(ANTS_E_UNIMPLEMENTED, "refit: RADIAL, XY and XYZ LRFs only (no XY symmetry classes)");
+    if (lrf->type > ANTS_LRF_XYZ) return fail(ANTS_E_UNIMPLEMENTED, "refit: RADIAL, XY and XYZ LRFs only");
     if (lrf->type != ANTS_LRF_RADIAL && p->shared) return fail(ANTS_E_ARG, "refit: groups are RADIAL only");
     if (p->refit_gains && !(lrf->type == ANTS_LRF_RADIAL && (p->shared || !lrf->groups.empty())))
         return fail(ANTS_E_ARG, "refit: gains are refitted for RADIAL groups only");

@@ -94,3 +94,23 @@ def test_symmetric_fit_matches_oracle(setup):
     cg = got.coefficients()
     assert cg.shape == want.coef.shape
     assert np.abs(cg - want.coef).max() <= 1e-9 * np.abs(want.coef).max()
+
+
+def test_symmetric_refit_matches_oracle(setup):
+    """The refit of the classes from reconstructed events (positions shifted
+    by the seeded offsets) equals the oracle's class fit of the same samples."""
+    import torch
+    import paper_1602_07247_gb300 as ants
+    ctx, det, L, lrf, k = setup
+    sig, tr = oracle.simulate(L, 6, 0, 3000, region="square", extent=18.0, e0=3000.0, e_spread=0.05)
+    sd = torch.from_numpy(sig.astype(np.float32)).cuda()
+    p = ants.CgsParams(n_xy=11, iters=8, step_xy=4.8, shrink=0.5)
+    res = ants.reconstruct(ctx, lrf, p, sd)
+    keep = np.nonzero(res.status.cpu().numpy() == 0)[0].astype(np.int32)
+    R = lrf.refit(sd, res.xyz, res.E, index=torch.from_numpy(keep).cuda(), shift_sigma=0.5, seed=4, cycle=2)
+    xyz = res.xyz.cpu().numpy()[keep].astype(np.float64)
+    xyz[:, :2] += oracle.shift_xy(4, 2, keep, 0.5)
+    want = oracle.lrf_refit(L, sig[keep], xyz, res.E.cpu().numpy()[keep].astype(np.float64))
+    c = R.coefficients()
+    assert c.shape == want.coef.shape
+    assert np.abs(c - want.coef).max() <= 1e-8 * np.abs(want.coef).max()
