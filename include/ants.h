@@ -415,8 +415,9 @@ ANTS_API int ants_lrf_create_grouped(ants_ctx *ctx, const ants_detector *det, co
  * per-sensor gains.  eta_i(p) = g_i F_class(i)(M_i^T (p - c) + c); a point is
  * inside the domain when every mapped point lies in the XY box.  Used by the
  * plain search (through the per-node kernel), the variants, the
- * minimisation, the simulator and evaluation; not by the precision and
- * learned forms or batches, not saved or refitted (ANTS_E_UNIMPLEMENTED).
+ * minimisation, the simulator, evaluation, the refit (each class refitted to
+ * its members' mapped samples, gains kept) and the iteration; not by the
+ * precision and learned forms or batches, not saved (ANTS_E_UNIMPLEMENTED).
  * Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_lrf_create_symmetric(ants_ctx *ctx, const ants_detector *det, const int *n_int, const double *lo,
                                        const double *hi, int n_classes, const int *class_host, const int *op_host,
