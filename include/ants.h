@@ -818,6 +818,9 @@ ANTS_API int ants_event_filter(ants_ctx *ctx, long n_events, const int32_t *stat
  *     p->refit_gains each sensor's gain against its group's new profile,
  *     scaled to mean 1 within the group (the group's profile taking the
  *     factor).  The output keeps the groups.
+ *   XY with symmetry classes (ants_lrf_create_symmetric): one fit per class
+ *     of its members' positions mapped into the class frame, values
+ *     v_ei / g_i; gains and classes kept.
  * The output has the input's knot grid, sensors and relative gains.
  * Synchronous.  Errors: ANTS_E_ARG, ANTS_E_LRF (a fit stayed singular, e.g.
  * no events), ANTS_E_OOM, ANTS_E_CUDA. */
