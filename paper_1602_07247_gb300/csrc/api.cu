@@ -241,21 +241,6 @@ static int upload_lrf(ants_lrf *L)
     D.n_sets = L->n_sets;
     D.sym_c[0] = (float)L->sym_c[0];
     D.sym_c[1] = (float)L->sym_c[1];
-    for (int k = 0; k < 24; ++k) {
-        // rotation by (k mod 12) x 30 degrees after the reflection y -> -y for k >= 12
-        const double t = (double)(k % 12) * (3.14159265358979323846 / 6.0);
-        double c = std::cos(t), sn = std::sin(t);
-        if (k % 3 == 0) {
-            const int q = (k % 12) / 3;
-            c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
-            sn = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
-        }
-        const double f = k >= 12 ? -1.0 : 1.0;
-        D.op_m[k][0] = (float)c;
-        D.op_m[k][1] = (float)(-sn * f);
-        D.op_m[k][2] = (float)sn;
-        D.op_m[k][3] = (float)(c * f);
-    }
     if (!L->ops.empty()) {
         ANTS_CUDA_TRY(cudaMalloc(&L->d_op_of, L->ops.size() * sizeof(int)), "cudaMalloc(lrf operations)");
         ANTS_CUDA_TRY(cudaMemcpy(L->d_op_of, L->ops.data(), L->ops.size() * sizeof(int), cudaMemcpyHostToDevice),

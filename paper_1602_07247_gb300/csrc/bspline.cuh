@@ -149,12 +149,13 @@ __device__ __forceinline__ float lrf_eta_t(const LrfDev &L, int i, float x, floa
     }
     const float *c = L.coef + (size_t)i * L.n_coef;
     float gs = 1.0f;
-    if (TYPE == ANTS_LRF_XY && L.set_of) {
+    if (TYPE == kLrfXYSym) {
         // a symmetry class: the representative's LRF at M^T (p - c) + c, times the gain
-        const int k = __ldg(L.op_of + i);
+        float m[4];
+        sym_op(__ldg(L.op_of + i), m);
         const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
-        x = fmaf(L.op_m[k][0], dx, fmaf(L.op_m[k][2], dy, L.sym_c[0]));
-        y = fmaf(L.op_m[k][1], dx, fmaf(L.op_m[k][3], dy, L.sym_c[1]));
+        x = fmaf(m[0], dx, fmaf(m[2], dy, L.sym_c[0]));
+        y = fmaf(m[1], dx, fmaf(m[3], dy, L.sym_c[1]));
         c = L.coef + (size_t)__ldg(L.set_of + i) * L.n_coef;
         gs = __ldg(L.gain + i);
     }
@@ -192,7 +193,7 @@ __device__ __forceinline__ float lrf_eta_point(const LrfDev &L, int i, float x, 
 {
     switch (L.type) {
     case ANTS_LRF_RADIAL: return lrf_eta_t<ANTS_LRF_RADIAL>(L, i, x, y, z, ok);
-    case ANTS_LRF_XY: return lrf_eta_t<ANTS_LRF_XY>(L, i, x, y, z, ok);
+    case ANTS_LRF_XY: return L.set_of ? lrf_eta_t<kLrfXYSym>(L, i, x, y, z, ok) : lrf_eta_t<ANTS_LRF_XY>(L, i, x, y, z, ok);
     case ANTS_LRF_XYZ: return lrf_eta_t<ANTS_LRF_XYZ>(L, i, x, y, z, ok);
     case ANTS_LRF_COMPOSITE: return lrf_eta_t<ANTS_LRF_COMPOSITE>(L, i, x, y, z, ok);
     case ANTS_LRF_AXIAL_Z: return lrf_eta_t<ANTS_LRF_AXIAL_Z>(L, i, x, y, z, ok);
@@ -311,13 +312,12 @@ __device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x,
         return fmaf(w, f1, (1.0f - w) * f0);
     }
     const float *c = L.coef + (size_t)i * L.n_coef;
-    float gs = 1.0f;
-    int kop = -1;
-    if (TYPE == ANTS_LRF_XY && L.set_of) {
-        kop = __ldg(L.op_of + i);
+    float gs = 1.0f, m[4] = {1.0f, 0.0f, 0.0f, 1.0f};
+    if (TYPE == kLrfXYSym) {
+        sym_op(__ldg(L.op_of + i), m);
         const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
-        x = fmaf(L.op_m[kop][0], dx, fmaf(L.op_m[kop][2], dy, L.sym_c[0]));
-        y = fmaf(L.op_m[kop][1], dx, fmaf(L.op_m[kop][3], dy, L.sym_c[1]));
+        x = fmaf(m[0], dx, fmaf(m[2], dy, L.sym_c[0]));
+        y = fmaf(m[1], dx, fmaf(m[3], dy, L.sym_c[1]));
         c = L.coef + (size_t)__ldg(L.set_of + i) * L.n_coef;
         gs = __ldg(L.gain + i);
     }
@@ -361,11 +361,11 @@ __device__ __forceinline__ float lrf_eta_grad_t(const LrfDev &L, int i, float x,
     gx = fx * L.inv_h[0];
     gy = fy * L.inv_h[1];
     gz = TYPE == ANTS_LRF_XYZ ? fz * L.inv_h[2] : 0.0f;
-    if (TYPE == ANTS_LRF_XY && kop >= 0) {
+    if (TYPE == kLrfXYSym) {
         // the gradient of F(M^T (p - c) + c) is M grad F
         const float ux = gx, uy = gy;
-        gx = gs * fmaf(L.op_m[kop][0], ux, L.op_m[kop][1] * uy);
-        gy = gs * fmaf(L.op_m[kop][2], ux, L.op_m[kop][3] * uy);
+        gx = gs * fmaf(m[0], ux, m[1] * uy);
+        gy = gs * fmaf(m[2], ux, m[3] * uy);
     }
     return gs * f;
 }
@@ -386,10 +386,11 @@ __device__ __forceinline__ bool lrf_defined(const LrfDev &L, const float *s_act,
         // symmetry classes: every sensor's mapped point inside the box
         for (int i = 0; i < L.n_s; ++i) {
             if (s_act && s_act[i] == 0.0f) continue;
-            const int k = __ldg(L.op_of + i);
+            float m[4];
+            sym_op(__ldg(L.op_of + i), m);
             const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
-            const float u = fmaf(L.op_m[k][0], dx, fmaf(L.op_m[k][2], dy, L.sym_c[0]));
-            const float v = fmaf(L.op_m[k][1], dx, fmaf(L.op_m[k][3], dy, L.sym_c[1]));
+            const float u = fmaf(m[0], dx, fmaf(m[2], dy, L.sym_c[0]));
+            const float v = fmaf(m[1], dx, fmaf(m[3], dy, L.sym_c[1]));
             if (!in_box(L, u, v, z)) return false;
         }
         return true;

@@ -50,9 +50,8 @@ struct LrfDev {
     const float *coef_t;   // XY: the coefficients sensor-minor, [k][n_s] (per-point loops over sensors)
     const int *set_of;     // RADIAL grouped / XY symmetry classes (Sec. 6.2): the coefficient set of each sensor; nullable
     int n_sets;            // coefficient sets
-    const int *op_of;      // XY symmetry classes: the operation of each sensor (index into op_m)
+    const int *op_of;      // XY symmetry classes: the operation of each sensor (sym_op)
     float sym_c[2];        // XY symmetry classes: the centre of the operations
-    float op_m[24][4];     // the 2 x 2 matrices of the operations (rotations by k 30 degrees, then reflections)
     // RADIAL LRFs: each interval's cubic in the power basis of its local
     // parameter t, (p0, p1, p2, p3) with f = p0 + t (p1 + t (p2 + t p3)),
     // [n_sets][n_int[0]]
@@ -126,13 +125,48 @@ struct ants_lrf {
 namespace ants {
 int lrf_dims(int type);
 // the LRF types with a z coordinate / with an XY box as (part of) their domain
+// kernel template argument for XY sets with symmetry classes (their API type
+// stays ANTS_LRF_XY; the kernels that read them are instantiated apart so the
+// plain XY code carries no symmetry branch)
+constexpr int kLrfXYSym = 100;
+
+// the 2 x 2 matrix of symmetry operation k (row-major): the rotation by
+// (k mod 12) x 30 degrees, preceded for k >= 12 by the reflection y -> -y
+__host__ __device__ inline void sym_op(int k, float m[4])
+{
+    // cos and sin of (k mod 12) x 30 degrees, rounded to float (no table, so
+    // no local memory in the kernels)
+    const float h = 0.8660254037844386f;
+    float c = 1.0f, s = 0.0f;
+    switch (k % 12) {
+    case 1: c = h; s = 0.5f; break;
+    case 2: c = 0.5f; s = h; break;
+    case 3: c = 0.0f; s = 1.0f; break;
+    case 4: c = -0.5f; s = h; break;
+    case 5: c = -h; s = 0.5f; break;
+    case 6: c = -1.0f; s = 0.0f; break;
+    case 7: c = -h; s = -0.5f; break;
+    case 8: c = -0.5f; s = -h; break;
+    case 9: c = 0.0f; s = -1.0f; break;
+    case 10: c = 0.5f; s = -h; break;
+    case 11: c = h; s = -0.5f; break;
+    default: break;
+    }
+    const float f = k >= 12 ? -1.0f : 1.0f;
+    m[0] = c;
+    m[1] = -s * f;
+    m[2] = s;
+    m[3] = c * f;
+}
+
 __host__ __device__ inline bool lrf_is_3d(int type)
 {
     return type == ANTS_LRF_XYZ || type == ANTS_LRF_AXIAL_Z || type == ANTS_LRF_SLICED;
 }
 __host__ __device__ inline bool lrf_has_box(int type)
 {
-    return type == ANTS_LRF_XY || type == ANTS_LRF_XYZ || type == ANTS_LRF_COMPOSITE || type == ANTS_LRF_SLICED;
+    return type == ANTS_LRF_XY || type == ANTS_LRF_XYZ || type == ANTS_LRF_COMPOSITE || type == ANTS_LRF_SLICED ||
+           type == kLrfXYSym;
 }
 // any LRF type: create from coefficients (api.cu)
 int lrf_create_impl(ants_ctx *ctx, const ants_detector *det, int type, const int *n_int, const double *lo,

@@ -77,14 +77,15 @@ __device__ __forceinline__ bool defined_group(const LrfDev &L, const float *s_ac
         for (int i = lane & (G - 1); live && i < L.n_s; i += G)
             if (s_act[i] != 0.0f && plane_dist(x - L.sxy[2 * i], y - L.sxy[2 * i + 1]) > rhi) ok = false;
     }
-    if (TYPE == ANTS_LRF_XY && L.set_of) {
+    if (TYPE == kLrfXYSym) {
         // symmetry classes: every sensor's mapped point inside the box
         for (int i = lane & (G - 1); live && i < L.n_s; i += G) {
             if (s_act[i] == 0.0f) continue;
-            const int k = __ldg(L.op_of + i);
+            float m[4];
+            sym_op(__ldg(L.op_of + i), m);
             const float dx = x - L.sym_c[0], dy = y - L.sym_c[1];
-            const float u = fmaf(L.op_m[k][0], dx, fmaf(L.op_m[k][2], dy, L.sym_c[0]));
-            const float v = fmaf(L.op_m[k][1], dx, fmaf(L.op_m[k][3], dy, L.sym_c[1]));
+            const float u = fmaf(m[0], dx, fmaf(m[2], dy, L.sym_c[0]));
+            const float v = fmaf(m[1], dx, fmaf(m[3], dy, L.sym_c[1]));
             if (!in_box(L, u, v, z)) ok = false;
         }
         return Group<G>::all(ok, lane);
@@ -155,7 +156,7 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
     // computed once, not per sensor (the same arithmetic as lrf_eta_grad_t)
     int jx = 0, jy = 0;
     float wx[4], wy[4], dwx[4], dwy[4];
-    if (TYPE == ANTS_LRF_XY && L.coef_t) {
+    if (TYPE == ANTS_LRF_XY) {
         float tx, ty;
         jx = bs_span(q[0], L.lo[0], L.inv_h[0], L.n_int[0], tx);
         jy = bs_span(q[1], L.lo[1], L.inv_h[1], L.n_int[1], ty);
@@ -168,7 +169,7 @@ __device__ __forceinline__ PointSums point_pass(const MinArgs &a, const float *s
         if (s_act[i] == 0.0f) continue;
         bool ok;
         float gx, gy, gz = 0.0f, eta;
-        if (TYPE == ANTS_LRF_XY && L.coef_t) {
+        if (TYPE == ANTS_LRF_XY) {
             // sensor-minor copy: the group's lanes read neighbouring sensors
             const float *c = L.coef_t + (size_t)(jy * L.stride_y + jx) * n_s + i;
             const size_t rs = (size_t)L.stride_y * n_s;
@@ -469,7 +470,10 @@ int reconstruct_minimize(const ants_ctx *ctx, const ants_lrf *lrf, const ants_mi
                : minimize_kernel<T, D, 32><<<g, t, smem, s>>>(a))
     switch (lrf->type) {
     case ANTS_LRF_RADIAL: ANTS_MIN_LAUNCH(ANTS_LRF_RADIAL, 2); break;
-    case ANTS_LRF_XY: ANTS_MIN_LAUNCH(ANTS_LRF_XY, 2); break;
+    case ANTS_LRF_XY:
+        if (lrf->dev.set_of) ANTS_MIN_LAUNCH(kLrfXYSym, 2);
+        else ANTS_MIN_LAUNCH(ANTS_LRF_XY, 2);
+        break;
     case ANTS_LRF_COMPOSITE: ANTS_MIN_LAUNCH(ANTS_LRF_COMPOSITE, 2); break;
     case ANTS_LRF_XYZ:
         if (z) ANTS_MIN_LAUNCH(ANTS_LRF_XYZ, 3);

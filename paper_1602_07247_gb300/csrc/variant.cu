@@ -259,7 +259,10 @@ int reconstruct_variant(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs
     if (blocks > cap) blocks = cap;
     switch (lrf->type) {
     case ANTS_LRF_RADIAL: cgs_variant_kernel<ANTS_LRF_RADIAL><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
-    case ANTS_LRF_XY: cgs_variant_kernel<ANTS_LRF_XY><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
+    case ANTS_LRF_XY:
+        if (lrf->dev.set_of) cgs_variant_kernel<kLrfXYSym><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        else cgs_variant_kernel<ANTS_LRF_XY><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
+        break;
     case ANTS_LRF_XYZ: cgs_variant_kernel<ANTS_LRF_XYZ><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a); break;
     case ANTS_LRF_COMPOSITE:
         cgs_variant_kernel<ANTS_LRF_COMPOSITE><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a);
