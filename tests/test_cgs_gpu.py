@@ -64,7 +64,10 @@ def test_cgs_parity(torch_cuda, ctx, name, n):
     stats = compare(w, L, ev.signals, gpu)
     print(name, stats)
     assert stats["n"] == n
-    assert stats["tie_frac"] < 0.5
+    # PMT workload: at most 5 % of events need a certified tie.  On the 8x8
+    # SiPM array the last grids' nodes (0.0375 mm apart) differ in F by less
+    # than one FP32 ulp of F, so about a fifth of the events do.
+    assert stats["tie_frac"] < {"hex19_radial": 0.05, "sipm8x8_xy": 0.3}[name]
 
 
 def test_cgs_parity_given_start(torch_cuda, ctx):
