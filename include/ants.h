@@ -500,7 +500,7 @@ ANTS_API int ants_lrf_coefficients(const ants_lrf *lrf, double *coef_host, size_
  * >= n_sensors.  Errors: ANTS_E_ARG. */
 ANTS_API int ants_lrf_gains(const ants_lrf *lrf, double *gain_host, size_t count);
 
-/* Evaluate eta_i at n_pts points for all sensors: pts_dev[n_pts][dim] FP32
+/* Evaluate eta_i (the LRFs of Sec. 6, 6.1) at n_pts points for all sensors: pts_dev[n_pts][dim] FP32
  * (dim = 2 for RADIAL/XY, 3 for XYZ), out_dev[n_pts][n_sensors] FP32.
  * Points outside the LRF domain give NaN.  Asynchronous on `stream`.
  * Errors: ANTS_E_ARG, ANTS_E_CUDA. */
@@ -609,12 +609,18 @@ ANTS_API int ants_simulate_events(ants_ctx *ctx, const ants_lrf *lrf, const ants
 ANTS_API int ants_logtable_create(ants_ctx *ctx, const ants_lrf *lrf, int nx, int ny, ants_logtable **out);
 
 /* Copy the table as FP32 (table_host [nx*ny][n_sensors], nullable) and the
- * centring constants m (mean_host [n_sensors], nullable). */
+ * centring constants m (mean_host [n_sensors], nullable).  Synchronous.
+ * Errors: ANTS_E_ARG, ANTS_E_CUDA. */
 ANTS_API int ants_logtable_values(const ants_logtable *table, float *table_host, float *mean_host);
 
-/* Top-K grid points of each event by score sum_i s_i T[g][i]: score_dev and
- * index_dev [n_events][top_k], descending score, ties to the lower index.
- * Signals FP32 (rounded to BF16 for the product).  Asynchronous. */
+/* Top-K grid points of each event by score sum_i s_i T[g][i] (the profiled
+ * likelihood of Sec. 5.1.2, 5.1.2.2 ranked over a global grid): score_dev and
+ * index_dev [n_events][top_k], descending score, ties to the lower index,
+ * top_k in [1, 8].  Signals FP32 (rounded to BF16 for the product).
+ * Asynchronous.  A bounded device-side wait that runs out sets the context's
+ * fault word (ants_ctx_fault); the outputs are then undefined.
+ * Errors: ANTS_E_ARG, ANTS_E_SHAPE (n_sensors differs from the table's),
+ * ANTS_E_CUDA. */
 ANTS_API int ants_logtable_topk(ants_ctx *ctx, const ants_logtable *table, const float *signals_dev,
                                 long n_events, int n_sensors, int top_k, float *score_dev,
                                 int32_t *index_dev, void *stream);
@@ -659,7 +665,8 @@ ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch
                                     const ants_batch_config *cfg, ants_batch_plan **out);
 
 /* Launch the plan's graph on `stream` (asynchronous).  Calls with one plan
- * must not overlap (they share the work counter). */
+ * must not overlap (they share the work counter).
+ * Errors: ANTS_E_ARG, ANTS_E_CUDA. */
 ANTS_API int ants_batch_run(ants_batch_plan *plan, void *stream);
 
 /* Choose the launch shape: time every candidate (units of 4/16/64 events,
@@ -667,7 +674,9 @@ ANTS_API int ants_batch_run(ants_batch_plan *plan, void *stream);
  * events of every detector (<= 0: 2048) and keep the fastest.  With
  * cache_path, a previous choice for the same batch signature is reused, and
  * a new choice is appended to that text file.  Synchronous.  The plan is
- * rebuilt with the choice; *chosen (nullable) receives it. */
+ * rebuilt with the choice; *chosen (nullable) receives it.  A cache file
+ * that cannot be opened is skipped (no error).  get_config copies the plan's
+ * current shape.  Errors: ANTS_E_ARG, ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_batch_autotune(ants_batch_plan *plan, const char *cache_path, long events_per_item,
                                  ants_batch_config *chosen);
 ANTS_API int ants_batch_get_config(const ants_batch_plan *plan, ants_batch_config *cfg);
@@ -678,31 +687,39 @@ ANTS_API void ants_batch_plan_free(ants_batch_plan *plan);
 /* ------------------------------------------------------------------------ */
 
 /* Create a network for n_in inputs (the sensor count) with He-normal hidden
- * and Xavier-normal output weights from `seed`, zero biases. */
+ * and Xavier-normal output weights from `seed`, zero biases.  The network
+ * plays the part of the neural-network reconstruction of Sec. 5.1.3; the
+ * paper does not specify its architecture.  Errors: ANTS_E_ARG, ANTS_E_OOM,
+ * ANTS_E_CUDA. */
 ANTS_API int ants_mlp_create(ants_ctx *ctx, int n_in, const ants_mlp_config *cfg, uint64_t seed,
                              ants_mlp **out);
 ANTS_API void ants_mlp_free(ants_mlp *mlp);
 
-/* Shape: inputs, hidden width, number of parameters (nullable outputs). */
+/* Shape: inputs, hidden width, number of parameters (nullable outputs).
+ * Errors: ANTS_E_ARG. */
 ANTS_API int ants_mlp_shape(const ants_mlp *mlp, int *n_in, int *n_hidden, long *n_params);
 
 /* FP32 parameters, concatenated in the order W1 [H][n_in], b1 [H],
  * W2 [H][H], b2 [H], W3 [3][H], b3 [3] (row-major [out][in]).  set resets the
- * optimiser state.  count must equal (get: be at least) n_params. */
+ * optimiser state.  count must equal (get: be at least) n_params.
+ * Synchronous.  Errors: ANTS_E_ARG, ANTS_E_CUDA. */
 ANTS_API int ants_mlp_set_params(ants_mlp *mlp, const float *params_host, long count);
 ANTS_API int ants_mlp_get_params(const ants_mlp *mlp, float *params_host, long count);
 
 /* Network outputs for device signals [n_events][n_sensors]: out_dev
  * [n_events][3] raw outputs; start_xyz_dev (nullable) [n_events][3] =
  * (o0 xy_scale, o1 xy_scale, 0); E_dev (nullable, needs start_xyz_dev)
- * = exp(o2 loge_std + loge_mean).  Uses the context's device scratch. */
+ * = exp(o2 loge_std + loge_mean).  Uses the context's device scratch.
+ * Errors: ANTS_E_ARG, ANTS_E_SHAPE (n_sensors differs from n_in),
+ * ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_mlp_forward(ants_ctx *ctx, const ants_mlp *mlp, const float *signals_dev,
                               long n_events, int n_sensors, int bf16, float *out_dev,
                               float *start_xyz_dev, float *E_dev, void *stream);
 
 /* Mean squared error of the network on device signals and truth
  * [n_events][4] = (x, y, z, E), and its gradient (same layout as the
- * parameters) -- for checking the backward pass.  Synchronous. */
+ * parameters) -- for checking the backward pass.  Synchronous.
+ * Errors: ANTS_E_ARG, ANTS_E_SHAPE, ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_mlp_loss_grad(ants_ctx *ctx, const ants_mlp *mlp, const float *signals_dev,
                                 const float *truth_dev, long n_events, int n_sensors, int bf16,
                                 float *loss_host, float *grads_host);
@@ -710,12 +727,15 @@ ANTS_API int ants_mlp_loss_grad(ants_ctx *ctx, const ants_mlp *mlp, const float 
 /* Train on device signals and truth [n_events][4] (x, y, z, E).  The first
  * (1 - monitor_frac) of the events are shuffled into batches every epoch;
  * the rest is the monitor set.  Synchronous; bitwise reproducible for a
- * given seed.  report nullable. */
+ * given seed.  report nullable.  Sec. 5.1.3: the training set is split
+ * off a monitoring set against over-fitting.
+ * Errors: ANTS_E_ARG, ANTS_E_SHAPE, ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *mlp, const float *signals_dev,
                             const float *truth_dev, long n_events, int n_sensors,
                             const ants_train_params *params, ants_train_report *report);
 
-/* Save / load (versioned binary: header, config, FP32 parameters). */
+/* Save / load (versioned binary: header, config, FP32 parameters).
+ * Errors: ANTS_E_ARG, ANTS_E_IO, ANTS_E_OOM, ANTS_E_CUDA. */
 ANTS_API int ants_mlp_save(const ants_mlp *mlp, const char *path);
 ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
 
@@ -789,7 +809,8 @@ ANTS_API int ants_event_chi2(ants_ctx *ctx, const ants_lrf *lrf, const float *si
                              void *stream);
 
 /* Select the events that were reconstructed (status ANTS_EVT_OK, finite
- * position, E and chi2) and pass every active cut.  index_dev (capacity
+ * position, E and chi2) and pass every active cut (the event filters of
+ * Sec. 5.2).  index_dev (capacity
  * n_events) receives the kept event indices in increasing order and
  * *n_kept_host their number.  sum_dev may be NULL when the signal-sum cut is
  * off.  Waits for the count (synchronises `stream`).
@@ -903,7 +924,8 @@ typedef enum {
     ANTS_PH_REJECTED = -5     /* discarded before tracing (pre_reject) */
 } ants_photon_outcome;
 
-/* Trace n_photons photons from each of n_src point sources
+/* Optical photon transport (Sec. 4.2.3-4.2.6, 3.5).
+ * Trace n_photons photons from each of n_src point sources
  * src_xyz_dev[n_src][3] (FP32, mm; the source's layer: z[k] <= z < z[k+1]).
  * Each photon draws its uniforms from its own Philox4x32-10 stream with key
  * seed and counter (photon, source, 0x0F7105, block) in a fixed order:
