@@ -747,8 +747,8 @@ ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
  * ants_reconstruct_host_noalloc (32 MiB). */
 #define ANTS_NOALLOC_STAGE_BYTES 33554432
 
-/* The same reconstruction as ants_reconstruct_host, for callers that must not
- * allocate device memory.  The paper has no counterpart: this is a service of
+/* The plain contracting-grid search of ants_reconstruct_host, for callers
+ * that must not allocate device memory.  The paper has no counterpart: this is a service of
  * the library, not a step of the method.
  *
  * Who needs it: programs that hand all device memory to their own pool (or
@@ -760,8 +760,10 @@ ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
  * calls neither cudaMalloc nor cudaFree nor any allocating library routine.
  *
  * Arguments and results are those of ants_reconstruct_host (host buffers;
- * synchronous: returns when the outputs are in host memory).  Limits and
- * behaviour:
+ * synchronous: returns when the outputs are in host memory), restricted to
+ * method ANTS_CGS_PLAIN and FP32 signals: the other methods and FP16 signals
+ * return ANTS_E_UNIMPLEMENTED, because the two forms need scratch that
+ * grows with the batch.  Limits and behaviour:
  *   - The staging area holds ANTS_NOALLOC_STAGE_BYTES on every GPU that loads
  *     the library, until the process exits.
  *   - The whole batch must fit it: 4*n_events*n_sensors bytes of signals,
@@ -777,7 +779,7 @@ ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
  *     example from two host threads on the same device at once) race on the
  *     area: serialise them.
  * Errors: as ants_reconstruct_host (ANTS_E_ARG also for a batch beyond the
- * capacity). */
+ * capacity; ANTS_E_UNIMPLEMENTED for another method or signal type). */
 ANTS_API int ants_reconstruct_host_noalloc(ants_ctx *ctx, const ants_lrf *lrf, int method,
                                            const void *params, const void *signals_host,
                                            int signal_dtype, long n_events, int n_sensors,

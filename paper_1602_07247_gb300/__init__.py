@@ -1025,7 +1025,9 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
 
 def reconstruct_host_noalloc(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndarray, start_xyz=None,
                              method: int = ANTS_CGS_PLAIN) -> Result:
-    """As reconstruct_host, without any device allocation (static staging area)."""
+    """The plain search of reconstruct_host (FP32 signals) without any device
+    allocation: signals and results pass through the library's static staging
+    area, so the batch must fit it (ANTS_NOALLOC_STAGE_BYTES)."""
     n = int(signals.shape[0])
     xyz = np.empty((n, 3), dtype=np.float32)
     E = np.empty(n, dtype=np.float32)
