@@ -769,7 +769,8 @@ ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
  *   - The whole batch must fit it: 4*n_events*n_sensors bytes of signals,
  *     24*n_events bytes of results and, with start positions, 12*n_events
  *     more, each region rounded up to 256 bytes — about
- *     33,554,432 / (4*n_sensors + 24) events (119,837 for 64 sensors).
+ *     33,554,432 / (4*n_sensors + 24) events (119,835 for 64 sensors;
+ *     114,910 with start positions).
  *     Larger batches are rejected with ANTS_E_ARG before any copy.
  *   - The first call on a device looks up the area's device address with
  *     cudaGetSymbolAddress while that device is current; make that first
