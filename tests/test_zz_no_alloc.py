@@ -62,3 +62,30 @@ def test_noalloc_given_start_and_rejects_oversized_batch():
     with pytest.raises(ants.AntsError) as e:
         ants.reconstruct_host_noalloc(ctx, lrf, p, big)
     assert e.value.code == -1 and "capacity" in str(e.value)
+
+
+@pytest.mark.parametrize("with_start,cap", [(False, 119_835), (True, 114_910)])
+def test_noalloc_capacity_boundary(with_start, cap):
+    """The stated limit for 64 sensors is exact: every region of the area is
+    rounded up to 256 bytes, so a full batch fits and one more event does not."""
+    import torch
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    import paper_1602_07247_gb300 as ants
+    w = synth.workloads.get("sipm8x8_xy").with_(n_xy=5, iters=4, step_xy=0.5)
+    assert w.n_sensors == 64
+    L = oracle_lrf(w)
+    ctx, det, lrf, p = gpu_objects(w, L)
+    ev = w.events(cap + 1, seed=31)
+    start = None
+    if with_start:
+        start = np.ascontiguousarray(np.clip(ev.xyz, -23, 23), dtype=np.float32)
+        start[:, 2] = 0.0
+    sig = np.ascontiguousarray(ev.signals[:cap], dtype=np.float32)
+    st = None if start is None else start[:cap]
+    want = ants.reconstruct_host(ctx, lrf, p, sig, start_xyz=st)
+    got = ants.reconstruct_host_noalloc(ctx, lrf, p, sig, start_xyz=st)
+    _close(got, want)
+    with pytest.raises(ants.AntsError) as e:
+        ants.reconstruct_host_noalloc(ctx, lrf, p, np.ascontiguousarray(ev.signals, dtype=np.float32),
+                                      start_xyz=start)
+    assert e.value.code == -1 and "capacity" in str(e.value)
