@@ -28,31 +28,50 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "events/s of ML position reconstruction, plain CGS vs chosen form, same error"
-SM_COUNT = 152
-MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM
-FMA_PER_CLK_SM = 128  # FP32 fused multiply-adds per clock per SM
+SM_COUNT_NOMINAL = 152  # used only where no device can be queried
+MUFU_PER_CLK_SM = 16  # 32-bit log2 per clock per SM (nominal)
+FMA_PER_CLK_SM = 128  # FP32 fused multiply-adds per clock per SM (nominal)
 # canonical FP32 multiply-adds per (node, sensor) evaluation of each search:
 # B-spline tensor product, likelihood term and energy sum
 F_FMA = {"radial": 19, "xy": 22, "xyz": 86, "local": 9, "composite": 41, "axial_z": 25, "sliced": 46,
          "xy_minimize": 70}
 
 
-def alu_roofline(evals_per_s: float, kind: str) -> dict:
-    """Evaluation rate against min(FP32 FMA peak / F, log2 peak / 1)."""
+def sm_count() -> int:
+    """Streaming multiprocessors of the current CUDA device (queried)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    return SM_COUNT_NOMINAL
+
+
+def alu_roofline(evals_per_s: float, kind: str, verbose: bool = True) -> dict:
+    """Evaluation rate against min(FP32 FMA peak / F, log2 peak / 1): nominal
+    per-SM rates x the device's SM count x the measured maximum SM clock."""
     pk, pk_kind = peaks()
     clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    fma_ceiling = SM_COUNT * FMA_PER_CLK_SM * clk / F_FMA[kind]
-    log_ceiling = SM_COUNT * MUFU_PER_CLK_SM * clk
+    sms = sm_count()
+    fma_ceiling = sms * FMA_PER_CLK_SM * clk / F_FMA[kind]
+    log_ceiling = sms * MUFU_PER_CLK_SM * clk
     peak = min(fma_ceiling, log_ceiling)
-    return {"bound": "alu", "achieved": evals_per_s / 1e12, "peak": peak / 1e12, "unit": "Teval/s",
-            "frac": evals_per_s / peak, "frac_of_log2_peak": evals_per_s / log_ceiling,
-            "peak_kind": f"min({SM_COUNT} SMs x {FMA_PER_CLK_SM} FMA/clk x {clk / 1e6:.0f} MHz / {F_FMA[kind]} FMA "
-                         f"per evaluation, {SM_COUNT} x {MUFU_PER_CLK_SM} log2/clk x {clk / 1e6:.0f} MHz); "
-                         f"{pk_kind} max clock"}
+    out = {"bound": "alu", "achieved": evals_per_s / 1e12, "peak": peak / 1e12, "unit": "Teval/s",
+           "frac": evals_per_s / peak, "frac_of_log2_peak": evals_per_s / log_ceiling}
+    if verbose:
+        out["peak_kind"] = (f"nominal {FMA_PER_CLK_SM} FMA and {MUFU_PER_CLK_SM} log2 per clock per SM x {sms} SMs "
+                            f"(device) x {clk / 1e6:.0f} MHz ({pk_kind} max clock), F = {F_FMA[kind]} FMA per "
+                            f"evaluation")
+    return out
 # DRAM bytes (read + write) per event of the headline kernel, from one ncu
-# capture of it on 600 000 events of the same workload (156.07 MB read +
-# 9.98 MB written); None once the kernel changes.
-XY_TRAFFIC_PER_EVENT = (156.071680e6 + 9.976064e6) / 600_000
+# capture of it on 600 000 events of the same workload (156.29 MB read +
+# 9.54 MB written); None once the kernel changes.
+XY_TRAFFIC_PER_EVENT = (156294656 + 9539328) / 600_000
+# thread-instructions the headline kernel issues per (node, sensor)
+# evaluation (ncu smsp__thread_inst_executed.sum / evaluations of the same
+# capture: 1.2944e12 / (600 000 x 121 x 8 x 64)); None once the kernel changes
+XY_INST_PER_EVAL = 1294395613330 / (600_000 * 121 * 8 * 64)
 
 
 def peaks():
@@ -225,7 +244,10 @@ def forms_comparison(args, ants, torch, ctx, stream):
     src = ants.SimParams("square", 24.0, 0.0, 0.0, 0.0, 0.0, 2000.0, 0.05, 0.0)
     tsig, truth = ants.simulate(ctx, lrf, src, args.train_events, seed=2001)
     mlp = ants.Mlp.create(ctx, w.n_sensors, 256, 25.6, float(np.log(2000.0)), 0.05, seed=2001)
+    torch.cuda.synchronize()
+    t_tr = time.perf_counter()
     rep = mlp.train(tsig, truth, ants.TrainParams(epochs=20, batch=1024, bf16=1, seed=2001))
+    train_s = time.perf_counter() - t_tr  # the call is synchronous
     del tsig, truth
     csig, _ = ants.simulate(ctx, lrf, src, 20000, seed=2002)
     rc = ants.reconstruct(ctx, lrf, plain, csig)
@@ -317,12 +339,91 @@ def forms_comparison(args, ants, torch, ctx, stream):
         "achieved": flop / dt / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": flop / dt / 1e12 / peak,
         "ms": 1e3 * dt, "flop_per_event": 2 * 64 * 64 * w.n_sensors,
         "peak_kind": f"{pk_kind} bf16 burst (cuBLAS 8192^3)"}
+    del sc, ix, sig, sig16
+    out["vs_oracle_fp64"] = forms_vs_oracle(args, ants, torch, ctx, w, lrf, (
+        ("plain", ants.ANTS_CGS_PLAIN, plain), ("learned", ants.ANTS_MLP_SEEDED, sp),
+        ("precision", ants.ANTS_GEMM_TOPK, gp), ("minimize", ants.ANTS_MINIMIZE, mp)), stream)
     return {"workload": f"{w.name}: 256 sensors, XY LRF 32x32, {n} events; plain {w.n_xy}x{w.n_xy}x{w.iters} vs "
                         f"MLP 256-256-256-3 (BF16, trained on the GPU on {args.train_events} events, "
                         f"{rep.epochs_run} epochs) + refine 5x5x4 + fallback at the 99.5 % deviance quantile; precision form: "
                         f"FP16 signals, 64x64 BF16 log-response table, tcgen05 top-8, suppression 1.5 cells, "
                         f"refine 7x7x5; continuous minimisation from the centroid (at most 40 trials, tol 1e-3 mm)",
+            "training": {"events": args.train_events, "epochs": rep.epochs_run, "seconds": train_s,
+                         "events_epochs_per_s": args.train_events * rep.epochs_run / train_s,
+                         "best_monitor_mse": rep.best_monitor_mse,
+                         "products": "BF16 tcgen05 (hidden layers, forward, backward, weight gradients)"},
+            "short": f"{w.name}: 256 sensors, {n} events (same events for every form)",
             "setup_s": setup_s, "deviance_max": thr, **out}
+
+
+def forms_vs_oracle(args, ants, torch, ctx, w, lrf, forms, stream):
+    """Each form's position and energy error against the FP64 oracle's plain
+    contracting-grid search (same grid as the plain form) on a sample of
+    events drawn by the seeded numpy generator; the oracle's LRF is its own
+    FP64 fit of the same samples the library's LRF was fitted to."""
+    import oracle
+    n = args.oracle_events
+    ev = w.events(n, seed=4001)
+    pts, vals = w.fit_samples()
+    coef, _, _ = oracle.lrf_fit(w.n_int, w.lo, w.hi, pts, vals)
+    L = oracle.Lrf(oracle.XY, w.sensor_xy, w.n_int + (0,), w.lo + (0.0,), w.hi + (0.0,), coef)
+    P = oracle.CgsParams(n_xy=w.n_xy, iters=w.iters, step_xy=w.step_xy, shrink=w.shrink)
+    t0 = time.perf_counter()
+    ref = oracle.cgs(L, P, ev.signals.astype(np.float64), gain_cog=w.gains)
+    t_or = time.perf_counter() - t0
+    sig = torch.from_numpy(ev.signals).cuda()
+    sig16 = sig.half()
+    assert bool((sig16.float() == sig).all())  # counts below 2048: exact in FP16
+    out = {"events": n, "oracle": f"FP64 plain {w.n_xy}x{w.n_xy}x{w.iters} search, {oracle.num_threads()} threads, "
+                                  f"{t_or:.1f} s"}
+    ok_ref = ref["status"] == 0
+    for name, method, params in forms:
+        r = ants.reconstruct(ctx, lrf, params, sig16 if method == ants.ANTS_GEMM_TOPK else sig, method=method,
+                             stream=stream)
+        torch.cuda.synchronize()
+        xyz = r.xyz.double().cpu().numpy()
+        E = r.E.double().cpu().numpy()
+        ok = ok_ref & np.isfinite(xyz[:, 0]) & np.isfinite(E)
+        d = np.hypot(xyz[ok, 0] - ref["xyz"][ok, 0], xyz[ok, 1] - ref["xyz"][ok, 1])
+        dE = np.abs(E[ok] / ref["E"][ok] - 1.0)
+        out[name] = {"rms_dxy_mm": float(np.sqrt((d ** 2).mean())), "p95_dxy_mm": float(np.quantile(d, 0.95)),
+                     "max_dxy_mm": float(d.max()), "rms_dE_rel": float(np.sqrt((dE ** 2).mean())),
+                     "p95_dE_rel": float(np.quantile(dE, 0.95)), "compared": int(ok.sum())}
+    return out
+
+
+def _g(x, digits=4):
+    """x rounded to a few significant digits (compact JSON)."""
+    return None if x is None else float(f"{x:.{digits}g}")
+
+
+def forms_compact(f):
+    """The forms comparison reduced to the numbers the metric needs: events/s
+    of each form on the same events, RMS error against the truth, ratios to
+    the plain search (same error: RMS ratio <= 1.02), each form's error
+    against the FP64 oracle's plain search, and the tensor-core scan's
+    roofline."""
+    if f is None or "error" in f:
+        return f
+    c = {"workload": f["short"]}
+    for k in ("plain", "learned", "precision", "minimize"):
+        o = f[k]
+        d = {"events_per_s": _g(o["events_per_s"]), "rms_dxy_mm": _g(o["rms_dxy_mm"])}
+        if k != "plain":
+            d.update(speedup=_g(o["speedup_vs_plain"], 3), rms_ratio=_g(o["rms_ratio_vs_plain"]),
+                     same_error=bool(o["rms_ratio_vs_plain"] <= 1.02))
+        d["roofline_frac"] = _g(o["roofline"]["frac"], 3)
+        c[k] = d
+    c["learned"]["fallback_frac"] = _g(f["learned"]["fallback_frac"], 3)
+    c["learned"]["train_s"] = _g(f["training"]["seconds"], 3)
+    sr = f["precision"]["scan_roofline"]
+    c["precision"]["scan"] = {"tflops": _g(sr["achieved"]), "frac": _g(sr["frac"], 3), "ms": _g(sr["ms"])}
+    vo = f["vs_oracle_fp64"]
+    c["vs_oracle_fp64"] = {"events": vo["events"], **{
+        k: {"rms_dxy_mm": _g(v["rms_dxy_mm"], 3), "p95_dxy_mm": _g(v["p95_dxy_mm"], 3),
+            "rms_dE_rel": _g(v["rms_dE_rel"], 3)} for k, v in vo.items() if isinstance(v, dict)}}
+    c["chosen"] = "learned"
+    return c
 
 
 def radial_run(args, ants, torch, ctx, stream):
@@ -817,7 +918,8 @@ def run_ours(args):
         return 0
     evals = n * w.iters * w.n_xy * w.n_xy * w.n_sensors
     traffic = None if XY_TRAFFIC_PER_EVENT is None else XY_TRAFFIC_PER_EVENT * n
-    roofline = {**alu_roofline(evals / kernel_s, "xy"), "traffic": traffic, "traffic_unit": "bytes per launch"}
+    roofline = {**alu_roofline(evals / kernel_s, "xy"), "traffic": traffic, "traffic_unit": "bytes per launch",
+                "thread_inst_per_eval": XY_INST_PER_EVAL}
     cpu = None
     if not args.no_cpu_baseline:
         rate, secs, cores, _ = cpu_oracle_rate(w, args.cpu_events, seed=w.event_seed)
@@ -835,22 +937,30 @@ def run_ours(args):
         except Exception as exc:  # the headline line must still be printed
             return {"error": f"{type(exc).__name__}: {exc}"}
 
-    radial = optional(radial_run, args.no_forms)
-    forms = optional(forms_comparison, args.no_forms)
-    batched = optional(batched_run, args.no_batched)
-    iterative = optional(iterative_run, args.no_iterative)
-    variants = optional(variants_run, args.no_variants)
-    schemes = optional(schemes_run, args.no_schemes)
-    minim = optional(minimize_run, args.no_minimize)
-    optics = optional(optics_run, args.no_optics)
+    # every optional section is printed as a line of its own (key "section"),
+    # before the headline, which is the last line and carries the forms
+    # comparison in compact form
+    forms = None
+    for name, fn, skip in (("forms_16x16", forms_comparison, args.no_forms),
+                           ("radial_hex19", radial_run, args.no_forms),
+                           ("batched_3d", batched_run, args.no_batched),
+                           ("iterative_lrf", iterative_run, args.no_iterative),
+                           ("variants_8x8", variants_run, args.no_variants),
+                           ("lrf_schemes_4x4", schemes_run, args.no_schemes),
+                           ("minimize_8x8", minimize_run, args.no_minimize),
+                           ("optics_4x4", optics_run, args.no_optics)):
+        r = optional(fn, skip)
+        if r is None:
+            continue
+        if name == "forms_16x16":
+            forms = r
+        print(json.dumps({"section": name, **r}), flush=True)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(w, n),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-        "rms_dxy_mm": rms, "radial_hex19": radial, "forms_16x16": forms, "batched_3d": batched,
-        "iterative_lrf": iterative, "variants_8x8": variants, "lrf_schemes_4x4": schemes,
-        "minimize_8x8": minim, "optics_4x4": optics,
+        "rms_dxy_mm": rms, "forms": forms_compact(forms),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -874,6 +984,8 @@ def main():
     ap.add_argument("--forms-events", type=int, default=4_000_000)
     ap.add_argument("--forms-steps", type=int, default=3)
     ap.add_argument("--train-events", type=int, default=1_000_000)
+    ap.add_argument("--oracle-events", type=int, default=20_000,
+                    help="events of the forms' comparison with the FP64 oracle's plain search")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-detector 3D batched run")
     ap.add_argument("--no-iterative", action="store_true", help="skip the iterative LRF reconstruction")
     ap.add_argument("--no-variants", action="store_true", help="skip the search variants")

@@ -764,17 +764,24 @@ ANTS_API int ants_mlp_load(ants_ctx *ctx, const char *path, ants_mlp **out);
  * method ANTS_CGS_PLAIN and FP32 signals: the other methods and FP16 signals
  * return ANTS_E_UNIMPLEMENTED, because the two forms need scratch that
  * grows with the batch.  Limits and behaviour:
- *   - The staging area holds ANTS_NOALLOC_STAGE_BYTES on every GPU that loads
- *     the library, until the process exits.
+ *   - The staging area takes ANTS_NOALLOC_STAGE_BYTES of device memory on
+ *     each GPU from the moment its module is loaded there until the process
+ *     exits.  Under CUDA's default lazy module loading that is the first
+ *     call of this entry point on the device (eager loading reserves it when
+ *     the context is created).  A call with n_events = 0 (buffers may be
+ *     NULL) does this set-up and nothing else: a caller that hands the rest
+ *     of device memory to its own pool makes that call first.
  *   - The whole batch must fit it: 4*n_events*n_sensors bytes of signals,
  *     24*n_events bytes of results and, with start positions, 12*n_events
  *     more, each region rounded up to 256 bytes — about
  *     33,554,432 / (4*n_sensors + 24) events (119,835 for 64 sensors;
  *     114,910 with start positions).
  *     Larger batches are rejected with ANTS_E_ARG before any copy.
- *   - The first call on a device looks up the area's device address with
- *     cudaGetSymbolAddress while that device is current; make that first
- *     call before any stream capture begins.
+ *   - The first call on a device (with any n_events) looks up the area's
+ *     device address with cudaGetSymbolAddress while that device is current
+ *     and keeps it for the life of the process; make that first call before
+ *     any stream capture begins.  A device reset (cudaDeviceReset) after
+ *     that call is not supported: the kept address would be stale.
  *   - Every call uses the same area and leaves the last call's data in it;
  *     nothing in it has to start at zero.  Calls that overlap on the GPU (for
  *     example from two host threads on the same device at once) race on the

@@ -23,6 +23,8 @@ LIB_PATH = _build.LIB
 
 # enums of include/ants.h
 ANTS_OK = 0
+ANTS_E_ARG, ANTS_E_CUDA, ANTS_E_OOM, ANTS_E_LRF, ANTS_E_SHAPE = -1, -2, -3, -4, -5
+ANTS_E_TIMEOUT, ANTS_E_INTERNAL, ANTS_E_UNIMPLEMENTED, ANTS_E_IO = -6, -7, -8, -9
 ANTS_LRF_RADIAL, ANTS_LRF_XY, ANTS_LRF_XYZ = 1, 2, 3
 ANTS_LRF_COMPOSITE, ANTS_LRF_AXIAL_Z, ANTS_LRF_SLICED = 4, 5, 6
 ANTS_EVT_OK, ANTS_EVT_FALLBACK, ANTS_EVT_ZERO_SIGNAL = 0, 1, 2
@@ -318,6 +320,39 @@ def _tptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _dtype_name(a) -> str:
+    return str(a.dtype).replace("torch.", "")
+
+
+def _check_signals(signals, signal_dtype: int) -> None:
+    """The signal buffer's element type must be the one signal_dtype names
+    (float32 for ANTS_F32, float16 for ANTS_F16): the library reads
+    n_events x n_sensors elements of that size from it."""
+    want = {ANTS_F32: "float32", ANTS_F16: "float16"}.get(signal_dtype)
+    if want is not None and _dtype_name(signals) != want:
+        raise TypeError(f"signals are {_dtype_name(signals)}, signal_dtype {signal_dtype} needs {want}")
+
+
+def _check_start(start_xyz, n: int) -> None:
+    """Start positions, when given: float32 [n_events, 3]."""
+    if start_xyz is None:
+        return
+    if _dtype_name(start_xyz) != "float32":
+        raise TypeError(f"start_xyz is {_dtype_name(start_xyz)}, needs float32")
+    if tuple(start_xyz.shape) != (n, 3):
+        raise ValueError(f"start_xyz has shape {tuple(start_xyz.shape)}, needs ({n}, 3)")
+
+
+def _signal_dtype_of(signals) -> int:
+    """ANTS_F16 for float16 signals, ANTS_F32 for float32; anything else is refused."""
+    name = _dtype_name(signals)
+    if name == "float16":
+        return ANTS_F16
+    if name == "float32":
+        return ANTS_F32
+    raise TypeError(f"signals must be float32 or float16, not {name}")
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         import torch
@@ -498,6 +533,8 @@ def ants_lrf_free(lrf: int) -> None:
 
 def ants_reconstruct(ctx: int, lrf: int, method: int, params, signals, n_sensors: int, xyz, E, logL, status,
                      start_xyz=None, trace=None, stream=None, signal_dtype: int = ANTS_F32) -> None:
+    _check_signals(signals, signal_dtype)
+    _check_start(start_xyz, int(signals.shape[0]))
     _check(lib().ants_reconstruct(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                   int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz), _tptr(E),
                                   _tptr(logL), _tptr(status), _tptr(trace), _stream_handle(stream)))
@@ -505,6 +542,8 @@ def ants_reconstruct(ctx: int, lrf: int, method: int, params, signals, n_sensors
 
 def ants_reconstruct_host(ctx: int, lrf: int, method: int, params, signals, n_sensors: int, xyz, E, logL,
                           status, start_xyz=None, signal_dtype: int = ANTS_F32) -> None:
+    _check_signals(signals, signal_dtype)
+    _check_start(start_xyz, int(signals.shape[0]))
     _check(lib().ants_reconstruct_host(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                        int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
                                        _tptr(E), _tptr(logL), _tptr(status)))
@@ -514,6 +553,8 @@ def ants_reconstruct_host_noalloc(ctx: int, lrf: int, method: int, params, signa
                                   status, start_xyz=None, signal_dtype: int = ANTS_F32) -> None:
     """Host-buffer reconstruction through the library's static staging area
     (no device allocation; batch limited by ANTS_NOALLOC_STAGE_BYTES)."""
+    _check_signals(signals, signal_dtype)
+    _check_start(start_xyz, int(signals.shape[0]))
     _check(lib().ants_reconstruct_host_noalloc(ctx, lrf, method, C.addressof(params), _tptr(signals), signal_dtype,
                                                int(signals.shape[0]), int(n_sensors), _tptr(start_xyz), _tptr(xyz),
                                                _tptr(E), _tptr(logL), _tptr(status)))
@@ -1017,7 +1058,7 @@ def reconstruct(ctx: Context, lrf: Lrf, params: CgsParams, signals, start_xyz=No
              else 1 if isinstance(params, MinimizeParams) else params.iters)
     trace = torch.empty((n, iters), dtype=torch.int16, device=dev) if want_trace else None
     n_s = int(signals.shape[1]) if signals.dim() == 2 else -1
-    dtype = ANTS_F16 if signals.dtype == torch.float16 else ANTS_F32
+    dtype = _signal_dtype_of(signals)
     ants_reconstruct(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
                      start_xyz=start_xyz, trace=trace, stream=stream, signal_dtype=dtype)
     return Result(xyz, E, logL, status, trace)
@@ -1034,6 +1075,8 @@ def reconstruct_host_noalloc(ctx: Context, lrf: Lrf, params: CgsParams, signals:
     logL = np.empty(n, dtype=np.float32)
     status = np.empty(n, dtype=np.int32)
     n_s = int(signals.shape[1]) if signals.ndim == 2 else -1
+    if _signal_dtype_of(signals) != ANTS_F32:
+        raise TypeError("reconstruct_host_noalloc reads float32 signals only")
     ants_reconstruct_host_noalloc(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
                                   start_xyz=start_xyz)
     return Result(xyz, E, logL, status)
@@ -1048,7 +1091,7 @@ def reconstruct_host(ctx: Context, lrf: Lrf, params: CgsParams, signals: np.ndar
     logL = np.empty(n, dtype=np.float32)
     status = np.empty(n, dtype=np.int32)
     n_s = int(signals.shape[1]) if signals.ndim == 2 else -1
-    dtype = ANTS_F16 if str(signals.dtype) in ("float16", "torch.float16") else ANTS_F32
+    dtype = _signal_dtype_of(signals)
     ants_reconstruct_host(ctx.handle, lrf.handle, method, params, signals, n_s, xyz, E, logL, status,
                           start_xyz=start_xyz, signal_dtype=dtype)
     return Result(xyz, E, logL, status)

@@ -18,9 +18,19 @@
 //   acc += s log2(eta / eta_c),  dH += eta - eta_c,
 // and F = acc - S log2(1 + dH / H_c) is the Poisson log-likelihood with the
 // energy E = S/H profiled out (Sec. 5.1.2.2), up to a per-event constant.
+// On grids narrower than half a knot interval the nodes' scores differ by
+// less than the error of the hardware log2 near 1 (about 2^-22 absolute per
+// term) plus the rounding of eta/eta_c to single precision; there the term is
+// log2(1 + u) with u = fma(eta, 1/eta_c, -1) (one rounding of the small
+// difference) and a degree-6 Taylor polynomial, exact to 1e-9 for |u| <= 1/16
+// (larger |u| falls back to the hardware log2).  The rounding of 1/eta_c
+// shifts every node of a grid by the same s log2(1 + d) and cancels in the
+// argmax.
 // Lanes store per-(node, slot) partial sums in shared memory; one thread per
 // node adds the slots, and a team argmax (ties to the lowest flat index)
 // picks the next centre.
+#include <type_traits>
+
 #include "bspline.cuh"
 #include "internal.cuh"
 
@@ -38,6 +48,7 @@ struct XyArgs {
     LrfDev L;
     int iters;
     float shrink, step_xy;
+    float prec_halfwidth;  // grids whose half-width is at most this use the accurate log
     const float *sig;
     long n_e;
     int row_div;      // event e reads signal row e / row_div ...
@@ -63,6 +74,24 @@ __device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
         return v;
     }
     return __ldg(gptr);
+}
+
+// log2(1 + u) for both lanes of a pair: Taylor series sum_k (-1)^(k+1) u^k /
+// (k ln 2) to degree 6 (truncation below 8e-10 for |u| <= 1/16), the hardware
+// log2 of 1 + u beyond that
+constexpr float kNearOne = 0.0625f;
+__device__ __forceinline__ float2 log2_1p_pair(float2 u)
+{
+    float2 p = ffma2(u, make_float2(-0.24044917348149393f, -0.24044917348149393f),
+                     make_float2(0.28853900817779268f, 0.28853900817779268f));
+    p = ffma2(p, u, make_float2(-0.36067376022224085f, -0.36067376022224085f));
+    p = ffma2(p, u, make_float2(0.48089834696298783f, 0.48089834696298783f));
+    p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
+    p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
+    p = fmul2(p, u);
+    if (fabsf(u.x) > kNearOne) p.x = __log2f(1.0f + u.x);
+    if (fabsf(u.y) > kNearOne) p.y = __log2f(1.0f + u.y);
+    return p;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -311,110 +340,123 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             const int ps = lay.part_stride;
             const int sy = L.stride_y;
             const unsigned rowb = (unsigned)sy * 8u;  // bytes per table row
-            for (int g = 0; g < group_end; g += kPPL) {
-                const float2 *gb[kPPL];
-                unsigned sb[kPPL];
-                float2 sp[kPPL], ic[kPPL], nec[kPPL];
-                bool on[kPPL];
-#pragma unroll
-                for (int m = 0; m < kPPL; ++m) {
-                    on[m] = g + m < pairs_mine;
-                    const int p = on[m] ? q + (g + m) * Q : 0;  // any valid pair when missing
-                    gb[m] = coef2 + (size_t)p * L.pair_stride + ix;
-                    sb[m] = SMEM ? (unsigned)__cvta_generic_to_shared(gb[m]) : 0u;
-                    sp[m] = on[m] ? s_sig2[p] : make_float2(0.0f, 0.0f);
-                    ic[m] = s_ic2[p];
-                    nec[m] = s_ec2[p];
-                }
-                float2 W[kPPL][4];
-                int top = s_iy[0];
-#pragma unroll
-                for (int m = 0; m < kPPL; ++m)
-#pragma unroll
-                    for (int a4 = 0; a4 < 4; ++a4)
-                        W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2);
-#pragma unroll 1
-                for (int k = 0; k < N; ++k) {
-                    const int iyk = s_iy[k];
-                    const int adv = iyk - top;
-                    const int r4 = top + 4;  // first row not yet in the window
-                    if (adv == 1) {
-#pragma unroll
-                        for (int m = 0; m < kPPL; ++m) {
-                            W[m][0] = W[m][1];
-                            W[m][1] = W[m][2];
-                            W[m][2] = W[m][3];
-                            W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
-                        }
-                    } else if (adv == 2) {
-#pragma unroll
-                        for (int m = 0; m < kPPL; ++m) {
-                            W[m][0] = W[m][2];
-                            W[m][1] = W[m][3];
-                            W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
-                            W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
-                        }
-                    } else if (adv == 3) {
-#pragma unroll
-                        for (int m = 0; m < kPPL; ++m) {
-                            W[m][0] = W[m][3];
-                            W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
-                            W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
-                            W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2);
-                        }
-                    } else if (adv >= 4) {
-#pragma unroll
-                        for (int m = 0; m < kPPL; ++m)
-#pragma unroll
-                            for (int a4 = 0; a4 < 4; ++a4)
-                                W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
-                                                      wx2);
-                    }
-                    top = iyk;
-                    const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
-                    const float2 w0 = make_float2(wa.x, wa.y), w1 = make_float2(wa.z, wa.w);
-                    const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
-                    float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
-#pragma unroll
+            // the sweep is compiled twice, with the hardware log2 of eta/eta_c
+            // and with the accurate log2(1 + u); the choice is uniform per grid
+            auto sweep = [&](auto accurate) {
+                constexpr bool ACC = decltype(accurate)::value;
+                for (int g = 0; g < group_end; g += kPPL) {
+                    const float2 *gb[kPPL];
+                    unsigned sb[kPPL];
+                    float2 sp[kPPL], ic[kPPL], nec[kPPL];
+                    bool on[kPPL];
+    #pragma unroll
                     for (int m = 0; m < kPPL; ++m) {
-                        float2 eta = fmul2(w0, W[m][0]);
-                        eta = ffma2(w1, W[m][1], eta);
-                        eta = ffma2(w2, W[m][2], eta);
-                        eta = ffma2(w3, W[m][3], eta);
-                        if (FLOOR) {
-                            eta.x = fmaxf(eta.x, kEtaFloor);
-                            eta.y = fmaxf(eta.y, kEtaFloor);
-                        }
-                        const float2 r = fmul2(eta, ic[m]);
-                        acc = ffma2(sp[m], make_float2(__log2f(r.x), __log2f(r.y)), acc);
-                        if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
+                        on[m] = g + m < pairs_mine;
+                        const int p = on[m] ? q + (g + m) * Q : 0;  // any valid pair when missing
+                        gb[m] = coef2 + (size_t)p * L.pair_stride + ix;
+                        sb[m] = SMEM ? (unsigned)__cvta_generic_to_shared(gb[m]) : 0u;
+                        sp[m] = on[m] ? s_sig2[p] : make_float2(0.0f, 0.0f);
+                        ic[m] = s_ic2[p];
+                        nec[m] = s_ec2[p];
                     }
-                    float va = acc.x + acc.y, vd = dh.x + dh.y;
-                    if (TEAM > 1) {
-                        // lanes l, l+N, l+2N, ... of a warp share grid column j:
-                        // lane l < N adds the lanes' own values
-                        const float a0 = va, d0 = vd;
-#pragma unroll
-                        for (int o = N; o < 32; o += N) {
-                            const float xa = __shfl_down_sync(kFull, a0, o), xd = __shfl_down_sync(kFull, d0, o);
-                            if (lane + o < 32) {
-                                va += xa;
-                                vd += xd;
+                    float2 W[kPPL][4];
+                    int top = s_iy[0];
+    #pragma unroll
+                    for (int m = 0; m < kPPL; ++m)
+    #pragma unroll
+                        for (int a4 = 0; a4 < 4; ++a4)
+                            W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2);
+    #pragma unroll 1
+                    for (int k = 0; k < N; ++k) {
+                        const int iyk = s_iy[k];
+                        const int adv = iyk - top;
+                        const int r4 = top + 4;  // first row not yet in the window
+                        if (adv == 1) {
+    #pragma unroll
+                            for (int m = 0; m < kPPL; ++m) {
+                                W[m][0] = W[m][1];
+                                W[m][1] = W[m][2];
+                                W[m][2] = W[m][3];
+                                W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                            }
+                        } else if (adv == 2) {
+    #pragma unroll
+                            for (int m = 0; m < kPPL; ++m) {
+                                W[m][0] = W[m][2];
+                                W[m][1] = W[m][3];
+                                W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
+                            }
+                        } else if (adv == 3) {
+    #pragma unroll
+                            for (int m = 0; m < kPPL; ++m) {
+                                W[m][0] = W[m][3];
+                                W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                                W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
+                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2);
+                            }
+                        } else if (adv >= 4) {
+    #pragma unroll
+                            for (int m = 0; m < kPPL; ++m)
+    #pragma unroll
+                                for (int a4 = 0; a4 < 4; ++a4)
+                                    W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
+                                                          wx2);
+                        }
+                        top = iyk;
+                        const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
+                        const float2 w0 = make_float2(wa.x, wa.y), w1 = make_float2(wa.z, wa.w);
+                        const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
+                        float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
+    #pragma unroll
+                        for (int m = 0; m < kPPL; ++m) {
+                            float2 eta = fmul2(w0, W[m][0]);
+                            eta = ffma2(w1, W[m][1], eta);
+                            eta = ffma2(w2, W[m][2], eta);
+                            eta = ffma2(w3, W[m][3], eta);
+                            if (FLOOR) {
+                                eta.x = fmaxf(eta.x, kEtaFloor);
+                                eta.y = fmaxf(eta.y, kEtaFloor);
+                            }
+                            float2 lg;
+                            if (ACC) {
+                                lg = log2_1p_pair(ffma2(eta, ic[m], make_float2(-1.0f, -1.0f)));
+                            } else {
+                                const float2 r = fmul2(eta, ic[m]);
+                                lg = make_float2(__log2f(r.x), __log2f(r.y));
+                            }
+                            acc = ffma2(sp[m], lg, acc);
+                            if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
+                        }
+                        float va = acc.x + acc.y, vd = dh.x + dh.y;
+                        if (TEAM > 1) {
+                            // lanes l, l+N, l+2N, ... of a warp share grid column j:
+                            // lane l < N adds the lanes' own values
+                            const float a0 = va, d0 = vd;
+    #pragma unroll
+                            for (int o = N; o < 32; o += N) {
+                                const float xa = __shfl_down_sync(kFull, a0, o), xd = __shfl_down_sync(kFull, d0, o);
+                                if (lane + o < 32) {
+                                    va += xa;
+                                    vd += xd;
+                                }
                             }
                         }
-                    }
-                    if (TEAM == 1 || lane < N) {
-                        const int slot = TEAM > 1 ? wit * N + j : t;
-                        float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
-                        if (g > 0) {
-                            va += *pa;
-                            vd += *pd;
+                        if (TEAM == 1 || lane < N) {
+                            const int slot = TEAM > 1 ? wit * N + j : t;
+                            float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
+                            if (g > 0) {
+                                va += *pa;
+                                vd += *pd;
+                            }
+                            *pa = va;
+                            *pd = vd;
                         }
-                        *pa = va;
-                        *pd = vd;
                     }
                 }
-            }
+            };
+            if (sxy * (float)C <= a.prec_halfwidth) sweep(std::true_type{});
+            else sweep(std::false_type{});
             team_sync<TEAM>(team);
 
             // ---- phase 3: node scores and team argmax --------------------------
@@ -581,6 +623,9 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     a.iters = p.iters;
     a.shrink = p.shrink;
     a.step_xy = p.step_xy;
+    // half a knot interval (the smaller axis): on such grids the LRF changes
+    // by a few per cent at most between a node and the centre
+    a.prec_halfwidth = 0.5f * fminf(1.0f / lrf->dev.inv_h[0], 1.0f / lrf->dev.inv_h[1]);
     a.sig = sig;
     a.n_e = n_e;
     a.start = start;

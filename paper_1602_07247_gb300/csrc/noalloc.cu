@@ -5,7 +5,9 @@
 // The staging area is a file-scope __device__ array.  Host code cannot use
 // its name as a device address, so the first call on each device looks the
 // address up with cudaGetSymbolAddress (with that device current) and keeps
-// it; every later call on that device reuses it.
+// it; every later call on that device reuses it.  With lazy module loading
+// (the CUDA default) that lookup is also what loads this file's module and so
+// reserves the area on the device; a call with n_events = 0 does only that.
 #include <mutex>
 
 #include "internal.cuh"
@@ -102,13 +104,13 @@ extern "C" ANTS_API int ants_reconstruct_host_noalloc(ants_ctx *ctx, const ants_
                     "ants_reconstruct_host_noalloc: %ld events exceed the static staging capacity of %ld events "
                     "for %d sensors (%zu bytes)",
                     n_events, cap, n_sensors, kStageBytes);
-    if (n_events == 0) return ANTS_OK;
-    if (!signals_host || !xyz_host || !E_host || !logL_host || !status_host)
+    if (n_events > 0 && (!signals_host || !xyz_host || !E_host || !logL_host || !status_host))
         return fail(ANTS_E_ARG, "ants_reconstruct_host_noalloc: NULL signal or output buffer");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     unsigned char *base = nullptr;
-    rc = stage_address(ctx->device, &base);
+    rc = stage_address(ctx->device, &base);  // set-up on the first call, also with n_events = 0
     if (rc != ANTS_OK) return rc;
+    if (n_events == 0) return ANTS_OK;
 
     // carve the staging area; nothing in it has to start at zero (every region
     // is written before it is read)

@@ -39,21 +39,43 @@ def random_net(ants, ctx, n_in, H, seed):
     return M, oracle.Mlp(*unpack(M.params(), n_in, H))
 
 
-def test_forward_matches_oracle(env):
+def bf16_forward_bound(parts, sig):
+    """First-order bound on the output error of the BF16 mode: every product
+    operand is rounded to BF16 (unit roundoff u = 2^-9), so each layer adds
+    2u |W| |x| and passes the error of its input on through |W| (and GELU,
+    whose slope is below 1.13).  Magnitudes from an FP64 pass in numpy."""
+    from scipy.special import erf
+    W1, b1, W2, b2, W3, b3 = parts
+    u = 2.0 ** -9
+    U = sig / sig.sum(1, keepdims=True)
+    gelu = lambda x: 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
+    H1 = gelu(U @ W1.T + b1)
+    H2 = gelu(H1 @ W2.T + b2)
+    e1 = 2 * u * (np.abs(U) @ np.abs(W1).T)
+    e2 = 2 * u * (np.abs(H1) @ np.abs(W2).T) + (1.13 * e1) @ np.abs(W2).T
+    return 2 * u * (np.abs(H2) @ np.abs(W3).T) + (1.13 * e2) @ np.abs(W3).T
+
+
+@pytest.mark.parametrize("name,n_in,H", [("sipm8x8_xy", 64, 96), ("sipm16x16_xy", 256, 256)])
+def test_forward_matches_oracle(env, name, n_in, H):
+    """Every output element: FP32 mode within 1e-5 of the oracle (relative,
+    floored at the output's RMS); BF16 mode within twice the first-order
+    rounding bound.  Also at the production width 256 -> 256 -> 256 -> 3."""
     torch, ants, ctx = env
-    M, ref = random_net(ants, ctx, 64, 96, 3)
-    sig = synth.workloads.get("sipm8x8_xy").events(777, seed=4).signals
+    M, ref = random_net(ants, ctx, n_in, H, 3)
+    sig = synth.workloads.get(name).events(777, seed=4).signals
     want = oracle.mlp_forward(ref, sig.astype(np.float64))
     s = torch.from_numpy(sig).cuda()
     out32 = torch.empty((777, 3), device="cuda")
     ants.ants_mlp_forward(ctx.handle, M.handle, s, out32, bf16=0)
     out16 = torch.empty((777, 3), device="cuda")
     ants.ants_mlp_forward(ctx.handle, M.handle, s, out16, bf16=1)
-    scale = np.abs(want).max()
-    e32 = np.abs(out32.cpu().numpy() - want).max() / scale
-    e16 = np.abs(out16.cpu().numpy() - want).max() / scale
-    print("forward rel err fp32", e32, "bf16", e16)
-    assert e32 < 1e-5 and e16 < 3e-2
+    floor = np.sqrt((want ** 2).mean(0))
+    e32 = (np.abs(out32.cpu().numpy() - want) / np.maximum(np.abs(want), floor)).max()
+    bound = bf16_forward_bound(unpack(M.params(), n_in, H), sig.astype(np.float64))
+    e16 = (np.abs(out16.cpu().numpy() - want) / (2.0 * bound + 1e-7)).max()
+    print("forward per element: fp32 rel", e32, "bf16 / bound", e16)
+    assert e32 < 1e-5 and e16 <= 1.0
 
 
 def test_forward_unaligned_widths(env):
@@ -72,10 +94,14 @@ def test_forward_unaligned_widths(env):
 
 
 @pytest.mark.parametrize("bf16,tol", [(0, 1e-4), (1, 3e-2)])
-def test_gradients_match_oracle(env, bf16, tol):
+@pytest.mark.parametrize("name,n_in,H", [("sipm8x8_xy", 64, 96), ("sipm16x16_xy", 256, 256)])
+def test_gradients_match_oracle(env, bf16, tol, name, n_in, H):
+    """Every gradient element against the FP64 oracle's back-propagation:
+    |g_gpu - g| <= tol * max(|g|, RMS of that tensor's g), tol 1e-4 in FP32
+    and 3e-2 in BF16 mode; at 64 -> 96 and at the production 256 -> 256."""
     torch, ants, ctx = env
-    M, ref = random_net(ants, ctx, 64, 96, 5)
-    w = synth.workloads.get("sipm8x8_xy")
+    M, ref = random_net(ants, ctx, n_in, H, 5)
+    w = synth.workloads.get(name)
     ev = w.events(300, seed=6)
     truth = np.concatenate([ev.xyz, ev.energy[:, None]], axis=1).astype(np.float32)
     tgt = np.stack([truth[:, 0] / 24.0, truth[:, 1] / 24.0, (np.log(truth[:, 3]) - np.log(3000.0)) / 0.05], axis=1)
@@ -83,10 +109,11 @@ def test_gradients_match_oracle(env, bf16, tol):
     loss_g, g_flat = ants.ants_mlp_loss_grad(ctx.handle, M.handle, torch.from_numpy(ev.signals).cuda(),
                                              torch.from_numpy(truth).cuda(), bf16=bf16)
     assert abs(loss_g / loss_o - 1.0) < tol
-    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), unpack(g_flat, 64, 96), g_o):
-        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        print(bf16, name, rel)
-        assert rel < tol, (name, rel)
+    for pname, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), unpack(g_flat, n_in, H), g_o):
+        floor = np.sqrt((b ** 2).mean())
+        rel = (np.abs(a - b) / np.maximum(np.abs(b), floor)).max()
+        print(bf16, pname, rel)
+        assert rel < tol, (pname, rel)
 
 
 def train_small(ants, ctx, torch, seed=2001, n=24000, epochs=4):
