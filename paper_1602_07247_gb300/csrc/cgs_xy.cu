@@ -78,7 +78,7 @@ __device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
 
 // log2(1 + u) for both lanes of a pair: Taylor series sum_k (-1)^(k+1) u^k /
 // (k ln 2) to degree 6 (truncation below 8e-10 for |u| <= 1/16), the hardware
-// log2 of 1 + u beyond that
+// log2 of 1 + u beyond that; every lane of the warp calls it together
 constexpr float kNearOne = 0.0625f;
 __device__ __forceinline__ float2 log2_1p_pair(float2 u)
 {
@@ -89,8 +89,11 @@ __device__ __forceinline__ float2 log2_1p_pair(float2 u)
     p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
     p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
     p = fmul2(p, u);
-    if (fabsf(u.x) > kNearOne) p.x = __log2f(1.0f + u.x);
-    if (fabsf(u.y) > kNearOne) p.y = __log2f(1.0f + u.y);
+    // a warp-uniform branch: the hardware log2 is issued only when a lane needs it
+    if (__any_sync(kFull, fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne)) {
+        if (fabsf(u.x) > kNearOne) p.x = __log2f(1.0f + u.x);
+        if (fabsf(u.y) > kNearOne) p.y = __log2f(1.0f + u.y);
+    }
     return p;
 }
 

@@ -214,6 +214,16 @@ int mma_topk(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16
              int K, int topk, float *val, int *idx, cudaStream_t s);
 int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const float *bias, int M,
                   int N, int K, __nv_bfloat16 *out, cudaStream_t s);
+// training products of the network with BF16 operands (umma.cu):
+// z = A W^T + b (FP32), h = GELU(z) (BF16), hT = h transposed [N][ldT] (nullable)
+int mma_train_forward(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *W, const float *bias,
+                      int M, int N, int K, float *z, __nv_bfloat16 *h, __nv_bfloat16 *hT, int ldT, cudaStream_t s);
+// dz = (dY Wt^T) GELU'(z) (FP32) and dzT = dz transposed in BF16 [N][ldT] (nullable)
+int mma_gelu_backward(const ants_ctx *ctx, const float *dY, const __nv_bfloat16 *Wt, const float *z, int M, int N,
+                      int K, float *dz, __nv_bfloat16 *dzT, int ldT, cudaStream_t s);
+// C = A B^T in FP32, A [M][K] and B [N][K] BF16 (any K with N <= 256)
+int mma_f32(const ants_ctx *ctx, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, float *C,
+            cudaStream_t s);
 // precision form (precision.cu)
 int check_gemm_params(const ants_lrf *lrf, const ants_gemm_params *P);
 int reconstruct_gemm_topk(ants_ctx *ctx, const ants_lrf *lrf, const ants_gemm_params &P, const float *sig, long n,

@@ -10,9 +10,16 @@
 // every matrix-product operand is rounded to BF16 and products accumulate in
 // FP32 (mixed precision); with bf16 = 0 everything is FP32.
 //
-// Matrix products use one tiled kernel (64 x 64 output tile per block, 4 x 4
-// per thread, K staged through shared memory in steps of 16); all sums are
-// taken in a fixed order, so training is bitwise reproducible.
+// With bf16 = 1 and input and hidden widths that are multiples of 8 and at
+// most 256, every product of the hidden layers runs on the tensor cores
+// (tcgen05, umma.cu): the forward products with bias and GELU fused (z kept
+// for the backward pass), the backward product dZ1 = (dZ2 W2) GELU'(z1)
+// fused likewise, and the weight gradients dW = dZ^T X with the batch as the
+// contraction (from transposed BF16 copies the epilogues write).  The 3-wide
+// output layer and its gradients, and the FP32 mode, use the tiled SIMT kernel
+// below (64 x 64 output tile per block, 4 x 4 per thread, K staged through
+// shared memory in steps of 16).  All sums are taken in a fixed order, so
+// training is bitwise reproducible.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,6 +47,7 @@ struct ants_mlp {
     __nv_bfloat16 *d_w1b = nullptr, *d_w2b = nullptr;
     float *d_bpad = nullptr;  // b1 [Hp], b2 [Hp]
     bool bf16_stale = true;
+    __nv_bfloat16 *d_w2tb = nullptr;  // W2 transposed [H][H] (tensor-core training only)
 };
 
 namespace ants {
@@ -211,14 +219,27 @@ __global__ void mse_grad(const float *__restrict__ O, const float *__restrict__ 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// out[j] = sum_r X[r][j] (fixed order over rows)
+// out[j] = sum_r X[r][j]: block (32, 8) per 32 columns; thread (c, t) adds
+// rows t, t+8, ... in order, then a fixed tree over t (reproducible)
 __global__ void column_sums(const float *__restrict__ X, long n, int N, float *__restrict__ out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+    __shared__ float red[8][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
     float acc = 0.0f;
-    for (long r = 0; r < n; ++r) acc += X[r * N + j];
-    out[j] = acc;
+    if (j < N)
+        for (long r = threadIdx.y; r < n; r += 8) acc += X[r * N + j];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 4; o; o >>= 1) {
+        if ((int)threadIdx.y < o) red[threadIdx.y][threadIdx.x] += red[threadIdx.y + o][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && j < N) out[j] = red[0][threadIdx.x];
+}
+
+void launch_column_sums(const float *X, long n, int N, float *out, cudaStream_t s)
+{
+    column_sums<<<(unsigned)((N + 31) / 32), dim3(32, 8), 0, s>>>(X, n, N, out);
 }
 
 __global__ void adam_kernel(size_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
@@ -299,6 +320,84 @@ __global__ void output_layer(const __nv_bfloat16 *__restrict__ h, long n, int H,
     }
 }
 
+// XT[c][r] = bf16(X[r][c]) for r < n and 0 for n <= r < ldT (X [n][cols] FP32);
+// 32 x 32 tiles through shared memory, block (32, 8)
+__global__ void transpose_bf16(const float *__restrict__ X, long n, int cols, int ldT, __nv_bfloat16 *__restrict__ XT)
+{
+    __shared__ float tile[32][33];
+    const long r0 = (long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32, tx = threadIdx.x;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const long r = r0 + k;
+        const int c = c0 + tx;
+        tile[k][tx] = (r < n && c < cols) ? X[r * cols + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k;
+        const long r = r0 + tx;
+        if (c < cols && r < ldT) XT[(size_t)c * ldT + r] = __float2bfloat16_rn(tile[tx][k]);
+    }
+}
+
+// BF16 copies of the hidden weights for the tensor cores: W1 [H][I], W2 [H][H]
+// and W2 transposed
+__global__ void weights_to_bf16(const float *__restrict__ W1, const float *__restrict__ W2, int H, int I,
+                                __nv_bfloat16 *__restrict__ w1b, __nv_bfloat16 *__restrict__ w2b,
+                                __nv_bfloat16 *__restrict__ w2tb)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n1 = (long)H * I;
+    if (t < n1) {
+        w1b[t] = __float2bfloat16_rn(W1[t]);
+    } else if (t < n1 + (long)H * H) {
+        const long u = t - n1;
+        const int r = (int)(u / H), c = (int)(u - (long)r * H);
+        const __nv_bfloat16 v = __float2bfloat16_rn(W2[u]);
+        w2b[u] = v;
+        w2tb[(size_t)c * H + r] = v;
+    }
+}
+
+// dZ2[b][i] = (sum_k bf16(dO[b][k]) bf16(W3[k][i])) GELU'(Z2[b][i])
+__global__ void output_backward(const float *__restrict__ dO, const float *__restrict__ W3,
+                                const float *__restrict__ Z2, long n, int H, float *__restrict__ dZ2)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * H) return;
+    const long b = t / H;
+    const int i = (int)(t - b * H);
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc = fmaf(rbf16(dO[b * 3 + k]), rbf16(W3[k * H + i]), acc);
+    dZ2[t] = acc * gelu_grad(Z2[t]);
+}
+
+// gW3[k][i] = sum_b bf16(dO[b][k]) h2[b][i] (h2 BF16 [n][H]); one block per i,
+// partial sums per thread in a fixed order, then a fixed tree
+__global__ void output_weight_grad(const float *__restrict__ dO, const __nv_bfloat16 *__restrict__ h2, long n, int H,
+                                   float *__restrict__ gW3)
+{
+    __shared__ float red[3][256];
+    const int i = blockIdx.x;
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (long b = threadIdx.x; b < n; b += blockDim.x) {
+        const float h = __bfloat162float(h2[b * H + i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] = fmaf(rbf16(dO[b * 3 + k]), h, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) gW3[threadIdx.x * H + i] = red[threadIdx.x][0];
+}
+
 // C = opA(A) opB(B) (+ beta C), dispatching on transposes and precision
 int gemm(bool ta, bool tb, bool bf, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
          int ldc, float beta, cudaStream_t s)
@@ -358,18 +457,130 @@ void backward_batch(const ants_mlp *M, const float *par, long n, bool bf, const 
     const int H = M->H, I = M->n_in;
     // output layer
     gemm(true, false, bf, 3, H, (int)n, dO, 3, a.H2, H, g + o.W3, H, 0.0f, s);
-    column_sums<<<1, 32, 0, s>>>(dO, n, 3, g + o.b3);
+    launch_column_sums(dO, n, 3, g + o.b3, s);
     gemm(false, false, bf, (int)n, H, 3, dO, 3, par + o.W3, H, dA, H, 0.0f, s);  // dH2
     gelu_backward<<<blocks_for(n * H, 256), 256, 0, s>>>(dA, a.Z2, n * H);        // dZ2
     // second hidden layer
     gemm(true, false, bf, H, H, (int)n, dA, H, a.H1, H, g + o.W2, H, 0.0f, s);
-    column_sums<<<blocks_for(H, 128), 128, 0, s>>>(dA, n, H, g + o.b2);
+    launch_column_sums(dA, n, H, g + o.b2, s);
     gemm(false, false, bf, (int)n, H, H, dA, H, par + o.W2, H, dB, H, 0.0f, s);  // dH1
     gelu_backward<<<blocks_for(n * H, 256), 256, 0, s>>>(dB, a.Z1, n * H);        // dZ1
     // first hidden layer
     gemm(true, false, bf, H, I, (int)n, dB, H, a.U, I, g + o.W1, I, 0.0f, s);
-    column_sums<<<blocks_for(H, 128), 128, 0, s>>>(dB, n, H, g + o.b1);
+    launch_column_sums(dB, n, H, g + o.b1, s);
     count_launch(5);
+}
+
+// ---- tensor-core training (BF16 operands) ---------------------------------
+
+// the shapes the tensor-core products take: widths multiples of 8, at most 256
+bool tc_trainable(const ants_mlp *M) { return M->n_in % 8 == 0 && M->H % 8 == 0 && M->n_in <= 256 && M->H <= 256; }
+
+long round8(long n) { return (n + 7) & ~7L; }
+
+// buffers of one batch of up to cap rows (FP32 and BF16 parts 256-byte aligned)
+struct TcActs {
+    float *U, *Z1, *Z2, *O, *dZ2, *dZ1;
+    __nv_bfloat16 *UT, *H1, *H1T, *H2, *dZ2T, *dZ1T;
+};
+
+size_t tc_bytes(long cap, int I, int H)
+{
+    const long ldT = round8(cap);
+    auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return r((size_t)cap * I * 4) + 4 * r((size_t)cap * H * 4) + r((size_t)cap * 3 * 4) + r((size_t)I * ldT * 2) +
+           2 * r((size_t)cap * H * 2) + 3 * r((size_t)H * ldT * 2);
+}
+
+TcActs tc_carve(unsigned char *base, long cap, int I, int H)
+{
+    const long ldT = round8(cap);
+    auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    TcActs a;
+    unsigned char *p = base;
+    auto f = [&](size_t n) { float *q = (float *)p; p += r(n * 4); return q; };
+    auto h = [&](size_t n) { __nv_bfloat16 *q = (__nv_bfloat16 *)p; p += r(n * 2); return q; };
+    a.U = f((size_t)cap * I);
+    a.Z1 = f((size_t)cap * H);
+    a.Z2 = f((size_t)cap * H);
+    a.dZ2 = f((size_t)cap * H);
+    a.dZ1 = f((size_t)cap * H);
+    a.O = f((size_t)cap * 3);
+    a.UT = h((size_t)I * ldT);
+    a.H1 = h((size_t)cap * H);
+    a.H2 = h((size_t)cap * H);
+    a.H1T = h((size_t)H * ldT);
+    a.dZ2T = h((size_t)H * ldT);
+    a.dZ1T = h((size_t)H * ldT);
+    return a;
+}
+
+// BF16 weight copies from the FP32 masters (allocated on first use)
+int tc_refresh_weights(ants_mlp *M, cudaStream_t s)
+{
+    const Offsets o = offsets(M->n_in, M->H);
+    const int H = M->H, I = M->n_in;
+    if (!M->d_w1b) {
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w1b, (size_t)H * I * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_w2b, (size_t)H * H * sizeof(__nv_bfloat16)), "bf16 weights");
+        ANTS_CUDA_TRY(cudaMalloc(&M->d_bpad, 2 * (size_t)H * sizeof(float)), "padded biases");
+    }
+    if (!M->d_w2tb) ANTS_CUDA_TRY(cudaMalloc(&M->d_w2tb, (size_t)H * H * sizeof(__nv_bfloat16)), "bf16 weights");
+    const long n = (long)H * I + (long)H * H;
+    weights_to_bf16<<<blocks_for(n, 256), 256, 0, s>>>(M->d_par + o.W1, M->d_par + o.W2, H, I, M->d_w1b, M->d_w2b,
+                                                        M->d_w2tb);
+    count_launch();
+    // the inference path's padded copies are these (widths already multiples of 8), biases aside
+    M->bf16_stale = true;
+    return ANTS_OK;
+}
+
+// forward of n rows (idx nullable) on the tensor cores into a.O; with
+// want_bwd the transposed copies the weight gradients need are written too
+int tc_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, const long *idx, long n, bool want_bwd,
+               const TcActs &a, cudaStream_t s)
+{
+    const Offsets o = offsets(M->n_in, M->H);
+    const int H = M->H, I = M->n_in;
+    const int ldT = (int)round8(n);
+    normalize_rows<<<blocks_for(n, 8), 256, 0, s>>>(sig, idx, n, I, a.U);
+    count_launch();
+    if (want_bwd) {
+        transpose_bf16<<<dim3((unsigned)((ldT + 31) / 32), (unsigned)((I + 31) / 32)), dim3(32, 8), 0, s>>>(
+            a.U, n, I, ldT, a.UT);
+        count_launch();
+    }
+    int rc = mma_train_forward(ctx, a.U, true, M->d_w1b, M->d_par + o.b1, (int)n, H, I, a.Z1, a.H1,
+                               want_bwd ? a.H1T : nullptr, ldT, s);
+    if (rc != ANTS_OK) return rc;
+    rc = mma_train_forward(ctx, a.H1, false, M->d_w2b, M->d_par + o.b2, (int)n, H, H, a.Z2, a.H2, nullptr, ldT, s);
+    if (rc != ANTS_OK) return rc;
+    output_layer<<<blocks_for(n, 8), 256, 0, s>>>(a.H2, n, H, H, M->d_par + o.W3, M->d_par + o.b3, a.O);
+    count_launch();
+    return ANTS_OK;
+}
+
+// gradient of the batch loss into g (parameter layout), from dO [n][3]
+int tc_backward(ants_ctx *ctx, const ants_mlp *M, long n, const TcActs &a, const float *dO, float *g,
+                cudaStream_t s)
+{
+    const Offsets o = offsets(M->n_in, M->H);
+    const int H = M->H, I = M->n_in;
+    const int ldT = (int)round8(n);
+    output_weight_grad<<<H, 256, 0, s>>>(dO, a.H2, n, H, g + o.W3);
+    launch_column_sums(dO, n, 3, g + o.b3, s);
+    output_backward<<<blocks_for(n * H, 256), 256, 0, s>>>(dO, M->d_par + o.W3, a.Z2, n, H, a.dZ2);
+    transpose_bf16<<<dim3((unsigned)((ldT + 31) / 32), (unsigned)((H + 31) / 32)), dim3(32, 8), 0, s>>>(
+        a.dZ2, n, H, ldT, a.dZ2T);
+    launch_column_sums(a.dZ2, n, H, g + o.b2, s);
+    count_launch(5);
+    int rc = mma_f32(ctx, a.dZ2T, a.H1T, H, H, ldT, g + o.W2, s);
+    if (rc != ANTS_OK) return rc;
+    rc = mma_gelu_backward(ctx, a.dZ2, M->d_w2tb, a.Z1, (int)n, H, H, a.dZ1, a.dZ1T, ldT, s);
+    if (rc != ANTS_OK) return rc;
+    launch_column_sums(a.dZ1, n, H, g + o.b1, s);
+    count_launch();
+    return mma_f32(ctx, a.dZ1T, a.UT, H, I, ldT, g + o.W1, s);
 }
 
 struct Buf {
@@ -555,6 +766,7 @@ ANTS_API void ants_mlp_free(ants_mlp *M)
     cudaFree(M->d_v);
     cudaFree(M->d_w1b);
     cudaFree(M->d_w2b);
+    cudaFree(M->d_w2tb);
     cudaFree(M->d_bpad);
     delete M;
     (void)cudaGetLastError();
@@ -630,19 +842,34 @@ ANTS_API int ants_mlp_loss_grad(ants_ctx *ctx, const ants_mlp *M, const float *s
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = ctx->stream[0];
     const int H = M->H;
+    const bool tc = bf16 != 0 && tc_trainable(M);  // BF16 products on the tensor cores
     Buf acts, tgt, dO, dA, dB, g, part;
-    MLP_TRY(acts.alloc(acts_floats(n_events, M->n_in, H) * sizeof(float), "activations"));
+    if (tc) {
+        MLP_TRY(acts.alloc(tc_bytes(n_events, M->n_in, H), "activations"));
+    } else {
+        MLP_TRY(acts.alloc(acts_floats(n_events, M->n_in, H) * sizeof(float), "activations"));
+        MLP_TRY(dA.alloc((size_t)n_events * H * sizeof(float), "dA"));
+        MLP_TRY(dB.alloc((size_t)n_events * H * sizeof(float), "dB"));
+    }
     MLP_TRY(tgt.alloc(n_events * 3 * sizeof(float), "targets"));
     MLP_TRY(dO.alloc(n_events * 3 * sizeof(float), "dO"));
-    MLP_TRY(dA.alloc((size_t)n_events * H * sizeof(float), "dA"));
-    MLP_TRY(dB.alloc((size_t)n_events * H * sizeof(float), "dB"));
     MLP_TRY(g.alloc(M->n_par * sizeof(float), "grads"));
     MLP_TRY(part.alloc(kLossBlocks * sizeof(float), "loss"));
-    Acts a = carve(acts.f(), n_events, M->n_in, H);
-    forward_batch(M, M->d_par, signals_dev, nullptr, n_events, bf16 != 0, a, s);
-    make_targets<<<blocks_for(n_events, 256), 256, 0, s>>>(truth_dev, nullptr, n_events, M->cfg, tgt.f());
-    mse_grad<<<kLossBlocks, 256, 0, s>>>(a.O, tgt.f(), n_events, dO.f(), part.f());
-    backward_batch(M, M->d_par, n_events, bf16 != 0, a, dO.f(), dA.f(), dB.f(), g.f(), s);
+    if (tc) {
+        const TcActs a = tc_carve((unsigned char *)acts.p, n_events, M->n_in, H);
+        // the BF16 copies are caches of the parameters, which stay unchanged
+        MLP_TRY(tc_refresh_weights(const_cast<ants_mlp *>(M), s));
+        MLP_TRY(tc_forward(ctx, M, signals_dev, nullptr, n_events, true, a, s));
+        make_targets<<<blocks_for(n_events, 256), 256, 0, s>>>(truth_dev, nullptr, n_events, M->cfg, tgt.f());
+        mse_grad<<<kLossBlocks, 256, 0, s>>>(a.O, tgt.f(), n_events, dO.f(), part.f());
+        MLP_TRY(tc_backward(ctx, M, n_events, a, dO.f(), g.f(), s));
+    } else {
+        Acts a = carve(acts.f(), n_events, M->n_in, H);
+        forward_batch(M, M->d_par, signals_dev, nullptr, n_events, bf16 != 0, a, s);
+        make_targets<<<blocks_for(n_events, 256), 256, 0, s>>>(truth_dev, nullptr, n_events, M->cfg, tgt.f());
+        mse_grad<<<kLossBlocks, 256, 0, s>>>(a.O, tgt.f(), n_events, dO.f(), part.f());
+        backward_batch(M, M->d_par, n_events, bf16 != 0, a, dO.f(), dA.f(), dB.f(), g.f(), s);
+    }
     count_launch(2);
     ANTS_CUDA_TRY(cudaGetLastError(), "mlp loss_grad launch");
     int rc;
@@ -672,19 +899,32 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
     cudaStream_t s = ctx->stream[0];
     const int H = M->H, B = tp->batch;
     const bool bf = tp->bf16 != 0;
+    const bool tc = bf && tc_trainable(M);  // BF16 products on the tensor cores
     const long mon_chunk = 8192;
     const long cap = std::max<long>(B, std::min(n_mon, mon_chunk));
     Buf acts, tgt, dO, dA, dB, g, part, best, idx;
-    MLP_TRY(acts.alloc(acts_floats(cap, M->n_in, H) * sizeof(float), "activations"));
+    if (tc) {
+        MLP_TRY(acts.alloc(tc_bytes(cap, M->n_in, H), "activations"));
+    } else {
+        MLP_TRY(acts.alloc(acts_floats(cap, M->n_in, H) * sizeof(float), "activations"));
+        MLP_TRY(dA.alloc((size_t)cap * H * sizeof(float), "dA"));
+        MLP_TRY(dB.alloc((size_t)cap * H * sizeof(float), "dB"));
+    }
     MLP_TRY(tgt.alloc(cap * 3 * sizeof(float), "targets"));
     MLP_TRY(dO.alloc(cap * 3 * sizeof(float), "dO"));
-    MLP_TRY(dA.alloc((size_t)cap * H * sizeof(float), "dA"));
-    MLP_TRY(dB.alloc((size_t)cap * H * sizeof(float), "dB"));
     MLP_TRY(g.alloc(M->n_par * sizeof(float), "grads"));
     MLP_TRY(part.alloc(kLossBlocks * sizeof(float), "loss"));
     MLP_TRY(best.alloc(M->n_par * sizeof(float), "best"));
     MLP_TRY(idx.alloc((size_t)n_events * sizeof(long), "index"));
-    Acts a = carve(acts.f(), cap, M->n_in, H);
+    Acts a{};
+    TcActs ta{};
+    if (tc) {
+        ta = tc_carve((unsigned char *)acts.p, cap, M->n_in, H);
+        MLP_TRY(tc_refresh_weights(M, s));
+    } else {
+        a = carve(acts.f(), cap, M->n_in, H);
+    }
+    float *const out_rows = tc ? ta.O : a.O;  // network outputs of the current batch
     std::vector<long> perm(n_tr);
     for (long i = 0; i < n_tr; ++i) perm[i] = i;
     std::mt19937_64 rng(tp->seed);
@@ -701,15 +941,18 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
         ANTS_CUDA_TRY(cudaMemcpyAsync(d_idx, perm.data(), n_tr * sizeof(long), cudaMemcpyHostToDevice, s), "upload");
         for (long off = 0; off + B <= n_tr; off += B) {
             const long *bidx = d_idx + off;
-            forward_batch(M, M->d_par, signals_dev, bidx, B, bf, a, s);
+            if (tc) MLP_TRY(tc_forward(ctx, M, signals_dev, bidx, B, true, ta, s));
+            else forward_batch(M, M->d_par, signals_dev, bidx, B, bf, a, s);
             make_targets<<<blocks_for(B, 256), 256, 0, s>>>(truth_dev, bidx, B, M->cfg, tgt.f());
-            mse_grad<<<kLossBlocks, 256, 0, s>>>(a.O, tgt.f(), B, dO.f(), part.f());
-            backward_batch(M, M->d_par, B, bf, a, dO.f(), dA.f(), dB.f(), g.f(), s);
+            mse_grad<<<kLossBlocks, 256, 0, s>>>(out_rows, tgt.f(), B, dO.f(), part.f());
+            if (tc) MLP_TRY(tc_backward(ctx, M, B, ta, dO.f(), g.f(), s));
+            else backward_batch(M, M->d_par, B, bf, a, dO.f(), dA.f(), dB.f(), g.f(), s);
             M->adam_t += 1;
             const float c1 = 1.0f - powf(tp->beta1, (float)M->adam_t), c2 = 1.0f - powf(tp->beta2, (float)M->adam_t);
             adam_kernel<<<blocks_for((long)M->n_par, 256), 256, 0, s>>>(M->n_par, M->d_par, g.f(), M->d_m, M->d_v,
                                                                         tp->lr, tp->beta1, tp->beta2, tp->eps, c1, c2);
             count_launch(3);
+            if (tc) MLP_TRY(tc_refresh_weights(M, s));
             if (off + 2 * B > n_tr) {  // loss of the last batch of the epoch
                 int rc;
                 last_train = host_sum(part.f(), kLossBlocks, s, &rc);
@@ -721,9 +964,10 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
         double mse = 0.0;
         for (long off = 0; off < n_mon; off += mon_chunk) {
             const long m = std::min(mon_chunk, n_mon - off);
-            forward_batch(M, M->d_par, signals_dev, d_mon + off, m, bf, a, s);
+            if (tc) MLP_TRY(tc_forward(ctx, M, signals_dev, d_mon + off, m, false, ta, s));
+            else forward_batch(M, M->d_par, signals_dev, d_mon + off, m, bf, a, s);
             make_targets<<<blocks_for(m, 256), 256, 0, s>>>(truth_dev, d_mon + off, m, M->cfg, tgt.f());
-            mse_grad<<<kLossBlocks, 256, 0, s>>>(a.O, tgt.f(), m, nullptr, part.f());
+            mse_grad<<<kLossBlocks, 256, 0, s>>>(out_rows, tgt.f(), m, nullptr, part.f());
             count_launch(2);
             int rc;
             const float chunk_mse = host_sum(part.f(), kLossBlocks, s, &rc);

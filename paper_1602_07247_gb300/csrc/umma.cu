@@ -4,9 +4,11 @@
 //   C[m][n] = sum_k A[m][k] B[n][k]     A [M][K]: FP32 (rounded to BF16 while
 //                                       it is staged) or BF16;  B [N][K] BF16
 //
-// K <= 256 and a multiple of 8; A rows 16-byte aligned.  Persistent CTAs (one
-// per SM) take 128-row bands of C ("m-tiles") in a fixed stride; every band
-// walks all of N in 256-column n-tiles.  Warp roles (22 warps):
+// K a multiple of 8, at most 256 unless N fits one 256-column n-tile (then
+// the band's A is streamed through its four 64-wide chunk slots, any K); A
+// rows 16-byte aligned.  Persistent CTAs (one per SM) take 128-row bands of C
+// ("m-tiles") in a fixed stride; every band walks all of N in 256-column
+// n-tiles.  Warp roles (22 warps):
 //   warp 0      TMA producer: B as 256 x 64 boxes (128-byte swizzle) through
 //               a 3-stage ring, re-read from L2 for every band;
 //   warp 1      allocates 512 TMEM columns; one thread issues
@@ -22,7 +24,14 @@
 // Epilogues:
 //   EPI_TOPK       running top-K per row over all N (value desc, column asc),
 //                  written as K (score, column) pairs per row;
-//   EPI_BIAS_GELU  GELU(C + bias[n]) stored as BF16 (N a multiple of 8).
+//   EPI_BIAS_GELU  GELU(C + bias[n]) stored as BF16 (N a multiple of 8);
+// and for training the network (Sec. 5.1.3) with BF16 operands (N a multiple
+// of 8; the transposed BF16 copies [N][ldT] are the K-major operands of the
+// weight gradients, rows M..ldT-1 written as zeros):
+//   EPI_SAVE       z = C + bias[n] kept in FP32, GELU(z) stored as BF16, and
+//                  optionally transposed;
+//   EPI_GELU_BWD   dz = C GELU'(z[m][n]) stored in FP32 and transposed BF16;
+//   EPI_F32        C stored in FP32 (weight gradients, K = batch).
 // Every mbarrier wait is bounded in time.  A wait that runs out sets a shared
 // abort flag and the context's fault word; every role then stops, waits
 // (bounded) for its own copies and products in flight, and the block frees its
@@ -48,7 +57,7 @@ constexpr uint32_t kAChunkBytes = kBM * kBK * 2;  // 16 KiB
 constexpr uint32_t kBStageBytes = kBN * kBK * 2;  // 32 KiB
 constexpr uint64_t kWaitNs = 1000000000ull;       // 1 s per wait
 
-enum { EPI_TOPK = 0, EPI_BIAS_GELU = 1 };
+enum { EPI_TOPK = 0, EPI_BIAS_GELU = 1, EPI_SAVE = 2, EPI_GELU_BWD = 3, EPI_F32 = 4 };
 
 // shared-memory map (offsets from a 1024-byte aligned base)
 constexpr uint32_t kOffA = 0;
@@ -69,6 +78,10 @@ struct UmmaArgs {
     int *top_idx;
     const float *bias;
     __nv_bfloat16 *out;
+    float *zbuf;               // EPI_SAVE: z written; EPI_GELU_BWD: z read ([M][N] FP32)
+    float *out_f;              // EPI_GELU_BWD, EPI_F32: [M][N] FP32
+    __nv_bfloat16 *out_t;      // transposed BF16 copy [N][ldT] (nullable)
+    int ldT;
     int *fault;
     int hold_producer;  // self-test only: the TMA producer issues nothing
 };
@@ -190,6 +203,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// d GELU / dx = Phi(x) + x phi(x)
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
 
 // grid index of column n; the empty-entry marker -1 ranks last
 __device__ __forceinline__ int gidx(const int *order, int n) { return n >= 0 ? __ldg(order + n) : 0x7fffffff; }
@@ -326,10 +345,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            int s = 0, j = 0, it = 0;
+            int s = 0, j = 0;
             uint32_t ph = 0;
+            uint32_t apar = 0;  // parity of each A chunk slot's next fill
             bool ok = true;
-            for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
+            for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x) {
                 for (int nt = 0; nt < n_nt && ok; ++nt, ++j) {
                     const int ab = j & 1;
                     const uint32_t use = (uint32_t)(j >> 1);
@@ -338,19 +358,21 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(ab * kBN);
                     for (int kc = 0; kc < n_kc; ++kc) {
+                        const int c = kc % kAChunks;  // A chunk slot (K > 256 only with one n-tile)
                         if (nt == 0) {
-                            ok = bar_wait(a_full(kc), (uint32_t)(it & 1), abort, a.fault);
+                            ok = bar_wait(a_full(c), (apar >> c) & 1u, abort, a.fault);
                             if (!ok) break;
+                            apar ^= 1u << c;
                         }
                         ok = bar_wait(b_full(s), ph, abort, a.fault);
                         if (!ok) break;
                         tc_fence_after();
                         const int ksteps = min(kBK / 16, (a.K - kc * kBK + 15) / 16);
                         for (int ks = 0; ks < ksteps; ++ks)
-                            umma(d, sdesc(sA + kc * kAChunkBytes + ks * 32), sdesc(sB + s * kBStageBytes + ks * 32),
+                            umma(d, sdesc(sA + c * kAChunkBytes + ks * 32), sdesc(sB + s * kBStageBytes + ks * 32),
                                  (kc | ks) != 0);
                         umma_commit(b_empty(s));
-                        if (nt == n_nt - 1) umma_commit(a_empty(kc));
+                        if (nt == n_nt - 1) umma_commit(a_empty(c));
                         if (++s == kStages) {
                             s = 0;
                             ph ^= 1;
@@ -368,13 +390,15 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
     } else if (warp < kEpiWarp0) {
         // ---------------- A loaders (FP32 -> BF16, or BF16) ----------------
         const int lt = threadIdx.x - kLoaderWarp0 * 32;  // 0..127
-        int it = 0;
+        uint32_t apar = 0;  // parity of each chunk slot's next fill
         bool ok = true;
-        for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
+        for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x) {
             const long m0 = (long)mt * kBM;
             for (int kc = 0; kc < n_kc && ok; ++kc) {
-                ok = bar_wait(a_empty(kc), (uint32_t)(it & 1) ^ 1, abort, a.fault);
+                const int c = kc % kAChunks;
+                ok = bar_wait(a_empty(c), ((apar >> c) & 1u) ^ 1u, abort, a.fault);
                 if (!ok) break;
+                apar ^= 1u << c;
 #pragma unroll 1
                 for (int half = 0; half < 2; ++half) {
                     uint4 packed[4];
@@ -419,14 +443,14 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int item = lt + 128 * (4 * half + q), r = item >> 3, c8 = item & 7;
-                        const uint32_t dst = sA + kc * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
+                        const uint32_t dst = sA + c * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
                         asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
                                      "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
                                      : "memory");
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                bar_arrive(a_full(kc));
+                bar_arrive(a_full(c));
             }
         }
     } else {
@@ -502,6 +526,47 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                                     }
                                 }
                             }
+                        }
+                    } else if (EPI != EPI_BIAS_GELU) {
+                        // training epilogues; the transposed copy gets each value as it is made
+                        const bool in_row = m < a.M;
+                        const bool tr = EPI != EPI_F32 && a.out_t != nullptr && m < a.ldT;
+                        uint32_t pk[16];  // EPI_SAVE: GELU values of the row as BF16 pairs
+                        float prev = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int n = n0 + q;
+                            const float c = __uint_as_float(v[q]);
+                            float o = 0.0f;
+                            if (in_row && n < a.N) {
+                                const size_t at = (size_t)m * a.N + n;
+                                if (EPI == EPI_SAVE) {
+                                    const float z = c + __ldg(a.bias + n);
+                                    a.zbuf[at] = z;
+                                    o = gelu_f(z);
+                                } else if (EPI == EPI_GELU_BWD) {
+                                    o = c * gelu_grad_f(a.zbuf[at]);
+                                    a.out_f[at] = o;
+                                } else {
+                                    o = c;
+                                    a.out_f[at] = o;
+                                }
+                            }
+                            if (tr && n < a.N) a.out_t[(size_t)n * a.ldT + m] = __float2bfloat16_rn(o);
+                            if (EPI == EPI_SAVE) {
+                                if (q & 1) {
+                                    __nv_bfloat162 hh = __floats2bfloat162_rn(prev, o);
+                                    pk[q >> 1] = *reinterpret_cast<uint32_t *>(&hh);
+                                } else {
+                                    prev = o;
+                                }
+                            }
+                        }
+                        if (EPI == EPI_SAVE && in_row) {
+                            __nv_bfloat16 *o = a.out + (size_t)m * a.N + n0;
+                            for (int q = 0; q < 4 && 8 * q < a.N - n0; ++q)
+                                reinterpret_cast<uint4 *>(o)[q] =
+                                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                         }
                     } else if (m < a.M) {
                         uint32_t pk[16];
@@ -601,8 +666,10 @@ int encode_b(CUtensorMap *map, const __nv_bfloat16 *B, int N, int K)
 
 int check_shape(const void *A, const __nv_bfloat16 *B, int M, int N, int K)
 {
-    if (M < 0 || N < 1 || K < 8 || K > kMaxK || K % 8 != 0)
-        return fail(ANTS_E_SHAPE, "tensor core product: need 8 <= K <= %d, K %% 8 == 0 (K = %d, N = %d)", kMaxK, K, N);
+    if (M < 0 || N < 1 || K < 8 || K % 8 != 0 || (K > kMaxK && N > kBN))
+        return fail(ANTS_E_SHAPE,
+                    "tensor core product: need K >= 8, K %% 8 == 0 and K <= %d unless N <= %d (K = %d, N = %d)", kMaxK,
+                    kBN, K, N);
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
         return fail(ANTS_E_ARG, "tensor core product: operands must be 16-byte aligned");
     return ANTS_OK;
@@ -670,6 +737,73 @@ int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfl
     a.out = out;
     a.fault = ctx->d_fault;
     return a_f32 ? launch<EPI_BIAS_GELU, true>(ctx, map, a, s) : launch<EPI_BIAS_GELU, false>(ctx, map, a, s);
+}
+
+int mma_train_forward(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *W, const float *bias,
+                      int M, int N, int K, float *z, __nv_bfloat16 *h, __nv_bfloat16 *hT, int ldT, cudaStream_t s)
+{
+    int rc = check_shape(A, W, M, N, K);
+    if (rc != ANTS_OK || M == 0) return rc;
+    if (N % 8 != 0 || K > kMaxK || (hT && ldT < M) || (reinterpret_cast<uintptr_t>(h) & 15) ||
+        (reinterpret_cast<uintptr_t>(z) & 15))
+        return fail(ANTS_E_SHAPE, "tensor core training forward: N %% 8, K <= %d, ldT >= M, aligned outputs", kMaxK);
+    CUtensorMap map;
+    rc = encode_b(&map, W, N, K);
+    if (rc != ANTS_OK) return rc;
+    UmmaArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.bias = bias;
+    a.out = h;
+    a.zbuf = z;
+    a.out_t = hT;
+    a.ldT = ldT;
+    a.fault = ctx->d_fault;
+    return a_f32 ? launch<EPI_SAVE, true>(ctx, map, a, s) : launch<EPI_SAVE, false>(ctx, map, a, s);
+}
+
+int mma_gelu_backward(const ants_ctx *ctx, const float *dY, const __nv_bfloat16 *Wt, const float *z, int M, int N,
+                      int K, float *dz, __nv_bfloat16 *dzT, int ldT, cudaStream_t s)
+{
+    int rc = check_shape(dY, Wt, M, N, K);
+    if (rc != ANTS_OK || M == 0) return rc;
+    if (N % 8 != 0 || K > kMaxK || (dzT && ldT < M))
+        return fail(ANTS_E_SHAPE, "tensor core GELU backward: N %% 8, K <= %d, ldT >= M", kMaxK);
+    CUtensorMap map;
+    rc = encode_b(&map, Wt, N, K);
+    if (rc != ANTS_OK) return rc;
+    UmmaArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = dY;
+    a.zbuf = const_cast<float *>(z);
+    a.out_f = dz;
+    a.out_t = dzT;
+    a.ldT = ldT;
+    a.fault = ctx->d_fault;
+    return launch<EPI_GELU_BWD, true>(ctx, map, a, s);
+}
+
+int mma_f32(const ants_ctx *ctx, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, float *C,
+            cudaStream_t s)
+{
+    int rc = check_shape(A, B, M, N, K);
+    if (rc != ANTS_OK || M == 0) return rc;
+    if (N % 8 != 0) return fail(ANTS_E_SHAPE, "tensor core product: FP32 output needs N %% 8 == 0");
+    CUtensorMap map;
+    rc = encode_b(&map, B, N, K);
+    if (rc != ANTS_OK) return rc;
+    UmmaArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.out_f = C;
+    a.fault = ctx->d_fault;
+    return launch<EPI_F32, false>(ctx, map, a, s);
 }
 
 }  // namespace ants
