@@ -235,6 +235,7 @@ static int upload_lrf(ants_lrf *L)
                   "upload cog weights");
     LrfDev &D = L->dev;
     D.coef2 = nullptr;
+    D.coef2_pf = nullptr;
     D.coef_t = nullptr;
     D.set_of = nullptr;
     D.op_of = nullptr;
@@ -268,6 +269,13 @@ static int upload_lrf(ants_lrf *L)
                       "upload coef pairs");
         D.coef2 = L->d_coef2;
         D.pair_stride = ps;
+        std::vector<float2> cpf(c2.size());
+        for (int p = 0; p < D.n_pairs; ++p)
+            for (int k = 0; k < ps; ++k) cpf[(size_t)k * D.n_pairs + p] = c2[(size_t)p * ps + k];
+        ANTS_CUDA_TRY(cudaMalloc(&L->d_coef2_pf, cpf.size() * sizeof(float2)), "cudaMalloc(lrf coef pairs, pair-fastest)");
+        ANTS_CUDA_TRY(cudaMemcpy(L->d_coef2_pf, cpf.data(), cpf.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                      "upload coef pairs (pair-fastest)");
+        D.coef2_pf = L->d_coef2_pf;
         std::vector<float> ct(c.size());
         for (int i = 0; i < L->n_s; ++i)
             for (int k = 0; k < ps; ++k) ct[(size_t)k * L->n_s + i] = c[(size_t)i * ps + k];
@@ -333,6 +341,7 @@ ANTS_API void ants_lrf_free(ants_lrf *lrf)
     cudaFree(lrf->d_cogw);
     cudaFree(lrf->d_coef2);
     cudaFree(lrf->d_coeft);
+    cudaFree(lrf->d_coef2_pf);
     cudaFree(lrf->d_set_of);
     cudaFree(lrf->d_op_of);
     cudaFree(lrf->d_rpoly);

@@ -29,6 +29,7 @@
 // Lanes store per-(node, slot) partial sums in shared memory; one thread per
 // node adds the slots, and a team argmax (ties to the lowest flat index)
 // picks the next centre.
+#include <cmath>
 #include <type_traits>
 
 #include "bspline.cuh"
@@ -80,7 +81,7 @@ __device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
 // (k ln 2) to degree 6 (truncation below 8e-10 for |u| <= 1/16), the hardware
 // log2 of 1 + u beyond that; every lane of the warp calls it together
 constexpr float kNearOne = 0.0625f;
-__device__ __forceinline__ float2 log2_1p_pair(float2 u)
+__device__ __forceinline__ float2 log2_1p_taylor(float2 u)
 {
     float2 p = ffma2(u, make_float2(-0.24044917348149393f, -0.24044917348149393f),
                      make_float2(0.28853900817779268f, 0.28853900817779268f));
@@ -88,7 +89,12 @@ __device__ __forceinline__ float2 log2_1p_pair(float2 u)
     p = ffma2(p, u, make_float2(0.48089834696298783f, 0.48089834696298783f));
     p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
     p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
-    p = fmul2(p, u);
+    return fmul2(p, u);
+}
+
+__device__ __forceinline__ float2 log2_1p_pair(float2 u)
+{
+    float2 p = log2_1p_taylor(u);
     // a warp-uniform branch: the hardware log2 is issued only when a lane needs it
     if (__any_sync(kFull, fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne)) {
         if (fabsf(u.x) > kNearOne) p.x = __log2f(1.0f + u.x);
@@ -564,6 +570,384 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     }
 }
 
+// ---- small grids on a table in global memory: one sensor pair per lane ----
+//
+// When the whole grid spans less than two knot intervals per axis (the
+// refines of the learned and precision forms), every node of a grid reads
+// coefficients from one patch of at most kPatch x kPatch per sensor.  A team
+// of TEAM warps reconstructs one event and its lane t owns sensor pair t
+// (32 TEAM >= pairs).  The lane reads its pair's patch row by row from the
+// pair-fastest copy (a warp's lanes read consecutive pairs: one contiguous
+// 256-byte run per load), contracts each row along x for every grid column
+// with the columns' B-spline weights placed in the patch ("dense" weights,
+// zero outside the column's four), and adds the row into every node with the
+// node rows' dense y weights.  The centre node gives eta_c; the pair's
+// likelihood terms of every node (as in the team kernel above) go to shared
+// memory and are summed over the team's lanes at the end of the grid.
+constexpr int kPatch = 6;           // coefficient rows and columns a grid may touch
+constexpr int kPatchThreads = 512;  // teams of TEAM warps, one block per SM
+
+template <int N>
+struct PatchSmem {
+    static constexpr int NN = N * N;
+    // floats per team of lt lanes: node terms [2 NN][lt + 1] (the odd row stride
+    // keeps both the writes and the row sums free of bank conflicts), x weights
+    // [N][kPatch], y weights [kPatch][N], half sums [2][2 NN], reduction slots [32]
+    __device__ __host__ static int stride(int lt) { return lt + 1; }
+    __device__ __host__ static int wx(int lt) { return 2 * NN * stride(lt); }
+    __device__ __host__ static int wy(int lt) { return wx(lt) + N * kPatch; }
+    __device__ __host__ static int tot(int lt) { return wy(lt) + kPatch * N; }
+    __device__ __host__ static int red(int lt) { return tot(lt) + 4 * NN; }
+    __device__ __host__ static int total(int lt) { return (red(lt) + 32 + 3) & ~3; }
+};
+
+template <int N, int TEAM, bool FLOOR>
+__global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a, int teams_per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NN = N * N, C = (N - 1) / 2, LT = 32 * TEAM;
+    using Lay = PatchSmem<N>;
+    const LrfDev &L = a.L;
+    const int n_s = L.n_s, n_pairs = L.n_pairs, sy = L.stride_y;
+    const int team = threadIdx.x / LT;
+    if (team >= teams_per_block) return;  // no block-wide barrier follows
+    const int t = threadIdx.x - team * LT, lane = threadIdx.x & 31, wit = t >> 5;
+    float *ts = reinterpret_cast<float *>(smem_raw) + (size_t)team * Lay::total(LT);
+    float *s_part = ts, *s_wx = ts + Lay::wx(LT), *s_wy = ts + Lay::wy(LT);
+    float *s_tot = ts + Lay::tot(LT), *s_red = ts + Lay::red(LT);
+    const float2 *cpf = L.coef2_pf;
+    const float qnan = __int_as_float(0x7fc00000);
+    const long team_stride = (long)gridDim.x * teams_per_block;
+    const bool mine = t < n_pairs;  // lane t owns pair t
+    const int pp = mine ? t : 0;    // lanes past the last pair repeat pair 0 and add nothing
+
+    for (long e = (long)blockIdx.x * teams_per_block + team; e < a.n_e; e += team_stride) {
+        // ---- prologue: signals, S, centroid, status --------------------------
+        const float *sg = a.sig + (size_t)(a.rows ? (long)a.rows[e] : e / a.row_div) * n_s;
+        float S = 0.0f, Sx = 0.0f, Sy = 0.0f, Sw = 0.0f;
+        int bad = 0;
+        for (int i = t; i < n_s; i += LT) {
+            const float v = sg[i];
+            bad |= !(v >= 0.0f) || isinf(v);
+            const float w = v * L.cog_w[i];
+            S += v;
+            Sx = fmaf(L.sxy[2 * i], w, Sx);
+            Sy = fmaf(L.sxy[2 * i + 1], w, Sy);
+            Sw += w;
+        }
+        bad = __any_sync(kFull, bad);
+        S = warp_sum(S);
+        Sx = warp_sum(Sx);
+        Sy = warp_sum(Sy);
+        Sw = warp_sum(Sw);
+        if (TEAM > 1) {
+            if (lane == 0) {
+                s_red[16 + 4 * wit] = S;
+                s_red[16 + 4 * wit + 1] = Sx;
+                s_red[16 + 4 * wit + 2] = Sy;
+                s_red[16 + 4 * wit + 3] = bad ? -1.0f : Sw;
+            }
+            team_sync<TEAM>(team);
+            S = Sx = Sy = Sw = 0.0f;
+            bad = 0;
+            for (int w = 0; w < TEAM; ++w) {
+                S += s_red[16 + 4 * w];
+                Sx += s_red[16 + 4 * w + 1];
+                Sy += s_red[16 + 4 * w + 2];
+                const float v = s_red[16 + 4 * w + 3];
+                bad |= v < 0.0f;
+                Sw += v;
+            }
+        }
+        int st = ANTS_EVT_OK;
+        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+        if (bad) st = ANTS_EVT_BAD_SIGNAL;
+        else if (!(S > 0.0f)) st = ANTS_EVT_ZERO_SIGNAL;
+        if (st == ANTS_EVT_OK) {
+            if (a.start) {
+                cx = a.start[3 * e];
+                cy = a.start[3 * e + 1];
+                cz = a.start[3 * e + 2];
+            } else {
+                cx = fminf(fmaxf(Sx / Sw, L.lo[0]), L.hi[0]);
+                cy = fminf(fmaxf(Sy / Sw, L.lo[1]), L.hi[1]);
+            }
+            if (!in_box(L, cx, cy, cz)) st = ANTS_EVT_OUT_OF_DOMAIN;
+        }
+        if (st != ANTS_EVT_OK) {
+            if (t == 0) {
+                a.xyz[3 * e] = a.xyz[3 * e + 1] = a.xyz[3 * e + 2] = qnan;
+                a.E[e] = qnan;
+                a.logL[e] = qnan;
+                a.status[e] = st;
+            }
+            if (a.trace)
+                for (int it = t; it < a.iters; it += LT) a.trace[e * a.iters + it] = -1;
+            team_sync<TEAM>(team);
+            continue;
+        }
+        const float2 sp = mine ? make_float2(sg[2 * t], 2 * t + 1 < n_s ? sg[2 * t + 1] : 0.0f)
+                               : make_float2(0.0f, 0.0f);
+
+        float sxy = a.step_xy;
+        for (int it = 0; it < a.iters; ++it) {
+            // ---- the grid's patch and dense weights (every thread knows the
+            //      patch origin; threads 0..N-1 write column weights, N..2N-1
+            //      row weights)
+            float t0;
+            const int ix0 = bs_span(fmaf((float)(-C), sxy, cx), L.lo[0], L.inv_h[0], L.n_int[0], t0);
+            const int iy0 = bs_span(fmaf((float)(-C), sxy, cy), L.lo[1], L.inv_h[1], L.n_int[1], t0);
+            const int ixN = bs_span(fmaf((float)C, sxy, cx), L.lo[0], L.inv_h[0], L.n_int[0], t0);
+            const int iyN = bs_span(fmaf((float)C, sxy, cy), L.lo[1], L.inv_h[1], L.n_int[1], t0);
+            const int pw = ixN - ix0 + 4, ph = iyN - iy0 + 4;  // <= kPatch (checked on the host)
+            if (t < 2 * N) {
+                const bool col = t < N;
+                const int jj = col ? t : t - N;
+                float tt, w[4];
+                const int spn = col ? bs_span(fmaf((float)(jj - C), sxy, cx), L.lo[0], L.inv_h[0], L.n_int[0], tt)
+                                    : bs_span(fmaf((float)(jj - C), sxy, cy), L.lo[1], L.inv_h[1], L.n_int[1], tt);
+                bs_weights(tt, w);
+                const int off = spn - (col ? ix0 : iy0);
+#pragma unroll
+                for (int c = 0; c < kPatch; ++c) {
+                    const int b = c - off;
+                    const float v = b == 0 ? w[0] : b == 1 ? w[1] : b == 2 ? w[2] : b == 3 ? w[3] : 0.0f;
+                    if (col) s_wx[jj * kPatch + c] = v;
+                    else s_wy[c * N + jj] = v;
+                }
+            }
+            team_sync<TEAM>(team);
+
+            // ---- this lane's pair at every node --------------------------------
+            float wx[N][kPatch];
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int c = 0; c < kPatch; ++c) wx[j][c] = s_wx[j * kPatch + c];
+            float2 eta[NN];
+#pragma unroll
+            for (int q = 0; q < NN; ++q) eta[q] = make_float2(0.0f, 0.0f);
+            const float2 *base = cpf + ((size_t)iy0 * sy + ix0) * n_pairs + pp;
+#pragma unroll
+            for (int r = 0; r < kPatch; ++r) {
+                if (r < ph) {
+                    float2 seg[kPatch];
+#pragma unroll
+                    for (int c = 0; c < kPatch; ++c)
+                        seg[c] = c < pw ? __ldg(base + ((size_t)r * sy + c) * n_pairs) : make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        float2 T = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int c = 0; c < kPatch; ++c) T = ffma2(make_float2(wx[j][c], wx[j][c]), seg[c], T);
+#pragma unroll
+                        for (int k = 0; k < N; ++k) {
+                            const float w = s_wy[r * N + k];
+                            eta[k * N + j] = ffma2(make_float2(w, w), T, eta[k * N + j]);
+                        }
+                    }
+                }
+            }
+            float2 ec = eta[C * N + C];
+            if (FLOOR) {
+                ec.x = fmaxf(ec.x, kEtaFloor);
+                ec.y = fmaxf(ec.y, kEtaFloor);
+            }
+            float hc = mine ? ec.x + (2 * t + 1 < n_s ? ec.y : 0.0f) : 0.0f;
+            const float2 ic = make_float2(__frcp_rn(ec.x), __frcp_rn(ec.y));
+            const float2 nec = make_float2(-ec.x, -ec.y);
+            const bool acc_log = sxy * (float)C <= a.prec_halfwidth;
+            constexpr int RS = LT + 1;
+            bool far = false;  // some |u| beyond the Taylor range (accurate grids)
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                float2 v = eta[q];
+                if (FLOOR) {
+                    v.x = fmaxf(v.x, kEtaFloor);
+                    v.y = fmaxf(v.y, kEtaFloor);
+                }
+                float2 lg;
+                if (acc_log) {
+                    const float2 u = ffma2(v, ic, make_float2(-1.0f, -1.0f));
+                    far = far || fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne;
+                    lg = log2_1p_taylor(u);
+                } else {
+                    const float2 r2 = fmul2(v, ic);
+                    lg = make_float2(__log2f(r2.x), __log2f(r2.y));
+                }
+                const float2 tt = fmul2(sp, lg);
+                const float2 d = fadd2(v, nec);
+                s_part[q * RS + t] = tt.x + tt.y;
+                s_part[(NN + q) * RS + t] = mine ? d.x + d.y : 0.0f;
+            }
+            if (acc_log && __any_sync(kFull, far)) {
+                // rare: redo the nodes whose |u| is beyond the Taylor range
+                // (unrolled: eta stays in registers)
+#pragma unroll
+                for (int q = 0; q < NN; ++q) {
+                    float2 v = eta[q];
+                    if (FLOOR) {
+                        v.x = fmaxf(v.x, kEtaFloor);
+                        v.y = fmaxf(v.y, kEtaFloor);
+                    }
+                    const float2 u = ffma2(v, ic, make_float2(-1.0f, -1.0f));
+                    if (fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne) {
+                        float2 lg = log2_1p_taylor(u);
+                        if (fabsf(u.x) > kNearOne) lg.x = __log2f(1.0f + u.x);
+                        if (fabsf(u.y) > kNearOne) lg.y = __log2f(1.0f + u.y);
+                        const float2 tt = fmul2(sp, lg);
+                        s_part[q * RS + t] = tt.x + tt.y;
+                    }
+                }
+            }
+            hc = warp_sum(hc);
+            if (TEAM > 1) {
+                if (lane == 0) s_red[8 + wit] = hc;
+            }
+            team_sync<TEAM>(team);
+            if (TEAM > 1) {
+                hc = 0.0f;
+                for (int w = 0; w < TEAM; ++w) hc += s_red[8 + w];
+            }
+            const float inv_hc = __frcp_rn(hc);
+
+            // ---- node sums over the team's lanes: item k = sigma + 2 NN h adds
+            //      half h of row sigma (consecutive threads take consecutive rows:
+            //      distinct banks with the odd row stride)
+            for (int k = t; k < 4 * NN; k += LT) {
+                const int h = k >= 2 * NN, sigma = k - 2 * NN * h;
+                const float *src = s_part + sigma * RS + h * (LT / 2);
+                float v = 0.0f;
+#pragma unroll 16
+                for (int i = 0; i < LT / 2; ++i) v += src[i];
+                s_tot[k] = v;
+            }
+            team_sync<TEAM>(team);
+
+            // ---- node scores and argmax (ties to the lowest index) ------------
+            float bestF = -INFINITY;
+            int bestk = 0x7fffffff;
+            if (wit == 0) {
+                for (int node = lane; node < NN; node += 32) {
+                    const int k = node / N, jj = node - k * N;
+                    const float xn = fmaf((float)(jj - C), sxy, cx);
+                    const float yn = fmaf((float)(k - C), sxy, cy);
+                    const bool ok = xn >= L.lo[0] && xn <= L.hi[0] && yn >= L.lo[1] && yn <= L.hi[1];
+                    const float sa = s_tot[node] + s_tot[2 * NN + node];
+                    const float sd = s_tot[NN + node] + s_tot[3 * NN + node];
+                    const float F = ok ? sa - S * (log1pf(sd * inv_hc) * kInvLn2) : -INFINITY;
+                    if (F > bestF) {
+                        bestF = F;
+                        bestk = node;
+                    }
+                }
+                for (int o = 16; o; o >>= 1) {
+                    const float F2 = __shfl_xor_sync(kFull, bestF, o);
+                    const int k2 = __shfl_xor_sync(kFull, bestk, o);
+                    if (F2 > bestF || (F2 == bestF && k2 < bestk)) {
+                        bestF = F2;
+                        bestk = k2;
+                    }
+                }
+                if (lane == 0) s_red[0] = __int_as_float(bestk);
+            }
+            team_sync<TEAM>(team);
+            bestk = __float_as_int(s_red[0]);
+            const int bj = bestk % N, bk = bestk / N;
+            cx = fmaf((float)(bj - C), sxy, cx);
+            cy = fmaf((float)(bk - C), sxy, cy);
+            if (a.trace && t == 0) a.trace[e * a.iters + it] = (int16_t)bestk;
+            sxy *= a.shrink;
+        }
+
+        // ---- energy and full Poisson log-likelihood at the result -------------
+        float H = 0.0f, ll = 0.0f;
+        float2 v = make_float2(kEtaFloor, kEtaFloor);
+        if (mine) {
+            v = pair_eta(L, L.coef2, t, cx, cy);
+            v.x = fmaxf(v.x, kEtaFloor);
+            v.y = fmaxf(v.y, kEtaFloor);
+            H = v.x + (2 * t + 1 < n_s ? v.y : 0.0f);
+        }
+        H = warp_sum(H);
+        if (TEAM > 1) {
+            if (lane == 0) s_red[12 + wit] = H;
+            team_sync<TEAM>(team);
+            H = 0.0f;
+            for (int w = 0; w < TEAM; ++w) H += s_red[12 + w];
+        }
+        const float E = S / H;
+        if (mine) {
+            const float vv[2] = {v.x, v.y};
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = 2 * t + hh;
+                if (i >= n_s) continue;
+                const float mu = E * vv[hh];
+                const float s = sg[i];
+                ll += s > 0.0f ? fmaf(s, logf(mu / s), s - mu) + poisson_const(s) : -mu;
+            }
+        }
+        ll = warp_sum(ll);
+        if (TEAM > 1) {
+            if (lane == 0) s_red[16 + wit] = ll;
+            team_sync<TEAM>(team);
+            ll = 0.0f;
+            for (int w = 0; w < TEAM; ++w) ll += s_red[16 + w];
+        }
+        if (t == 0) {
+            a.xyz[3 * e] = cx;
+            a.xyz[3 * e + 1] = cy;
+            a.xyz[3 * e + 2] = cz;
+            a.E[e] = E;
+            a.logL[e] = ll;
+            a.status[e] = ANTS_EVT_OK;
+        }
+        team_sync<TEAM>(team);  // s_red and the weights are reused by the next event
+    }
+}
+
+// the patch kernel serves an XY LRF whose table stays in global memory, with
+// at most 128 sensor pairs, when every grid of the search touches at most
+// kPatch coefficients per axis
+bool patch_fits(const ants_lrf *lrf, const ants_cgs_params &p)
+{
+    if (!lrf->dev.coef2_pf || p.n_xy != 5 || lrf->dev.n_pairs > 128 || !(p.shrink > 0.0f && p.shrink <= 1.0f))
+        return false;
+    // a range of R covers at most floor(R/h) + 2 spans: patch <= floor(R/h) + 5
+    const double R = (double)(p.n_xy - 1) * p.step_xy;
+    const double hx = 1.0 / lrf->dev.inv_h[0], hy = 1.0 / lrf->dev.inv_h[1];
+    return std::floor(R / hx + 1e-3) + 5 <= kPatch && std::floor(R / hy + 1e-3) + 5 <= kPatch;
+}
+
+template <int N, int TEAM, bool FLOOR>
+int launch_patch(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
+{
+    constexpr int LT = 32 * TEAM;
+    const int teams = kPatchThreads / LT;
+    const size_t smem = (size_t)teams * PatchSmem<N>::total(LT) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(cgs_xy_patch_kernel<N, TEAM, FLOOR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_xy_patch)");
+    long blocks = (a.n_e + teams - 1) / teams;
+    const long cap = (long)ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    cgs_xy_patch_kernel<N, TEAM, FLOOR><<<(unsigned)blocks, kPatchThreads, smem, stream>>>(a, teams);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cgs_xy_patch_kernel launch");
+    count_launch();
+    return ANTS_OK;
+}
+
+template <bool FLOOR>
+int launch_patch_n5(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
+{
+    const int np = a.L.n_pairs;
+    if (np <= 32) return launch_patch<5, 1, FLOOR>(ctx, a, stream);
+    if (np <= 64) return launch_patch<5, 2, FLOOR>(ctx, a, stream);
+    return launch_patch<5, 4, FLOOR>(ctx, a, stream);
+}
+
 template <int N, int TEAM>
 int launch_nt(const ants_ctx *ctx, const XyArgs &a, bool floor_needed, cudaStream_t stream)
 {
@@ -640,6 +1024,10 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     // the floor is needed when an LRF value can be <= 0, or to neutralise the
     // zero-coefficient padding sensor of an odd sensor count
     bool floor_needed = !lrf->dev.positive || (lrf->n_s & 1);
+    // tables too large for shared memory: small grids take the patch kernel
+    const size_t table_bytes = (size_t)lrf->dev.n_pairs * lrf->dev.pair_stride * sizeof(float2);
+    if (table_bytes + 4096 > ctx->smem_optin && patch_fits(lrf, p))
+        return floor_needed ? launch_patch_n5<true>(ctx, a, stream) : launch_patch_n5<false>(ctx, a, stream);
     switch (p.n_xy) {
     case 5: return launch_nt<5, 1>(ctx, a, floor_needed, stream);
     case 7: return launch_nt<7, 1>(ctx, a, floor_needed, stream);

@@ -47,6 +47,9 @@ struct LrfDev {
     // XY LRFs: sensors interleaved in pairs, [n_pairs][n_int[1]+3][n_int[0]+3]
     // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
     const float2 *coef2;
+    // XY LRFs: the same pairs with the pair index fastest, [n_int[1]+3][n_int[0]+3][n_pairs]
+    // float2 (a warp whose lanes take consecutive pairs reads one contiguous run)
+    const float2 *coef2_pf;
     const float *coef_t;   // XY: the coefficients sensor-minor, [k][n_s] (per-point loops over sensors)
     const int *set_of;     // RADIAL grouped / XY symmetry classes (Sec. 6.2): the coefficient set of each sensor; nullable
     int n_sets;            // coefficient sets
@@ -112,6 +115,7 @@ struct ants_lrf {
     int n_planes = 0;              // SLICED
     float *d_coef = nullptr, *d_sxy = nullptr, *d_gain = nullptr, *d_cogw = nullptr;
     float2 *d_coef2 = nullptr;
+    float2 *d_coef2_pf = nullptr;
     float *d_coeft = nullptr;
     int *d_set_of = nullptr;
     std::vector<int> groups;       // RADIAL grouped / XY classes: the group of each sensor (empty otherwise)

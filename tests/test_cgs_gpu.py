@@ -228,6 +228,45 @@ def test_cgs_xy_table_in_global_memory(torch_cuda, ctx):
     print(stats)
 
 
+@pytest.mark.parametrize("side,pitch,n_int,step", [(16, 3.2, 32, 0.5), (15, 3.2, 30, 0.3), (10, 6.0, 48, 0.5),
+                                                  (7, 6.0, 48, 0.4)])
+def test_cgs_xy_patch_kernel(torch_cuda, ctx, side, pitch, n_int, step):
+    """5 x 5 grids on a coefficient table larger than shared memory take the
+    patch kernel (a team of warps per event, one sensor pair per lane): 16 x 16
+    and 15 x 15 SiPMs (teams of four warps; 15 x 15 is odd: one padding
+    sensor), 10 x 10 (two warps) and 7 x 7 (one warp, odd) on fine knot grids;
+    starts near the sources, on the edges and in the corners of the field of
+    view, and a zero-signal event."""
+    sxy = synth.square_array(side, pitch)
+    half = 0.5 * pitch * side
+    w = synth.workloads.sipm16x16_xy().with_(
+        name=f"sipm{side}x{side}", sensor_xy=sxy, gains=synth.sensor_gains(side * side, 0.05, 9 + side),
+        lo=(-half, -half), hi=(half, half), n_int=(n_int, n_int), n_xy=5, iters=4, step_xy=step,
+        event=dict(region="square", extent=half - 0.5 * pitch, e0=2000.0))
+    L = oracle_lrf(w)
+    _, det, lrf, p = gpu_objects(w, L, ctx)
+    n = 301
+    ev = w.events(n, seed=40 + side)
+    sig = ev.signals.copy()
+    sig[7] = 0.0
+    rng = np.random.default_rng(side)
+    start = ev.xyz.copy()
+    start[:, :2] += rng.normal(0.0, 0.4, (n, 2))
+    start[:8, :2] = [[half, half], [-half, -half], [half, -half], [-half, half], [half, 0.0], [0.0, -half],
+                     [half - 0.2, half - 0.7], [0.0, 0.0]]
+    # starts in single precision inside the box (25.6 rounds up in FP32)
+    s32 = np.clip(start, -half, half).astype(np.float32)
+    out = np.abs(s32.astype(np.float64)) > half
+    s32[out] = np.nextafter(s32[out], np.float32(0.0))
+    start = s32.astype(np.float64)
+    start[:, 2] = 0.0
+    gpu = run_gpu(torch_cuda, ctx, lrf, p, sig, start=start)
+    assert gpu["status"][7] == 2
+    stats = compare(w, L, sig, gpu, start=start)
+    print(side, n_int, step, stats)
+    assert stats["tie_frac"] < 0.05
+
+
 def test_cgs_xyz_parity(torch_cuda, ctx):
     w = synth.workloads.get("sipm4x4_xyz")
     L = oracle_lrf(w)
