@@ -343,6 +343,29 @@ ANTS_API int ants_ctx_fault(ants_ctx *ctx, int *fault);
  * ANTS_E_INTERNAL otherwise; it clears the fault word. */
 ANTS_API int ants_selftest_stalled_product(ants_ctx *ctx);
 
+/* Build options of the loaded library (no counterpart in the paper):
+ * ANTS_BUILD_DEBUG_BOUNDS set when it was compiled with ANTS_DEBUG_BOUNDS. */
+#define ANTS_BUILD_DEBUG_BOUNDS 1
+ANTS_API int ants_build_flags(void);
+
+/* Index checks of the ANTS_DEBUG_BOUNDS build (no counterpart in the paper;
+ * it stands in for a memory checker).  In that build the search kernels
+ * (separable XY team kernel, small-grid patch kernel) and the tensor-core
+ * product check their shared-memory, tensor-memory and global indices against
+ * the buffers' extents; an index out of range is not accessed, and the number
+ * of the first failing check site goes to a per-context device word, after
+ * which ants_reconstruct, ants_logtable_topk and ants_mlp_train return
+ * ANTS_E_INTERNAL (they synchronise in that build).  This call synchronises
+ * the device, stores the recorded site in *site (0: none; always 0 in the
+ * normal build) and clears it.  Errors: ANTS_E_ARG, ANTS_E_CUDA. */
+ANTS_API int ants_debug_bounds_site(ants_ctx *ctx, int *site);
+
+/* Self-test of the index checks (no counterpart in the paper): one thread
+ * checks the index 7 against an extent of 5 at site 9999 and performs no
+ * access.  The debug build must then report site 9999 through
+ * ants_debug_bounds_site; the normal build reports 0.  Synchronous. */
+ANTS_API int ants_selftest_bounds(ants_ctx *ctx);
+
 /* ------------------------------------------------------------------------ */
 /* Detector definition (Sec. 2 "detector definitions"; Sec. 5.1.1 gains)      */
 /* ------------------------------------------------------------------------ */

@@ -19,7 +19,9 @@ import numpy as np
 
 from . import _build
 
-LIB_PATH = _build.LIB
+# the library to load: the in-tree build, or another build of the same sources
+# named by ANTS_LIBRARY (the index-checking ANTS_DEBUG_BOUNDS build, _build.DEBUG_LIB)
+LIB_PATH = os.environ.get("ANTS_LIBRARY") or _build.LIB
 
 # enums of include/ants.h
 ANTS_OK = 0
@@ -41,6 +43,7 @@ ANTS_START_COG, ANTS_START_MAX_SENSOR = 0, 1
 ANTS_F32 = 0
 ANTS_F16 = 1
 ANTS_NOALLOC_STAGE_BYTES = 33554432
+ANTS_BUILD_DEBUG_BOUNDS = 1
 
 _STATUS_NAMES = {0: "ANTS_OK", -1: "ANTS_E_ARG", -2: "ANTS_E_CUDA", -3: "ANTS_E_OOM", -4: "ANTS_E_LRF",
                  -5: "ANTS_E_SHAPE", -6: "ANTS_E_TIMEOUT", -7: "ANTS_E_INTERNAL", -8: "ANTS_E_UNIMPLEMENTED",
@@ -223,6 +226,9 @@ def lib() -> C.CDLL:
         L.ants_ctx_destroy.restype = None
         L.ants_ctx_fault.argtypes = [_VP, C.POINTER(C.c_int)]
         L.ants_selftest_stalled_product.argtypes = [_VP]
+        L.ants_build_flags.restype = C.c_int
+        L.ants_debug_bounds_site.argtypes = [_VP, C.POINTER(C.c_int)]
+        L.ants_selftest_bounds.argtypes = [_VP]
         L.ants_detector_create.argtypes = [C.c_int, _DP, _DP, C.POINTER(_VP)]
         L.ants_detector_free.argtypes = [_VP]
         L.ants_detector_free.restype = None
@@ -389,6 +395,22 @@ def ants_ctx_fault(ctx: int) -> int:
     f = C.c_int(0)
     _check(lib().ants_ctx_fault(ctx, C.byref(f)))
     return f.value
+
+
+def ants_build_flags() -> int:
+    return int(lib().ants_build_flags())
+
+
+def ants_debug_bounds_site(ctx: int) -> int:
+    """Site of the first out-of-range index a checked kernel recorded (0: none),
+    then cleared; always 0 in the normal build."""
+    site = C.c_int(0)
+    _check(lib().ants_debug_bounds_site(ctx, C.byref(site)))
+    return site.value
+
+
+def ants_selftest_bounds(ctx: int) -> None:
+    _check(lib().ants_selftest_bounds(ctx))
 
 
 def ants_selftest_stalled_product(ctx: int) -> None:

@@ -91,6 +91,37 @@ int widen_half(const __half *h, size_t n, float *f, cudaStream_t s)
 
 using namespace ants;
 
+namespace ants {
+namespace {
+
+__global__ void bounds_selftest_kernel(int *word)
+{
+    if (ANTS_IN_RANGE(word, 7, 5, 9999)) {
+        // an access would go here; the check keeps it from happening
+    }
+}
+
+}  // namespace
+}  // namespace ants
+
+namespace ants {
+
+int check_bounds(const ants_ctx *ctx, cudaStream_t s)
+{
+#ifdef ANTS_DEBUG_BOUNDS
+    int site = 0;
+    ANTS_CUDA_TRY(cudaStreamSynchronize(s), "index check: synchronize");
+    ANTS_CUDA_TRY(cudaMemcpy(&site, ctx->d_bounds, sizeof(int), cudaMemcpyDeviceToHost), "index check: read");
+    if (site) return fail(ANTS_E_INTERNAL, "index check: an index out of range at site %d", site);
+#else
+    (void)ctx;
+    (void)s;
+#endif
+    return ANTS_OK;
+}
+
+}  // namespace ants
+
 extern "C" {
 
 ANTS_API const char *ants_last_error(void) { return t_err.c_str(); }
@@ -127,6 +158,8 @@ ANTS_API int ants_ctx_create(int device, ants_ctx **out)
     }
     e = cudaMalloc(&c->d_fault, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_fault, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bounds, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_bounds, 0, sizeof(int));
     if (e != cudaSuccess) { ants_ctx_destroy(c); return cuda_fail(e, "fault word"); }
     *out = c;
     return ANTS_OK;
@@ -155,6 +188,7 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     free_host_buffers(ctx);
     for (int k = 0; k < 13; ++k) cudaFree(ctx->scratch[k]);
     cudaFree(ctx->d_fault);
+    cudaFree(ctx->d_bounds);
     for (int k = 0; k < 2; ++k)
         if (ctx->stream[k]) cudaStreamDestroy(ctx->stream[k]);
     delete ctx;
@@ -170,6 +204,41 @@ ANTS_API int ants_ctx_fault(ants_ctx *ctx, int *fault)
     ANTS_CUDA_TRY(cudaMemset(ctx->d_fault, 0, sizeof(int)), "ants_ctx_fault: clear");
     return *fault ? fail(ANTS_E_TIMEOUT, "a device-side wait ran out of time") : ANTS_OK;
 }
+
+ANTS_API int ants_build_flags(void)
+{
+#ifdef ANTS_DEBUG_BOUNDS
+    return ANTS_BUILD_DEBUG_BOUNDS;
+#else
+    return 0;
+#endif
+}
+
+ANTS_API int ants_debug_bounds_site(ants_ctx *ctx, int *site)
+{
+    begin_call();
+    if (!ctx || !site) return fail(ANTS_E_ARG, "ants_debug_bounds_site: NULL argument");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ANTS_CUDA_TRY(cudaDeviceSynchronize(), "ants_debug_bounds_site: synchronize");
+    ANTS_CUDA_TRY(cudaMemcpy(site, ctx->d_bounds, sizeof(int), cudaMemcpyDeviceToHost), "ants_debug_bounds_site: read");
+    ANTS_CUDA_TRY(cudaMemset(ctx->d_bounds, 0, sizeof(int)), "ants_debug_bounds_site: clear");
+    return ANTS_OK;
+}
+
+
+ANTS_API int ants_selftest_bounds(ants_ctx *ctx)
+{
+    using namespace ants;
+    begin_call();
+    if (!ctx) return fail(ANTS_E_ARG, "ants_selftest_bounds: NULL context");
+    ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    bounds_selftest_kernel<<<1, 1>>>(ctx->d_bounds);
+    ANTS_CUDA_TRY(cudaGetLastError(), "bounds self-test launch");
+    ANTS_CUDA_TRY(cudaDeviceSynchronize(), "bounds self-test");
+    return ANTS_OK;
+}
+
+
 
 // ---------------------------------------------------------------------------
 // detector
@@ -234,6 +303,7 @@ static int upload_lrf(ants_lrf *L)
     ANTS_CUDA_TRY(cudaMemcpy(L->d_cogw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice),
                   "upload cog weights");
     LrfDev &D = L->dev;
+    D.dbg = L->ctx->d_bounds;
     D.coef2 = nullptr;
     D.coef2_pf = nullptr;
     D.coef_t = nullptr;
@@ -647,6 +717,7 @@ ANTS_API int ants_lrf_eval(const ants_lrf *lrf, const float *pts_dev, long n_pts
                            float *out_dev, void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_lrf_eval");
     if (!lrf) return fail(ANTS_E_ARG, "ants_lrf_eval: lrf is NULL");
     if (n_pts < 0) return fail(ANTS_E_ARG, "ants_lrf_eval: n_pts < 0");
     int need = lrf_is_3d(lrf->type) ? 3 : 2;
@@ -767,12 +838,11 @@ static int reconstruct_f32(ants_ctx *ctx, const ants_lrf *lrf, int method, const
                             logL_dev, status_dev, trace_dev, stream);
 }
 
-ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+static int reconstruct_device(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
                               const void *signals_dev, int signal_dtype, long n_events, int n_sensors,
                               const float *start_xyz_dev, float *xyz_dev, float *E_dev, float *logL_dev,
                               int32_t *status_dev, int16_t *trace_dev, void *stream)
 {
-    begin_call();
     int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
     if (rc != ANTS_OK) return rc;
     if (n_events == 0) return ANTS_OK;
@@ -811,12 +881,26 @@ ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, co
     return ANTS_OK;
 }
 
+ANTS_API int ants_reconstruct(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
+                              const void *signals_dev, int signal_dtype, long n_events, int n_sensors,
+                              const float *start_xyz_dev, float *xyz_dev, float *E_dev, float *logL_dev,
+                              int32_t *status_dev, int16_t *trace_dev, void *stream)
+{
+    begin_call();
+    ANTS_NVTX("ants_reconstruct");
+    int rc = reconstruct_device(ctx, lrf, method, params, signals_dev, signal_dtype, n_events, n_sensors,
+                                start_xyz_dev, xyz_dev, E_dev, logL_dev, status_dev, trace_dev, stream);
+    if (rc == ANTS_OK && ctx && n_events > 0) rc = check_bounds(ctx, (cudaStream_t)stream);
+    return rc;
+}
+
 ANTS_API int ants_reconstruct_host(ants_ctx *ctx, const ants_lrf *lrf, int method, const void *params,
                                    const void *signals_host, int signal_dtype, long n_events,
                                    int n_sensors, const float *start_xyz_host, float *xyz_host,
                                    float *E_host, float *logL_host, int32_t *status_host)
 {
     begin_call();
+    ANTS_NVTX("ants_reconstruct_host");
     int rc = check_common(ctx, lrf, method, params, signal_dtype, n_events, n_sensors);
     if (rc != ANTS_OK) return rc;
     if (n_events == 0) return ANTS_OK;

@@ -936,6 +936,7 @@ ANTS_API int ants_batch_plan_create(ants_ctx *ctx, int n_items, const ants_batch
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_batch_plan_create");
     if (!out) return fail(ANTS_E_ARG, "ants_batch_plan_create: out is NULL");
     *out = nullptr;
     if (!ctx || n_items < 1 || n_items > 4096 || !items) return fail(ANTS_E_ARG, "ants_batch_plan_create: bad items");
@@ -974,6 +975,7 @@ ANTS_API int ants_batch_run(ants_batch_plan *P, void *stream)
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_batch_run");
     if (!P || !P->exec) return fail(ANTS_E_ARG, "ants_batch_run: no plan");
     ANTS_CUDA_TRY(cudaSetDevice(P->ctx->device), "cudaSetDevice");
     ANTS_CUDA_TRY(cudaGraphLaunch(P->exec, (cudaStream_t)stream), "graph launch");
@@ -995,6 +997,7 @@ ANTS_API int ants_batch_autotune(ants_batch_plan *P, const char *cache_path, lon
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_batch_autotune");
     if (!P) return fail(ANTS_E_ARG, "ants_batch_autotune: no plan");
     if (events_per_item < 1) events_per_item = 2048;
     ANTS_CUDA_TRY(cudaSetDevice(P->ctx->device), "cudaSetDevice");

@@ -130,6 +130,9 @@ __device__ __forceinline__ float2 pair_eta(const LrfDev &L, const float2 *coef2,
     bs_weights(ty, wy);
     const float2 *c = coef2 + (size_t)p * L.pair_stride + jy * L.stride_y + jx;
     float2 f = make_float2(0.0f, 0.0f);
+    const long lo_i = c - coef2, n_tab = (long)L.n_pairs * L.pair_stride;
+    if (!ANTS_IN_RANGE(L.dbg, lo_i, n_tab, 101) || !ANTS_IN_RANGE(L.dbg, lo_i + 3 * L.stride_y + 3, n_tab, 102))
+        return f;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const float2 *row = c + b * L.stride_y;
@@ -144,8 +147,10 @@ __device__ __forceinline__ float2 pair_eta(const LrfDev &L, const float2 *coef2,
 // x-contracted row: sum_b wx[b] C[r][ix+b] for both sensors of a pair;
 // `g` / `sa` address C[r][ix] (global pointer / shared byte address)
 template <bool SMEM>
-__device__ __forceinline__ float2 trow(const float2 *g, unsigned sa, const float2 wx2[4])
+__device__ __forceinline__ float2 trow(const float2 *g, unsigned sa, const float2 wx2[4], const float2 *base, long n,
+                                       int *dbg)
 {
+    if (!ANTS_IN_RANGE(dbg, g - base, n - 3, 103)) return make_float2(0.0f, 0.0f);
     float2 v = fmul2(wx2[0], ldc<SMEM>(g, sa));
     v = ffma2(wx2[1], ldc<SMEM>(g + 1, sa + 8), v);
     v = ffma2(wx2[2], ldc<SMEM>(g + 2, sa + 16), v);
@@ -200,6 +205,8 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     const size_t table = SMEM ? (size_t)n_pairs * L.pair_stride : 0;  // float2 entries
     float2 *cs = reinterpret_cast<float2 *>(smem_raw);
     const float2 *coef2 = L.coef2;
+    const long n_tab = (long)n_pairs * L.pair_stride;  // float2 entries of the table (index checks)
+    (void)n_tab;
     if (SMEM) {
         const float4 *src = reinterpret_cast<const float4 *>(L.coef2);
         float4 *dst = reinterpret_cast<float4 *>(cs);
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                     for (int m = 0; m < kPPL; ++m)
     #pragma unroll
                         for (int a4 = 0; a4 < 4; ++a4)
-                            W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2);
+                            W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2, coef2, n_tab, L.dbg);
     #pragma unroll 1
                     for (int k = 0; k < N; ++k) {
                         const int iyk = s_iy[k];
@@ -386,23 +393,23 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                                 W[m][0] = W[m][1];
                                 W[m][1] = W[m][2];
                                 W[m][2] = W[m][3];
-                                W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
+                                W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
                             }
                         } else if (adv == 2) {
     #pragma unroll
                             for (int m = 0; m < kPPL; ++m) {
                                 W[m][0] = W[m][2];
                                 W[m][1] = W[m][3];
-                                W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
-                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
+                                W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
                             }
                         } else if (adv == 3) {
     #pragma unroll
                             for (int m = 0; m < kPPL; ++m) {
                                 W[m][0] = W[m][3];
-                                W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2);
-                                W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2);
-                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2);
+                                W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
+                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2, coef2, n_tab, L.dbg);
                             }
                         } else if (adv >= 4) {
     #pragma unroll
@@ -410,7 +417,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     #pragma unroll
                                 for (int a4 = 0; a4 < 4; ++a4)
                                     W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
-                                                          wx2);
+                                                          wx2, coef2, n_tab, L.dbg);
                         }
                         top = iyk;
                         const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
@@ -451,7 +458,8 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                                 }
                             }
                         }
-                        if (TEAM == 1 || lane < N) {
+                        if ((TEAM == 1 || lane < N) &&
+                            ANTS_IN_RANGE(L.dbg, (N + k) * ps + (TEAM > 1 ? wit * N + j : t), 2 * N * ps, 104)) {
                             const int slot = TEAM > 1 ? wit * N + j : t;
                             float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
                             if (g > 0) {
@@ -734,7 +742,10 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                     float2 seg[kPatch];
 #pragma unroll
                     for (int c = 0; c < kPatch; ++c)
-                        seg[c] = c < pw ? __ldg(base + ((size_t)r * sy + c) * n_pairs) : make_float2(0.0f, 0.0f);
+                        seg[c] = c < pw && ANTS_IN_RANGE(L.dbg, ((long)(iy0 + r) * sy + ix0 + c) * n_pairs + pp,
+                                                         (long)(L.n_int[1] + 3) * sy * n_pairs, 201)
+                                     ? __ldg(base + ((size_t)r * sy + c) * n_pairs)
+                                     : make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int j = 0; j < N; ++j) {
                         float2 T = make_float2(0.0f, 0.0f);
@@ -777,8 +788,10 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                 }
                 const float2 tt = fmul2(sp, lg);
                 const float2 d = fadd2(v, nec);
-                s_part[q * RS + t] = tt.x + tt.y;
-                s_part[(NN + q) * RS + t] = mine ? d.x + d.y : 0.0f;
+                if (ANTS_IN_RANGE(L.dbg, (NN + q) * RS + t, Lay::wx(LT), 203)) {
+                    s_part[q * RS + t] = tt.x + tt.y;
+                    s_part[(NN + q) * RS + t] = mine ? d.x + d.y : 0.0f;
+                }
             }
             if (acc_log && __any_sync(kFull, far)) {
                 // rare: redo the nodes whose |u| is beyond the Taylor range
@@ -818,8 +831,10 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                 const int h = k >= 2 * NN, sigma = k - 2 * NN * h;
                 const float *src = s_part + sigma * RS + h * (LT / 2);
                 float v = 0.0f;
+                if (ANTS_IN_RANGE(L.dbg, sigma * RS + h * (LT / 2) + LT / 2 - 1, Lay::wx(LT), 204)) {
 #pragma unroll 16
-                for (int i = 0; i < LT / 2; ++i) v += src[i];
+                    for (int i = 0; i < LT / 2; ++i) v += src[i];
+                }
                 s_tot[k] = v;
             }
             team_sync<TEAM>(team);

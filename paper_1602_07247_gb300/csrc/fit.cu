@@ -697,6 +697,7 @@ extern "C" ANTS_API int ants_lrf_fit_symmetric(ants_ctx *ctx, const ants_detecto
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_lrf_fit_symmetric");
     if (!out) return fail(ANTS_E_ARG, "ants_lrf_fit_symmetric: out is NULL");
     *out = nullptr;
     if (!ctx || !det || !n_int || !lo || !hi || !class_host || !op_host || !centre ||
@@ -773,6 +774,7 @@ extern "C" ANTS_API int ants_lrf_fit(ants_ctx *ctx, const ants_detector *det, in
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_lrf_fit");
     if (!out) return fail(ANTS_E_ARG, "ants_lrf_fit: out is NULL");
     *out = nullptr;
     if (!ctx || !det || !n_int || !lo || !hi || (n_pts > 0 && (!pts_host || !vals_host)))

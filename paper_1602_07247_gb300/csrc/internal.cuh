@@ -5,6 +5,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdarg>
 #include <string>
 #include <vector>
@@ -28,6 +30,34 @@ void count_launch(long n = 1);
     } while (0)
 
 // ---------------------------------------------------------------------------
+// index checks of the ANTS_DEBUG_BOUNDS build: ANTS_IN_RANGE(word, i, n, site)
+// is true when 0 <= i < n; in that build an index outside the range records
+// `site` in *word (the first one wins) and the caller skips the access, so a
+// wrong index is reported instead of touching memory.  In the normal build the
+// macro is the constant true and every check compiles away.
+// ---------------------------------------------------------------------------
+#ifdef ANTS_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_in_range(int *word, long long i, long long n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    if (word) atomicCAS(word, 0, site);
+    return false;
+}
+#define ANTS_IN_RANGE(word, i, n, site) ::ants::dbg_in_range((word), (long long)(i), (long long)(n), (site))
+#else
+#define ANTS_IN_RANGE(word, i, n, site) true
+#endif
+
+// a named NVTX range over one library call (seen by profilers that record NVTX)
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+#define ANTS_NVTX(name) ::ants::NvtxScope ants_nvtx_scope_(name)
+
+// ---------------------------------------------------------------------------
 // device view of an LRF set, passed by value to kernels
 // ---------------------------------------------------------------------------
 struct LrfDev {
@@ -44,6 +74,7 @@ struct LrfDev {
     const float *sxy;  // [n_s][2]
     const float *gain; // [n_s] factor on a RADIAL LRF
     const float *cog_w;// [n_s] 1 / relative gain (centroid weights)
+    int *dbg;          // the context's index-check word (written only by the ANTS_DEBUG_BOUNDS build)
     // XY LRFs: sensors interleaved in pairs, [n_pairs][n_int[1]+3][n_int[0]+3]
     // float2 = (sensor 2p, sensor 2p+1); an odd count is padded with zeros
     const float2 *coef2;
@@ -92,6 +123,9 @@ struct ants_ctx {
     size_t scratch_cap[13] = {};
     // device word set by a kernel whose bounded wait ran out (ants_ctx_fault)
     int *d_fault = nullptr;
+    // device word of the ANTS_DEBUG_BOUNDS build: the site of the first index
+    // a checked kernel found out of range (ants_debug_bounds_site)
+    int *d_bounds = nullptr;
 };
 
 struct ants_detector {
@@ -212,6 +246,9 @@ int widen_half(const __half *h, size_t n, float *f, cudaStream_t s);
 int mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig, long n, bool bf, float *O, cudaStream_t s);
 int mlp_decode(const ants_mlp *M, const float *O, long n, float *xyz, float *E, cudaStream_t s);
 int mlp_n_in(const ants_mlp *M);
+// ANTS_DEBUG_BOUNDS build: wait for stream s and fail with ANTS_E_INTERNAL when
+// a checked kernel recorded an index out of range (a no-op otherwise)
+int check_bounds(const ants_ctx *ctx, cudaStream_t s);
 // tcgen05 products with fused epilogues (umma.cu); B [N][K] BF16, K <= 256
 // top-K: columns ranked by value, ties by order[n] (the grid index of column n)
 int mma_topk(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16 *B, const int *order, int M, int N,

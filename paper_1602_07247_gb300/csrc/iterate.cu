@@ -638,6 +638,7 @@ extern "C" ANTS_API int ants_event_centroid(ants_ctx *ctx, const ants_lrf *lrf, 
                                             long n_events, float *xyz_dev, float *sum_dev, void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_event_centroid");
     if (!ctx || !lrf || lrf->ctx != ctx || n_events < 0) return fail(ANTS_E_ARG, "ants_event_centroid: bad arguments");
     if (n_events == 0) return ANTS_OK;
     if (!signals_dev || !xyz_dev) return fail(ANTS_E_ARG, "ants_event_centroid: NULL buffer");
@@ -665,6 +666,7 @@ extern "C" ANTS_API int ants_event_chi2(ants_ctx *ctx, const ants_lrf *lrf, cons
                                         void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_event_chi2");
     if (!ctx || !lrf || lrf->ctx != ctx || n_events < 0) return fail(ANTS_E_ARG, "ants_event_chi2: bad arguments");
     if (n_events == 0) return ANTS_OK;
     if (!signals_dev || !xyz_dev || !E_dev || !chi2_dev) return fail(ANTS_E_ARG, "ants_event_chi2: NULL buffer");
@@ -682,6 +684,7 @@ extern "C" ANTS_API int ants_event_filter(ants_ctx *ctx, long n_events, const in
                                           long *n_kept_host, void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_event_filter");
     if (!ctx || n_events < 0 || !n_kept_host) return fail(ANTS_E_ARG, "ants_event_filter: bad arguments");
     IT_TRY(check_cuts(cuts));
     *n_kept_host = 0;
@@ -701,6 +704,7 @@ extern "C" ANTS_API int ants_lrf_refit(ants_ctx *ctx, const ants_lrf *lrf, const
                                        long n_kept, const ants_refit_params *p, ants_lrf **out)
 {
     begin_call();
+    ANTS_NVTX("ants_lrf_refit");
     if (!out) return fail(ANTS_E_ARG, "ants_lrf_refit: out is NULL");
     *out = nullptr;
     if (!ctx || !lrf || lrf->ctx != ctx) return fail(ANTS_E_ARG, "ants_lrf_refit: bad context or LRF");
@@ -718,6 +722,7 @@ extern "C" ANTS_API int ants_lrf_iterate(ants_ctx *ctx, const ants_lrf *lrf_init
                                          ants_lrf **out)
 {
     begin_call();
+    ANTS_NVTX("ants_lrf_iterate");
     if (!out) return fail(ANTS_E_ARG, "ants_lrf_iterate: out is NULL");
     *out = nullptr;
     if (!ctx || !lrf_init || lrf_init->ctx != ctx || !p) return fail(ANTS_E_ARG, "ants_lrf_iterate: bad arguments");

@@ -813,6 +813,7 @@ ANTS_API int ants_mlp_forward(ants_ctx *ctx, const ants_mlp *M, const float *sig
                               void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_mlp_forward");
     MLP_TRY(check_mlp(M, "ants_mlp_forward"));
     if (!ctx || M->ctx != ctx) return fail(ANTS_E_ARG, "ants_mlp_forward: network belongs to another context");
     if (n_sensors != M->n_in)
@@ -834,6 +835,7 @@ ANTS_API int ants_mlp_loss_grad(ants_ctx *ctx, const ants_mlp *M, const float *s
                                 long n_events, int n_sensors, int bf16, float *loss_host, float *grads_host)
 {
     begin_call();
+    ANTS_NVTX("ants_mlp_loss_grad");
     MLP_TRY(check_mlp(M, "ants_mlp_loss_grad"));
     if (!ctx || M->ctx != ctx) return fail(ANTS_E_ARG, "ants_mlp_loss_grad: network belongs to another context");
     if (n_sensors != M->n_in) return fail(ANTS_E_SHAPE, "ants_mlp_loss_grad: n_sensors %d", n_sensors);
@@ -885,6 +887,7 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
                             long n_events, int n_sensors, const ants_train_params *tp, ants_train_report *report)
 {
     begin_call();
+    ANTS_NVTX("ants_mlp_train");
     MLP_TRY(check_mlp(M, "ants_mlp_train"));
     if (!ctx || M->ctx != ctx || !tp) return fail(ANTS_E_ARG, "ants_mlp_train: bad ctx or params");
     if (n_sensors != M->n_in) return fail(ANTS_E_SHAPE, "ants_mlp_train: n_sensors %d", n_sensors);
@@ -989,6 +992,7 @@ ANTS_API int ants_mlp_train(ants_ctx *ctx, ants_mlp *M, const float *signals_dev
                   "restore best");
     M->bf16_stale = true;
     ANTS_CUDA_TRY(cudaStreamSynchronize(s), "mlp train");
+    MLP_TRY(check_bounds(ctx, s));
     if (report) {
         report->epochs_run = epochs_run;
         report->best_epoch = best_epoch;

@@ -355,6 +355,7 @@ extern "C" ANTS_API int ants_trace_photons(ants_ctx *ctx, const ants_optics_para
                                            int32_t *counts_dev, int16_t *outcome_dev, float *eta_dev, void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_trace_photons");
     if (!ctx || !P) return fail(ANTS_E_ARG, "ants_trace_photons: NULL ctx or params");
     if (n_src < 0 || n_photons < 0) return fail(ANTS_E_ARG, "ants_trace_photons: negative counts");
     if (n_src > 65535) return fail(ANTS_E_ARG, "ants_trace_photons: at most 65535 sources per call");

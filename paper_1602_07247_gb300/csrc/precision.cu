@@ -281,6 +281,7 @@ extern "C" {
 ANTS_API int ants_logtable_create(ants_ctx *ctx, const ants_lrf *lrf, int nx, int ny, ants_logtable **out)
 {
     begin_call();
+    ANTS_NVTX("ants_logtable_create");
     if (!out) return fail(ANTS_E_ARG, "ants_logtable_create: out is NULL");
     *out = nullptr;
     if (!ctx || !lrf || lrf->ctx != ctx) return fail(ANTS_E_ARG, "ants_logtable_create: bad ctx or lrf");
@@ -348,14 +349,17 @@ ANTS_API int ants_logtable_topk(ants_ctx *ctx, const ants_logtable *T, const flo
                                 int n_sensors, int top_k, float *score_dev, int32_t *index_dev, void *stream)
 {
     begin_call();
+    ANTS_NVTX("ants_logtable_topk");
     if (!ctx || !T || T->ctx != ctx) return fail(ANTS_E_ARG, "ants_logtable_topk: bad ctx or table");
     if (n_sensors != T->n_s) return fail(ANTS_E_SHAPE, "ants_logtable_topk: n_sensors %d", n_sensors);
     if (n_events < 0 || n_events > (1L << 30)) return fail(ANTS_E_ARG, "ants_logtable_topk: n_events out of range");
     if (n_events == 0) return ANTS_OK;
     if (!signals_dev || !score_dev || !index_dev) return fail(ANTS_E_ARG, "ants_logtable_topk: NULL buffer");
     ANTS_CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
-    return mma_topk(ctx, signals_dev, true, T->d_Tp, T->d_order, (int)n_events, T->nx * T->ny, T->n_s, top_k,
-                    score_dev, index_dev, (cudaStream_t)stream);
+    int rc = mma_topk(ctx, signals_dev, true, T->d_Tp, T->d_order, (int)n_events, T->nx * T->ny, T->n_s, top_k,
+                      score_dev, index_dev, (cudaStream_t)stream);
+    if (rc == ANTS_OK) rc = check_bounds(ctx, (cudaStream_t)stream);
+    return rc;
 }
 
 ANTS_API void ants_logtable_free(ants_logtable *T)

@@ -217,6 +217,7 @@ extern "C" ANTS_API int ants_lrf_fit_scheme(ants_ctx *ctx, const ants_detector *
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_lrf_fit_scheme");
     if (!out) return fail(ANTS_E_ARG, "ants_lrf_fit_scheme: out is NULL");
     *out = nullptr;
     if (!ctx || !det || !n_int || !lo || !hi || (n_pts > 0 && (!pts_host || !vals_host)))

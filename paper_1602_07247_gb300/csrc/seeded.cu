@@ -203,6 +203,7 @@ extern "C" ANTS_API int ants_deviance(ants_ctx *ctx, const ants_lrf *lrf, const 
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_deviance");
     if (!ctx || !lrf || lrf->ctx != ctx) return fail(ANTS_E_ARG, "ants_deviance: bad ctx or lrf");
     if (n_sensors != lrf->n_s) return fail(ANTS_E_SHAPE, "ants_deviance: n_sensors %d", n_sensors);
     if (n_events < 0) return fail(ANTS_E_ARG, "ants_deviance: n_events < 0");

@@ -130,6 +130,7 @@ extern "C" ANTS_API int ants_simulate_events(ants_ctx *ctx, const ants_lrf *lrf,
 {
     using namespace ants;
     begin_call();
+    ANTS_NVTX("ants_simulate_events");
     if (!ctx || !lrf || !params || lrf->ctx != ctx) return fail(ANTS_E_ARG, "ants_simulate_events: bad arguments");
     if (n_events < 0 || first_event < 0) return fail(ANTS_E_ARG, "ants_simulate_events: negative count");
     const ants_sim_params &p = *params;

@@ -83,6 +83,7 @@ struct UmmaArgs {
     __nv_bfloat16 *out_t;      // transposed BF16 copy [N][ldT] (nullable)
     int ldT;
     int *fault;
+    int *dbg;                  // index-check word (ANTS_DEBUG_BOUNDS build)
     int hold_producer;  // self-test only: the TMA producer issues nothing
 };
 
@@ -329,7 +330,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                         ok = bar_wait(b_empty(s), ph ^ 1, abort, a.fault);
                         if (!ok) break;
                         bar_expect_tx(b_full(s), kBStageBytes);
-                        tma_load_2d(sB + s * kBStageBytes, &tmB, kc * kBK, nt * kBN, b_full(s));
+                        if (ANTS_IN_RANGE(a.dbg, s, kStages, 302))
+                            tma_load_2d(sB + s * kBStageBytes, &tmB, kc * kBK, nt * kBN, b_full(s));
                         issued |= 1u << s;
                         issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
                         if (++s == kStages) {
@@ -369,8 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                         tc_fence_after();
                         const int ksteps = min(kBK / 16, (a.K - kc * kBK + 15) / 16);
                         for (int ks = 0; ks < ksteps; ++ks)
-                            umma(d, sdesc(sA + c * kAChunkBytes + ks * 32), sdesc(sB + s * kBStageBytes + ks * 32),
-                                 (kc | ks) != 0);
+                            if (ANTS_IN_RANGE(a.dbg, c * kAChunkBytes + ks * 32, kAChunks * kAChunkBytes, 303) &&
+                                ANTS_IN_RANGE(a.dbg, ab * kBN + kBN - 1, 512, 304))
+                                umma(d, sdesc(sA + c * kAChunkBytes + ks * 32), sdesc(sB + s * kBStageBytes + ks * 32),
+                                     (kc | ks) != 0);
                         umma_commit(b_empty(s));
                         if (nt == n_nt - 1) umma_commit(a_empty(c));
                         if (++s == kStages) {
@@ -444,9 +448,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                     for (int q = 0; q < 4; ++q) {
                         const int item = lt + 128 * (4 * half + q), r = item >> 3, c8 = item & 7;
                         const uint32_t dst = sA + c * kAChunkBytes + r * 128 + ((c8 ^ (r & 7)) << 4);
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
-                                     "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
-                                     : "memory");
+                        if (ANTS_IN_RANGE(a.dbg, dst - sA + 15, kAChunks * kAChunkBytes, 301))
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(packed[q].x),
+                                         "r"(packed[q].y), "r"(packed[q].z), "r"(packed[q].w)
+                                         : "memory");
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -489,7 +494,12 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                 for (int h = 0; h < kGroupCols / 32; ++h) {
                     const int col0 = grp * kGroupCols + h * 32;
                     uint32_t v[32];
-                    tmem_ld32(tl + (uint32_t)(ab * kBN + col0), v);
+                    if (ANTS_IN_RANGE(a.dbg, ab * kBN + col0 + 31, 512, 305)) {
+                        tmem_ld32(tl + (uint32_t)(ab * kBN + col0), v);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] = 0u;
+                    }
                     if (h == kGroupCols / 32 - 1) {
                         tc_fence_before();
                         bar_arrive(acc_empty(ab));
@@ -512,7 +522,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                         }
                         if (__any_sync(0xffffffffu, mask != 0)) {
 #pragma unroll
-                            for (int q = 0; q < 32; ++q) cand[q * kEpiThreads + et] = __uint_as_float(v[q]);
+                            for (int q = 0; q < 32; ++q)
+                                if (ANTS_IN_RANGE(a.dbg, q * kEpiThreads + et, kChunk * kEpiThreads, 306))
+                                    cand[q * kEpiThreads + et] = __uint_as_float(v[q]);
                             // the warp drains its lanes' candidates together
                             while (__any_sync(0xffffffffu, mask != 0)) {
                                 if (mask) {
@@ -538,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                             const int n = n0 + q;
                             const float c = __uint_as_float(v[q]);
                             float o = 0.0f;
-                            if (in_row && n < a.N) {
+                            if (in_row && n < a.N && ANTS_IN_RANGE(a.dbg, (long)m * a.N + n, (long)a.M * a.N, 309)) {
                                 const size_t at = (size_t)m * a.N + n;
                                 if (EPI == EPI_SAVE) {
                                     const float z = c + __ldg(a.bias + n);
@@ -552,7 +564,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                                     a.out_f[at] = o;
                                 }
                             }
-                            if (tr && n < a.N) a.out_t[(size_t)n * a.ldT + m] = __float2bfloat16_rn(o);
+                            if (tr && n < a.N && ANTS_IN_RANGE(a.dbg, (long)n * a.ldT + m, (long)a.N * a.ldT, 310))
+                                a.out_t[(size_t)n * a.ldT + m] = __float2bfloat16_rn(o);
                             if (EPI == EPI_SAVE) {
                                 if (q & 1) {
                                     __nv_bfloat162 hh = __floats2bfloat162_rn(prev, o);
@@ -564,7 +577,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                         }
                         if (EPI == EPI_SAVE && in_row) {
                             __nv_bfloat16 *o = a.out + (size_t)m * a.N + n0;
-                            for (int q = 0; q < 4 && 8 * q < a.N - n0; ++q)
+                            for (int q = 0; q < 4 && 8 * q < a.N - n0 &&
+                                            ANTS_IN_RANGE(a.dbg, (long)m * a.N + n0 + 8 * q + 7, (long)a.M * a.N, 311);
+                                 ++q)
                                 reinterpret_cast<uint4 *>(o)[q] =
                                     make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                         }
@@ -580,7 +595,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                             pk[q] = *reinterpret_cast<uint32_t *>(&hh);
                         }
                         __nv_bfloat16 *o = a.out + (size_t)m * a.N + n0;
-                        for (int q = 0; q < 4 && 8 * q < a.N - n0; ++q)
+                        for (int q = 0; q < 4 && 8 * q < a.N - n0 &&
+                                        ANTS_IN_RANGE(a.dbg, (long)m * a.N + n0 + 8 * q + 7, (long)a.M * a.N, 308);
+                             ++q)
                             reinterpret_cast<uint4 *>(o)[q] =
                                 make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                     }
@@ -608,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                                 reg_insert(tv, tn, x, n, a.order);
                         }
                     bar_arrive(mrg_empty);
-                    if (m < a.M)
+                    if (m < a.M && ANTS_IN_RANGE(a.dbg, (long)m * a.topk + a.topk - 1, (long)a.M * a.topk, 307))
 #pragma unroll
                         for (int q = 0; q < kMaxTop; ++q)
                             if (q < a.topk) {
@@ -715,6 +732,7 @@ int mma_topk(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfloat16
     a.top_val = val;
     a.top_idx = idx;
     a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
     return a_f32 ? launch<EPI_TOPK, true>(ctx, map, a, s) : launch<EPI_TOPK, false>(ctx, map, a, s);
 }
 
@@ -736,6 +754,7 @@ int mma_bias_gelu(const ants_ctx *ctx, const void *A, bool a_f32, const __nv_bfl
     a.bias = bias;
     a.out = out;
     a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
     return a_f32 ? launch<EPI_BIAS_GELU, true>(ctx, map, a, s) : launch<EPI_BIAS_GELU, false>(ctx, map, a, s);
 }
 
@@ -761,6 +780,7 @@ int mma_train_forward(const ants_ctx *ctx, const void *A, bool a_f32, const __nv
     a.out_t = hT;
     a.ldT = ldT;
     a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
     return a_f32 ? launch<EPI_SAVE, true>(ctx, map, a, s) : launch<EPI_SAVE, false>(ctx, map, a, s);
 }
 
@@ -784,6 +804,7 @@ int mma_gelu_backward(const ants_ctx *ctx, const float *dY, const __nv_bfloat16 
     a.out_t = dzT;
     a.ldT = ldT;
     a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
     return launch<EPI_GELU_BWD, true>(ctx, map, a, s);
 }
 
@@ -803,6 +824,7 @@ int mma_f32(const ants_ctx *ctx, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
     a.A = A;
     a.out_f = C;
     a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
     return launch<EPI_F32, false>(ctx, map, a, s);
 }
 
@@ -856,6 +878,7 @@ extern "C" ANTS_API int ants_selftest_stalled_product(ants_ctx *ctx)
         a.top_val = val;
         a.top_idx = idx;
         a.fault = ctx->d_fault;
+    a.dbg = ctx->d_bounds;
         a.hold_producer = 1;
         rc = launch<EPI_TOPK, true>(ctx, map, a, nullptr);
         if (rc == ANTS_OK) {
