@@ -614,6 +614,9 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NN = N * N, C = (N - 1) / 2, LT = 32 * TEAM;
+    // grid columns in register groups: all of a 5 x 5 grid at once; a 7 x 7 grid as
+    // columns C-1..C+1 (holding the centre, needed first), then 0..C-2, then C+2..
+    constexpr int NG = N <= 5 ? 1 : 3, JG = N <= 5 ? N : 3;
     using Lay = PatchSmem<N>;
     const LrfDev &L = a.L;
     const int n_s = L.n_s, n_pairs = L.n_pairs, sy = L.stride_y;
@@ -726,79 +729,108 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
             }
             team_sync<TEAM>(team);
 
-            // ---- this lane's pair at every node --------------------------------
-            float wx[N][kPatch];
-#pragma unroll
-            for (int j = 0; j < N; ++j)
-#pragma unroll
-                for (int c = 0; c < kPatch; ++c) wx[j][c] = s_wx[j * kPatch + c];
-            float2 eta[NN];
-#pragma unroll
-            for (int q = 0; q < NN; ++q) eta[q] = make_float2(0.0f, 0.0f);
+            // ---- this lane's pair at every node, by groups of JG columns (the
+            //      node accumulators of a group stay in registers) ------------
             const float2 *base = cpf + ((size_t)iy0 * sy + ix0) * n_pairs + pp;
-#pragma unroll
-            for (int r = 0; r < kPatch; ++r) {
-                if (r < ph) {
-                    float2 seg[kPatch];
-#pragma unroll
-                    for (int c = 0; c < kPatch; ++c)
-                        seg[c] = c < pw && ANTS_IN_RANGE(L.dbg, ((long)(iy0 + r) * sy + ix0 + c) * n_pairs + pp,
-                                                         (long)(L.n_int[1] + 3) * sy * n_pairs, 201)
-                                     ? __ldg(base + ((size_t)r * sy + c) * n_pairs)
-                                     : make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int j = 0; j < N; ++j) {
-                        float2 T = make_float2(0.0f, 0.0f);
-#pragma unroll
-                        for (int c = 0; c < kPatch; ++c) T = ffma2(make_float2(wx[j][c], wx[j][c]), seg[c], T);
-#pragma unroll
-                        for (int k = 0; k < N; ++k) {
-                            const float w = s_wy[r * N + k];
-                            eta[k * N + j] = ffma2(make_float2(w, w), T, eta[k * N + j]);
-                        }
-                    }
-                }
-            }
-            float2 ec = eta[C * N + C];
-            if (FLOOR) {
-                ec.x = fmaxf(ec.x, kEtaFloor);
-                ec.y = fmaxf(ec.y, kEtaFloor);
-            }
-            float hc = mine ? ec.x + (2 * t + 1 < n_s ? ec.y : 0.0f) : 0.0f;
-            const float2 ic = make_float2(__frcp_rn(ec.x), __frcp_rn(ec.y));
-            const float2 nec = make_float2(-ec.x, -ec.y);
+            const int row_step = sy * n_pairs;  // float2 entries per table row (< 2^31)
             const bool acc_log = sxy * (float)C <= a.prec_halfwidth;
             constexpr int RS = LT + 1;
             bool far = false;  // some |u| beyond the Taylor range (accurate grids)
+            float hc = 0.0f;
+            float2 ic = make_float2(0.0f, 0.0f), nec = ic;
+#pragma unroll 1
+            for (int g = 0; g < NG; ++g) {
+                constexpr int JGc = JG;
+                const int j0 = N <= 5 ? 0 : g == 0 ? C - 1 : g == 1 ? 0 : C + 2;
+                const int nj = N <= 5 ? N : g == 0 ? 3 : g == 1 ? C - 1 : N - C - 2;
+                const int jc = C - j0;  // the centre column within group 0
+                float wx[JGc][kPatch];
 #pragma unroll
-            for (int q = 0; q < NN; ++q) {
-                float2 v = eta[q];
-                if (FLOOR) {
-                    v.x = fmaxf(v.x, kEtaFloor);
-                    v.y = fmaxf(v.y, kEtaFloor);
+                for (int jj = 0; jj < JGc; ++jj)
+#pragma unroll
+                    for (int c = 0; c < kPatch; ++c) wx[jj][c] = jj < nj ? s_wx[(j0 + jj) * kPatch + c] : 0.0f;
+                float2 eta[N * JGc];
+#pragma unroll
+                for (int q = 0; q < N * JGc; ++q) eta[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int r = 0; r < kPatch; ++r) {
+                    if (r < ph) {
+                        float2 seg[kPatch];
+#pragma unroll
+                        for (int c = 0; c < kPatch; ++c)
+                            seg[c] = c < pw && ANTS_IN_RANGE(L.dbg, ((long)(iy0 + r) * sy + ix0 + c) * n_pairs + pp,
+                                                             (long)(L.n_int[1] + 3) * sy * n_pairs, 201)
+                                         ? __ldg(base + (r * row_step + c * n_pairs))
+                                         : make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int jj = 0; jj < JGc; ++jj) {
+                            if (jj < nj) {
+                                float2 T = make_float2(0.0f, 0.0f);
+#pragma unroll
+                                for (int c = 0; c < kPatch; ++c) T = ffma2(make_float2(wx[jj][c], wx[jj][c]), seg[c], T);
+#pragma unroll
+                                for (int k = 0; k < N; ++k) {
+                                    const float w = s_wy[r * N + k];
+                                    eta[k * JGc + jj] = ffma2(make_float2(w, w), T, eta[k * JGc + jj]);
+                                }
+                            }
+                        }
+                    }
                 }
-                float2 lg;
-                if (acc_log) {
-                    const float2 u = ffma2(v, ic, make_float2(-1.0f, -1.0f));
-                    far = far || fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne;
-                    lg = log2_1p_taylor(u);
-                } else {
-                    const float2 r2 = fmul2(v, ic);
-                    lg = make_float2(__log2f(r2.x), __log2f(r2.y));
+                if (g == 0) {  // the centre node (C, C) lies in the first group
+                    float2 ec = eta[C * JGc + jc];
+                    if (FLOOR) {
+                        ec.x = fmaxf(ec.x, kEtaFloor);
+                        ec.y = fmaxf(ec.y, kEtaFloor);
+                    }
+                    hc = mine ? ec.x + (2 * t + 1 < n_s ? ec.y : 0.0f) : 0.0f;
+                    ic = make_float2(__frcp_rn(ec.x), __frcp_rn(ec.y));
+                    nec = make_float2(-ec.x, -ec.y);
                 }
-                const float2 tt = fmul2(sp, lg);
-                const float2 d = fadd2(v, nec);
-                if (ANTS_IN_RANGE(L.dbg, (NN + q) * RS + t, Lay::wx(LT), 203)) {
-                    s_part[q * RS + t] = tt.x + tt.y;
-                    s_part[(NN + q) * RS + t] = mine ? d.x + d.y : 0.0f;
-                }
+                // the group's node terms, compiled once per log form (uniform per grid)
+                auto terms = [&](auto accurate) {
+                    constexpr bool ACC = decltype(accurate)::value;
+#pragma unroll
+                    for (int k = 0; k < N; ++k)
+#pragma unroll
+                        for (int jj = 0; jj < JGc; ++jj) {
+                            if (jj >= nj) continue;
+                            const int q = k * N + j0 + jj;
+                            float2 v = eta[k * JGc + jj];
+                            if (FLOOR) {
+                                v.x = fmaxf(v.x, kEtaFloor);
+                                v.y = fmaxf(v.y, kEtaFloor);
+                            }
+                            float2 lg;
+                            if (ACC) {
+                                const float2 u = ffma2(v, ic, make_float2(-1.0f, -1.0f));
+                                far = far || fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne;
+                                lg = log2_1p_taylor(u);
+                            } else {
+                                const float2 r2 = fmul2(v, ic);
+                                lg = make_float2(__log2f(r2.x), __log2f(r2.y));
+                            }
+                            const float2 tt = fmul2(sp, lg);
+                            const float2 d = fadd2(v, nec);
+                            if (ANTS_IN_RANGE(L.dbg, (NN + q) * RS + t, Lay::wx(LT), 203)) {
+                                s_part[q * RS + t] = tt.x + tt.y;
+                                s_part[(NN + q) * RS + t] = mine ? d.x + d.y : 0.0f;
+                            }
+                        }
+                };
+                if (acc_log) terms(std::true_type{});
+                else terms(std::false_type{});
             }
             if (acc_log && __any_sync(kFull, far)) {
-                // rare: redo the nodes whose |u| is beyond the Taylor range
-                // (unrolled: eta stays in registers)
-#pragma unroll
+                // rare: some |u| beyond the Taylor range; recompute this lane's
+                // pair at every node (per node, 16 coefficients) and redo those
+                // nodes' log terms with the hardware log2
+#pragma unroll 1
                 for (int q = 0; q < NN; ++q) {
-                    float2 v = eta[q];
+                    const int k = q / N, jj = q - k * N;
+                    const float xn = fminf(fmaxf(fmaf((float)(jj - C), sxy, cx), L.lo[0]), L.hi[0]);
+                    const float yn = fminf(fmaxf(fmaf((float)(k - C), sxy, cy), L.lo[1]), L.hi[1]);
+                    float2 v = pair_eta(L, L.coef2, pp, xn, yn);
                     if (FLOOR) {
                         v.x = fmaxf(v.x, kEtaFloor);
                         v.y = fmaxf(v.y, kEtaFloor);
@@ -922,12 +954,13 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
     }
 }
 
-// the patch kernel serves an XY LRF whose table stays in global memory, with
-// at most 128 sensor pairs, when every grid of the search touches at most
-// kPatch coefficients per axis
+// the patch kernel serves 5 x 5 and 7 x 7 grids on an XY LRF whose table stays
+// in global memory, with at most 128 sensor pairs, when every grid of the
+// search touches at most kPatch coefficients per axis
 bool patch_fits(const ants_lrf *lrf, const ants_cgs_params &p)
 {
-    if (!lrf->dev.coef2_pf || p.n_xy != 5 || lrf->dev.n_pairs > 128 || !(p.shrink > 0.0f && p.shrink <= 1.0f))
+    if (!lrf->dev.coef2_pf || (p.n_xy != 5 && p.n_xy != 7) || lrf->dev.n_pairs > 128 ||
+        !(p.shrink > 0.0f && p.shrink <= 1.0f))
         return false;
     // a range of R covers at most floor(R/h) + 2 spans: patch <= floor(R/h) + 5
     const double R = (double)(p.n_xy - 1) * p.step_xy;
@@ -954,13 +987,13 @@ int launch_patch(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
     return ANTS_OK;
 }
 
-template <bool FLOOR>
-int launch_patch_n5(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
+template <int N, bool FLOOR>
+int launch_patch_n(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
 {
     const int np = a.L.n_pairs;
-    if (np <= 32) return launch_patch<5, 1, FLOOR>(ctx, a, stream);
-    if (np <= 64) return launch_patch<5, 2, FLOOR>(ctx, a, stream);
-    return launch_patch<5, 4, FLOOR>(ctx, a, stream);
+    if (np <= 32) return launch_patch<N, 1, FLOOR>(ctx, a, stream);
+    if (np <= 64) return launch_patch<N, 2, FLOOR>(ctx, a, stream);
+    return launch_patch<N, 4, FLOOR>(ctx, a, stream);
 }
 
 template <int N, int TEAM>
@@ -1042,7 +1075,10 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     // tables too large for shared memory: small grids take the patch kernel
     const size_t table_bytes = (size_t)lrf->dev.n_pairs * lrf->dev.pair_stride * sizeof(float2);
     if (table_bytes + 4096 > ctx->smem_optin && patch_fits(lrf, p))
-        return floor_needed ? launch_patch_n5<true>(ctx, a, stream) : launch_patch_n5<false>(ctx, a, stream);
+        return p.n_xy == 5 ? (floor_needed ? launch_patch_n<5, true>(ctx, a, stream)
+                                           : launch_patch_n<5, false>(ctx, a, stream))
+                           : (floor_needed ? launch_patch_n<7, true>(ctx, a, stream)
+                                           : launch_patch_n<7, false>(ctx, a, stream));
     switch (p.n_xy) {
     case 5: return launch_nt<5, 1>(ctx, a, floor_needed, stream);
     case 7: return launch_nt<7, 1>(ctx, a, floor_needed, stream);

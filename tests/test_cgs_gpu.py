@@ -228,20 +228,21 @@ def test_cgs_xy_table_in_global_memory(torch_cuda, ctx):
     print(stats)
 
 
-@pytest.mark.parametrize("side,pitch,n_int,step", [(16, 3.2, 32, 0.5), (15, 3.2, 30, 0.3), (10, 6.0, 48, 0.5),
-                                                  (7, 6.0, 48, 0.4)])
-def test_cgs_xy_patch_kernel(torch_cuda, ctx, side, pitch, n_int, step):
-    """5 x 5 grids on a coefficient table larger than shared memory take the
-    patch kernel (a team of warps per event, one sensor pair per lane): 16 x 16
-    and 15 x 15 SiPMs (teams of four warps; 15 x 15 is odd: one padding
-    sensor), 10 x 10 (two warps) and 7 x 7 (one warp, odd) on fine knot grids;
-    starts near the sources, on the edges and in the corners of the field of
-    view, and a zero-signal event."""
+@pytest.mark.parametrize("side,pitch,n_int,n_xy,step", [
+    (16, 3.2, 32, 5, 0.5), (15, 3.2, 30, 5, 0.3), (10, 6.0, 48, 5, 0.5), (7, 6.0, 48, 5, 0.4),
+    (16, 3.2, 32, 7, 0.8 / 3), (15, 3.2, 30, 7, 0.25), (10, 6.0, 48, 7, 0.3), (7, 6.0, 48, 7, 0.25)])
+def test_cgs_xy_patch_kernel(torch_cuda, ctx, side, pitch, n_int, n_xy, step):
+    """5 x 5 and 7 x 7 grids on a coefficient table larger than shared memory
+    take the patch kernel (a team of warps per event, one sensor pair per lane;
+    7 x 7 grids in three groups of columns): 16 x 16 and 15 x 15 SiPMs (teams
+    of four warps; 15 x 15 is odd: one padding sensor), 10 x 10 (two warps) and
+    7 x 7 (one warp, odd) on fine knot grids; starts near the sources, on the
+    edges and in the corners of the field of view, and a zero-signal event."""
     sxy = synth.square_array(side, pitch)
     half = 0.5 * pitch * side
     w = synth.workloads.sipm16x16_xy().with_(
         name=f"sipm{side}x{side}", sensor_xy=sxy, gains=synth.sensor_gains(side * side, 0.05, 9 + side),
-        lo=(-half, -half), hi=(half, half), n_int=(n_int, n_int), n_xy=5, iters=4, step_xy=step,
+        lo=(-half, -half), hi=(half, half), n_int=(n_int, n_int), n_xy=n_xy, iters=4, step_xy=step,
         event=dict(region="square", extent=half - 0.5 * pitch, e0=2000.0))
     L = oracle_lrf(w)
     _, det, lrf, p = gpu_objects(w, L, ctx)
@@ -263,7 +264,7 @@ def test_cgs_xy_patch_kernel(torch_cuda, ctx, side, pitch, n_int, step):
     gpu = run_gpu(torch_cuda, ctx, lrf, p, sig, start=start)
     assert gpu["status"][7] == 2
     stats = compare(w, L, sig, gpu, start=start)
-    print(side, n_int, step, stats)
+    print(side, n_int, n_xy, step, stats)
     assert stats["tie_frac"] < 0.05
 
 
