@@ -18,12 +18,13 @@
 //   acc += s log2(eta / eta_c),  dH += eta - eta_c,
 // and F = acc - S log2(1 + dH / H_c) is the Poisson log-likelihood with the
 // energy E = S/H profiled out (Sec. 5.1.2.2), up to a per-event constant.
-// On grids narrower than half a knot interval the nodes' scores differ by
-// less than the error of the hardware log2 near 1 (about 2^-22 absolute per
+// On grids narrower than a quarter of a knot interval the nodes' scores differ
+// by less than the error of the hardware log2 near 1 (about 2^-22 absolute per
 // term) plus the rounding of eta/eta_c to single precision; there the term is
 // log2(1 + u) with u = fma(eta, 1/eta_c, -1) (one rounding of the small
-// difference) and a degree-6 Taylor polynomial, exact to 1e-9 for |u| <= 1/16
-// (larger |u| falls back to the hardware log2).  The rounding of 1/eta_c
+// difference) and a degree-5 Taylor polynomial (truncation below 1.5e-8 for
+// |u| <= 1/16, below 2e-11 for the |u| <= 0.02 such grids see; larger |u|
+// falls back to the hardware log2).  The rounding of 1/eta_c
 // shifts every node of a grid by the same s log2(1 + d) and cancels in the
 // argmax.
 // Lanes store per-(node, slot) partial sums in shared memory; one thread per
@@ -78,29 +79,17 @@ __device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
 }
 
 // log2(1 + u) for both lanes of a pair: Taylor series sum_k (-1)^(k+1) u^k /
-// (k ln 2) to degree 6 (truncation below 8e-10 for |u| <= 1/16), the hardware
-// log2 of 1 + u beyond that; every lane of the warp calls it together
+// (k ln 2) to degree 5 (truncation below 1.5e-8 for |u| <= 1/16); the callers
+// record an |u| beyond that and redo those terms with the hardware log2
 constexpr float kNearOne = 0.0625f;
 __device__ __forceinline__ float2 log2_1p_taylor(float2 u)
 {
-    float2 p = ffma2(u, make_float2(-0.24044917348149393f, -0.24044917348149393f),
-                     make_float2(0.28853900817779268f, 0.28853900817779268f));
-    p = ffma2(p, u, make_float2(-0.36067376022224085f, -0.36067376022224085f));
+    float2 p = ffma2(u, make_float2(0.28853900817779268f, 0.28853900817779268f),
+                     make_float2(-0.36067376022224085f, -0.36067376022224085f));
     p = ffma2(p, u, make_float2(0.48089834696298783f, 0.48089834696298783f));
     p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
     p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
     return fmul2(p, u);
-}
-
-__device__ __forceinline__ float2 log2_1p_pair(float2 u)
-{
-    float2 p = log2_1p_taylor(u);
-    // a warp-uniform branch: the hardware log2 is issued only when a lane needs it
-    if (__any_sync(kFull, fabsf(u.x) > kNearOne || fabsf(u.y) > kNearOne)) {
-        if (fabsf(u.x) > kNearOne) p.x = __log2f(1.0f + u.x);
-        if (fabsf(u.y) > kNearOne) p.y = __log2f(1.0f + u.y);
-    }
-    return p;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -358,6 +347,9 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             const unsigned rowb = (unsigned)sy * 8u;  // bytes per table row
             // the sweep is compiled twice, with the hardware log2 of eta/eta_c
             // and with the accurate log2(1 + u); the choice is uniform per grid
+            // with the accurate log, `far` records an |u| beyond the Taylor range
+            // (then the warp sweeps again with the hardware log2)
+            bool far = false;
             auto sweep = [&](auto accurate) {
                 constexpr bool ACC = decltype(accurate)::value;
                 for (int g = 0; g < group_end; g += kPPL) {
@@ -436,7 +428,9 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                             }
                             float2 lg;
                             if (ACC) {
-                                lg = log2_1p_pair(ffma2(eta, ic[m], make_float2(-1.0f, -1.0f)));
+                                const float2 u = ffma2(eta, ic[m], make_float2(-1.0f, -1.0f));
+                                far = far || fmaxf(fabsf(u.x), fabsf(u.y)) > kNearOne;
+                                lg = log2_1p_taylor(u);
                             } else {
                                 const float2 r = fmul2(eta, ic[m]);
                                 lg = make_float2(__log2f(r.x), __log2f(r.y));
@@ -472,8 +466,14 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                     }
                 }
             };
-            if (sxy * (float)C <= a.prec_halfwidth) sweep(std::true_type{});
-            else sweep(std::false_type{});
+            if (sxy * (float)C <= a.prec_halfwidth) {
+                sweep(std::true_type{});
+                // rare: a lane met an |u| beyond the Taylor range; this warp's
+                // partial sums are rewritten from the start with the hardware log2
+                if (__any_sync(kFull, far)) sweep(std::false_type{});
+            } else {
+                sweep(std::false_type{});
+            }
             team_sync<TEAM>(team);
 
             // ---- phase 3: node scores and team argmax --------------------------
@@ -1058,9 +1058,11 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     a.iters = p.iters;
     a.shrink = p.shrink;
     a.step_xy = p.step_xy;
-    // half a knot interval (the smaller axis): on such grids the LRF changes
-    // by a few per cent at most between a node and the centre
-    a.prec_halfwidth = 0.5f * fminf(1.0f / lrf->dev.inv_h[0], 1.0f / lrf->dev.inv_h[1]);
+    // a quarter of a knot interval (the smaller axis): on such grids the LRF
+    // changes by a few per cent at most between a node and the centre, and the
+    // last two grids of a halving search are the ones whose nodes' scores are
+    // close enough for the logarithm's error to decide the argmax
+    a.prec_halfwidth = 0.25f * fminf(1.0f / lrf->dev.inv_h[0], 1.0f / lrf->dev.inv_h[1]);
     a.sig = sig;
     a.n_e = n_e;
     a.start = start;
