@@ -133,6 +133,31 @@ __device__ __forceinline__ float2 pair_eta(const LrfDev &L, const float2 *coef2,
     return f;
 }
 
+// eta of both sensors of pair p at one point inside the box, from the
+// pair-fastest copy (lanes taking consecutive pairs read contiguous runs)
+__device__ __forceinline__ float2 pair_eta_pf(const LrfDev &L, int p, float x, float y)
+{
+    float tx, ty, wx[4], wy[4];
+    const int jx = bs_span(x, L.lo[0], L.inv_h[0], L.n_int[0], tx);
+    const int jy = bs_span(y, L.lo[1], L.inv_h[1], L.n_int[1], ty);
+    bs_weights(tx, wx);
+    bs_weights(ty, wy);
+    const int np = L.n_pairs;
+    const float2 *c = L.coef2_pf + ((size_t)jy * L.stride_y + jx) * np + p;
+    float2 f = make_float2(0.0f, 0.0f);
+    const long n_tab = (long)np * L.pair_stride, hi_i = ((long)(jy + 3) * L.stride_y + jx + 3) * np + p;
+    if (!ANTS_IN_RANGE(L.dbg, hi_i, n_tab, 105)) return f;
+    const int rs = L.stride_y * np;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float2 fr = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fr = ffma2(make_float2(wx[a], wx[a]), __ldg(c + b * rs + a * np), fr);
+        f = ffma2(make_float2(wy[b], wy[b]), fr, f);
+    }
+    return f;
+}
+
 // x-contracted row: sum_b wx[b] C[r][ix+b] for both sensors of a pair;
 // `g` / `sa` address C[r][ix] (global pointer / shared byte address)
 template <bool SMEM>
@@ -752,31 +777,41 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                 float2 eta[N * JGc];
 #pragma unroll
                 for (int q = 0; q < N * JGc; ++q) eta[q] = make_float2(0.0f, 0.0f);
+                // the patch rows, compiled for each patch width (4, 5 or 6 columns;
+                // uniform per grid): only the columns the grid touches are read
+                // and contracted
+                auto rows = [&](auto width) {
+                    constexpr int PW = decltype(width)::value;
 #pragma unroll
-                for (int r = 0; r < kPatch; ++r) {
-                    if (r < ph) {
-                        float2 seg[kPatch];
+                    for (int r = 0; r < kPatch; ++r) {
+                        if (r < ph) {
+                            float2 seg[PW];
 #pragma unroll
-                        for (int c = 0; c < kPatch; ++c)
-                            seg[c] = c < pw && ANTS_IN_RANGE(L.dbg, ((long)(iy0 + r) * sy + ix0 + c) * n_pairs + pp,
-                                                             (long)(L.n_int[1] + 3) * sy * n_pairs, 201)
-                                         ? __ldg(base + (r * row_step + c * n_pairs))
-                                         : make_float2(0.0f, 0.0f);
+                            for (int c = 0; c < PW; ++c)
+                                seg[c] = ANTS_IN_RANGE(L.dbg, ((long)(iy0 + r) * sy + ix0 + c) * n_pairs + pp,
+                                                       (long)(L.n_int[1] + 3) * sy * n_pairs, 201)
+                                             ? __ldg(base + (r * row_step + c * n_pairs))
+                                             : make_float2(0.0f, 0.0f);
 #pragma unroll
-                        for (int jj = 0; jj < JGc; ++jj) {
-                            if (jj < nj) {
-                                float2 T = make_float2(0.0f, 0.0f);
+                            for (int jj = 0; jj < JGc; ++jj) {
+                                if (jj < nj) {
+                                    float2 T = make_float2(0.0f, 0.0f);
 #pragma unroll
-                                for (int c = 0; c < kPatch; ++c) T = ffma2(make_float2(wx[jj][c], wx[jj][c]), seg[c], T);
+                                    for (int c = 0; c < PW; ++c)
+                                        T = ffma2(make_float2(wx[jj][c], wx[jj][c]), seg[c], T);
 #pragma unroll
-                                for (int k = 0; k < N; ++k) {
-                                    const float w = s_wy[r * N + k];
-                                    eta[k * JGc + jj] = ffma2(make_float2(w, w), T, eta[k * JGc + jj]);
+                                    for (int k = 0; k < N; ++k) {
+                                        const float w = s_wy[r * N + k];
+                                        eta[k * JGc + jj] = ffma2(make_float2(w, w), T, eta[k * JGc + jj]);
+                                    }
                                 }
                             }
                         }
                     }
-                }
+                };
+                if (pw <= 4) rows(std::integral_constant<int, 4>{});
+                else if (pw == 5) rows(std::integral_constant<int, 5>{});
+                else rows(std::integral_constant<int, kPatch>{});
                 if (g == 0) {  // the centre node (C, C) lies in the first group
                     float2 ec = eta[C * JGc + jc];
                     if (FLOOR) {
@@ -911,7 +946,7 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
         float H = 0.0f, ll = 0.0f;
         float2 v = make_float2(kEtaFloor, kEtaFloor);
         if (mine) {
-            v = pair_eta(L, L.coef2, t, cx, cy);
+            v = pair_eta_pf(L, t, cx, cy);
             v.x = fmaxf(v.x, kEtaFloor);
             v.y = fmaxf(v.y, kEtaFloor);
             H = v.x + (2 * t + 1 < n_s ? v.y : 0.0f);
