@@ -220,48 +220,82 @@ __device__ __forceinline__ bool ahead_of(float x, int ox, float w, int d, const 
     return x > w || (x == w && ox < gidx(order, d));
 }
 
-// insert (x, column n) into the descending list (tv, tn); entries past the
-// k-th are kept but never reported
-__device__ __forceinline__ void reg_insert(float (&tv)[kMaxTop], int (&tn)[kMaxTop], float x, int n, const int *order)
+// The running top-K of a row is an unsorted list: slots j < K hold entries
+// (value tv, column tn; empty: -inf, -1), slots j >= K hold +inf and are never
+// the worst.  Only the worst entry is tracked (slot wj, value thr, column
+// thr_n); a candidate that ranks ahead of it replaces it.  The list is sorted
+// once, when the row is written.
+
+// replace slot wj by (x, n)
+__device__ __forceinline__ void list_replace(float (&tv)[kMaxTop], int (&tn)[kMaxTop], int wj, float x, int n)
 {
-    int p = 0;  // entries that stay ahead of x
-    bool tie = false;
 #pragma unroll
     for (int j = 0; j < kMaxTop; ++j) {
-        p += tv[j] > x ? 1 : 0;
-        tie = tie || tv[j] == x;
-    }
-    if (tie) {  // equal values rank by grid index (loaded only then)
-        const int ox = gidx(order, n);
-        p = 0;
-#pragma unroll
-        for (int j = 0; j < kMaxTop; ++j) p += (tv[j] > x || (tv[j] == x && gidx(order, tn[j]) < ox)) ? 1 : 0;
-    }
-#pragma unroll
-    for (int j = kMaxTop - 1; j >= 0; --j) {
-        const float pv = j > 0 ? tv[j - 1] : x;
-        const int pn = j > 0 ? tn[j - 1] : n;
-        tv[j] = j > p ? pv : (j == p ? x : tv[j]);
-        tn[j] = j > p ? pn : (j == p ? n : tn[j]);
+        const bool h = j == wj;
+        tv[j] = h ? x : tv[j];
+        tn[j] = h ? n : tn[j];
     }
 }
 
-// entry k-1 of a register list, by masking (a select chain on k would be
-// turned into an indexed local-memory load)
-__device__ __forceinline__ float kth(const float (&t)[kMaxTop], int k)
+// the worst entry: the smallest value, among equal values the largest grid
+// index (the empty marker -1 ranks last); grid indices are loaded only when
+// several entries share the smallest value
+__device__ __forceinline__ void list_worst(const float (&tv)[kMaxTop], const int (&tn)[kMaxTop], const int *order,
+                                           int &wj, float &thr, int &thr_n)
 {
-    uint32_t r = 0;
+    float wv = tv[0];
 #pragma unroll
-    for (int j = 0; j < kMaxTop; ++j) r |= __float_as_uint(t[j]) & (0u - (uint32_t)(j == k - 1));
-    return __uint_as_float(r);
+    for (int j = 1; j < kMaxTop; ++j) wv = fminf(wv, tv[j]);
+    int w = 0, wn = tn[0];
+    bool found = false, tie = false;
+#pragma unroll
+    for (int j = 0; j < kMaxTop; ++j) {
+        const bool eq = tv[j] == wv;
+        tie = tie || (eq && found);
+        w = (eq && !found) ? j : w;
+        wn = (eq && !found) ? tn[j] : wn;
+        found = found || eq;
+    }
+    if (tie) {
+        int wg = -1;
+#pragma unroll
+        for (int j = 0; j < kMaxTop; ++j)
+            if (tv[j] == wv) {
+                const int g = gidx(order, tn[j]);
+                if (g > wg) {
+                    wg = g;
+                    w = j;
+                    wn = tn[j];
+                }
+            }
+    }
+    wj = w;
+    thr = wv;
+    thr_n = wn;
 }
 
-__device__ __forceinline__ int kth(const int (&t)[kMaxTop], int k)
+// sort the list for output: value descending, grid index ascending; slots
+// j >= k (unused) go last; g receives the grid indices (empty: 0x7fffffff)
+__device__ __forceinline__ void list_sort(float (&tv)[kMaxTop], int (&g)[kMaxTop], const int (&tn)[kMaxTop], int k,
+                                          const int *order)
 {
-    uint32_t r = 0;
 #pragma unroll
-    for (int j = 0; j < kMaxTop; ++j) r |= (uint32_t)t[j] & (0u - (uint32_t)(j == k - 1));
-    return (int)r;
+    for (int j = 0; j < kMaxTop; ++j) {
+        g[j] = j < k ? gidx(order, tn[j]) : 0x7fffffff;
+        if (j >= k) tv[j] = -INFINITY;
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxTop; ++r)
+#pragma unroll
+        for (int j = r & 1; j + 1 < kMaxTop; j += 2) {
+            const bool sw = tv[j + 1] > tv[j] || (tv[j + 1] == tv[j] && g[j + 1] < g[j]);
+            const float v0 = tv[j], v1 = tv[j + 1];
+            const int g0 = g[j], g1 = g[j + 1];
+            tv[j] = sw ? v1 : v0;
+            tv[j + 1] = sw ? v0 : v1;
+            g[j] = sw ? g1 : g0;
+            g[j + 1] = sw ? g0 : g1;
+        }
 }
 
 // ---- the kernel -------------------------------------------------------------
@@ -476,10 +510,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
             int tn[kMaxTop];
 #pragma unroll
             for (int q = 0; q < kMaxTop; ++q) {
-                tv[q] = -INFINITY;
+                tv[q] = q < a.topk ? -INFINITY : INFINITY;
                 tn[q] = -1;
             }
-            float thr = -INFINITY;  // k-th value so far
+            float thr = -INFINITY;  // the worst entry's value (the k-th so far) ...
+            int thr_n = -1, wj = 0;  // ... its column and slot
             if (EPI == EPI_TOPK && grp > 0) {
                 // group 0 has read this thread's list of the previous band
                 if (!(ok = bar_wait(mrg_empty, par ^ 1, abort, a.fault))) break;
@@ -532,9 +567,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                                     mask &= mask - 1;
                                     const float x = cand[q * kEpiThreads + et];
                                     const int n = n0 + q;
-                                    if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, kth(tn, a.topk)))) {
-                                        reg_insert(tv, tn, x, n, a.order);
-                                        thr = kth(tv, a.topk);
+                                    if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, thr_n))) {
+                                        list_replace(tv, tn, wj, x, n);
+                                        list_worst(tv, tn, a.order, wj, thr, thr_n);
                                     }
                                 }
                             }
@@ -621,16 +656,20 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                         for (int q = 0; q < a.topk; ++q) {
                             const float x = cand[q * kEpiThreads + et + 128 * g];
                             const int n = __float_as_int(cand[(kMaxTop + q) * kEpiThreads + et + 128 * g]);
-                            if (n >= 0 && ahead_of(x, gidx(a.order, n), kth(tv, a.topk), kth(tn, a.topk), a.order))
-                                reg_insert(tv, tn, x, n, a.order);
+                            if (n >= 0 && ahead_of(x, gidx(a.order, n), thr, thr_n, a.order)) {
+                                list_replace(tv, tn, wj, x, n);
+                                list_worst(tv, tn, a.order, wj, thr, thr_n);
+                            }
                         }
                     bar_arrive(mrg_empty);
+                    int gi[kMaxTop];
+                    list_sort(tv, gi, tn, a.topk, a.order);
                     if (m < a.M && ANTS_IN_RANGE(a.dbg, (long)m * a.topk + a.topk - 1, (long)a.M * a.topk, 307))
 #pragma unroll
                         for (int q = 0; q < kMaxTop; ++q)
                             if (q < a.topk) {
                                 a.top_val[(size_t)m * a.topk + q] = tv[q];
-                                a.top_idx[(size_t)m * a.topk + q] = tn[q] >= 0 ? gidx(a.order, tn[q]) : 0x7fffffff;
+                                a.top_idx[(size_t)m * a.topk + q] = gi[q];
                             }
                 }
             }
