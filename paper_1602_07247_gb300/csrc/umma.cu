@@ -47,7 +47,7 @@ namespace ants {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 3, kMaxK = 256, kMaxTop = 8;
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 2, kMaxK = 256, kMaxTop = 8;
 constexpr int kAChunks = kMaxK / kBK;
 constexpr int kLoaderWarp0 = 2, kEpiWarp0 = 6, kEpiWarps = 16;
 constexpr int kEpiGroups = kEpiWarps / 4, kGroupCols = kBN / kEpiGroups;  // 4 groups of 64 columns
@@ -64,7 +64,8 @@ constexpr uint32_t kOffA = 0;
 constexpr uint32_t kOffB = kOffA + kAChunks * kAChunkBytes;
 constexpr int kChunk = 32;                                                // columns staged per candidate pass
 constexpr uint32_t kOffCand = kOffB + kStages * kBStageBytes;             // staged values [kChunk][kEpiThreads]
-constexpr uint32_t kOffBar = kOffCand + kChunk * kEpiThreads * 4;
+constexpr uint32_t kOffThr = kOffCand + kChunk * kEpiThreads * 4;          // top-K thresholds [kEpiGroups][kBM]
+constexpr uint32_t kOffBar = kOffThr + kEpiGroups * kBM * 4;
 constexpr int kNumBars = 2 * kStages + 2 * kAChunks + 4 + 1 + 2;
 constexpr uint32_t kOffMisc = kOffBar + kNumBars * 8;                     // tmem base, abort flag
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;                     // + alignment slack
@@ -342,6 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (EPI == EPI_TOPK && threadIdx.x < kEpiGroups * kBM)
+        reinterpret_cast<float *>(smem + kOffThr)[threadIdx.x] = -INFINITY;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tmem_slot))
                      : "memory");
@@ -501,6 +504,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
         // of groups 1-3 leave their lists in their own slots (entry q: value in
         // row q, column in row kMaxTop + q) for the group-0 thread on that row
         float *cand = reinterpret_cast<float *>(smem + kOffCand);
+        // each row's four groups publish the value of their list's worst entry:
+        // a score below another group's is not in the row's top-K (that group
+        // holds K entries above it); stale values are lower, so still safe
+        volatile float *s_thr = reinterpret_cast<volatile float *>(smem + kOffThr);
+        const int my_thr = grp * kBM + row;
         int j = 0, it = 0;
         bool ok = true;
         for (int mt = blockIdx.x; mt < n_mt && ok; mt += gridDim.x, ++it) {
@@ -542,18 +550,22 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                     const int n0 = nt * kBN + col0;
                     if (EPI == EPI_TOPK) {
                         // candidates: values not below the k-th (ties are ranked
-                        // by grid index below)
+                        // by grid index below) nor below another group's k-th
+                        float tsh = thr;
+#pragma unroll
+                        for (int g2 = 0; g2 < kEpiGroups; ++g2)
+                            if (g2 != grp) tsh = fmaxf(tsh, s_thr[g2 * kBM + row]);
                         uint32_t mask = 0;
                         if (n0 + 32 <= a.N) {
 #pragma unroll
                             for (int q = 0; q < 32; ++q)
                                 asm("{ .reg .pred p; setp.ge.f32 p, %1, %2; @p or.b32 %0, %0, %3; }"
                                     : "+r"(mask)
-                                    : "f"(__uint_as_float(v[q])), "f"(thr), "r"(1u << q));
+                                    : "f"(__uint_as_float(v[q])), "f"(tsh), "r"(1u << q));
                         } else {
 #pragma unroll
                             for (int q = 0; q < 32; ++q)
-                                mask |= (n0 + q < a.N && __uint_as_float(v[q]) >= thr) ? (1u << q) : 0u;
+                                mask |= (n0 + q < a.N && __uint_as_float(v[q]) >= tsh) ? (1u << q) : 0u;
                         }
                         if (__any_sync(0xffffffffu, mask != 0)) {
 #pragma unroll
@@ -570,6 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                                     if (x > thr || (x == thr && gidx(a.order, n) < gidx(a.order, thr_n))) {
                                         list_replace(tv, tn, wj, x, n);
                                         list_worst(tv, tn, a.order, wj, thr, thr_n);
+                                        s_thr[my_thr] = thr;
                                     }
                                 }
                             }
@@ -640,6 +653,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
             }
             if (!ok) break;
             if (EPI == EPI_TOPK) {
+                // the row's thresholds start the next band at -inf: each group
+                // resets its own before the merge hand-off (which orders the
+                // groups' bands)
+                s_thr[my_thr] = -INFINITY;
                 // group 0 merges the lists of the other groups' threads on its row
                 if (grp > 0) {
 #pragma unroll
