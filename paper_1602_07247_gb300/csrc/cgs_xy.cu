@@ -44,7 +44,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
 constexpr float kInvLn2 = 1.4426950408889634f;
 constexpr int kXyThreads = 512;  // 16 warps per block, one block per SM
-constexpr int kPPL = 3;          // sensor pairs in flight per lane
 
 struct XyArgs {
     LrfDev L;
@@ -90,6 +89,17 @@ __device__ __forceinline__ float2 log2_1p_taylor(float2 u)
     p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
     p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
     return fmul2(p, u);
+}
+
+// log2 of a positive ratio by the hardware approximation, with subnormal
+// inputs flushed: the argument is first raised to the smallest normal float,
+// so a node whose LRF value lies more than 2^126 below the centre's keeps a
+// finite term (-126 per unit signal; a sensor without signal adds 0 either way)
+__device__ __forceinline__ float log2_ratio(float r)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(r, 1.17549435e-38f)));
+    return y;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -207,7 +217,7 @@ struct TeamSmem {
     __device__ __host__ int total(int N) const { return (red(N) + 32 + 3) & ~3; }
 };
 
-template <int N, int TEAM, bool SMEM, bool FLOOR>
+template <int N, int TEAM, int PPL, bool SMEM, bool FLOOR>
 __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int teams_per_block, int team_floats)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     const int pairs_mine = active ? (n_pairs - q + Q - 1) / Q : 0;  // pairs q, q+Q, ... below n_pairs
     // every lane runs the same number of pair groups (the shuffles of the
     // partial sums need the whole warp); missing pairs contribute zero
-    const int group_end = ((n_pairs + Q - 1) / Q + kPPL - 1) / kPPL * kPPL;
+    const int group_end = ((n_pairs + Q - 1) / Q + PPL - 1) / PPL * PPL;
     const float qnan = __int_as_float(0x7fc00000);
     const long team_stride = (long)gridDim.x * teams_per_block;
 
@@ -348,16 +358,28 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                 s_wy[2 * t + 1] = make_float4(w[2], w[2], w[3], w[3]);
                 s_iy[t] = iy;
             }
+            // grid rows inside the LRF box (the node scores below apply the
+            // same test): a contiguous range, the only rows swept
+            unsigned rows_in = 0;
+            if (wit == 0) {
+                const float y = fmaf((float)(lane - C), sxy, cy);
+                rows_in = __ballot_sync(kFull, lane < N && y >= L.lo[1] && y <= L.hi[1]);
+            }
             hc = warp_sum(hc);
             if (TEAM > 1) {
-                if (lane == 0) s_red[8 + wit] = hc;
+                if (lane == 0) {
+                    s_red[8 + wit] = hc;
+                    if (wit == 0) s_red[12] = __uint_as_float(rows_in);
+                }
                 team_sync<TEAM>(team);
                 hc = 0.0f;
                 for (int w = 0; w < TEAM; ++w) hc += s_red[8 + w];
+                rows_in = __float_as_uint(s_red[12]);
             } else {
                 __syncwarp();
             }
             const float inv_hc = __frcp_rn(hc);
+            const int k_first = rows_in ? __ffs(rows_in) - 1 : 0, k_last = rows_in ? 31 - __clz(rows_in) : -1;
 
             // ---- phase 2: each lane sums its column over its sensor pairs -----
             const float x = fmaf((float)(j - C), sxy, cx);
@@ -377,13 +399,13 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             bool far = false;
             auto sweep = [&](auto accurate) {
                 constexpr bool ACC = decltype(accurate)::value;
-                for (int g = 0; g < group_end; g += kPPL) {
-                    const float2 *gb[kPPL];
-                    unsigned sb[kPPL];
-                    float2 sp[kPPL], ic[kPPL], nec[kPPL];
-                    bool on[kPPL];
+                for (int g = 0; g < group_end; g += PPL) {
+                    const float2 *gb[PPL];
+                    unsigned sb[PPL];
+                    float2 sp[PPL], ic[PPL], nec[PPL];
+                    bool on[PPL];
     #pragma unroll
-                    for (int m = 0; m < kPPL; ++m) {
+                    for (int m = 0; m < PPL; ++m) {
                         on[m] = g + m < pairs_mine;
                         const int p = on[m] ? q + (g + m) * Q : 0;  // any valid pair when missing
                         gb[m] = coef2 + (size_t)p * L.pair_stride + ix;
@@ -392,21 +414,21 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                         ic[m] = s_ic2[p];
                         nec[m] = s_ec2[p];
                     }
-                    float2 W[kPPL][4];
-                    int top = s_iy[0];
+                    float2 W[PPL][4];
+                    int top = s_iy[k_first];
     #pragma unroll
-                    for (int m = 0; m < kPPL; ++m)
+                    for (int m = 0; m < PPL; ++m)
     #pragma unroll
                         for (int a4 = 0; a4 < 4; ++a4)
                             W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2, coef2, n_tab, L.dbg);
     #pragma unroll 1
-                    for (int k = 0; k < N; ++k) {
+                    for (int k = k_first; k <= k_last; ++k) {
                         const int iyk = s_iy[k];
                         const int adv = iyk - top;
                         const int r4 = top + 4;  // first row not yet in the window
                         if (adv == 1) {
     #pragma unroll
-                            for (int m = 0; m < kPPL; ++m) {
+                            for (int m = 0; m < PPL; ++m) {
                                 W[m][0] = W[m][1];
                                 W[m][1] = W[m][2];
                                 W[m][2] = W[m][3];
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                             }
                         } else if (adv == 2) {
     #pragma unroll
-                            for (int m = 0; m < kPPL; ++m) {
+                            for (int m = 0; m < PPL; ++m) {
                                 W[m][0] = W[m][2];
                                 W[m][1] = W[m][3];
                                 W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
@@ -422,7 +444,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                             }
                         } else if (adv == 3) {
     #pragma unroll
-                            for (int m = 0; m < kPPL; ++m) {
+                            for (int m = 0; m < PPL; ++m) {
                                 W[m][0] = W[m][3];
                                 W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
                                 W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                             }
                         } else if (adv >= 4) {
     #pragma unroll
-                            for (int m = 0; m < kPPL; ++m)
+                            for (int m = 0; m < PPL; ++m)
     #pragma unroll
                                 for (int a4 = 0; a4 < 4; ++a4)
                                     W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
@@ -442,7 +464,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                         const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
                         float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
     #pragma unroll
-                        for (int m = 0; m < kPPL; ++m) {
+                        for (int m = 0; m < PPL; ++m) {
                             float2 eta = fmul2(w0, W[m][0]);
                             eta = ffma2(w1, W[m][1], eta);
                             eta = ffma2(w2, W[m][2], eta);
@@ -458,7 +480,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                                 lg = log2_1p_taylor(u);
                             } else {
                                 const float2 r = fmul2(eta, ic[m]);
-                                lg = make_float2(__log2f(r.x), __log2f(r.y));
+                                lg = make_float2(log2_ratio(r.x), log2_ratio(r.y));
                             }
                             acc = ffma2(sp[m], lg, acc);
                             if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
@@ -843,7 +865,7 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                                 lg = log2_1p_taylor(u);
                             } else {
                                 const float2 r2 = fmul2(v, ic);
-                                lg = make_float2(__log2f(r2.x), __log2f(r2.y));
+                                lg = make_float2(log2_ratio(r2.x), log2_ratio(r2.y));
                             }
                             const float2 tt = fmul2(sp, lg);
                             const float2 d = fadd2(v, nec);
@@ -1031,7 +1053,7 @@ int launch_patch_n(const ants_ctx *ctx, const XyArgs &a, cudaStream_t stream)
     return launch_patch<N, 4, FLOOR>(ctx, a, stream);
 }
 
-template <int N, int TEAM>
+template <int N, int TEAM, int PPL>
 int launch_nt(const ants_ctx *ctx, const XyArgs &a, bool floor_needed, cudaStream_t stream)
 {
     constexpr int LT = 32 * TEAM;
@@ -1054,10 +1076,10 @@ int launch_nt(const ants_ctx *ctx, const XyArgs &a, bool floor_needed, cudaStrea
     cudaError_t e = cudaSuccess;
 #define ANTS_XY_LAUNCH(SM, FL)                                                                                 \
     do {                                                                                                       \
-        e = cudaFuncSetAttribute(cgs_xy_kernel<N, TEAM, SM, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+        e = cudaFuncSetAttribute(cgs_xy_kernel<N, TEAM, PPL, SM, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  (int)smem);                                                                   \
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cgs_xy)");                              \
-        cgs_xy_kernel<N, TEAM, SM, FL><<<(unsigned)blocks, kXyThreads, smem, stream>>>(a, teams, team_floats); \
+        cgs_xy_kernel<N, TEAM, PPL, SM, FL><<<(unsigned)blocks, kXyThreads, smem, stream>>>(a, teams, team_floats); \
     } while (0)
     if (smem_table) {
         if (floor_needed) ANTS_XY_LAUNCH(true, true);
@@ -1117,12 +1139,12 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
                            : (floor_needed ? launch_patch_n<7, true>(ctx, a, stream)
                                            : launch_patch_n<7, false>(ctx, a, stream));
     switch (p.n_xy) {
-    case 5: return launch_nt<5, 1>(ctx, a, floor_needed, stream);
-    case 7: return launch_nt<7, 1>(ctx, a, floor_needed, stream);
-    case 9: return launch_nt<9, 4>(ctx, a, floor_needed, stream);
-    case 11: return launch_nt<11, 4>(ctx, a, floor_needed, stream);
-    case 13: return launch_nt<13, 4>(ctx, a, floor_needed, stream);
-    default: return launch_nt<15, 4>(ctx, a, floor_needed, stream);
+    case 5: return launch_nt<5, 1, 3>(ctx, a, floor_needed, stream);
+    case 7: return launch_nt<7, 1, 3>(ctx, a, floor_needed, stream);
+    case 9: return launch_nt<9, 4, 3>(ctx, a, floor_needed, stream);
+    case 11: return launch_nt<11, 3, 4>(ctx, a, floor_needed, stream);
+    case 13: return launch_nt<13, 4, 3>(ctx, a, floor_needed, stream);
+    default: return launch_nt<15, 4, 3>(ctx, a, floor_needed, stream);
     }
 }
 
