@@ -51,7 +51,7 @@ int lrf_dims(int type)
 
 void *ctx_scratch(ants_ctx *ctx, int slot, size_t bytes)
 {
-    if (slot < 0 || slot >= 13) {
+    if (slot < 0 || slot >= kScratchSlots) {
         fail(ANTS_E_INTERNAL, "scratch slot %d", slot);
         return nullptr;
     }
@@ -186,7 +186,7 @@ ANTS_API void ants_ctx_destroy(ants_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_host_buffers(ctx);
-    for (int k = 0; k < 13; ++k) cudaFree(ctx->scratch[k]);
+    for (int k = 0; k < kScratchSlots; ++k) cudaFree(ctx->scratch[k]);
     cudaFree(ctx->d_fault);
     cudaFree(ctx->d_bounds);
     for (int k = 0; k < 2; ++k)
@@ -279,11 +279,18 @@ ANTS_API void ants_detector_free(ants_detector *det) { delete det; }
 static int upload_lrf(ants_lrf *L)
 {
     std::vector<float> c(L->coef.size()), xy(L->sxy.size()), g(L->n_s), w(L->n_s);
+    // positive: every coefficient > 0 and max <= 2^100 min, so every LRF value
+    // (between the smallest and the largest coefficient) is > 0 and every
+    // ratio of two values is a normal float
     int positive = 1;
+    float cmin = INFINITY, cmax = 0.0f;
     for (size_t k = 0; k < c.size(); ++k) {
         c[k] = (float)L->coef[k];
         if (!(c[k] > 0.0f)) positive = 0;
+        cmin = std::min(cmin, c[k]);
+        cmax = std::max(cmax, c[k]);
     }
+    if (positive && !(cmax <= std::ldexp(cmin, 100))) positive = 0;
     for (size_t k = 0; k < xy.size(); ++k) xy[k] = (float)L->sxy[k];
     for (int i = 0; i < L->n_s; ++i) {
         g[i] = (float)L->gain[i];

@@ -91,14 +91,19 @@ __device__ __forceinline__ float2 log2_1p_taylor(float2 u)
     return fmul2(p, u);
 }
 
-// log2 of a positive ratio by the hardware approximation, with subnormal
-// inputs flushed: the argument is first raised to the smallest normal float,
-// so a node whose LRF value lies more than 2^126 below the centre's keeps a
-// finite term (-126 per unit signal; a sensor without signal adds 0 either way)
+// log2 of a positive ratio by the hardware approximation, subnormal inputs
+// flushed.  Without the floor every LRF value lies between the smallest and
+// the largest coefficient (B-spline partition of unity), and the host takes
+// that path only when their ratio is at most 2^100, so every ratio of two
+// values is a normal float.  With the floor the argument is first raised to
+// the smallest normal float: a node whose value lies more than 2^126 below
+// the centre's keeps a finite term (a sensor without signal adds 0).
+template <bool FLOOR>
 __device__ __forceinline__ float log2_ratio(float r)
 {
     float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(r, 1.17549435e-38f)));
+    if (FLOOR) r = fmaxf(r, 1.17549435e-38f);
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r));
     return y;
 }
 
@@ -421,96 +426,105 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
     #pragma unroll
                         for (int a4 = 0; a4 < 4; ++a4)
                             W[m][a4] = trow<SMEM>(gb[m] + (top + a4) * sy, sb[m] + (unsigned)(top + a4) * rowb, wx2, coef2, n_tab, L.dbg);
-    #pragma unroll 1
-                    for (int k = k_first; k <= k_last; ++k) {
-                        const int iyk = s_iy[k];
-                        const int adv = iyk - top;
-                        const int r4 = top + 4;  // first row not yet in the window
-                        if (adv == 1) {
-    #pragma unroll
+                    // grids whose rows all share one window (the fine grids) skip
+                    // the window bookkeeping
+                    auto rows = [&](auto fixed_window) {
+                        constexpr bool FIXED = decltype(fixed_window)::value;
+        #pragma unroll 1
+                        for (int k = k_first; k <= k_last; ++k) {
+                            if (!FIXED) {
+                                const int iyk = s_iy[k];
+                                const int adv = iyk - top;
+                                const int r4 = top + 4;  // first row not yet in the window
+                                if (adv == 1) {
+            #pragma unroll
+                                    for (int m = 0; m < PPL; ++m) {
+                                        W[m][0] = W[m][1];
+                                        W[m][1] = W[m][2];
+                                        W[m][2] = W[m][3];
+                                        W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                    }
+                                } else if (adv == 2) {
+            #pragma unroll
+                                    for (int m = 0; m < PPL; ++m) {
+                                        W[m][0] = W[m][2];
+                                        W[m][1] = W[m][3];
+                                        W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                        W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
+                                    }
+                                } else if (adv == 3) {
+            #pragma unroll
+                                    for (int m = 0; m < PPL; ++m) {
+                                        W[m][0] = W[m][3];
+                                        W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                        W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
+                                        W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2, coef2, n_tab, L.dbg);
+                                    }
+                                } else if (adv >= 4) {
+            #pragma unroll
+                                    for (int m = 0; m < PPL; ++m)
+            #pragma unroll
+                                        for (int a4 = 0; a4 < 4; ++a4)
+                                            W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
+                                                                  wx2, coef2, n_tab, L.dbg);
+                                }
+                                top = iyk;
+                            }
+                            const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
+                            const float2 w0 = make_float2(wa.x, wa.y), w1 = make_float2(wa.z, wa.w);
+                            const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
+                            float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
+        #pragma unroll
                             for (int m = 0; m < PPL; ++m) {
-                                W[m][0] = W[m][1];
-                                W[m][1] = W[m][2];
-                                W[m][2] = W[m][3];
-                                W[m][3] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
+                                float2 eta = fmul2(w0, W[m][0]);
+                                eta = ffma2(w1, W[m][1], eta);
+                                eta = ffma2(w2, W[m][2], eta);
+                                eta = ffma2(w3, W[m][3], eta);
+                                if (FLOOR) {
+                                    eta.x = fmaxf(eta.x, kEtaFloor);
+                                    eta.y = fmaxf(eta.y, kEtaFloor);
+                                }
+                                float2 lg;
+                                if (ACC) {
+                                    const float2 u = ffma2(eta, ic[m], make_float2(-1.0f, -1.0f));
+                                    far = far || fmaxf(fabsf(u.x), fabsf(u.y)) > kNearOne;
+                                    lg = log2_1p_taylor(u);
+                                } else {
+                                    const float2 r = fmul2(eta, ic[m]);
+                                    lg = make_float2(log2_ratio<FLOOR>(r.x), log2_ratio<FLOOR>(r.y));
+                                }
+                                acc = ffma2(sp[m], lg, acc);
+                                if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
                             }
-                        } else if (adv == 2) {
-    #pragma unroll
-                            for (int m = 0; m < PPL; ++m) {
-                                W[m][0] = W[m][2];
-                                W[m][1] = W[m][3];
-                                W[m][2] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
-                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
-                            }
-                        } else if (adv == 3) {
-    #pragma unroll
-                            for (int m = 0; m < PPL; ++m) {
-                                W[m][0] = W[m][3];
-                                W[m][1] = trow<SMEM>(gb[m] + r4 * sy, sb[m] + (unsigned)r4 * rowb, wx2, coef2, n_tab, L.dbg);
-                                W[m][2] = trow<SMEM>(gb[m] + (r4 + 1) * sy, sb[m] + (unsigned)(r4 + 1) * rowb, wx2, coef2, n_tab, L.dbg);
-                                W[m][3] = trow<SMEM>(gb[m] + (r4 + 2) * sy, sb[m] + (unsigned)(r4 + 2) * rowb, wx2, coef2, n_tab, L.dbg);
-                            }
-                        } else if (adv >= 4) {
-    #pragma unroll
-                            for (int m = 0; m < PPL; ++m)
-    #pragma unroll
-                                for (int a4 = 0; a4 < 4; ++a4)
-                                    W[m][a4] = trow<SMEM>(gb[m] + (iyk + a4) * sy, sb[m] + (unsigned)(iyk + a4) * rowb,
-                                                          wx2, coef2, n_tab, L.dbg);
-                        }
-                        top = iyk;
-                        const float4 wa = s_wy[2 * k], wb = s_wy[2 * k + 1];
-                        const float2 w0 = make_float2(wa.x, wa.y), w1 = make_float2(wa.z, wa.w);
-                        const float2 w2 = make_float2(wb.x, wb.y), w3 = make_float2(wb.z, wb.w);
-                        float2 acc = make_float2(0.0f, 0.0f), dh = make_float2(0.0f, 0.0f);
-    #pragma unroll
-                        for (int m = 0; m < PPL; ++m) {
-                            float2 eta = fmul2(w0, W[m][0]);
-                            eta = ffma2(w1, W[m][1], eta);
-                            eta = ffma2(w2, W[m][2], eta);
-                            eta = ffma2(w3, W[m][3], eta);
-                            if (FLOOR) {
-                                eta.x = fmaxf(eta.x, kEtaFloor);
-                                eta.y = fmaxf(eta.y, kEtaFloor);
-                            }
-                            float2 lg;
-                            if (ACC) {
-                                const float2 u = ffma2(eta, ic[m], make_float2(-1.0f, -1.0f));
-                                far = far || fmaxf(fabsf(u.x), fabsf(u.y)) > kNearOne;
-                                lg = log2_1p_taylor(u);
-                            } else {
-                                const float2 r = fmul2(eta, ic[m]);
-                                lg = make_float2(log2_ratio(r.x), log2_ratio(r.y));
-                            }
-                            acc = ffma2(sp[m], lg, acc);
-                            if (on[m]) dh = fadd2(dh, fadd2(eta, nec[m]));
-                        }
-                        float va = acc.x + acc.y, vd = dh.x + dh.y;
-                        if (TEAM > 1) {
-                            // lanes l, l+N, l+2N, ... of a warp share grid column j:
-                            // lane l < N adds the lanes' own values
-                            const float a0 = va, d0 = vd;
-    #pragma unroll
-                            for (int o = N; o < 32; o += N) {
-                                const float xa = __shfl_down_sync(kFull, a0, o), xd = __shfl_down_sync(kFull, d0, o);
-                                if (lane + o < 32) {
-                                    va += xa;
-                                    vd += xd;
+                            float va = acc.x + acc.y, vd = dh.x + dh.y;
+                            if (TEAM > 1) {
+                                // lanes l, l+N, l+2N, ... of a warp share grid column j:
+                                // lane l < N adds the lanes' own values
+                                const float a0 = va, d0 = vd;
+        #pragma unroll
+                                for (int o = N; o < 32; o += N) {
+                                    const float xa = __shfl_down_sync(kFull, a0, o), xd = __shfl_down_sync(kFull, d0, o);
+                                    if (lane + o < 32) {
+                                        va += xa;
+                                        vd += xd;
+                                    }
                                 }
                             }
-                        }
-                        if ((TEAM == 1 || lane < N) &&
-                            ANTS_IN_RANGE(L.dbg, (N + k) * ps + (TEAM > 1 ? wit * N + j : t), 2 * N * ps, 104)) {
-                            const int slot = TEAM > 1 ? wit * N + j : t;
-                            float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
-                            if (g > 0) {
-                                va += *pa;
-                                vd += *pd;
+                            if ((TEAM == 1 || lane < N) &&
+                                ANTS_IN_RANGE(L.dbg, (N + k) * ps + (TEAM > 1 ? wit * N + j : t), 2 * N * ps, 104)) {
+                                const int slot = TEAM > 1 ? wit * N + j : t;
+                                float *pa = s_part + k * ps + slot, *pd = s_part + (N + k) * ps + slot;
+                                if (g > 0) {
+                                    va += *pa;
+                                    vd += *pd;
+                                }
+                                *pa = va;
+                                *pd = vd;
                             }
-                            *pa = va;
-                            *pd = vd;
                         }
-                    }
+                    };
+                    if (top == s_iy[k_last]) rows(std::true_type{});
+                    else rows(std::false_type{});
                 }
             };
             if (sxy * (float)C <= a.prec_halfwidth) {
@@ -865,7 +879,7 @@ __global__ void __launch_bounds__(kPatchThreads, 1) cgs_xy_patch_kernel(XyArgs a
                                 lg = log2_1p_taylor(u);
                             } else {
                                 const float2 r2 = fmul2(v, ic);
-                                lg = make_float2(log2_ratio(r2.x), log2_ratio(r2.y));
+                                lg = make_float2(log2_ratio<FLOOR>(r2.x), log2_ratio<FLOOR>(r2.y));
                             }
                             const float2 tt = fmul2(sp, lg);
                             const float2 d = fadd2(v, nec);
@@ -1128,8 +1142,9 @@ int launch_cgs_xy(const ants_ctx *ctx, const ants_lrf *lrf, const ants_cgs_param
     a.logL = logL;
     a.status = status;
     a.trace = trace;
-    // the floor is needed when an LRF value can be <= 0, or to neutralise the
-    // zero-coefficient padding sensor of an odd sensor count
+    // the floor is needed when an LRF value can be <= 0 or the coefficients
+    // span more than 2^100, or to neutralise the zero-coefficient padding
+    // sensor of an odd sensor count
     bool floor_needed = !lrf->dev.positive || (lrf->n_s & 1);
     // tables too large for shared memory: small grids take the patch kernel
     const size_t table_bytes = (size_t)lrf->dev.n_pairs * lrf->dev.pair_stride * sizeof(float2);

@@ -68,7 +68,7 @@ struct LrfDev {
     int n_int[3];      // intervals per axis
     int stride_y;      // n_int[0] + 3
     int stride_z;      // (n_int[0] + 3) * (n_int[1] + 3)
-    int positive;      // every coefficient > 0 (eta > 0 everywhere)
+    int positive;      // every coefficient > 0 and max <= 2^100 min (eta > 0, ratios normal)
     float lo[3], hi[3], inv_h[3];
     const float *coef; // [n_sets][n_coef] FP32
     const float *sxy;  // [n_s][2]
@@ -103,6 +103,8 @@ struct LrfDev {
 
 }  // namespace ants
 
+constexpr int kScratchSlots = 13;
+
 struct ants_ctx {
     int device = 0;
     int n_sm = 0;
@@ -119,8 +121,8 @@ struct ants_ctx {
     // 0 network activations, 1-6 precision and learned forms, 7 FP16
     // widening, 8-9 LRF fit, 10 refit samples, 11 event filter, 12 mapped
     // samples of symmetry classes
-    void *scratch[13] = {};
-    size_t scratch_cap[13] = {};
+    void *scratch[kScratchSlots] = {};
+    size_t scratch_cap[kScratchSlots] = {};
     // device word set by a kernel whose bounded wait ran out (ants_ctx_fault)
     int *d_fault = nullptr;
     // device word of the ANTS_DEBUG_BOUNDS build: the site of the first index
