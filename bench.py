@@ -65,13 +65,13 @@ def alu_roofline(evals_per_s: float, kind: str, verbose: bool = True) -> dict:
                             f"evaluation")
     return out
 # DRAM bytes (read + write) per event of the headline kernel, from one ncu
-# capture of it on 600 000 events of the same workload (156.00 MB read +
-# 9.51 MB written); None once the kernel changes.
-XY_TRAFFIC_PER_EVENT = (156001792 + 9511168) / 600_000
+# capture of it on 600 000 events of the same workload (156.12 MB read +
+# 10.44 MB written); None once the kernel changes.
+XY_TRAFFIC_PER_EVENT = (156121344 + 10440960) / 600_000
 # thread-instructions the headline kernel issues per (node, sensor)
 # evaluation (ncu smsp__thread_inst_executed.sum / evaluations of the same
-# capture: 1.1392e12 / (600 000 x 121 x 8 x 64)); None once the kernel changes
-XY_INST_PER_EVAL = 1139164678870 / (600_000 * 121 * 8 * 64)
+# capture: 8.7677e11 / (600 000 x 121 x 8 x 64)); None once the kernel changes
+XY_INST_PER_EVAL = 876769575801 / (600_000 * 121 * 8 * 64)
 
 
 def peaks():
