@@ -124,13 +124,28 @@ __device__ __forceinline__ uint64_t now_ns()
     return t;
 }
 
+// the same test, the thread suspended until the phase completes or about
+// kSuspendNs have passed (a waiting role then takes no issue slots from the
+// roles that work)
+constexpr uint32_t kSuspendNs = 20000;
+__device__ __forceinline__ bool bar_try_suspend(uint32_t b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(b), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
 // bounded wait; false once this or another role has given up
 __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int *abort, int *fault)
 {
     if (bar_try(b, parity)) return true;
     const uint64_t t0 = now_ns();
     while (true) {
-        if (bar_try(b, parity)) return true;
+        if (bar_try_suspend(b, parity)) return true;
         if (*abort) return false;
         if (now_ns() - t0 > kWaitNs) {
             *abort = 1;
@@ -144,7 +159,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile i
 __device__ __forceinline__ void bar_drain(uint32_t b, uint32_t parity, int *fault)
 {
     const uint64_t t0 = now_ns();
-    while (!bar_try(b, parity))
+    while (!bar_try_suspend(b, parity))
         if (now_ns() - t0 > kWaitNs) {
             atomicExch(fault, 1);
             return;
