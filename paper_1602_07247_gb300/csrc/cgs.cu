@@ -286,9 +286,15 @@ __device__ __forceinline__ float4 poly_at(const float4 *poly, unsigned saddr, in
 }
 
 // Scores of a radial-LRF grid, NPL nodes per lane at a time sharing each
-// sensor's data; per (node, sensor) the same operations in the same order as
-// node_score.  Updates the lane's best (score, node).  With SPOLY the
-// cubics are read from the block's shared copy `polys`.
+// sensor's data.  Sensors are taken in pairs with packed FP32x2 arithmetic
+// (each element as node_score computes it; the two halves of a node's sums
+// are added at the end), an odd last sensor on its own.  Updates the lane's
+// best (score, node).  With SPOLY the cubics are read from the block's shared
+// copy `polys`.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 template <int NPL, bool SPOLY>
 __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, const float *s_sig, const float *s_ic,
                                              const float *s_ec, float S, float inv_hc, float cx, float cy, float sxy,
@@ -296,46 +302,82 @@ __device__ __forceinline__ void radial_nodes(const CgsArgs &a, const LrfDev &L, 
 {
     const int c_xy = (a.n_xy - 1) / 2;
     const float hi = L.hi[0];
+    const float inv_h = L.inv_h[0];
+    const int n_int = L.n_int[0];
+    auto poly_of = [&](int i) { return polys + (L.shared ? 0 : (L.set_of ? __ldg(L.set_of + i) : i)) * n_int; };
     for (int k0 = 0; k0 < nodes; k0 += 32 * NPL) {
-        float xs[NPL], ys[NPL], acc[NPL], dh[NPL];
-        bool ok[NPL];
+        float xs[NPL], ys[NPL], rmax[NPL];
+        float2 acc[NPL], dh[NPL];
 #pragma unroll
         for (int m = 0; m < NPL; ++m) {
             const int k = k0 + lane + 32 * m;
             const int ix = k % a.n_xy, iy = (k / a.n_xy) % a.n_xy;
             xs[m] = fmaf((float)(ix - c_xy), sxy, cx);
             ys[m] = fmaf((float)(iy - c_xy), sxy, cy);
-            acc[m] = dh[m] = 0.0f;
-            ok[m] = true;
+            acc[m] = dh[m] = make_float2(0.0f, 0.0f);
+            rmax[m] = 0.0f;
         }
-        const float inv_h = L.inv_h[0];
-        const int n_int = L.n_int[0];
-        for (int i = 0; i < L.n_s; ++i) {
+        const float2 inv_h2 = make_float2(inv_h, inv_h);
+        const int n_pair = L.n_s >> 1;
+        for (int pr = 0; pr < n_pair; ++pr) {
+            const int i = 2 * pr;
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(L.sxy) + pr);  // x_i y_i x_i+1 y_i+1
+            const float2 nsx = make_float2(-q.x, -q.z), nsy = make_float2(-q.y, -q.w);
+            const float2 si = make_float2(s_sig[i], s_sig[i + 1]), ici = make_float2(s_ic[i], s_ic[i + 1]);
+            const float2 neci = make_float2(-s_ec[i], -s_ec[i + 1]);
+            const float2 gi = __ldg(reinterpret_cast<const float2 *>(L.gain) + pr);
+            const float4 *p0 = poly_of(i), *p1 = poly_of(i + 1);
+            const unsigned sp0 = SPOLY ? (unsigned)__cvta_generic_to_shared(p0) : 0u;
+            const unsigned sp1 = SPOLY ? (unsigned)__cvta_generic_to_shared(p1) : 0u;
+#pragma unroll
+            for (int m = 0; m < NPL; ++m) {
+                const float2 dx = fadd2(make_float2(xs[m], xs[m]), nsx);
+                const float2 dy = fadd2(make_float2(ys[m], ys[m]), nsy);
+                const float2 r2 = ffma2(dx, dx, fmul2(dy, dy));
+                const float2 r = fmul2(r2, make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f))));
+                rmax[m] = fmaxf(rmax[m], fmaxf(r.x, r.y));
+                // the span and local parameter of radial_profile
+                const float2 u = fmul2(make_float2(fminf(r.x, hi), fminf(r.y, hi)), inv_h2);
+                const int j0 = min((int)u.x, n_int - 1), j1 = min((int)u.y, n_int - 1);
+                const float2 t = fadd2(u, make_float2(-(float)j0, -(float)j1));
+                const float4 c0 = poly_at<SPOLY>(p0, sp0, j0), c1 = poly_at<SPOLY>(p1, sp1, j1);
+                float2 f = ffma2(t, make_float2(c0.w, c1.w), make_float2(c0.z, c1.z));
+                f = ffma2(t, f, make_float2(c0.y, c1.y));
+                f = ffma2(t, f, make_float2(c0.x, c1.x));
+                float2 eta = fmul2(gi, f);
+                eta = make_float2(fmaxf(eta.x, kEtaFloor), fmaxf(eta.y, kEtaFloor));
+                const float2 rr = fmul2(eta, ici);
+                acc[m] = ffma2(si, make_float2(__log2f(rr.x), __log2f(rr.y)), acc[m]);
+                dh[m] = fadd2(dh[m], fadd2(eta, neci));
+            }
+        }
+        if (L.n_s & 1) {
+            const int i = L.n_s - 1;
             const float sx = __ldg(L.sxy + 2 * i), sy = __ldg(L.sxy + 2 * i + 1);
             const float si = s_sig[i], ici = s_ic[i], eci = s_ec[i];
             const float gi = __ldg(L.gain + i);
-            const float4 *poly = polys + (L.shared ? 0 : (L.set_of ? __ldg(L.set_of + i) : i)) * n_int;
+            const float4 *poly = poly_of(i);
             const unsigned sp = SPOLY ? (unsigned)__cvta_generic_to_shared(poly) : 0u;
 #pragma unroll
             for (int m = 0; m < NPL; ++m) {
                 const float r = plane_dist(xs[m] - sx, ys[m] - sy);
-                ok[m] = ok[m] && r <= hi;
-                // the span and local parameter of radial_profile
+                rmax[m] = fmaxf(rmax[m], r);
                 const float u = fminf(r, hi) * inv_h;
                 const int j = min((int)u, n_int - 1);
                 const float t = u - (float)j;
                 const float4 pc = poly_at<SPOLY>(poly, sp, j);
                 const float f = fmaf(t, fmaf(t, fmaf(t, pc.w, pc.z), pc.y), pc.x);
                 const float eta = fmaxf(gi * f, kEtaFloor);
-                acc[m] = fmaf(si, __log2f(eta * ici), acc[m]);
-                dh[m] += eta - eci;
+                acc[m].x = fmaf(si, __log2f(eta * ici), acc[m].x);
+                dh[m].x += eta - eci;
             }
         }
 #pragma unroll
         for (int m = 0; m < NPL; ++m) {
             const int k = k0 + lane + 32 * m;
             if (k < nodes) {
-                const float F = ok[m] ? acc[m] - S * (log1pf(dh[m] * inv_hc) * 1.4426950408889634f) : -INFINITY;
+                const float A = acc[m].x + acc[m].y, D = dh[m].x + dh[m].y;
+                const float F = rmax[m] <= hi ? A - S * (log1pf(D * inv_hc) * 1.4426950408889634f) : -INFINITY;
                 if (F > bestF) {
                     bestF = F;
                     bestk = k;
