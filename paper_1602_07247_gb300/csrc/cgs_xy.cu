@@ -22,8 +22,8 @@
 // by less than the error of the hardware log2 near 1 (about 2^-22 absolute per
 // term) plus the rounding of eta/eta_c to single precision; there the term is
 // log2(1 + u) with u = fma(eta, 1/eta_c, -1) (one rounding of the small
-// difference) and a degree-5 Taylor polynomial (truncation below 1.5e-8 for
-// |u| <= 1/16, below 2e-11 for the |u| <= 0.02 such grids see; larger |u|
+// difference) and a degree-4 Taylor polynomial (truncation below 9e-9 for
+// |u| <= 1/32, below 1e-9 for the |u| <= 0.02 such grids see; larger |u|
 // falls back to the hardware log2).  The rounding of 1/eta_c
 // shifts every node of a grid by the same s log2(1 + d) and cancels in the
 // argmax.
@@ -78,14 +78,13 @@ __device__ __forceinline__ float2 ldc(const float2 *gptr, unsigned saddr)
 }
 
 // log2(1 + u) for both lanes of a pair: Taylor series sum_k (-1)^(k+1) u^k /
-// (k ln 2) to degree 5 (truncation below 1.5e-8 for |u| <= 1/16); the callers
+// (k ln 2) to degree 4 (truncation below 9e-9 for |u| <= 1/32); the callers
 // record an |u| beyond that and redo those terms with the hardware log2
-constexpr float kNearOne = 0.0625f;
+constexpr float kNearOne = 0.03125f;
 __device__ __forceinline__ float2 log2_1p_taylor(float2 u)
 {
-    float2 p = ffma2(u, make_float2(0.28853900817779268f, 0.28853900817779268f),
-                     make_float2(-0.36067376022224085f, -0.36067376022224085f));
-    p = ffma2(p, u, make_float2(0.48089834696298783f, 0.48089834696298783f));
+    float2 p = ffma2(u, make_float2(-0.36067376022224085f, -0.36067376022224085f),
+                     make_float2(0.48089834696298783f, 0.48089834696298783f));
     p = ffma2(p, u, make_float2(-0.72134752044448170f, -0.72134752044448170f));
     p = ffma2(p, u, make_float2(1.4426950408889634f, 1.4426950408889634f));
     return fmul2(p, u);
@@ -399,9 +398,9 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
             const unsigned rowb = (unsigned)sy * 8u;  // bytes per table row
             // the sweep is compiled twice, with the hardware log2 of eta/eta_c
             // and with the accurate log2(1 + u); the choice is uniform per grid
-            // with the accurate log, `far` records an |u| beyond the Taylor range
-            // (then the warp sweeps again with the hardware log2)
-            bool far = false;
+            // with the accurate log, `umax` tracks the largest |u| (beyond the
+            // Taylor range the warp sweeps again with the hardware log2)
+            float umax = 0.0f;
             auto sweep = [&](auto accurate) {
                 constexpr bool ACC = decltype(accurate)::value;
                 for (int g = 0; g < group_end; g += PPL) {
@@ -487,7 +486,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                                 float2 lg;
                                 if (ACC) {
                                     const float2 u = ffma2(eta, ic[m], make_float2(-1.0f, -1.0f));
-                                    far = far || fmaxf(fabsf(u.x), fabsf(u.y)) > kNearOne;
+                                    umax = fmaxf(umax, fmaxf(fabsf(u.x), fabsf(u.y)));
                                     lg = log2_1p_taylor(u);
                                 } else {
                                     const float2 r = fmul2(eta, ic[m]);
@@ -531,7 +530,7 @@ __global__ void __launch_bounds__(kXyThreads, 1) cgs_xy_kernel(XyArgs a, int tea
                 sweep(std::true_type{});
                 // rare: a lane met an |u| beyond the Taylor range; this warp's
                 // partial sums are rewritten from the start with the hardware log2
-                if (__any_sync(kFull, far)) sweep(std::false_type{});
+                if (__any_sync(kFull, umax > kNearOne)) sweep(std::false_type{});
             } else {
                 sweep(std::false_type{});
             }
