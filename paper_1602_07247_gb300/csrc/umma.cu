@@ -564,6 +564,20 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                     }
                     const int n0 = nt * kBN + col0;
                     if (EPI == EPI_TOPK) {
+                        // a band's first chunk fills the empty list with its first K
+                        // values directly; the others are candidates as usual
+                        uint32_t skip = 0;
+                        if (nt == 0 && h == 0 && n0 + 32 <= a.N) {
+#pragma unroll
+                            for (int q = 0; q < kMaxTop; ++q)
+                                if (q < a.topk) {
+                                    tv[q] = __uint_as_float(v[q]);
+                                    tn[q] = n0 + q;
+                                }
+                            list_worst(tv, tn, a.order, wj, thr, thr_n);
+                            s_thr[my_thr] = thr;
+                            skip = (1u << a.topk) - 1u;
+                        }
                         // candidates: values not below the k-th (ties are ranked
                         // by grid index below) nor below another group's k-th
                         float tsh = thr;
@@ -582,6 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_tn_kernel(const __grid_const
                             for (int q = 0; q < 32; ++q)
                                 mask |= (n0 + q < a.N && __uint_as_float(v[q]) >= tsh) ? (1u << q) : 0u;
                         }
+                        mask &= ~skip;
                         if (__any_sync(0xffffffffu, mask != 0)) {
 #pragma unroll
                             for (int q = 0; q < 32; ++q)
