@@ -65,13 +65,13 @@ def alu_roofline(evals_per_s: float, kind: str, verbose: bool = True) -> dict:
                             f"evaluation")
     return out
 # DRAM bytes (read + write) per event of the headline kernel, from one ncu
-# capture of it on 600 000 events of the same workload (156.12 MB read +
-# 10.44 MB written); None once the kernel changes.
-XY_TRAFFIC_PER_EVENT = (156121344 + 10440960) / 600_000
+# capture of it on 600 000 events of the same workload (156.46 MB read +
+# 10.98 MB written); None once the kernel changes.
+XY_TRAFFIC_PER_EVENT = (156464640 + 10975232) / 600_000
 # thread-instructions the headline kernel issues per (node, sensor)
 # evaluation (ncu smsp__thread_inst_executed.sum / evaluations of the same
-# capture: 8.7677e11 / (600 000 x 121 x 8 x 64)); None once the kernel changes
-XY_INST_PER_EVAL = 876769575801 / (600_000 * 121 * 8 * 64)
+# capture: 8.6601e11 / (600 000 x 121 x 8 x 64)); None once the kernel changes
+XY_INST_PER_EVAL = 866006665465 / (600_000 * 121 * 8 * 64)
 
 
 def peaks():
