@@ -7,7 +7,11 @@
 // (slot q = t / N, grid column j = t % N), Q = 32*TEAM / N.  Sensors are
 // interleaved in pairs (float2 coefficients), and slot q owns pairs
 // q, q+Q, q+2Q, ...; a lane processes them PPL at a time so that PPL
-// independent dependency chains are in flight.
+// independent dependency chains are in flight (11 x 11 grids: teams of three
+// warps, Q = 8, four pairs per lane, 88 of 96 lanes busy; a grid row's fixed
+// work is spread over eight evaluations per lane).  Only the grid rows inside
+// the LRF box are swept (the others score -inf), and grids whose rows all
+// share one 4-row window skip the window bookkeeping.
 //
 // Column trick: every node of column j shares x_j, so with
 //   T[r] = sum_b wx_j[b] C[r][ix_j + b]          (x-contracted row r)
@@ -43,7 +47,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kEtaFloor = 1e-30f;
 constexpr float kInvLn2 = 1.4426950408889634f;
-constexpr int kXyThreads = 512;  // 16 warps per block, one block per SM
+constexpr int kXyThreads = 512;  // 16 warps per block (teams that fit: 15 with 3-warp teams), one block per SM
 
 struct XyArgs {
     LrfDev L;
