@@ -197,7 +197,7 @@ def test_full_size_sampled(torch_cuda, ctx):
     assert rms < 2.0
 
 
-@pytest.mark.parametrize("n_xy", [5, 7, 9, 13, 15])
+@pytest.mark.parametrize("n_xy", [5, 7, 9, 11, 13, 15])
 @pytest.mark.parametrize("rows", [3, 4])
 def test_cgs_xy_grid_sizes_and_odd_sensor_counts(torch_cuda, ctx, n_xy, rows):
     """Every templated grid size of the separable XY kernel; 9 sensors (odd:
